@@ -1,0 +1,794 @@
+/*
+ * FP64 CPU oracle for the factorized shading-term bake of
+ * "Factorized Inverse Path Tracing" (Wu et al., ICCV 2023, arXiv 2304.05669).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the package smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no
+ * code, header, table or constant generator with the CUDA path, and the
+ * CUDA path never calls it.
+ *
+ * Everything here is the plain definition, written for a reader who checks
+ * it against the paper by eye:
+ *   - Philox4x32-10 counter-based RNG (Salmon et al., SC'11).
+ *   - Shading integrals of Eq. 6 with the Fresnel split of Eq. 7, estimated
+ *     by BRDF importance sampling (Sec. 6, stage 1) with the one-segment
+ *     cache query of Eq. 9: L_i = front-face L_e + L'(x1) at the first hit.
+ *   - Closest hit by brute force or by an independent top-down
+ *     spatial-median BVH; FP64 Moeller-Trumbore with inclusive edges.
+ *   - Morton codes and the binary radix tree over them (the bit-exact
+ *     targets for the device LBVH), built top-down by splitting each key
+ *     range at its highest differing bit.
+ *
+ * Compile with -ffp-contract=off: the Morton quantisation must be a chain
+ * of individually rounded IEEE double operations.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OPI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: */
+/* as easy as 1, 2, 3", SC'11).  Ten rounds; the key is bumped by the   */
+/* Weyl constants between rounds.                                       */
+/* ------------------------------------------------------------------ */
+static const uint32_t PHILOX_M0 = 0xD2511F53u, PHILOX_M1 = 0xCD9E8D57u;
+static const uint32_t PHILOX_W0 = 0x9E3779B9u, PHILOX_W1 = 0xBB67AE85u;
+
+static void philox10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out)
+{
+    for (int64_t i = 0; i < n; ++i) philox10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* A 32-bit output word -> uniform in [0,1): its top 24 bits times 2^-24. */
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------ */
+/* Small vector helpers                                                 */
+/* ------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return a[0]*b[0] + a[1]*b[1] + a[2]*b[2]; }
+static void cross3(const double a[3], const double b[3], double r[3])
+{
+    r[0] = a[1]*b[2] - a[2]*b[1];
+    r[1] = a[2]*b[0] - a[0]*b[2];
+    r[2] = a[0]*b[1] - a[1]*b[0];
+}
+static void sub3(const double a[3], const double b[3], double r[3]) { r[0]=a[0]-b[0]; r[1]=a[1]-b[1]; r[2]=a[2]-b[2]; }
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+static void normalize3(double a[3]) { double l = norm3(a); a[0] /= l; a[1] /= l; a[2] /= l; }
+
+/* ------------------------------------------------------------------ */
+/* Scene                                                                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double v0[3], v1[3], v2[3];
+    double e1[3], e2[3];
+    double ng[3];        /* (v1-v0) x (v2-v0), not normalised */
+    double area2;        /* |ng| = twice the area */
+    double h[3];         /* altitude onto the edge opposite vertex i */
+    double lo[3], hi[3]; /* bounding box */
+    double c[3];         /* box centre, used to split the BVH */
+} otri;
+
+typedef struct {
+    double lo[3], hi[3];
+    int left, right;     /* children, or -1 for a leaf */
+    int start, count;    /* triangle range in idx[] for a leaf */
+} onode;
+
+typedef struct {
+    int64_t T;
+    otri* tri;
+    double* Le;          /* T x 3 */
+    double* cache;       /* T x 3 */
+    onode* node;
+    int nnode;
+    int* idx;
+    double slo[3], shi[3]; /* scene box from float vertex min / max */
+    double L;              /* largest extent of the scene box */
+    double diag;           /* length of its diagonal */
+    double eps;            /* ray-origin offset, 1e-4 * L */
+} oscene;
+
+static int build_node(oscene* S, int start, int count, int* cap)
+{
+    if (S->nnode >= *cap) {
+        *cap *= 2;
+        S->node = (onode*)realloc(S->node, sizeof(onode) * (size_t)(*cap));
+    }
+    int id = S->nnode++;
+    onode nd;
+    for (int a = 0; a < 3; ++a) { nd.lo[a] = INFINITY; nd.hi[a] = -INFINITY; }
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = start; i < start + count; ++i) {
+        const otri* t = &S->tri[S->idx[i]];
+        for (int a = 0; a < 3; ++a) {
+            if (t->lo[a] < nd.lo[a]) nd.lo[a] = t->lo[a];
+            if (t->hi[a] > nd.hi[a]) nd.hi[a] = t->hi[a];
+            if (t->c[a] < clo[a]) clo[a] = t->c[a];
+            if (t->c[a] > chi[a]) chi[a] = t->c[a];
+        }
+    }
+    nd.left = nd.right = -1;
+    nd.start = start;
+    nd.count = count;
+    if (count > 4) {
+        int ax = 0;
+        for (int a = 1; a < 3; ++a) if (chi[a] - clo[a] > chi[ax] - clo[ax]) ax = a;
+        double mid = 0.5 * (clo[ax] + chi[ax]);
+        int i = start, j = start + count - 1;
+        while (i <= j) {                       /* partition about the midpoint */
+            if (S->tri[S->idx[i]].c[ax] < mid) ++i;
+            else { int tmp = S->idx[i]; S->idx[i] = S->idx[j]; S->idx[j] = tmp; --j; }
+        }
+        int nl = i - start;
+        if (nl == 0 || nl == count) nl = count / 2;   /* all centres equal: halve */
+        S->node[id] = nd;
+        int l = build_node(S, start, nl, cap);
+        int r = build_node(S, start + nl, count - nl, cap);
+        S->node[id].left = l;
+        S->node[id].right = r;
+        S->node[id].count = 0;
+        return id;
+    }
+    S->node[id] = nd;
+    return id;
+}
+
+oscene* oracle_scene_create(const float* V, int64_t nV, const int32_t* F, int64_t T,
+                            const float* Le, const float* cache)
+{
+    oscene* S = (oscene*)calloc(1, sizeof(oscene));
+    S->T = T;
+    S->tri = (otri*)calloc((size_t)(T > 0 ? T : 1), sizeof(otri));
+    S->Le = (double*)calloc((size_t)(3 * (T > 0 ? T : 1)), sizeof(double));
+    S->cache = (double*)calloc((size_t)(3 * (T > 0 ? T : 1)), sizeof(double));
+    float flo[3] = {INFINITY, INFINITY, INFINITY}, fhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nV; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (V[3*i+a] < flo[a]) flo[a] = V[3*i+a];
+            if (V[3*i+a] > fhi[a]) fhi[a] = V[3*i+a];
+        }
+    S->L = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        S->slo[a] = nV ? flo[a] : 0.0;
+        S->shi[a] = nV ? fhi[a] : 0.0;
+        if (S->shi[a] - S->slo[a] > S->L) S->L = S->shi[a] - S->slo[a];
+    }
+    double dg[3]; sub3(S->shi, S->slo, dg);
+    S->diag = norm3(dg);
+    S->eps = 1e-4 * S->L;
+    for (int64_t t = 0; t < T; ++t) {
+        otri* r = &S->tri[t];
+        for (int a = 0; a < 3; ++a) {
+            r->v0[a] = V[3*F[3*t+0]+a];
+            r->v1[a] = V[3*F[3*t+1]+a];
+            r->v2[a] = V[3*F[3*t+2]+a];
+        }
+        sub3(r->v1, r->v0, r->e1);
+        sub3(r->v2, r->v0, r->e2);
+        cross3(r->e1, r->e2, r->ng);
+        r->area2 = norm3(r->ng);
+        double e12[3]; sub3(r->v2, r->v1, e12);
+        double l0 = norm3(e12), l1 = norm3(r->e2), l2 = norm3(r->e1);
+        r->h[0] = l0 > 0 ? r->area2 / l0 : 0.0;
+        r->h[1] = l1 > 0 ? r->area2 / l1 : 0.0;
+        r->h[2] = l2 > 0 ? r->area2 / l2 : 0.0;
+        for (int a = 0; a < 3; ++a) {
+            r->lo[a] = fmin(r->v0[a], fmin(r->v1[a], r->v2[a]));
+            r->hi[a] = fmax(r->v0[a], fmax(r->v1[a], r->v2[a]));
+            r->c[a] = 0.5 * (r->lo[a] + r->hi[a]);
+        }
+        for (int a = 0; a < 3; ++a) {
+            S->Le[3*t+a] = Le ? Le[3*t+a] : 0.0;
+            S->cache[3*t+a] = cache ? cache[3*t+a] : 0.0;
+        }
+    }
+    S->idx = (int*)malloc(sizeof(int) * (size_t)(T > 0 ? T : 1));
+    for (int64_t t = 0; t < T; ++t) S->idx[t] = (int)t;
+    int cap = 1024;
+    S->node = (onode*)malloc(sizeof(onode) * (size_t)cap);
+    S->nnode = 0;
+    if (T > 0) build_node(S, 0, (int)T, &cap);
+    return S;
+}
+
+void oracle_scene_destroy(oscene* S)
+{
+    if (!S) return;
+    free(S->tri); free(S->Le); free(S->cache); free(S->node); free(S->idx); free(S);
+}
+
+void oracle_scene_info(const oscene* S, double* lo, double* hi, double* eps, double* L)
+{
+    for (int a = 0; a < 3; ++a) { lo[a] = S->slo[a]; hi[a] = S->shi[a]; }
+    *eps = S->eps;
+    *L = S->L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Closest hit                                                          */
+/* ------------------------------------------------------------------ */
+/* Line through o with direction d against the triangle's plane
+ * (Moeller-Trumbore in FP64).  Returns 0 when the ray is parallel to the
+ * plane.  lam = barycentric coordinates (weights of v0, v1, v2), cosabs =
+ * |cos| of the angle between d and the face normal. */
+static int tri_plane(const otri* tr, const double o[3], const double d[3],
+                     double* t, double lam[3], double* cosabs)
+{
+    double p[3], s[3], q[3];
+    cross3(d, tr->e2, p);
+    double det = dot3(tr->e1, p);
+    if (det == 0.0 || tr->area2 == 0.0) return 0;
+    double inv = 1.0 / det;
+    sub3(o, tr->v0, s);
+    double u = dot3(s, p) * inv;
+    cross3(s, tr->e1, q);
+    double v = dot3(d, q) * inv;
+    *t = dot3(tr->e2, q) * inv;
+    lam[0] = 1.0 - u - v; lam[1] = u; lam[2] = v;
+    *cosabs = fabs(dot3(d, tr->ng)) / (norm3(d) * tr->area2);
+    return 1;
+}
+
+/* One hit: triangle id (-1 = miss), distance, whether the ray meets the
+ * front face (d . n_g < 0), and whether that facing is within rounding of
+ * grazing (so a float32 evaluation may decide it either way). */
+typedef struct { int32_t id; double t; int front; int front_amb; } ohit;
+
+#define OMAXC 24
+typedef struct {
+    ohit nominal;        /* exact FP64 closest hit, ties by (t, id) */
+    int n;               /* candidates: hits a perturbed ray may report */
+    ohit c[OMAXC];
+    int miss_possible;   /* a perturbed ray may miss everything */
+    int overflow;        /* more candidates than OMAXC */
+} ocands;
+
+/* eta == 0: exact closest hit only.  eta > 0: additionally collect every
+ * triangle that a ray perturbed by about eta * (L + t) could report as its
+ * closest hit (see the header of oracle.py for the rule). */
+static void closest(const oscene* S, const double o[3], const double d[3], int32_t skip,
+                    double eta, ocands* out)
+{
+    out->nominal.id = -1; out->nominal.t = INFINITY; out->nominal.front = 0; out->nominal.front_amb = 0;
+    out->n = 0; out->miss_possible = 1; out->overflow = 0;
+    if (S->T == 0) return;
+    double inv[3];
+    for (int a = 0; a < 3; ++a) inv[a] = 1.0 / d[a];   /* +-inf for zero components */
+    const double dl = norm3(d);
+    const double mmax = eta * (S->L + S->diag);
+    const double pad = (eta > 0 ? 20.0 * mmax : 0.0) + 1e-9 * (S->L + 1.0);
+    double tc = INFINITY;      /* closest certain hit */
+    double bound = INFINITY;   /* no triangle beyond this can matter */
+    int stack[256];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const onode* nd = &S->node[stack[--sp]];
+        /* slab test against the padded box */
+        double t0 = -pad / (dl > 0 ? dl : 1.0), t1 = bound + pad;
+        int miss = 0;
+        for (int a = 0; a < 3; ++a) {
+            double lo = nd->lo[a] - pad, hi = nd->hi[a] + pad;
+            if (d[a] == 0.0) {
+                if (o[a] < lo || o[a] > hi) { miss = 1; break; }
+                continue;
+            }
+            double ta = (lo - o[a]) * inv[a], tb = (hi - o[a]) * inv[a];
+            if (ta > tb) { double tmp = ta; ta = tb; tb = tmp; }
+            if (ta > t0) t0 = ta;
+            if (tb < t1) t1 = tb;
+            if (t0 > t1) { miss = 1; break; }
+        }
+        if (miss) continue;
+        if (nd->count == 0) {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+            continue;
+        }
+        for (int k = nd->start; k < nd->start + nd->count; ++k) {
+            int id = S->idx[k];
+            if (id == skip) continue;
+            const otri* tr = &S->tri[id];
+            double t, lam[3], ca;
+            if (!tri_plane(tr, o, d, &t, lam, &ca)) continue;
+            int front = dot3(d, tr->ng) < 0.0;
+            /* exact hit: inclusive edges, t > 0 */
+            if (lam[0] >= 0 && lam[1] >= 0 && lam[2] >= 0 && t > 0) {
+                if (t < out->nominal.t || (t == out->nominal.t && id < out->nominal.id)) {
+                    out->nominal.id = id; out->nominal.t = t; out->nominal.front = front;
+                }
+            }
+            if (eta <= 0) continue;
+            double m = eta * (S->L + fabs(t));
+            double mp = m / (ca > 0.05 ? ca : 0.05);
+            int inflated = t > -m, certain = t > m;
+            for (int i = 0; i < 3; ++i) {
+                double dist = lam[i] * tr->h[i];
+                if (dist < -mp) inflated = 0;
+                if (dist < mp) certain = 0;
+            }
+            if (!inflated) continue;
+            if (certain && t < tc) {
+                tc = t;
+                bound = tc + eta * (S->L + tc);
+            }
+            if (out->n < OMAXC) {
+                ohit* h = &out->c[out->n++];
+                h->id = id; h->t = t; h->front = front;
+                h->front_amb = ca < 1e-5;
+            } else {
+                out->overflow = 1;
+            }
+        }
+    }
+    if (eta <= 0) { out->n = 0; out->miss_possible = out->nominal.id < 0; return; }
+    /* keep inflated hits that are not beyond the certain closest hit */
+    int w = 0;
+    for (int i = 0; i < out->n; ++i)
+        if (out->c[i].t <= bound) out->c[w++] = out->c[i];
+    out->n = w;
+    out->miss_possible = (tc == INFINITY);
+    if (out->nominal.id >= 0) {
+        const otri* tr = &S->tri[out->nominal.id];
+        out->nominal.front_amb = fabs(dot3(d, tr->ng)) / (dl * tr->area2) < 1e-5;
+    }
+}
+
+/* Brute-force closest hit over every triangle (exact FP64, ties by id). */
+static void closest_brute(const oscene* S, const double o[3], const double d[3], int32_t skip, ohit* h)
+{
+    h->id = -1; h->t = INFINITY; h->front = 0; h->front_amb = 0;
+    for (int64_t id = 0; id < S->T; ++id) {
+        if (id == skip) continue;
+        const otri* tr = &S->tri[id];
+        double t, lam[3], ca;
+        if (!tri_plane(tr, o, d, &t, lam, &ca)) continue;
+        if (lam[0] >= 0 && lam[1] >= 0 && lam[2] >= 0 && t > 0) {
+            if (t < h->t || (t == h->t && id < h->id)) {
+                h->id = (int32_t)id; h->t = t; h->front = dot3(d, tr->ng) < 0.0;
+            }
+        }
+    }
+}
+
+/* Public closest-hit query.  brute != 0 uses the brute-force loop (exact
+ * hit only; candidates left empty).  cand_* are nR x OMAXC. */
+int oracle_closest(const oscene* S, const double* orig, const double* dir, int64_t nR,
+                   const int32_t* skip, double eta, int brute,
+                   int32_t* hit_id, double* hit_t, int32_t* hit_front,
+                   int32_t* cand_id, double* cand_t, int32_t* n_cand,
+                   int32_t* miss_possible)
+{
+    for (int64_t r = 0; r < nR; ++r) {
+        const double* o = orig + 3 * r;
+        const double* d = dir + 3 * r;
+        int32_t sk = skip ? skip[r] : -1;
+        if (brute) {
+            ohit h;
+            closest_brute(S, o, d, sk, &h);
+            hit_id[r] = h.id; hit_t[r] = h.t; hit_front[r] = h.front;
+            if (n_cand) n_cand[r] = 0;
+            if (miss_possible) miss_possible[r] = h.id < 0;
+            continue;
+        }
+        ocands c;
+        closest(S, o, d, sk, eta, &c);
+        hit_id[r] = c.nominal.id; hit_t[r] = c.nominal.t; hit_front[r] = c.nominal.front;
+        if (n_cand) n_cand[r] = c.overflow ? -1 : c.n;
+        if (miss_possible) miss_possible[r] = c.miss_possible;
+        if (cand_id)
+            for (int i = 0; i < c.n; ++i) { cand_id[OMAXC*r+i] = c.c[i].id; cand_t[OMAXC*r+i] = c.c[i].t; }
+    }
+    return OMAXC;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sampling (Sec. 6: BRDF importance sampling in stage 1)               */
+/* ------------------------------------------------------------------ */
+/* Orthonormal basis (t, b, n) around a unit normal: Duff et al.,
+ * "Building an orthonormal basis, revisited", JCGT 2017. */
+static void onb(const double n[3], double t[3], double b[3])
+{
+    double s = copysign(1.0, n[2]);
+    double a = -1.0 / (s + n[2]);
+    double c = n[0] * n[1] * a;
+    t[0] = 1.0 + s * n[0] * n[0] * a; t[1] = s * c; t[2] = -s * n[0];
+    b[0] = c; b[1] = s + n[1] * n[1] * a; b[2] = -n[1];
+}
+
+static void to_world(const double t[3], const double b[3], const double n[3],
+                     double x, double y, double z, double w[3])
+{
+    for (int a = 0; a < 3; ++a) w[a] = x * t[a] + y * b[a] + z * n[a];
+}
+
+/* Smith-GGX masking for one direction with cosine mu to the normal
+ * (Walter et al. 2007, separable form), alpha2 = alpha^2. */
+static double smith_g1(double mu, double alpha2)
+{
+    return 2.0 * mu / (mu + sqrt(alpha2 + (1.0 - alpha2) * mu * mu));
+}
+
+/* ------------------------------------------------------------------ */
+/* Bake (Eq. 6, 7, 9)                                                   */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const oscene* S;
+    const float *qx, *qn, *qwo;
+    const int32_t* qtri;
+    int64_t N;
+    uint64_t seed;
+    uint32_t request_id, point_base;
+    int spp_d, spp_s, K;
+    const double* sigma;
+    double eta;
+    double *nominal, *lo, *hi;
+    int64_t* n_amb;
+    int64_t next;      /* work counter */
+} bake_job;
+
+/* Incident radiance for one hit: emission counted on the front face only,
+ * plus the per-triangle cache; a miss brings nothing. */
+static void radiance(const oscene* S, int32_t id, int front, double L[3])
+{
+    if (id < 0) { L[0] = L[1] = L[2] = 0.0; return; }
+    for (int a = 0; a < 3; ++a) L[a] = (front ? S->Le[3*id+a] : 0.0) + S->cache[3*id+a];
+}
+
+/* Range of the incident radiance over every hit a perturbed ray may report
+ * (candidates, both facings when grazing, and a miss when possible). */
+static int radiance_range(const oscene* S, const ocands* c, double Lmin[3], double Lmax[3])
+{
+    for (int a = 0; a < 3; ++a) { Lmin[a] = INFINITY; Lmax[a] = -INFINITY; }
+    int alts = 0;
+    double L[3];
+#define OR_ACC(id_, fr_) do { radiance(S, (id_), (fr_), L); ++alts; \
+        for (int a = 0; a < 3; ++a) { if (L[a] < Lmin[a]) Lmin[a] = L[a]; if (L[a] > Lmax[a]) Lmax[a] = L[a]; } } while (0)
+    OR_ACC(c->nominal.id, c->nominal.front);
+    if (c->nominal.id >= 0 && c->nominal.front_amb) OR_ACC(c->nominal.id, !c->nominal.front);
+    for (int i = 0; i < c->n; ++i) {
+        OR_ACC(c->c[i].id, c->c[i].front);
+        if (c->c[i].front_amb) OR_ACC(c->c[i].id, !c->c[i].front);
+    }
+    if (c->miss_possible) OR_ACC(-1, 0);
+#undef OR_ACC
+    int amb = 0;
+    for (int a = 0; a < 3; ++a) if (Lmin[a] != Lmax[a]) amb = 1;
+    if (c->overflow) {
+        /* Too many candidates to enumerate: bound by every value in the scene. */
+        for (int a = 0; a < 3; ++a) { Lmin[a] = 0.0; Lmax[a] = INFINITY; }
+        amb = 1;
+    }
+    return amb;
+}
+
+static void bake_point(bake_job* J, int64_t p)
+{
+    const oscene* S = J->S;
+    const int K = J->K;
+    const int W = 3 + 6 * K;
+    double* nom = J->nominal + (size_t)W * p;
+    double* lo = J->lo ? J->lo + (size_t)W * p : NULL;
+    double* hi = J->hi ? J->hi + (size_t)W * p : NULL;
+    int64_t amb_rays = 0;
+    for (int i = 0; i < W; ++i) { nom[i] = 0.0; if (lo) lo[i] = 0.0; if (hi) hi[i] = 0.0; }
+
+    double x[3], n[3], wo[3];
+    for (int a = 0; a < 3; ++a) { x[a] = J->qx[3*p+a]; n[a] = J->qn[3*p+a]; wo[a] = J->qwo[3*p+a]; }
+    normalize3(n);
+    normalize3(wo);
+    const int32_t skip = J->qtri[p];
+    double o[3];
+    for (int a = 0; a < 3; ++a) o[a] = x[a] + S->eps * n[a];
+    double tb[3], bb[3];
+    onb(n, tb, bb);
+    const double mu_o = dot3(n, wo);
+    const uint32_t key[2] = {(uint32_t)J->seed, (uint32_t)(J->seed >> 32)};
+    const uint32_t pid = J->point_base + (uint32_t)p;
+
+    /* Diffuse shading L_d (Eq. 6): cosine-weighted directions, pdf = cos/pi,
+     * so each sample contributes its incident radiance unweighted. */
+    for (int s = 0; s < J->spp_d; ++s) {
+        uint32_t ctr[4] = {pid, (uint32_t)s, 0u, J->request_id}, r[4];
+        philox10(ctr, key, r);
+        double u1 = u24(r[0]), u2 = u24(r[1]);
+        double rad = sqrt(u1), phi = 2.0 * OPI * u2;
+        double wi[3];
+        to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u1), wi);
+        ocands c;
+        closest(S, o, wi, skip, J->eta, &c);
+        double L[3];
+        radiance(S, c.nominal.id, c.nominal.front, L);
+        for (int a = 0; a < 3; ++a) nom[a] += L[a];
+        if (lo) {
+            double Lmin[3], Lmax[3];
+            amb_rays += radiance_range(S, &c, Lmin, Lmax);
+            for (int a = 0; a < 3; ++a) { lo[a] += Lmin[a]; hi[a] += Lmax[a]; }
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        nom[a] /= J->spp_d;
+        if (lo) { lo[a] /= J->spp_d; hi[a] /= J->spp_d; }
+    }
+
+    /* Specular shadings L_s0, L_s1 (Eq. 6, 7) per roughness level: GGX
+     * half-vector sampling with density D(h)(n.h) (Walter et al. 2007),
+     * reflected to wi; the estimator weight F*D*G/(4 n.wo) / pdf(wi) reduces
+     * to F * G * (wo.h) / ((n.wo)(n.h)).  Points seen at n.wo <= 1e-2 get 0. */
+    if (mu_o <= 1e-2) goto done;
+    for (int k = 0; k < K; ++k) {
+        const double alpha = J->sigma[k] * J->sigma[k];
+        const double a2 = alpha * alpha;
+        const double g1o = smith_g1(mu_o, a2);
+        double s0[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
+        double l0[3] = {0, 0, 0}, l1[3] = {0, 0, 0}, h0[3] = {0, 0, 0}, h1[3] = {0, 0, 0};
+        for (int s = 0; s < J->spp_s; ++s) {
+            uint32_t ctr[4] = {pid, (uint32_t)s, (uint32_t)(k + 1), J->request_id}, r[4];
+            philox10(ctr, key, r);
+            double u1 = u24(r[0]), u2 = u24(r[1]);
+            double cos2 = (1.0 - u1) / (1.0 + (a2 - 1.0) * u1);
+            double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2));
+            double phi = 2.0 * OPI * u2;
+            double h[3];
+            to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, h);
+            double c = dot3(wo, h);
+            double wi[3];
+            for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * h[a] - wo[a];
+            double mu_i = dot3(n, wi);
+            if (mu_i <= 0.0 || c <= 0.0) continue;     /* counts as a zero sample */
+            double G = smith_g1(mu_i, a2) * g1o;
+            double w = G * c / (mu_o * ch);
+            double F1 = pow(1.0 - c, 5.0);
+            double F0 = 1.0 - F1;
+            ocands cd;
+            closest(S, o, wi, skip, J->eta, &cd);
+            double L[3];
+            radiance(S, cd.nominal.id, cd.nominal.front, L);
+            for (int a = 0; a < 3; ++a) { s0[a] += L[a] * F0 * w; s1[a] += L[a] * F1 * w; }
+            if (lo) {
+                double Lmin[3], Lmax[3];
+                amb_rays += radiance_range(S, &cd, Lmin, Lmax);
+                for (int a = 0; a < 3; ++a) {
+                    l0[a] += Lmin[a] * F0 * w; h0[a] += Lmax[a] * F0 * w;
+                    l1[a] += Lmin[a] * F1 * w; h1[a] += Lmax[a] * F1 * w;
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            nom[3 + 3*k + a] = s0[a] / J->spp_s;
+            nom[3 + 3*K + 3*k + a] = s1[a] / J->spp_s;
+            if (lo) {
+                lo[3 + 3*k + a] = l0[a] / J->spp_s;  hi[3 + 3*k + a] = h0[a] / J->spp_s;
+                lo[3 + 3*K + 3*k + a] = l1[a] / J->spp_s;  hi[3 + 3*K + 3*k + a] = h1[a] / J->spp_s;
+            }
+        }
+    }
+done:
+    if (J->n_amb) J->n_amb[p] = amb_rays;
+}
+
+static void* bake_worker(void* arg)
+{
+    bake_job* J = (bake_job*)arg;
+    for (;;) {
+        int64_t p = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (p >= J->N) break;
+        bake_point(J, p);
+    }
+    return NULL;
+}
+
+/* Bake every query point.  Output row per point (length 3 + 6K):
+ *   [L_d rgb | L_s0(sigma_0..K-1) rgb | L_s1(sigma_0..K-1) rgb].
+ * nominal: the estimator on exact FP64 hits.  lo / hi (nullable, need
+ * eta > 0): the same estimator with every ray's incident radiance replaced
+ * by its minimum / maximum over the hits a perturbed ray may report.
+ * n_amb (nullable): per point, the number of rays with more than one
+ * possible radiance. */
+int oracle_bake(const oscene* S, const float* qx, const float* qn, const float* qwo,
+                const int32_t* qtri, int64_t N, uint64_t seed, uint32_t request_id,
+                uint32_t point_base, int spp_d, int spp_s, int K, const double* sigma,
+                double eta, int nthreads, double* nominal, double* lo, double* hi,
+                int64_t* n_amb)
+{
+    bake_job J;
+    J.S = S; J.qx = qx; J.qn = qn; J.qwo = qwo; J.qtri = qtri; J.N = N;
+    J.seed = seed; J.request_id = request_id; J.point_base = point_base;
+    J.spp_d = spp_d; J.spp_s = spp_s; J.K = K; J.sigma = sigma; J.eta = eta;
+    J.nominal = nominal; J.lo = (eta > 0) ? lo : NULL; J.hi = (eta > 0) ? hi : NULL;
+    J.n_amb = n_amb; J.next = 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    for (int i = 1; i < nthreads; ++i) pthread_create(&th[i], NULL, bake_worker, &J);
+    bake_worker(&J);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Pinhole first hits (query generation)                                */
+/* ------------------------------------------------------------------ */
+/* Camera row: eye xyz, forward xyz, up xyz, vertical fov (radians).
+ * right = normalize(fwd x up), up' = right x fwd; pixel (i, j) of a W x H
+ * image (j = 0 at the top) looks along
+ *   normalize(fwd + sx * right + sy * up'),
+ *   sx = (2 (i + 0.5) / W - 1) * tan(fov/2) * W / H,
+ *   sy = (1 - 2 (j + 0.5) / H) * tan(fov/2).
+ * Output per pixel p (view-major, then row, then column): query record
+ * x = eye + t d, n = unit face normal turned toward the camera, wo = -d,
+ * tri = hit triangle, valid = hit; plus the candidate count as in
+ * oracle_closest (n_cand = number of alternative hits, miss_possible). */
+int oracle_camera_queries(const oscene* S, const float* cams, int n_views, int W, int H,
+                          const int64_t* pixels, int64_t n_pix, double eta,
+                          double* qx, double* qn, double* qwo, int32_t* qtri,
+                          int32_t* n_cand, int32_t* cand_id, int32_t* miss_possible)
+{
+    for (int64_t k = 0; k < n_pix; ++k) {
+        int64_t p = pixels[k];
+        int v = (int)(p / ((int64_t)W * H));
+        if (v < 0 || v >= n_views) return -1;
+        int64_t rem = p % ((int64_t)W * H);
+        int j = (int)(rem / W), i = (int)(rem % W);
+        const float* c = cams + 10 * v;
+        double eye[3] = {c[0], c[1], c[2]}, fwd[3] = {c[3], c[4], c[5]}, up[3] = {c[6], c[7], c[8]};
+        normalize3(fwd);
+        double right[3], up2[3];
+        cross3(fwd, up, right); normalize3(right);
+        cross3(right, fwd, up2);
+        double th = tan(0.5 * (double)c[9]);
+        double sx = (2.0 * (i + 0.5) / W - 1.0) * th * ((double)W / H);
+        double sy = (1.0 - 2.0 * (j + 0.5) / H) * th;
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = fwd[a] + sx * right[a] + sy * up2[a];
+        normalize3(d);
+        ocands cd;
+        closest(S, eye, d, -1, eta, &cd);
+        qtri[k] = cd.nominal.id;
+        if (n_cand) n_cand[k] = cd.overflow ? -1 : cd.n;
+        if (miss_possible) miss_possible[k] = cd.miss_possible;
+        if (cand_id) for (int q = 0; q < cd.n; ++q) cand_id[OMAXC * k + q] = cd.c[q].id;
+        if (cd.nominal.id < 0) {
+            for (int a = 0; a < 3; ++a) { qx[3*k+a] = 0; qn[3*k+a] = 0; qwo[3*k+a] = 0; }
+            continue;
+        }
+        const otri* tr = &S->tri[cd.nominal.id];
+        double ng[3] = {tr->ng[0], tr->ng[1], tr->ng[2]};
+        normalize3(ng);
+        double sgn = dot3(ng, d) > 0 ? -1.0 : 1.0;
+        for (int a = 0; a < 3; ++a) {
+            qx[3*k+a] = eye[a] + cd.nominal.t * d[a];
+            qn[3*k+a] = sgn * ng[a];
+            qwo[3*k+a] = -d[a];
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Morton codes and the binary radix tree (bit-exact LBVH targets)      */
+/* ------------------------------------------------------------------ */
+/* Per triangle: box centre c = 0.5 * (double(min) + double(max)) per axis,
+ * quantised against the scene box [lo, hi] taken from the float vertices:
+ *   q = min(2^21 - 1, floor((c - lo) * (2^21 / (hi - lo))))   (q = 0 if hi == lo)
+ * with every operation a single IEEE double rounding.  Bit i of qx, qy, qz
+ * goes to bit 3i+2, 3i+1, 3i of the 63-bit code. */
+static uint64_t spread21(uint32_t v)
+{
+    uint64_t r = 0;
+    for (int i = 0; i < 21; ++i) r |= (uint64_t)((v >> i) & 1u) << (3 * i);
+    return r;
+}
+
+int oracle_morton(const float* V, int64_t nV, const int32_t* F, int64_t T, uint64_t* codes)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nV; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (V[3*i+a] < lo[a]) lo[a] = V[3*i+a];
+            if (V[3*i+a] > hi[a]) hi[a] = V[3*i+a];
+        }
+    for (int64_t t = 0; t < T; ++t) {
+        uint32_t q[3];
+        for (int a = 0; a < 3; ++a) {
+            float x0 = V[3*F[3*t+0]+a], x1 = V[3*F[3*t+1]+a], x2 = V[3*F[3*t+2]+a];
+            float mn = x0 < x1 ? x0 : x1; mn = mn < x2 ? mn : x2;
+            float mx = x0 > x1 ? x0 : x1; mx = mx > x2 ? mx : x2;
+            double c = 0.5 * ((double)mn + (double)mx);
+            double ext = (double)hi[a] - (double)lo[a];
+            if (!(ext > 0.0)) { q[a] = 0; continue; }
+            double scale = 2097152.0 / ext;
+            double f = floor((c - (double)lo[a]) * scale);
+            if (f < 0.0) f = 0.0;
+            if (f > 2097151.0) f = 2097151.0;
+            q[a] = (uint32_t)f;
+        }
+        codes[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    }
+    return 0;
+}
+
+/* Length of the common prefix of the augmented keys (code_i || i) and
+ * (code_j || j): 64-bit code, then 32-bit index. */
+static int prefix_len(const uint64_t* code, int64_t i, int64_t j)
+{
+    uint64_t x = code[i] ^ code[j];
+    if (x) return __builtin_clzll(x);
+    uint32_t y = (uint32_t)i ^ (uint32_t)j;
+    return 64 + (y ? __builtin_clz(y) : 32);
+}
+
+/* bit at position `pos` counted from the top of the 96-bit augmented key */
+static int key_bit(const uint64_t* code, int64_t i, int pos)
+{
+    if (pos < 64) return (int)((code[i] >> (63 - pos)) & 1u);
+    return (int)(((uint32_t)i >> (31 - (pos - 64))) & 1u);
+}
+
+typedef struct {
+    const uint64_t* code;
+    const float* box;     /* T x 6 triangle boxes in sorted order: lo xyz, hi xyz */
+    int32_t *first, *last, *split;
+    float* nbox;          /* (T-1) x 6 */
+    int64_t n;
+} rt_job;
+
+/* Radix-tree node over sorted keys [f, l], f < l: split after the last key
+ * whose bit at the first differing position is 0.  Writes node boxes as the
+ * float min / max over the triangles of the range (children first). */
+static void rt_build(rt_job* R, int64_t f, int64_t l, float out_box[6])
+{
+    if (f == l) {
+        for (int a = 0; a < 6; ++a) out_box[a] = R->box[6*f+a];
+        return;
+    }
+    int64_t id = R->n++;
+    int pos = prefix_len(R->code, f, l);
+    int64_t s = f;
+    while (s + 1 <= l && key_bit(R->code, s + 1, pos) == 0) ++s;
+    R->first[id] = (int32_t)f; R->last[id] = (int32_t)l; R->split[id] = (int32_t)s;
+    float bl[6], br[6];
+    rt_build(R, f, s, bl);
+    rt_build(R, s + 1, l, br);
+    for (int a = 0; a < 3; ++a) {
+        out_box[a] = bl[a] < br[a] ? bl[a] : br[a];
+        out_box[3+a] = bl[3+a] > br[3+a] ? bl[3+a] : br[3+a];
+    }
+    for (int a = 0; a < 6; ++a) R->nbox[6*id+a] = out_box[a];
+}
+
+/* codes: sorted Morton codes (ties in index order); tri_box: T x 6 boxes of
+ * the triangles in that order.  Output: T-1 internal nodes in pre-order. */
+int oracle_radix_tree(const uint64_t* codes, const float* tri_box, int64_t T,
+                      int32_t* first, int32_t* last, int32_t* split, float* node_box)
+{
+    if (T < 2) return 0;
+    rt_job R = {codes, tri_box, first, last, split, node_box, 0};
+    float root[6];
+    rt_build(&R, 0, T - 1, root);
+    return (int)R.n;
+}
