@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the factorized shading-term bake hot path on one GB300.
+
+Workload (default): the ~176k-triangle procedural room, 24 pinhole views
+at 320x208 whose first 2^20 hits are the query points, 128 samples per
+point for L_d and for each of the 6 roughness levels of L_s0/L_s1.  One
+step runs the whole path on device-resident inputs:
+
+  scene build (bounds, Morton, radix sort, Karras tree, pack, refit)
+  -> pinhole first hits -> compaction to 2^20 queries
+  -> bake of L_d, L_s0, L_s1 (N * S * (1 + K) = 939,524,096 rays)
+  -> factorized render forward (+ tone-mapped loss) and backward
+  -> per-triangle rendering error.
+
+value = rays per step / step time (Mrays/s); L2 is flushed between steps.
+The e2e figure repeats the steps through the same public calls with the
+inputs copied from pinned host memory and the tables, loss, gradients and
+per-triangle error copied back, all inside the timed region.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample.
+
+Run under torchrun for N > 1: every rank bakes its own batch (its own
+Philox request id), no collective on the data path; rank 0 prints one
+JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Mrays/s and shading-term points/s at 1e-4 rel. vs oracle; "
+          "served p50/p99 bake latency")
+SIGMA = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
+WORKLOADS = {
+    # name: scene, views, W, H, N, spp_d, spp_s, scene seed, view seed
+    "room": dict(scene="room", views=24, W=320, H=208, N=1 << 20, spp_d=128, spp_s=128,
+                 desc="procedural room 175,926 tris; 24 views 320x208; first 2^20 hits; "
+                      "128 spp; 6-level roughness grid"),
+    "cornell": dict(scene="cornell", views=4, W=64, H=64, N=4096, spp_d=64, spp_s=64,
+                    desc="Cornell box 36 tris; 4096 first hits; 64 spp"),
+    "floor": dict(scene="floor", views=16, W=512, H=512, N=1 << 22, spp_d=256, spp_s=256,
+                  desc="building floor 2,045,464 tris; 16 views 512x512; 2^22 hits; 256 spp"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-points", type=int, default=16384,
+                    help="points in the CPU-oracle sample (cpu_baseline)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(name):
+    from workloads import building_floor, cornell_box, procedural_room
+    if name == "room":
+        return procedural_room(1)
+    if name == "cornell":
+        return cornell_box(closed=True)
+    return building_floor(5)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for f in ("trace.cu", "fipt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2304_05669_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload):
+    """DRAM bytes per ray of the bake kernel from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "bake_%s_traffic.json" % workload)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_digest") != source_digest():
+        return None
+    return float(d["dram_bytes_per_ray"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1]:
+                continue
+            rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
+        pw = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(mesh, cams, W, H, npts, spp_d, spp_s, request_id=0):
+    """Oracle first hits of the first pixels (view-major order), then the
+    oracle bake of the first ``npts`` valid points.
+    Returns (rays, seconds, threads, points)."""
+    import oracle as O
+    S = O.OracleScene.from_mesh(mesh)
+    pix = np.arange(min(len(cams) * W * H, int(npts * 1.5) + 64))
+    cq = S.camera_queries(cams, W, H, pix)
+    ok = np.nonzero(cq["tri"] >= 0)[0][:npts]
+    q = {"x": cq["x"][ok].astype(np.float32), "n": cq["n"][ok].astype(np.float32),
+         "wo": cq["wo"][ok].astype(np.float32), "tri": cq["tri"][ok].astype(np.int32)}
+    threads = O.default_threads()
+    t0 = time.perf_counter()
+    S.bake(q, SIGMA, spp_d, spp_s, seed=0, request_id=request_id, nthreads=threads)
+    dt = time.perf_counter() - t0
+    rays = len(ok) * (spp_d + len(SIGMA) * spp_s)
+    return rays, dt, threads, len(ok)
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return
+    mesh = make_scene(wl["scene"])
+    from workloads import pinhole_views
+    cams = pinhole_views(mesh, wl["views"], seed=2)
+    npts = max(64, min(args.cpu_points, 2048))
+    for _ in range(args.warmup):
+        oracle_sample(mesh, cams, wl["W"], wl["H"], 64, wl["spp_d"], wl["spp_s"])
+    tot_rays, tot_t, threads, n = 0, 0.0, 1, 0
+    for s in range(args.steps):
+        r, dt, threads, n = oracle_sample(mesh, cams, wl["W"], wl["H"], npts, wl["spp_d"],
+                                          wl["spp_s"], request_id=s)
+        tot_rays += r
+        tot_t += dt
+    v = tot_rays / tot_t / 1e6
+    sample = "%d oracle first hits (first pixels of view 0) per step, %d+6x%d spp, FP64" % (n, wl["spp_d"], wl["spp_s"])
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mrays/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot_t / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": sample},
+        "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, wl, world, rank, local):
+    import torch
+    import paper_2304_05669_gb300 as F
+    from paper_2304_05669_gb300._native import lib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mesh = make_scene(wl["scene"])
+    from workloads import material_params, pinhole_views
+    cams = pinhole_views(mesh, wl["views"], seed=2)
+    N, W, H = wl["N"], wl["W"], wl["H"]
+    spp_d, spp_s = wl["spp_d"], wl["spp_s"]
+    K = len(SIGMA)
+    rays_per_step = N * (spp_d + K * spp_s)
+
+    host = {"V": mesh.V, "F": mesh.F, "Le": mesh.Le, "cache": mesh.cache, "cams": cams}
+    mp = material_params(N, seed=3)
+    gt = material_params(N, seed=4)
+    host.update({"albedo": mp["albedo"], "rough": mp["rough"], "metal": mp["metal"]})
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    dv = {k: v.to(dev) for k, v in pinned.items()}
+    gt_d = {k: torch.from_numpy(v).to(dev) for k, v in gt.items()}
+    stream = torch.cuda.current_stream()
+    ctx = F.context(local)
+    request_id = rank
+
+    def step(d, Lgt, ev=None):
+        sc = F.Scene(d["V"], d["F"], d["Le"], d["cache"], ctx=ctx)
+        qa, valid = sc.camera_queries(d["cams"], W, H)
+        q, _pix, _n = F.compact_queries(qa, valid, N)
+        if ev is not None:
+            ev[0].record(stream)
+        Ld, Ls0, Ls1 = F.bake(sc, q, SIGMA, spp_d, spp_s, seed=0, request_id=request_id)
+        if ev is not None:
+            ev[1].record(stream)
+        if Lgt is None:
+            return sc, (Ld, Ls0, Ls1), q
+        Lr, loss = F.render_fwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
+        grads = F.render_bwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
+        err, cnt = F.tri_error(q, Lr, Lgt, mesh.T)
+        return sc, (Ld, Ls0, Ls1), q, loss, grads, (err, cnt)
+
+    # ground-truth images for the render loss: the same tables rendered with
+    # a second set of material parameters (computed once, an input)
+    sc0, tabs0, q0 = step(dv, None)
+    Lgt = F.render_fwd(*tabs0, SIGMA, gt_d["albedo"], gt_d["rough"], gt_d["metal"])[0].clone()
+    n_valid = int(F.compact_queries(*sc0.camera_queries(dv["cams"], W, H), N)[2].item())
+    ctx.sync_status()
+    if n_valid < N:
+        raise RuntimeError("workload has only %d hits < %d" % (n_valid, N))
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(dv, Lgt)
+    torch.cuda.synchronize()
+
+    # -------------------------------------------------- timed: device-resident
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    ev_bake = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    launches0 = lib().fipt_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            ev_step[s][0].record(stream)
+            step(dv, Lgt, ev_bake[s])
+            ev_step[s][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = lib().fipt_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    bake_ms = [a.elapsed_time(b) for a, b in ev_bake]
+    t_total = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    ctx.sync_status()
+
+    # -------------------------------------------------- e2e: host in, host out
+    e2e = None
+    if not args.no_e2e:
+        out_host = None
+        in_keys = ["V", "F", "Le", "cache", "cams", "albedo", "rough", "metal"]
+        Lgt_host = Lgt.cpu().pin_memory()
+        h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in in_keys) \
+            + Lgt_host.numel() * 4
+        d2h = 0
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(args.steps):
+            d = {k: pinned[k].to(dev, non_blocking=True) for k in in_keys}
+            Lg = Lgt_host.to(dev, non_blocking=True)
+            _sc, (Ld, Ls0, Ls1), _q, loss, grads, (err, cnt) = step(d, Lg)
+            res = [Ld, Ls0, Ls1, loss, grads[0], grads[1], grads[2], err, cnt]
+            if out_host is None:
+                out_host = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
+            for h, r in zip(out_host, res):
+                h.copy_(r, non_blocking=True)
+            d2h = sum(r.numel() * r.element_size() for r in res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+        e2e = {"value": round(world * rays_per_step * args.steps / t_e2e / 1e6, 3),
+               "unit": "Mrays/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(1e3 * t_e2e / args.steps, 3)}
+
+    # -------------------------------------------------- roofline of the bake
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    F.bake(sc0, q0, SIGMA, spp_d, spp_s, seed=0, request_id=request_id, stats=stats)
+    ctx.sync_status()
+    n_rays, n_nodes, n_tris, max_depth = [int(x) for x in stats.cpu().tolist()]
+    bytes_per_ray = (64.0 * n_nodes + 48.0 * n_tris + 24.0 * n_rays) / max(n_rays, 1)
+    alg_bytes = bytes_per_ray * n_rays + N * (40 + 4 * 3 * (1 + 2 * K))
+    bake_s = float(np.mean(bake_ms)) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / bake_s / 1e9
+    traffic_per_ray = recorded_traffic(args.workload)
+
+    # -------------------------------------------------- CPU baseline (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, dt, threads, n = oracle_sample(mesh, cams, W, H, args.cpu_points, spp_d, spp_s)
+        cpu = {"value": round(r / dt / 1e6, 4), "unit": "Mrays/s", "cores": threads,
+               "kind": "oracle",
+               "sample": "%d oracle first hits (first pixels of view 0), %d+6x%d spp, FP64, %.1f s" %
+                         (n, spp_d, spp_s, dt)}
+
+    if rank != 0:
+        return
+    value = world * rays_per_step * args.steps / t_total / 1e6
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "scene_tris": mesh.T, "points": N,
+                   "spp_diffuse": spp_d, "spp_specular": spp_s, "roughness_levels": K,
+                   "rays_per_step": rays_per_step, "views": wl["views"], "resolution": [W, H],
+                   "l2": "flushed between steps (512 MB write outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "step": "scene build + first hits + compaction + bake + render fwd/bwd + "
+                           "per-triangle error"},
+        "points_per_s": round(world * N * args.steps / t_total, 1),
+        "bake_ms": round(1e3 * bake_s, 3),
+        "bake_mrays_per_s": round(rays_per_step / bake_s / 1e6, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": (round(traffic_per_ray * n_rays) if traffic_per_ray else None),
+                     "kernel": "k_bake", "peak_kind": peak_kind,
+                     "alg_bytes_per_ray": round(bytes_per_ray, 1),
+                     "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2),
+                     "tris_per_ray": round(n_tris / max(n_rays, 1), 2),
+                     "max_stack": max_depth},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+    else:
+        run_ours(args, wl, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

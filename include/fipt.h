@@ -1,0 +1,258 @@
+/*
+ * fipt.h -- C ABI of the GB300 bake of the factorized shading terms of
+ * "Factorized Inverse Path Tracing" (Wu et al., ICCV 2023, arXiv 2304.05669).
+ *
+ * The paper factors the material out of the rendering integral (Sec. 4.1,
+ * Eq. 5-7) so that three shading terms per surface point -- the diffuse
+ * shading L_d and the two specular shadings L_s0, L_s1 tabulated over a
+ * roughness grid (Eq. 8) -- can be baked once and reused by a cheap
+ * factorized render.  This library builds a BVH over a triangle mesh, bakes
+ * those terms by BRDF importance sampling with the one-segment cache query
+ * of Eq. 9 (Sec. 4.2, Sec. 6 stage 1), renders the factorized model with a
+ * tone-mapped loss (Eq. 14) and its gradient, and reduces the rendering
+ * error per triangle to locate emitters (Sec. 4.4).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns fipt_status; FIPT_OK is 0.  On failure a message is
+ *    kept per host thread and returned by fipt_last_error().
+ *  - Array arguments are DEVICE pointers on the context's device, owned by
+ *    the caller, contiguous, in the dtype and layout stated; they must be
+ *    4-byte aligned, and 16-byte aligned where stated.  Host pointers are
+ *    marked "host".  Nothing is allocated on the bake/render path: scratch
+ *    comes from caller workspaces sized by the *_workspace_size queries.
+ *  - Work is enqueued on the caller's stream and is asynchronous.  A kernel
+ *    that detects a bad state (traversal stack overflow) records a code in
+ *    the context's device status word instead of faulting; read and clear it
+ *    with fipt_sync_status().
+ *  - Sizes of 0 are valid and enqueue nothing.
+ */
+#ifndef FIPT_H
+#define FIPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fipt_status {
+    FIPT_OK = 0,
+    FIPT_ERR_INVALID_ARG = 1,   /* null / misaligned pointer, bad size or parameter */
+    FIPT_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    FIPT_ERR_WORKSPACE = 3,     /* the workspace passed is smaller than required */
+    FIPT_ERR_BUDGET = 4,        /* a request does not fit the server's memory budget */
+    FIPT_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
+    FIPT_ERR_DEVICE_CHECK = 6,  /* a kernel recorded a failed check (see fipt_sync_status) */
+    FIPT_ERR_NOT_FOUND = 7      /* unknown ticket / handle */
+} fipt_status;
+
+/* Device status codes written by kernels (bit flags). */
+#define FIPT_DEV_STACK_OVERFLOW 1   /* a traversal stack was full; that ray was cut short */
+#define FIPT_DEV_BAD_NODE 2         /* a BVH reference was out of range; that ray was stopped */
+#define FIPT_DEV_STEP_LIMIT 4       /* a walk exceeded the steps a valid tree allows; stopped */
+
+typedef void* fipt_stream;               /* a cudaStream_t; NULL = the legacy default stream */
+typedef struct fipt_ctx fipt_ctx;
+typedef struct fipt_scene fipt_scene;
+
+/* One surface query (40 bytes): the point x, its unit normal n on the side
+ * it is seen from, the unit viewing direction wo (n . wo > 0), and the index
+ * of the triangle x lies on (-1: none).  Sec. 3 / Eq. 2-4: one per camera
+ * ray (x, wo); Sec. 4.1: the shadings are baked per input-view pixel. */
+typedef struct fipt_query {
+    float x[3];
+    float n[3];
+    float wo[3];
+    int32_t tri;
+} fipt_query;
+
+#define FIPT_MAX_K 8
+
+/* Bake parameters (host struct).
+ *  seed, request_id, point_base: the Philox4x32-10 stream.  Ray s of lobe l
+ *    (0 = diffuse, k+1 = roughness level k) at query i draws its two
+ *    uniforms from counter (point_base + i, s, l, request_id) under key
+ *    (seed low 32 bits, seed high 32 bits): word >> 8 times 2^-24.  Results
+ *    therefore do not depend on how a batch is split or scheduled.
+ *  spp_diffuse, spp_specular: samples per point for L_d and for each level
+ *    of L_s0/L_s1 (Sec. 6 uses 128 and 64).
+ *  K, sigma[K]: roughness levels (Eq. 8), each in (0, 1]; alpha = sigma^2.
+ *  stats: NULL, or a device pointer to 4 unsigned 64-bit counters to which
+ *    the bake ADDS: rays traced, BVH nodes visited, triangles tested, and
+ *    (max, not added) the deepest traversal stack seen. */
+typedef struct fipt_bake_params {
+    uint64_t seed;
+    uint32_t request_id;
+    uint32_t point_base;
+    int32_t spp_diffuse;
+    int32_t spp_specular;
+    int32_t K;
+    float sigma[FIPT_MAX_K];
+    unsigned long long* stats;
+} fipt_bake_params;
+
+/* ------------------------------------------------------------ context */
+const char* fipt_last_error(void);
+const char* fipt_status_string(fipt_status s);
+/* Library build tag (string literal, host). */
+const char* fipt_version(void);
+/* Number of kernels this library has launched in the process (all
+ * contexts, all threads); benchmarks difference it around a timed region. */
+uint64_t fipt_launch_count(void);
+
+/* Creates a context on CUDA device `device` (allocates its 4-byte device
+ * status word; the only allocation outside the server).  *out owned by the
+ * caller, released with fipt_ctx_destroy. */
+fipt_status fipt_ctx_create(int device, fipt_ctx** out);
+fipt_status fipt_ctx_destroy(fipt_ctx* ctx);
+
+/* Waits for `stream`, then reads and clears the device status word.
+ * *device_code (host, nullable) receives the FIPT_DEV_* bits.  Returns
+ * FIPT_ERR_DEVICE_CHECK when any bit was set. */
+fipt_status fipt_sync_status(fipt_ctx* ctx, fipt_stream stream, int32_t* device_code);
+
+/* ------------------------------------------------------------ scene */
+/* Bytes of device workspace a scene of nV vertices and T triangles needs
+ * (BVH nodes, packed triangles, per-triangle radiance, build scratch). */
+fipt_status fipt_scene_workspace_size(int64_t nV, int64_t T, size_t* bytes);
+
+/* Builds the scene on the device, stream-ordered, no host synchronisation.
+ *  V [nV,3] f32 positions; F [T,3] i32 vertex indices (each in [0, nV));
+ *  Le [T,3] f32 view-independent emission (Sec. 3), seen only from the side
+ *  (v1-v0)x(v2-v0) points to; cache [T,3] f32 the diffuse radiance cache L'
+ *  at each triangle (Eq. 9; a per-triangle stand-in for Sec. 4.2's voxels).
+ *  workspace: >= fipt_scene_workspace_size bytes, 256-byte aligned; the
+ *  scene keeps pointers into it (caller keeps it alive until destroy).
+ *  V, F, Le, cache may be freed once the stream has passed this call.
+ * The BVH is a linear BVH: 63-bit Morton codes of triangle box centres
+ * quantised in FP64 against the vertex bounding box, a stable radix sort of
+ * (code, index), Karras's binary radix tree over the sorted codes, and a
+ * bottom-up refit of the node boxes.  T = 0 gives a scene every ray misses. */
+fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t nV, const int32_t* F,
+                              int64_t T, const float* Le, const float* cache, void* workspace,
+                              size_t ws_bytes, fipt_stream stream, fipt_scene** out);
+
+/* Replaces the radiance cache (cache [T,3] f32, original triangle order)
+ * without rebuilding the BVH -- the refined-cache update between stages. */
+fipt_status fipt_scene_set_cache(fipt_scene* scene, const float* cache, fipt_stream stream);
+fipt_status fipt_scene_destroy(fipt_scene* scene);
+
+/* Host-side scene facts: triangle count, ray-origin offset
+ * eps = 1e-4 * largest extent (valid after the build has run; this call
+ * synchronises the stream), and the workspace bytes in use. */
+fipt_status fipt_scene_info(fipt_scene* scene, fipt_stream stream, int64_t* T, float* eps,
+                            float* lo3, float* hi3);
+
+/* Parity export of the LBVH (device outputs, any may be NULL):
+ *  morton [T] u64 codes in sorted order; order [T] i32 triangle index at
+ *  each sorted position; node_range [(T-1),3] i32 (first, last, split) of
+ *  every internal node over sorted positions; node_box [(T-1),6] f32 the
+ *  node's box (lo xyz, hi xyz) = union of its two child boxes. */
+fipt_status fipt_scene_debug_export(fipt_scene* scene, uint64_t* morton, int32_t* order,
+                                    int32_t* node_range, float* node_box, fipt_stream stream);
+
+/* ------------------------------------------------------------ rays */
+/* Closest hit of nR rays o + t d, t > 0 (orig, dir [nR,3] f32; dir need
+ * not be unit).  skip_tri [nR] i32 (nullable): a triangle each ray ignores.
+ * Outputs [nR]: hit_tri i32 (original index, -1 = miss), hit_t f32 (+inf on
+ * a miss), hit_front i32 (1 when d . ((v1-v0)x(v2-v0)) < 0).  Among equal t
+ * the lower triangle index wins.  Watertight float32 test (Woop, Benthin,
+ * Wald, JCGT 2013) with a float64 retry of exactly-zero edge functions. */
+fipt_status fipt_trace_closest(fipt_scene* scene, const float* orig, const float* dir,
+                               int64_t nR, const int32_t* skip_tri, int32_t* hit_tri,
+                               float* hit_t, int32_t* hit_front, fipt_stream stream);
+
+/* Pinhole first hits -> query records, one per pixel (P = nViews*W*H,
+ * view-major, then row from the top, then column).
+ *  cams [nViews,10] f32: eye xyz, forward xyz, up xyz, vertical fov (rad).
+ *  right = normalize(fwd x up), up' = right x fwd; pixel (i, j) looks along
+ *  normalize(fwd + sx right + sy up'), sx = (2(i+0.5)/W - 1) tan(fov/2) W/H,
+ *  sy = (1 - 2(j+0.5)/H) tan(fov/2).
+ *  out [P] fipt_query (16-byte aligned): x = eye + t d, n = unit face normal
+ *  turned toward the camera, wo = -d, tri = hit; valid [P] i32 = 1 on a hit
+ *  (records of misses are zero with tri = -1). */
+fipt_status fipt_camera_queries(fipt_scene* scene, const float* cams, int32_t nViews, int32_t W,
+                                int32_t H, fipt_query* out, int32_t* valid, fipt_stream stream);
+
+/* Stream compaction of query records in order: the first max_out records
+ * with valid != 0 are copied to out; pixel_of [max_out] i32 (nullable)
+ * receives their source index; *n_out (device i64) the count written. */
+fipt_status fipt_compact_workspace_size(int64_t P, size_t* bytes);
+fipt_status fipt_compact_queries(const fipt_query* in, const int32_t* valid, int64_t P,
+                                 int64_t max_out, fipt_query* out, int32_t* pixel_of,
+                                 int64_t* n_out, void* workspace, size_t ws_bytes,
+                                 fipt_stream stream);
+
+/* ------------------------------------------------------------ bake */
+/* Bakes the shading terms of Eq. 6 with the Fresnel split of Eq. 7 at N
+ * query points (q [N] fipt_query, 8-byte aligned), by the Monte Carlo
+ * estimator of Sec. 6 (stage 1, BRDF importance sampling) with the one-
+ * segment cache query of Eq. 9: a ray leaves o = x + eps n, and its
+ * incident radiance is L_e (front face only) + L' of the first triangle it
+ * hits other than q.tri, or 0 on a miss.
+ *  L_d: cosine-distributed directions; each sample contributes its radiance.
+ *  L_s0/L_s1 at sigma_k: GGX half vectors drawn with density D(h)(n.h)
+ *  (Walter et al. 2007), alpha = sigma_k^2, reflected to wi; a sample with
+ *  n.wi <= 0 or wo.h <= 0 contributes 0; otherwise radiance times
+ *  F0 w and F1 w, w = G (wo.h) / ((n.wo)(n.h)), G the separable Smith-GGX
+ *  masking, F1 = (1 - wo.h)^5, F0 = 1 - F1.  Points with n.wo <= 1e-2
+ *  get zero specular terms.
+ * Outputs (f32): Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3]; each value is the sum
+ * of its samples in sample order divided by the sample count, so results
+ * are deterministic. */
+fipt_status fipt_bake(fipt_scene* scene, const fipt_query* q, int64_t N,
+                      const fipt_bake_params* params, float* Ld, float* Ls0, float* Ls1,
+                      fipt_stream stream);
+
+/* ------------------------------------------------------------ render */
+/* Factorized render, Eq. 5 with k_d = a(1-m), k_s = 0.04(1-m) + a m (Eq. 1)
+ * and the roughness lerp of Eq. 8: sigma is clamped to
+ * [sigma_grid[0], sigma_grid[K-1]], segment i is the largest i <= K-2 with
+ * sigma_grid[i] <= sigma.  Inputs: tables as produced by fipt_bake;
+ * sigma_grid [K] HOST f32 increasing; albedo [N,3], rough [N], metal [N]
+ * f32.  Outputs: Lr [N,3] f32.  When Lgt [N,3] is given, *loss (device
+ * f64) = sum over points with mask != 0 (mask [N] u8, NULL = all) and
+ * channels of (Gamma(Lr) - Gamma(Lgt))^2 (Eq. 14 with alpha = 0),
+ * Gamma(x) = sRGB(log(1 + max(x, 0))); summed in a fixed order. */
+fipt_status fipt_render_workspace_size(int64_t N, size_t* bytes);
+fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                            int32_t K, const float* sigma_grid, const float* albedo,
+                            const float* rough, const float* metal, const float* Lgt,
+                            const uint8_t* mask, float* Lr, double* loss, void* workspace,
+                            size_t ws_bytes, fipt_stream stream);
+
+/* Gradient of that loss times *grad_loss (device f64 scalar, NULL = 1)
+ * with respect to albedo [N,3], rough [N], metal [N] (f32 outputs).  The
+ * derivative in sigma is 0 where sigma is outside the grid; at grid nodes
+ * it is the right segment's slope. */
+fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                            int32_t K, const float* sigma_grid, const float* albedo,
+                            const float* rough, const float* metal, const float* Lgt,
+                            const uint8_t* mask, const double* grad_loss, float* g_albedo,
+                            float* g_rough, float* g_metal, fipt_stream stream);
+
+/* ------------------------------------------------------------ emitters */
+/* Per-triangle rendering error (Sec. 4.4: rendering without emission
+ * leaves large error on emitters).  tri: first-hit triangle of each pixel
+ * (-1 = none, ignored), pixel p's index at tri[p * tri_stride] (i32; 1 for
+ * a plain array, 10 to read the tri field of fipt_query records); Lr, Lgt
+ * [P,3] f32.  Outputs: err_sum [T] f64
+ * = sum of ||Lr - Lgt||^2 over the triangle's pixels, summed in pixel
+ * order; count [T] i32.  Pixels are grouped by a stable radix sort on the
+ * triangle index held in the workspace. */
+fipt_status fipt_tri_error_workspace_size(int64_t P, int64_t T, size_t* bytes);
+fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* Lr,
+                           const float* Lgt, int64_t P, int64_t T, double* err_sum, int32_t* count, void* workspace,
+                           size_t ws_bytes, fipt_stream stream);
+
+/* ------------------------------------------------------------ checks */
+/* Philox4x32-10 on the device (parity check of the sampler's stream):
+ * ctr [n,4] u32, key [n,2] u32 -> out [n,4] u32. */
+fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n,
+                              uint32_t* out, fipt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIPT_H */

@@ -1,0 +1,331 @@
+"""GB300 bake of the factorized shading terms of Factorized Inverse Path
+Tracing (Wu et al., ICCV 2023) -- Python binding of libfipt.so.
+
+Everything here marshals torch CUDA tensors into the C ABI of
+``include/fipt.h``; every step of the computation runs in the library's
+sm_103a kernels.  PyTorch supplies device memory and streams only.
+
+Queries are float32 tensors [N, 10]: x (3), n (3), wo (3) and the triangle
+index stored as int32 bits in column 9 -- the 40-byte ``fipt_query``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._native import BakeParams, FiptError, FIPT_MAX_K, check, lib, library_path
+
+__all__ = ["Context", "Scene", "bake", "render_fwd", "render_bwd", "FactorizedRender",
+           "factorized_render_loss", "tri_error", "compact_queries", "pack_queries",
+           "unpack_queries", "philox", "FiptError", "library_path", "context"]
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    return t.contiguous()
+
+
+def _workspace(nbytes, device):
+    """A byte tensor whose data pointer is 256-byte aligned."""
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf[off:off + int(nbytes)]
+
+
+class Context:
+    """A library context on one CUDA device (holds the device status word)."""
+
+    def __init__(self, device: int = 0):
+        lib()
+        h = ctypes.c_void_p()
+        check(lib().fipt_ctx_create(int(device), ctypes.byref(h)))
+        self.handle = h
+        self.device = int(device)
+
+    def sync_status(self, stream=None) -> int:
+        """Waits for the stream; returns the kernels' status bits (raises if set)."""
+        code = ctypes.c_int32(0)
+        st = lib().fipt_sync_status(self.handle, _stream(stream), ctypes.byref(code))
+        if st != 0:
+            raise FiptError(st, lib().fipt_last_error().decode())
+        return code.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fipt_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _contexts:
+        _contexts[d] = Context(d)
+    return _contexts[d]
+
+
+def pack_queries(x, n, wo, tri):
+    """[N,3] x, n, wo (float32) and [N] tri (int32) -> [N,10] query tensor."""
+    N = x.shape[0]
+    q = torch.empty((N, 10), dtype=torch.float32, device=x.device)
+    q[:, 0:3] = x
+    q[:, 3:6] = n
+    q[:, 6:9] = wo
+    q[:, 9:10].view(torch.int32)[:, 0] = tri.to(torch.int32)
+    return q
+
+
+def unpack_queries(q):
+    return {"x": q[:, 0:3], "n": q[:, 3:6], "wo": q[:, 6:9],
+            "tri": q[:, 9:10].contiguous().view(torch.int32)[:, 0]}
+
+
+class Scene:
+    """A triangle mesh with its device-built LBVH (``fipt_scene_create``)."""
+
+    def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None):
+        V = _dev(V, torch.float32, "V")
+        F = _dev(F, torch.int32, "F")
+        Le = _dev(Le, torch.float32, "Le")
+        cache = _dev(cache, torch.float32, "cache")
+        self.ctx = ctx or context(V.device.index)
+        self.device = V.device
+        self.T = int(F.shape[0])
+        self.nV = int(V.shape[0])
+        nbytes = ctypes.c_size_t()
+        check(lib().fipt_scene_workspace_size(self.nV, self.T, ctypes.byref(nbytes)))
+        self._buf, self.workspace = _workspace(nbytes.value, V.device)
+        h = ctypes.c_void_p()
+        check(lib().fipt_scene_create(self.ctx.handle, _ptr(V), self.nV, _ptr(F), self.T, _ptr(Le),
+                                      _ptr(cache), _ptr(self.workspace), nbytes.value,
+                                      _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        self._keep = (V, F, Le, cache)    # alive until the stream has consumed them
+
+    @classmethod
+    def from_mesh(cls, mesh, device="cuda", **kw):
+        t = lambda a: torch.from_numpy(a).to(device)
+        return cls(t(mesh.V), t(mesh.F), t(mesh.Le), t(mesh.cache), **kw)
+
+    def info(self, stream=None):
+        T = ctypes.c_int64()
+        eps = ctypes.c_float()
+        lo = (ctypes.c_float * 3)()
+        hi = (ctypes.c_float * 3)()
+        check(lib().fipt_scene_info(self.handle, _stream(stream), ctypes.byref(T), ctypes.byref(eps),
+                                    lo, hi))
+        return {"T": T.value, "eps": eps.value, "lo": list(lo), "hi": list(hi)}
+
+    def set_cache(self, cache, stream=None):
+        cache = _dev(cache, torch.float32, "cache")
+        check(lib().fipt_scene_set_cache(self.handle, _ptr(cache), _stream(stream)))
+        self._keep = self._keep + (cache,)
+
+    def export(self, stream=None):
+        T = self.T
+        ni = max(T - 1, 1 if T == 1 else 0)
+        d = self.device
+        out = {"morton": torch.empty(T, dtype=torch.int64, device=d),
+               "order": torch.empty(T, dtype=torch.int32, device=d),
+               "range": torch.empty((ni, 3), dtype=torch.int32, device=d),
+               "box": torch.empty((ni, 6), dtype=torch.float32, device=d)}
+        check(lib().fipt_scene_debug_export(self.handle, _ptr(out["morton"]), _ptr(out["order"]),
+                                            _ptr(out["range"]), _ptr(out["box"]), _stream(stream)))
+        return out
+
+    def trace(self, orig, dirs, skip=None, stream=None):
+        """Closest hits: (tri int32, t float32, front int32) per ray."""
+        orig = _dev(orig, torch.float32, "orig")
+        dirs = _dev(dirs, torch.float32, "dirs")
+        n = orig.shape[0]
+        skip = None if skip is None else _dev(skip, torch.int32, "skip")
+        tri = torch.empty(n, dtype=torch.int32, device=orig.device)
+        t = torch.empty(n, dtype=torch.float32, device=orig.device)
+        fr = torch.empty(n, dtype=torch.int32, device=orig.device)
+        check(lib().fipt_trace_closest(self.handle, _ptr(orig), _ptr(dirs), n, _ptr(skip), _ptr(tri),
+                                       _ptr(t), _ptr(fr), _stream(stream)))
+        return tri, t, fr
+
+    def camera_queries(self, cams, W, H, stream=None, out=None, valid=None):
+        cams = _dev(cams, torch.float32, "cams")
+        P = cams.shape[0] * W * H
+        if out is None:
+            out = torch.empty((P, 10), dtype=torch.float32, device=cams.device)
+        if valid is None:
+            valid = torch.empty(P, dtype=torch.int32, device=cams.device)
+        check(lib().fipt_camera_queries(self.handle, _ptr(cams), cams.shape[0], int(W), int(H),
+                                        _ptr(out), _ptr(valid), _stream(stream)))
+        return out, valid
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fipt_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def compact_queries(q, valid, max_out, stream=None):
+    """First ``max_out`` valid records in order -> (out, pixel_of, n_out[1] int64)."""
+    P = q.shape[0]
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_compact_workspace_size(P, ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, q.device)
+    out = torch.empty((int(max_out), 10), dtype=torch.float32, device=q.device)
+    pix = torch.empty(int(max_out), dtype=torch.int32, device=q.device)
+    n_out = torch.empty(1, dtype=torch.int64, device=q.device)
+    check(lib().fipt_compact_queries(_ptr(q), _ptr(valid), P, int(max_out), _ptr(out), _ptr(pix),
+                                     _ptr(n_out), _ptr(ws), nbytes.value, _stream(stream)))
+    return out, pix, n_out
+
+
+def bake_params(sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0, point_base=0,
+                stats=None):
+    p = BakeParams()
+    p.seed = int(seed) & (2 ** 64 - 1)
+    p.request_id = int(request_id)
+    p.point_base = int(point_base)
+    p.spp_diffuse = int(spp_diffuse)
+    p.spp_specular = int(spp_diffuse if spp_specular is None else spp_specular)
+    sig = [float(s) for s in sigma]
+    if not 1 <= len(sig) <= FIPT_MAX_K:
+        raise ValueError("need 1..%d roughness levels" % FIPT_MAX_K)
+    p.K = len(sig)
+    for k, s in enumerate(sig):
+        p.sigma[k] = s
+    p.stats = stats.data_ptr() if stats is not None else None
+    return p
+
+
+def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0,
+         point_base=0, stats=None, out=None, stream=None):
+    """Shading terms (Eq. 6-7) at the query points -> (Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3])."""
+    q = _dev(q, torch.float32, "q")
+    N = q.shape[0]
+    K = len(sigma)
+    if out is None:
+        out = (torch.empty((N, 3), dtype=torch.float32, device=q.device),
+               torch.empty((N, K, 3), dtype=torch.float32, device=q.device),
+               torch.empty((N, K, 3), dtype=torch.float32, device=q.device))
+    p = bake_params(sigma, spp_diffuse, spp_specular, seed, request_id, point_base, stats)
+    check(lib().fipt_bake(scene.handle, _ptr(q), N, ctypes.byref(p), _ptr(out[0]), _ptr(out[1]),
+                          _ptr(out[2]), _stream(stream)))
+    return out
+
+
+def _grid(sigma_grid):
+    g = (ctypes.c_float * len(sigma_grid))(*[float(s) for s in sigma_grid])
+    return g, len(sigma_grid)
+
+
+def render_fwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt=None, mask=None, stream=None,
+               Lr=None):
+    """Eq. 5 + Eq. 8 -> Lr [N,3]; with Lgt also the Eq. 14 loss (float64 [1])."""
+    N = Ld.shape[0]
+    g, K = _grid(sigma_grid)
+    if Lr is None:
+        Lr = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
+    loss = torch.zeros(1, dtype=torch.float64, device=Ld.device) if Lgt is not None else None
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_render_workspace_size(N, ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, Ld.device)
+    check(lib().fipt_render_fwd(_ptr(Ld), _ptr(Ls0), _ptr(Ls1), N, K, g, _ptr(albedo), _ptr(rough),
+                                _ptr(metal), _ptr(Lgt), _ptr(mask), _ptr(Lr), _ptr(loss), _ptr(ws),
+                                nbytes.value, _stream(stream)))
+    return Lr, loss
+
+
+def render_bwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask=None, grad_loss=None,
+               stream=None):
+    """d loss / d (albedo, rough, metal), scaled by grad_loss (float64 device scalar)."""
+    N = Ld.shape[0]
+    g, K = _grid(sigma_grid)
+    ga = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
+    gr = torch.empty(N, dtype=torch.float32, device=Ld.device)
+    gm = torch.empty(N, dtype=torch.float32, device=Ld.device)
+    check(lib().fipt_render_bwd(_ptr(Ld), _ptr(Ls0), _ptr(Ls1), N, K, g, _ptr(albedo), _ptr(rough),
+                                _ptr(metal), _ptr(Lgt), _ptr(mask), _ptr(grad_loss), _ptr(ga),
+                                _ptr(gr), _ptr(gm), _stream(stream)))
+    return ga, gr, gm
+
+
+class FactorizedRender(torch.autograd.Function):
+    """Tone-mapped factorized-render loss (Eq. 5, 8, 14) with the library's
+    hand-written backward for per-point albedo, roughness and metallic."""
+
+    @staticmethod
+    def forward(ctx, albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask, sigma_grid):
+        albedo, rough, metal = albedo.contiguous(), rough.contiguous(), metal.contiguous()
+        _, loss = render_fwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask)
+        ctx.save_for_backward(albedo, rough, metal, Ld, Ls0, Ls1, Lgt,
+                              mask if mask is not None else torch.empty(0, device=Ld.device))
+        ctx.has_mask = mask is not None
+        ctx.sigma_grid = list(sigma_grid)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask = ctx.saved_tensors
+        g = grad_out.detach().to(torch.float64).reshape(1).contiguous()
+        ga, gr, gm = render_bwd(Ld, Ls0, Ls1, ctx.sigma_grid, albedo, rough, metal, Lgt,
+                                mask if ctx.has_mask else None, g)
+        return ga, gr, gm, None, None, None, None, None, None
+
+
+def factorized_render_loss(albedo, rough, metal, tables, Lgt, sigma_grid, mask=None):
+    Ld, Ls0, Ls1 = tables
+    return FactorizedRender.apply(albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask, sigma_grid)
+
+
+def tri_error(tri, Lr, Lgt, T, stream=None, tri_stride=1):
+    """Per-triangle sum of ||Lr - Lgt||^2 (float64 [T]) and pixel count (int32 [T]).
+
+    ``tri`` is an int32 tensor of pixel triangle ids, or a [P,10] query tensor
+    (its triangle field is read in place, tri_stride = 10)."""
+    if tri.dtype == torch.float32 and tri.dim() == 2 and tri.shape[1] == 10:
+        P, tri_stride = tri.shape[0], 10
+        tri = tri[:, 9:10]
+    else:
+        P = tri.shape[0]
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_tri_error_workspace_size(P, int(T), ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, tri.device)
+    err = torch.empty(int(T), dtype=torch.float64, device=tri.device)
+    cnt = torch.empty(int(T), dtype=torch.int32, device=tri.device)
+    check(lib().fipt_tri_error(_ptr(tri), int(tri_stride), _ptr(Lr), _ptr(Lgt), P, int(T), _ptr(err),
+                               _ptr(cnt),
+                               _ptr(ws), nbytes.value, _stream(stream)))
+    return err, cnt
+
+
+def philox(ctr, key, stream=None):
+    """Device Philox4x32-10: ctr [n,4], key [n,2] (int32 tensors holding u32 bits)."""
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    check(lib().fipt_debug_philox(_ptr(ctr), _ptr(key), n, _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,267 @@
+// Internal declarations shared by the CUDA translation units of libfipt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/fipt.h"
+
+// ---------------------------------------------------------------- host glue
+struct fipt_ctx {
+    int device;
+    int32_t* status;    // device status word (FIPT_DEV_* bits)
+};
+
+// Device-resident scene constants, written by the build kernels.
+struct SceneConst {
+    int lo_key[3];      // vertex bounding box as order-preserving ints
+    int hi_key[3];
+    float lo[3];
+    float hi[3];
+    float eps;          // ray-origin offset, 1e-4 * largest extent
+    int pad;
+};
+
+// Internal BVH node (64 bytes): both child boxes plus child references.
+// A reference >= 0 is an internal node; < 0 is the leaf ~ref (one triangle
+// at that sorted position).
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   d = (child0, child1, -, -)
+struct __align__(16) BvhNode {
+    float4 a, b, c;
+    int4 d;
+};
+
+struct SceneView {
+    const BvhNode* nodes;   // max(T-1, 1)
+    const float4* tris;     // 3 per leaf: (v0, orig id bits), (v1, 0), (v2, 0)
+    const float4* shade;    // 2 per leaf: (Le rgb, 0), (cache rgb, 0)
+    const SceneConst* cst;
+    int64_t T;
+    int n_inner;            // internal nodes: a reference r is valid iff -T <= r < n_inner
+    int max_steps;          // node + leaf visits a valid tree can need for one ray (2T + 2)
+};
+
+struct fipt_scene {
+    fipt_ctx* ctx;
+    int64_t nV, T;
+    SceneConst* cst;
+    BvhNode* nodes;
+    float4* tris;
+    float4* shade;
+    int32_t* order;        // [T] original index at each sorted position
+    uint64_t* keys;        // [T] sorted Morton codes
+    int32_t* range;        // [(T-1)*3] first, last, split
+    int32_t* parent;       // [T-1]
+    int32_t* leaf_parent;  // [T]
+    int32_t* flags;        // [T-1]
+    uint64_t* keys_alt;
+    uint32_t* vals;
+    uint32_t* vals_alt;
+    uint32_t* hist;
+    size_t ws_bytes;
+    SceneView view() const {
+        const int64_t steps = 2 * T + 2;
+        return SceneView{nodes, tris, shade, cst, T, (int)(T > 1 ? T - 1 : 1),
+                         (int)(steps < 2147483647 ? steps : 2147483647)};
+    }
+};
+
+fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
+void fipt_count_launch();
+
+// Launches a kernel and counts it (fipt_launch_count reports the total).
+#define FIPT_LAUNCH(kern, grid, block, smem, st, ...)          \
+    do {                                                       \
+        kern<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);  \
+        fipt_count_launch();                                   \
+    } while (0)
+fipt_status fipt_check_cuda(cudaError_t e, const char* what);
+bool fipt_aligned(const void* p, size_t a);
+
+#define FIPT_REQUIRE(cond, ...)                                               \
+    do {                                                                       \
+        if (!(cond)) return fipt_set_error(FIPT_ERR_INVALID_ARG, __VA_ARGS__); \
+    } while (0)
+
+#define FIPT_CUDA(call)                                                 \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return fipt_check_cuda(e_, #call);       \
+    } while (0)
+
+#define FIPT_LAUNCHED(what)                                             \
+    do {                                                                \
+        cudaError_t e_ = cudaGetLastError();                            \
+        if (e_ != cudaSuccess) return fipt_check_cuda(e_, what);        \
+    } while (0)
+
+// Carves aligned sub-buffers out of a caller workspace.
+struct Carver {
+    char* base;
+    size_t off;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (key, value) pairs, 8 bits per pass, in caller
+// scratch.  Sorts bits [0, bits) of the keys; returns in *out_keys/out_vals
+// which of the two buffers holds the result.
+size_t radix_sort_scratch_bytes(int64_t n);
+template <class K>
+fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                             uint32_t* hist, int64_t n, int bits, cudaStream_t st,
+                             K** out_keys, uint32_t** out_vals);
+
+// ---------------------------------------------------------------- device math
+#define FIPT_DONE (-2147483647 - 1)   // traversal finished (not a node, not a leaf)
+
+__device__ __forceinline__ int float_to_ordered(float f) {
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float ordered_to_float(int i) {
+    return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u24f(uint32_t w) {
+    return (float)(w >> 8) * (1.0f / 16777216.0f);
+}
+
+// Ray in the form the watertight test wants (Woop, Benthin, Wald 2013):
+// kz = dominant axis of d, kx/ky the others (swapped when d[kz] < 0 to keep
+// the winding), shear S.
+struct TraceRay {
+    float ox, oy, oz;
+    float ix, iy, iz;       // 1/d for the slab tests
+    float Sx, Sy, Sz;
+    int k;                  // kx | ky << 2 | kz << 4
+};
+
+__device__ __forceinline__ float pick3(float x, float y, float z, int k) {
+    return k == 0 ? x : (k == 1 ? y : z);
+}
+
+__device__ __forceinline__ TraceRay make_ray(float ox, float oy, float oz, float dx, float dy,
+                                             float dz) {
+    TraceRay r;
+    r.ox = ox; r.oy = oy; r.oz = oz;
+    const float tiny = 1e-20f;
+    r.ix = 1.0f / (fabsf(dx) < tiny ? copysignf(tiny, dx) : dx);
+    r.iy = 1.0f / (fabsf(dy) < tiny ? copysignf(tiny, dy) : dy);
+    r.iz = 1.0f / (fabsf(dz) < tiny ? copysignf(tiny, dz) : dz);
+    const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+    int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dkz = pick3(dx, dy, dz, kz);
+    if (dkz < 0.0f) { int t = kx; kx = ky; ky = t; }
+    r.Sx = pick3(dx, dy, dz, kx) / dkz;
+    r.Sy = pick3(dx, dy, dz, ky) / dkz;
+    r.Sz = 1.0f / dkz;
+    r.k = kx | (ky << 2) | (kz << 4);
+    return r;
+}
+
+// Watertight ray-triangle test.  Edge functions are computed with separately
+// rounded products so that the two triangles sharing an edge get exactly
+// opposite values; exact zeros are recomputed in double.  Returns the hit
+// distance in *t (t > 0) and the facing (front: d . n_g < 0, i.e. det > 0).
+__device__ __forceinline__ bool tri_intersect(const TraceRay& r, float4 p0, float4 p1, float4 p2,
+                                              float& t, bool& front) {
+    const int kx = r.k & 3, ky = (r.k >> 2) & 3, kz = (r.k >> 4) & 3;
+    const float Ax0 = p0.x - r.ox, Ay0 = p0.y - r.oy, Az0 = p0.z - r.oz;
+    const float Bx0 = p1.x - r.ox, By0 = p1.y - r.oy, Bz0 = p1.z - r.oz;
+    const float Cx0 = p2.x - r.ox, Cy0 = p2.y - r.oy, Cz0 = p2.z - r.oz;
+    const float Akz = pick3(Ax0, Ay0, Az0, kz), Bkz = pick3(Bx0, By0, Bz0, kz),
+                Ckz = pick3(Cx0, Cy0, Cz0, kz);
+    const float Ax = fmaf(-r.Sx, Akz, pick3(Ax0, Ay0, Az0, kx));
+    const float Ay = fmaf(-r.Sy, Akz, pick3(Ax0, Ay0, Az0, ky));
+    const float Bx = fmaf(-r.Sx, Bkz, pick3(Bx0, By0, Bz0, kx));
+    const float By = fmaf(-r.Sy, Bkz, pick3(Bx0, By0, Bz0, ky));
+    const float Cx = fmaf(-r.Sx, Ckz, pick3(Cx0, Cy0, Cz0, kx));
+    const float Cy = fmaf(-r.Sy, Ckz, pick3(Cx0, Cy0, Cz0, ky));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        V = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T = U * (r.Sz * Akz) + V * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+    t = __fdiv_rn(T, det);
+    front = det > 0.0f;
+    return t > 0.0f;
+}
+
+// Slab test of both child boxes of a node against [0, tmax]; conservative by
+// a few ulps so that float rounding never culls a box the triangle test
+// would hit.
+__device__ __forceinline__ void node_test(const TraceRay& r, const BvhNode& n, float tmax,
+                                          bool& hit0, bool& hit1, float& t0, float& t1) {
+    const float ox = r.ox, oy = r.oy, oz = r.oz;
+    const float a0 = (n.a.x - ox) * r.ix, a1 = (n.a.y - ox) * r.ix;
+    const float a2 = (n.a.z - oy) * r.iy, a3 = (n.a.w - oy) * r.iy;
+    const float a4 = (n.c.x - oz) * r.iz, a5 = (n.c.y - oz) * r.iz;
+    const float b0 = (n.b.x - ox) * r.ix, b1 = (n.b.y - ox) * r.ix;
+    const float b2 = (n.b.z - oy) * r.iy, b3 = (n.b.w - oy) * r.iy;
+    const float b4 = (n.c.z - oz) * r.iz, b5 = (n.c.w - oz) * r.iz;
+    const float robust = 1.0000005f;
+    const float n0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), 0.0f));
+    const float f0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), tmax));
+    const float n1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), 0.0f));
+    const float f1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), tmax));
+    hit0 = n0 <= f0 * robust;
+    hit1 = n1 <= f1 * robust;
+    t0 = n0;
+    t1 = n1;
+}
+
+__device__ __forceinline__ BvhNode load_node(const BvhNode* nodes, int i) {
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    BvhNode n;
+    n.a = __ldg(p + 0);
+    n.b = __ldg(p + 1);
+    n.c = __ldg(p + 2);
+    n.d = __ldg(reinterpret_cast<const int4*>(p + 3));
+    return n;
+}
+
+// Orthonormal basis (t, b) completing a unit normal n (Duff et al. 2017).
+__device__ __forceinline__ void onb(float nx, float ny, float nz, float3& t, float3& b) {
+    const float s = copysignf(1.0f, nz);
+    const float a = -1.0f / (s + nz);
+    const float c = nx * ny * a;
+    t = make_float3(1.0f + s * nx * nx * a, s * c, -s * nx);
+    b = make_float3(c, s + ny * ny * a, -ny);
+}

@@ -1,0 +1,525 @@
+// Scene build on the device: linear BVH (Karras 2012) over the triangles.
+//
+//   bounds  -> vertex bounding box (order-preserving int atomics, exact)
+//   morton  -> 63-bit Morton code of each triangle's box centre, quantised
+//              with individually rounded IEEE double operations
+//   sort    -> stable LSD radix sort of (code, triangle index)
+//   karras  -> binary radix tree over the sorted codes (ties by index)
+//   pack    -> triangles and their radiance in sorted (leaf) order
+//   refit   -> bottom-up node boxes with per-node arrival counters
+#include "fipt_internal.cuh"
+
+namespace {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int RADIX = 256;
+constexpr int SCAN_THREADS = 1024;
+
+int64_t sort_blocks(int64_t n) { return (n + SORT_TILE - 1) / SORT_TILE; }
+
+// ---------------------------------------------------------------- radix sort
+template <class K>
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t cnt[RADIX];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t i = base + it * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of m counters in one block (digit-major histogram).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(uint32_t* __restrict__ a, int64_t m) {
+    __shared__ uint32_t part[SCAN_THREADS];
+    const int64_t per = (m + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int64_t beg = threadIdx.x * per;
+    const int64_t end = beg + per < m ? beg + per : m;
+    uint32_t s = 0;
+    for (int64_t i = beg; i < end; ++i) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int64_t i = beg; i < end; ++i) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter: an element's rank among equal digits in its tile follows
+// (iteration, warp, lane), i.e. index order.
+template <class K>
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+               uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist) {
+    constexpr int WARPS = SORT_THREADS / 32;
+    __shared__ uint32_t base_off[RADIX];
+    __shared__ uint32_t run[RADIX];
+    __shared__ uint32_t wcnt[WARPS][RADIX];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    base_off[tid] = hist[(int64_t)tid * gridDim.x + blockIdx.x];
+    run[tid] = 0;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t i = base + it * SORT_THREADS + tid;
+        const bool valid = i < n;
+        K k = 0;
+        uint32_t v = 0;
+        uint32_t digit = RADIX;
+        if (valid) {
+            k = kin[i];
+            v = vin[i];
+            digit = (uint32_t)(k >> shift) & (RADIX - 1);
+        }
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+        const uint32_t rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t r = run[tid];
+#pragma unroll
+            for (int w = 0; w < WARPS; ++w) {
+                const uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = r;
+                r += c;
+            }
+            run[tid] = r;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = base_off[digit] + wcnt[warp][digit] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- bounds
+__global__ void k_bounds_init(SceneConst* c) {
+    if (threadIdx.x < 3) {
+        c->lo_key[threadIdx.x] = float_to_ordered(__int_as_float(0x7f800000));   // +inf
+        c->hi_key[threadIdx.x] = float_to_ordered(__int_as_float(0xff800000));   // -inf
+    }
+}
+
+__global__ void k_bounds(const float* __restrict__ V, int64_t nV, SceneConst* c) {
+    float lo[3] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+    float hi[3] = {-lo[0], -lo[1], -lo[2]};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nV;
+         i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float x = V[3 * i + a];
+            lo[a] = fminf(lo[a], x);
+            hi[a] = fmaxf(hi[a], x);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&c->lo_key[a], float_to_ordered(lo[a]));
+            atomicMax(&c->hi_key[a], float_to_ordered(hi[a]));
+        }
+    }
+}
+
+__global__ void k_bounds_final(SceneConst* c, int64_t nV) {
+    if (threadIdx.x != 0) return;
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        c->lo[a] = nV ? ordered_to_float(c->lo_key[a]) : 0.0f;
+        c->hi[a] = nV ? ordered_to_float(c->hi_key[a]) : 0.0f;
+        ext = fmaxf(ext, c->hi[a] - c->lo[a]);
+    }
+    c->eps = 1e-4f * ext;
+}
+
+// ---------------------------------------------------------------- morton
+__device__ __forceinline__ uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ V, const int32_t* __restrict__ F, int64_t T,
+                         const SceneConst* __restrict__ c, uint64_t* __restrict__ keys,
+                         uint32_t* __restrict__ vals) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    uint32_t q[3];
+    const int i0 = F[3 * t], i1 = F[3 * t + 1], i2 = F[3 * t + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x0 = V[3 * (int64_t)i0 + a], x1 = V[3 * (int64_t)i1 + a], x2 = V[3 * (int64_t)i2 + a];
+        const float mn = fminf(fminf(x0, x1), x2), mx = fmaxf(fmaxf(x0, x1), x2);
+        const double cc = __dmul_rn(0.5, __dadd_rn((double)mn, (double)mx));
+        const double lo = (double)c->lo[a];
+        const double ext = __dsub_rn((double)c->hi[a], lo);
+        if (!(ext > 0.0)) {
+            q[a] = 0;
+            continue;
+        }
+        const double scale = __ddiv_rn(2097152.0, ext);
+        double f = floor(__dmul_rn(__dsub_rn(cc, lo), scale));
+        f = f < 0.0 ? 0.0 : (f > 2097151.0 ? 2097151.0 : f);
+        q[a] = (uint32_t)f;
+    }
+    keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    vals[t] = (uint32_t)t;
+}
+
+// ---------------------------------------------------------------- karras
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    const uint64_t x = k[i] ^ k[j];
+    if (x) return __clzll((long long)x);
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, BvhNode* __restrict__ nodes,
+                         int32_t* __restrict__ parent, int32_t* __restrict__ leaf_parent,
+                         int32_t* __restrict__ range) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) > 0 ? 1 : -1;
+    const int dmin = delta(k, n, i, i - d);
+    int64_t lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    const int64_t j = i + l * d;
+    const int dnode = delta(k, n, i, j);
+    int64_t s = 0;
+    int64_t div = 2;
+    for (;;) {
+        const int64_t t = (l + div - 1) / div;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+        div <<= 1;
+    }
+    const int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    const int64_t first = i < j ? i : j, last = i < j ? j : i;
+    const int c0 = (first == gamma) ? ~(int)gamma : (int)gamma;
+    const int c1 = (last == gamma + 1) ? ~(int)(gamma + 1) : (int)(gamma + 1);
+    nodes[i].d = make_int4(c0, c1, 0, 0);
+    if (c0 >= 0) parent[c0] = (int)i; else leaf_parent[~c0] = (int)i;
+    if (c1 >= 0) parent[c1] = (int)i; else leaf_parent[~c1] = (int)i;
+    range[3 * i + 0] = (int)first;
+    range[3 * i + 1] = (int)last;
+    range[3 * i + 2] = (int)gamma;
+    if (i == 0) parent[0] = -1;
+}
+
+// ---------------------------------------------------------------- pack
+__global__ void k_pack(const float* __restrict__ V, const int32_t* __restrict__ F,
+                       const float* __restrict__ Le, const float* __restrict__ cache,
+                       const uint32_t* __restrict__ sorted_idx, int64_t T, float4* __restrict__ tris,
+                       float4* __restrict__ shade, int32_t* __restrict__ order) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    const uint32_t t = sorted_idx[leaf];
+    order[leaf] = (int32_t)t;
+    const int64_t i0 = F[3 * (int64_t)t], i1 = F[3 * (int64_t)t + 1], i2 = F[3 * (int64_t)t + 2];
+    tris[3 * leaf + 0] = make_float4(V[3 * i0], V[3 * i0 + 1], V[3 * i0 + 2], __int_as_float((int)t));
+    tris[3 * leaf + 1] = make_float4(V[3 * i1], V[3 * i1 + 1], V[3 * i1 + 2], 0.0f);
+    tris[3 * leaf + 2] = make_float4(V[3 * i2], V[3 * i2 + 1], V[3 * i2 + 2], 0.0f);
+    shade[2 * leaf + 0] = make_float4(Le[3 * t], Le[3 * t + 1], Le[3 * t + 2], 0.0f);
+    shade[2 * leaf + 1] = make_float4(cache[3 * t], cache[3 * t + 1], cache[3 * t + 2], 0.0f);
+}
+
+__global__ void k_set_cache(const float* __restrict__ cache, const int32_t* __restrict__ order,
+                            int64_t T, float4* __restrict__ shade) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    const int64_t t = order[leaf];
+    shade[2 * leaf + 1] = make_float4(cache[3 * t], cache[3 * t + 1], cache[3 * t + 2], 0.0f);
+}
+
+// ---------------------------------------------------------------- refit
+struct Box {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ Box leaf_box(const float4* tris, int leaf) {
+    const float4 a = tris[3 * leaf], b = tris[3 * leaf + 1], c = tris[3 * leaf + 2];
+    return Box{fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z),
+               fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z)};
+}
+
+// Box of an internal node = union of its two child boxes, read through L2
+// (written by another thread of this kernel before its fence + counter).
+__device__ __forceinline__ Box node_box(const BvhNode* nodes, int i) {
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    const float4 a = __ldcg(p), b = __ldcg(p + 1), c = __ldcg(p + 2);
+    return Box{fminf(a.x, b.x), fminf(a.z, b.z), fminf(c.x, c.z),
+               fmaxf(a.y, b.y), fmaxf(a.w, b.w), fmaxf(c.y, c.w)};
+}
+
+__global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
+                        const int32_t* __restrict__ parent, const int32_t* __restrict__ leaf_parent,
+                        int32_t* flags, int64_t T) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    int p = leaf_parent[leaf];
+    // a radix tree over 96-bit augmented keys is at most 97 levels deep
+    for (int level = 0; p >= 0 && p < T - 1 && level < 128; ++level) {
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;   // the sibling finishes this node
+        __threadfence();
+        const int4 ch = __ldcg(reinterpret_cast<const int4*>(nodes + p) + 3);
+        const Box b0 = ch.x < 0 ? leaf_box(tris, ~ch.x) : node_box(nodes, ch.x);
+        const Box b1 = ch.y < 0 ? leaf_box(tris, ~ch.y) : node_box(nodes, ch.y);
+        float4* q = reinterpret_cast<float4*>(nodes + p);
+        __stcg(q + 0, make_float4(b0.lx, b0.hx, b0.ly, b0.hy));
+        __stcg(q + 1, make_float4(b1.lx, b1.hx, b1.ly, b1.hy));
+        __stcg(q + 2, make_float4(b0.lz, b0.hz, b1.lz, b1.hz));
+        p = parent[p];
+    }
+}
+
+// One-triangle scene: a root whose first child is leaf 0 and whose second
+// child has an empty box.
+__global__ void k_single(BvhNode* nodes, const float4* __restrict__ tris, int32_t* range) {
+    const Box b = leaf_box(tris, 0);
+    const float inf = __int_as_float(0x7f800000);
+    nodes[0].a = make_float4(b.lx, b.hx, b.ly, b.hy);
+    nodes[0].b = make_float4(inf, -inf, inf, -inf);
+    nodes[0].c = make_float4(b.lz, b.hz, inf, -inf);
+    nodes[0].d = make_int4(~0, ~0, 0, 0);
+    range[0] = 0; range[1] = 0; range[2] = 0;
+}
+
+__global__ void k_export_boxes(const BvhNode* __restrict__ nodes, int64_t n, float* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BvhNode nd = nodes[i];
+    out[6 * i + 0] = fminf(nd.a.x, nd.b.x);
+    out[6 * i + 1] = fminf(nd.a.z, nd.b.z);
+    out[6 * i + 2] = fminf(nd.c.x, nd.c.z);
+    out[6 * i + 3] = fmaxf(nd.a.y, nd.b.y);
+    out[6 * i + 4] = fmaxf(nd.a.w, nd.b.w);
+    out[6 * i + 5] = fmaxf(nd.c.y, nd.c.w);
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- sort driver
+size_t radix_sort_scratch_bytes(int64_t n) {
+    return (size_t)RADIX * (size_t)(sort_blocks(n) > 0 ? sort_blocks(n) : 1) * sizeof(uint32_t);
+}
+
+template <class K>
+fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                             uint32_t* hist, int64_t n, int bits, cudaStream_t st, K** out_keys,
+                             uint32_t** out_vals) {
+    K *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    const int64_t nb = sort_blocks(n);
+    if (n > 0) {
+        for (int shift = 0; shift < bits; shift += 8) {
+            FIPT_LAUNCH(k_sort_hist<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, n, shift, hist);
+            FIPT_LAUNCH(k_scan_single, 1, SCAN_THREADS, 0, st, hist, (int64_t)RADIX * nb);
+            FIPT_LAUNCH(k_sort_scatter<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, va, kb, vb, n, shift, hist);
+            K* tk = ka; ka = kb; kb = tk;
+            uint32_t* tv = va; va = vb; vb = tv;
+        }
+        FIPT_LAUNCHED("radix sort");
+    }
+    *out_keys = ka;
+    *out_vals = va;
+    return FIPT_OK;
+}
+
+template fipt_status radix_sort_pairs<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*,
+                                                uint32_t*, int64_t, int, cudaStream_t,
+                                                uint64_t**, uint32_t**);
+template fipt_status radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                                uint32_t*, int64_t, int, cudaStream_t,
+                                                uint32_t**, uint32_t**);
+
+// ---------------------------------------------------------------- C ABI
+namespace {
+struct SceneLayout {
+    SceneConst* cst;
+    BvhNode* nodes;
+    float4* tris;
+    float4* shade;
+    int32_t* order;
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt, *hist;
+    int32_t *range, *parent, *leaf_parent, *flags;
+    size_t bytes;
+};
+
+SceneLayout carve_scene(void* ws, int64_t T) {
+    Carver c{static_cast<char*>(ws), 0};
+    SceneLayout L;
+    const int64_t ni = T > 1 ? T - 1 : 1;
+    const int64_t t1 = T > 0 ? T : 1;
+    L.cst = c.take<SceneConst>(1);
+    L.nodes = c.take<BvhNode>((size_t)ni);
+    L.tris = c.take<float4>((size_t)(3 * t1));
+    L.shade = c.take<float4>((size_t)(2 * t1));
+    L.order = c.take<int32_t>((size_t)t1);
+    L.keys = c.take<uint64_t>((size_t)t1);
+    L.keys_alt = c.take<uint64_t>((size_t)t1);
+    L.vals = c.take<uint32_t>((size_t)t1);
+    L.vals_alt = c.take<uint32_t>((size_t)t1);
+    L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(t1) / sizeof(uint32_t));
+    L.range = c.take<int32_t>((size_t)(3 * ni));
+    L.parent = c.take<int32_t>((size_t)ni);
+    L.leaf_parent = c.take<int32_t>((size_t)t1);
+    L.flags = c.take<int32_t>((size_t)ni);
+    L.bytes = c.off + 256;
+    return L;
+}
+}  // namespace
+
+extern "C" fipt_status fipt_scene_workspace_size(int64_t nV, int64_t T, size_t* bytes) {
+    FIPT_REQUIRE(bytes, "bytes is NULL");
+    FIPT_REQUIRE(nV >= 0 && T >= 0 && T < (int64_t)1 << 31, "bad sizes nV=%lld T=%lld",
+                 (long long)nV, (long long)T);
+    *bytes = carve_scene(nullptr, T).bytes;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t nV,
+                                         const int32_t* F, int64_t T, const float* Le,
+                                         const float* cache, void* workspace, size_t ws_bytes,
+                                         fipt_stream stream, fipt_scene** out) {
+    FIPT_REQUIRE(ctx && out, "ctx / out is NULL");
+    FIPT_REQUIRE(nV >= 0 && T >= 0 && T < (int64_t)1 << 31, "bad sizes nV=%lld T=%lld",
+                 (long long)nV, (long long)T);
+    FIPT_REQUIRE(T == 0 || (V && F && Le && cache), "V / F / Le / cache is NULL");
+    FIPT_REQUIRE(T == 0 || nV > 0, "triangles without vertices");
+    FIPT_REQUIRE(fipt_aligned(V, 4) && fipt_aligned(F, 4) && fipt_aligned(Le, 4) &&
+                 fipt_aligned(cache, 4), "inputs must be 4-byte aligned");
+    FIPT_REQUIRE(workspace && fipt_aligned(workspace, 256), "workspace must be 256-byte aligned");
+    SceneLayout L = carve_scene(workspace, T);
+    if (ws_bytes < L.bytes)
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "scene workspace %zu < %zu bytes", ws_bytes, L.bytes);
+    FIPT_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    fipt_scene* s = new fipt_scene();
+    s->ctx = ctx; s->nV = nV; s->T = T;
+    s->cst = L.cst; s->nodes = L.nodes; s->tris = L.tris; s->shade = L.shade; s->order = L.order;
+    s->keys = L.keys; s->keys_alt = L.keys_alt; s->vals = L.vals; s->vals_alt = L.vals_alt;
+    s->hist = L.hist; s->range = L.range; s->parent = L.parent; s->leaf_parent = L.leaf_parent;
+    s->flags = L.flags; s->ws_bytes = L.bytes;
+
+    FIPT_LAUNCH(k_bounds_init, 1, 32, 0, st, L.cst);
+    if (nV > 0) {
+        const int64_t nb = (nV + 255) / 256;
+        FIPT_LAUNCH(k_bounds, (unsigned)(nb < 1216 ? nb : 1216), 256, 0, st, V, nV, L.cst);
+    }
+    FIPT_LAUNCH(k_bounds_final, 1, 32, 0, st, L.cst, nV);
+    if (T > 0) {
+        FIPT_LAUNCH(k_morton, grid_for(T, 256), 256, 0, st, V, F, T, L.cst, L.keys, L.vals);
+        uint64_t* sk;
+        uint32_t* sv;
+        fipt_status r = radix_sort_pairs<uint64_t>(L.keys, L.keys_alt, L.vals, L.vals_alt, L.hist,
+                                                   T, 64, st, &sk, &sv);
+        if (r != FIPT_OK) { delete s; return r; }
+        s->keys = sk;   // 8 passes: the result is back in the first buffer
+        FIPT_LAUNCH(k_pack, grid_for(T, 256), 256, 0, st, V, F, Le, cache, sv, T, L.tris, L.shade, L.order);
+        if (T == 1) {
+            FIPT_LAUNCH(k_single, 1, 1, 0, st, L.nodes, L.tris, L.range);
+        } else {
+            FIPT_LAUNCH(k_karras, grid_for(T - 1, 256), 256, 0, st, sk, T, L.nodes, L.parent,
+                                                           L.leaf_parent, L.range);
+            cudaError_t e = cudaMemsetAsync(L.flags, 0, sizeof(int32_t) * (size_t)(T - 1), st);
+            if (e != cudaSuccess) { delete s; return fipt_check_cuda(e, "memset flags"); }
+            FIPT_LAUNCH(k_refit, grid_for(T, 256), 256, 0, st, L.nodes, L.tris, L.parent, L.leaf_parent,
+                                                      L.flags, T);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { delete s; return fipt_check_cuda(e, "scene build"); }
+    *out = s;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_set_cache(fipt_scene* s, const float* cache, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(s->T == 0 || (cache && fipt_aligned(cache, 4)), "cache is NULL or misaligned");
+    if (s->T == 0) return FIPT_OK;
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    FIPT_LAUNCH(k_set_cache, grid_for(s->T, 256), 256, 0, static_cast<cudaStream_t>(stream), cache, s->order, s->T, s->shade);
+    FIPT_LAUNCHED("set cache");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_destroy(fipt_scene* s) {
+    delete s;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_info(fipt_scene* s, fipt_stream stream, int64_t* T, float* eps,
+                                       float* lo3, float* hi3) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    SceneConst c;
+    FIPT_CUDA(cudaMemcpyAsync(&c, s->cst, sizeof(c), cudaMemcpyDeviceToHost,
+                              static_cast<cudaStream_t>(stream)));
+    FIPT_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    if (T) *T = s->T;
+    if (eps) *eps = c.eps;
+    for (int a = 0; a < 3; ++a) {
+        if (lo3) lo3[a] = c.lo[a];
+        if (hi3) hi3[a] = c.hi[a];
+    }
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_debug_export(fipt_scene* s, uint64_t* morton, int32_t* order,
+                                               int32_t* node_range, float* node_box,
+                                               fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t T = s->T, ni = T > 1 ? T - 1 : (T == 1 ? 1 : 0);
+    if (T == 0) return FIPT_OK;
+    if (morton) FIPT_CUDA(cudaMemcpyAsync(morton, s->keys, 8 * (size_t)T, cudaMemcpyDeviceToDevice, st));
+    if (order) FIPT_CUDA(cudaMemcpyAsync(order, s->order, 4 * (size_t)T, cudaMemcpyDeviceToDevice, st));
+    if (node_range)
+        FIPT_CUDA(cudaMemcpyAsync(node_range, s->range, 12 * (size_t)ni, cudaMemcpyDeviceToDevice, st));
+    if (node_box) {
+        FIPT_LAUNCH(k_export_boxes, grid_for(ni, 256), 256, 0, st, s->nodes, ni, node_box);
+        FIPT_LAUNCHED("export boxes");
+    }
+    return FIPT_OK;
+}

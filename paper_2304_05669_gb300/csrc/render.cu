@@ -1,0 +1,250 @@
+// Factorized render (Eq. 5 with the lerp of Eq. 8), the tone-mapped loss of
+// Eq. 14 (alpha = 0) and its gradient with respect to per-point albedo,
+// roughness and metallic.  Both kernels stream one point per thread; the
+// loss is reduced in a fixed order (per-block FP64 partials, then one block
+// over the partials) so it is bit-reproducible.
+#include "fipt_internal.cuh"
+
+namespace {
+
+constexpr int RENDER_THREADS = 256;
+
+struct Grid {
+    int K;
+    float s[FIPT_MAX_K];
+};
+
+struct Lerp {
+    int i;
+    float t;
+    float inv_w;
+    bool clamped;
+};
+
+__device__ __forceinline__ Lerp lerp_of(float rough, const Grid& g) {
+    Lerp l;
+    const float lo = g.s[0], hi = g.s[g.K - 1];
+    l.clamped = rough < lo || rough > hi;
+    const float s = fminf(fmaxf(rough, lo), hi);
+    int i = 0;
+#pragma unroll
+    for (int k = 1; k < FIPT_MAX_K - 1; ++k)
+        if (k <= g.K - 2 && g.s[k] <= s) i = k;
+    l.i = i;
+    const float w = g.s[i + 1] - g.s[i];
+    l.inv_w = 1.0f / w;
+    l.t = (s - g.s[i]) / w;
+    return l;
+}
+
+// Gamma of Eq. 14: sRGB transfer curve of log(1 + max(x, 0)).
+__device__ __forceinline__ float tonemap(float x) {
+    const float y = log1pf(fmaxf(x, 0.0f));
+    return y <= 0.0031308f ? 12.92f * y : 1.055f * powf(y, 1.0f / 2.4f) - 0.055f;
+}
+
+__device__ __forceinline__ float tonemap_grad(float x) {
+    if (x < 0.0f) return 0.0f;
+    const float y = log1pf(x);
+    const float ds = y <= 0.0031308f ? 12.92f : (1.055f / 2.4f) * powf(y, 1.0f / 2.4f - 1.0f);
+    return ds / (1.0f + x);
+}
+
+struct PointShade {
+    float Ld[3], S0[3], S1[3], dS0[3], dS1[3];
+    float a[3], m;
+    Lerp l;
+};
+
+__device__ __forceinline__ void load_point(int64_t p, int K, const Grid& g, const float* Ld,
+                                           const float* Ls0, const float* Ls1, const float* albedo,
+                                           const float* rough, const float* metal, PointShade& P,
+                                           bool with_slopes) {
+    P.l = lerp_of(rough[p], g);
+    const float t = P.l.t;
+    const float* s0 = Ls0 + (p * K + P.l.i) * 3;
+    const float* s1 = Ls1 + (p * K + P.l.i) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P.Ld[c] = Ld[3 * p + c];
+        const float a0 = s0[c], b0 = s0[3 + c], a1 = s1[c], b1 = s1[3 + c];
+        P.S0[c] = (1.0f - t) * a0 + t * b0;
+        P.S1[c] = (1.0f - t) * a1 + t * b1;
+        if (with_slopes) {
+            P.dS0[c] = (b0 - a0) * P.l.inv_w;
+            P.dS1[c] = (b1 - a1) * P.l.inv_w;
+        }
+        P.a[c] = albedo[3 * p + c];
+    }
+    P.m = metal[p];
+}
+
+__global__ void __launch_bounds__(RENDER_THREADS)
+k_render_fwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const float* __restrict__ Ls1,
+             int64_t N, Grid g, const float* __restrict__ albedo, const float* __restrict__ rough,
+             const float* __restrict__ metal, const float* __restrict__ Lgt,
+             const uint8_t* __restrict__ mask, float* __restrict__ Lr, double* __restrict__ partial) {
+    const int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x;
+    double loss = 0.0;
+    if (p < N) {
+        PointShade P;
+        load_point(p, g.K, g, Ld, Ls0, Ls1, albedo, rough, metal, P, false);
+        const float m = P.m;
+        float lr[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float kd = P.a[c] * (1.0f - m);
+            const float ks = 0.04f * (1.0f - m) + P.a[c] * m;
+            lr[c] = kd * P.Ld[c] + ks * P.S0[c] + P.S1[c];
+            Lr[3 * p + c] = lr[c];
+        }
+        if (Lgt && (!mask || mask[p])) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float d = tonemap(lr[c]) - tonemap(Lgt[3 * p + c]);
+                loss += (double)d * (double)d;
+            }
+        }
+    }
+    if (!partial) return;
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    __shared__ double ws[RENDER_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < RENDER_THREADS / 32; ++w) s += ws[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partial, int64_t n,
+                                                      double* __restrict__ out) {
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) s += partial[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 32; ++w) t += ws[w];
+        *out = t;
+    }
+}
+
+__global__ void __launch_bounds__(RENDER_THREADS)
+k_render_bwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const float* __restrict__ Ls1,
+             int64_t N, Grid g, const float* __restrict__ albedo, const float* __restrict__ rough,
+             const float* __restrict__ metal, const float* __restrict__ Lgt,
+             const uint8_t* __restrict__ mask, const double* __restrict__ grad_loss,
+             float* __restrict__ g_albedo, float* __restrict__ g_rough, float* __restrict__ g_metal) {
+    const int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x;
+    if (p >= N) return;
+    PointShade P;
+    load_point(p, g.K, g, Ld, Ls0, Ls1, albedo, rough, metal, P, true);
+    const float scale = grad_loss ? (float)*grad_loss : 1.0f;
+    const bool on = !mask || mask[p];
+    const float m = P.m;
+    float gs = 0.0f, gm = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float a = P.a[c];
+        const float kd = a * (1.0f - m);
+        const float ks = 0.04f * (1.0f - m) + a * m;
+        const float lr = kd * P.Ld[c] + ks * P.S0[c] + P.S1[c];
+        const float gc = on ? 2.0f * (tonemap(lr) - tonemap(Lgt[3 * p + c])) * tonemap_grad(lr) * scale
+                            : 0.0f;
+        g_albedo[3 * p + c] = gc * ((1.0f - m) * P.Ld[c] + m * P.S0[c]);
+        gm += gc * (-a * P.Ld[c] + (a - 0.04f) * P.S0[c]);
+        gs += gc * (ks * P.dS0[c] + P.dS1[c]);
+    }
+    g_rough[p] = P.l.clamped ? 0.0f : gs;
+    g_metal[p] = gm;
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+fipt_status make_grid(int32_t K, const float* sigma_grid, Grid& g) {
+    FIPT_REQUIRE(K >= 2 && K <= FIPT_MAX_K, "K must be in [2, %d]", FIPT_MAX_K);
+    FIPT_REQUIRE(sigma_grid, "sigma_grid (host) is NULL");
+    g.K = K;
+    for (int k = 0; k < FIPT_MAX_K; ++k) g.s[k] = k < K ? sigma_grid[k] : sigma_grid[K - 1];
+    for (int k = 1; k < K; ++k)
+        FIPT_REQUIRE(g.s[k] > g.s[k - 1], "sigma_grid must increase strictly");
+    return FIPT_OK;
+}
+
+fipt_status check_render_arrays(int64_t N, const float* Ld, const float* Ls0, const float* Ls1,
+                                const float* albedo, const float* rough, const float* metal) {
+    FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 40), "bad point count");
+    if (N == 0) return FIPT_OK;
+    FIPT_REQUIRE(Ld && Ls0 && Ls1 && albedo && rough && metal, "NULL input array");
+    FIPT_REQUIRE(fipt_aligned(Ld, 4) && fipt_aligned(Ls0, 4) && fipt_aligned(Ls1, 4) &&
+                 fipt_aligned(albedo, 4) && fipt_aligned(rough, 4) && fipt_aligned(metal, 4),
+                 "inputs must be 4-byte aligned");
+    return FIPT_OK;
+}
+
+}  // namespace
+
+extern "C" fipt_status fipt_render_workspace_size(int64_t N, size_t* bytes) {
+    FIPT_REQUIRE(bytes && N >= 0, "bad arguments");
+    *bytes = (size_t)(blocks(N, RENDER_THREADS) + 1) * sizeof(double) + 256;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                                       int32_t K, const float* sigma_grid, const float* albedo,
+                                       const float* rough, const float* metal, const float* Lgt,
+                                       const uint8_t* mask, float* Lr, double* loss, void* ws,
+                                       size_t ws_bytes, fipt_stream stream) {
+    Grid g;
+    fipt_status r = make_grid(K, sigma_grid, g);
+    if (r != FIPT_OK) return r;
+    r = check_render_arrays(N, Ld, Ls0, Ls1, albedo, rough, metal);
+    if (r != FIPT_OK) return r;
+    FIPT_REQUIRE(!Lgt || loss, "loss must be given with Lgt");
+    FIPT_REQUIRE(fipt_aligned(loss, 8) && fipt_aligned(Lgt, 4) && fipt_aligned(Lr, 4),
+                 "misaligned output");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        if (loss) FIPT_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
+        return FIPT_OK;
+    }
+    FIPT_REQUIRE(Lr, "Lr is NULL");
+    double* partial = nullptr;
+    if (Lgt) {
+        size_t need;
+        fipt_render_workspace_size(N, &need);
+        if (!ws || ws_bytes < need)
+            return fipt_set_error(FIPT_ERR_WORKSPACE, "render workspace %zu < %zu", ws_bytes, need);
+        FIPT_REQUIRE(fipt_aligned(ws, 8), "workspace must be 8-byte aligned");
+        partial = static_cast<double*>(ws);
+    }
+    const unsigned nb = blocks(N, RENDER_THREADS);
+    FIPT_LAUNCH(k_render_fwd, nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt, mask,
+                                                Lr, partial);
+    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    FIPT_LAUNCHED("render_fwd");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                                       int32_t K, const float* sigma_grid, const float* albedo,
+                                       const float* rough, const float* metal, const float* Lgt,
+                                       const uint8_t* mask, const double* grad_loss, float* g_albedo,
+                                       float* g_rough, float* g_metal, fipt_stream stream) {
+    Grid g;
+    fipt_status r = make_grid(K, sigma_grid, g);
+    if (r != FIPT_OK) return r;
+    r = check_render_arrays(N, Ld, Ls0, Ls1, albedo, rough, metal);
+    if (r != FIPT_OK) return r;
+    if (N == 0) return FIPT_OK;
+    FIPT_REQUIRE(Lgt && g_albedo && g_rough && g_metal, "Lgt / gradient output is NULL");
+    FIPT_REQUIRE(fipt_aligned(Lgt, 4) && fipt_aligned(g_albedo, 4) && fipt_aligned(g_rough, 4) &&
+                 fipt_aligned(g_metal, 4) && fipt_aligned(grad_loss, 8), "misaligned array");
+    FIPT_LAUNCH(k_render_bwd, blocks(N, RENDER_THREADS), RENDER_THREADS, 0, static_cast<cudaStream_t>(stream), Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt, mask, grad_loss, g_albedo, g_rough, g_metal);
+    FIPT_LAUNCHED("render_bwd");
+    return FIPT_OK;
+}

@@ -1,0 +1,583 @@
+// Ray traversal kernels: closest hit, pinhole first hits, query compaction
+// and the bake of the factorized shading terms (Eq. 6-7, Eq. 9, Sec. 6).
+//
+// Traversal is a per-thread stack walk of the binary LBVH in "while-while"
+// form (inner nodes until a leaf, then leaves until an inner node), with
+// the stack in shared memory, laid out [depth][thread] so that the threads
+// of a warp touch consecutive banks.  Node (64 B) and triangle (48 B) reads
+// are 16-byte vector loads through the read-only path.
+#include "fipt_internal.cuh"
+
+namespace {
+
+constexpr int TRACE_THREADS = 128;
+constexpr int STACK_DEPTH = 48;
+constexpr float FINF = __builtin_huge_valf();
+
+struct BestHit {
+    float t;
+    int leaf;
+    int orig;
+    bool front;
+};
+
+// Closest hit of one ray; `stack` is this thread's column of the shared
+// stack (element k at stack[k * TRACE_THREADS]).  Returns false and raises
+// the overflow bit if the stack would exceed STACK_DEPTH.
+__device__ __forceinline__ void closest_hit(const SceneView& sc, const TraceRay& r, int skip,
+                                            int* stack, BestHit& best, int32_t* status) {
+    best.t = FINF;
+    best.leaf = -1;
+    best.orig = 0x7fffffff;
+    best.front = false;
+    if (sc.T == 0) return;
+    int node = 0, sp = 0, steps = 0;
+    while (node != FIPT_DONE) {
+        while (node >= 0) {
+            if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                return;
+            }
+            const BvhNode n = load_node(sc.nodes, node);
+            bool h0, h1;
+            float t0, t1;
+            node_test(r, n, best.t, h0, h1, t0, t1);
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp < STACK_DEPTH) {
+                    stack[sp * TRACE_THREADS] = first0 ? n.d.y : n.d.x;
+                    ++sp;
+                } else {
+                    atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                }
+                node = first0 ? n.d.x : n.d.y;
+            } else if (h0) {
+                node = n.d.x;
+            } else if (h1) {
+                node = n.d.y;
+            } else {
+                node = sp > 0 ? stack[--sp * TRACE_THREADS] : FIPT_DONE;
+            }
+        }
+        while (node < 0 && node != FIPT_DONE) {
+            const int leaf = ~node;
+            if (leaf >= sc.T || ++steps > sc.max_steps) {
+                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                return;
+            }
+            const float4 p0 = __ldg(sc.tris + 3 * leaf);
+            const int orig = __float_as_int(p0.w);
+            if (orig != skip) {
+                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
+                float t;
+                bool fr;
+                if (tri_intersect(r, p0, p1, p2, t, fr) &&
+                    (t < best.t || (t == best.t && orig < best.orig))) {
+                    best.t = t;
+                    best.leaf = leaf;
+                    best.orig = orig;
+                    best.front = fr;
+                }
+            }
+            node = sp > 0 ? stack[--sp * TRACE_THREADS] : FIPT_DONE;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS)
+k_trace(SceneView sc, const float* __restrict__ orig, const float* __restrict__ dir, int64_t n,
+        const int32_t* __restrict__ skip, int32_t* __restrict__ hit_tri, float* __restrict__ hit_t,
+        int32_t* __restrict__ hit_front, int32_t* status) {
+    __shared__ int stk[STACK_DEPTH * TRACE_THREADS];
+    const int64_t i = blockIdx.x * (int64_t)TRACE_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const TraceRay r = make_ray(orig[3 * i], orig[3 * i + 1], orig[3 * i + 2], dir[3 * i],
+                                dir[3 * i + 1], dir[3 * i + 2]);
+    BestHit b;
+    closest_hit(sc, r, skip ? skip[i] : -1, stk + threadIdx.x, b, status);
+    hit_tri[i] = b.leaf >= 0 ? b.orig : -1;
+    hit_t[i] = b.t;
+    hit_front[i] = b.leaf >= 0 && b.front ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(TRACE_THREADS)
+k_camera(SceneView sc, const float* __restrict__ cams, int W, int H, int64_t P,
+         fipt_query* __restrict__ out, int32_t* __restrict__ valid, int32_t* status) {
+    __shared__ int stk[STACK_DEPTH * TRACE_THREADS];
+    const int64_t p = blockIdx.x * (int64_t)TRACE_THREADS + threadIdx.x;
+    if (p >= P) return;
+    const int64_t wh = (int64_t)W * H;
+    const int v = (int)(p / wh);
+    const int64_t rem = p - v * wh;
+    const int j = (int)(rem / W), i = (int)(rem - (int64_t)j * W);
+    const float* c = cams + 10 * v;
+    float fx = c[3], fy = c[4], fz = c[5];
+    const float fl = 1.0f / sqrtf(fx * fx + fy * fy + fz * fz);
+    fx *= fl; fy *= fl; fz *= fl;
+    const float ux = c[6], uy = c[7], uz = c[8];
+    float rx = fy * uz - fz * uy, ry = fz * ux - fx * uz, rz = fx * uy - fy * ux;
+    const float rl = 1.0f / sqrtf(rx * rx + ry * ry + rz * rz);
+    rx *= rl; ry *= rl; rz *= rl;
+    const float vx = ry * fz - rz * fy, vy = rz * fx - rx * fz, vz = rx * fy - ry * fx;
+    const float th = tanf(0.5f * c[9]);
+    const float sx = (2.0f * ((float)i + 0.5f) / (float)W - 1.0f) * th * ((float)W / (float)H);
+    const float sy = (1.0f - 2.0f * ((float)j + 0.5f) / (float)H) * th;
+    float dx = fx + sx * rx + sy * vx, dy = fy + sx * ry + sy * vy, dz = fz + sx * rz + sy * vz;
+    const float dl = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= dl; dy *= dl; dz *= dl;
+    const TraceRay r = make_ray(c[0], c[1], c[2], dx, dy, dz);
+    BestHit b;
+    closest_hit(sc, r, -1, stk + threadIdx.x, b, status);
+    fipt_query qr;
+    if (b.leaf < 0) {
+        for (int a = 0; a < 3; ++a) { qr.x[a] = 0.0f; qr.n[a] = 0.0f; qr.wo[a] = 0.0f; }
+        qr.tri = -1;
+        valid[p] = 0;
+    } else {
+        const float4 p0 = __ldg(sc.tris + 3 * b.leaf), p1 = __ldg(sc.tris + 3 * b.leaf + 1),
+                     p2 = __ldg(sc.tris + 3 * b.leaf + 2);
+        const float e1x = p1.x - p0.x, e1y = p1.y - p0.y, e1z = p1.z - p0.z;
+        const float e2x = p2.x - p0.x, e2y = p2.y - p0.y, e2z = p2.z - p0.z;
+        float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+        const float nl = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+        const float sg = (nx * dx + ny * dy + nz * dz) > 0.0f ? -nl : nl;
+        qr.x[0] = c[0] + b.t * dx; qr.x[1] = c[1] + b.t * dy; qr.x[2] = c[2] + b.t * dz;
+        qr.n[0] = sg * nx; qr.n[1] = sg * ny; qr.n[2] = sg * nz;
+        qr.wo[0] = -dx; qr.wo[1] = -dy; qr.wo[2] = -dz;
+        qr.tri = b.orig;
+        valid[p] = 1;
+    }
+    out[p] = qr;
+}
+
+// ---------------------------------------------------------------- compaction
+constexpr int CMP_THREADS = 512;
+constexpr int CMP_ITEMS = 8;
+constexpr int CMP_TILE = CMP_THREADS * CMP_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? warp_sums[warp - 1] : 0u;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(CMP_THREADS)
+k_count_valid(const int32_t* __restrict__ valid, int64_t P, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * CMP_TILE + threadIdx.x * CMP_ITEMS;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < CMP_ITEMS; ++k) c += (base + k < P && valid[base + k] != 0) ? 1u : 0u;
+    uint32_t tot;
+    block_exclusive_scan(c, ws, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsum(uint32_t* __restrict__ a, int64_t m, int64_t max_out,
+                                                   int64_t* __restrict__ n_out) {
+    __shared__ uint32_t ws[32];
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < m; b += 1024) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t v = i < m ? a[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, ws, &tot);
+        if (i < m) a[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_out = (int64_t)carry < max_out ? (int64_t)carry : max_out;
+}
+
+__global__ void __launch_bounds__(CMP_THREADS)
+k_compact(const fipt_query* __restrict__ in, const int32_t* __restrict__ valid, int64_t P,
+          int64_t max_out, const uint32_t* __restrict__ boff, fipt_query* __restrict__ out,
+          int32_t* __restrict__ pixel_of) {
+    __shared__ uint32_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * CMP_TILE + threadIdx.x * CMP_ITEMS;
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < CMP_ITEMS; ++k) c += (base + k < P && valid[base + k] != 0) ? 1u : 0u;
+    uint32_t tot;
+    int64_t pos = (int64_t)boff[blockIdx.x] + block_exclusive_scan(c, ws, &tot);
+    for (int k = 0; k < CMP_ITEMS; ++k) {
+        const int64_t i = base + k;
+        if (i < P && valid[i] != 0) {
+            if (pos < max_out) {
+                out[pos] = in[i];
+                if (pixel_of) pixel_of[pos] = (int32_t)i;
+            }
+            ++pos;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- bake
+constexpr int BAKE_THREADS = 128;
+
+struct BakeArgs {
+    uint2 key;
+    uint32_t request_id;
+    uint32_t point_base;
+    int spp_d, spp_s, K;
+    float sigma[FIPT_MAX_K];
+};
+
+// One thread owns one (point, lobe) pair and walks its samples in order:
+// lobe 0 is the diffuse term, lobe k+1 roughness level k.  A warp holds 32
+// consecutive points of one lobe; consecutive warps cycle through the
+// lobes of the same 32 points.  Finished rays are replaced by the lane's
+// next sample immediately (no per-ray warp reconvergence), so a warp only
+// idles at the very end of its lanes' sample lists.
+template <bool STATS>
+__global__ void __launch_bounds__(BAKE_THREADS)
+k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
+       float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
+       unsigned long long* stats) {
+    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
+    int* stack = stk + threadIdx.x;
+    const int L = 1 + A.K;
+    const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
+    const int64_t w = g >> 5;
+    const int lane = (int)(g & 31);
+    const int lobe = (int)(w % L);
+    const int64_t p = (w / L) * 32 + lane;
+    if (p >= N) return;
+
+    const float2* qp = reinterpret_cast<const float2*>(q + p);
+    const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
+    float nx = q1.y, ny = q2.x, nz = q2.y;
+    float ox = q3.x, oy = q3.y, oz = q4.x;          // wo for now
+    const int skip = __float_as_int(q4.y);
+    {
+        const float il = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
+        nx *= il; ny *= il; nz *= il;
+        const float jl = 1.0f / sqrtf(ox * ox + oy * oy + oz * oz);
+        ox *= jl; oy *= jl; oz *= jl;
+    }
+    const float wox = ox, woy = oy, woz = oz;
+    const float mu_o = nx * wox + ny * woy + nz * woz;
+    const int K = A.K;
+    if (lobe > 0 && mu_o <= 1e-2f) {
+        float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
+        float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
+        o0[0] = o0[1] = o0[2] = 0.0f;
+        o1[0] = o1[1] = o1[2] = 0.0f;
+        return;
+    }
+    const int S = lobe == 0 ? A.spp_d : A.spp_s;
+    float a2 = 0.0f, g1o = 0.0f;
+    if (lobe > 0) {
+        const float sg = A.sigma[lobe - 1];
+        const float al = sg * sg;
+        a2 = al * al;
+        g1o = 2.0f * mu_o / (mu_o + sqrtf(a2 + (1.0f - a2) * mu_o * mu_o));
+    }
+    float3 tb, bb;
+    onb(nx, ny, nz, tb, bb);
+    const float eps = sc.cst->eps;
+    ox = q0.x + eps * nx;
+    oy = q0.y + eps * ny;
+    oz = q1.x + eps * nz;
+    const uint32_t pid = A.point_base + (uint32_t)p;
+
+    float acc0x = 0, acc0y = 0, acc0z = 0, acc1x = 0, acc1y = 0, acc1z = 0;
+    float wF0 = 1.0f, wF1 = 0.0f;
+    int s = 0, node = FIPT_DONE, sp = 0, steps = 0;
+    bool active = false;
+    TraceRay r;
+    BestHit best;
+    best.leaf = -1;
+    unsigned long long n_rays = 0, n_nodes = 0, n_tris = 0;
+    int max_sp = 0;
+
+    for (;;) {
+        if (node == FIPT_DONE) {
+            if (active) {
+                if (best.leaf >= 0) {
+                    const float4 le = __ldg(sc.shade + 2 * best.leaf);
+                    const float4 ca = __ldg(sc.shade + 2 * best.leaf + 1);
+                    const float lx = (best.front ? le.x : 0.0f) + ca.x;
+                    const float ly = (best.front ? le.y : 0.0f) + ca.y;
+                    const float lz = (best.front ? le.z : 0.0f) + ca.z;
+                    if (lobe == 0) {
+                        acc0x += lx; acc0y += ly; acc0z += lz;
+                    } else {
+                        acc0x += lx * wF0; acc0y += ly * wF0; acc0z += lz * wF0;
+                        acc1x += lx * wF1; acc1y += ly * wF1; acc1z += lz * wF1;
+                    }
+                }
+                active = false;
+            }
+            while (s < S) {
+                const uint4 rnd = philox4x32_10(make_uint4(pid, (uint32_t)s, (uint32_t)lobe, A.request_id), A.key);
+                ++s;
+                const float u1 = u24f(rnd.x), u2 = u24f(rnd.y);
+                float sn, cs;
+                sincospif(2.0f * u2, &sn, &cs);
+                float dx, dy, dz;
+                if (lobe == 0) {
+                    const float rr = sqrtf(u1), lz = sqrtf(1.0f - u1);
+                    const float lx = rr * cs, ly = rr * sn;
+                    dx = lx * tb.x + ly * bb.x + lz * nx;
+                    dy = lx * tb.y + ly * bb.y + lz * ny;
+                    dz = lx * tb.z + ly * bb.z + lz * nz;
+                } else {
+                    const float om = 1.0f - u1;
+                    const float den = om + a2 * u1;
+                    const float ch = sqrtf(om / den), sh = sqrtf(a2 * u1 / den);
+                    const float lx = sh * cs, ly = sh * sn;
+                    const float hx = lx * tb.x + ly * bb.x + ch * nx;
+                    const float hy = lx * tb.y + ly * bb.y + ch * ny;
+                    const float hz = lx * tb.z + ly * bb.z + ch * nz;
+                    const float c = wox * hx + woy * hy + woz * hz;
+                    dx = 2.0f * c * hx - wox;
+                    dy = 2.0f * c * hy - woy;
+                    dz = 2.0f * c * hz - woz;
+                    const float mu_i = nx * dx + ny * dy + nz * dz;
+                    if (mu_i <= 0.0f || c <= 0.0f) continue;    // a zero sample
+                    const float g1i = 2.0f * mu_i / (mu_i + sqrtf(a2 + (1.0f - a2) * mu_i * mu_i));
+                    const float wt = g1i * g1o * c / (mu_o * ch);
+                    const float x1 = 1.0f - c, x2 = x1 * x1;
+                    const float F1 = x2 * x2 * x1;
+                    wF0 = (1.0f - F1) * wt;
+                    wF1 = F1 * wt;
+                }
+                r = make_ray(ox, oy, oz, dx, dy, dz);
+                best.t = FINF;
+                best.leaf = -1;
+                best.orig = 0x7fffffff;
+                best.front = false;
+                sp = 0;
+                steps = 0;
+                node = sc.T > 0 ? 0 : FIPT_DONE;
+                active = true;
+                if (STATS) ++n_rays;
+                break;
+            }
+            if (!active) break;
+            if (node == FIPT_DONE) continue;
+        }
+        while (node >= 0) {
+            if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                node = FIPT_DONE;
+                sp = 0;
+                break;
+            }
+            const BvhNode n = load_node(sc.nodes, node);
+            if (STATS) ++n_nodes;
+            bool h0, h1;
+            float t0, t1;
+            node_test(r, n, best.t, h0, h1, t0, t1);
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp < STACK_DEPTH) {
+                    stack[sp * BAKE_THREADS] = first0 ? n.d.y : n.d.x;
+                    ++sp;
+                    if (STATS) max_sp = max(max_sp, sp);
+                } else {
+                    atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                }
+                node = first0 ? n.d.x : n.d.y;
+            } else if (h0) {
+                node = n.d.x;
+            } else if (h1) {
+                node = n.d.y;
+            } else {
+                node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+            }
+        }
+        while (node < 0 && node != FIPT_DONE) {
+            const int leaf = ~node;
+            if (leaf >= sc.T || ++steps > sc.max_steps) {
+                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                node = FIPT_DONE;
+                sp = 0;
+                break;
+            }
+            const float4 p0 = __ldg(sc.tris + 3 * leaf);
+            const int orig = __float_as_int(p0.w);
+            if (orig != skip) {
+                if (STATS) ++n_tris;
+                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
+                float t;
+                bool fr;
+                if (tri_intersect(r, p0, p1, p2, t, fr) &&
+                    (t < best.t || (t == best.t && orig < best.orig))) {
+                    best.t = t;
+                    best.leaf = leaf;
+                    best.orig = orig;
+                    best.front = fr;
+                }
+            }
+            node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+        }
+    }
+
+    const float inv = 1.0f / (float)S;
+    if (lobe == 0) {
+        Ld[3 * p + 0] = acc0x / (float)S;
+        Ld[3 * p + 1] = acc0y / (float)S;
+        Ld[3 * p + 2] = acc0z / (float)S;
+    } else {
+        float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
+        float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
+        o0[0] = acc0x / (float)S; o0[1] = acc0y / (float)S; o0[2] = acc0z / (float)S;
+        o1[0] = acc1x / (float)S; o1[1] = acc1y / (float)S; o1[2] = acc1z / (float)S;
+    }
+    (void)inv;
+    if (STATS) {
+        atomicAdd(&stats[0], n_rays);
+        atomicAdd(&stats[1], n_nodes);
+        atomicAdd(&stats[2], n_tris);
+        atomicMax(&stats[3], (unsigned long long)max_sp);
+    }
+}
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
+                         uint32_t* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 r = philox4x32_10(c, make_uint2(key[2 * i], key[2 * i + 1]));
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" fipt_status fipt_trace_closest(fipt_scene* s, const float* orig, const float* dir,
+                                          int64_t nR, const int32_t* skip_tri, int32_t* hit_tri,
+                                          float* hit_t, int32_t* hit_front, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(nR >= 0 && nR < ((int64_t)1 << 40), "bad ray count %lld", (long long)nR);
+    if (nR == 0) return FIPT_OK;
+    FIPT_REQUIRE(orig && dir && hit_tri && hit_t && hit_front, "NULL ray / hit array");
+    FIPT_REQUIRE(fipt_aligned(orig, 4) && fipt_aligned(dir, 4) && fipt_aligned(hit_tri, 4) &&
+                 fipt_aligned(hit_t, 4) && fipt_aligned(hit_front, 4) && fipt_aligned(skip_tri, 4),
+                 "arrays must be 4-byte aligned");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    FIPT_LAUNCH(k_trace, blocks(nR, TRACE_THREADS), TRACE_THREADS, 0, static_cast<cudaStream_t>(stream), s->view(), orig, dir, nR, skip_tri, hit_tri, hit_t, hit_front, s->ctx->status);
+    FIPT_LAUNCHED("trace_closest");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_camera_queries(fipt_scene* s, const float* cams, int32_t nViews,
+                                           int32_t W, int32_t H, fipt_query* out, int32_t* valid,
+                                           fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(nViews >= 0 && W >= 0 && H >= 0, "negative camera sizes");
+    const int64_t P = (int64_t)nViews * W * H;
+    if (P == 0) return FIPT_OK;
+    FIPT_REQUIRE(P < ((int64_t)1 << 31), "too many pixels");
+    FIPT_REQUIRE(cams && out && valid, "NULL camera / output array");
+    FIPT_REQUIRE(fipt_aligned(cams, 4) && fipt_aligned(out, 16) && fipt_aligned(valid, 4),
+                 "cams 4-byte, out 16-byte, valid 4-byte alignment required");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    FIPT_LAUNCH(k_camera, blocks(P, TRACE_THREADS), TRACE_THREADS, 0, static_cast<cudaStream_t>(stream), s->view(), cams, W, H, P, out, valid, s->ctx->status);
+    FIPT_LAUNCHED("camera_queries");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_compact_workspace_size(int64_t P, size_t* bytes) {
+    FIPT_REQUIRE(bytes && P >= 0, "bad arguments");
+    *bytes = (size_t)(blocks(P, CMP_TILE) + 1) * sizeof(uint32_t) + 256;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_compact_queries(const fipt_query* in, const int32_t* valid, int64_t P,
+                                            int64_t max_out, fipt_query* out, int32_t* pixel_of,
+                                            int64_t* n_out, void* ws, size_t ws_bytes,
+                                            fipt_stream stream) {
+    FIPT_REQUIRE(P >= 0 && P < ((int64_t)1 << 31) && max_out >= 0, "bad sizes");
+    FIPT_REQUIRE(n_out && fipt_aligned(n_out, 8), "n_out NULL or not 8-byte aligned");
+    size_t need;
+    fipt_compact_workspace_size(P, &need);
+    if (ws_bytes < need || !ws)
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "compact workspace %zu < %zu", ws_bytes, need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P == 0) {
+        FIPT_CUDA(cudaMemsetAsync(n_out, 0, sizeof(int64_t), st));
+        return FIPT_OK;
+    }
+    FIPT_REQUIRE(in && valid && out && fipt_aligned(in, 16) && fipt_aligned(out, 16) &&
+                 fipt_aligned(valid, 4) && fipt_aligned(pixel_of, 4), "NULL or misaligned array");
+    const unsigned nb = blocks(P, CMP_TILE);
+    uint32_t* bsum = static_cast<uint32_t*>(ws);
+    FIPT_LAUNCH(k_count_valid, nb, CMP_THREADS, 0, st, valid, P, bsum);
+    FIPT_LAUNCH(k_scan_bsum, 1, 1024, 0, st, bsum, nb, max_out, n_out);
+    FIPT_LAUNCH(k_compact, nb, CMP_THREADS, 0, st, in, valid, P, max_out, bsum, out, pixel_of);
+    FIPT_LAUNCHED("compact_queries");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
+                                 const fipt_bake_params* prm, float* Ld, float* Ls0, float* Ls1,
+                                 fipt_stream stream) {
+    FIPT_REQUIRE(s && prm, "scene / params is NULL");
+    FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 32), "bad point count %lld", (long long)N);
+    FIPT_REQUIRE(prm->K >= 1 && prm->K <= FIPT_MAX_K, "K must be in [1, %d]", FIPT_MAX_K);
+    FIPT_REQUIRE(prm->spp_diffuse >= 1 && prm->spp_specular >= 1, "spp must be >= 1");
+    for (int k = 0; k < prm->K; ++k)
+        FIPT_REQUIRE(prm->sigma[k] > 0.0f && prm->sigma[k] <= 1.0f, "sigma[%d] = %g not in (0, 1]",
+                     k, (double)prm->sigma[k]);
+    if (N == 0) return FIPT_OK;
+    FIPT_REQUIRE(q && Ld && Ls0 && Ls1, "NULL query / output array");
+    FIPT_REQUIRE(fipt_aligned(q, 8) && fipt_aligned(Ld, 4) && fipt_aligned(Ls0, 4) &&
+                 fipt_aligned(Ls1, 4) && fipt_aligned(prm->stats, 8),
+                 "q must be 8-byte aligned, outputs 4-byte");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    BakeArgs A;
+    A.key = make_uint2((uint32_t)prm->seed, (uint32_t)(prm->seed >> 32));
+    A.request_id = prm->request_id;
+    A.point_base = prm->point_base;
+    A.spp_d = prm->spp_diffuse;
+    A.spp_s = prm->spp_specular;
+    A.K = prm->K;
+    for (int k = 0; k < FIPT_MAX_K; ++k) A.sigma[k] = k < prm->K ? prm->sigma[k] : 1.0f;
+    const int64_t warps = ((N + 31) / 32) * (1 + prm->K);
+    const int64_t threads = warps * 32;
+    const unsigned nb = blocks(threads, BAKE_THREADS);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (prm->stats)
+        FIPT_LAUNCH(k_bake<true>, nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1, s->ctx->status,
+                                                  prm->stats);
+    else
+        FIPT_LAUNCH(k_bake<false>, nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1, s->ctx->status,
+                                                   nullptr);
+    FIPT_LAUNCHED("bake");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n,
+                                         uint32_t* out, fipt_stream stream) {
+    FIPT_REQUIRE(n >= 0, "negative n");
+    if (n == 0) return FIPT_OK;
+    FIPT_REQUIRE(ctr && key && out, "NULL array");
+    FIPT_LAUNCH(k_philox, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream), ctr, key, n, out);
+    FIPT_LAUNCHED("philox");
+    return FIPT_OK;
+}

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every entry point include/fipt.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "fipt.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:fipt_status|const char\*|uint64_t)\s+(fipt_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2304_05669_gb300 import _native
+    return _native.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for must in ("fipt_scene_create", "fipt_bake", "fipt_render_fwd", "fipt_render_bwd",
+                 "fipt_tri_error", "fipt_trace_closest", "fipt_camera_queries"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert missing == []
+
+
+def test_python_signatures_cover_the_header():
+    from paper_2304_05669_gb300 import _native
+    assert set(declared_symbols()) <= set(_native.SIGNATURES)
+
+
+def test_host_side_argument_checks(L):
+    from paper_2304_05669_gb300 import _native
+    n = ctypes.c_size_t()
+    assert L.fipt_scene_workspace_size(100, 36, ctypes.byref(n)) == 0
+    assert n.value > 36 * (64 + 48 + 32)
+    assert L.fipt_scene_workspace_size(-1, 36, ctypes.byref(n)) == 1
+    assert L.fipt_bake(None, None, 0, None, None, None, None, None) == 1
+    assert b"NULL" in L.fipt_last_error()
+    p = _native.BakeParams()
+    p.K = 0
+    assert L.fipt_bake(ctypes.c_void_p(1), None, 10, ctypes.byref(p), None, None, None, None) == 1
+    assert L.fipt_tri_error_workspace_size(10, 5, ctypes.byref(n)) == 0
+    assert L.fipt_render_workspace_size(1000, ctypes.byref(n)) == 0
+    assert L.fipt_compact_workspace_size(1000, ctypes.byref(n)) == 0
+    assert L.fipt_status_string(3) == b"workspace too small"
+    assert L.fipt_version().startswith(b"fipt-gb300")
+
+
+def test_query_record_is_40_bytes():
+    # x, n, wo (9 floats) + tri (int32), the layout the bindings pack
+    class Q(ctypes.Structure):
+        _fields_ = [("x", ctypes.c_float * 3), ("n", ctypes.c_float * 3),
+                    ("wo", ctypes.c_float * 3), ("tri", ctypes.c_int32)]
+    assert ctypes.sizeof(Q) == 40

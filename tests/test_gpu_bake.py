@@ -1,0 +1,131 @@
+"""GPU bake of the shading terms (Eq. 6-7, Eq. 9) vs the FP64 oracle on the
+same Philox streams, plus the closed forms the kernel must meet directly."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from parity import ETA_BAKE, bake_flat, check_bake
+from workloads import cornell_box, procedural_room, surface_queries
+
+pytestmark = pytest.mark.gpu
+
+SIGMA = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
+
+
+@pytest.fixture(scope="module")
+def fipt():
+    import paper_2304_05669_gb300 as F
+    return F
+
+
+def gpu_queries(F, q):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return F.pack_queries(t(q["x"]), t(q["n"]), t(q["wo"]), t(q["tri"]))
+
+
+def gpu_bake(F, sc, q, spp_d, spp_s, seed=0, request_id=0, point_base=0, sigma=SIGMA):
+    Ld, Ls0, Ls1 = F.bake(sc, gpu_queries(F, q), sigma, spp_d, spp_s, seed, request_id, point_base)
+    F.context().sync_status()
+    return bake_flat(Ld.cpu().numpy(), Ls0.cpu().numpy(), Ls1.cpu().numpy())
+
+
+def test_cornell_bake_matches_oracle(fipt):
+    """The 36-triangle Cornell box, 4096 points, 64 spp."""
+    m = cornell_box()
+    q = surface_queries(m, 4096, seed=0)
+    g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 64, 64, seed=0)
+    ora = O.OracleScene.from_mesh(m).bake(q, SIGMA, 64, 64, seed=0, eta=ETA_BAKE)
+    rep = check_bake(g, ora, max_ambiguous_frac=0.05)
+    print(rep)
+
+
+def test_room_bake_matches_oracle(fipt):
+    """The ~176k-triangle room, 384 points, 128 spp."""
+    m = procedural_room(1)
+    q = surface_queries(m, 384, seed=12)
+    g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 128, 128, seed=77, request_id=3)
+    ora = O.OracleScene.from_mesh(m).bake(q, SIGMA, 128, 128, seed=77, request_id=3, eta=ETA_BAKE)
+    print(check_bake(g, ora))
+
+
+def test_room_full_size_sampled(fipt):
+    """2^20 points at 128 spp in one launch (the benchmark's configuration);
+    the oracle recomputes a sample of points one by one."""
+    m = procedural_room(1)
+    N = 1 << 20
+    q = surface_queries(m, N, seed=21)
+    sc = fipt.Scene.from_mesh(m)
+    g = gpu_bake(fipt, sc, q, 128, 128, seed=5)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(N, 96, replace=False))
+    idx[-1] = N - 1
+    # each sampled point keeps its global index in the Philox counter
+    flat = np.zeros((len(idx), 3 + 6 * len(SIGMA)))
+    lo = np.zeros_like(flat)
+    hi = np.zeros_like(flat)
+    namb = np.zeros(len(idx), np.int64)
+    S = O.OracleScene.from_mesh(m)
+    for j, i in enumerate(idx):
+        one = {k: v[i:i + 1] for k, v in q.items()}
+        r = S.bake(one, SIGMA, 128, 128, seed=5, point_base=int(i), eta=ETA_BAKE)
+        flat[j], lo[j], hi[j], namb[j] = r["flat"][0], r["lo"][0], r["hi"][0], r["n_amb"][0]
+    print(check_bake(g[idx], {"flat": flat, "lo": lo, "hi": hi, "n_amb": namb}))
+
+
+def test_furnace_is_exact_and_leak_free(fipt):
+    L = 0.7
+    m = cornell_box(closed=True, furnace_radiance=L)
+    q = surface_queries(m, 8192, seed=3)
+    g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 64, 16)
+    Lf = np.float32(L)
+    assert np.max(np.abs(g[:, :3] - Lf)) <= 2e-6 * Lf
+
+
+def test_chunked_bake_equals_whole(fipt):
+    m = cornell_box()
+    q = surface_queries(m, 1000, seed=1)
+    sc = fipt.Scene.from_mesh(m)
+    whole = gpu_bake(fipt, sc, q, 16, 8, seed=9, request_id=2)
+    a = gpu_bake(fipt, sc, {k: v[:333] for k, v in q.items()}, 16, 8, seed=9, request_id=2)
+    b = gpu_bake(fipt, sc, {k: v[333:] for k, v in q.items()}, 16, 8, seed=9, request_id=2,
+                 point_base=333)
+    assert np.array_equal(whole, np.concatenate([a, b]))
+    again = gpu_bake(fipt, sc, q, 16, 8, seed=9, request_id=2)
+    assert np.array_equal(whole, again)
+    other = gpu_bake(fipt, sc, q, 16, 8, seed=9, request_id=3)
+    assert not np.array_equal(whole, other)
+
+
+@pytest.mark.parametrize("N", [1, 31, 33, 100])
+def test_ragged_sizes(fipt, N):
+    m = cornell_box()
+    q = surface_queries(m, N, seed=N)
+    g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 32, 32, seed=1)
+    ora = O.OracleScene.from_mesh(m).bake(q, SIGMA, 32, 32, seed=1, eta=ETA_BAKE)
+    check_bake(g, ora)
+
+
+def test_grazing_view_and_empty_batch(fipt):
+    m = cornell_box()
+    sc = fipt.Scene.from_mesh(m)
+    mu = 0.005
+    q = {"x": np.array([[0.5, 0.0, 0.6]], np.float32), "n": np.array([[0, 1, 0]], np.float32),
+         "wo": np.array([[np.sqrt(1 - mu * mu), mu, 0]], np.float32), "tri": np.array([-1], np.int32)}
+    g = gpu_bake(fipt, sc, q, 64, 64)
+    assert np.all(g[0, 3:] == 0) and np.all(g[0, :3] > 0)
+    empty = {k: v[:0] for k, v in q.items()}
+    Ld, Ls0, Ls1 = fipt.bake(sc, gpu_queries(fipt, empty), SIGMA, 4, 4)
+    assert Ld.shape == (0, 3) and Ls0.shape == (0, 6, 3)
+
+
+def test_stats_counters(fipt):
+    m = procedural_room(1)
+    q = surface_queries(m, 2048, seed=2)
+    sc = fipt.Scene.from_mesh(m)
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    fipt.bake(sc, gpu_queries(fipt, q), SIGMA, 8, 8, stats=stats)
+    fipt.context().sync_status()
+    rays, nodes, tris, depth = stats.cpu().tolist()
+    assert 0 < rays <= 2048 * 8 * 7
+    assert nodes > rays and tris > 0 and 0 < depth <= 48

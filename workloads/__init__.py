@@ -6,8 +6,8 @@ material parameters.  It holds none of the method's arithmetic (no sampling,
 no ray casting, no shading), so both sides of every parity test can consume
 identical bytes without sharing any computation.
 """
-from .scenes import (Mesh, cornell_box, procedural_room, building_floor,
+from .scenes import (Mesh, cornell_box, procedural_room, building_floor, shading_tables,
                      surface_queries, pinhole_views, material_params)
 
-__all__ = ["Mesh", "cornell_box", "procedural_room", "building_floor",
+__all__ = ["Mesh", "cornell_box", "procedural_room", "building_floor", "shading_tables",
            "surface_queries", "pinhole_views", "material_params"]

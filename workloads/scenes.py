@@ -405,3 +405,16 @@ def material_params(n: int, seed: int = 3):
     return {"albedo": rng.uniform(0.0, 1.0, (n, 3)).astype(np.float32),
             "rough": rng.uniform(0.02, 1.0, n).astype(np.float32),
             "metal": rng.uniform(0.0, 1.0, n).astype(np.float32)}
+
+
+def shading_tables(n: int, K: int = 6, seed: int = 7):
+    """Synthetic shading tables of the baked layout for render tests:
+    Ld [n,3], Ls0 [n,K,3], Ls1 [n,K,3] float32, non-negative, with L_s0
+    and L_s1 smooth in the roughness index (radiance-like magnitudes)."""
+    rng = np.random.default_rng(seed)
+    base = np.exp(rng.uniform(np.log(0.05), np.log(5.0), (n, 1, 3)))
+    ramp = np.linspace(1.0, 0.4, K)[None, :, None]
+    Ld = (base[:, 0] * rng.uniform(0.5, 1.5, (n, 3))).astype(np.float32)
+    Ls0 = (base * ramp * rng.uniform(0.8, 1.2, (n, K, 3))).astype(np.float32)
+    Ls1 = (0.1 * base * ramp * rng.uniform(0.8, 1.2, (n, K, 3))).astype(np.float32)
+    return Ld, Ls0, Ls1
