@@ -51,6 +51,7 @@ typedef enum fipt_status {
 #define FIPT_DEV_STACK_OVERFLOW 1   /* a traversal stack was full; that ray was cut short */
 #define FIPT_DEV_BAD_NODE 2         /* a BVH reference was out of range; that ray was stopped */
 #define FIPT_DEV_STEP_LIMIT 4       /* a walk exceeded the steps a valid tree allows; stopped */
+#define FIPT_DEV_BAD_INDEX 8        /* an input vertex index was outside [0, nV); read as 0 */
 
 typedef void* fipt_stream;               /* a cudaStream_t; NULL = the legacy default stream */
 typedef struct fipt_ctx fipt_ctx;

@@ -171,16 +171,29 @@ __device__ __forceinline__ uint64_t spread21(uint32_t v) {
     return x;
 }
 
-__global__ void k_morton(const float* __restrict__ V, const int32_t* __restrict__ F, int64_t T,
-                         const SceneConst* __restrict__ c, uint64_t* __restrict__ keys,
-                         uint32_t* __restrict__ vals) {
+// Vertex index of corner k of triangle t, clamped into [0, nV) (and flagged)
+// so that a bad index in the caller's F can never read out of bounds.
+__device__ __forceinline__ int64_t corner(const int32_t* F, int64_t t, int k, int64_t nV,
+                                          int32_t* status) {
+    const int32_t i = F[3 * t + k];
+    if (i < 0 || i >= nV) {
+        atomicOr(status, FIPT_DEV_BAD_INDEX);
+        return 0;
+    }
+    return i;
+}
+
+__global__ void k_morton(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
+                         int64_t T, const SceneConst* __restrict__ c, uint64_t* __restrict__ keys,
+                         uint32_t* __restrict__ vals, int32_t* status) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= T) return;
     uint32_t q[3];
-    const int i0 = F[3 * t], i1 = F[3 * t + 1], i2 = F[3 * t + 2];
+    const int64_t i0 = corner(F, t, 0, nV, status), i1 = corner(F, t, 1, nV, status),
+                  i2 = corner(F, t, 2, nV, status);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float x0 = V[3 * (int64_t)i0 + a], x1 = V[3 * (int64_t)i1 + a], x2 = V[3 * (int64_t)i2 + a];
+        const float x0 = V[3 * i0 + a], x1 = V[3 * i1 + a], x2 = V[3 * i2 + a];
         const float mn = fminf(fminf(x0, x1), x2), mx = fmaxf(fmaxf(x0, x1), x2);
         const double cc = __dmul_rn(0.5, __dadd_rn((double)mn, (double)mx));
         const double lo = (double)c->lo[a];
@@ -242,15 +255,16 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int64_t n, BvhNode* __r
 }
 
 // ---------------------------------------------------------------- pack
-__global__ void k_pack(const float* __restrict__ V, const int32_t* __restrict__ F,
+__global__ void k_pack(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
                        const float* __restrict__ Le, const float* __restrict__ cache,
                        const uint32_t* __restrict__ sorted_idx, int64_t T, float4* __restrict__ tris,
-                       float4* __restrict__ shade, int32_t* __restrict__ order) {
+                       float4* __restrict__ shade, int32_t* __restrict__ order, int32_t* status) {
     const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (leaf >= T) return;
     const uint32_t t = sorted_idx[leaf];
     order[leaf] = (int32_t)t;
-    const int64_t i0 = F[3 * (int64_t)t], i1 = F[3 * (int64_t)t + 1], i2 = F[3 * (int64_t)t + 2];
+    const int64_t i0 = corner(F, t, 0, nV, status), i1 = corner(F, t, 1, nV, status),
+                  i2 = corner(F, t, 2, nV, status);
     tris[3 * leaf + 0] = make_float4(V[3 * i0], V[3 * i0 + 1], V[3 * i0 + 2], __int_as_float((int)t));
     tris[3 * leaf + 1] = make_float4(V[3 * i1], V[3 * i1 + 1], V[3 * i1 + 2], 0.0f);
     tris[3 * leaf + 2] = make_float4(V[3 * i2], V[3 * i2 + 1], V[3 * i2 + 2], 0.0f);
@@ -298,6 +312,9 @@ __global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
         if (atomicAdd(&flags[p], 1) == 0) return;   // the sibling finishes this node
         __threadfence();
         const int4 ch = __ldcg(reinterpret_cast<const int4*>(nodes + p) + 3);
+        if ((ch.x < 0 ? (int64_t)~ch.x >= T : (int64_t)ch.x >= T - 1) ||
+            (ch.y < 0 ? (int64_t)~ch.y >= T : (int64_t)ch.y >= T - 1))
+            return;
         const Box b0 = ch.x < 0 ? leaf_box(tris, ~ch.x) : node_box(nodes, ch.x);
         const Box b1 = ch.y < 0 ? leaf_box(tris, ~ch.y) : node_box(nodes, ch.y);
         float4* q = reinterpret_cast<float4*>(nodes + p);
@@ -448,14 +465,16 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
     }
     FIPT_LAUNCH(k_bounds_final, 1, 32, 0, st, L.cst, nV);
     if (T > 0) {
-        FIPT_LAUNCH(k_morton, grid_for(T, 256), 256, 0, st, V, F, T, L.cst, L.keys, L.vals);
+        FIPT_LAUNCH(k_morton, grid_for(T, 256), 256, 0, st, V, nV, F, T, L.cst, L.keys, L.vals,
+                    ctx->status);
         uint64_t* sk;
         uint32_t* sv;
         fipt_status r = radix_sort_pairs<uint64_t>(L.keys, L.keys_alt, L.vals, L.vals_alt, L.hist,
                                                    T, 64, st, &sk, &sv);
         if (r != FIPT_OK) { delete s; return r; }
         s->keys = sk;   // 8 passes: the result is back in the first buffer
-        FIPT_LAUNCH(k_pack, grid_for(T, 256), 256, 0, st, V, F, Le, cache, sv, T, L.tris, L.shade, L.order);
+        FIPT_LAUNCH(k_pack, grid_for(T, 256), 256, 0, st, V, nV, F, Le, cache, sv, T, L.tris, L.shade,
+                    L.order, ctx->status);
         if (T == 1) {
             FIPT_LAUNCH(k_single, 1, 1, 0, st, L.nodes, L.tris, L.range);
         } else {
