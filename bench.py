@@ -64,6 +64,9 @@ def parse():
                     help="points in the CPU-oracle sample (cpu_baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=None,
+                    help="override the query count (small profiling cases)")
+    ap.add_argument("--spp", type=int, default=None, help="override both sample counts")
     return ap.parse_args()
 
 
@@ -413,7 +416,13 @@ def run_ours(args, wl, world, rank, local):
 
 def main():
     args = parse()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.points:
+        wl["N"] = args.points
+        wl["desc"] += "; overridden to %d points" % args.points
+    if args.spp:
+        wl["spp_d"] = wl["spp_s"] = args.spp
+        wl["desc"] += "; overridden to %d spp" % args.spp
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, wl, world, rank)

@@ -177,8 +177,9 @@ fipt_status fipt_camera_queries(fipt_scene* scene, const float* cams, int32_t nV
                                 int32_t H, fipt_query* out, int32_t* valid, fipt_stream stream);
 
 /* Stream compaction of query records in order: the first max_out records
- * with valid != 0 are copied to out; pixel_of [max_out] i32 (nullable)
- * receives their source index; *n_out (device i64) the count written. */
+ * with valid != 0 are copied to out (16-byte aligned; may be NULL when
+ * max_out is 0); pixel_of [max_out] i32 (nullable) receives their source
+ * index; *n_out (device i64) the count written. */
 fipt_status fipt_compact_workspace_size(int64_t P, size_t* bytes);
 fipt_status fipt_compact_queries(const fipt_query* in, const int32_t* valid, int64_t P,
                                  int64_t max_out, fipt_query* out, int32_t* pixel_of,

@@ -523,8 +523,9 @@ extern "C" fipt_status fipt_compact_queries(const fipt_query* in, const int32_t*
         FIPT_CUDA(cudaMemsetAsync(n_out, 0, sizeof(int64_t), st));
         return FIPT_OK;
     }
-    FIPT_REQUIRE(in && valid && out && fipt_aligned(in, 16) && fipt_aligned(out, 16) &&
-                 fipt_aligned(valid, 4) && fipt_aligned(pixel_of, 4), "NULL or misaligned array");
+    FIPT_REQUIRE(in && valid && (out || max_out == 0) && fipt_aligned(in, 16) &&
+                 fipt_aligned(out, 16) && fipt_aligned(valid, 4) && fipt_aligned(pixel_of, 4),
+                 "NULL or misaligned array");
     const unsigned nb = blocks(P, CMP_TILE);
     uint32_t* bsum = static_cast<uint32_t*>(ws);
     FIPT_LAUNCH(k_count_valid, nb, CMP_THREADS, 0, st, valid, P, bsum);
