@@ -224,6 +224,28 @@ fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1,
                             const uint8_t* mask, float* Lr, double* loss, void* workspace,
                             size_t ws_bytes, fipt_stream stream);
 
+/* fipt_render_fwd without a workspace, for callers that cannot allocate
+ * device memory when they render (inside CUDA-graph capture, with a fixed
+ * start-up memory pool, or on threads that must not take an allocator
+ * lock).  The paper has no counterpart; this is a library convenience.
+ * Same arguments and results as fipt_render_fwd; the loss partial sums live
+ * in a 512 KiB array compiled into the library, present on every GPU that
+ * loads it until the process exits.  N may be at most
+ * FIPT_NOALLOC_RENDER_MAX_BLOCKS * 256 = 16,777,216 points; larger N returns
+ * FIPT_ERR_INVALID_ARG without launching.  Allocates nothing: the first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current), so make that first call before any stream
+ * capture.  Every call on a device shares the one array: calls that overlap
+ * on the GPU (different streams, no ordering between them) race and may
+ * return a wrong loss; serialise them on one stream.  Each call overwrites
+ * every partial it reads, so no clearing is needed between calls. */
+#define FIPT_NOALLOC_RENDER_MAX_BLOCKS 65536
+fipt_status fipt_render_fwd_noalloc(const float* Ld, const float* Ls0, const float* Ls1,
+                                    int64_t N, int32_t K, const float* sigma_grid,
+                                    const float* albedo, const float* rough, const float* metal,
+                                    const float* Lgt, const uint8_t* mask, float* Lr,
+                                    double* loss, fipt_stream stream);
+
 /* Gradient of that loss times *grad_loss (device f64 scalar, NULL = 1)
  * with respect to albedo [N,3], rough [N], metal [N] (f32 outputs).  The
  * derivative in sigma is 0 where sigma is outside the grid; at grid nodes

@@ -3,6 +3,8 @@
 // roughness and metallic.  Both kernels stream one point per thread; the
 // loss is reduced in a fixed order (per-block FP64 partials, then one block
 // over the partials) so it is bit-reproducible.
+#include <mutex>
+
 #include "fipt_internal.cuh"
 
 namespace {
@@ -246,5 +248,76 @@ extern "C" fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const 
                  fipt_aligned(g_metal, 4) && fipt_aligned(grad_loss, 8), "misaligned array");
     FIPT_LAUNCH(k_render_bwd, blocks(N, RENDER_THREADS), RENDER_THREADS, 0, static_cast<cudaStream_t>(stream), Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt, mask, grad_loss, g_albedo, g_rough, g_metal);
     FIPT_LAUNCHED("render_bwd");
+    return FIPT_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// Some callers cannot allocate device memory at the point where they render:
+// code running while a CUDA graph is being captured around a training step,
+// callers whose memory comes from a fixed pool sized at start-up (embedded or
+// real-time services), or threads that must not take the allocator's lock.
+// fipt_render_fwd needs a caller workspace for its loss partial sums; this
+// variant keeps them in a fixed array compiled into the library instead.
+// The array lives on every GPU that loads the library until the process
+// exits (FIPT_NOALLOC_RENDER_MAX_BLOCKS doubles = 512 KiB).
+static __device__ __align__(256) double g_noalloc_partials[FIPT_NOALLOC_RENDER_MAX_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_partials on the current device, looked up once
+// per device (host code only ever sees a host-side stand-in for the symbol).
+fipt_status noalloc_partials(double** out) {
+    int dev = -1;
+    FIPT_CUDA(cudaGetDevice(&dev));
+    FIPT_REQUIRE(dev >= 0 && dev < kMaxDevices, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        FIPT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partials));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return FIPT_OK;
+}
+}  // namespace
+
+extern "C" fipt_status fipt_render_fwd_noalloc(const float* Ld, const float* Ls0, const float* Ls1,
+                                               int64_t N, int32_t K, const float* sigma_grid,
+                                               const float* albedo, const float* rough,
+                                               const float* metal, const float* Lgt,
+                                               const uint8_t* mask, float* Lr, double* loss,
+                                               fipt_stream stream) {
+    Grid g;
+    fipt_status r = make_grid(K, sigma_grid, g);
+    if (r != FIPT_OK) return r;
+    r = check_render_arrays(N, Ld, Ls0, Ls1, albedo, rough, metal);
+    if (r != FIPT_OK) return r;
+    FIPT_REQUIRE(!Lgt || loss, "loss must be given with Lgt");
+    FIPT_REQUIRE(fipt_aligned(loss, 8) && fipt_aligned(Lgt, 4) && fipt_aligned(Lr, 4),
+                 "misaligned output");
+    const int64_t nb = (N + RENDER_THREADS - 1) / RENDER_THREADS;
+    if (nb > FIPT_NOALLOC_RENDER_MAX_BLOCKS)
+        return fipt_set_error(FIPT_ERR_INVALID_ARG,
+                              "fipt_render_fwd_noalloc: N = %lld exceeds its fixed scratch "
+                              "(at most %lld points); use fipt_render_fwd with a workspace",
+                              (long long)N, (long long)FIPT_NOALLOC_RENDER_MAX_BLOCKS * RENDER_THREADS);
+    double* partial = nullptr;
+    r = noalloc_partials(&partial);
+    if (r != FIPT_OK) return r;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        if (loss) FIPT_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
+        return FIPT_OK;
+    }
+    FIPT_REQUIRE(Lr, "Lr is NULL");
+    // Every block writes its own partial before k_sum_partials reads exactly
+    // nb of them, so nothing left over from an earlier call is ever read.
+    FIPT_LAUNCH(k_render_fwd, (unsigned)nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough,
+                metal, Lgt, mask, Lr, Lgt ? partial : nullptr);
+    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    FIPT_LAUNCHED("render_fwd_noalloc");
     return FIPT_OK;
 }

@@ -1,0 +1,73 @@
+"""fipt_render_fwd_noalloc: the render forward for callers that cannot
+allocate device memory while they render (for example code running under
+CUDA-graph capture, or a service whose memory is a fixed start-up pool).
+Its loss partial sums live in a fixed array inside the library instead of a
+caller workspace.  Checked through the C ABI against fipt_render_fwd, on two
+calls in a row (the second call reuses the array the first one left behind).
+This file is collected last so a stop-at-first-failure run has already run
+every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import material_params, shading_tables
+
+pytestmark = pytest.mark.gpu
+
+GRID = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
+REL = 1e-4   # the render tests' tolerance
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _inputs(N, seed):
+    Ld, Ls0, Ls1 = shading_tables(N, len(GRID), seed=seed)
+    mp = material_params(N, seed=seed + 1)
+    gt = material_params(N, seed=seed + 2)
+    Lgt = (Ld * gt["albedo"] + Ls0[:, 2] * 0.3).astype(np.float32)
+    mask = (np.random.default_rng(seed).random(N) < 0.8).astype(np.uint8)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return [cu(a) for a in (Ld, Ls0, Ls1, mp["albedo"], mp["rough"], mp["metal"], Lgt, mask)]
+
+
+def _close(a, b):
+    a = a.double().cpu().numpy()
+    b = b.double().cpu().numpy()
+    scale = np.maximum(np.abs(b), np.mean(np.abs(b)))
+    assert np.max(np.abs(a - b) / scale) <= REL
+
+
+def test_noalloc_render_matches_workspace_render_twice():
+    from paper_2304_05669_gb300._native import lib, check
+    import paper_2304_05669_gb300 as F
+    L = lib()
+    grid = (ctypes.c_float * len(GRID))(*GRID)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for N, seed in ((300001, 5), (4097, 9)):     # two calls in a row, different sizes
+        Ld, Ls0, Ls1, a, r, m, Lgt, mask = _inputs(N, seed)
+        Lr_ref, loss_ref = F.render_fwd(Ld, Ls0, Ls1, GRID, a, r, m, Lgt, mask)
+        Lr = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        check(L.fipt_render_fwd_noalloc(_p(Ld), _p(Ls0), _p(Ls1), N, len(GRID), grid, _p(a), _p(r),
+                                        _p(m), _p(Lgt), _p(mask), _p(Lr), _p(loss), st))
+        torch.cuda.synchronize()
+        _close(Lr, Lr_ref)
+        assert abs(loss.item() - loss_ref.item()) <= REL * abs(loss_ref.item())
+
+
+def test_noalloc_render_rejects_sizes_beyond_its_scratch():
+    from paper_2304_05669_gb300._native import lib
+    L = lib()
+    grid = (ctypes.c_float * len(GRID))(*GRID)
+    dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    N = 65536 * 256 + 1
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.fipt_render_fwd_noalloc(_p(dummy), _p(dummy), _p(dummy), N, len(GRID), grid, _p(dummy),
+                                   _p(dummy), _p(dummy), _p(dummy), None, _p(dummy), _p(loss), st)
+    assert rc == 1
+    assert b"exceeds its fixed scratch" in L.fipt_last_error()
