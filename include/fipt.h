@@ -270,6 +270,102 @@ fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* 
                            const float* Lgt, int64_t P, int64_t T, double* err_sum, int32_t* count, void* workspace,
                            size_t ws_bytes, fipt_stream stream);
 
+/* ------------------------------------------------------------ serving */
+/* A request loop over resident scenes with continuous batching (a serving
+ * pattern around the bake; the paper runs one bake per scene offline).
+ *
+ * fipt_server_create allocates one device arena of hbm_budget bytes (the
+ * admission budget), two streams, and starts a host scheduler thread.
+ * Requests are admitted in arrival order as arena space frees up; each
+ * batch takes chunks of up to chunk_points points round-robin from every
+ * admitted bake request (any scene) until max_batch_rays rays and runs them
+ * in ONE kernel launch, together with the render requests admitted so far;
+ * up to two batches are in flight, so later arrivals overlap earlier work.
+ * A chunk keeps the request-local Philox counters (point_base = its offset
+ * in the request), so every result is bit-identical to a standalone
+ * fipt_bake / fipt_render_fwd / fipt_render_bwd of the same request.
+ * All host buffers of a request must stay valid until it completes; pinned
+ * (page-locked) buffers let copies overlap compute.  No device code waits;
+ * the scheduler polls CUDA events on the host. */
+#define FIPT_REQ_BAKE 0
+#define FIPT_REQ_RENDER 1
+
+typedef struct fipt_server fipt_server;
+
+typedef struct fipt_request {
+    int32_t kind;                 /* FIPT_REQ_BAKE or FIPT_REQ_RENDER */
+    int32_t target;               /* scene id (bake) or table id (render) */
+    int64_t n;                    /* points (bake) or table rows (render) */
+    int64_t first;                /* render: first table row */
+    /* bake: HOST queries [n]; params (point_base ignored, stats must be
+     * NULL); HOST outputs Ld [n,3], Ls0 [n,K,3], Ls1 [n,K,3] */
+    const fipt_query* queries;
+    fipt_bake_params params;
+    float* Ld;
+    float* Ls0;
+    float* Ls1;
+    /* render (Eq. 5, 8, 14 over table rows [first, first+n)): HOST inputs
+     * albedo [n,3], rough [n], metal [n], Lgt [n,3]; HOST outputs (each may
+     * be NULL) Lr [n,3], loss [1], g_albedo [n,3], g_rough [n], g_metal [n] */
+    const float* albedo;
+    const float* rough;
+    const float* metal;
+    const float* Lgt;
+    float* Lr;
+    double* loss;
+    float* g_albedo;
+    float* g_rough;
+    float* g_metal;
+} fipt_request;
+
+typedef struct fipt_server_stats {
+    uint64_t batches;                /* batches launched */
+    uint64_t chunks;                 /* bake chunks launched */
+    uint64_t rays;                   /* bake rays launched */
+    uint64_t max_requests_per_batch; /* most requests sharing one batch */
+    uint64_t bytes_in_use;           /* arena bytes held by admitted requests */
+    uint64_t peak_bytes;
+    uint64_t pending;                /* requests waiting for admission */
+} fipt_server_stats;
+
+fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int64_t max_batch_rays,
+                               int64_t chunk_points, fipt_server** out);
+/* Registers a built scene (kept alive by the caller) -> *id for bake requests. */
+fipt_status fipt_server_add_scene(fipt_server* srv, fipt_scene* scene, int32_t* id);
+/* Registers resident device tables (Ld [N,3], Ls0/Ls1 [N,K,3]; sigma_grid
+ * HOST [K]) -> *id for render requests.  Kept alive by the caller. */
+fipt_status fipt_server_add_table(fipt_server* srv, const float* Ld, const float* Ls0,
+                                  const float* Ls1, int64_t N, int32_t K,
+                                  const float* sigma_grid, int32_t* id);
+/* Queues a request (the struct is copied) -> *ticket.  A request needing
+ * more device memory than the whole budget completes at once with result
+ * FIPT_ERR_BUDGET; bad ids / parameters return FIPT_ERR_INVALID_ARG. */
+fipt_status fipt_server_submit(fipt_server* srv, const fipt_request* req, uint64_t* ticket);
+/* *done = 1 once the request's outputs are in its host buffers; *result is
+ * its status (FIPT_OK, FIPT_ERR_BUDGET, FIPT_ERR_DEVICE_CHECK, ...). */
+fipt_status fipt_server_poll(fipt_server* srv, uint64_t ticket, int32_t* done, fipt_status* result);
+/* Blocks until done or timeout_us elapses (then returns FIPT_ERR_TIMEOUT). */
+fipt_status fipt_server_wait(fipt_server* srv, uint64_t ticket, int64_t timeout_us,
+                             fipt_status* result);
+/* Host steady-clock seconds at submit, admission and completion. */
+fipt_status fipt_server_times(fipt_server* srv, uint64_t ticket, double* t_submit, double* t_admit,
+                              double* t_done);
+/* Forgets a finished request. */
+fipt_status fipt_server_release(fipt_server* srv, uint64_t ticket);
+fipt_status fipt_server_get_stats(fipt_server* srv, fipt_server_stats* out);
+/* Cancels requests not yet admitted (result FIPT_ERR_NOT_FOUND), drains
+ * admitted work, joins the scheduler and frees the arena. */
+fipt_status fipt_server_destroy(fipt_server* srv);
+
+/* First-fit arena bookkeeping the server uses for admission (host only,
+ * offsets in [0, bytes), 256-byte granularity, neighbours coalesce). */
+typedef struct fipt_arena fipt_arena;
+fipt_status fipt_arena_create(size_t bytes, fipt_arena** out);
+fipt_status fipt_arena_alloc(fipt_arena* a, size_t bytes, size_t* offset);  /* FIPT_ERR_BUDGET when full */
+fipt_status fipt_arena_free(fipt_arena* a, size_t offset, size_t bytes);
+fipt_status fipt_arena_info(fipt_arena* a, size_t* used, size_t* peak, size_t* largest_free);
+fipt_status fipt_arena_destroy(fipt_arena* a);
+
 /* ------------------------------------------------------------ checks */
 /* Philox4x32-10 on the device (parity check of the sampler's stream):
  * ctr [n,4] u32, key [n,2] u32 -> out [n,4] u32. */

@@ -14,11 +14,12 @@ import ctypes
 
 import torch
 
-from ._native import BakeParams, FiptError, FIPT_MAX_K, check, lib, library_path
+from ._native import (BakeParams, FiptError, FIPT_MAX_K, Request, ServerStats, check, lib,
+                      library_path)
 
 __all__ = ["Context", "Scene", "bake", "render_fwd", "render_bwd", "FactorizedRender",
            "factorized_render_loss", "tri_error", "compact_queries", "pack_queries",
-           "unpack_queries", "philox", "FiptError", "library_path", "context"]
+           "unpack_queries", "philox", "FiptError", "library_path", "context", "Server"]
 
 
 def _ptr(t):
@@ -329,3 +330,116 @@ def philox(ctr, key, stream=None):
     out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
     check(lib().fipt_debug_philox(_ptr(ctr), _ptr(key), n, _ptr(out), _stream(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching request loop over resident scenes (fipt_server_*).
+
+    Host inputs should be pinned CPU tensors so copies overlap compute; the
+    server allocates pinned host outputs per request."""
+
+    BAKE, RENDER = 0, 1
+
+    def __init__(self, hbm_budget: int, max_batch_rays: int = 1 << 28, chunk_points: int = 65536,
+                 ctx: Context | None = None):
+        self.ctx = ctx or context()
+        h = ctypes.c_void_p()
+        check(lib().fipt_server_create(self.ctx.handle, int(hbm_budget), int(max_batch_rays),
+                                       int(chunk_points), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+        self._scenes = []
+        self._tables = []
+
+    def add_scene(self, scene: "Scene") -> int:
+        i = ctypes.c_int32()
+        check(lib().fipt_server_add_scene(self.handle, scene.handle, ctypes.byref(i)))
+        self._scenes.append(scene)
+        return i.value
+
+    def add_table(self, Ld, Ls0, Ls1, sigma_grid) -> int:
+        g, K = _grid(sigma_grid)
+        i = ctypes.c_int32()
+        check(lib().fipt_server_add_table(self.handle, _ptr(Ld), _ptr(Ls0), _ptr(Ls1), Ld.shape[0], K,
+                                          g, ctypes.byref(i)))
+        self._tables.append((Ld, Ls0, Ls1))
+        return i.value
+
+    def _submit(self, req, keep):
+        t = ctypes.c_uint64()
+        check(lib().fipt_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_bake(self, scene_id, queries, sigma, spp_diffuse, spp_specular=None, seed=0,
+                    request_id=0):
+        """queries: CPU float32 [n,10] (pinned for overlap).  Returns a ticket."""
+        q = queries.contiguous()
+        n, K = q.shape[0], len(sigma)
+        out = {"Ld": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
+               "Ls0": torch.empty((n, K, 3), dtype=torch.float32, pin_memory=True),
+               "Ls1": torch.empty((n, K, 3), dtype=torch.float32, pin_memory=True)}
+        r = Request()
+        r.kind, r.target, r.n, r.first = self.BAKE, int(scene_id), n, 0
+        r.queries = q.data_ptr()
+        r.params = bake_params(sigma, spp_diffuse, spp_specular, seed, request_id)
+        r.Ld, r.Ls0, r.Ls1 = out["Ld"].data_ptr(), out["Ls0"].data_ptr(), out["Ls1"].data_ptr()
+        return self._submit(r, {"in": q, "out": out})
+
+    def submit_render(self, table_id, first, albedo, rough, metal, Lgt):
+        """Render fwd/bwd over table rows [first, first+n); host tensors in."""
+        ins = [x.contiguous() for x in (albedo, rough, metal, Lgt)]
+        n = ins[0].shape[0]
+        out = {"Lr": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
+               "loss": torch.zeros(1, dtype=torch.float64, pin_memory=True),
+               "g_albedo": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
+               "g_rough": torch.empty(n, dtype=torch.float32, pin_memory=True),
+               "g_metal": torch.empty(n, dtype=torch.float32, pin_memory=True)}
+        r = Request()
+        r.kind, r.target, r.n, r.first = self.RENDER, int(table_id), n, int(first)
+        r.albedo, r.rough, r.metal, r.Lgt = [x.data_ptr() for x in ins]
+        r.Lr, r.loss = out["Lr"].data_ptr(), out["loss"].data_ptr()
+        r.g_albedo, r.g_rough, r.g_metal = (out["g_albedo"].data_ptr(), out["g_rough"].data_ptr(),
+                                            out["g_metal"].data_ptr())
+        return self._submit(r, {"in": ins, "out": out})
+
+    def poll(self, ticket):
+        done = ctypes.c_int32()
+        st = ctypes.c_int()
+        check(lib().fipt_server_poll(self.handle, int(ticket), ctypes.byref(done), ctypes.byref(st)))
+        return bool(done.value), st.value
+
+    def wait(self, ticket, timeout_s: float = 600.0) -> int:
+        """Blocks until the request is done; returns its status (0 = ok)."""
+        st = ctypes.c_int()
+        check(lib().fipt_server_wait(self.handle, int(ticket), int(timeout_s * 1e6), ctypes.byref(st)))
+        return st.value
+
+    def result(self, ticket):
+        return self._keep[ticket]["out"]
+
+    def times(self, ticket):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().fipt_server_times(self.handle, int(ticket), ctypes.byref(a), ctypes.byref(b),
+                                      ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def release(self, ticket):
+        check(lib().fipt_server_release(self.handle, int(ticket)))
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        s = ServerStats()
+        check(lib().fipt_server_get_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fipt_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,6 +25,21 @@ class BakeParams(ctypes.Structure):
                 ("sigma", ctypes.c_float * FIPT_MAX_K), ("stats", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("target", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("first", ctypes.c_int64), ("queries", ctypes.c_void_p), ("params", BakeParams),
+                ("Ld", ctypes.c_void_p), ("Ls0", ctypes.c_void_p), ("Ls1", ctypes.c_void_p),
+                ("albedo", ctypes.c_void_p), ("rough", ctypes.c_void_p), ("metal", ctypes.c_void_p),
+                ("Lgt", ctypes.c_void_p), ("Lr", ctypes.c_void_p), ("loss", ctypes.c_void_p),
+                ("g_albedo", ctypes.c_void_p), ("g_rough", ctypes.c_void_p),
+                ("g_metal", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("batches", "chunks", "rays", "max_requests_per_batch",
+                                               "bytes_in_use", "peak_bytes", "pending")]
+
+
 # name -> argtypes (restype is fipt_status = int unless listed in _RESTYPE)
 SIGNATURES = {
     "fipt_last_error": [],
@@ -52,6 +67,21 @@ SIGNATURES = {
     "fipt_tri_error_workspace_size": [I64, I64, P],
     "fipt_tri_error": [P, I64, P, P, I64, I64, P, P, P, SZ, P],
     "fipt_debug_philox": [P, P, I64, P, P],
+    "fipt_server_create": [P, SZ, I64, I64, P],
+    "fipt_server_add_scene": [P, P, P],
+    "fipt_server_add_table": [P, P, P, P, I64, I32, P, P],
+    "fipt_server_submit": [P, P, P],
+    "fipt_server_poll": [P, U64, P, P],
+    "fipt_server_wait": [P, U64, I64, P],
+    "fipt_server_times": [P, U64, P, P, P],
+    "fipt_server_release": [P, U64],
+    "fipt_server_get_stats": [P, P],
+    "fipt_server_destroy": [P],
+    "fipt_arena_create": [SZ, P],
+    "fipt_arena_alloc": [P, SZ, P],
+    "fipt_arena_free": [P, SZ, SZ],
+    "fipt_arena_info": [P, P, P, P],
+    "fipt_arena_destroy": [P],
 }
 _RESTYPE = {"fipt_last_error": ctypes.c_char_p, "fipt_status_string": ctypes.c_char_p,
             "fipt_version": ctypes.c_char_p, "fipt_launch_count": ctypes.c_uint64}

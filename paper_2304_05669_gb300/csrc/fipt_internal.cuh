@@ -72,6 +72,29 @@ struct fipt_scene {
     }
 };
 
+// Bake parameters as the kernels read them.
+struct BakeArgs {
+    uint2 key;
+    uint32_t request_id;
+    uint32_t point_base;
+    int spp_d, spp_s, K;
+    float sigma[FIPT_MAX_K];
+};
+
+// A slice of one request's points for the batched bake.
+struct BakeChunk {
+    SceneView sc;
+    const fipt_query* q;     // the chunk's first query
+    float *Ld, *Ls0, *Ls1;   // the chunk's first output rows
+    int64_t n;               // points in the chunk
+    int64_t warp_begin;      // first global warp of the chunk
+    BakeArgs A;              // A.point_base = request-local index of the first point
+};
+
+// Bake of a list of chunks (several requests / scenes) in one launch.
+fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
+                              int32_t* status, cudaStream_t st);
+
 fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
 void fipt_count_launch();
 

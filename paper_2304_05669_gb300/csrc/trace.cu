@@ -235,35 +235,17 @@ k_compact(const fipt_query* __restrict__ in, const int32_t* __restrict__ valid, 
 // ---------------------------------------------------------------- bake
 constexpr int BAKE_THREADS = 128;
 
-struct BakeArgs {
-    uint2 key;
-    uint32_t request_id;
-    uint32_t point_base;
-    int spp_d, spp_s, K;
-    float sigma[FIPT_MAX_K];
-};
 
-// One thread owns one (point, lobe) pair and walks its samples in order:
-// lobe 0 is the diffuse term, lobe k+1 roughness level k.  A warp holds 32
-// consecutive points of one lobe; consecutive warps cycle through the
-// lobes of the same 32 points.  Finished rays are replaced by the lane's
-// next sample immediately (no per-ray warp reconvergence), so a warp only
-// idles at the very end of its lanes' sample lists.
+// Bakes one (point, lobe) pair: lobe 0 is the diffuse term, lobe k+1
+// roughness level k.  The thread walks the pair's samples in order; a
+// finished ray is replaced by the next sample immediately (no per-ray warp
+// reconvergence), so a warp only idles at the end of its lanes' lists.
 template <bool STATS>
-__global__ void __launch_bounds__(BAKE_THREADS)
-k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
-       float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
-       unsigned long long* stats) {
-    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
-    int* stack = stk + threadIdx.x;
-    const int L = 1 + A.K;
-    const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
-    const int64_t w = g >> 5;
-    const int lane = (int)(g & 31);
-    const int lobe = (int)(w % L);
-    const int64_t p = (w / L) * 32 + lane;
-    if (p >= N) return;
-
+__device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
+                                          const int64_t p, const int lobe, const BakeArgs& A,
+                                          float* __restrict__ Ld, float* __restrict__ Ls0,
+                                          float* __restrict__ Ls1, int32_t* status,
+                                          unsigned long long* stats, int* stack) {
     const float2* qp = reinterpret_cast<const float2*>(q + p);
     const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
     float nx = q1.y, ny = q2.x, nz = q2.y;
@@ -288,7 +270,10 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int S = lobe == 0 ? A.spp_d : A.spp_s;
     float a2 = 0.0f, g1o = 0.0f;
     if (lobe > 0) {
-        const float sg = A.sigma[lobe - 1];
+        float sg = A.sigma[0];
+#pragma unroll
+        for (int k = 1; k < FIPT_MAX_K; ++k)
+            if (lobe - 1 == k) sg = A.sigma[k];
         const float al = sg * sg;
         a2 = al * al;
         g1o = 2.0f * mu_o / (mu_o + sqrtf(a2 + (1.0f - a2) * mu_o * mu_o));
@@ -435,7 +420,6 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
         }
     }
 
-    const float inv = 1.0f / (float)S;
     if (lobe == 0) {
         Ld[3 * p + 0] = acc0x / (float)S;
         Ld[3 * p + 1] = acc0y / (float)S;
@@ -446,13 +430,60 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
         o0[0] = acc0x / (float)S; o0[1] = acc0y / (float)S; o0[2] = acc0z / (float)S;
         o1[0] = acc1x / (float)S; o1[1] = acc1y / (float)S; o1[2] = acc1z / (float)S;
     }
-    (void)inv;
     if (STATS) {
         atomicAdd(&stats[0], n_rays);
         atomicAdd(&stats[1], n_nodes);
         atomicAdd(&stats[2], n_tris);
         atomicMax(&stats[3], (unsigned long long)max_sp);
     }
+}
+
+// A warp holds 32 consecutive points of one lobe; consecutive warps cycle
+// through the lobes of the same 32 points.
+template <bool STATS>
+__global__ void __launch_bounds__(BAKE_THREADS)
+k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
+       float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
+       unsigned long long* stats) {
+    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
+    const int L = 1 + A.K;
+    const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
+    const int64_t w = g >> 5;
+    const int lane = (int)(g & 31);
+    const int lobe = (int)(w % L);
+    const int64_t p = (w / L) * 32 + lane;
+    if (p >= N) return;
+    bake_item<STATS>(sc, q, p, lobe, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
+}
+
+// One launch over chunks of several requests, possibly on several scenes
+// (continuous batching in the server).  Chunk c owns global warps
+// [warp_begin, warp_begin + ceil(n/32) * (1 + K)); inside a chunk the
+// mapping is the single-request one, and the Philox counter uses the
+// chunk's request-local point_base, so every value equals the one a
+// separate fipt_bake of that request would produce.
+__global__ void __launch_bounds__(BAKE_THREADS)
+k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
+             int32_t* status) {
+    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
+    const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
+    const int64_t w = g >> 5;
+    const int lane = (int)(g & 31);
+    if (w >= total_warps) return;
+    int lo = 0, hi = n_chunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (chunks[mid].warp_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    const BakeChunk* C = chunks + lo;
+    const BakeArgs A = C->A;
+    const int64_t wl = w - C->warp_begin;
+    const int L = 1 + A.K;
+    const int lobe = (int)(wl % L);
+    const int64_t p = (wl / L) * 32 + lane;
+    if (p >= C->n) return;
+    bake_item<false>(C->sc, C->q, p, lobe, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
+                     stk + threadIdx.x);
 }
 
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
@@ -580,5 +611,16 @@ extern "C" fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* ke
     FIPT_REQUIRE(ctr && key && out, "NULL array");
     FIPT_LAUNCH(k_philox, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream), ctr, key, n, out);
     FIPT_LAUNCHED("philox");
+    return FIPT_OK;
+}
+
+// Internal launcher used by the serving runtime.
+fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
+                              int32_t* status, cudaStream_t st) {
+    if (n_chunks <= 0 || total_warps <= 0) return FIPT_OK;
+    const int64_t threads = total_warps * 32;
+    FIPT_LAUNCH(k_bake_batch, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks, n_chunks,
+                total_warps, status);
+    FIPT_LAUNCHED("bake_batch");
     return FIPT_OK;
 }

@@ -1,0 +1,123 @@
+"""Serving loop (continuous batching over resident scenes): every request's
+result equals a standalone bake / render of the same request, requests
+from several scenes share batches, admission respects the HBM budget, and
+waits time out instead of hanging."""
+import numpy as np
+import pytest
+import torch
+
+from workloads import cornell_box, material_params, procedural_room, shading_tables, surface_queries
+
+pytestmark = pytest.mark.gpu
+SIGMA = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_2304_05669_gb300 as F
+    scenes = [F.Scene.from_mesh(cornell_box()), F.Scene.from_mesh(procedural_room(1))]
+    meshes = [cornell_box(), procedural_room(1)]
+    return F, scenes, meshes
+
+
+def host_queries(F, q):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    return F.pack_queries(t(q["x"]), t(q["n"]), t(q["wo"]), t(q["tri"])).pin_memory()
+
+
+def close(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = np.maximum(np.abs(b), np.mean(np.abs(b)) if b.size else 0.0)
+    return b.size == 0 or np.max(np.abs(a - b) / np.where(scale > 0, scale, 1)) <= REL
+
+
+def test_mixed_requests_equal_standalone_results(setup):
+    F, scenes, meshes = setup
+    srv = F.Server(256 << 20, max_batch_rays=1 << 23, chunk_points=2048)
+    ids = [srv.add_scene(s) for s in scenes]
+    rng = np.random.default_rng(1)
+    jobs = []
+    for j in range(14):
+        sc = j % 2
+        n = int(rng.choice([1, 33, 1000, 5000, 20000]))
+        spp = int(rng.choice([4, 8, 16]))
+        q = surface_queries(meshes[sc], n, seed=100 + j)
+        qh = host_queries(F, q)
+        t = srv.submit_bake(ids[sc], qh, SIGMA, spp, spp, seed=7, request_id=j)
+        jobs.append((t, sc, qh, spp, j))
+    # render requests on a resident table
+    N = 50000
+    Ld, Ls0, Ls1 = [torch.from_numpy(a).cuda() for a in shading_tables(N, 6, seed=3)]
+    tab = srv.add_table(Ld, Ls0, Ls1, SIGMA)
+    renders = []
+    for j, (first, n) in enumerate([(0, 4096), (1000, 20000), (40000, 10000)]):
+        mp = material_params(n, seed=50 + j)
+        gt = material_params(n, seed=60 + j)
+        Lgt = (np.asarray(mp["albedo"]) * 0.5 + 0.1).astype(np.float32)
+        ins = [torch.from_numpy(a).pin_memory() for a in (mp["albedo"], mp["rough"], mp["metal"], Lgt)]
+        renders.append((srv.submit_render(tab, first, *ins), first, n, ins))
+    for t, sc, qh, spp, j in jobs:
+        assert srv.wait(t) == 0
+        got = srv.result(t)
+        ref = F.bake(scenes[sc], qh.cuda(), SIGMA, spp, spp, seed=7, request_id=j)
+        for g, r in zip((got["Ld"], got["Ls0"], got["Ls1"]), ref):
+            assert close(g.numpy(), r.cpu().numpy())
+    for t, first, n, ins in renders:
+        assert srv.wait(t) == 0
+        got = srv.result(t)
+        d = [x.cuda() for x in ins]
+        sl = slice(first, first + n)
+        Lr, loss = F.render_fwd(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
+        ga, gr, gm = F.render_bwd(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
+        assert close(got["Lr"].numpy(), Lr.cpu().numpy())
+        assert abs(got["loss"].item() - loss.item()) <= REL * abs(loss.item())
+        for g, r in ((got["g_albedo"], ga), (got["g_rough"], gr), (got["g_metal"], gm)):
+            assert close(g.numpy(), r.cpu().numpy())
+    st = srv.stats()
+    assert st["batches"] > 1 and st["max_requests_per_batch"] > 2   # requests share batches
+    assert st["peak_bytes"] <= 256 << 20 and st["bytes_in_use"] == 0
+    srv.close()
+    F.context().sync_status()
+
+
+def test_budget_admission_and_timeouts(setup):
+    F, scenes, meshes = setup
+    budget = 4 << 20                      # fits one ~20k-point bake at a time
+    srv = F.Server(budget, max_batch_rays=1 << 22, chunk_points=4096)
+    sid = srv.add_scene(scenes[1])
+    q = surface_queries(meshes[1], 20000, seed=3)
+    qh = host_queries(F, q)
+    tickets = [srv.submit_bake(sid, qh, SIGMA, 64, 64, seed=1, request_id=i) for i in range(4)]
+    # a zero timeout on work still queued reports FIPT_ERR_TIMEOUT instead of blocking
+    with pytest.raises(F.FiptError) as e:
+        srv.wait(tickets[-1], timeout_s=0.0)
+    assert e.value.status == 5
+    # a request bigger than the whole budget completes at once with FIPT_ERR_BUDGET (4)
+    big = host_queries(F, surface_queries(meshes[1], 40000, seed=4))
+    tb = srv.submit_bake(sid, big, SIGMA, 4, 4)
+    assert srv.wait(tb, 5.0) == 4
+    for t in tickets:
+        assert srv.wait(t) == 0
+    ref = F.bake(scenes[1], qh.cuda(), SIGMA, 64, 64, seed=1, request_id=3)
+    assert close(srv.result(tickets[3])["Ld"].numpy(), ref[0].cpu().numpy())
+    st = srv.stats()
+    assert st["peak_bytes"] <= budget
+    # admissions were serialised by the budget: later requests were admitted
+    # only after earlier ones finished
+    t0 = [srv.times(t) for t in tickets]
+    assert t0[1][1] >= t0[0][2] - 1e-3
+    srv.close()
+
+
+def test_submit_rejects_bad_requests(setup):
+    F, scenes, meshes = setup
+    srv = F.Server(1 << 20)
+    qh = host_queries(F, surface_queries(meshes[0], 10, seed=0))
+    with pytest.raises(F.FiptError):
+        srv.submit_bake(3, qh, SIGMA, 4, 4)          # unknown scene
+    sid = srv.add_scene(scenes[0])
+    with pytest.raises(F.FiptError):
+        srv.submit_bake(sid, qh, [1.5], 4, 4)        # sigma outside (0, 1]
+    srv.close()
