@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--points", type=int, default=None,
                     help="override the query count (small profiling cases)")
     ap.add_argument("--spp", type=int, default=None, help="override both sample counts")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests in the serving trace (0 = skip the serving measurement)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, req/s")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="HBM admission budget")
     return ap.parse_args()
 
 
@@ -243,6 +247,100 @@ def run_reference(args, wl, world, rank):
     }))
 
 
+# ---------------------------------------------------------------- serving
+def run_serving(args, F, dev):
+    """Poisson trace of bake and render requests over four resident scenes
+    (Cornell box, room, two-room and four-room floors), served with
+    continuous batching, then the same trace one request at a time."""
+    import torch
+    from workloads import (building_floor, cornell_box, material_params, pinhole_views,
+                           procedural_room, shading_tables)
+    rng = np.random.default_rng(6)
+    meshes = [cornell_box(closed=True), procedural_room(1), building_floor(5, rooms=2),
+              building_floor(5, rooms=4)]
+    scenes = [F.Scene.from_mesh(m) for m in meshes]
+    # query pools: pinhole first hits of each scene, kept in pinned host memory
+    pools = []
+    for m, sc in zip(meshes, scenes):
+        cams = torch.from_numpy(pinhole_views(m, 16, seed=8)).to(dev)
+        qa, valid = sc.camera_queries(cams, 512, 256)
+        q, _pix, n = F.compact_queries(qa, valid, 2_000_000)
+        pools.append(q[:int(n.item())].cpu().pin_memory())
+    tab_n = 266_240
+    tabs = [torch.from_numpy(a).to(dev) for a in shading_tables(tab_n, len(SIGMA), seed=9)]
+    mp = material_params(tab_n, seed=10)
+    params = [torch.from_numpy(mp[k]).pin_memory() for k in ("albedo", "rough", "metal")]
+    Lgt = torch.from_numpy(mp["albedo"] * 0.5 + 0.05).pin_memory()
+    trace = []
+    t = 0.0
+    for i in range(args.serve_requests):
+        t += rng.exponential(1.0 / args.serve_rate)
+        sc = int(rng.integers(0, 4))
+        if rng.random() < 0.5:
+            pool = pools[sc]
+            n = int(min(len(pool), np.exp(rng.uniform(np.log(1e3), np.log(2e6)))))
+            spp = int(rng.choice([16, 64, 256]))
+            off = int(rng.integers(0, len(pool) - n + 1))
+            trace.append(("bake", t, sc, off, n, spp, i))
+        else:
+            n = int(np.exp(rng.uniform(np.log(4096), np.log(266_240))))
+            first = int(rng.integers(0, tab_n - n + 1))
+            trace.append(("render", t, 0, first, n, 0, i))
+    bake_rays = sum(r[4] * r[5] * (1 + len(SIGMA)) for r in trace if r[0] == "bake")
+
+    def serve(serial):
+        srv = F.Server(int(args.serve_budget_gb * (1 << 30)), max_batch_rays=1 << 28,
+                       chunk_points=65536)
+        sids = [srv.add_scene(s) for s in scenes]
+        tid = srv.add_table(*tabs, SIGMA)
+
+        def submit(r):
+            kind, _t, sc, off, n, spp, i = r
+            if kind == "bake":
+                return srv.submit_bake(sids[sc], pools[sc][off:off + n], SIGMA, spp, spp,
+                                       seed=0, request_id=i)
+            sl = slice(off, off + n)
+            return srv.submit_render(tid, off, params[0][sl], params[1][sl], params[2][sl], Lgt[sl])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = []
+        for r in trace:
+            if serial:
+                tk = submit(r)
+                if srv.wait(tk) != 0:
+                    raise RuntimeError("request failed")
+                tickets.append(tk)
+            else:
+                delay = t0 + r[1] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(submit(r))
+        for tk in tickets:
+            if srv.wait(tk) != 0:
+                raise RuntimeError("request failed")
+        wall = time.perf_counter() - t0
+        lat = [srv.times(tk)[2] - srv.times(tk)[0] for tk in tickets]
+        st = srv.stats()
+        srv.close()
+        return wall, lat, st
+
+    wall_b, lat_b, st_b = serve(False)
+    wall_s, lat_s, _ = serve(True)
+    return {"requests": len(trace), "rate_per_s": args.serve_rate,
+            "budget_gb": args.serve_budget_gb,
+            "scenes_tris": [m.T for m in meshes],
+            "p50_ms": round(1e3 * float(np.percentile(lat_b, 50)), 2),
+            "p99_ms": round(1e3 * float(np.percentile(lat_b, 99)), 2),
+            "mrays_per_s_batched": round(bake_rays / wall_b / 1e6, 2),
+            "mrays_per_s_serial": round(bake_rays / wall_s / 1e6, 2),
+            "serial_p50_ms": round(1e3 * float(np.percentile(lat_s, 50)), 2),
+            "wall_s_batched": round(wall_b, 3), "wall_s_serial": round(wall_s, 3),
+            "batches": int(st_b["batches"]),
+            "max_requests_per_batch": int(st_b["max_requests_per_batch"]),
+            "note": "latency = completion - submission (host steady clock); "
+                    "serial = same trace, one request at a time, no arrival gaps"}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_ours(args, wl, world, rank, local):
     import torch
@@ -380,6 +478,10 @@ def run_ours(args, wl, world, rank, local):
                "sample": "%d oracle first hits (first pixels of view 0), %d+6x%d spp, FP64, %.1f s" %
                          (n, spp_d, spp_s, dt)}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        serving = run_serving(args, F, dev)
+
     if rank != 0:
         return
     value = world * rays_per_step * args.steps / t_total / 1e6
@@ -408,6 +510,7 @@ def run_ours(args, wl, world, rank, local):
                      "max_stack": max_depth},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
