@@ -38,15 +38,15 @@ def test_mixed_requests_equal_standalone_results(setup):
     srv = F.Server(256 << 20, max_batch_rays=1 << 23, chunk_points=2048)
     ids = [srv.add_scene(s) for s in scenes]
     rng = np.random.default_rng(1)
-    jobs = []
+    work = []
     for j in range(14):
         sc = j % 2
         n = int(rng.choice([1, 33, 1000, 5000, 20000]))
         spp = int(rng.choice([4, 8, 16]))
-        q = surface_queries(meshes[sc], n, seed=100 + j)
-        qh = host_queries(F, q)
-        t = srv.submit_bake(ids[sc], qh, SIGMA, spp, spp, seed=7, request_id=j)
-        jobs.append((t, sc, qh, spp, j))
+        work.append((sc, host_queries(F, surface_queries(meshes[sc], n, seed=100 + j)), spp, j))
+    # submitted in a burst, so the scheduler finds several requests waiting
+    jobs = [(srv.submit_bake(ids[sc], qh, SIGMA, spp, spp, seed=7, request_id=j), sc, qh, spp, j)
+            for sc, qh, spp, j in work]
     # render requests on a resident table
     N = 50000
     Ld, Ls0, Ls1 = [torch.from_numpy(a).cuda() for a in shading_tables(N, 6, seed=3)]
