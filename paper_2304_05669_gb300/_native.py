@@ -104,7 +104,10 @@ def lib(auto_build: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    override = os.environ.get("FIPT_LIBRARY")
+    if override:           # a library built elsewhere (e.g. another configuration)
+        auto_build = False
+    path = override or _build.LIB
     if auto_build:
         try:
             path = _build.build()

@@ -11,7 +11,10 @@
 namespace {
 
 constexpr int TRACE_THREADS = 128;
-constexpr int STACK_DEPTH = 48;
+#ifndef FIPT_STACK_DEPTH
+#define FIPT_STACK_DEPTH 32      // traversal stack entries per thread (shared memory)
+#endif
+constexpr int STACK_DEPTH = FIPT_STACK_DEPTH;
 constexpr float FINF = __builtin_huge_valf();
 
 struct BestHit {
@@ -233,41 +236,63 @@ k_compact(const fipt_query* __restrict__ in, const int32_t* __restrict__ valid, 
 }
 
 // ---------------------------------------------------------------- bake
-constexpr int BAKE_THREADS = 128;
+#ifndef FIPT_BAKE_THREADS
+#define FIPT_BAKE_THREADS 64      // small blocks: the shared stack, not threads, bounds residency
+#endif
+#ifndef FIPT_BAKE_MINB
+#define FIPT_BAKE_MINB 24        // blocks per SM the register budget must allow (75% occupancy)
+#endif
+constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 
 
-// Bakes one (point, lobe) pair: lobe 0 is the diffuse term, lobe k+1
-// roughness level k.  The thread walks the pair's samples in order; a
-// finished ray is replaced by the next sample immediately (no per-ray warp
-// reconvergence), so a warp only idles at the end of its lanes' lists.
+#ifndef FIPT_BAKE_REFILL
+#define FIPT_BAKE_REFILL 24      // lanes that must be waiting before a warp draws new rays
+#endif
+#ifndef FIPT_BAKE_SPECULATE
+#define FIPT_BAKE_SPECULATE 1    // keep walking inner nodes while other lanes look for a leaf
+#endif
+
+// Bakes one (point, lobe) pair per lane: lobe 0 is the diffuse term, lobe
+// k+1 roughness level k.  Each lane walks its pair's samples in order and
+// sums their contributions in that order (so the result does not depend on
+// scheduling).  All 32 lanes of the warp stay in the loop until every lane
+// is done (lanes without a pair, `valid` false, just vote), because three
+// warp-level decisions keep the lanes doing the same work at the same time:
+//  * refill: a lane whose ray has finished waits until FIPT_BAKE_REFILL
+//    lanes (or all remaining lanes) are waiting; they then gather their
+//    results and draw their next rays together, so the Philox stream,
+//    direction sampling and ray set-up run with many lanes active;
+//  * speculation (Aila and Laine 2009): a lane that reaches a leaf parks
+//    it and keeps descending inner nodes until every lane has a leaf;
+//  * leaves are then tested together.
 template <bool STATS>
 __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
-                                          const int64_t p, const int lobe, const BakeArgs& A,
-                                          float* __restrict__ Ld, float* __restrict__ Ls0,
-                                          float* __restrict__ Ls1, int32_t* status,
-                                          unsigned long long* stats, int* stack) {
-    const float2* qp = reinterpret_cast<const float2*>(q + p);
-    const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
-    float nx = q1.y, ny = q2.x, nz = q2.y;
-    float ox = q3.x, oy = q3.y, oz = q4.x;          // wo for now
-    const int skip = __float_as_int(q4.y);
-    {
+                                          const int64_t p, const int lobe, const bool valid,
+                                          const BakeArgs& A, float* __restrict__ Ld,
+                                          float* __restrict__ Ls0, float* __restrict__ Ls1,
+                                          int32_t* status, unsigned long long* stats, int* stack) {
+    constexpr unsigned FULL = 0xffffffffu;
+    float nx = 0.0f, ny = 0.0f, nz = 1.0f, wox = 0.0f, woy = 0.0f, woz = 1.0f;
+    float px = 0.0f, py = 0.0f, pz = 0.0f;
+    int skip = -1;
+    if (valid) {
+        const float2* qp = reinterpret_cast<const float2*>(q + p);
+        const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
+        px = q0.x; py = q0.y; pz = q1.x;
+        nx = q1.y; ny = q2.x; nz = q2.y;
+        wox = q3.x; woy = q3.y; woz = q4.x;
+        skip = __float_as_int(q4.y);
         const float il = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
         nx *= il; ny *= il; nz *= il;
-        const float jl = 1.0f / sqrtf(ox * ox + oy * oy + oz * oz);
-        ox *= jl; oy *= jl; oz *= jl;
+        const float jl = 1.0f / sqrtf(wox * wox + woy * woy + woz * woz);
+        wox *= jl; woy *= jl; woz *= jl;
     }
-    const float wox = ox, woy = oy, woz = oz;
     const float mu_o = nx * wox + ny * woy + nz * woz;
     const int K = A.K;
-    if (lobe > 0 && mu_o <= 1e-2f) {
-        float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
-        float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
-        o0[0] = o0[1] = o0[2] = 0.0f;
-        o1[0] = o1[1] = o1[2] = 0.0f;
-        return;
-    }
-    const int S = lobe == 0 ? A.spp_d : A.spp_s;
+    // pairs with nothing to sample: padding lanes, and specular terms of
+    // points seen at grazing angles (defined as zero)
+    const bool grazing = lobe > 0 && mu_o <= 1e-2f;
+    const int S = (!valid || grazing) ? 0 : (lobe == 0 ? A.spp_d : A.spp_s);
     float a2 = 0.0f, g1o = 0.0f;
     if (lobe > 0) {
         float sg = A.sigma[0];
@@ -281,14 +306,12 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
     float3 tb, bb;
     onb(nx, ny, nz, tb, bb);
     const float eps = sc.cst->eps;
-    ox = q0.x + eps * nx;
-    oy = q0.y + eps * ny;
-    oz = q1.x + eps * nz;
+    const float ox = px + eps * nx, oy = py + eps * ny, oz = pz + eps * nz;
     const uint32_t pid = A.point_base + (uint32_t)p;
 
     float acc0x = 0, acc0y = 0, acc0z = 0, acc1x = 0, acc1y = 0, acc1z = 0;
     float wF0 = 1.0f, wF1 = 0.0f;
-    int s = 0, node = FIPT_DONE, sp = 0, steps = 0;
+    int s = 0, node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
     bool active = false;
     TraceRay r;
     BestHit best;
@@ -297,7 +320,13 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
     int max_sp = 0;
 
     for (;;) {
-        if (node == FIPT_DONE) {
+        // ---------------- refill: gather finished rays, draw new ones together
+        const bool idle = node == FIPT_DONE && pleaf < 0;
+        const bool need = idle && (active || s < S);
+        const unsigned m_need = __ballot_sync(FULL, need);
+        const unsigned m_busy = __ballot_sync(FULL, !idle);
+        if ((m_need | m_busy) == 0) break;
+        if (m_need != 0 && (m_busy == 0 || __popc(m_need) >= FIPT_BAKE_REFILL) && need) {
             if (active) {
                 if (best.leaf >= 0) {
                     const float4 le = __ldg(sc.shade + 2 * best.leaf);
@@ -360,41 +389,50 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                 if (STATS) ++n_rays;
                 break;
             }
-            if (!active) break;
-            if (node == FIPT_DONE) continue;
         }
-        while (node >= 0) {
-            if (node >= sc.n_inner || ++steps > sc.max_steps) {
-                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
-                node = FIPT_DONE;
-                sp = 0;
-                break;
-            }
-            const BvhNode n = load_node(sc.nodes, node);
-            if (STATS) ++n_nodes;
-            bool h0, h1;
-            float t0, t1;
-            node_test(r, n, best.t, h0, h1, t0, t1);
-            if (h0 && h1) {
-                const bool first0 = t0 <= t1;
-                if (sp < STACK_DEPTH) {
-                    stack[sp * BAKE_THREADS] = first0 ? n.d.y : n.d.x;
-                    ++sp;
-                    if (STATS) max_sp = max(max_sp, sp);
+        // ---------------- inner nodes (speculative)
+        for (;;) {
+            if (node >= 0 && (FIPT_BAKE_SPECULATE || pleaf < 0)) {
+                if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                    atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                    node = FIPT_DONE;
+                    pleaf = -1;
+                    sp = 0;
                 } else {
-                    atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                    const BvhNode n = load_node(sc.nodes, node);
+                    if (STATS) ++n_nodes;
+                    bool h0, h1;
+                    float t0, t1;
+                    node_test(r, n, best.t, h0, h1, t0, t1);
+                    if (h0 && h1) {
+                        const bool first0 = t0 <= t1;
+                        if (sp < STACK_DEPTH) {
+                            stack[sp * BAKE_THREADS] = first0 ? n.d.y : n.d.x;
+                            ++sp;
+                            if (STATS) max_sp = max(max_sp, sp);
+                        } else {
+                            atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                        }
+                        node = first0 ? n.d.x : n.d.y;
+                    } else if (h0) {
+                        node = n.d.x;
+                    } else if (h1) {
+                        node = n.d.y;
+                    } else {
+                        node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+                    }
                 }
-                node = first0 ? n.d.x : n.d.y;
-            } else if (h0) {
-                node = n.d.x;
-            } else if (h1) {
-                node = n.d.y;
-            } else {
+            }
+            if (node < 0 && node != FIPT_DONE && pleaf < 0) {   // park the first leaf found
+                pleaf = ~node;
                 node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
             }
+            if (!__any_sync(FULL, pleaf < 0 && node >= 0)) break;   // every lane has a leaf or is done
         }
-        while (node < 0 && node != FIPT_DONE) {
-            const int leaf = ~node;
+        // ---------------- leaves
+        while (pleaf >= 0) {
+            const int leaf = pleaf;
+            pleaf = -1;
             if (leaf >= sc.T || ++steps > sc.max_steps) {
                 atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
                 node = FIPT_DONE;
@@ -416,19 +454,25 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     best.front = fr;
                 }
             }
-            node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+            if (node < 0 && node != FIPT_DONE) {      // the next entry is a leaf too
+                pleaf = ~node;
+                node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+            }
         }
     }
 
-    if (lobe == 0) {
-        Ld[3 * p + 0] = acc0x / (float)S;
-        Ld[3 * p + 1] = acc0y / (float)S;
-        Ld[3 * p + 2] = acc0z / (float)S;
-    } else {
-        float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
-        float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
-        o0[0] = acc0x / (float)S; o0[1] = acc0y / (float)S; o0[2] = acc0z / (float)S;
-        o1[0] = acc1x / (float)S; o1[1] = acc1y / (float)S; o1[2] = acc1z / (float)S;
+    if (valid) {
+        const float fs = (float)(S > 0 ? S : 1);
+        if (lobe == 0) {
+            Ld[3 * p + 0] = acc0x / fs;
+            Ld[3 * p + 1] = acc0y / fs;
+            Ld[3 * p + 2] = acc0z / fs;
+        } else {
+            float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
+            float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
+            o0[0] = acc0x / fs; o0[1] = acc0y / fs; o0[2] = acc0z / fs;
+            o1[0] = acc1x / fs; o1[1] = acc1y / fs; o1[2] = acc1z / fs;
+        }
     }
     if (STATS) {
         atomicAdd(&stats[0], n_rays);
@@ -441,7 +485,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
 // A warp holds 32 consecutive points of one lobe; consecutive warps cycle
 // through the lobes of the same 32 points.
 template <bool STATS>
-__global__ void __launch_bounds__(BAKE_THREADS)
+__global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
        float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
        unsigned long long* stats) {
@@ -452,8 +496,8 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int lane = (int)(g & 31);
     const int lobe = (int)(w % L);
     const int64_t p = (w / L) * 32 + lane;
-    if (p >= N) return;
-    bake_item<STATS>(sc, q, p, lobe, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
+    if ((w / L) * 32 >= N) return;          // whole warp past the end
+    bake_item<STATS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
 }
 
 // One launch over chunks of several requests, possibly on several scenes
@@ -462,7 +506,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
 // mapping is the single-request one, and the Philox counter uses the
 // chunk's request-local point_base, so every value equals the one a
 // separate fipt_bake of that request would produce.
-__global__ void __launch_bounds__(BAKE_THREADS)
+__global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
              int32_t* status) {
     __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
@@ -481,8 +525,7 @@ k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_w
     const int L = 1 + A.K;
     const int lobe = (int)(wl % L);
     const int64_t p = (wl / L) * 32 + lane;
-    if (p >= C->n) return;
-    bake_item<false>(C->sc, C->q, p, lobe, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
+    bake_item<false>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
                      stk + threadIdx.x);
 }
 

@@ -128,4 +128,4 @@ def test_stats_counters(fipt):
     fipt.context().sync_status()
     rays, nodes, tris, depth = stats.cpu().tolist()
     assert 0 < rays <= 2048 * 8 * 7
-    assert nodes > rays and tris > 0 and 0 < depth <= 48
+    assert nodes > rays and tris > 0 and 0 < depth <= 32
