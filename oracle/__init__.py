@@ -79,6 +79,8 @@ def _L():
         L.oracle_camera_queries.argtypes = [P, P, I32, I32, I32, P, I64, D, P, P, P, P,
                                             P, P, P]
         L.oracle_camera_queries.restype = I32
+        L.oracle_refine.argtypes = [P, P, P, P, P, P, P, P, I64, U64, U32, U32, I32, I32, I32, P,
+                                    D, I32, I32, D, I32, P, P, P]
         L.oracle_morton.argtypes = [P, I64, P, I64, P]
         L.oracle_radix_tree.argtypes = [P, P, I64, P, P, P, P]
         L.oracle_radix_tree.restype = I32
@@ -193,6 +195,35 @@ class OracleScene:
             out["hi"] = hi
             out["n_amb"] = namb
         return out
+
+    def refine(self, q, sigma, spp_d, spp_s, albedo, rough, metal, sigma_c=0.6, max_depth=8,
+               mis=True, seed=0, request_id=0, point_base=0, eta=0.0, per_sample=False,
+               nthreads=None):
+        """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10; MIS per Sec. 6) with
+        per-triangle materials albedo [T,3], rough [T], metal [T].  Returns the
+        bake layout; with per_sample also every sample's 6 values
+        ([N, 1+K, Smax, 6]) and its ambiguity flag ([N, 1+K, Smax])."""
+        sig = _c(sigma, np.float64)
+        K = len(sig)
+        x, nn, wo, tri = (_c(q["x"], np.float32), _c(q["n"], np.float32),
+                          _c(q["wo"], np.float32), _c(q["tri"], np.int32))
+        a, r, m = _c(albedo, np.float32), _c(rough, np.float32), _c(metal, np.float32)
+        N = len(x)
+        W = 3 + 6 * K
+        out = np.zeros((N, W))
+        smax = max(spp_d, spp_s)
+        ps = np.zeros((N, K + 1, smax, 6)) if per_sample else None
+        amb = np.zeros((N, K + 1, smax), np.uint8) if per_sample else None
+        _L().oracle_refine(self._h, _p(a), _p(r), _p(m), _p(x), _p(nn), _p(wo), _p(tri), N,
+                           int(seed) & (2**64 - 1), int(request_id), int(point_base), int(spp_d),
+                           int(spp_s), K, _p(sig), float(sigma_c), int(max_depth), int(bool(mis)),
+                           float(eta), int(nthreads or default_threads()), _p(out), _p(ps), _p(amb))
+        res = {"Ld": out[:, :3], "Ls0": out[:, 3:3 + 3 * K].reshape(N, K, 3),
+               "Ls1": out[:, 3 + 3 * K:].reshape(N, K, 3), "flat": out}
+        if per_sample:
+            res["per_sample"] = ps
+            res["amb"] = amb.astype(bool)
+        return res
 
     def camera_queries(self, cams, W, H, pixels, eta=0.0):
         """First hits of pinhole pixels (row layout as oracle_camera_queries)."""

@@ -792,3 +792,424 @@ int oracle_radix_tree(const uint64_t* codes, const float* tri_box, int64_t T,
     rt_build(&R, 0, T - 1, root);
     return (int)R.n;
 }
+
+/* ------------------------------------------------------------------ */
+/* Stage-3 path-traced refinement (Sec. 4.3, Eq. 10; MIS per Sec. 6)    */
+/* ------------------------------------------------------------------ */
+/* A sample starts like the stage-1 bake (same lobe, same Philox stream)
+ * and grows its path through surfaces with roughness <= sigma_c, sampling
+ * the full BRDF of Eq. 1 there, until it reaches an emitter (radiance
+ * L_e, front face only) or a surface rougher than sigma_c (radiance L',
+ * the diffuse cache).  With mis != 0 every vertex also samples a point on
+ * the emitters (area-uniform over all emitter triangles) and the two
+ * strategies are combined with the power heuristic (Veach 1997).
+ *
+ * Philox counters (lobe as in the bake: 0 diffuse, k+1 roughness level k):
+ *   lobe direction at x          (pid, s, lobe, rid)                 words 0, 1
+ *   emitter sample at x          (pid, s, lobe | 0x100, rid)         words 0 (triangle), 1, 2 (point)
+ *   BRDF at path vertex i >= 1   (pid, s, lobe | i << 9, rid)        words 0, 1 (direction), 2 (lobe)
+ *   emitter sample at vertex i   (pid, s, lobe | i << 9 | 0x100, rid) words 0, 1, 2
+ * Path vertices beyond the first hit are at most max_depth.  Per-vertex
+ * choice of the diffuse lobe: P_d = clamp(mean(k_d) / (mean(k_d) +
+ * mean(k_s)), 0.1, 0.9); at vertices seen at n.wo <= 1e-2 the specular lobe
+ * is dropped (P_d = 1), as in the bake. */
+typedef struct {
+    const oscene* S;
+    const float *ma, *ms, *mm;   /* per-triangle albedo [T,3], roughness, metallic */
+    int n_emit;
+    int* emit;                   /* emitter triangles in index order */
+    double* cdf;                 /* cumulative areas */
+    double A;                    /* total emitter area */
+    const float *qx, *qn, *qwo;
+    const int32_t* qtri;
+    int64_t N;
+    uint64_t seed;
+    uint32_t request_id, point_base;
+    int spp_d, spp_s, K;
+    const double* sigma;
+    double sigma_c;
+    int max_depth, mis;
+    double eta;
+    double* out;                 /* N x (3 + 6K) */
+    double* per_sample;          /* nullable: N x (1+K) x Smax x 6 */
+    uint8_t* amb;                /* nullable: N x (1+K) x Smax */
+    int smax;
+    int64_t next;
+} refine_job;
+
+static double ggx_D(double ch, double a2)
+{
+    double c2 = ch * ch;
+    double den = (1.0 - c2) + a2 * c2;
+    return a2 / (OPI * den * den);
+}
+
+static void philox_words(uint32_t pid, uint32_t s, uint32_t lane, uint32_t rid, uint64_t seed, double u[4])
+{
+    uint32_t ctr[4] = {pid, s, lane, rid}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)}, r[4];
+    philox10(ctr, key, r);
+    for (int i = 0; i < 4; ++i) u[i] = u24(r[i]);
+}
+
+/* Emitter sample: triangle by area (first k with cdf[k] > u0 A), uniform
+ * point by the square-root map.  Returns the triangle; *amb when u0 A lies
+ * within 1e-6 A of a cumulative boundary. */
+static int emitter_sample(const refine_job* R, const double u[4], double y[3], int* amb)
+{
+    double target = u[0] * R->A;
+    int lo = 0, hi = R->n_emit - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (R->cdf[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    if (R->n_emit > 1) {
+        if (fabs(R->cdf[lo] - target) < 1e-6 * R->A) *amb = 1;
+        if (lo > 0 && fabs(R->cdf[lo - 1] - target) < 1e-6 * R->A) *amb = 1;
+    }
+    const otri* tr = &R->S->tri[R->emit[lo]];
+    double r1 = sqrt(u[1]);
+    double b0 = 1.0 - r1, b1 = r1 * (1.0 - u[2]), b2 = r1 * u[2];
+    for (int a = 0; a < 3; ++a) y[a] = b0 * tr->v0[a] + b1 * tr->v1[a] + b2 * tr->v2[a];
+    return R->emit[lo];
+}
+
+static int is_emitter(const oscene* S, int t)
+{
+    return S->Le[3*t] > 0 || S->Le[3*t+1] > 0 || S->Le[3*t+2] > 0;
+}
+
+/* Closest hit with ambiguity flag (candidate set larger than one, or a
+ * grazing facing, or a possible miss next to a hit). */
+static void trace_flag(const refine_job* R, const double o[3], const double d[3], int skip,
+                       ohit* h, int* amb)
+{
+    ocands c;
+    closest(R->S, o, d, skip, R->eta, &c);
+    *h = c.nominal;
+    if (R->eta > 0) {
+        int distinct = 0;
+        for (int i = 0; i < c.n; ++i) if (c.c[i].id != c.nominal.id) distinct = 1;
+        if (distinct || c.overflow || c.nominal.front_amb || (c.miss_possible && c.nominal.id >= 0) ||
+            (!c.miss_possible && c.nominal.id < 0))
+            *amb = 1;
+        for (int i = 0; i < c.n; ++i) if (c.c[i].front_amb) *amb = 1;
+    }
+}
+
+/* Probability of drawing the diffuse lobe at a vertex of triangle t. */
+static double vertex_pd(const refine_job* R, int t, double mu_o)
+{
+    double kd = 0, ks = 0;
+    const double m = R->mm[t];
+    for (int c = 0; c < 3; ++c) {
+        kd += R->ma[3*t+c] * (1.0 - m);
+        ks += 0.04 * (1.0 - m) + R->ma[3*t+c] * m;
+    }
+    double Pd = kd / (kd + ks);
+    if (Pd < 0.1) Pd = 0.1;
+    if (Pd > 0.9) Pd = 0.9;
+    return mu_o > 1e-2 ? Pd : 1.0;
+}
+
+/* Full BRDF of Eq. 1 (including the cosine) at a vertex, RGB, and the pdf
+ * of the vertex's mixture sampler; P_d as in the header. */
+static void vertex_brdf(const refine_job* R, int t, const double n[3], const double wo[3],
+                        const double wi[3], double f[3], double* pdf, double* Pd_out, int* amb)
+{
+    const double a[3] = {R->ma[3*t], R->ma[3*t+1], R->ma[3*t+2]};
+    const double sg = R->ms[t], m = R->mm[t];
+    const double al = sg * sg, a2 = al * al;
+    double kd[3], ks[3];
+    for (int c = 0; c < 3; ++c) { kd[c] = a[c] * (1.0 - m); ks[c] = 0.04 * (1.0 - m) + a[c] * m; }
+    const double mu_o = dot3(n, wo), mu_i = dot3(n, wi);
+    double Pd = vertex_pd(R, t, mu_o);
+    const int spec = mu_o > 1e-2;
+    if (fabs(mu_o - 1e-2) < 1e-6) *amb = 1;
+    *Pd_out = Pd;
+    for (int c = 0; c < 3; ++c) f[c] = 0.0;
+    *pdf = 0.0;
+    if (fabs(mu_i) < 1e-5) *amb = 1;
+    if (mu_i <= 0.0) return;
+    for (int c = 0; c < 3; ++c) f[c] = kd[c] * mu_i / OPI;
+    *pdf = Pd * mu_i / OPI;
+    if (!spec) return;
+    double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+    normalize3(h);
+    const double ch = dot3(n, h), co = dot3(wo, h);
+    if (fabs(co) < 1e-5) *amb = 1;
+    if (ch <= 0.0 || co <= 0.0) return;
+    const double D = ggx_D(ch, a2);
+    const double G = smith_g1(mu_i, a2) * smith_g1(mu_o, a2);
+    const double F1 = pow(1.0 - co, 5.0), F0 = 1.0 - F1;
+    for (int c = 0; c < 3; ++c) f[c] += (ks[c] * F0 + F1) * D * G / (4.0 * mu_o);
+    *pdf += (1.0 - Pd) * D * ch / (4.0 * co);
+}
+
+/* Radiance arriving along a path that leaves `o` (offset origin of a
+ * surface point on triangle `skip`) in direction d, estimated from the
+ * first hit on (Eq. 10 with MIS).  pdf_prev = density with which d was
+ * drawn (for the MIS weight of an emitter hit). */
+static void path_radiance(const refine_job* R, const double o0[3], const double d0[3], int skip0,
+                          double pdf_prev, uint32_t pid, uint32_t s, uint32_t lobe, double L[3],
+                          int* amb)
+{
+    const oscene* S = R->S;
+    double o[3] = {o0[0], o0[1], o0[2]}, d[3] = {d0[0], d0[1], d0[2]};
+    int skip = skip0;
+    double beta[3] = {1, 1, 1};
+    L[0] = L[1] = L[2] = 0.0;
+    for (int depth = 1;; ++depth) {
+        ohit h;
+        trace_flag(R, o, d, skip, &h, amb);
+        if (h.id < 0) return;
+        if (is_emitter(S, h.id)) {
+            if (!h.front) return;
+            double w = 1.0;
+            if (R->mis && R->n_emit > 0) {
+                const otri* tr = &S->tri[h.id];
+                double ce = fabs(dot3(d, tr->ng)) / tr->area2;
+                double pl = h.t * h.t / (R->A * ce);
+                w = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
+            }
+            for (int c = 0; c < 3; ++c) L[c] += beta[c] * w * S->Le[3*h.id+c];
+            return;
+        }
+        if ((double)R->ms[h.id] > R->sigma_c) {
+            for (int c = 0; c < 3; ++c) L[c] += beta[c] * S->cache[3*h.id+c];
+            return;
+        }
+        if (depth > R->max_depth) return;
+        /* continue through a smooth surface */
+        const otri* tr = &S->tri[h.id];
+        double x[3], n[3] = {tr->ng[0], tr->ng[1], tr->ng[2]}, wo[3] = {-d[0], -d[1], -d[2]};
+        normalize3(n);
+        for (int a = 0; a < 3; ++a) x[a] = o[a] + h.t * d[a];
+        if (dot3(n, wo) < 0) for (int a = 0; a < 3; ++a) n[a] = -n[a];
+        double xo[3];
+        for (int a = 0; a < 3; ++a) xo[a] = x[a] + S->eps * n[a];
+        const uint32_t lane = lobe | ((uint32_t)depth << 9);
+        if (R->mis && R->n_emit > 0) {      /* next-event estimation at this vertex */
+            double u[4], y[3];
+            philox_words(pid, s, lane | 0x100u, R->request_id, R->seed, u);
+            int e = emitter_sample(R, u, y, amb);
+            double wl[3];
+            sub3(y, xo, wl);
+            double dist = norm3(wl);
+            for (int a = 0; a < 3; ++a) wl[a] /= dist;
+            const otri* te = &S->tri[e];
+            double ce = -dot3(wl, te->ng) / te->area2;
+            if (fabs(ce) < 1e-5) *amb = 1;
+            if (ce > 0) {
+                double f[3], pb, Pd;
+                vertex_brdf(R, h.id, n, wo, wl, f, &pb, &Pd, amb);
+                if (f[0] > 0 || f[1] > 0 || f[2] > 0) {
+                    ohit vh;
+                    trace_flag(R, xo, wl, h.id, &vh, amb);
+                    if (vh.id == e) {
+                        double pl = dist * dist / (R->A * ce);
+                        double w = pl * pl / (pl * pl + pb * pb);
+                        for (int c = 0; c < 3; ++c) L[c] += beta[c] * w * S->Le[3*e+c] * f[c] / pl;
+                    }
+                }
+            }
+        }
+        /* BRDF sample */
+        double u[4];
+        philox_words(pid, s, lane, R->request_id, R->seed, u);
+        double Pd = vertex_pd(R, h.id, dot3(n, wo));
+        double tb[3], bb[3], wi[3];
+        onb(n, tb, bb);
+        if (fabs(u[2] - Pd) < 1e-5) *amb = 1;
+        if (u[2] < Pd) {
+            double rad = sqrt(u[0]), phi = 2.0 * OPI * u[1];
+            to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u[0]), wi);
+        } else {
+            const double al = (double)R->ms[h.id] * (double)R->ms[h.id], a2 = al * al;
+            double cos2 = (1.0 - u[0]) / (1.0 + (a2 - 1.0) * u[0]);
+            double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2)), phi = 2.0 * OPI * u[1];
+            double hh[3];
+            to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, hh);
+            double c = dot3(wo, hh);
+            for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * hh[a] - wo[a];
+        }
+        double f[3], pdf;
+        vertex_brdf(R, h.id, n, wo, wi, f, &pdf, &Pd, amb);
+        if (pdf <= 0.0) return;
+        for (int c = 0; c < 3; ++c) beta[c] *= f[c] / pdf;
+        for (int a = 0; a < 3; ++a) { o[a] = xo[a]; d[a] = wi[a]; }
+        skip = h.id;
+        pdf_prev = pdf;
+    }
+}
+
+static void refine_point(refine_job* R, int64_t p)
+{
+    const oscene* S = R->S;
+    const int K = R->K, W = 3 + 6 * K;
+    double* out = R->out + (size_t)W * p;
+    for (int i = 0; i < W; ++i) out[i] = 0.0;
+    double x[3], n[3], wo[3];
+    for (int a = 0; a < 3; ++a) { x[a] = R->qx[3*p+a]; n[a] = R->qn[3*p+a]; wo[a] = R->qwo[3*p+a]; }
+    normalize3(n);
+    normalize3(wo);
+    const int32_t skip = R->qtri[p];
+    double o[3];
+    for (int a = 0; a < 3; ++a) o[a] = x[a] + S->eps * n[a];
+    double tb[3], bb[3];
+    onb(n, tb, bb);
+    const double mu_o = dot3(n, wo);
+    const uint32_t pid = R->point_base + (uint32_t)p;
+    for (int lobe = 0; lobe <= K; ++lobe) {
+        const int Sn = lobe == 0 ? R->spp_d : R->spp_s;
+        if (lobe > 0 && mu_o <= 1e-2) continue;
+        double a2 = 0, g1o = 0;
+        if (lobe > 0) {
+            const double al = R->sigma[lobe - 1] * R->sigma[lobe - 1];
+            a2 = al * al;
+            g1o = smith_g1(mu_o, a2);
+        }
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int s = 0; s < Sn; ++s) {
+            int amb = 0;
+            double c6[6] = {0, 0, 0, 0, 0, 0};
+            /* emitter sample at x (MIS) */
+            if (R->mis && R->n_emit > 0) {
+                double u[4], y[3], wl[3];
+                philox_words(pid, (uint32_t)s, (uint32_t)lobe | 0x100u, R->request_id, R->seed, u);
+                int e = emitter_sample(R, u, y, &amb);
+                sub3(y, o, wl);
+                double dist = norm3(wl);
+                for (int a = 0; a < 3; ++a) wl[a] /= dist;
+                const otri* te = &S->tri[e];
+                double ce = -dot3(wl, te->ng) / te->area2;
+                double mu_i = dot3(n, wl);
+                if (fabs(ce) < 1e-5 || fabs(mu_i) < 1e-5) amb = 1;
+                double g0 = 0, g1 = 0, pb = 0;
+                if (ce > 0 && mu_i > 0) {
+                    if (lobe == 0) { g0 = mu_i / OPI; pb = mu_i / OPI; }
+                    else {
+                        double h[3] = {wl[0] + wo[0], wl[1] + wo[1], wl[2] + wo[2]};
+                        normalize3(h);
+                        double ch = dot3(n, h), c = dot3(wo, h);
+                        if (fabs(c) < 1e-5) amb = 1;
+                        if (ch > 0 && c > 0) {
+                            double D = ggx_D(ch, a2), G = smith_g1(mu_i, a2) * g1o;
+                            double F1 = pow(1.0 - c, 5.0);
+                            g0 = (1.0 - F1) * D * G / (4.0 * mu_o);
+                            g1 = F1 * D * G / (4.0 * mu_o);
+                            pb = D * ch / (4.0 * c);
+                        }
+                    }
+                }
+                if (g0 > 0 || g1 > 0) {
+                    ohit vh;
+                    trace_flag(R, o, wl, skip, &vh, &amb);
+                    if (vh.id == e) {
+                        double pl = dist * dist / (R->A * ce);
+                        double w = pl * pl / (pl * pl + pb * pb);
+                        for (int c = 0; c < 3; ++c) {
+                            c6[c] += w * S->Le[3*e+c] * g0 / pl;
+                            c6[3+c] += w * S->Le[3*e+c] * g1 / pl;
+                        }
+                    }
+                }
+            }
+            /* lobe sample at x, as in the bake */
+            double u[4];
+            philox_words(pid, (uint32_t)s, (uint32_t)lobe, R->request_id, R->seed, u);
+            double wi[3], W0 = 1.0, W1 = 0.0, pb = 0.0;
+            int valid = 1;
+            if (lobe == 0) {
+                double rad = sqrt(u[0]), phi = 2.0 * OPI * u[1];
+                to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u[0]), wi);
+                pb = sqrt(1.0 - u[0]) / OPI;
+            } else {
+                double cos2 = (1.0 - u[0]) / (1.0 + (a2 - 1.0) * u[0]);
+                double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2)), phi = 2.0 * OPI * u[1];
+                double h[3];
+                to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, h);
+                double c = dot3(wo, h);
+                for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * h[a] - wo[a];
+                double mu_i = dot3(n, wi);
+                if (fabs(mu_i) < 1e-5 || fabs(c) < 1e-5) amb = 1;
+                if (mu_i <= 0.0 || c <= 0.0) valid = 0;
+                else {
+                    double G = smith_g1(mu_i, a2) * g1o, w = G * c / (mu_o * ch);
+                    double F1 = pow(1.0 - c, 5.0);
+                    W0 = (1.0 - F1) * w;
+                    W1 = F1 * w;
+                    pb = ggx_D(ch, a2) * ch / (4.0 * c);
+                }
+            }
+            if (valid) {
+                double L[3];
+                path_radiance(R, o, wi, skip, pb, pid, (uint32_t)s, (uint32_t)lobe, L, &amb);
+                for (int c = 0; c < 3; ++c) { c6[c] += W0 * L[c]; c6[3+c] += W1 * L[c]; }
+            }
+            for (int i = 0; i < 6; ++i) acc[i] += c6[i];
+            if (R->per_sample) {
+                double* ps = R->per_sample + ((size_t)(p * (K + 1) + lobe) * R->smax + s) * 6;
+                for (int i = 0; i < 6; ++i) ps[i] = c6[i];
+            }
+            if (R->amb) R->amb[(size_t)(p * (K + 1) + lobe) * R->smax + s] = (uint8_t)amb;
+        }
+        if (lobe == 0) for (int c = 0; c < 3; ++c) out[c] = acc[c] / Sn;
+        else for (int c = 0; c < 3; ++c) {
+            out[3 + 3*(lobe-1) + c] = acc[c] / Sn;
+            out[3 + 3*K + 3*(lobe-1) + c] = acc[3+c] / Sn;
+        }
+    }
+}
+
+static void* refine_worker(void* arg)
+{
+    refine_job* R = (refine_job*)arg;
+    for (;;) {
+        int64_t p = __atomic_fetch_add(&R->next, 1, __ATOMIC_RELAXED);
+        if (p >= R->N) break;
+        refine_point(R, p);
+    }
+    return NULL;
+}
+
+/* Stage-3 bake.  mat_a [T,3], mat_sigma [T], mat_m [T] per triangle.
+ * Outputs as oracle_bake (nominal only); per_sample (nullable) gets every
+ * sample's 6 values (L_d uses the first 3), amb (nullable) 1 for samples
+ * whose path takes a decision within rounding of a threshold. */
+int oracle_refine(const oscene* S, const float* mat_a, const float* mat_sigma, const float* mat_m,
+                  const float* qx, const float* qn, const float* qwo, const int32_t* qtri, int64_t N,
+                  uint64_t seed, uint32_t request_id, uint32_t point_base, int spp_d, int spp_s,
+                  int K, const double* sigma, double sigma_c, int max_depth, int mis, double eta,
+                  int nthreads, double* out, double* per_sample, uint8_t* amb)
+{
+    refine_job R;
+    memset(&R, 0, sizeof(R));
+    R.S = S; R.ma = mat_a; R.ms = mat_sigma; R.mm = mat_m;
+    R.emit = (int*)malloc(sizeof(int) * (size_t)(S->T > 0 ? S->T : 1));
+    R.cdf = (double*)malloc(sizeof(double) * (size_t)(S->T > 0 ? S->T : 1));
+    R.n_emit = 0;
+    R.A = 0.0;
+    for (int64_t t = 0; t < S->T; ++t)
+        if (is_emitter(S, (int)t)) {
+            R.A += 0.5 * S->tri[t].area2;
+            R.emit[R.n_emit] = (int)t;
+            R.cdf[R.n_emit] = R.A;
+            R.n_emit++;
+        }
+    R.qx = qx; R.qn = qn; R.qwo = qwo; R.qtri = qtri; R.N = N;
+    R.seed = seed; R.request_id = request_id; R.point_base = point_base;
+    R.spp_d = spp_d; R.spp_s = spp_s; R.K = K; R.sigma = sigma;
+    R.sigma_c = sigma_c; R.max_depth = max_depth; R.mis = mis; R.eta = eta;
+    R.out = out; R.per_sample = per_sample; R.amb = amb;
+    R.smax = spp_d > spp_s ? spp_d : spp_s;
+    R.next = 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    for (int i = 1; i < nthreads; ++i) pthread_create(&th[i], NULL, refine_worker, &R);
+    refine_worker(&R);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    free(R.emit);
+    free(R.cdf);
+    return 0;
+}
