@@ -207,6 +207,33 @@ fipt_status fipt_bake(fipt_scene* scene, const fipt_query* q, int64_t N,
                       const fipt_bake_params* params, float* Ld, float* Ls0, float* Ls1,
                       fipt_stream stream);
 
+/* Per-triangle materials for the refinement (stage-2 estimates in the
+ * paper): albedo [T,3], roughness [T], metallic [T] f32, original order. */
+fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, const float* rough,
+                                     const float* metal, fipt_stream stream);
+
+/* Stage-3 path-traced refinement of the shading terms (Sec. 4.3, Eq. 10,
+ * with multiple importance sampling as Sec. 6 states).  A sample starts as
+ * in fipt_bake (same lobe, same Philox stream) and grows its path through
+ * surfaces whose roughness is <= sigma_c (0.6 in the paper), sampling the
+ * full BRDF of Eq. 1 there (diffuse lobe with probability
+ * clamp(mean(k_d)/(mean(k_d)+mean(k_s)), 0.1, 0.9)), until it reaches an
+ * emitter (L_e, front face) or a rougher surface (the cache L'); at most
+ * max_depth vertices beyond the first hit.  mis != 0: every vertex also
+ * samples a point on the emitters (area-uniform over all triangles with
+ * L_e > 0) and the two strategies are combined by the power heuristic.
+ * Philox counters: lobe direction at x (pid, s, lobe, rid); emitter sample
+ * at x (pid, s, lobe|0x100, rid); BRDF at vertex i (pid, s, lobe|i<<9, rid);
+ * emitter sample at vertex i (pid, s, lobe|i<<9|0x100, rid).
+ * Outputs as fipt_bake; per_sample (nullable, device f32
+ * [N, 1+K, max(spp), 6]) receives every sample's contribution (L_d uses the
+ * first 3 values, L_s0 / L_s1 the two triples).  Requires
+ * fipt_scene_set_materials. */
+fipt_status fipt_bake_refine(fipt_scene* scene, const fipt_query* q, int64_t N,
+                             const fipt_bake_params* params, float sigma_c, int32_t max_depth,
+                             int32_t mis, float* Ld, float* Ls0, float* Ls1, float* per_sample,
+                             fipt_stream stream);
+
 /* ------------------------------------------------------------ render */
 /* Factorized render, Eq. 5 with k_d = a(1-m), k_s = 0.04(1-m) + a m (Eq. 1)
  * and the roughness lerp of Eq. 8: sigma is clamped to

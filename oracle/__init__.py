@@ -202,7 +202,9 @@ class OracleScene:
         """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10; MIS per Sec. 6) with
         per-triangle materials albedo [T,3], rough [T], metal [T].  Returns the
         bake layout; with per_sample also every sample's 6 values
-        ([N, 1+K, Smax, 6]) and its ambiguity flag ([N, 1+K, Smax])."""
+        ([N, 1+K, Smax, 6]) and its ambiguity flag ([N, 1+K, Smax]).  The
+        roughness threshold is rounded to float32 first: materials are
+        float32, so "rougher than sigma_c" is decided on float32 values."""
         sig = _c(sigma, np.float64)
         K = len(sig)
         x, nn, wo, tri = (_c(q["x"], np.float32), _c(q["n"], np.float32),
@@ -216,7 +218,8 @@ class OracleScene:
         amb = np.zeros((N, K + 1, smax), np.uint8) if per_sample else None
         _L().oracle_refine(self._h, _p(a), _p(r), _p(m), _p(x), _p(nn), _p(wo), _p(tri), N,
                            int(seed) & (2**64 - 1), int(request_id), int(point_base), int(spp_d),
-                           int(spp_s), K, _p(sig), float(sigma_c), int(max_depth), int(bool(mis)),
+                           int(spp_s), K, _p(sig), float(np.float32(sigma_c)), int(max_depth),
+                           int(bool(mis)),
                            float(eta), int(nthreads or default_threads()), _p(out), _p(ps), _p(amb))
         res = {"Ld": out[:, :3], "Ls0": out[:, 3:3 + 3 * K].reshape(N, K, 3),
                "Ls1": out[:, 3 + 3 * K:].reshape(N, K, 3), "flat": out}

@@ -17,7 +17,7 @@ import torch
 from ._native import (BakeParams, FiptError, FIPT_MAX_K, Request, ServerStats, check, lib,
                       library_path)
 
-__all__ = ["Context", "Scene", "bake", "render_fwd", "render_bwd", "FactorizedRender",
+__all__ = ["Context", "Scene", "bake", "bake_refine", "render_fwd", "render_bwd", "FactorizedRender",
            "factorized_render_loss", "tri_error", "compact_queries", "pack_queries",
            "unpack_queries", "philox", "FiptError", "library_path", "context", "Server"]
 
@@ -143,6 +143,15 @@ class Scene:
         check(lib().fipt_scene_set_cache(self.handle, _ptr(cache), _stream(stream)))
         self._keep = self._keep + (cache,)
 
+    def set_materials(self, albedo, rough, metal, stream=None):
+        """Per-triangle albedo [T,3], roughness [T], metallic [T] (refinement)."""
+        albedo = _dev(albedo, torch.float32, "albedo")
+        rough = _dev(rough, torch.float32, "rough")
+        metal = _dev(metal, torch.float32, "metal")
+        check(lib().fipt_scene_set_materials(self.handle, _ptr(albedo), _ptr(rough), _ptr(metal),
+                                             _stream(stream)))
+        self._keep = self._keep + (albedo, rough, metal)
+
     def export(self, stream=None):
         T = self.T
         ni = max(T - 1, 1 if T == 1 else 0)
@@ -237,6 +246,25 @@ def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request
     check(lib().fipt_bake(scene.handle, _ptr(q), N, ctypes.byref(p), _ptr(out[0]), _ptr(out[1]),
                           _ptr(out[2]), _stream(stream)))
     return out
+
+
+def bake_refine(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, sigma_c=0.6, max_depth=8,
+                mis=True, seed=0, request_id=0, point_base=0, per_sample=False, stream=None):
+    """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10, MIS) -> (Ld, Ls0, Ls1[, per_sample])."""
+    q = _dev(q, torch.float32, "q")
+    N = q.shape[0]
+    K = len(sigma)
+    spp_s = spp_diffuse if spp_specular is None else spp_specular
+    out = (torch.empty((N, 3), dtype=torch.float32, device=q.device),
+           torch.empty((N, K, 3), dtype=torch.float32, device=q.device),
+           torch.empty((N, K, 3), dtype=torch.float32, device=q.device))
+    ps = (torch.empty((N, K + 1, max(spp_diffuse, spp_s), 6), dtype=torch.float32, device=q.device)
+          if per_sample else None)
+    p = bake_params(sigma, spp_diffuse, spp_s, seed, request_id, point_base)
+    check(lib().fipt_bake_refine(scene.handle, _ptr(q), N, ctypes.byref(p), float(sigma_c),
+                                 int(max_depth), int(bool(mis)), _ptr(out[0]), _ptr(out[1]),
+                                 _ptr(out[2]), _ptr(ps), _stream(stream)))
+    return out + ((ps,) if per_sample else ())
 
 
 def _grid(sigma_grid):

@@ -22,7 +22,8 @@ struct SceneConst {
     float lo[3];
     float hi[3];
     float eps;          // ray-origin offset, 1e-4 * largest extent
-    int pad;
+    int n_emit;         // emitter triangles (any L_e channel > 0)
+    double A_emit;      // their total area
 };
 
 // Internal BVH node (64 bytes): both child boxes plus child references.
@@ -45,6 +46,9 @@ struct SceneView {
     int64_t T;
     int n_inner;            // internal nodes: a reference r is valid iff -T <= r < n_inner
     int max_steps;          // node + leaf visits a valid tree can need for one ray (2T + 2)
+    const float4* mats;     // 2 per leaf: (albedo rgb, roughness), (metallic, 0, 0, 0)
+    const int32_t* emit_leaf;   // emitter triangles in original index order -> leaf
+    const double* emit_cdf;     // cumulative emitter areas (same order)
 };
 
 struct fipt_scene {
@@ -64,11 +68,16 @@ struct fipt_scene {
     uint32_t* vals;
     uint32_t* vals_alt;
     uint32_t* hist;
+    float4* mats;          // [2T] per-leaf materials (fipt_scene_set_materials)
+    int32_t* inv;          // [T] leaf of each original triangle
+    int32_t* emit_leaf;    // [T] (first n_emit used)
+    double* emit_cdf;      // [T]
+    bool has_materials = false;
     size_t ws_bytes;
     SceneView view() const {
         const int64_t steps = 2 * T + 2;
         return SceneView{nodes, tris, shade, cst, T, (int)(T > 1 ? T - 1 : 1),
-                         (int)(steps < 2147483647 ? steps : 2147483647)};
+                         (int)(steps < 2147483647 ? steps : 2147483647), mats, emit_leaf, emit_cdf};
     }
 };
 
@@ -288,3 +297,82 @@ __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& t, flo
     t = make_float3(1.0f + s * nx * nx * a, s * c, -s * nx);
     b = make_float3(c, s + ny * ny * a, -ny);
 }
+
+// ---------------------------------------------------------------- traversal
+#ifndef FIPT_STACK_DEPTH
+#define FIPT_STACK_DEPTH 32      // traversal stack entries per thread (shared memory)
+#endif
+constexpr int STACK_DEPTH = FIPT_STACK_DEPTH;
+constexpr float FINF = __builtin_huge_valf();
+
+struct BestHit {
+    float t;
+    int leaf;
+    int orig;
+    bool front;
+};
+
+// Closest hit of one ray; `stack` is this thread's column of the shared
+// stack (element k at stack[k * STRIDE]).  A full stack raises the
+// overflow bit (the ray loses that subtree).
+template <int STRIDE>
+__device__ __forceinline__ void closest_hit(const SceneView& sc, const TraceRay& r, int skip,
+                                            int* stack, BestHit& best, int32_t* status) {
+    best.t = FINF;
+    best.leaf = -1;
+    best.orig = 0x7fffffff;
+    best.front = false;
+    if (sc.T == 0) return;
+    int node = 0, sp = 0, steps = 0;
+    while (node != FIPT_DONE) {
+        while (node >= 0) {
+            if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                return;
+            }
+            const BvhNode n = load_node(sc.nodes, node);
+            bool h0, h1;
+            float t0, t1;
+            node_test(r, n, best.t, h0, h1, t0, t1);
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp < STACK_DEPTH) {
+                    stack[sp * STRIDE] = first0 ? n.d.y : n.d.x;
+                    ++sp;
+                } else {
+                    atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                }
+                node = first0 ? n.d.x : n.d.y;
+            } else if (h0) {
+                node = n.d.x;
+            } else if (h1) {
+                node = n.d.y;
+            } else {
+                node = sp > 0 ? stack[--sp * STRIDE] : FIPT_DONE;
+            }
+        }
+        while (node < 0 && node != FIPT_DONE) {
+            const int leaf = ~node;
+            if (leaf >= sc.T || ++steps > sc.max_steps) {
+                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                return;
+            }
+            const float4 p0 = __ldg(sc.tris + 3 * leaf);
+            const int orig = __float_as_int(p0.w);
+            if (orig != skip) {
+                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
+                float t;
+                bool fr;
+                if (tri_intersect(r, p0, p1, p2, t, fr) &&
+                    (t < best.t || (t == best.t && orig < best.orig))) {
+                    best.t = t;
+                    best.leaf = leaf;
+                    best.orig = orig;
+                    best.front = fr;
+                }
+            }
+            node = sp > 0 ? stack[--sp * STRIDE] : FIPT_DONE;
+        }
+    }
+}
+

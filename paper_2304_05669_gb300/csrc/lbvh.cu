@@ -115,6 +115,10 @@ k_sort_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* _
 
 // ---------------------------------------------------------------- bounds
 __global__ void k_bounds_init(SceneConst* c) {
+    if (threadIdx.x == 0) {
+        c->n_emit = 0;
+        c->A_emit = 0.0;
+    }
     if (threadIdx.x < 3) {
         c->lo_key[threadIdx.x] = float_to_ordered(__int_as_float(0x7f800000));   // +inf
         c->hi_key[threadIdx.x] = float_to_ordered(__int_as_float(0xff800000));   // -inf
@@ -280,6 +284,94 @@ __global__ void k_set_cache(const float* __restrict__ cache, const int32_t* __re
     shade[2 * leaf + 1] = make_float4(cache[3 * t], cache[3 * t + 1], cache[3 * t + 2], 0.0f);
 }
 
+// ---------------------------------------------------------------- emitters
+__global__ void k_inverse(const int32_t* __restrict__ order, int64_t T, int32_t* __restrict__ inv) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf < T) inv[order[leaf]] = (int32_t)leaf;
+}
+
+// Emitter table for area sampling: emitter triangles in original index
+// order, their leaf, and cumulative areas in FP64 (areas from the float
+// vertices in double), built by one block scanning T in chunks.
+__global__ void __launch_bounds__(1024)
+k_emitters(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
+           const float* __restrict__ Le, int64_t T, const int32_t* __restrict__ inv,
+           int32_t* __restrict__ emit_leaf, double* __restrict__ emit_cdf, SceneConst* c) {
+    __shared__ int wcnt[32];
+    __shared__ double warea[32];
+    int carry = 0;
+    double carry_area = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < T; base += 1024) {
+        const int64_t t = base + threadIdx.x;
+        int flag = 0;
+        double area = 0.0;
+        if (t < T && (Le[3 * t] > 0.0f || Le[3 * t + 1] > 0.0f || Le[3 * t + 2] > 0.0f)) {
+            flag = 1;
+            int64_t i[3];
+            for (int k = 0; k < 3; ++k) {
+                const int32_t v = F[3 * t + k];
+                i[k] = (v >= 0 && v < nV) ? v : 0;
+            }
+            double e1[3], e2[3];
+            for (int a = 0; a < 3; ++a) {
+                e1[a] = (double)V[3 * i[1] + a] - (double)V[3 * i[0] + a];
+                e2[a] = (double)V[3 * i[2] + a] - (double)V[3 * i[0] + a];
+            }
+            const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+            const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+            const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+            area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+        }
+        // inclusive warp scans of the flags and areas
+        int ic = flag;
+        double ia = area;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yc = __shfl_up_sync(0xffffffffu, ic, o);
+            const double ya = __shfl_up_sync(0xffffffffu, ia, o);
+            if (lane >= o) { ic += yc; ia += ya; }
+        }
+        if (lane == 31) { wcnt[warp] = ic; warea[warp] = ia; }
+        __syncthreads();
+        if (warp == 0) {
+            int sc = wcnt[lane];
+            double sa = warea[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const int yc = __shfl_up_sync(0xffffffffu, sc, o);
+                const double ya = __shfl_up_sync(0xffffffffu, sa, o);
+                if (lane >= o) { sc += yc; sa += ya; }
+            }
+            wcnt[lane] = sc;
+            warea[lane] = sa;
+        }
+        __syncthreads();
+        const int before = warp > 0 ? wcnt[warp - 1] : 0;
+        const double before_a = warp > 0 ? warea[warp - 1] : 0.0;
+        if (flag) {
+            const int pos = carry + before + ic - 1;
+            emit_leaf[pos] = inv[t];
+            emit_cdf[pos] = carry_area + before_a + ia;
+        }
+        carry += wcnt[31];
+        carry_area += warea[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        c->n_emit = carry;
+        c->A_emit = carry_area;
+    }
+}
+
+__global__ void k_set_materials(const float* __restrict__ albedo, const float* __restrict__ rough,
+                                const float* __restrict__ metal, const int32_t* __restrict__ order,
+                                int64_t T, float4* __restrict__ mats) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    const int64_t t = order[leaf];
+    mats[2 * leaf] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], rough[t]);
+    mats[2 * leaf + 1] = make_float4(metal[t], 0.0f, 0.0f, 0.0f);
+}
+
 // ---------------------------------------------------------------- refit
 struct Box {
     float lx, ly, lz, hx, hy, hz;
@@ -398,6 +490,9 @@ struct SceneLayout {
     uint64_t *keys, *keys_alt;
     uint32_t *vals, *vals_alt, *hist;
     int32_t *range, *parent, *leaf_parent, *flags;
+    float4* mats;
+    int32_t *inv, *emit_leaf;
+    double* emit_cdf;
     size_t bytes;
 };
 
@@ -420,6 +515,10 @@ SceneLayout carve_scene(void* ws, int64_t T) {
     L.parent = c.take<int32_t>((size_t)ni);
     L.leaf_parent = c.take<int32_t>((size_t)t1);
     L.flags = c.take<int32_t>((size_t)ni);
+    L.mats = c.take<float4>((size_t)(2 * t1));
+    L.inv = c.take<int32_t>((size_t)t1);
+    L.emit_leaf = c.take<int32_t>((size_t)t1);
+    L.emit_cdf = c.take<double>((size_t)t1);
     L.bytes = c.off + 256;
     return L;
 }
@@ -457,6 +556,7 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
     s->keys = L.keys; s->keys_alt = L.keys_alt; s->vals = L.vals; s->vals_alt = L.vals_alt;
     s->hist = L.hist; s->range = L.range; s->parent = L.parent; s->leaf_parent = L.leaf_parent;
     s->flags = L.flags; s->ws_bytes = L.bytes;
+    s->mats = L.mats; s->inv = L.inv; s->emit_leaf = L.emit_leaf; s->emit_cdf = L.emit_cdf;
 
     FIPT_LAUNCH(k_bounds_init, 1, 32, 0, st, L.cst);
     if (nV > 0) {
@@ -485,6 +585,8 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
             FIPT_LAUNCH(k_refit, grid_for(T, 256), 256, 0, st, L.nodes, L.tris, L.parent, L.leaf_parent,
                                                       L.flags, T);
         }
+        FIPT_LAUNCH(k_inverse, grid_for(T, 256), 256, 0, st, L.order, T, L.inv);
+        FIPT_LAUNCH(k_emitters, 1, 1024, 0, st, V, nV, F, Le, T, L.inv, L.emit_leaf, L.emit_cdf, L.cst);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { delete s; return fipt_check_cuda(e, "scene build"); }
@@ -540,5 +642,20 @@ extern "C" fipt_status fipt_scene_debug_export(fipt_scene* s, uint64_t* morton, 
         FIPT_LAUNCH(k_export_boxes, grid_for(ni, 256), 256, 0, st, s->nodes, ni, node_box);
         FIPT_LAUNCHED("export boxes");
     }
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_set_materials(fipt_scene* s, const float* albedo, const float* rough,
+                                                const float* metal, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(s->T == 0 || (albedo && rough && metal), "material array is NULL");
+    FIPT_REQUIRE(fipt_aligned(albedo, 4) && fipt_aligned(rough, 4) && fipt_aligned(metal, 4),
+                 "materials must be 4-byte aligned");
+    s->has_materials = true;
+    if (s->T == 0) return FIPT_OK;
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    FIPT_LAUNCH(k_set_materials, grid_for(s->T, 256), 256, 0, static_cast<cudaStream_t>(stream),
+                albedo, rough, metal, s->order, s->T, s->mats);
+    FIPT_LAUNCHED("set materials");
     return FIPT_OK;
 }

@@ -11,81 +11,6 @@
 namespace {
 
 constexpr int TRACE_THREADS = 128;
-#ifndef FIPT_STACK_DEPTH
-#define FIPT_STACK_DEPTH 32      // traversal stack entries per thread (shared memory)
-#endif
-constexpr int STACK_DEPTH = FIPT_STACK_DEPTH;
-constexpr float FINF = __builtin_huge_valf();
-
-struct BestHit {
-    float t;
-    int leaf;
-    int orig;
-    bool front;
-};
-
-// Closest hit of one ray; `stack` is this thread's column of the shared
-// stack (element k at stack[k * TRACE_THREADS]).  Returns false and raises
-// the overflow bit if the stack would exceed STACK_DEPTH.
-__device__ __forceinline__ void closest_hit(const SceneView& sc, const TraceRay& r, int skip,
-                                            int* stack, BestHit& best, int32_t* status) {
-    best.t = FINF;
-    best.leaf = -1;
-    best.orig = 0x7fffffff;
-    best.front = false;
-    if (sc.T == 0) return;
-    int node = 0, sp = 0, steps = 0;
-    while (node != FIPT_DONE) {
-        while (node >= 0) {
-            if (node >= sc.n_inner || ++steps > sc.max_steps) {
-                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
-                return;
-            }
-            const BvhNode n = load_node(sc.nodes, node);
-            bool h0, h1;
-            float t0, t1;
-            node_test(r, n, best.t, h0, h1, t0, t1);
-            if (h0 && h1) {
-                const bool first0 = t0 <= t1;
-                if (sp < STACK_DEPTH) {
-                    stack[sp * TRACE_THREADS] = first0 ? n.d.y : n.d.x;
-                    ++sp;
-                } else {
-                    atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
-                }
-                node = first0 ? n.d.x : n.d.y;
-            } else if (h0) {
-                node = n.d.x;
-            } else if (h1) {
-                node = n.d.y;
-            } else {
-                node = sp > 0 ? stack[--sp * TRACE_THREADS] : FIPT_DONE;
-            }
-        }
-        while (node < 0 && node != FIPT_DONE) {
-            const int leaf = ~node;
-            if (leaf >= sc.T || ++steps > sc.max_steps) {
-                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
-                return;
-            }
-            const float4 p0 = __ldg(sc.tris + 3 * leaf);
-            const int orig = __float_as_int(p0.w);
-            if (orig != skip) {
-                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
-                float t;
-                bool fr;
-                if (tri_intersect(r, p0, p1, p2, t, fr) &&
-                    (t < best.t || (t == best.t && orig < best.orig))) {
-                    best.t = t;
-                    best.leaf = leaf;
-                    best.orig = orig;
-                    best.front = fr;
-                }
-            }
-            node = sp > 0 ? stack[--sp * TRACE_THREADS] : FIPT_DONE;
-        }
-    }
-}
 
 __global__ void __launch_bounds__(TRACE_THREADS)
 k_trace(SceneView sc, const float* __restrict__ orig, const float* __restrict__ dir, int64_t n,
@@ -97,7 +22,7 @@ k_trace(SceneView sc, const float* __restrict__ orig, const float* __restrict__ 
     const TraceRay r = make_ray(orig[3 * i], orig[3 * i + 1], orig[3 * i + 2], dir[3 * i],
                                 dir[3 * i + 1], dir[3 * i + 2]);
     BestHit b;
-    closest_hit(sc, r, skip ? skip[i] : -1, stk + threadIdx.x, b, status);
+    closest_hit<TRACE_THREADS>(sc, r, skip ? skip[i] : -1, stk + threadIdx.x, b, status);
     hit_tri[i] = b.leaf >= 0 ? b.orig : -1;
     hit_t[i] = b.t;
     hit_front[i] = b.leaf >= 0 && b.front ? 1 : 0;
@@ -130,7 +55,7 @@ k_camera(SceneView sc, const float* __restrict__ cams, int W, int H, int64_t P,
     dx *= dl; dy *= dl; dz *= dl;
     const TraceRay r = make_ray(c[0], c[1], c[2], dx, dy, dz);
     BestHit b;
-    closest_hit(sc, r, -1, stk + threadIdx.x, b, status);
+    closest_hit<TRACE_THREADS>(sc, r, -1, stk + threadIdx.x, b, status);
     fipt_query qr;
     if (b.leaf < 0) {
         for (int a = 0; a < 3; ++a) { qr.x[a] = 0.0f; qr.n[a] = 0.0f; qr.wo[a] = 0.0f; }

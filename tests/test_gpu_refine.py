@@ -1,0 +1,119 @@
+"""GPU stage-3 refinement (Sec. 4.3, Eq. 10, MIS) vs the FP64 oracle on the
+same Philox streams.
+
+Multi-bounce paths branch on float decisions (which triangle a ray hits,
+which lobe a vertex draws, which emitter triangle an area sample picks);
+the oracle flags every sample whose path takes such a decision within
+rounding of its threshold.  Every unflagged sample must agree to 1e-4
+(relative to the larger of its own magnitude and the column's mean), and
+so must the per-point estimates of points with no flagged sample."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from workloads import cornell_box, procedural_room, surface_queries
+
+pytestmark = pytest.mark.gpu
+SIGMA = [0.02, 0.25, 1.0]
+ETA = 1e-5
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fipt():
+    import paper_2304_05669_gb300 as F
+    return F
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_both(F, m, q, albedo, rough, metal, spp, mis=True, sigma_c=0.6, max_depth=8, seed=3):
+    sc = F.Scene.from_mesh(m)
+    sc.set_materials(cu(albedo), cu(rough), cu(metal))
+    qt = F.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+    Ld, Ls0, Ls1, ps = F.bake_refine(sc, qt, SIGMA, spp, spp, sigma_c=sigma_c, max_depth=max_depth,
+                                     mis=mis, seed=seed, request_id=1, per_sample=True)
+    F.context().sync_status()
+    ora = O.OracleScene.from_mesh(m).refine(q, SIGMA, spp, spp, albedo, rough, metal,
+                                            sigma_c=sigma_c, max_depth=max_depth, mis=mis,
+                                            seed=seed, request_id=1, eta=ETA, per_sample=True)
+    g = {"Ld": Ld.cpu().numpy(), "Ls0": Ls0.cpu().numpy(), "Ls1": Ls1.cpu().numpy(),
+         "ps": ps.cpu().numpy().astype(np.float64)}
+    return g, ora
+
+
+def check(g, ora, min_clean_samples, min_clean_points):
+    ps_o, amb = ora["per_sample"], ora["amb"]
+    ps_g = g["ps"]
+    col = np.mean(np.abs(ps_o), axis=(0, 2), keepdims=True)        # per lobe / value
+    scale = np.maximum(np.abs(ps_o), col)
+    err = np.abs(ps_g - ps_o) / np.where(scale > 0, scale, 1.0)
+    clean = ~amb[..., None].repeat(6, axis=-1)
+    assert err[clean].max() <= REL, (err[clean].max(), np.argwhere(clean & (err > REL))[:3])
+    frac_s = clean[..., 0].mean()
+    assert frac_s >= min_clean_samples, frac_s
+    pts = ~amb.reshape(len(amb), -1).any(1)
+    flat_g = np.concatenate([g["Ld"], g["Ls0"].reshape(len(pts), -1), g["Ls1"].reshape(len(pts), -1)], 1)
+    flat_o = ora["flat"]
+    sc = np.maximum(np.abs(flat_o), np.mean(np.abs(flat_o), axis=0, keepdims=True))
+    e = np.abs(flat_g - flat_o) / np.where(sc > 0, sc, 1.0)
+    assert e[pts].max() <= REL, e[pts].max()
+    assert pts.mean() >= min_clean_points, pts.mean()
+    return frac_s, pts.mean()
+
+
+def test_refine_mirror_floor_cornell(fipt):
+    m = cornell_box()
+    T = m.T
+    a = np.full((T, 3), 0.8, np.float32)
+    r = np.ones(T, np.float32)
+    mt = np.zeros(T, np.float32)
+    r[m.floor] = 0.05
+    mt[m.floor] = 1.0
+    q = surface_queries(m, 512, seed=4)
+    g, ora = run_both(fipt, m, q, a, r, mt, 16)
+    print(check(g, ora, 0.99, 0.8))
+
+
+def test_refine_without_mis_equals_stage_one_on_rough_scene(fipt):
+    m = cornell_box()
+    T = m.T
+    q = surface_queries(m, 300, seed=5)
+    a, r, mt = np.full((T, 3), 0.5, np.float32), np.ones(T, np.float32), np.zeros(T, np.float32)
+    sc = fipt.Scene.from_mesh(m)
+    sc.set_materials(cu(a), cu(r), cu(mt))
+    qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+    ref = fipt.bake(sc, qt, SIGMA, 32, 16, seed=2)
+    got = fipt.bake_refine(sc, qt, SIGMA, 32, 16, mis=False, seed=2)
+    for x, y in zip(got, ref):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        assert np.allclose(x, y, rtol=1e-5, atol=1e-6 * np.abs(y).mean())
+
+
+def test_refine_room_random_materials(fipt):
+    m = procedural_room(1)
+    T = m.T
+    rng = np.random.default_rng(8)
+    a = rng.uniform(0, 1, (T, 3)).astype(np.float32)
+    r = rng.uniform(0.02, 1.0, T).astype(np.float32)
+    mt = rng.uniform(0, 1, T).astype(np.float32)
+    q = surface_queries(m, 192, seed=6)
+    g, ora = run_both(fipt, m, q, a, r, mt, 8)
+    print(check(g, ora, 0.9, 0.2))
+
+
+def test_refine_ragged_and_empty(fipt):
+    m = cornell_box()
+    T = m.T
+    a, r, mt = np.full((T, 3), 0.5, np.float32), np.full(T, 0.3, np.float32), np.zeros(T, np.float32)
+    for N in (1, 33):
+        q = surface_queries(m, N, seed=N)
+        g, ora = run_both(fipt, m, q, a, r, mt, 4, max_depth=3)
+        check(g, ora, 0.9, 0.0)
+    sc = fipt.Scene.from_mesh(m)
+    sc.set_materials(cu(a), cu(r), cu(mt))
+    out = fipt.bake_refine(sc, torch.zeros((0, 10), device="cuda"), SIGMA, 4)
+    assert out[0].shape == (0, 3)
