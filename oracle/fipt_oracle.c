@@ -410,10 +410,12 @@ int oracle_closest(const oscene* S, const double* orig, const double* dir, int64
 /* Sampling (Sec. 6: BRDF importance sampling in stage 1)               */
 /* ------------------------------------------------------------------ */
 /* Orthonormal basis (t, b, n) around a unit normal: Duff et al.,
- * "Building an orthonormal basis, revisited", JCGT 2017. */
+ * "Building an orthonormal basis, revisited", JCGT 2017.  The branch is
+ * taken on n.z >= 0 so that +0 and -0 (axis-aligned faces) give the same
+ * frame whatever the sign of the zero. */
 static void onb(const double n[3], double t[3], double b[3])
 {
-    double s = copysign(1.0, n[2]);
+    double s = n[2] >= 0.0 ? 1.0 : -1.0;
     double a = -1.0 / (s + n[2]);
     double c = n[0] * n[1] * a;
     t[0] = 1.0 + s * n[0] * n[0] * a; t[1] = s * c; t[2] = -s * n[0];
@@ -913,8 +915,35 @@ static double vertex_pd(const refine_job* R, int t, double mu_o)
 
 /* Full BRDF of Eq. 1 (including the cosine) at a vertex, RGB, and the pdf
  * of the vertex's mixture sampler; P_d as in the header. */
+/* Relative change of the GGX distribution per radian of half-vector tilt,
+ * |d ln D / d theta| = 4 tan / (tan^2 + alpha^2) (up to 1 - alpha^2). */
+static double ggx_log_slope(double ch, double sh, double a2)
+{
+    if (ch <= 0) return INFINITY;
+    double t = sh / ch;
+    return 4.0 * t / (t * t + a2);
+}
+
+/* A half vector recomputed from two directions carries float32 rounding of
+ * about 2e-6 rad on the kernel's side; where D changes by more than 1e-4
+ * under that tilt the sample is flagged as ill-conditioned. */
+#define OR_SLOPE_LIMIT 50.0
+
+static void vertex_brdf_h(const refine_job* R, int t, const double n[3], const double wo[3],
+                          const double wi[3], const double* hs, double f[3], double* pdf,
+                          double* Pd_out, int* amb);
+
 static void vertex_brdf(const refine_job* R, int t, const double n[3], const double wo[3],
                         const double wi[3], double f[3], double* pdf, double* Pd_out, int* amb)
+{
+    vertex_brdf_h(R, t, n, wo, wi, NULL, f, pdf, Pd_out, amb);
+}
+
+/* hs != NULL: wi was reflected about the sampled half vector hs, whose D is
+ * then evaluated at hs itself (no recomputation from wi). */
+static void vertex_brdf_h(const refine_job* R, int t, const double n[3], const double wo[3],
+                          const double wi[3], const double* hs, double f[3], double* pdf,
+                          double* Pd_out, int* amb)
 {
     const double a[3] = {R->ma[3*t], R->ma[3*t+1], R->ma[3*t+2]};
     const double sg = R->ms[t], m = R->mm[t];
@@ -934,11 +963,17 @@ static void vertex_brdf(const refine_job* R, int t, const double n[3], const dou
     *pdf = Pd * mu_i / OPI;
     if (!spec) return;
     double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+    if (hs) { h[0] = hs[0]; h[1] = hs[1]; h[2] = hs[2]; }
     normalize3(h);
     const double ch = dot3(n, h), co = dot3(wo, h);
     if (fabs(co) < 1e-5) *amb = 1;
     if (ch <= 0.0 || co <= 0.0) return;
     const double D = ggx_D(ch, a2);
+    if (!hs) {
+        double cr[3];
+        cross3(n, h, cr);
+        if (ggx_log_slope(ch, norm3(cr), a2) > OR_SLOPE_LIMIT) *amb = 1;
+    }
     const double G = smith_g1(mu_i, a2) * smith_g1(mu_o, a2);
     const double F1 = pow(1.0 - co, 5.0), F0 = 1.0 - F1;
     for (int c = 0; c < 3; ++c) f[c] += (ks[c] * F0 + F1) * D * G / (4.0 * mu_o);
@@ -985,6 +1020,7 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
         normalize3(n);
         for (int a = 0; a < 3; ++a) x[a] = o[a] + h.t * d[a];
         if (dot3(n, wo) < 0) for (int a = 0; a < 3; ++a) n[a] = -n[a];
+        if (n[2] != 0.0 && fabs(n[2]) < 1e-6) *amb = 1;     /* frame branch within rounding */
         double xo[3];
         for (int a = 0; a < 3; ++a) xo[a] = x[a] + S->eps * n[a];
         const uint32_t lane = lobe | ((uint32_t)depth << 9);
@@ -1020,20 +1056,21 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
         double tb[3], bb[3], wi[3];
         onb(n, tb, bb);
         if (fabs(u[2] - Pd) < 1e-5) *amb = 1;
-        if (u[2] < Pd) {
+        double hh[3];
+        const int glossy = !(u[2] < Pd);
+        if (!glossy) {
             double rad = sqrt(u[0]), phi = 2.0 * OPI * u[1];
             to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u[0]), wi);
         } else {
             const double al = (double)R->ms[h.id] * (double)R->ms[h.id], a2 = al * al;
             double cos2 = (1.0 - u[0]) / (1.0 + (a2 - 1.0) * u[0]);
             double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2)), phi = 2.0 * OPI * u[1];
-            double hh[3];
             to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, hh);
             double c = dot3(wo, hh);
             for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * hh[a] - wo[a];
         }
         double f[3], pdf;
-        vertex_brdf(R, h.id, n, wo, wi, f, &pdf, &Pd, amb);
+        vertex_brdf_h(R, h.id, n, wo, wi, glossy ? hh : NULL, f, &pdf, &Pd, amb);
         if (pdf <= 0.0) return;
         for (int c = 0; c < 3; ++c) beta[c] *= f[c] / pdf;
         for (int a = 0; a < 3; ++a) { o[a] = xo[a]; d[a] = wi[a]; }
@@ -1092,6 +1129,9 @@ static void refine_point(refine_job* R, int64_t p)
                         normalize3(h);
                         double ch = dot3(n, h), c = dot3(wo, h);
                         if (fabs(c) < 1e-5) amb = 1;
+                        double cr[3];
+                        cross3(n, h, cr);
+                        if (ggx_log_slope(ch, norm3(cr), a2) > OR_SLOPE_LIMIT) amb = 1;
                         if (ch > 0 && c > 0) {
                             double D = ggx_D(ch, a2), G = smith_g1(mu_i, a2) * g1o;
                             double F1 = pow(1.0 - c, 5.0);

@@ -289,9 +289,10 @@ __device__ __forceinline__ BvhNode load_node(const BvhNode* nodes, int i) {
     return n;
 }
 
-// Orthonormal basis (t, b) completing a unit normal n (Duff et al. 2017).
+// Orthonormal basis (t, b) completing a unit normal n (Duff et al. 2017);
+// the branch is taken on n.z >= 0 so +0 and -0 give the same frame.
 __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& t, float3& b) {
-    const float s = copysignf(1.0f, nz);
+    const float s = nz >= 0.0f ? 1.0f : -1.0f;
     const float a = -1.0f / (s + nz);
     const float c = nx * ny * a;
     t = make_float3(1.0f + s * nx * nx * a, s * c, -s * nx);

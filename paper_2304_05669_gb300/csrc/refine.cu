@@ -115,9 +115,12 @@ __device__ __forceinline__ Mat vertex_mat(const SceneView& sc, int leaf, float m
     return M;
 }
 
-// Full BRDF of Eq. 1 (cosine included) and the vertex's mixture pdf.
+// Full BRDF of Eq. 1 (cosine included) and the vertex's mixture pdf.  When
+// hs is given, wi was reflected about that sampled half vector and D is
+// evaluated there (sin2h = its squared sine), not at a recomputed one.
 __device__ __forceinline__ void vertex_brdf(const Mat& M, float3 n, float3 wo, float3 wi, float mu_o,
-                                            float f[3], float& pdf) {
+                                            float f[3], float& pdf, const float3* hs = nullptr,
+                                            float sin2h = 0.0f) {
     f[0] = f[1] = f[2] = 0.0f;
     pdf = 0.0f;
     const float mu_i = n.x * wi.x + n.y * wi.y + n.z * wi.z;
@@ -126,13 +129,18 @@ __device__ __forceinline__ void vertex_brdf(const Mat& M, float3 n, float3 wo, f
     for (int c = 0; c < 3; ++c) f[c] = M.kd[c] * mu_i / PI_F;
     pdf = M.Pd * mu_i / PI_F;
     if (!M.spec) return;
-    float hx = wi.x + wo.x, hy = wi.y + wo.y, hz = wi.z + wo.z;
-    const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
-    hx *= hl; hy *= hl; hz *= hl;
+    float hx, hy, hz;
+    if (hs) {
+        hx = hs->x; hy = hs->y; hz = hs->z;
+    } else {
+        hx = wi.x + wo.x; hy = wi.y + wo.y; hz = wi.z + wo.z;
+        const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
+        hx *= hl; hy *= hl; hz *= hl;
+    }
     const float ch = n.x * hx + n.y * hy + n.z * hz;
     const float co = wo.x * hx + wo.y * hy + wo.z * hz;
     if (ch <= 0.0f || co <= 0.0f) return;
-    const float D = ggx_d(sin2_between(n, hx, hy, hz), ch * ch, M.a2);
+    const float D = ggx_d(hs ? sin2h : sin2_between(n, hx, hy, hz), ch * ch, M.a2);
     const float G = smith_g1(mu_i, M.a2) * smith_g1(mu_o, M.a2);
     const float x1 = 1.0f - co, x2 = x1 * x1, F1 = x2 * x2 * x1, F0 = 1.0f - F1;
 #pragma unroll
@@ -221,22 +229,25 @@ __device__ void path_radiance(const SceneView& sc, const RefineArgs& R, int n_em
         const float4 u = u4(pid, s, lane, R.A);
         float3 tb, bb;
         onb(n.x, n.y, n.z, tb, bb);
-        float3 wi;
+        float3 wi, hh = make_float3(0.0f, 0.0f, 1.0f);
+        float sin2h = 0.0f;
         float sn, cs;
         sincospif(2.0f * u.y, &sn, &cs);
-        if (u.z < M.Pd) {
+        const bool glossy = !(u.z < M.Pd);
+        if (!glossy) {
             const float rr = sqrtf(u.x);
             wi = to_world(tb, bb, n, rr * cs, rr * sn, sqrtf(1.0f - u.x));
         } else {
             const float om = 1.0f - u.x;
             const float den = om + M.a2 * u.x;
-            const float ch = sqrtf(om / den), sh = sqrtf(M.a2 * u.x / den);
-            const float3 hh = to_world(tb, bb, n, sh * cs, sh * sn, ch);
+            sin2h = M.a2 * u.x / den;
+            const float ch = sqrtf(om / den), sh = sqrtf(sin2h);
+            hh = to_world(tb, bb, n, sh * cs, sh * sn, ch);
             const float c = wo.x * hh.x + wo.y * hh.y + wo.z * hh.z;
             wi = make_float3(2.0f * c * hh.x - wo.x, 2.0f * c * hh.y - wo.y, 2.0f * c * hh.z - wo.z);
         }
         float f[3], pdf;
-        vertex_brdf(M, n, wo, wi, mu_o, f, pdf);
+        vertex_brdf(M, n, wo, wi, mu_o, f, pdf, glossy ? &hh : nullptr, sin2h);
         if (pdf <= 0.0f) return;
         beta[0] *= f[0] / pdf;
         beta[1] *= f[1] / pdf;
