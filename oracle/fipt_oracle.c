@@ -411,11 +411,14 @@ int oracle_closest(const oscene* S, const double* orig, const double* dir, int64
 /* ------------------------------------------------------------------ */
 /* Orthonormal basis (t, b, n) around a unit normal: Duff et al.,
  * "Building an orthonormal basis, revisited", JCGT 2017.  The branch is
- * taken on n.z >= 0 so that +0 and -0 (axis-aligned faces) give the same
- * frame whatever the sign of the zero. */
+ * taken at n.z >= -1e-6 (the float constant), not at the sign of n.z, so
+ * that faces with n.z = 0 -- axis-aligned walls, symmetric sphere facets,
+ * whose computed z is +-0 or a rounding-sized value of either sign -- get
+ * the same frame on every side. */
+#define OR_ONB_BRANCH ((double)(-1e-6f))
 static void onb(const double n[3], double t[3], double b[3])
 {
-    double s = n[2] >= 0.0 ? 1.0 : -1.0;
+    double s = n[2] >= OR_ONB_BRANCH ? 1.0 : -1.0;
     double a = -1.0 / (s + n[2]);
     double c = n[0] * n[1] * a;
     t[0] = 1.0 + s * n[0] * n[0] * a; t[1] = s * c; t[2] = -s * n[0];
@@ -1020,7 +1023,7 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
         normalize3(n);
         for (int a = 0; a < 3; ++a) x[a] = o[a] + h.t * d[a];
         if (dot3(n, wo) < 0) for (int a = 0; a < 3; ++a) n[a] = -n[a];
-        if (n[2] != 0.0 && fabs(n[2]) < 1e-6) *amb = 1;     /* frame branch within rounding */
+        if (fabs(n[2] - OR_ONB_BRANCH) < 2e-7) *amb = 1;    /* frame branch within rounding */
         double xo[3];
         for (int a = 0; a < 3; ++a) xo[a] = x[a] + S->eps * n[a];
         const uint32_t lane = lobe | ((uint32_t)depth << 9);

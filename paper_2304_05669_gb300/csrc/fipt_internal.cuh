@@ -289,10 +289,12 @@ __device__ __forceinline__ BvhNode load_node(const BvhNode* nodes, int i) {
     return n;
 }
 
-// Orthonormal basis (t, b) completing a unit normal n (Duff et al. 2017);
-// the branch is taken on n.z >= 0 so +0 and -0 give the same frame.
+// Orthonormal basis (t, b) completing a unit normal n (Duff et al. 2017).
+// The branch is taken at n.z >= -1e-6 rather than on the sign of n.z, so a
+// face whose normal z is zero (+0, -0 or a rounding-sized value) gets the
+// same frame however its normal was rounded.
 __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& t, float3& b) {
-    const float s = nz >= 0.0f ? 1.0f : -1.0f;
+    const float s = nz >= -1e-6f ? 1.0f : -1.0f;
     const float a = -1.0f / (s + nz);
     const float c = nx * ny * a;
     t = make_float3(1.0f + s * nx * nx * a, s * c, -s * nx);
