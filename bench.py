@@ -71,6 +71,9 @@ def parse():
                     help="requests in the serving trace (0 = skip the serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, req/s")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="HBM admission budget")
+    ap.add_argument("--refine-points", type=int, default=1 << 18,
+                    help="points of the stage-3 refinement measurement (0 = skip)")
+    ap.add_argument("--refine-spp", type=int, default=32)
     return ap.parse_args()
 
 
@@ -341,6 +344,66 @@ def run_serving(args, F, dev):
                     "serial = same trace, one request at a time, no arrival gaps"}
 
 
+# ---------------------------------------------------------------- stage-3 refinement
+def refine_materials(mesh, seed=11):
+    """Per-triangle stage-2-like materials: albedo U[0,1]^3, roughness
+    U[0.02,1] (so ~60% of surfaces continue paths at sigma_c = 0.6),
+    metallic U[0,1]."""
+    rng = np.random.default_rng(seed)
+    T = mesh.T
+    return (rng.uniform(0, 1, (T, 3)).astype(np.float32),
+            rng.uniform(0.02, 1.0, T).astype(np.float32),
+            rng.uniform(0, 1, T).astype(np.float32))
+
+
+def run_refine(args, F, dev, mesh, sc, q_all, with_cpu):
+    """Stage-3 path-traced refinement (Sec. 4.3, Eq. 10, MIS) of the first
+    --refine-points queries at --refine-spp, timed with CUDA events."""
+    import torch
+    N, S = args.refine_points, args.refine_spp
+    a, r, m = refine_materials(mesh)
+    sc.set_materials(*[torch.from_numpy(x).to(dev) for x in (a, r, m)])
+    q = q_all[:N].contiguous()
+    for _ in range(2):
+        F.bake_refine(sc, q, SIGMA, S, S)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F.bake_refine(sc, q, SIGMA, S, S)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    F.context().sync_status()
+    samples = N * S * (1 + len(SIGMA))
+    out = {"points": N, "spp": S, "sigma_c": 0.6, "max_depth": 8, "mis": True,
+           "ms": round(1e3 * float(np.median(ts)), 3),
+           "msamples_per_s": round(samples / float(np.median(ts)) / 1e6, 2),
+           "points_per_s": round(N / float(np.median(ts)), 1)}
+    if with_cpu:
+        import oracle as O
+        cams = pinhole_views_for(mesh)
+        S_o = O.OracleScene.from_mesh(mesh)
+        npts = 1024
+        cq = S_o.camera_queries(cams, 320, 208, np.arange(int(npts * 1.5)))
+        ok = np.nonzero(cq["tri"] >= 0)[0][:npts]
+        qo = {k: cq[k][ok].astype(np.float32 if k != "tri" else np.int32)
+              for k in ("x", "n", "wo", "tri")}
+        t0 = time.perf_counter()
+        S_o.refine(qo, SIGMA, S, S, a, r, m, nthreads=O.default_threads())
+        dt = time.perf_counter() - t0
+        out["cpu_oracle_msamples_per_s"] = round(len(ok) * S * (1 + len(SIGMA)) / dt / 1e6, 4)
+        out["cpu_oracle_sample"] = "%d oracle first hits, %d spp, %d threads, %.1f s" % (
+            len(ok), S, O.default_threads(), dt)
+    return out
+
+
+def pinhole_views_for(mesh):
+    from workloads import pinhole_views
+    return pinhole_views(mesh, 24, seed=2)
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_ours(args, wl, world, rank, local):
     import torch
@@ -478,6 +541,10 @@ def run_ours(args, wl, world, rank, local):
                "sample": "%d oracle first hits (first pixels of view 0), %d+6x%d spp, FP64, %.1f s" %
                          (n, spp_d, spp_s, dt)}
 
+    refine = None
+    if rank == 0 and world == 1 and args.refine_points > 0:
+        refine = run_refine(args, F, dev, mesh, sc0, q0, not args.no_cpu_baseline)
+
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = run_serving(args, F, dev)
@@ -510,6 +577,7 @@ def run_ours(args, wl, world, rank, local):
                      "max_stack": max_depth},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "refine": refine,
         "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
