@@ -207,6 +207,15 @@ fipt_status fipt_bake(fipt_scene* scene, const fipt_query* q, int64_t N,
                       const fipt_bake_params* params, float* Ld, float* Ls0, float* Ls1,
                       fipt_stream stream);
 
+/* Environment radiance for rays that leave the scene (light through a
+ * window, Sec. 8): env [H, W, 3] f32 device, caller-owned, kept alive while
+ * set; NULL clears it (misses then bring 0).  Direction d maps to longitude
+ * u = atan2(d.x, -d.z) / 2pi + 1/2 and colatitude v = acos(d.y) / pi;
+ * texel (i, j) is centred at ((i + 1/2) / W, (j + 1/2) / H); lookups are
+ * bilinear, wrapping in u and clamped in v.  Used by fipt_bake,
+ * fipt_bake_refine and the server's batched bakes. */
+fipt_status fipt_scene_set_environment(fipt_scene* scene, const float* env, int32_t W, int32_t H);
+
 /* Per-triangle materials for the refinement (stage-2 estimates in the
  * paper): albedo [T,3], roughness [T], metallic [T] f32, original order. */
 fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, const float* rough,

@@ -81,6 +81,7 @@ def _L():
         L.oracle_camera_queries.restype = I32
         L.oracle_refine.argtypes = [P, P, P, P, P, P, P, P, I64, U64, U32, U32, I32, I32, I32, P,
                                     D, I32, I32, D, I32, P, P, P]
+        L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
         L.oracle_morton.argtypes = [P, I64, P, I64, P]
         L.oracle_radix_tree.argtypes = [P, P, I64, P, P, P, P]
         L.oracle_radix_tree.restype = I32
@@ -142,6 +143,17 @@ class OracleScene:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.oracle_scene_destroy(self._h)
             self._h = None
+
+    def set_environment(self, env):
+        """Equirectangular environment radiance [H, W, 3] for rays that miss
+        (None clears it); see env_lookup in fipt_oracle.c for the mapping."""
+        if env is None:
+            _L().oracle_scene_set_environment(self._h, None, 0, 0)
+            self._env = None
+            return
+        self._env = _c(env, np.float32)
+        H, W = self._env.shape[:2]
+        _L().oracle_scene_set_environment(self._h, _p(self._env), int(W), int(H))
 
     def closest(self, orig, dirs, skip=None, eta=0.0, brute=False):
         """Closest hit of rays (o + t d, t > 0), ties by (t, id); FP64 MT."""

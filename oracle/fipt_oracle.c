@@ -110,6 +110,8 @@ typedef struct {
     double L;              /* largest extent of the scene box */
     double diag;           /* length of its diagonal */
     double eps;            /* ray-origin offset, 1e-4 * L */
+    double* env;           /* environment radiance [H][W][3] (NULL: misses bring 0) */
+    int env_w, env_h;
 } oscene;
 
 static int build_node(oscene* S, int start, int count, int* cap)
@@ -218,7 +220,51 @@ oscene* oracle_scene_create(const float* V, int64_t nV, const int32_t* F, int64_
 void oracle_scene_destroy(oscene* S)
 {
     if (!S) return;
-    free(S->tri); free(S->Le); free(S->cache); free(S->node); free(S->idx); free(S);
+    free(S->tri); free(S->Le); free(S->cache); free(S->node); free(S->idx); free(S->env); free(S);
+}
+
+/* Environment radiance seen by rays that leave the scene (a window's light,
+ * Sec. 8): an equirectangular RGB map [H][W][3]; NULL clears it. */
+void oracle_scene_set_environment(oscene* S, const float* env, int W, int H)
+{
+    free(S->env);
+    S->env = NULL;
+    S->env_w = S->env_h = 0;
+    if (!env || W <= 0 || H <= 0) return;
+    S->env = (double*)malloc(sizeof(double) * 3 * (size_t)W * (size_t)H);
+    for (size_t i = 0; i < 3 * (size_t)W * (size_t)H; ++i) S->env[i] = env[i];
+    S->env_w = W;
+    S->env_h = H;
+}
+
+/* Radiance of the environment in unit direction d: longitude
+ * u = atan2(d.x, -d.z) / 2pi + 1/2, colatitude v = acos(d.y) / pi, texel
+ * (i, j) centred at ((i + 1/2) / W, (j + 1/2) / H); bilinear, wrapping in u
+ * and clamping in v. */
+static void env_lookup(const oscene* S, const double d[3], double L[3])
+{
+    L[0] = L[1] = L[2] = 0.0;
+    if (!S->env) return;
+    const int W = S->env_w, H = S->env_h;
+    double dl = norm3(d);
+    double y = d[1] / dl;
+    if (y > 1.0) y = 1.0;
+    if (y < -1.0) y = -1.0;
+    double u = atan2(d[0] / dl, -d[2] / dl) / (2.0 * OPI) + 0.5;
+    double v = acos(y) / OPI;
+    double fx = u * W - 0.5, fy = v * H - 0.5;
+    double i0f = floor(fx), j0f = floor(fy);
+    double tx = fx - i0f, ty = fy - j0f;
+    int i0 = (int)i0f, j0 = (int)j0f;
+    for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+            int i = ((i0 + di) % W + W) % W;
+            int j = j0 + dj;
+            if (j < 0) j = 0;
+            if (j > H - 1) j = H - 1;
+            double w = (di ? tx : 1.0 - tx) * (dj ? ty : 1.0 - ty);
+            for (int c = 0; c < 3; ++c) L[c] += w * S->env[3 * ((size_t)j * W + i) + c];
+        }
 }
 
 void oracle_scene_info(const oscene* S, double* lo, double* hi, double* eps, double* L)
@@ -458,20 +504,21 @@ typedef struct {
 
 /* Incident radiance for one hit: emission counted on the front face only,
  * plus the per-triangle cache; a miss brings nothing. */
-static void radiance(const oscene* S, int32_t id, int front, double L[3])
+static void radiance(const oscene* S, int32_t id, int front, const double d[3], double L[3])
 {
-    if (id < 0) { L[0] = L[1] = L[2] = 0.0; return; }
+    if (id < 0) { env_lookup(S, d, L); return; }
     for (int a = 0; a < 3; ++a) L[a] = (front ? S->Le[3*id+a] : 0.0) + S->cache[3*id+a];
 }
 
 /* Range of the incident radiance over every hit a perturbed ray may report
  * (candidates, both facings when grazing, and a miss when possible). */
-static int radiance_range(const oscene* S, const ocands* c, double Lmin[3], double Lmax[3])
+static int radiance_range(const oscene* S, const ocands* c, const double d[3], double Lmin[3],
+                          double Lmax[3])
 {
     for (int a = 0; a < 3; ++a) { Lmin[a] = INFINITY; Lmax[a] = -INFINITY; }
     int alts = 0;
     double L[3];
-#define OR_ACC(id_, fr_) do { radiance(S, (id_), (fr_), L); ++alts; \
+#define OR_ACC(id_, fr_) do { radiance(S, (id_), (fr_), d, L); ++alts; \
         for (int a = 0; a < 3; ++a) { if (L[a] < Lmin[a]) Lmin[a] = L[a]; if (L[a] > Lmax[a]) Lmax[a] = L[a]; } } while (0)
     OR_ACC(c->nominal.id, c->nominal.front);
     if (c->nominal.id >= 0 && c->nominal.front_amb) OR_ACC(c->nominal.id, !c->nominal.front);
@@ -527,11 +574,11 @@ static void bake_point(bake_job* J, int64_t p)
         ocands c;
         closest(S, o, wi, skip, J->eta, &c);
         double L[3];
-        radiance(S, c.nominal.id, c.nominal.front, L);
+        radiance(S, c.nominal.id, c.nominal.front, wi, L);
         for (int a = 0; a < 3; ++a) nom[a] += L[a];
         if (lo) {
             double Lmin[3], Lmax[3];
-            amb_rays += radiance_range(S, &c, Lmin, Lmax);
+            amb_rays += radiance_range(S, &c, wi, Lmin, Lmax);
             for (int a = 0; a < 3; ++a) { lo[a] += Lmin[a]; hi[a] += Lmax[a]; }
         }
     }
@@ -572,11 +619,11 @@ static void bake_point(bake_job* J, int64_t p)
             ocands cd;
             closest(S, o, wi, skip, J->eta, &cd);
             double L[3];
-            radiance(S, cd.nominal.id, cd.nominal.front, L);
+            radiance(S, cd.nominal.id, cd.nominal.front, wi, L);
             for (int a = 0; a < 3; ++a) { s0[a] += L[a] * F0 * w; s1[a] += L[a] * F1 * w; }
             if (lo) {
                 double Lmin[3], Lmax[3];
-                amb_rays += radiance_range(S, &cd, Lmin, Lmax);
+                amb_rays += radiance_range(S, &cd, wi, Lmin, Lmax);
                 for (int a = 0; a < 3; ++a) {
                     l0[a] += Lmin[a] * F0 * w; h0[a] += Lmax[a] * F0 * w;
                     l1[a] += Lmin[a] * F1 * w; h1[a] += Lmax[a] * F1 * w;
@@ -999,7 +1046,12 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
     for (int depth = 1;; ++depth) {
         ohit h;
         trace_flag(R, o, d, skip, &h, amb);
-        if (h.id < 0) return;
+        if (h.id < 0) {
+            double Le[3];
+            env_lookup(S, d, Le);
+            for (int c = 0; c < 3; ++c) L[c] += beta[c] * Le[c];
+            return;
+        }
         if (is_emitter(S, h.id)) {
             if (!h.front) return;
             double w = 1.0;

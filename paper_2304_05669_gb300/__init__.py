@@ -143,6 +143,17 @@ class Scene:
         check(lib().fipt_scene_set_cache(self.handle, _ptr(cache), _stream(stream)))
         self._keep = self._keep + (cache,)
 
+    def set_environment(self, env):
+        """Environment radiance [H, W, 3] (CUDA float32) seen by rays that miss;
+        None clears it."""
+        if env is None:
+            check(lib().fipt_scene_set_environment(self.handle, None, 0, 0))
+            self._env = None
+            return
+        env = _dev(env, torch.float32, "env")
+        check(lib().fipt_scene_set_environment(self.handle, _ptr(env), env.shape[1], env.shape[0]))
+        self._env = env
+
     def set_materials(self, albedo, rough, metal, stream=None):
         """Per-triangle albedo [T,3], roughness [T], metallic [T] (refinement)."""
         albedo = _dev(albedo, torch.float32, "albedo")

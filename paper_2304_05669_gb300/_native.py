@@ -68,6 +68,7 @@ SIGNATURES = {
     "fipt_tri_error": [P, I64, P, P, I64, I64, P, P, P, SZ, P],
     "fipt_debug_philox": [P, P, I64, P, P],
     "fipt_scene_set_materials": [P, P, P, P, P],
+    "fipt_scene_set_environment": [P, P, I32, I32],
     "fipt_bake_refine": [P, P, I64, ctypes.POINTER(BakeParams), F32, I32, I32, P, P, P, P, P],
     "fipt_server_create": [P, SZ, I64, I64, P],
     "fipt_server_add_scene": [P, P, P],

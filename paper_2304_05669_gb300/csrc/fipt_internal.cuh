@@ -49,6 +49,8 @@ struct SceneView {
     const float4* mats;     // 2 per leaf: (albedo rgb, roughness), (metallic, 0, 0, 0)
     const int32_t* emit_leaf;   // emitter triangles in original index order -> leaf
     const double* emit_cdf;     // cumulative emitter areas (same order)
+    const float* env;           // environment radiance [H][W][3] for misses, or NULL
+    int env_w, env_h;
 };
 
 struct fipt_scene {
@@ -73,11 +75,14 @@ struct fipt_scene {
     int32_t* emit_leaf;    // [T] (first n_emit used)
     double* emit_cdf;      // [T]
     bool has_materials = false;
+    const float* env = nullptr;   // caller-owned environment map
+    int env_w = 0, env_h = 0;
     size_t ws_bytes;
     SceneView view() const {
         const int64_t steps = 2 * T + 2;
         return SceneView{nodes, tris, shade, cst, T, (int)(T > 1 ? T - 1 : 1),
-                         (int)(steps < 2147483647 ? steps : 2147483647), mats, emit_leaf, emit_cdf};
+                         (int)(steps < 2147483647 ? steps : 2147483647), mats, emit_leaf, emit_cdf,
+                         env, env_w, env_h};
     }
 };
 
@@ -102,7 +107,7 @@ struct BakeChunk {
 
 // Bake of a list of chunks (several requests / scenes) in one launch.
 fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st);
+                              int32_t* status, cudaStream_t st, bool env);
 
 fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
 void fipt_count_launch();
@@ -299,6 +304,36 @@ __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& t, flo
     const float c = nx * ny * a;
     t = make_float3(1.0f + s * nx * nx * a, s * c, -s * nx);
     b = make_float3(c, s + ny * ny * a, -ny);
+}
+
+// Environment radiance for a ray that leaves the scene (unit direction d):
+// longitude u = atan2(d.x, -d.z) / 2pi + 1/2, colatitude v = acos(d.y) / pi,
+// texel (i, j) centred at ((i + 1/2) / W, (j + 1/2) / H), bilinear with u
+// wrapping and v clamped.
+__device__ __forceinline__ float3 env_lookup(const SceneView& sc, float dx, float dy, float dz) {
+    const int W = sc.env_w, H = sc.env_h;
+    const float il = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    const float y = fminf(fmaxf(dy * il, -1.0f), 1.0f);
+    const float u = atan2f(dx * il, -dz * il) * 0.15915494309189535f + 0.5f;
+    const float v = acosf(y) * 0.3183098861837907f;
+    const float fx = u * (float)W - 0.5f, fy = v * (float)H - 0.5f;
+    const float i0f = floorf(fx), j0f = floorf(fy);
+    const float tx = fx - i0f, ty = fy - j0f;
+    const int i0 = (int)i0f, j0 = (int)j0f;
+    float3 L = make_float3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+            const int i = ((i0 + di) % W + W) % W;
+            const int j = min(max(j0 + dj, 0), H - 1);
+            const float w = (di ? tx : 1.0f - tx) * (dj ? ty : 1.0f - ty);
+            const float* t = sc.env + 3 * ((size_t)j * W + i);
+            L.x += w * __ldg(t);
+            L.y += w * __ldg(t + 1);
+            L.z += w * __ldg(t + 2);
+        }
+    return L;
 }
 
 // ---------------------------------------------------------------- traversal

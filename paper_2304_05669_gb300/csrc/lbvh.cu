@@ -659,3 +659,19 @@ extern "C" fipt_status fipt_scene_set_materials(fipt_scene* s, const float* albe
     FIPT_LAUNCHED("set materials");
     return FIPT_OK;
 }
+
+extern "C" fipt_status fipt_scene_set_environment(fipt_scene* s, const float* env, int32_t W,
+                                                  int32_t H) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    if (!env) {
+        s->env = nullptr;
+        s->env_w = s->env_h = 0;
+        return FIPT_OK;
+    }
+    FIPT_REQUIRE(W > 0 && H > 0, "environment size must be positive");
+    FIPT_REQUIRE(fipt_aligned(env, 4), "environment map must be 4-byte aligned");
+    s->env = env;
+    s->env_w = W;
+    s->env_h = H;
+    return FIPT_OK;
+}

@@ -166,7 +166,15 @@ __device__ void path_radiance(const SceneView& sc, const RefineArgs& R, int n_em
         const TraceRay r = make_ray(o.x, o.y, o.z, d.x, d.y, d.z);
         BestHit h;
         closest_hit<STRIDE>(sc, r, skip, stack, h, status);
-        if (h.leaf < 0) return;
+        if (h.leaf < 0) {
+            if (sc.env) {
+                const float3 e = env_lookup(sc, d.x, d.y, d.z);
+                L[0] += beta[0] * e.x;
+                L[1] += beta[1] * e.y;
+                L[2] += beta[2] * e.z;
+            }
+            return;
+        }
         const float4 le = __ldg(sc.shade + 2 * h.leaf);
         if (is_emitter(le)) {
             if (!h.front) return;

@@ -190,7 +190,7 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 //  * speculation (Aila and Laine 2009): a lane that reaches a leaf parks
 //    it and keeps descending inner nodes until every lane has a leaf;
 //  * leaves are then tested together.
-template <bool STATS>
+template <bool STATS, bool ENV>
 __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
                                           const int64_t p, const int lobe, const bool valid,
                                           const BakeArgs& A, float* __restrict__ Ld,
@@ -236,6 +236,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
 
     float acc0x = 0, acc0y = 0, acc0z = 0, acc1x = 0, acc1y = 0, acc1z = 0;
     float wF0 = 1.0f, wF1 = 0.0f;
+    float rdx = 0.0f, rdy = 0.0f, rdz = 1.0f;     // current ray direction (environment lookups)
     int s = 0, node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
     bool active = false;
     TraceRay r;
@@ -253,12 +254,20 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
         if ((m_need | m_busy) == 0) break;
         if (m_need != 0 && (m_busy == 0 || __popc(m_need) >= FIPT_BAKE_REFILL) && need) {
             if (active) {
-                if (best.leaf >= 0) {
+                bool lit = best.leaf >= 0;
+                float lx = 0.0f, ly = 0.0f, lz = 0.0f;
+                if (lit) {
                     const float4 le = __ldg(sc.shade + 2 * best.leaf);
                     const float4 ca = __ldg(sc.shade + 2 * best.leaf + 1);
-                    const float lx = (best.front ? le.x : 0.0f) + ca.x;
-                    const float ly = (best.front ? le.y : 0.0f) + ca.y;
-                    const float lz = (best.front ? le.z : 0.0f) + ca.z;
+                    lx = (best.front ? le.x : 0.0f) + ca.x;
+                    ly = (best.front ? le.y : 0.0f) + ca.y;
+                    lz = (best.front ? le.z : 0.0f) + ca.z;
+                } else if (ENV) {
+                    const float3 e = env_lookup(sc, rdx, rdy, rdz);
+                    lx = e.x; ly = e.y; lz = e.z;
+                    lit = true;
+                }
+                if (lit) {
                     if (lobe == 0) {
                         acc0x += lx; acc0y += ly; acc0z += lz;
                     } else {
@@ -303,6 +312,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     wF1 = F1 * wt;
                 }
                 r = make_ray(ox, oy, oz, dx, dy, dz);
+                if (ENV) { rdx = dx; rdy = dy; rdz = dz; }
                 best.t = FINF;
                 best.leaf = -1;
                 best.orig = 0x7fffffff;
@@ -409,7 +419,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
 
 // A warp holds 32 consecutive points of one lobe; consecutive warps cycle
 // through the lobes of the same 32 points.
-template <bool STATS>
+template <bool STATS, bool ENV>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
        float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
@@ -422,7 +432,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int lobe = (int)(w % L);
     const int64_t p = (w / L) * 32 + lane;
     if ((w / L) * 32 >= N) return;          // whole warp past the end
-    bake_item<STATS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
+    bake_item<STATS, ENV>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
 }
 
 // One launch over chunks of several requests, possibly on several scenes
@@ -431,6 +441,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
 // mapping is the single-request one, and the Philox counter uses the
 // chunk's request-local point_base, so every value equals the one a
 // separate fipt_bake of that request would produce.
+template <bool ENV>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
              int32_t* status) {
@@ -450,8 +461,8 @@ k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_w
     const int L = 1 + A.K;
     const int lobe = (int)(wl % L);
     const int64_t p = (wl / L) * 32 + lane;
-    bake_item<false>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
-                     stk + threadIdx.x);
+    bake_item<false, ENV>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
+                          stk + threadIdx.x);
 }
 
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
@@ -562,12 +573,19 @@ extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
     const int64_t threads = warps * 32;
     const unsigned nb = blocks(threads, BAKE_THREADS);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (prm->stats)
-        FIPT_LAUNCH(k_bake<true>, nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1, s->ctx->status,
-                                                  prm->stats);
+    const bool env = s->env != nullptr;
+    if (prm->stats && env)
+        FIPT_LAUNCH((k_bake<true, true>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
+                    s->ctx->status, prm->stats);
+    else if (prm->stats)
+        FIPT_LAUNCH((k_bake<true, false>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
+                    s->ctx->status, prm->stats);
+    else if (env)
+        FIPT_LAUNCH((k_bake<false, true>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
+                    s->ctx->status, nullptr);
     else
-        FIPT_LAUNCH(k_bake<false>, nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1, s->ctx->status,
-                                                   nullptr);
+        FIPT_LAUNCH((k_bake<false, false>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
+                    s->ctx->status, nullptr);
     FIPT_LAUNCHED("bake");
     return FIPT_OK;
 }
@@ -584,11 +602,15 @@ extern "C" fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* ke
 
 // Internal launcher used by the serving runtime.
 fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st) {
+                              int32_t* status, cudaStream_t st, bool env) {
     if (n_chunks <= 0 || total_warps <= 0) return FIPT_OK;
     const int64_t threads = total_warps * 32;
-    FIPT_LAUNCH(k_bake_batch, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks, n_chunks,
-                total_warps, status);
+    if (env)
+        FIPT_LAUNCH(k_bake_batch<true>, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks,
+                    n_chunks, total_warps, status);
+    else
+        FIPT_LAUNCH(k_bake_batch<false>, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks,
+                    n_chunks, total_warps, status);
     FIPT_LAUNCHED("bake_batch");
     return FIPT_OK;
 }
