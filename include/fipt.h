@@ -216,6 +216,26 @@ fipt_status fipt_bake(fipt_scene* scene, const fipt_query* q, int64_t N,
  * fipt_bake_refine and the server's batched bakes. */
 fipt_status fipt_scene_set_environment(fipt_scene* scene, const float* env, int32_t W, int32_t H);
 
+/* Voxel radiance cache (Sec. 4.2): L' as an R^3 grid spanned over the
+ * scene box, average-pooled from input pixels at their first hits and
+ * queried at the voxel containing a hit point (the paper uses R = 256).
+ * fipt_voxel_cache_build pools P pixels: point p at x[p * x_stride + 0..2]
+ * (x_stride 3 for a plain [P,3] array, 10 to read fipt_query records) with
+ * radiance L [P,3] f32; pixels are assigned to cell
+ * floor((x - lo) * (R / (hi - lo))) per axis (clamped to [0, R-1]), each
+ * operation one IEEE double rounding; grid [R,R,R,4] f32 (index [z][y][x],
+ * 16-byte aligned, caller-owned) receives (mean rgb, pixel count), zero for
+ * empty voxels; each mean is summed in pixel order in FP64.  R in
+ * [1, 1024]; workspace from fipt_voxel_cache_workspace_size(P). */
+fipt_status fipt_voxel_cache_workspace_size(int64_t P, size_t* bytes);
+fipt_status fipt_voxel_cache_build(fipt_scene* scene, const float* x, int64_t x_stride,
+                                   const float* L, int64_t P, int32_t R, float* grid,
+                                   void* workspace, size_t ws_bytes, fipt_stream stream);
+/* Uses a built grid (kept alive by the caller) as the cache L' of the bake,
+ * the refinement and the server's batches instead of the per-triangle
+ * values; NULL returns to per-triangle values. */
+fipt_status fipt_scene_set_voxel_cache(fipt_scene* scene, const float* grid, int32_t R);
+
 /* Per-triangle materials for the refinement (stage-2 estimates in the
  * paper): albedo [T,3], roughness [T], metallic [T] f32, original order. */
 fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, const float* rough,

@@ -82,6 +82,8 @@ def _L():
         L.oracle_refine.argtypes = [P, P, P, P, P, P, P, P, I64, U64, U32, U32, I32, I32, I32, P,
                                     D, I32, I32, D, I32, P, P, P]
         L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
+        L.oracle_voxel_pool.argtypes = [P, P, P, I64, I32, P]
+        L.oracle_scene_set_voxel_cache.argtypes = [P, P, I32]
         L.oracle_morton.argtypes = [P, I64, P, I64, P]
         L.oracle_radix_tree.argtypes = [P, P, I64, P, P, P, P]
         L.oracle_radix_tree.restype = I32
@@ -154,6 +156,24 @@ class OracleScene:
         self._env = _c(env, np.float32)
         H, W = self._env.shape[:2]
         _L().oracle_scene_set_environment(self._h, _p(self._env), int(W), int(H))
+
+    def voxel_pool(self, x, L, R):
+        """Sec. 4.2: average pooling of pixel radiance L [P,3] at first-hit
+        points x [P,3] onto an R^3 grid over the scene box -> [R,R,R,4]
+        (mean rgb, count), index [z][y][x]."""
+        x = _c(x, np.float32)
+        L = _c(L, np.float32)
+        out = np.zeros((R, R, R, 4))
+        _L().oracle_voxel_pool(self._h, _p(x), _p(L), len(x), int(R), _p(out))
+        return out
+
+    def set_voxel_cache(self, grid):
+        """Use a pooled grid as the cache L' (None: per-triangle values)."""
+        if grid is None:
+            _L().oracle_scene_set_voxel_cache(self._h, None, 0)
+            return
+        g = _c(grid, np.float64)
+        _L().oracle_scene_set_voxel_cache(self._h, _p(g), int(g.shape[0]))
 
     def closest(self, orig, dirs, skip=None, eta=0.0, brute=False):
         """Closest hit of rays (o + t d, t > 0), ties by (t, id); FP64 MT."""

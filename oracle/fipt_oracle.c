@@ -112,6 +112,8 @@ typedef struct {
     double eps;            /* ray-origin offset, 1e-4 * L */
     double* env;           /* environment radiance [H][W][3] (NULL: misses bring 0) */
     int env_w, env_h;
+    double* vox;           /* voxel radiance cache [R^3][4]: mean rgb, pixel count (NULL: per-triangle) */
+    int vox_r;
 } oscene;
 
 static int build_node(oscene* S, int start, int count, int* cap)
@@ -220,7 +222,82 @@ oscene* oracle_scene_create(const float* V, int64_t nV, const int32_t* F, int64_
 void oracle_scene_destroy(oscene* S)
 {
     if (!S) return;
-    free(S->tri); free(S->Le); free(S->cache); free(S->node); free(S->idx); free(S->env); free(S);
+    free(S->tri); free(S->Le); free(S->cache); free(S->node); free(S->idx); free(S->env); free(S->vox);
+    free(S);
+}
+
+/* Voxel of a point: grid of R cells per axis over the scene box [lo, hi]
+ * (from the float vertices), cell = floor((p - lo) * (R / (hi - lo))) clamped
+ * to [0, R-1], each operation one IEEE double rounding (as the Morton
+ * quantisation).  frac (nullable) receives the position inside the cell. */
+static int64_t voxel_of(const oscene* S, int R, const double p[3], double frac[3])
+{
+    int64_t idx[3];
+    for (int a = 0; a < 3; ++a) {
+        double ext = S->shi[a] - S->slo[a];
+        double f = ext > 0 ? (p[a] - S->slo[a]) * ((double)R / ext) : 0.0;
+        double fl = floor(f);
+        if (frac) frac[a] = f - fl;
+        if (fl < 0) { fl = 0; if (frac) frac[a] = 0.5; }
+        if (fl > R - 1) { fl = R - 1; if (frac) frac[a] = 0.5; }
+        idx[a] = (int64_t)fl;
+    }
+    return (idx[2] * R + idx[1]) * R + idx[0];
+}
+
+/* Average pooling of pixel radiance onto the voxel grid (Sec. 4.2): every
+ * pixel p with first-hit point x[p] adds its radiance L[p] to its voxel;
+ * out[v] = (mean rgb, count), zero where no pixel fell. */
+void oracle_voxel_pool(const oscene* S, const float* x, const float* L, int64_t P, int R, double* out)
+{
+    const int64_t nv = (int64_t)R * R * R;
+    for (int64_t v = 0; v < 4 * nv; ++v) out[v] = 0.0;
+    for (int64_t p = 0; p < P; ++p) {
+        double q[3] = {x[3*p], x[3*p+1], x[3*p+2]};
+        int64_t v = voxel_of(S, R, q, NULL);
+        for (int c = 0; c < 3; ++c) out[4*v+c] += L[3*p+c];
+        out[4*v+3] += 1.0;
+    }
+    for (int64_t v = 0; v < nv; ++v)
+        if (out[4*v+3] > 0) for (int c = 0; c < 3; ++c) out[4*v+c] /= out[4*v+3];
+}
+
+/* Uses a pooled grid (as oracle_voxel_pool writes it) as the cache L'
+ * looked up at the voxel containing a hit; NULL returns to per-triangle. */
+void oracle_scene_set_voxel_cache(oscene* S, const double* grid, int R)
+{
+    free(S->vox);
+    S->vox = NULL;
+    S->vox_r = 0;
+    if (!grid || R <= 0) return;
+    size_t n = 4 * (size_t)R * R * R;
+    S->vox = (double*)malloc(sizeof(double) * n);
+    memcpy(S->vox, grid, sizeof(double) * n);
+    S->vox_r = R;
+}
+
+/* Cache radiance at a hit point: the voxel grid when set, else the hit
+ * triangle's value. */
+static void cache_at(const oscene* S, int32_t id, const double p[3], double C[3])
+{
+    if (S->vox) {
+        int64_t v = voxel_of(S, S->vox_r, p, NULL);
+        for (int c = 0; c < 3; ++c) C[c] = S->vox[4*v+c];
+    } else {
+        for (int c = 0; c < 3; ++c) C[c] = S->cache[3*id+c];
+    }
+}
+
+/* Whether a float32 hit point may fall in a neighbouring voxel: some
+ * coordinate lies within 1e-3 of a cell face (a float32 hit point is off
+ * by ~1e-6 of the scene size, ~1e-4 of a 256-cell voxel). */
+static int voxel_ambiguous(const oscene* S, const double p[3])
+{
+    if (!S->vox) return 0;
+    double fr[3];
+    voxel_of(S, S->vox_r, p, fr);
+    for (int a = 0; a < 3; ++a) if (fr[a] < 1e-3 || fr[a] > 1.0 - 1e-3) return 1;
+    return 0;
 }
 
 /* Environment radiance seen by rays that leave the scene (a window's light,
@@ -504,29 +581,71 @@ typedef struct {
 
 /* Incident radiance for one hit: emission counted on the front face only,
  * plus the per-triangle cache; a miss brings nothing. */
-static void radiance(const oscene* S, int32_t id, int front, const double d[3], double L[3])
+/* Incident radiance along d from a hit on triangle id at distance t from
+ * o: front-face emission + the cache L' there (Eq. 9); a miss brings the
+ * environment (or 0). */
+static void radiance(const oscene* S, int32_t id, int front, const double o[3], const double d[3],
+                     double t, double L[3])
 {
     if (id < 0) { env_lookup(S, d, L); return; }
-    for (int a = 0; a < 3; ++a) L[a] = (front ? S->Le[3*id+a] : 0.0) + S->cache[3*id+a];
+    double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]}, C[3];
+    cache_at(S, id, p, C);
+    for (int a = 0; a < 3; ++a) L[a] = (front ? S->Le[3*id+a] : 0.0) + C[a];
+}
+
+/* Cache values of every voxel a float32 hit point near p may fall in. */
+static void voxel_range(const oscene* S, const double p[3], double lo[3], double hi[3])
+{
+    const int R = S->vox_r;
+    double fr[3];
+    int64_t v = voxel_of(S, R, p, fr);
+    int64_t base[3] = {v % R, (v / R) % R, v / ((int64_t)R * R)};
+    for (int c = 0; c < 3; ++c) { lo[c] = INFINITY; hi[c] = -INFINITY; }
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int dd[3] = {dx, dy, dz};
+                int ok = 1;
+                int64_t ix[3];
+                for (int a = 0; a < 3; ++a) {
+                    if (dd[a] == -1 && !(fr[a] < 1e-3)) ok = 0;
+                    if (dd[a] == 1 && !(fr[a] > 1.0 - 1e-3)) ok = 0;
+                    ix[a] = base[a] + dd[a];
+                    if (ix[a] < 0 || ix[a] > R - 1) ok = 0;
+                }
+                if (!ok) continue;
+                int64_t w = (ix[2] * R + ix[1]) * R + ix[0];
+                for (int c = 0; c < 3; ++c) {
+                    if (S->vox[4*w+c] < lo[c]) lo[c] = S->vox[4*w+c];
+                    if (S->vox[4*w+c] > hi[c]) hi[c] = S->vox[4*w+c];
+                }
+            }
 }
 
 /* Range of the incident radiance over every hit a perturbed ray may report
  * (candidates, both facings when grazing, and a miss when possible). */
-static int radiance_range(const oscene* S, const ocands* c, const double d[3], double Lmin[3],
-                          double Lmax[3])
+static int radiance_range(const oscene* S, const ocands* c, const double o[3], const double d[3],
+                          double Lmin[3], double Lmax[3])
 {
     for (int a = 0; a < 3; ++a) { Lmin[a] = INFINITY; Lmax[a] = -INFINITY; }
     int alts = 0;
     double L[3];
-#define OR_ACC(id_, fr_) do { radiance(S, (id_), (fr_), d, L); ++alts; \
-        for (int a = 0; a < 3; ++a) { if (L[a] < Lmin[a]) Lmin[a] = L[a]; if (L[a] > Lmax[a]) Lmax[a] = L[a]; } } while (0)
-    OR_ACC(c->nominal.id, c->nominal.front);
-    if (c->nominal.id >= 0 && c->nominal.front_amb) OR_ACC(c->nominal.id, !c->nominal.front);
+#define OR_ACC(id_, fr_, t_) do { radiance(S, (id_), (fr_), o, d, (t_), L); ++alts; \
+        for (int a = 0; a < 3; ++a) { if (L[a] < Lmin[a]) Lmin[a] = L[a]; if (L[a] > Lmax[a]) Lmax[a] = L[a]; } \
+        if ((id_) >= 0 && S->vox) { \
+            double p_[3] = {o[0] + (t_) * d[0], o[1] + (t_) * d[1], o[2] + (t_) * d[2]}, vl[3], vh[3]; \
+            voxel_range(S, p_, vl, vh); \
+            for (int a = 0; a < 3; ++a) { double e_ = (fr_) ? S->Le[3*(id_)+a] : 0.0; \
+                Lmin[a] = fmin(Lmin[a], e_ + vl[a]); \
+                Lmax[a] = fmax(Lmax[a], e_ + vh[a]); } } \
+    } while (0)
+    OR_ACC(c->nominal.id, c->nominal.front, c->nominal.t);
+    if (c->nominal.id >= 0 && c->nominal.front_amb) OR_ACC(c->nominal.id, !c->nominal.front, c->nominal.t);
     for (int i = 0; i < c->n; ++i) {
-        OR_ACC(c->c[i].id, c->c[i].front);
-        if (c->c[i].front_amb) OR_ACC(c->c[i].id, !c->c[i].front);
+        OR_ACC(c->c[i].id, c->c[i].front, c->c[i].t);
+        if (c->c[i].front_amb) OR_ACC(c->c[i].id, !c->c[i].front, c->c[i].t);
     }
-    if (c->miss_possible) OR_ACC(-1, 0);
+    if (c->miss_possible) OR_ACC(-1, 0, 0.0);
 #undef OR_ACC
     int amb = 0;
     for (int a = 0; a < 3; ++a) if (Lmin[a] != Lmax[a]) amb = 1;
@@ -574,11 +693,11 @@ static void bake_point(bake_job* J, int64_t p)
         ocands c;
         closest(S, o, wi, skip, J->eta, &c);
         double L[3];
-        radiance(S, c.nominal.id, c.nominal.front, wi, L);
+        radiance(S, c.nominal.id, c.nominal.front, o, wi, c.nominal.t, L);
         for (int a = 0; a < 3; ++a) nom[a] += L[a];
         if (lo) {
             double Lmin[3], Lmax[3];
-            amb_rays += radiance_range(S, &c, wi, Lmin, Lmax);
+            amb_rays += radiance_range(S, &c, o, wi, Lmin, Lmax);
             for (int a = 0; a < 3; ++a) { lo[a] += Lmin[a]; hi[a] += Lmax[a]; }
         }
     }
@@ -619,11 +738,11 @@ static void bake_point(bake_job* J, int64_t p)
             ocands cd;
             closest(S, o, wi, skip, J->eta, &cd);
             double L[3];
-            radiance(S, cd.nominal.id, cd.nominal.front, wi, L);
+            radiance(S, cd.nominal.id, cd.nominal.front, o, wi, cd.nominal.t, L);
             for (int a = 0; a < 3; ++a) { s0[a] += L[a] * F0 * w; s1[a] += L[a] * F1 * w; }
             if (lo) {
                 double Lmin[3], Lmax[3];
-                amb_rays += radiance_range(S, &cd, wi, Lmin, Lmax);
+                amb_rays += radiance_range(S, &cd, o, wi, Lmin, Lmax);
                 for (int a = 0; a < 3; ++a) {
                     l0[a] += Lmin[a] * F0 * w; h0[a] += Lmax[a] * F0 * w;
                     l1[a] += Lmin[a] * F1 * w; h1[a] += Lmax[a] * F1 * w;
@@ -1065,7 +1184,10 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
             return;
         }
         if ((double)R->ms[h.id] > R->sigma_c) {
-            for (int c = 0; c < 3; ++c) L[c] += beta[c] * S->cache[3*h.id+c];
+            double p[3] = {o[0] + h.t * d[0], o[1] + h.t * d[1], o[2] + h.t * d[2]}, C[3];
+            if (voxel_ambiguous(S, p)) *amb = 1;
+            cache_at(S, h.id, p, C);
+            for (int c = 0; c < 3; ++c) L[c] += beta[c] * C[c];
             return;
         }
         if (depth > R->max_depth) return;

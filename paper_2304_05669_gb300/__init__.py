@@ -154,6 +154,31 @@ class Scene:
         check(lib().fipt_scene_set_environment(self.handle, _ptr(env), env.shape[1], env.shape[0]))
         self._env = env
 
+    def voxel_cache(self, x, L, R=256, stream=None):
+        """Sec. 4.2: pools pixel radiance L [P,3] at first-hit points x ([P,3],
+        or [P,10] query records) onto an R^3 grid -> [R,R,R,4] (mean rgb, count)."""
+        x = _dev(x, torch.float32, "x")
+        L = _dev(L, torch.float32, "L")
+        stride = 10 if (x.dim() == 2 and x.shape[1] == 10) else 3
+        P = x.shape[0]
+        nbytes = ctypes.c_size_t()
+        check(lib().fipt_voxel_cache_workspace_size(P, ctypes.byref(nbytes)))
+        _b, ws = _workspace(nbytes.value, x.device)
+        grid = torch.empty((R, R, R, 4), dtype=torch.float32, device=x.device)
+        check(lib().fipt_voxel_cache_build(self.handle, _ptr(x), stride, _ptr(L), P, int(R), _ptr(grid),
+                                           _ptr(ws), nbytes.value, _stream(stream)))
+        return grid
+
+    def set_voxel_cache(self, grid):
+        """Use a pooled grid as the cache L' (None: per-triangle values)."""
+        if grid is None:
+            check(lib().fipt_scene_set_voxel_cache(self.handle, None, 0))
+            self._vox = None
+            return
+        grid = _dev(grid, torch.float32, "grid")
+        check(lib().fipt_scene_set_voxel_cache(self.handle, _ptr(grid), grid.shape[0]))
+        self._vox = grid
+
     def set_materials(self, albedo, rough, metal, stream=None):
         """Per-triangle albedo [T,3], roughness [T], metallic [T] (refinement)."""
         albedo = _dev(albedo, torch.float32, "albedo")

@@ -69,6 +69,9 @@ SIGNATURES = {
     "fipt_debug_philox": [P, P, I64, P, P],
     "fipt_scene_set_materials": [P, P, P, P, P],
     "fipt_scene_set_environment": [P, P, I32, I32],
+    "fipt_voxel_cache_workspace_size": [I64, P],
+    "fipt_voxel_cache_build": [P, P, I64, P, I64, I32, P, P, SZ, P],
+    "fipt_scene_set_voxel_cache": [P, P, I32],
     "fipt_bake_refine": [P, P, I64, ctypes.POINTER(BakeParams), F32, I32, I32, P, P, P, P, P],
     "fipt_server_create": [P, SZ, I64, I64, P],
     "fipt_server_add_scene": [P, P, P],

@@ -51,6 +51,8 @@ struct SceneView {
     const double* emit_cdf;     // cumulative emitter areas (same order)
     const float* env;           // environment radiance [H][W][3] for misses, or NULL
     int env_w, env_h;
+    const float4* vox;          // voxel radiance cache [R^3] (mean rgb, count), or NULL
+    int vox_r;
 };
 
 struct fipt_scene {
@@ -77,12 +79,14 @@ struct fipt_scene {
     bool has_materials = false;
     const float* env = nullptr;   // caller-owned environment map
     int env_w = 0, env_h = 0;
+    const float4* vox = nullptr;  // caller-owned voxel radiance cache
+    int vox_r = 0;
     size_t ws_bytes;
     SceneView view() const {
         const int64_t steps = 2 * T + 2;
         return SceneView{nodes, tris, shade, cst, T, (int)(T > 1 ? T - 1 : 1),
                          (int)(steps < 2147483647 ? steps : 2147483647), mats, emit_leaf, emit_cdf,
-                         env, env_w, env_h};
+                         env, env_w, env_h, vox, vox_r};
     }
 };
 
@@ -107,7 +111,7 @@ struct BakeChunk {
 
 // Bake of a list of chunks (several requests / scenes) in one launch.
 fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st, bool env);
+                              int32_t* status, cudaStream_t st, int flags);
 
 fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
 void fipt_count_launch();
@@ -334,6 +338,24 @@ __device__ __forceinline__ float3 env_lookup(const SceneView& sc, float dx, floa
             L.z += w * __ldg(t + 2);
         }
     return L;
+}
+
+// Cache radiance L' at a hit point p: the voxel containing p (cell =
+// floor((p - lo) * R / (hi - lo)) per axis, clamped) when a voxel cache is
+// set.
+__device__ __forceinline__ float3 voxel_lookup(const SceneView& sc, float px, float py, float pz) {
+    const SceneConst* c = sc.cst;
+    const int R = sc.vox_r;
+    const float p[3] = {px, py, pz};
+    int ix[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float ext = c->hi[a] - c->lo[a];
+        const float f = ext > 0.0f ? (p[a] - c->lo[a]) * ((float)R / ext) : 0.0f;
+        ix[a] = min(max((int)floorf(f), 0), R - 1);
+    }
+    const float4 v = __ldg(sc.vox + ((size_t)ix[2] * R + ix[1]) * R + ix[0]);
+    return make_float3(v.x, v.y, v.z);
 }
 
 // ---------------------------------------------------------------- traversal

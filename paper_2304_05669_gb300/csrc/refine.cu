@@ -192,7 +192,13 @@ __device__ void path_radiance(const SceneView& sc, const RefineArgs& R, int n_em
         }
         const float4 m0 = __ldg(sc.mats + 2 * h.leaf);
         if (m0.w > R.sigma_c) {
-            const float4 ca = __ldg(sc.shade + 2 * h.leaf + 1);
+            float3 ca;
+            if (sc.vox) {
+                ca = voxel_lookup(sc, o.x + h.t * d.x, o.y + h.t * d.y, o.z + h.t * d.z);
+            } else {
+                const float4 c4 = __ldg(sc.shade + 2 * h.leaf + 1);
+                ca = make_float3(c4.x, c4.y, c4.z);
+            }
             L[0] += beta[0] * ca.x;
             L[1] += beta[1] * ca.y;
             L[2] += beta[2] * ca.z;

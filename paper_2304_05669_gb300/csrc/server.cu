@@ -313,10 +313,10 @@ void fipt_server::launch_batch() {
     if (involved.empty()) return;
     for (uint64_t t : involved) cudaStreamWaitEvent(compute, reqs[t]->h2d, 0);
     if (nch > 0) {
-        bool env = false;
-        for (int c = 0; c < nch; ++c) env = env || H[c].sc.env != nullptr;
+        int flags = 0;
+        for (int c = 0; c < nch; ++c) flags |= (H[c].sc.env ? 1 : 0) | (H[c].sc.vox ? 2 : 0);
         cudaMemcpyAsync(chunk_dev[slot], H, sizeof(BakeChunk) * (size_t)nch, cudaMemcpyHostToDevice, compute);
-        fipt_status st = launch_bake_batch(chunk_dev[slot], nch, warps, status, compute, env);
+        fipt_status st = launch_bake_batch(chunk_dev[slot], nch, warps, status, compute, flags);
         if (st != FIPT_OK) { fatal = st; snprintf(fatal_msg, sizeof(fatal_msg), "%s", fipt_last_error()); }
     }
     for (uint64_t t : involved) {

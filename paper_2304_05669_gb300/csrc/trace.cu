@@ -190,7 +190,8 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 //  * speculation (Aila and Laine 2009): a lane that reaches a leaf parks
 //    it and keeps descending inner nodes until every lane has a leaf;
 //  * leaves are then tested together.
-template <bool STATS, bool ENV>
+// FLAGS: 1 = environment light for misses, 2 = voxel radiance cache.
+template <bool STATS, int FLAGS>
 __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
                                           const int64_t p, const int lobe, const bool valid,
                                           const BakeArgs& A, float* __restrict__ Ld,
@@ -258,11 +259,17 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                 float lx = 0.0f, ly = 0.0f, lz = 0.0f;
                 if (lit) {
                     const float4 le = __ldg(sc.shade + 2 * best.leaf);
-                    const float4 ca = __ldg(sc.shade + 2 * best.leaf + 1);
+                    float3 ca;
+                    if (FLAGS & 2) {
+                        ca = voxel_lookup(sc, ox + best.t * rdx, oy + best.t * rdy, oz + best.t * rdz);
+                    } else {
+                        const float4 c4 = __ldg(sc.shade + 2 * best.leaf + 1);
+                        ca = make_float3(c4.x, c4.y, c4.z);
+                    }
                     lx = (best.front ? le.x : 0.0f) + ca.x;
                     ly = (best.front ? le.y : 0.0f) + ca.y;
                     lz = (best.front ? le.z : 0.0f) + ca.z;
-                } else if (ENV) {
+                } else if (FLAGS & 1) {
                     const float3 e = env_lookup(sc, rdx, rdy, rdz);
                     lx = e.x; ly = e.y; lz = e.z;
                     lit = true;
@@ -312,7 +319,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     wF1 = F1 * wt;
                 }
                 r = make_ray(ox, oy, oz, dx, dy, dz);
-                if (ENV) { rdx = dx; rdy = dy; rdz = dz; }
+                if (FLAGS) { rdx = dx; rdy = dy; rdz = dz; }
                 best.t = FINF;
                 best.leaf = -1;
                 best.orig = 0x7fffffff;
@@ -419,7 +426,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
 
 // A warp holds 32 consecutive points of one lobe; consecutive warps cycle
 // through the lobes of the same 32 points.
-template <bool STATS, bool ENV>
+template <bool STATS, int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
        float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
@@ -432,7 +439,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int lobe = (int)(w % L);
     const int64_t p = (w / L) * 32 + lane;
     if ((w / L) * 32 >= N) return;          // whole warp past the end
-    bake_item<STATS, ENV>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
+    bake_item<STATS, FLAGS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
 }
 
 // One launch over chunks of several requests, possibly on several scenes
@@ -441,7 +448,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
 // mapping is the single-request one, and the Philox counter uses the
 // chunk's request-local point_base, so every value equals the one a
 // separate fipt_bake of that request would produce.
-template <bool ENV>
+template <int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
              int32_t* status) {
@@ -461,8 +468,8 @@ k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_w
     const int L = 1 + A.K;
     const int lobe = (int)(wl % L);
     const int64_t p = (wl / L) * 32 + lane;
-    bake_item<false, ENV>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
-                          stk + threadIdx.x);
+    bake_item<false, FLAGS>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
+                            stk + threadIdx.x);
 }
 
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
@@ -573,19 +580,28 @@ extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
     const int64_t threads = warps * 32;
     const unsigned nb = blocks(threads, BAKE_THREADS);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool env = s->env != nullptr;
-    if (prm->stats && env)
-        FIPT_LAUNCH((k_bake<true, true>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
-                    s->ctx->status, prm->stats);
-    else if (prm->stats)
-        FIPT_LAUNCH((k_bake<true, false>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
-                    s->ctx->status, prm->stats);
-    else if (env)
-        FIPT_LAUNCH((k_bake<false, true>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
-                    s->ctx->status, nullptr);
-    else
-        FIPT_LAUNCH((k_bake<false, false>), nb, BAKE_THREADS, 0, st, s->view(), q, N, A, Ld, Ls0, Ls1,
-                    s->ctx->status, nullptr);
+    const int flags = (s->env ? 1 : 0) | (s->vox ? 2 : 0);
+    const SceneView sv = s->view();
+    unsigned long long* stats = prm->stats;
+#define FIPT_BAKE_CASE(ST, FL)                                                                   \
+    FIPT_LAUNCH((k_bake<ST, FL>), nb, BAKE_THREADS, 0, st, sv, q, N, A, Ld, Ls0, Ls1, s->ctx->status, \
+                stats)
+    if (stats) {
+        switch (flags) {
+            case 0: FIPT_BAKE_CASE(true, 0); break;
+            case 1: FIPT_BAKE_CASE(true, 1); break;
+            case 2: FIPT_BAKE_CASE(true, 2); break;
+            default: FIPT_BAKE_CASE(true, 3); break;
+        }
+    } else {
+        switch (flags) {
+            case 0: FIPT_BAKE_CASE(false, 0); break;
+            case 1: FIPT_BAKE_CASE(false, 1); break;
+            case 2: FIPT_BAKE_CASE(false, 2); break;
+            default: FIPT_BAKE_CASE(false, 3); break;
+        }
+    }
+#undef FIPT_BAKE_CASE
     FIPT_LAUNCHED("bake");
     return FIPT_OK;
 }
@@ -602,15 +618,15 @@ extern "C" fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* ke
 
 // Internal launcher used by the serving runtime.
 fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st, bool env) {
+                              int32_t* status, cudaStream_t st, int flags) {
     if (n_chunks <= 0 || total_warps <= 0) return FIPT_OK;
-    const int64_t threads = total_warps * 32;
-    if (env)
-        FIPT_LAUNCH(k_bake_batch<true>, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks,
-                    n_chunks, total_warps, status);
-    else
-        FIPT_LAUNCH(k_bake_batch<false>, blocks(threads, BAKE_THREADS), BAKE_THREADS, 0, st, d_chunks,
-                    n_chunks, total_warps, status);
+    const unsigned nb = blocks(total_warps * 32, BAKE_THREADS);
+    switch (flags) {
+        case 0: FIPT_LAUNCH(k_bake_batch<0>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
+        case 1: FIPT_LAUNCH(k_bake_batch<1>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
+        case 2: FIPT_LAUNCH(k_bake_batch<2>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
+        default: FIPT_LAUNCH(k_bake_batch<3>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
+    }
     FIPT_LAUNCHED("bake_batch");
     return FIPT_OK;
 }

@@ -301,8 +301,10 @@ def building_floor(seed: int = 5, rooms: int = 4, step: float = 0.05,
                 "floor%d" % rooms)
 
 
-def surface_queries(mesh: Mesh, n: int, seed: int = 0, min_cos: float = 0.05):
-    """Area-uniform query points on the triangles marked ``sample_ok``.
+def surface_queries(mesh: Mesh, n: int, seed: int = 0, min_cos: float = 0.05,
+                    all_triangles: bool = False):
+    """Area-uniform query points on the triangles marked ``sample_ok`` (every
+    triangle, with no footprint rejection, when ``all_triangles``).
 
     Returns a dict of float32 arrays ``x`` [n,3], ``n`` [n,3] (unit face normal
     on the visible side), ``wo`` [n,3] (unit viewing direction with
@@ -312,7 +314,7 @@ def surface_queries(mesh: Mesh, n: int, seed: int = 0, min_cos: float = 0.05):
     rng = np.random.default_rng(seed)
     V = mesh.V.astype(np.float64)
     F = mesh.F
-    cand = np.nonzero(mesh.sample_ok)[0]
+    cand = np.arange(mesh.T) if all_triangles else np.nonzero(mesh.sample_ok)[0]
     v0, v1, v2 = V[F[cand, 0]], V[F[cand, 1]], V[F[cand, 2]]
     cr = np.cross(v1 - v0, v2 - v0)
     area = 0.5 * np.linalg.norm(cr, axis=1)
@@ -328,7 +330,7 @@ def surface_queries(mesh: Mesh, n: int, seed: int = 0, min_cos: float = 0.05):
              + (r1 * w)[:, None] * v2[k])
         ok = np.ones(len(k), bool)
         onfloor = mesh.floor[cand[k]]
-        for x0, x1, z0, z1 in mesh.footprints:
+        for x0, x1, z0, z1 in ([] if all_triangles else mesh.footprints):
             inside = (x[:, 0] >= x0) & (x[:, 0] <= x1) & (x[:, 2] >= z0) & (x[:, 2] <= z1)
             ok &= ~(onfloor & inside)
         xs.append(x[ok])
