@@ -11,7 +11,8 @@ Contents (each function cites the passage it restates):
 * ``fipt_oracle.c`` (compiled by :func:`build`): Philox4x32-10, the bake of
   Eq. 6-7 through the one-segment cache query of Eq. 9, closest hit (brute
   force and an independent spatial-median BVH), pinhole first hits, Morton
-  codes and the binary radix tree.
+  codes and the binary radix tree, the voxel radiance cache, and emitter
+  extraction (sampling, mask classification, the median of Eq. 12).
 * this module: ctypes bindings, plus the factorized render of Eq. 5 with the
   roughness lerp of Eq. 8, the tone-mapped loss of Eq. 14, its analytic
   gradient, and the per-triangle rendering error of Sec. 4.4.
@@ -84,6 +85,9 @@ def _L():
         L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
         L.oracle_voxel_pool.argtypes = [P, P, P, I64, I32, P]
         L.oracle_scene_set_voxel_cache.argtypes = [P, P, I32]
+        L.oracle_emitter_points.argtypes = [P, U64, U32, I32, P]
+        L.oracle_emitter_classify.argtypes = [P, I64, I32, ctypes.c_float, P, P]
+        L.oracle_emitter_radiance.argtypes = [P, I64, P, I64, P, I64, P, P]
         L.oracle_morton.argtypes = [P, I64, P, I64, P]
         L.oracle_radix_tree.argtypes = [P, P, I64, P, P, P, P]
         L.oracle_radix_tree.restype = I32
@@ -174,6 +178,13 @@ class OracleScene:
             return
         g = _c(grid, np.float64)
         _L().oracle_scene_set_voxel_cache(self._h, _p(g), int(g.shape[0]))
+
+    def emitter_points(self, n_per_tri=100, seed=0, request_id=0):
+        """Sec. 4.4: n_per_tri uniform locations on every triangle (FP64,
+        [T * n_per_tri, 3], triangle-major), Philox counter (t, j, 0x400, rid)."""
+        out = np.zeros((self.T * int(n_per_tri), 3))
+        _L().oracle_emitter_points(self._h, int(seed), int(request_id), int(n_per_tri), _p(out))
+        return out
 
     def closest(self, orig, dirs, skip=None, eta=0.0, brute=False):
         """Closest hit of rays (o + t d, t > 0), ties by (t, id); FP64 MT."""
@@ -411,3 +422,29 @@ def tri_error(tri, Lr, Lgt, T):
     err = np.bincount(tri[v], weights=e[v], minlength=T)[:T]
     cnt = np.bincount(tri[v], minlength=T)[:T].astype(np.int32)
     return err, cnt
+
+
+def emitter_classify(alpha, n_per_tri=100, threshold=0.01):
+    """Sec. 4.4: emitter when the mean of a triangle's n_per_tri mask values
+    exceeds the threshold.  Returns (flag u8 [T], mean f64 [T])."""
+    a = _c(alpha, np.float32).reshape(-1)
+    T = a.size // int(n_per_tri)
+    mean = np.zeros(T)
+    flag = np.zeros(T, np.uint8)
+    _L().oracle_emitter_classify(_p(a), T, int(n_per_tri), float(threshold), _p(mean), _p(flag))
+    return flag, mean
+
+
+def emitter_radiance(tri, rgb, flag, tri_stride=1):
+    """Eq. 12 with zero reflectance at emitters: per-channel lower median of
+    the pixels hitting each emitter triangle.  Returns (Le f32 [T,3], count)."""
+    tri = _c(tri, np.int32).reshape(-1)
+    rgb = _c(rgb, np.float32).reshape(-1, 3)
+    flag = _c(flag, np.uint8)
+    T = len(flag)
+    P = len(rgb)
+    assert tri.size >= (P - 1) * tri_stride + 1 if P else True
+    Le = np.zeros((T, 3), np.float32)
+    cnt = np.zeros(T, np.int32)
+    _L().oracle_emitter_radiance(_p(tri), int(tri_stride), _p(rgb), P, _p(flag), T, _p(Le), _p(cnt))
+    return Le, cnt

@@ -1430,3 +1430,93 @@ int oracle_refine(const oscene* S, const float* mat_a, const float* mat_sigma, c
     free(R.cdf);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Emitter extraction (Sec. 4.4, Eq. 12)                                */
+/* ------------------------------------------------------------------ */
+
+/* n locations uniform on every triangle: the square-root map of two
+ * uniforms (u1, u2) from the Philox words of counter (t, j, 0x400, rid)
+ * gives barycentrics (1 - sqrt u1, sqrt u1 (1 - u2), sqrt u1 u2).
+ * x: [T * n][3], triangle-major. */
+void oracle_emitter_points(const oscene* S, uint64_t seed, uint32_t rid, int n, double* x)
+{
+    for (int64_t t = 0; t < S->T; ++t) {
+        const otri* tr = &S->tri[t];
+        for (int j = 0; j < n; ++j) {
+            double u[4];
+            philox_words((uint32_t)t, (uint32_t)j, 0x400u, rid, seed, u);
+            double r1 = sqrt(u[0]);
+            double b0 = 1.0 - r1, b1 = r1 * (1.0 - u[1]), b2 = r1 * u[1];
+            double* p = x + 3 * (t * n + j);
+            for (int a = 0; a < 3; ++a) p[a] = b0 * tr->v0[a] + b1 * tr->v1[a] + b2 * tr->v2[a];
+        }
+    }
+}
+
+/* A triangle is an emitter when the mean of its n mask values is above the
+ * threshold (0.01 in the paper); the sum runs in sample order in FP64. */
+void oracle_emitter_classify(const float* alpha, int64_t T, int n, float thr, double* mean, uint8_t* flag)
+{
+    for (int64_t t = 0; t < T; ++t) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += (double)alpha[t * n + j];
+        double m = s / (double)n;
+        mean[t] = m;
+        flag[t] = m > (double)thr;
+    }
+}
+
+/* IEEE totalOrder on floats: -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN. */
+static int float_total_order(const void* pa, const void* pb)
+{
+    float a = *(const float*)pa, b = *(const float*)pb;
+    int ca = isnan(a) ? (signbit(a) ? 0 : 2) : 1;
+    int cb = isnan(b) ? (signbit(b) ? 0 : 2) : 1;
+    if (ca != cb) return ca < cb ? -1 : 1;
+    if (ca == 1) {
+        if (a < b) return -1;
+        if (a > b) return 1;
+        if (signbit(a) != signbit(b)) return signbit(a) ? -1 : 1;
+        return 0;
+    }
+    uint32_t ua, ub;
+    memcpy(&ua, &a, 4);
+    memcpy(&ub, &b, 4);
+    if (ua == ub) return 0;
+    return ((ua < ub) == (ca == 2)) ? -1 : 1;
+}
+
+/* Eq. 12 with zero reflectance at an emitter: the L1 fit of L_e to the
+ * pixels whose first hit is the triangle is their per-channel median; with
+ * an even count the lower of the two middle values.  Pixel p's triangle is
+ * tri[p * stride] (outside [0, T): none).  Non-emitters and emitters no
+ * pixel hits get 0. */
+void oracle_emitter_radiance(const int32_t* tri, int64_t stride, const float* rgb, int64_t P,
+                             const uint8_t* flag, int64_t T, float* Le, int32_t* count)
+{
+    int64_t* start = (int64_t*)calloc((size_t)T + 1, sizeof(int64_t));
+    float* vals = (float*)malloc(sizeof(float) * (size_t)(P > 0 ? P : 1));
+    int64_t* fill = (int64_t*)calloc((size_t)T + 1, sizeof(int64_t));
+    for (int64_t t = 0; t < T; ++t) count[t] = 0;
+    for (int64_t p = 0; p < P; ++p) {
+        int32_t t = tri[p * stride];
+        if (t >= 0 && t < T && flag[t]) count[t]++;
+    }
+    for (int64_t t = 0; t < T; ++t) start[t + 1] = start[t] + count[t];
+    for (int c = 0; c < 3; ++c) {
+        for (int64_t t = 0; t < T; ++t) fill[t] = start[t];
+        for (int64_t p = 0; p < P; ++p) {
+            int32_t t = tri[p * stride];
+            if (t >= 0 && t < T && flag[t]) vals[fill[t]++] = rgb[3 * p + c];
+        }
+        for (int64_t t = 0; t < T; ++t) {
+            if (count[t] == 0) { Le[3 * t + c] = 0.0f; continue; }
+            qsort(vals + start[t], (size_t)count[t], sizeof(float), float_total_order);
+            Le[3 * t + c] = vals[start[t] + (count[t] - 1) / 2];
+        }
+    }
+    free(start);
+    free(vals);
+    free(fill);
+}

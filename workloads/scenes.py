@@ -420,3 +420,28 @@ def shading_tables(n: int, K: int = 6, seed: int = 7):
     Ls0 = (base * ramp * rng.uniform(0.8, 1.2, (n, K, 3))).astype(np.float32)
     Ls1 = (0.1 * base * ramp * rng.uniform(0.8, 1.2, (n, K, 3))).astype(np.float32)
     return Ld, Ls0, Ls1
+
+
+def emitter_pixels(mesh: Mesh, P: int, seed: int = 0, miss_frac: float = 0.1,
+                   emitter_frac: float = 0.3, outlier_frac: float = 0.05):
+    """Input pixels for emitter extraction: (tri int32 [P], rgb float32 [P,3]).
+
+    A fraction ``miss_frac`` of pixels hits nothing (tri = -1), a fraction
+    ``emitter_frac`` hits an emitter triangle (uniform over them) with
+    radiance L_e times a per-channel lognormal factor of median 1 (sigma
+    0.2), the rest hit other triangles with radiance U[0, 1]^3.  A fraction
+    ``outlier_frac`` of all pixels is scaled by U[3, 10] (highlights)."""
+    rng = np.random.default_rng(seed)
+    em = np.nonzero(mesh.emitter)[0]
+    other = np.nonzero(~mesh.emitter)[0]
+    kind = rng.uniform(size=P)
+    tri = np.full(P, -1, np.int64)
+    on_e = (kind >= miss_frac) & (kind < miss_frac + emitter_frac) & (len(em) > 0)
+    on_o = kind >= miss_frac + emitter_frac
+    tri[on_e] = em[rng.integers(0, max(len(em), 1), on_e.sum())] if len(em) else -1
+    tri[on_o] = other[rng.integers(0, len(other), on_o.sum())]
+    rgb = rng.uniform(0.0, 1.0, (P, 3))
+    rgb[on_e] = mesh.Le[tri[on_e]] * rng.lognormal(0.0, 0.2, (on_e.sum(), 3))
+    out = rng.uniform(size=P) < outlier_frac
+    rgb[out] *= rng.uniform(3.0, 10.0, (out.sum(), 1))
+    return tri.astype(np.int32), rgb.astype(np.float32)
