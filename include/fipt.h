@@ -236,6 +236,43 @@ fipt_status fipt_voxel_cache_build(fipt_scene* scene, const float* x, int64_t x_
  * values; NULL returns to per-triangle values. */
 fipt_status fipt_scene_set_voxel_cache(fipt_scene* scene, const float* grid, int32_t R);
 
+/* ------------------------------------------------ emitter extraction */
+/* Emitter extraction (Sec. 4.4, Eq. 12).  Step 1: n_per_tri locations
+ * uniform on every triangle, for the caller to evaluate its emission-mask
+ * field alpha at: point j of triangle t uses the Philox words of counter
+ * (t, j, 0x400, request_id), key (seed lo, seed hi); u1, u2 from the first
+ * two words (top 24 bits times 2^-24), barycentrics (1 - sqrt(u1),
+ * sqrt(u1) (1 - u2), sqrt(u1) u2) on the triangle's float vertices in f32.
+ * x: device f32 [T * n_per_tri, 3] (triangle-major, original triangle
+ * order, caller-owned).  n_per_tri in [1, 2^20] (the paper uses 100). */
+fipt_status fipt_emitter_sample_points(fipt_scene* scene, uint64_t seed, uint32_t request_id,
+                                       int32_t n_per_tri, float* x, fipt_stream stream);
+/* Step 2: triangle t is an emitter when the mean of
+ * alpha[t * n_per_tri .. +n_per_tri) (device f32, summed in order in FP64,
+ * divided by n_per_tri) is > threshold (0.01 in the paper, compared in
+ * FP64).  is_emitter: device u8 [T] (0/1); mean_alpha: device f64 [T] or
+ * NULL. */
+fipt_status fipt_emitter_classify(const float* alpha, int64_t T, int32_t n_per_tri, float threshold,
+                                  double* mean_alpha, uint8_t* is_emitter, fipt_stream stream);
+/* Step 3: with zero reflectance at emitters the L1 fit of Eq. 12 has the
+ * closed form L_e = per-channel median of the radiance of the input pixels
+ * whose first hit is the triangle.  tri: device i32, pixel p's triangle at
+ * tri[p * tri_stride] (stride 10 reads the id of fipt_query records; < 0 or
+ * >= T: no triangle); rgb: device f32 [P,3]; is_emitter: device u8 [T].
+ * Le: device f32 [T,3] receives the lower median (sorted value at index
+ * (c - 1) / 2 of the c pixels) of emitter triangles, 0 for other triangles
+ * and for emitters no pixel hits; count: device i32 [T] or NULL, the pixels
+ * per emitter triangle.  Values order as IEEE totalOrder (NaN above +inf).
+ * Workspace from fipt_emitter_radiance_workspace_size(P, T). */
+fipt_status fipt_emitter_radiance_workspace_size(int64_t P, int64_t T, size_t* bytes);
+fipt_status fipt_emitter_radiance(const int32_t* tri, int64_t tri_stride, const float* rgb, int64_t P,
+                                  const uint8_t* is_emitter, int64_t T, float* Le, int32_t* count,
+                                  void* workspace, size_t ws_bytes, fipt_stream stream);
+/* Replaces the scene's emission L_e (device f32 [T,3], original order) and
+ * rebuilds the emitter table the refinement samples, without rebuilding
+ * the BVH. */
+fipt_status fipt_scene_set_emission(fipt_scene* scene, const float* Le, fipt_stream stream);
+
 /* Per-triangle materials for the refinement (stage-2 estimates in the
  * paper): albedo [T,3], roughness [T], metallic [T] f32, original order. */
 fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, const float* rough,

@@ -19,7 +19,8 @@ from ._native import (BakeParams, FiptError, FIPT_MAX_K, Request, ServerStats, c
 
 __all__ = ["Context", "Scene", "bake", "bake_refine", "render_fwd", "render_bwd", "FactorizedRender",
            "factorized_render_loss", "tri_error", "compact_queries", "pack_queries",
-           "unpack_queries", "philox", "FiptError", "library_path", "context", "Server"]
+           "unpack_queries", "philox", "emitter_classify", "emitter_radiance", "extract_emitters",
+           "FiptError", "library_path", "context", "Server"]
 
 
 def _ptr(t):
@@ -178,6 +179,20 @@ class Scene:
         grid = _dev(grid, torch.float32, "grid")
         check(lib().fipt_scene_set_voxel_cache(self.handle, _ptr(grid), grid.shape[0]))
         self._vox = grid
+
+    def set_emission(self, Le, stream=None):
+        """Replaces L_e [T,3] (rebuilds the emitter table, keeps the BVH)."""
+        Le = _dev(Le, torch.float32, "Le")
+        check(lib().fipt_scene_set_emission(self.handle, _ptr(Le), _stream(stream)))
+        self._keep = self._keep + (Le,)
+
+    def emitter_points(self, n_per_tri=100, seed=0, request_id=0, stream=None):
+        """Sec. 4.4: n_per_tri uniform locations on every triangle -> f32
+        [T * n_per_tri, 3] (triangle-major), where the emission mask is read."""
+        x = torch.empty((self.T * int(n_per_tri), 3), dtype=torch.float32, device=self.device)
+        check(lib().fipt_emitter_sample_points(self.handle, int(seed), int(request_id), int(n_per_tri),
+                                               _ptr(x), _stream(stream)))
+        return x
 
     def set_materials(self, albedo, rough, metal, stream=None):
         """Per-triangle albedo [T,3], roughness [T], metallic [T] (refinement)."""
@@ -386,6 +401,60 @@ def tri_error(tri, Lr, Lgt, T, stream=None, tri_stride=1):
                                _ptr(cnt),
                                _ptr(ws), nbytes.value, _stream(stream)))
     return err, cnt
+
+
+def emitter_classify(alpha, n_per_tri=100, threshold=0.01, stream=None):
+    """Sec. 4.4: a triangle is an emitter when the mean of its n_per_tri mask
+    values (alpha, f32 [T * n_per_tri], triangle-major) exceeds threshold.
+    Returns (is_emitter u8 [T], mean f64 [T])."""
+    alpha = _dev(alpha, torch.float32, "alpha").reshape(-1)
+    n = int(n_per_tri)
+    if alpha.numel() % n:
+        raise ValueError("alpha has %d values, not a multiple of n_per_tri=%d" % (alpha.numel(), n))
+    T = alpha.numel() // n
+    flag = torch.empty(T, dtype=torch.uint8, device=alpha.device)
+    mean = torch.empty(T, dtype=torch.float64, device=alpha.device)
+    check(lib().fipt_emitter_classify(_ptr(alpha), T, n, float(threshold), _ptr(mean), _ptr(flag),
+                                      _stream(stream)))
+    return flag, mean
+
+
+def emitter_radiance(tri, rgb, is_emitter, stream=None, tri_stride=1):
+    """Eq. 12 with zero reflectance at emitters: per-channel (lower) median of
+    the radiance rgb [P,3] of the pixels whose first hit is each emitter
+    triangle.  ``tri`` as in :func:`tri_error`.  Returns (Le f32 [T,3],
+    count i32 [T])."""
+    if tri.dtype == torch.float32 and tri.dim() == 2 and tri.shape[1] == 10:
+        P, tri_stride = tri.shape[0], 10
+        tri = tri[:, 9:10]
+    else:
+        P = tri.shape[0]
+    rgb = _dev(rgb, torch.float32, "rgb")
+    is_emitter = _dev(is_emitter, torch.uint8, "is_emitter")
+    T = is_emitter.shape[0]
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_emitter_radiance_workspace_size(P, T, ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, rgb.device)
+    Le = torch.empty((T, 3), dtype=torch.float32, device=rgb.device)
+    cnt = torch.empty(T, dtype=torch.int32, device=rgb.device)
+    check(lib().fipt_emitter_radiance(_ptr(tri), int(tri_stride), _ptr(rgb), P, _ptr(is_emitter), T,
+                                      _ptr(Le), _ptr(cnt), _ptr(ws), nbytes.value, _stream(stream)))
+    return Le, cnt
+
+
+def extract_emitters(scene: Scene, alpha_fn, pixel_tri, pixel_rgb, n_per_tri=100, threshold=0.01,
+                     seed=0, set_emission=True, stream=None):
+    """The emitter-extraction step end to end (Sec. 4.4): sample every
+    triangle, read the mask field ``alpha_fn(points [M,3]) -> [M]`` there,
+    classify, take L_e in closed form from the pixels, and (by default)
+    install it as the scene's emission.  Returns (is_emitter, Le, count)."""
+    x = scene.emitter_points(n_per_tri, seed=seed, stream=stream)
+    alpha = alpha_fn(x).to(torch.float32).reshape(-1)
+    flag, _ = emitter_classify(alpha, n_per_tri, threshold, stream=stream)
+    Le, cnt = emitter_radiance(pixel_tri, pixel_rgb, flag, stream=stream)
+    if set_emission:
+        scene.set_emission(Le, stream=stream)
+    return flag, Le, cnt
 
 
 def philox(ctr, key, stream=None):

@@ -72,6 +72,11 @@ SIGNATURES = {
     "fipt_voxel_cache_workspace_size": [I64, P],
     "fipt_voxel_cache_build": [P, P, I64, P, I64, I32, P, P, SZ, P],
     "fipt_scene_set_voxel_cache": [P, P, I32],
+    "fipt_emitter_sample_points": [P, U64, U32, I32, P, P],
+    "fipt_emitter_classify": [P, I64, I32, F32, P, P, P],
+    "fipt_emitter_radiance_workspace_size": [I64, I64, P],
+    "fipt_emitter_radiance": [P, I64, P, I64, P, I64, P, P, P, SZ, P],
+    "fipt_scene_set_emission": [P, P, P],
     "fipt_bake_refine": [P, P, I64, ctypes.POINTER(BakeParams), F32, I32, I32, P, P, P, P, P],
     "fipt_server_create": [P, SZ, I64, I64, P],
     "fipt_server_add_scene": [P, P, P],

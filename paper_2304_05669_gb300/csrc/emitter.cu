@@ -1,0 +1,215 @@
+// Emitter extraction (Sec. 4.4, Eq. 12).
+//
+// 1. Sample n locations uniformly on every triangle (square-root map of two
+//    Philox uniforms, counter (t, j, 0x400, request)); the caller evaluates
+//    its emission-mask field alpha there.
+// 2. A triangle is an emitter when the mean of its n alphas exceeds the
+//    threshold (0.01 in the paper); the mean is summed in sample order in
+//    FP64, so the decision is deterministic.
+// 3. With zero reflectance at emitters, the L1 problem of Eq. 12 is solved
+//    per channel by the median of the radiance of the input pixels whose
+//    first hit is the triangle.  Pixels are sorted per channel by the 64-bit
+//    key (triangle << 32 | order-preserving bits of the value); non-emitter
+//    pixels get triangle T and sort last.  Each triangle's segment in the
+//    sorted keys gives its count, and the lower median (index (c - 1) / 2)
+//    its value.
+#include "fipt_internal.cuh"
+
+namespace {
+
+constexpr uint32_t EMIT_LANE = 0x400u;
+
+__global__ void k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv,
+                              int64_t T, int n, uint2 key, uint32_t rid, float* __restrict__ x) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T * n) return;
+    const int64_t t = i / n;
+    const uint32_t j = (uint32_t)(i - t * n);
+    const int leaf = inv[t];
+    const float4 p0 = __ldg(tris + 3 * leaf), p1 = __ldg(tris + 3 * leaf + 1), p2 = __ldg(tris + 3 * leaf + 2);
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)t, j, EMIT_LANE, rid), key);
+    const float u1 = u24f(w.x), u2 = u24f(w.y);
+    const float r1 = sqrtf(u1);
+    const float b0 = 1.0f - r1, b1 = r1 * (1.0f - u2), b2 = r1 * u2;
+    x[3 * i + 0] = b0 * p0.x + b1 * p1.x + b2 * p2.x;
+    x[3 * i + 1] = b0 * p0.y + b1 * p1.y + b2 * p2.y;
+    x[3 * i + 2] = b0 * p0.z + b1 * p1.z + b2 * p2.z;
+}
+
+__global__ void k_emit_classify(const float* __restrict__ alpha, int64_t T, int n, double thr,
+                                double* __restrict__ mean, uint8_t* __restrict__ flag) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const float* a = alpha + t * n;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += (double)__ldg(a + j);
+    const double m = s / (double)n;
+    if (mean) mean[t] = m;
+    flag[t] = m > thr ? 1 : 0;
+}
+
+// Order-preserving map of float bits to unsigned (negative values flipped).
+__device__ __forceinline__ uint32_t fkey(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float funkey(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__global__ void k_emit_keys(const int32_t* __restrict__ tri, int64_t stride, const float* __restrict__ rgb,
+                            int64_t P, const uint8_t* __restrict__ flag, int64_t T, int c,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int32_t t = tri[p * stride];
+    const uint64_t seg = (t >= 0 && t < T && flag[t]) ? (uint64_t)t : (uint64_t)T;
+    keys[p] = (seg << 32) | fkey(rgb[3 * p + c]);
+    vals[p] = (uint32_t)p;
+}
+
+__global__ void k_emit_bounds(const uint64_t* __restrict__ keys, int64_t P, int64_t T,
+                              int32_t* __restrict__ start, int32_t* __restrict__ end) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= P) return;
+    const uint64_t s = keys[j] >> 32;
+    if (s >= (uint64_t)T) return;
+    if (j == 0 || (keys[j - 1] >> 32) != s) start[s] = (int32_t)j;
+    if (j == P - 1 || (keys[j + 1] >> 32) != s) end[s] = (int32_t)j;
+}
+
+__global__ void k_emit_median(const uint64_t* __restrict__ keys, const int32_t* __restrict__ start,
+                              const int32_t* __restrict__ end, int64_t T, int c,
+                              float* __restrict__ Le, int32_t* __restrict__ count) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int32_t a = start[t];
+    float v = 0.0f;
+    int32_t cnt = 0;
+    if (a >= 0) {
+        cnt = end[t] - a + 1;
+        v = funkey((uint32_t)(keys[a + (cnt - 1) / 2] & 0xFFFFFFFFu));
+    }
+    Le[3 * t + c] = v;
+    if (count && c == 0) count[t] = cnt;
+}
+
+__global__ void k_set_emission(const float* __restrict__ Le, const int32_t* __restrict__ order,
+                               int64_t T, float4* __restrict__ shade) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    const int64_t t = order[leaf];
+    shade[2 * leaf] = make_float4(Le[3 * t], Le[3 * t + 1], Le[3 * t + 2], 0.0f);
+}
+
+struct EmitLayout {
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt, *hist;
+    int32_t *start, *end;
+    size_t bytes;
+};
+
+EmitLayout carve(void* ws, int64_t P, int64_t T) {
+    Carver c{static_cast<char*>(ws), 0};
+    EmitLayout L;
+    const int64_t p1 = P > 0 ? P : 1, t1 = T > 0 ? T : 1;
+    L.keys = c.take<uint64_t>((size_t)p1);
+    L.keys_alt = c.take<uint64_t>((size_t)p1);
+    L.vals = c.take<uint32_t>((size_t)p1);
+    L.vals_alt = c.take<uint32_t>((size_t)p1);
+    L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(p1) / sizeof(uint32_t));
+    L.start = c.take<int32_t>((size_t)t1);
+    L.end = c.take<int32_t>((size_t)t1);
+    L.bytes = c.off + 256;
+    return L;
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+extern "C" fipt_status fipt_emitter_sample_points(fipt_scene* s, uint64_t seed, uint32_t request_id,
+                                                  int32_t n_per_tri, float* x, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(n_per_tri >= 1 && n_per_tri <= (1 << 20), "n_per_tri must be in [1, 2^20]");
+    FIPT_REQUIRE(s->T * (int64_t)n_per_tri < ((int64_t)1 << 40), "T * n_per_tri too large");
+    if (s->T == 0) return FIPT_OK;
+    FIPT_REQUIRE(x && fipt_aligned(x, 4), "x is NULL or misaligned");
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    const int64_t n = s->T * n_per_tri;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    FIPT_LAUNCH(k_emit_points, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream), s->tris, s->inv,
+                s->T, n_per_tri, key, request_id, x);
+    FIPT_LAUNCHED("emitter sample points");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_emitter_classify(const float* alpha, int64_t T, int32_t n_per_tri,
+                                             float threshold, double* mean_alpha, uint8_t* is_emitter,
+                                             fipt_stream stream) {
+    FIPT_REQUIRE(T >= 0 && T < ((int64_t)1 << 31), "bad T");
+    FIPT_REQUIRE(n_per_tri >= 1 && n_per_tri <= (1 << 20), "n_per_tri must be in [1, 2^20]");
+    if (T == 0) return FIPT_OK;
+    FIPT_REQUIRE(alpha && is_emitter && fipt_aligned(alpha, 4), "alpha / is_emitter NULL or misaligned");
+    FIPT_REQUIRE(!mean_alpha || fipt_aligned(mean_alpha, 8), "mean_alpha misaligned");
+    FIPT_LAUNCH(k_emit_classify, blocks(T, 128), 128, 0, static_cast<cudaStream_t>(stream), alpha, T,
+                n_per_tri, (double)threshold, mean_alpha, is_emitter);
+    FIPT_LAUNCHED("emitter classify");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_emitter_radiance_workspace_size(int64_t P, int64_t T, size_t* bytes) {
+    FIPT_REQUIRE(bytes && P >= 0 && P < ((int64_t)1 << 31) && T >= 0 && T < ((int64_t)1 << 31),
+                 "bad arguments");
+    *bytes = carve(nullptr, P, T).bytes;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_emitter_radiance(const int32_t* tri, int64_t tri_stride, const float* rgb,
+                                             int64_t P, const uint8_t* is_emitter, int64_t T, float* Le,
+                                             int32_t* count, void* ws, size_t ws_bytes,
+                                             fipt_stream stream) {
+    FIPT_REQUIRE(P >= 0 && P < ((int64_t)1 << 31) && T >= 0 && T < ((int64_t)1 << 31) && tri_stride >= 1,
+                 "bad sizes");
+    if (T == 0) return FIPT_OK;
+    FIPT_REQUIRE(is_emitter && Le && fipt_aligned(Le, 4), "is_emitter / Le NULL or misaligned");
+    FIPT_REQUIRE(!count || fipt_aligned(count, 4), "count misaligned");
+    FIPT_REQUIRE(P == 0 || (tri && rgb && fipt_aligned(tri, 4) && fipt_aligned(rgb, 4)),
+                 "tri / rgb NULL or misaligned");
+    EmitLayout Y = carve(ws, P, T);
+    if (!ws || ws_bytes < Y.bytes || !fipt_aligned(ws, 256))
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "emitter workspace %zu < %zu bytes (256-aligned)",
+                              ws_bytes, Y.bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FIPT_CUDA(cudaMemsetAsync(Y.start, 0xFF, sizeof(int32_t) * (size_t)T, st));
+    FIPT_CUDA(cudaMemsetAsync(Y.end, 0xFF, sizeof(int32_t) * (size_t)T, st));
+    int bits = 32;
+    while (((int64_t)1 << (bits - 32)) <= T) ++bits;       // segment ids 0..T
+    bits = (bits + 7) & ~7;
+    for (int c = 0; c < 3; ++c) {
+        uint64_t* sk = Y.keys;
+        if (P > 0) {
+            FIPT_LAUNCH(k_emit_keys, blocks(P, 256), 256, 0, st, tri, tri_stride, rgb, P, is_emitter, T, c,
+                        Y.keys, Y.vals);
+            uint32_t* sv;
+            fipt_status r = radix_sort_pairs<uint64_t>(Y.keys, Y.keys_alt, Y.vals, Y.vals_alt, Y.hist, P,
+                                                       bits, st, &sk, &sv);
+            if (r != FIPT_OK) return r;
+            if (c == 0) FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, P, T, Y.start, Y.end);
+        }
+        FIPT_LAUNCH(k_emit_median, blocks(T, 256), 256, 0, st, sk, Y.start, Y.end, T, c, Le, count);
+    }
+    FIPT_LAUNCHED("emitter radiance");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_set_emission(fipt_scene* s, const float* Le, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(s->T == 0 || (Le && fipt_aligned(Le, 4)), "Le is NULL or misaligned");
+    if (s->T == 0) return FIPT_OK;
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FIPT_LAUNCH(k_set_emission, blocks(s->T, 256), 256, 0, st, Le, s->order, s->T, s->shade);
+    return rebuild_emitter_table(s, st);
+}

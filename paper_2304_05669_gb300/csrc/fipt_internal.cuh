@@ -160,6 +160,9 @@ struct Carver {
 // scratch.  Sorts bits [0, bits) of the keys; returns in *out_keys/out_vals
 // which of the two buffers holds the result.
 size_t radix_sort_scratch_bytes(int64_t n);
+// Rebuilds the emitter table (leaves, FP64 area CDF, n_emit, A_emit) from
+// the packed triangles and their current L_e.
+fipt_status rebuild_emitter_table(fipt_scene* s, cudaStream_t st);
 template <class K>
 fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              uint32_t* hist, int64_t n, int bits, cudaStream_t st,

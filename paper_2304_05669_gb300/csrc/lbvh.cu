@@ -290,13 +290,14 @@ __global__ void k_inverse(const int32_t* __restrict__ order, int64_t T, int32_t*
     if (leaf < T) inv[order[leaf]] = (int32_t)leaf;
 }
 
-// Emitter table for area sampling: emitter triangles in original index
-// order, their leaf, and cumulative areas in FP64 (areas from the float
-// vertices in double), built by one block scanning T in chunks.
+// Emitter table for area sampling: emitter triangles (L_e > 0 in some
+// channel) in original index order, their leaf, and cumulative areas in
+// FP64 (areas from the packed float vertices in double), built by one block
+// scanning T in chunks.
 __global__ void __launch_bounds__(1024)
-k_emitters(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ F,
-           const float* __restrict__ Le, int64_t T, const int32_t* __restrict__ inv,
-           int32_t* __restrict__ emit_leaf, double* __restrict__ emit_cdf, SceneConst* c) {
+k_emitters(const float4* __restrict__ tris, const float4* __restrict__ shade, int64_t T,
+           const int32_t* __restrict__ inv, int32_t* __restrict__ emit_leaf,
+           double* __restrict__ emit_cdf, SceneConst* c) {
     __shared__ int wcnt[32];
     __shared__ double warea[32];
     int carry = 0;
@@ -306,18 +307,15 @@ k_emitters(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ 
         const int64_t t = base + threadIdx.x;
         int flag = 0;
         double area = 0.0;
-        if (t < T && (Le[3 * t] > 0.0f || Le[3 * t + 1] > 0.0f || Le[3 * t + 2] > 0.0f)) {
+        const int leaf = t < T ? inv[t] : 0;
+        const float4 le = t < T ? shade[2 * leaf] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (le.x > 0.0f || le.y > 0.0f || le.z > 0.0f) {
             flag = 1;
-            int64_t i[3];
-            for (int k = 0; k < 3; ++k) {
-                const int32_t v = F[3 * t + k];
-                i[k] = (v >= 0 && v < nV) ? v : 0;
-            }
-            double e1[3], e2[3];
-            for (int a = 0; a < 3; ++a) {
-                e1[a] = (double)V[3 * i[1] + a] - (double)V[3 * i[0] + a];
-                e2[a] = (double)V[3 * i[2] + a] - (double)V[3 * i[0] + a];
-            }
+            const float4 p0 = tris[3 * leaf], p1 = tris[3 * leaf + 1], p2 = tris[3 * leaf + 2];
+            const double e1[3] = {(double)p1.x - (double)p0.x, (double)p1.y - (double)p0.y,
+                                  (double)p1.z - (double)p0.z};
+            const double e2[3] = {(double)p2.x - (double)p0.x, (double)p2.y - (double)p0.y,
+                                  (double)p2.z - (double)p0.z};
             const double cx = e1[1] * e2[2] - e1[2] * e2[1];
             const double cy = e1[2] * e2[0] - e1[0] * e2[2];
             const double cz = e1[0] * e2[1] - e1[1] * e2[0];
@@ -349,7 +347,7 @@ k_emitters(const float* __restrict__ V, int64_t nV, const int32_t* __restrict__ 
         const double before_a = warp > 0 ? warea[warp - 1] : 0.0;
         if (flag) {
             const int pos = carry + before + ic - 1;
-            emit_leaf[pos] = inv[t];
+            emit_leaf[pos] = leaf;
             emit_cdf[pos] = carry_area + before_a + ia;
         }
         carry += wcnt[31];
@@ -479,6 +477,14 @@ template fipt_status radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*,
                                                 uint32_t*, int64_t, int, cudaStream_t,
                                                 uint32_t**, uint32_t**);
 
+fipt_status rebuild_emitter_table(fipt_scene* s, cudaStream_t st) {
+    if (s->T == 0) return FIPT_OK;
+    FIPT_LAUNCH(k_emitters, 1, 1024, 0, st, s->tris, s->shade, s->T, s->inv, s->emit_leaf, s->emit_cdf,
+                s->cst);
+    FIPT_LAUNCHED("emitter table");
+    return FIPT_OK;
+}
+
 // ---------------------------------------------------------------- C ABI
 namespace {
 struct SceneLayout {
@@ -586,7 +592,8 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
                                                       L.flags, T);
         }
         FIPT_LAUNCH(k_inverse, grid_for(T, 256), 256, 0, st, L.order, T, L.inv);
-        FIPT_LAUNCH(k_emitters, 1, 1024, 0, st, V, nV, F, Le, T, L.inv, L.emit_leaf, L.emit_cdf, L.cst);
+        fipt_status re = rebuild_emitter_table(s, st);
+        if (re != FIPT_OK) { delete s; return re; }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { delete s; return fipt_check_cuda(e, "scene build"); }
