@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--refine-points", type=int, default=1 << 18,
                     help="points of the stage-3 refinement measurement (0 = skip)")
     ap.add_argument("--refine-spp", type=int, default=32)
+    ap.add_argument("--next-spp", type=int, default=32,
+                    help="spp of the voxel-cache / environment bakes (0 = skip those rows)")
     return ap.parse_args()
 
 
@@ -399,6 +401,142 @@ def run_refine(args, F, dev, mesh, sc, q_all, with_cpu):
     return out
 
 
+# ---------------------------------------------------------------- next rows (f2-f4)
+def _device_time(fn, reps=5, warm=2):
+    """Median CUDA-event seconds of fn() on the current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(ts))
+
+
+def _sort_passes(bits):
+    return (bits + 7) // 8
+
+
+def run_next_rows(args, F, dev, mesh, sc, q, Lgt, qa, with_cpu, peak):
+    """Voxel radiance cache (Sec. 4.2), environment light (Sec. 8 window
+    light) and emitter extraction (Sec. 4.4, Eq. 12), each timed with CUDA
+    events (median of 5) on the benchmark's scene, with its algorithmic
+    bytes against the measured HBM copy rate and the FP64 oracle timed on a
+    sample beside it."""
+    import torch
+    out = {}
+    N = q.shape[0]
+    K = len(SIGMA)
+    spp = args.next_spp
+
+    def bake_rate(scene, qq, stats_too=True):
+        t = _device_time(lambda: F.bake(scene, qq, SIGMA, spp, spp, seed=5), reps=3, warm=1)
+        rays = qq.shape[0] * spp * (1 + K)
+        st = torch.zeros(4, dtype=torch.int64, device=dev)
+        F.bake(scene, qq, SIGMA, spp, spp, seed=5, stats=st)
+        n_rays, n_nodes, n_tris, _ = [int(x) for x in st.cpu().tolist()]
+        alg = 64.0 * n_nodes + 48.0 * n_tris + 24.0 * n_rays + qq.shape[0] * (40 + 12 * (1 + 2 * K))
+        return t, rays, alg
+
+    # ---- f3: voxel cache over the N pixels' first hits and radiance
+    R = 256
+    grid = sc.voxel_cache(q, Lgt, R)
+    t_pool = _device_time(lambda: sc.voxel_cache(q, Lgt, R))
+    nonempty = int((grid[..., 3] > 0).sum().item())
+    bits = max(8, int(np.ceil(np.log2(R ** 3))))
+    pool_bytes = 16.0 * R ** 3 + N * (24 + 8 + 24 * _sort_passes(bits) + 20) + 16.0 * nonempty
+    t_plain, rays, _ = bake_rate(sc, q)
+    sc.set_voxel_cache(grid)
+    t_vox, _, alg_vox = bake_rate(sc, q)
+    sc.set_voxel_cache(None)
+    vox = {"R": R, "pixels": N, "nonempty_voxels": nonempty,
+           "pool_ms": round(1e3 * t_pool, 3), "pool_mpixels_per_s": round(N / t_pool / 1e6, 1),
+           "pool_alg_bytes": int(pool_bytes),
+           "pool_roofline": {"bound": "hbm", "achieved": round(pool_bytes / t_pool / 1e9, 1),
+                             "peak": peak, "unit": "GB/s",
+                             "frac": round(pool_bytes / t_pool / 1e9 / peak, 4)},
+           "bake_spp": spp, "bake_plain_mrays_per_s": round(rays / t_plain / 1e6, 1),
+           "bake_voxel_mrays_per_s": round(rays / t_vox / 1e6, 1),
+           "bake_voxel_roofline_frac": round(alg_vox / t_vox / 1e9 / peak, 4)}
+    # ---- f4: environment map, open Cornell box (rays leave through the front)
+    from workloads import cornell_box, surface_queries
+    cb = cornell_box()
+    scb = F.Scene.from_mesh(cb, device=dev)
+    nq = 1 << 20
+    sq = surface_queries(cb, nq, seed=12)
+    qc = F.pack_queries(*[torch.from_numpy(np.ascontiguousarray(sq[k])).to(dev)
+                          for k in ("x", "n", "wo", "tri")])
+    rng = np.random.default_rng(13)
+    env = torch.from_numpy(rng.uniform(0, 3, (512, 1024, 3)).astype(np.float32)).to(dev)
+    t_noenv, rays_c, _ = bake_rate(scb, qc)
+    scb.set_environment(env)
+    t_env, _, alg_env = bake_rate(scb, qc)
+    envr = {"scene": "open Cornell box 36 tris", "points": nq, "spp": spp, "env": [512, 1024],
+            "bake_without_env_mrays_per_s": round(rays_c / t_noenv / 1e6, 1),
+            "bake_env_mrays_per_s": round(rays_c / t_env / 1e6, 1),
+            "bake_env_roofline_frac": round(alg_env / t_env / 1e9 / peak, 4)}
+    # ---- f2: emitter extraction on the benchmark scene
+    n_per = 100
+    T = mesh.T
+    Pq = qa.shape[0]
+    rgb = torch.rand((Pq, 3), device=dev, generator=torch.Generator(device=dev).manual_seed(14)) * 4
+
+    def alpha_fn(x):
+        return (x[:, 1] > 2.9).float() * 0.05
+
+    pts = sc.emitter_points(n_per)
+    alpha = alpha_fn(pts)
+    t_pts = _device_time(lambda: sc.emitter_points(n_per))
+    t_cls = _device_time(lambda: F.emitter_classify(alpha, n_per, 0.01))
+    flag, _ = F.emitter_classify(alpha, n_per, 0.01)
+    t_rad = _device_time(lambda: F.emitter_radiance(qa, rgb, flag))
+    seg_bits = 32 + int(np.ceil(np.log2(T + 1)))
+    rad_bytes = 3 * Pq * (4 + 4 + 12 + 24 * _sort_passes(seg_bits) + 8) + 3 * T * 16
+    b_pts = 12.0 * T * n_per + 52.0 * T
+    b_cls = 4.0 * T * n_per + 9.0 * T
+    em = {"triangles": T, "samples_per_triangle": n_per, "pixels": Pq,
+          "emitters_found": int(flag.sum().item()),
+          "points_ms": round(1e3 * t_pts, 3), "classify_ms": round(1e3 * t_cls, 3),
+          "radiance_ms": round(1e3 * t_rad, 3),
+          "points_roofline_frac": round(b_pts / t_pts / 1e9 / peak, 4),
+          "classify_roofline_frac": round(b_cls / t_cls / 1e9 / peak, 4),
+          "radiance_roofline_frac": round(rad_bytes / t_rad / 1e9 / peak, 4),
+          "radiance_mpixels_per_s": round(Pq / t_rad / 1e6, 1)}
+    if with_cpu:
+        import oracle as O
+        S = O.OracleScene.from_mesh(mesh)
+        xh = q[:, :3].cpu().numpy().copy()
+        Lh = Lgt.cpu().numpy()
+        t0 = time.perf_counter()
+        S.voxel_pool(xh, Lh, R)
+        vox["cpu_oracle_pool_mpixels_per_s"] = round(N / (time.perf_counter() - t0) / 1e6, 2)
+        t0 = time.perf_counter()
+        S.emitter_points(n_per)
+        em["cpu_oracle_points_ms"] = round(1e3 * (time.perf_counter() - t0), 1)
+        ah = alpha.cpu().numpy()
+        t0 = time.perf_counter()
+        fo, _ = O.emitter_classify(ah, n_per, 0.01)
+        em["cpu_oracle_classify_ms"] = round(1e3 * (time.perf_counter() - t0), 1)
+        trih = qa[:, 9].contiguous().view(torch.int32).cpu().numpy()
+        rgbh = rgb.cpu().numpy()
+        t0 = time.perf_counter()
+        O.emitter_radiance(trih, rgbh, fo)
+        em["cpu_oracle_radiance_ms"] = round(1e3 * (time.perf_counter() - t0), 1)
+        em["cpu_oracle_threads"] = 1
+        vox["cpu_oracle_threads"] = 1
+    F.context().sync_status()
+    out["voxel_cache"] = vox
+    out["environment"] = envr
+    out["emitter_extraction"] = em
+    return out
+
+
 def pinhole_views_for(mesh):
     from workloads import pinhole_views
     return pinhole_views(mesh, 24, seed=2)
@@ -545,6 +683,12 @@ def run_ours(args, wl, world, rank, local):
     if rank == 0 and world == 1 and args.refine_points > 0:
         refine = run_refine(args, F, dev, mesh, sc0, q0, not args.no_cpu_baseline)
 
+    next_rows = None
+    if rank == 0 and world == 1 and args.next_spp > 0:
+        qa0, _v = sc0.camera_queries(dv["cams"], W, H)
+        next_rows = run_next_rows(args, F, dev, mesh, sc0, q0, Lgt, qa0, not args.no_cpu_baseline,
+                                  measured_peaks()[0])
+
     serving = None
     if rank == 0 and world == 1 and args.serve_requests > 0:
         serving = run_serving(args, F, dev)
@@ -578,6 +722,7 @@ def run_ours(args, wl, world, rank, local):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "refine": refine,
+        "next_rows": next_rows,
         "serving": serving,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),

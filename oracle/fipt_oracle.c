@@ -290,13 +290,20 @@ static void cache_at(const oscene* S, int32_t id, const double p[3], double C[3]
 
 /* Whether a float32 hit point may fall in a neighbouring voxel: some
  * coordinate lies within 1e-3 of a cell face (a float32 hit point is off
- * by ~1e-6 of the scene size, ~1e-4 of a 256-cell voxel). */
+ * by ~1e-6 of the scene size, ~1e-4 of a 256-cell voxel) and the cell
+ * across that face is inside the grid (beyond the grid, both sides clamp
+ * into the same border cell). */
 static int voxel_ambiguous(const oscene* S, const double p[3])
 {
     if (!S->vox) return 0;
+    const int R = S->vox_r;
     double fr[3];
-    voxel_of(S, S->vox_r, p, fr);
-    for (int a = 0; a < 3; ++a) if (fr[a] < 1e-3 || fr[a] > 1.0 - 1e-3) return 1;
+    int64_t v = voxel_of(S, R, p, fr);
+    int64_t ix[3] = {v % R, (v / R) % R, v / ((int64_t)R * R)};
+    for (int a = 0; a < 3; ++a) {
+        if (fr[a] < 1e-3 && ix[a] > 0) return 1;
+        if (fr[a] > 1.0 - 1e-3 && ix[a] < R - 1) return 1;
+    }
     return 0;
 }
 
