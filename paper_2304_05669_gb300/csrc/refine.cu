@@ -19,7 +19,14 @@
 
 namespace {
 
-constexpr int REFINE_THREADS = 128;
+#ifndef FIPT_REFINE_THREADS
+#define FIPT_REFINE_THREADS 64
+#endif
+#ifndef FIPT_REFINE_MINB
+#define FIPT_REFINE_MINB 12
+#endif
+constexpr int REFINE_THREADS = FIPT_REFINE_THREADS;
+constexpr int REFINE_MINB = FIPT_REFINE_MINB;
 constexpr float PI_F = 3.14159265358979f;
 
 struct RefineArgs {
@@ -119,7 +126,8 @@ __device__ __forceinline__ Mat vertex_mat(const SceneView& sc, int leaf, float m
 // hs is given, wi was reflected about that sampled half vector and D is
 // evaluated there (sin2h = its squared sine), not at a recomputed one.
 __device__ __forceinline__ void vertex_brdf(const Mat& M, float3 n, float3 wo, float3 wi, float mu_o,
-                                            float f[3], float& pdf, const float3* hs = nullptr,
+                                            float f[3], float& pdf, bool use_h = false,
+                                            float3 hs = make_float3(0.0f, 0.0f, 1.0f),
                                             float sin2h = 0.0f) {
     f[0] = f[1] = f[2] = 0.0f;
     pdf = 0.0f;
@@ -130,8 +138,8 @@ __device__ __forceinline__ void vertex_brdf(const Mat& M, float3 n, float3 wo, f
     pdf = M.Pd * mu_i / PI_F;
     if (!M.spec) return;
     float hx, hy, hz;
-    if (hs) {
-        hx = hs->x; hy = hs->y; hz = hs->z;
+    if (use_h) {
+        hx = hs.x; hy = hs.y; hz = hs.z;
     } else {
         hx = wi.x + wo.x; hy = wi.y + wo.y; hz = wi.z + wo.z;
         const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
@@ -140,7 +148,7 @@ __device__ __forceinline__ void vertex_brdf(const Mat& M, float3 n, float3 wo, f
     const float ch = n.x * hx + n.y * hy + n.z * hz;
     const float co = wo.x * hx + wo.y * hy + wo.z * hz;
     if (ch <= 0.0f || co <= 0.0f) return;
-    const float D = ggx_d(hs ? sin2h : sin2_between(n, hx, hy, hz), ch * ch, M.a2);
+    const float D = ggx_d(use_h ? sin2h : sin2_between(n, hx, hy, hz), ch * ch, M.a2);
     const float G = smith_g1(mu_i, M.a2) * smith_g1(mu_o, M.a2);
     const float x1 = 1.0f - co, x2 = x1 * x1, F1 = x2 * x2 * x1, F0 = 1.0f - F1;
 #pragma unroll
@@ -153,165 +161,61 @@ __device__ __forceinline__ float3 to_world(float3 t, float3 b, float3 n, float x
                        x * t.z + y * b.z + z * n.z);
 }
 
-// Radiance arriving along the ray (o, d) that leaves a surface point on
-// original triangle skip0, estimated from its first hit on (Eq. 10 + MIS).
-template <int STRIDE>
-__device__ void path_radiance(const SceneView& sc, const RefineArgs& R, int n_emit, double A_emit,
-                              float3 o, float3 d, int skip, float pdf_prev, uint32_t pid, uint32_t s,
-                              uint32_t lobe, float L[3], int* stack, int32_t* status) {
-    float beta[3] = {1.0f, 1.0f, 1.0f};
-    L[0] = L[1] = L[2] = 0.0f;
-    const float eps = sc.cst->eps;
-    for (int depth = 1;; ++depth) {
-        const TraceRay r = make_ray(o.x, o.y, o.z, d.x, d.y, d.z);
-        BestHit h;
-        closest_hit<STRIDE>(sc, r, skip, stack, h, status);
-        if (h.leaf < 0) {
-            if (sc.env) {
-                const float3 e = env_lookup(sc, d.x, d.y, d.z);
-                L[0] += beta[0] * e.x;
-                L[1] += beta[1] * e.y;
-                L[2] += beta[2] * e.z;
-            }
-            return;
-        }
-        const float4 le = __ldg(sc.shade + 2 * h.leaf);
-        if (is_emitter(le)) {
-            if (!h.front) return;
-            float w = 1.0f;
-            if (R.mis && n_emit > 0) {
-                const float3 ne = leaf_normal(sc, h.leaf);
-                const float ce = fabsf(d.x * ne.x + d.y * ne.y + d.z * ne.z);
-                const float pl = (float)((double)h.t * h.t / (A_emit * ce));
-                w = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
-            }
-            L[0] += beta[0] * w * le.x;
-            L[1] += beta[1] * w * le.y;
-            L[2] += beta[2] * w * le.z;
-            return;
-        }
-        const float4 m0 = __ldg(sc.mats + 2 * h.leaf);
-        if (m0.w > R.sigma_c) {
-            float3 ca;
-            if (sc.vox) {
-                ca = voxel_lookup(sc, o.x + h.t * d.x, o.y + h.t * d.y, o.z + h.t * d.z);
-            } else {
-                const float4 c4 = __ldg(sc.shade + 2 * h.leaf + 1);
-                ca = make_float3(c4.x, c4.y, c4.z);
-            }
-            L[0] += beta[0] * ca.x;
-            L[1] += beta[1] * ca.y;
-            L[2] += beta[2] * ca.z;
-            return;
-        }
-        if (depth > R.max_depth) return;
-        // a smooth surface: continue the path
-        float3 n = leaf_normal(sc, h.leaf);
-        const float3 wo = make_float3(-d.x, -d.y, -d.z);
-        if (n.x * wo.x + n.y * wo.y + n.z * wo.z < 0.0f) n = make_float3(-n.x, -n.y, -n.z);
-        const float3 x = make_float3(o.x + h.t * d.x, o.y + h.t * d.y, o.z + h.t * d.z);
-        const float3 xo = make_float3(x.x + eps * n.x, x.y + eps * n.y, x.z + eps * n.z);
-        const float mu_o = n.x * wo.x + n.y * wo.y + n.z * wo.z;
-        const Mat M = vertex_mat(sc, h.leaf, mu_o);
-        const uint32_t lane = lobe | ((uint32_t)depth << 9);
-        if (R.mis && n_emit > 0) {
-            float3 y;
-            const int e = emitter_sample(sc, n_emit, A_emit, u4(pid, s, lane | 0x100u, R.A), y);
-            float wx = y.x - xo.x, wy = y.y - xo.y, wz = y.z - xo.z;
-            const float dist = sqrtf(wx * wx + wy * wy + wz * wz);
-            wx /= dist; wy /= dist; wz /= dist;
-            const float3 ne = leaf_normal(sc, e);
-            const float ce = -(wx * ne.x + wy * ne.y + wz * ne.z);
-            if (ce > 0.0f) {
-                float f[3], pb;
-                vertex_brdf(M, n, wo, make_float3(wx, wy, wz), mu_o, f, pb);
-                if (f[0] > 0.0f || f[1] > 0.0f || f[2] > 0.0f) {
-                    BestHit vh;
-                    closest_hit<STRIDE>(sc, make_ray(xo.x, xo.y, xo.z, wx, wy, wz), h.orig, stack, vh,
-                                        status);
-                    if (vh.leaf == e) {
-                        const float pl = (float)((double)dist * dist / (A_emit * ce));
-                        const float w = pl * pl / (pl * pl + pb * pb);
-                        const float4 lee = __ldg(sc.shade + 2 * e);
-                        L[0] += beta[0] * w * lee.x * f[0] / pl;
-                        L[1] += beta[1] * w * lee.y * f[1] / pl;
-                        L[2] += beta[2] * w * lee.z * f[2] / pl;
-                    }
-                }
-            }
-        }
-        const float4 u = u4(pid, s, lane, R.A);
-        float3 tb, bb;
-        onb(n.x, n.y, n.z, tb, bb);
-        float3 wi, hh = make_float3(0.0f, 0.0f, 1.0f);
-        float sin2h = 0.0f;
-        float sn, cs;
-        sincospif(2.0f * u.y, &sn, &cs);
-        const bool glossy = !(u.z < M.Pd);
-        if (!glossy) {
-            const float rr = sqrtf(u.x);
-            wi = to_world(tb, bb, n, rr * cs, rr * sn, sqrtf(1.0f - u.x));
-        } else {
-            const float om = 1.0f - u.x;
-            const float den = om + M.a2 * u.x;
-            sin2h = M.a2 * u.x / den;
-            const float ch = sqrtf(om / den), sh = sqrtf(sin2h);
-            hh = to_world(tb, bb, n, sh * cs, sh * sn, ch);
-            const float c = wo.x * hh.x + wo.y * hh.y + wo.z * hh.z;
-            wi = make_float3(2.0f * c * hh.x - wo.x, 2.0f * c * hh.y - wo.y, 2.0f * c * hh.z - wo.z);
-        }
-        float f[3], pdf;
-        vertex_brdf(M, n, wo, wi, mu_o, f, pdf, glossy ? &hh : nullptr, sin2h);
-        if (pdf <= 0.0f) return;
-        beta[0] *= f[0] / pdf;
-        beta[1] *= f[1] / pdf;
-        beta[2] *= f[2] / pdf;
-        o = xo;
-        d = wi;
-        skip = h.orig;
-        pdf_prev = pdf;
-    }
+// Lane state machine of the refinement.  A lane owns one (point, lobe) pair
+// and walks its samples in order; each sample traces, one ray at a time:
+//   K_S0   the shadow ray of the emitter sample at x (MIS only),
+//   K_PATH a path segment (the lobe sample at x, then BRDF samples),
+//   K_SV   the shadow ray of the emitter sample at a path vertex; the
+//          vertex's BRDF sample (the next K_PATH) is drawn after it.
+// All rays go through the single traversal loop of k_refine, so lanes in
+// different states still walk the BVH together; a lane whose ray finished
+// waits until FIPT_REFINE_REFILL lanes (or all busy lanes) are waiting, and
+// the waiting lanes then consume their hits and set up their next rays
+// together, as the stage-1 bake does.  Shadow rays stop looking beyond the
+// sampled emitter point (only whether that emitter is the closest hit
+// matters).
+enum : int { K_NONE = 0, K_S0 = 1, K_PATH = 2, K_SV = 3 };
+enum : int { A_START, A_MAIN, A_VERTEX_BSDF, A_END_PATH, A_END_SAMPLE, A_RAY };
+
+#ifndef FIPT_REFINE_REFILL
+#define FIPT_REFINE_REFILL 16
+#endif
+
+__device__ __forceinline__ void start_ray(TraceRay& r, BestHit& best, int& node, int& sp, int& steps,
+                                          const SceneView& sc, float ox, float oy, float oz, float dx,
+                                          float dy, float dz, float tmax) {
+    r = make_ray(ox, oy, oz, dx, dy, dz);
+    best.t = tmax;
+    best.leaf = -1;
+    best.orig = 0x7fffffff;
+    best.front = false;
+    sp = 0;
+    steps = 0;
+    node = sc.T > 0 ? 0 : FIPT_DONE;
 }
 
 template <bool PER_SAMPLE>
-__global__ void __launch_bounds__(REFINE_THREADS)
+__global__ void __launch_bounds__(REFINE_THREADS, REFINE_MINB)
 k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R, float* __restrict__ Ld,
          float* __restrict__ Ls0, float* __restrict__ Ls1, float* __restrict__ per_sample,
          int32_t* status) {
+    constexpr unsigned FULL = 0xffffffffu;
     __shared__ int stk[STACK_DEPTH * REFINE_THREADS];
     int* stack = stk + threadIdx.x;
     const BakeArgs& A = R.A;
     const int K = A.K, L = 1 + K;
     const int64_t g = blockIdx.x * (int64_t)REFINE_THREADS + threadIdx.x;
     const int64_t w = g >> 5;
-    const int lane = (int)(g & 31);
     const int lobe = (int)(w % L);
-    const int64_t p = (w / L) * 32 + lane;
-    if (p >= N) return;
-    const float2* qp = reinterpret_cast<const float2*>(q + p);
-    const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
-    float3 n = make_float3(q1.y, q2.x, q2.y);
-    float3 wo = make_float3(q3.x, q3.y, q4.x);
-    const int skip = __float_as_int(q4.y);
-    {
-        const float il = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
-        n = make_float3(n.x * il, n.y * il, n.z * il);
-        const float jl = 1.0f / sqrtf(wo.x * wo.x + wo.y * wo.y + wo.z * wo.z);
-        wo = make_float3(wo.x * jl, wo.y * jl, wo.z * jl);
-    }
-    const float mu_o = n.x * wo.x + n.y * wo.y + n.z * wo.z;
-    const int S = lobe == 0 ? A.spp_d : A.spp_s;
-    float* ps = PER_SAMPLE ? per_sample + ((size_t)(p * L + lobe) * R.smax) * 6 : nullptr;
-    if (lobe > 0 && mu_o <= 1e-2f) {
-        float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
-        float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
-        o0[0] = o0[1] = o0[2] = 0.0f;
-        o1[0] = o1[1] = o1[2] = 0.0f;
-        if (PER_SAMPLE)
-            for (int s = 0; s < R.smax * 6; ++s) ps[s] = 0.0f;
-        return;
-    }
-    float a2 = 0.0f, g1o = 0.0f;
+    const int64_t p = (w / L) * 32 + (int)(g & 31);
+    if ((w / L) * 32 >= N) return;          // whole warp past the end
+    const bool valid = p < N;
+    const float eps = sc.cst->eps;
+    const int n_emit = sc.cst->n_emit;
+    const double A_emit = sc.cst->A_emit;
+    const bool mis = R.mis && n_emit > 0;
+    const uint32_t pid = A.point_base + (uint32_t)p;
+    float a2 = 0.0f;
     if (lobe > 0) {
         float sg = A.sigma[0];
 #pragma unroll
@@ -319,119 +223,385 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
             if (lobe - 1 == k) sg = A.sigma[k];
         const float al = sg * sg;
         a2 = al * al;
-        g1o = smith_g1(mu_o, a2);
     }
-    float3 tb, bb;
-    onb(n.x, n.y, n.z, tb, bb);
-    const float eps = sc.cst->eps;
-    const float3 o = make_float3(q0.x + eps * n.x, q0.y + eps * n.y, q1.x + eps * n.z);
-    const uint32_t pid = A.point_base + (uint32_t)p;
-    const int n_emit = sc.cst->n_emit;
-    const double A_emit = sc.cst->A_emit;
-    float acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int s = 0; s < S; ++s) {
-        float c6[6] = {0, 0, 0, 0, 0, 0};
-        if (R.mis && n_emit > 0) {            // emitter sample at x
-            float3 y;
-            const int e = emitter_sample(sc, n_emit, A_emit, u4(pid, (uint32_t)s, (uint32_t)lobe | 0x100u, A), y);
-            float wx = y.x - o.x, wy = y.y - o.y, wz = y.z - o.z;
-            const float dist = sqrtf(wx * wx + wy * wy + wz * wz);
-            wx /= dist; wy /= dist; wz /= dist;
-            const float3 ne = leaf_normal(sc, e);
-            const float ce = -(wx * ne.x + wy * ne.y + wz * ne.z);
-            const float mu_i = n.x * wx + n.y * wy + n.z * wz;
-            float g0 = 0.0f, g1 = 0.0f, pb = 0.0f;
-            if (ce > 0.0f && mu_i > 0.0f) {
-                if (lobe == 0) {
-                    g0 = mu_i / PI_F;
-                    pb = g0;
+    int S = 0;
+    if (valid) {
+        const float2* qp = reinterpret_cast<const float2*>(q + p);
+        const float2 q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
+        const float nl = 1.0f / sqrtf(q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
+        const float wl = 1.0f / sqrtf(q3.x * q3.x + q3.y * q3.y + q4.x * q4.x);
+        const float mu = (q1.y * nl) * (q3.x * wl) + (q2.x * nl) * (q3.y * wl) + (q2.y * nl) * (q4.x * wl);
+        // specular terms of points seen at grazing angles are defined as zero
+        S = (lobe > 0 && mu <= 1e-2f) ? 0 : (lobe == 0 ? A.spp_d : A.spp_s);
+    }
+
+    // per-lane path state
+    int kind = K_NONE, s = 0, depth = 0, skip = -1, tgt = -1, vleaf = -1;
+    float dx = 0.0f, dy = 0.0f, dz = 1.0f;            // current path direction
+    float b0 = 1.0f, b1 = 1.0f, b2 = 1.0f;            // path throughput
+    float l0 = 0.0f, l1 = 0.0f, l2 = 0.0f;            // path radiance
+    float W0 = 1.0f, W1 = 0.0f, pdf_prev = 0.0f;
+    float sw0 = 0.0f, sw1 = 0.0f, sw2 = 0.0f;         // shadow-ray weights
+    float a0 = 0.0f, a1 = 0.0f, a2s = 0.0f, a3 = 0.0f, a4 = 0.0f, a5 = 0.0f;   // sums over samples
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f, c5 = 0.0f;    // this sample (per-sample output)
+    TraceRay r;
+    BestHit best;
+    best.t = FINF;
+    best.leaf = -1;
+    best.orig = 0x7fffffff;
+    best.front = false;
+    r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
+    int node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
+
+#define FIPT_ADD6(cv, av, v)       \
+    do {                           \
+        if (PER_SAMPLE) cv += (v); \
+        else av += (v);            \
+    } while (0)
+
+    for (;;) {
+        const bool idle = node == FIPT_DONE && pleaf < 0;
+        const bool need = idle && (kind != K_NONE || s < S);
+        const unsigned m_need = __ballot_sync(FULL, need);
+        const unsigned m_busy = __ballot_sync(FULL, !idle);
+        if ((m_need | m_busy) == 0) break;
+        if (m_need != 0 && (m_busy == 0 || __popc(m_need) >= FIPT_REFINE_REFILL) && need) {
+            // ---------------- consume the finished ray
+            int act = A_START;
+            float xox = 0.0f, xoy = 0.0f, xoz = 0.0f;     // origin of a vertex's continuation
+            if (kind == K_S0) {
+                if (best.leaf == tgt) {
+                    const float4 le = __ldg(sc.shade + 2 * tgt);
+                    FIPT_ADD6(c0, a0, sw0 * le.x); FIPT_ADD6(c1, a1, sw0 * le.y); FIPT_ADD6(c2, a2s, sw0 * le.z);
+                    FIPT_ADD6(c3, a3, sw1 * le.x); FIPT_ADD6(c4, a4, sw1 * le.y); FIPT_ADD6(c5, a5, sw1 * le.z);
+                }
+                act = A_MAIN;
+            } else if (kind == K_SV) {
+                if (best.leaf == tgt) {
+                    const float4 le = __ldg(sc.shade + 2 * tgt);
+                    l0 += sw0 * le.x; l1 += sw1 * le.y; l2 += sw2 * le.z;
+                }
+                xox = r.ox; xoy = r.oy; xoz = r.oz;
+                act = A_VERTEX_BSDF;
+            } else if (kind == K_PATH) {
+                act = A_END_PATH;
+                if (best.leaf < 0) {
+                    if (sc.env) {
+                        const float3 e = env_lookup(sc, dx, dy, dz);
+                        l0 += b0 * e.x; l1 += b1 * e.y; l2 += b2 * e.z;
+                    }
                 } else {
-                    float hx = wx + wo.x, hy = wy + wo.y, hz = wz + wo.z;
-                    const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
-                    hx *= hl; hy *= hl; hz *= hl;
-                    const float ch = n.x * hx + n.y * hy + n.z * hz;
-                    const float c = wo.x * hx + wo.y * hy + wo.z * hz;
-                    if (ch > 0.0f && c > 0.0f) {
-                        const float D = ggx_d(sin2_between(n, hx, hy, hz), ch * ch, a2);
-                        const float G = smith_g1(mu_i, a2) * g1o;
-                        const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
-                        g0 = (1.0f - F1) * D * G / (4.0f * mu_o);
-                        g1 = F1 * D * G / (4.0f * mu_o);
-                        pb = D * ch / (4.0f * c);
+                    const int leaf = best.leaf;
+                    const float hx = r.ox + best.t * dx, hy = r.oy + best.t * dy, hz = r.oz + best.t * dz;
+                    const float4 le = __ldg(sc.shade + 2 * leaf);
+                    if (is_emitter(le)) {
+                        if (best.front) {
+                            float wgt = 1.0f;
+                            if (mis) {
+                                const float3 ne = leaf_normal(sc, leaf);
+                                const float ce = fabsf(dx * ne.x + dy * ne.y + dz * ne.z);
+                                const float pl = (float)((double)best.t * best.t / (A_emit * ce));
+                                wgt = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
+                            }
+                            l0 += b0 * wgt * le.x; l1 += b1 * wgt * le.y; l2 += b2 * wgt * le.z;
+                        }
+                    } else if (__ldg(&sc.mats[2 * leaf].w) > R.sigma_c) {
+                        float3 ca;
+                        if (sc.vox) {
+                            ca = voxel_lookup(sc, hx, hy, hz);
+                        } else {
+                            const float4 c4 = __ldg(sc.shade + 2 * leaf + 1);
+                            ca = make_float3(c4.x, c4.y, c4.z);
+                        }
+                        l0 += b0 * ca.x; l1 += b1 * ca.y; l2 += b2 * ca.z;
+                    } else if (depth <= R.max_depth) {
+                        // a smooth surface: a path vertex
+                        float3 nv = leaf_normal(sc, leaf);
+                        if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
+                        xox = hx + eps * nv.x; xoy = hy + eps * nv.y; xoz = hz + eps * nv.z;
+                        vleaf = leaf;
+                        skip = best.orig;
+                        act = A_VERTEX_BSDF;
+                        if (mis) {
+                            const float3 wv = make_float3(-dx, -dy, -dz);
+                            const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
+                            const Mat M = vertex_mat(sc, leaf, mu_v);
+                            float3 y;
+                            const uint32_t lc = (uint32_t)lobe | ((uint32_t)depth << 9) | 0x100u;
+                            const int e = emitter_sample(sc, n_emit, A_emit, u4(pid, (uint32_t)s, lc, A), y);
+                            float ex = y.x - xox, ey = y.y - xoy, ez = y.z - xoz;
+                            const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                            ex /= dist; ey /= dist; ez /= dist;
+                            const float3 ne = leaf_normal(sc, e);
+                            const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
+                            if (ce > 0.0f) {
+                                float f[3], pb;
+                                vertex_brdf(M, nv, wv, make_float3(ex, ey, ez), mu_v, f, pb);
+                                if (f[0] > 0.0f || f[1] > 0.0f || f[2] > 0.0f) {
+                                    const float pl = (float)((double)dist * dist / (A_emit * ce));
+                                    const float wgt = pl * pl / (pl * pl + pb * pb);
+                                    sw0 = b0 * wgt * f[0] / pl;
+                                    sw1 = b1 * wgt * f[1] / pl;
+                                    sw2 = b2 * wgt * f[2] / pl;
+                                    tgt = e;
+                                    start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, ex, ey, ez,
+                                              1.001f * dist + eps);
+                                    kind = K_SV;
+                                    act = A_RAY;
+                                }
+                            }
+                        }
                     }
                 }
             }
-            if (g0 > 0.0f || g1 > 0.0f) {
-                BestHit vh;
-                closest_hit<REFINE_THREADS>(sc, make_ray(o.x, o.y, o.z, wx, wy, wz), skip, stack, vh,
-                                            status);
-                if (vh.leaf == e) {
-                    const float pl = (float)((double)dist * dist / (A_emit * ce));
-                    const float wgt = pl * pl / (pl * pl + pb * pb);
-                    const float4 lee = __ldg(sc.shade + 2 * e);
-                    c6[0] += wgt * lee.x * g0 / pl; c6[1] += wgt * lee.y * g0 / pl; c6[2] += wgt * lee.z * g0 / pl;
-                    c6[3] += wgt * lee.x * g1 / pl; c6[4] += wgt * lee.y * g1 / pl; c6[5] += wgt * lee.z * g1 / pl;
+            // ---------------- set up the next ray
+            while (act != A_RAY) {
+                if (act == A_VERTEX_BSDF) {            // BRDF sample at path vertex `depth`
+                    float3 nv = leaf_normal(sc, vleaf);
+                    if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
+                    const float3 wv = make_float3(-dx, -dy, -dz);
+                    const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
+                    const Mat M = vertex_mat(sc, vleaf, mu_v);
+                    const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe | ((uint32_t)depth << 9), A);
+                    float3 tb, bb;
+                    onb(nv.x, nv.y, nv.z, tb, bb);
+                    float3 wi, hh = make_float3(0.0f, 0.0f, 1.0f);
+                    float sin2h = 0.0f, sn, cs;
+                    sincospif(2.0f * u.y, &sn, &cs);
+                    const bool glossy = !(u.z < M.Pd);
+                    if (!glossy) {
+                        const float rr = sqrtf(u.x);
+                        wi = to_world(tb, bb, nv, rr * cs, rr * sn, sqrtf(1.0f - u.x));
+                    } else {
+                        const float om = 1.0f - u.x;
+                        const float den = om + M.a2 * u.x;
+                        sin2h = M.a2 * u.x / den;
+                        const float ch = sqrtf(om / den), sh = sqrtf(sin2h);
+                        hh = to_world(tb, bb, nv, sh * cs, sh * sn, ch);
+                        const float c = wv.x * hh.x + wv.y * hh.y + wv.z * hh.z;
+                        wi = make_float3(2.0f * c * hh.x - wv.x, 2.0f * c * hh.y - wv.y, 2.0f * c * hh.z - wv.z);
+                    }
+                    float f[3], pdf;
+                    vertex_brdf(M, nv, wv, wi, mu_v, f, pdf, glossy, hh, sin2h);
+                    if (pdf <= 0.0f) {
+                        act = A_END_PATH;
+                    } else {
+                        b0 *= f[0] / pdf; b1 *= f[1] / pdf; b2 *= f[2] / pdf;
+                        start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, wi.x, wi.y, wi.z, FINF);
+                        dx = wi.x; dy = wi.y; dz = wi.z;
+                        pdf_prev = pdf;
+                        ++depth;
+                        kind = K_PATH;
+                        act = A_RAY;
+                        break;
+                    }
+                }
+                if (act == A_END_PATH) {
+                    FIPT_ADD6(c0, a0, W0 * l0); FIPT_ADD6(c1, a1, W0 * l1); FIPT_ADD6(c2, a2s, W0 * l2);
+                    FIPT_ADD6(c3, a3, W1 * l0); FIPT_ADD6(c4, a4, W1 * l1); FIPT_ADD6(c5, a5, W1 * l2);
+                    act = A_END_SAMPLE;
+                }
+                if (act == A_END_SAMPLE) {
+                    if (PER_SAMPLE) {
+                        float* ps = per_sample + ((size_t)(p * L + lobe) * R.smax + s) * 6;
+                        a0 += c0; a1 += c1; a2s += c2; a3 += c3; a4 += c4; a5 += c5;
+                        ps[0] = c0; ps[1] = c1; ps[2] = c2; ps[3] = c3; ps[4] = c4; ps[5] = c5;
+                    }
+                    ++s;
+                    act = A_START;
+                }
+                kind = K_NONE;
+                if (act == A_START && s >= S) break;  // this pair is done
+                // A_START or A_MAIN: the query point's frame
+                const float2* qp = reinterpret_cast<const float2*>(q + p);
+                const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
+                float3 n = make_float3(q1.y, q2.x, q2.y), wo = make_float3(q3.x, q3.y, q4.x);
+                {
+                    const float il = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+                    n = make_float3(n.x * il, n.y * il, n.z * il);
+                    const float jl = 1.0f / sqrtf(wo.x * wo.x + wo.y * wo.y + wo.z * wo.z);
+                    wo = make_float3(wo.x * jl, wo.y * jl, wo.z * jl);
+                }
+                const float mu_o = n.x * wo.x + n.y * wo.y + n.z * wo.z;
+                const float ox = q0.x + eps * n.x, oy = q0.y + eps * n.y, oz = q1.x + eps * n.z;
+                const float g1o = lobe > 0 ? smith_g1(mu_o, a2) : 0.0f;
+                if (act == A_START) {
+                    c0 = c1 = c2 = c3 = c4 = c5 = 0.0f;
+                    act = A_MAIN;
+                    if (mis) {                         // emitter sample at x
+                        float3 y;
+                        const int e = emitter_sample(sc, n_emit, A_emit,
+                                                     u4(pid, (uint32_t)s, (uint32_t)lobe | 0x100u, A), y);
+                        float ex = y.x - ox, ey = y.y - oy, ez = y.z - oz;
+                        const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                        ex /= dist; ey /= dist; ez /= dist;
+                        const float3 ne = leaf_normal(sc, e);
+                        const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
+                        const float mu_i = n.x * ex + n.y * ey + n.z * ez;
+                        float g0 = 0.0f, g1 = 0.0f, pb = 0.0f;
+                        if (ce > 0.0f && mu_i > 0.0f) {
+                            if (lobe == 0) {
+                                g0 = mu_i / PI_F;
+                                pb = g0;
+                            } else {
+                                float hx = ex + wo.x, hy = ey + wo.y, hz = ez + wo.z;
+                                const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
+                                hx *= hl; hy *= hl; hz *= hl;
+                                const float ch = n.x * hx + n.y * hy + n.z * hz;
+                                const float c = wo.x * hx + wo.y * hy + wo.z * hz;
+                                if (ch > 0.0f && c > 0.0f) {
+                                    const float D = ggx_d(sin2_between(n, hx, hy, hz), ch * ch, a2);
+                                    const float G = smith_g1(mu_i, a2) * g1o;
+                                    const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
+                                    g0 = (1.0f - F1) * D * G / (4.0f * mu_o);
+                                    g1 = F1 * D * G / (4.0f * mu_o);
+                                    pb = D * ch / (4.0f * c);
+                                }
+                            }
+                        }
+                        if (g0 > 0.0f || g1 > 0.0f) {
+                            const float pl = (float)((double)dist * dist / (A_emit * ce));
+                            const float wgt = pl * pl / (pl * pl + pb * pb);
+                            sw0 = wgt * g0 / pl;
+                            sw1 = wgt * g1 / pl;
+                            tgt = e;
+                            skip = __float_as_int(q4.y);
+                            start_ray(r, best, node, sp, steps, sc, ox, oy, oz, ex, ey, ez, 1.001f * dist + eps);
+                            kind = K_S0;
+                            act = A_RAY;
+                            break;
+                        }
+                    }
+                }
+                // A_MAIN: the lobe sample at x (the stage-1 sampler)
+                const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe, A);
+                float3 tb, bb;
+                onb(n.x, n.y, n.z, tb, bb);
+                float sn, cs;
+                sincospif(2.0f * u.y, &sn, &cs);
+                float3 wi;
+                W0 = 1.0f;
+                W1 = 0.0f;
+                float pb = 0.0f;
+                if (lobe == 0) {
+                    const float rr = sqrtf(u.x), lz = sqrtf(1.0f - u.x);
+                    wi = to_world(tb, bb, n, rr * cs, rr * sn, lz);
+                    pb = lz / PI_F;
+                } else {
+                    const float om = 1.0f - u.x;
+                    const float den = om + a2 * u.x;
+                    const float cos2 = om / den, sin2 = a2 * u.x / den;
+                    const float ch = sqrtf(cos2), sh = sqrtf(sin2);
+                    const float3 h = to_world(tb, bb, n, sh * cs, sh * sn, ch);
+                    const float c = wo.x * h.x + wo.y * h.y + wo.z * h.z;
+                    wi = make_float3(2.0f * c * h.x - wo.x, 2.0f * c * h.y - wo.y, 2.0f * c * h.z - wo.z);
+                    const float mu_i = n.x * wi.x + n.y * wi.y + n.z * wi.z;
+                    if (mu_i <= 0.0f || c <= 0.0f) {   // a zero sample
+                        act = A_END_SAMPLE;
+                        continue;
+                    }
+                    const float wt = smith_g1(mu_i, a2) * g1o * c / (mu_o * ch);
+                    const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
+                    W0 = (1.0f - F1) * wt;
+                    W1 = F1 * wt;
+                    pb = ggx_d(sin2, cos2, a2) * ch / (4.0f * c);
+                }
+                b0 = b1 = b2 = 1.0f;
+                l0 = l1 = l2 = 0.0f;
+                pdf_prev = pb;
+                depth = 1;
+                skip = __float_as_int(q4.y);
+                dx = wi.x; dy = wi.y; dz = wi.z;
+                start_ray(r, best, node, sp, steps, sc, ox, oy, oz, wi.x, wi.y, wi.z, FINF);
+                kind = K_PATH;
+                act = A_RAY;
+            }
+        }
+        // ---------------- inner nodes (speculative)
+        for (;;) {
+            if (node >= 0) {
+                if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                    atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                    node = FIPT_DONE;
+                    pleaf = -1;
+                    sp = 0;
+                } else {
+                    const BvhNode nd = load_node(sc.nodes, node);
+                    bool h0, h1;
+                    float t0, t1;
+                    node_test(r, nd, best.t, h0, h1, t0, t1);
+                    if (h0 && h1) {
+                        const bool first0 = t0 <= t1;
+                        if (sp < STACK_DEPTH) {
+                            stack[sp * REFINE_THREADS] = first0 ? nd.d.y : nd.d.x;
+                            ++sp;
+                        } else {
+                            atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                        }
+                        node = first0 ? nd.d.x : nd.d.y;
+                    } else if (h0) {
+                        node = nd.d.x;
+                    } else if (h1) {
+                        node = nd.d.y;
+                    } else {
+                        node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
+                    }
                 }
             }
+            if (node < 0 && node != FIPT_DONE && pleaf < 0) {   // park the first leaf found
+                pleaf = ~node;
+                node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
+            }
+            if (!__any_sync(FULL, pleaf < 0 && node >= 0)) break;
         }
-        // lobe sample at x (the stage-1 sampler)
-        const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe, A);
-        float sn, cs;
-        sincospif(2.0f * u.y, &sn, &cs);
-        float3 wi;
-        float W0 = 1.0f, W1 = 0.0f, pb = 0.0f;
-        bool valid = true;
-        if (lobe == 0) {
-            const float rr = sqrtf(u.x), lz = sqrtf(1.0f - u.x);
-            wi = to_world(tb, bb, n, rr * cs, rr * sn, lz);
-            pb = lz / PI_F;
-        } else {
-            const float om = 1.0f - u.x;
-            const float den = om + a2 * u.x;
-            const float cos2 = om / den, sin2 = a2 * u.x / den;
-            const float ch = sqrtf(cos2), sh = sqrtf(sin2);
-            const float3 h = to_world(tb, bb, n, sh * cs, sh * sn, ch);
-            const float c = wo.x * h.x + wo.y * h.y + wo.z * h.z;
-            wi = make_float3(2.0f * c * h.x - wo.x, 2.0f * c * h.y - wo.y, 2.0f * c * h.z - wo.z);
-            const float mu_i = n.x * wi.x + n.y * wi.y + n.z * wi.z;
-            if (mu_i <= 0.0f || c <= 0.0f) {
-                valid = false;
-            } else {
-                const float wt = smith_g1(mu_i, a2) * g1o * c / (mu_o * ch);
-                const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
-                W0 = (1.0f - F1) * wt;
-                W1 = F1 * wt;
-                pb = ggx_d(sin2, cos2, a2) * ch / (4.0f * c);
+        // ---------------- leaves
+        while (pleaf >= 0) {
+            const int leaf = pleaf;
+            pleaf = -1;
+            if (leaf >= sc.T || ++steps > sc.max_steps) {
+                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                node = FIPT_DONE;
+                sp = 0;
+                break;
+            }
+            const float4 p0 = __ldg(sc.tris + 3 * leaf);
+            const int orig = __float_as_int(p0.w);
+            if (orig != skip) {
+                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
+                float t;
+                bool fr;
+                if (tri_intersect(r, p0, p1, p2, t, fr) &&
+                    (t < best.t || (t == best.t && orig < best.orig))) {
+                    best.t = t;
+                    best.leaf = leaf;
+                    best.orig = orig;
+                    best.front = fr;
+                }
+            }
+            if (node < 0 && node != FIPT_DONE) {
+                pleaf = ~node;
+                node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
             }
         }
-        if (valid) {
-            float Lp[3];
-            path_radiance<REFINE_THREADS>(sc, R, n_emit, A_emit, o, wi, skip, pb, pid, (uint32_t)s,
-                                          (uint32_t)lobe, Lp, stack, status);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                c6[c] += W0 * Lp[c];
-                c6[3 + c] += W1 * Lp[c];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) acc[i] += c6[i];
-        if (PER_SAMPLE)
-            for (int i = 0; i < 6; ++i) ps[s * 6 + i] = c6[i];
     }
-    if (PER_SAMPLE)
-        for (int s = S; s < R.smax; ++s)
-            for (int i = 0; i < 6; ++i) ps[s * 6 + i] = 0.0f;
-    const float fs = (float)S;
+#undef FIPT_ADD6
+
+    if (!valid) return;
+    if (PER_SAMPLE) {
+        float* ps = per_sample + (size_t)(p * L + lobe) * R.smax * 6;
+        for (int i = S; i < R.smax; ++i)
+            for (int c = 0; c < 6; ++c) ps[i * 6 + c] = 0.0f;
+    }
+    const float fs = (float)(S > 0 ? S : 1);
     if (lobe == 0) {
-        Ld[3 * p + 0] = acc[0] / fs;
-        Ld[3 * p + 1] = acc[1] / fs;
-        Ld[3 * p + 2] = acc[2] / fs;
+        Ld[3 * p + 0] = a0 / fs;
+        Ld[3 * p + 1] = a1 / fs;
+        Ld[3 * p + 2] = a2s / fs;
     } else {
         float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
         float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
-        o0[0] = acc[0] / fs; o0[1] = acc[1] / fs; o0[2] = acc[2] / fs;
-        o1[0] = acc[3] / fs; o1[1] = acc[4] / fs; o1[2] = acc[5] / fs;
+        o0[0] = a0 / fs; o0[1] = a1 / fs; o0[2] = a2s / fs;
+        o1[0] = a3 / fs; o1[1] = a4 / fs; o1[2] = a5 / fs;
     }
 }
 
