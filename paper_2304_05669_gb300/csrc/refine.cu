@@ -23,7 +23,7 @@ namespace {
 #define FIPT_REFINE_THREADS 64
 #endif
 #ifndef FIPT_REFINE_MINB
-#define FIPT_REFINE_MINB 12
+#define FIPT_REFINE_MINB 20
 #endif
 constexpr int REFINE_THREADS = FIPT_REFINE_THREADS;
 constexpr int REFINE_MINB = FIPT_REFINE_MINB;
@@ -178,7 +178,7 @@ enum : int { K_NONE = 0, K_S0 = 1, K_PATH = 2, K_SV = 3 };
 enum : int { A_START, A_MAIN, A_VERTEX_BSDF, A_END_PATH, A_END_SAMPLE, A_RAY };
 
 #ifndef FIPT_REFINE_REFILL
-#define FIPT_REFINE_REFILL 16
+#define FIPT_REFINE_REFILL 24
 #endif
 
 __device__ __forceinline__ void start_ray(TraceRay& r, BestHit& best, int& node, int& sp, int& steps,
