@@ -244,7 +244,8 @@ fipt_status fipt_scene_set_voxel_cache(fipt_scene* scene, const float* grid, int
  * two words (top 24 bits times 2^-24), barycentrics (1 - sqrt(u1),
  * sqrt(u1) (1 - u2), sqrt(u1) u2) on the triangle's float vertices in f32.
  * x: device f32 [T * n_per_tri, 3] (triangle-major, original triangle
- * order, caller-owned).  n_per_tri in [1, 2^20] (the paper uses 100). */
+ * order, caller-owned).  n_per_tri in [1, 2^20] (the paper uses 100), T *
+ * n_per_tri < 2^39. */
 fipt_status fipt_emitter_sample_points(fipt_scene* scene, uint64_t seed, uint32_t request_id,
                                        int32_t n_per_tri, float* x, fipt_stream stream);
 /* Step 2: triangle t is an emitter when the mean of

@@ -19,12 +19,15 @@ namespace {
 
 constexpr uint32_t EMIT_LANE = 0x400u;
 
+// IDX: uint32_t when T * n < 2^32 (a 32-bit division splits the sample
+// index), int64_t otherwise.
+template <class IDX>
 __global__ void k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv,
                               int64_t T, int n, uint2 key, uint32_t rid, float* __restrict__ x) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T * n) return;
-    const int64_t t = i / n;
-    const uint32_t j = (uint32_t)(i - t * n);
+    const IDX t = (IDX)i / (IDX)n;
+    const uint32_t j = (uint32_t)((IDX)i - t * (IDX)n);
     const int leaf = inv[t];
     const float4 p0 = __ldg(tris + 3 * leaf), p1 = __ldg(tris + 3 * leaf + 1), p2 = __ldg(tris + 3 * leaf + 2);
     const uint4 w = philox4x32_10(make_uint4((uint32_t)t, j, EMIT_LANE, rid), key);
@@ -36,13 +39,35 @@ __global__ void k_emit_points(const float4* __restrict__ tris, const int32_t* __
     x[3 * i + 2] = b0 * p0.z + b1 * p1.z + b2 * p2.z;
 }
 
-__global__ void k_emit_classify(const float* __restrict__ alpha, int64_t T, int n, double thr,
-                                double* __restrict__ mean, uint8_t* __restrict__ flag) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// One thread per triangle.  When a block's CLS_THREADS rows of alpha fit in
+// shared memory, the block first copies them there with coalesced loads;
+// each thread then sums its row in order.
+constexpr int CLS_THREADS = 64;
+constexpr int CLS_MAX_N = 192;            // 64 rows x 192 floats = 48 KB
+
+__global__ void __launch_bounds__(CLS_THREADS)
+k_emit_classify(const float* __restrict__ alpha, int64_t T, int n, double thr,
+                double* __restrict__ mean, uint8_t* __restrict__ flag) {
+    __shared__ float rows[CLS_THREADS * CLS_MAX_N];
+    const int64_t t0 = (int64_t)blockIdx.x * CLS_THREADS;
+    const int64_t t = t0 + threadIdx.x;
+    const bool staged = n <= CLS_MAX_N;
+    if (staged) {
+        const int64_t rows_here = (T - t0) < CLS_THREADS ? (T - t0) : CLS_THREADS;
+        const int64_t cnt = rows_here * n;
+        const float* src = alpha + t0 * n;
+        for (int64_t k = threadIdx.x; k < cnt; k += CLS_THREADS) rows[k] = __ldg(src + k);
+        __syncthreads();
+    }
     if (t >= T) return;
-    const float* a = alpha + t * n;
     double s = 0.0;
-    for (int j = 0; j < n; ++j) s += (double)__ldg(a + j);
+    if (staged) {
+        const float* a = rows + threadIdx.x * n;
+        for (int j = 0; j < n; ++j) s += (double)a[j];
+    } else {
+        const float* a = alpha + t * n;
+        for (int j = 0; j < n; ++j) s += (double)__ldg(a + j);
+    }
     const double m = s / (double)n;
     if (mean) mean[t] = m;
     flag[t] = m > thr ? 1 : 0;
@@ -133,14 +158,18 @@ extern "C" fipt_status fipt_emitter_sample_points(fipt_scene* s, uint64_t seed, 
                                                   int32_t n_per_tri, float* x, fipt_stream stream) {
     FIPT_REQUIRE(s, "scene is NULL");
     FIPT_REQUIRE(n_per_tri >= 1 && n_per_tri <= (1 << 20), "n_per_tri must be in [1, 2^20]");
-    FIPT_REQUIRE(s->T * (int64_t)n_per_tri < ((int64_t)1 << 40), "T * n_per_tri too large");
+    FIPT_REQUIRE(s->T * (int64_t)n_per_tri < ((int64_t)1 << 39), "T * n_per_tri must be < 2^39");
     if (s->T == 0) return FIPT_OK;
     FIPT_REQUIRE(x && fipt_aligned(x, 4), "x is NULL or misaligned");
     FIPT_CUDA(cudaSetDevice(s->ctx->device));
     const int64_t n = s->T * n_per_tri;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    FIPT_LAUNCH(k_emit_points, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream), s->tris, s->inv,
-                s->T, n_per_tri, key, request_id, x);
+    if (n < ((int64_t)1 << 32))
+        FIPT_LAUNCH(k_emit_points<uint32_t>, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
+                    s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
+    else
+        FIPT_LAUNCH(k_emit_points<int64_t>, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
+                    s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
     FIPT_LAUNCHED("emitter sample points");
     return FIPT_OK;
 }
@@ -153,8 +182,8 @@ extern "C" fipt_status fipt_emitter_classify(const float* alpha, int64_t T, int3
     if (T == 0) return FIPT_OK;
     FIPT_REQUIRE(alpha && is_emitter && fipt_aligned(alpha, 4), "alpha / is_emitter NULL or misaligned");
     FIPT_REQUIRE(!mean_alpha || fipt_aligned(mean_alpha, 8), "mean_alpha misaligned");
-    FIPT_LAUNCH(k_emit_classify, blocks(T, 128), 128, 0, static_cast<cudaStream_t>(stream), alpha, T,
-                n_per_tri, (double)threshold, mean_alpha, is_emitter);
+    FIPT_LAUNCH(k_emit_classify, blocks(T, CLS_THREADS), CLS_THREADS, 0, static_cast<cudaStream_t>(stream),
+                alpha, T, n_per_tri, (double)threshold, mean_alpha, is_emitter);
     FIPT_LAUNCHED("emitter classify");
     return FIPT_OK;
 }

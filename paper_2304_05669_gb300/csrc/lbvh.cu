@@ -60,6 +60,67 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(uint32_t* __restri
     }
 }
 
+// Multi-block exclusive scan for large histograms: k_scan_reduce sums
+// chunks of SCAN_CHUNK counters, k_scan_single scans those sums, and
+// k_scan_apply scans each chunk from its scanned sum.  Thread i of a block
+// owns counters 4i .. 4i+3 of the chunk.
+constexpr int SCAN_CHUNK = 4 * SCAN_THREADS;
+
+__device__ __forceinline__ uint4 load4(const uint32_t* a, int64_t i, int64_t m) {
+    if (i + 3 < m) return *reinterpret_cast<const uint4*>(a + i);
+    return make_uint4(i < m ? a[i] : 0u, i + 1 < m ? a[i + 1] : 0u, i + 2 < m ? a[i + 2] : 0u, 0u);
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan_reduce(const uint32_t* __restrict__ a, int64_t m, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t wsum[SCAN_THREADS / 32];
+    const int64_t i = (int64_t)blockIdx.x * SCAN_CHUNK + 4 * threadIdx.x;
+    const uint4 v = load4(a, i, m);
+    uint32_t t = v.x + v.y + v.z + v.w;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t u = wsum[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = u;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan_apply(uint32_t* __restrict__ a, int64_t m, const uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t wsum[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * SCAN_CHUNK + 4 * threadIdx.x;
+    const uint4 v = load4(a, i, m);
+    const uint32_t t = v.x + v.y + v.z + v.w;
+    uint32_t incl = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t u = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += y;
+        }
+        wsum[lane] = u;
+    }
+    __syncthreads();
+    uint32_t run = bsum[blockIdx.x] + (warp > 0 ? wsum[warp - 1] : 0u) + incl - t;
+    const uint32_t e0 = run, e1 = e0 + v.x, e2 = e1 + v.y, e3 = e2 + v.z;
+    if (i + 3 < m) {
+        *reinterpret_cast<uint4*>(a + i) = make_uint4(e0, e1, e2, e3);
+    } else {
+        if (i < m) a[i] = e0;
+        if (i + 1 < m) a[i + 1] = e1;
+        if (i + 2 < m) a[i + 2] = e2;
+    }
+}
+
 // Stable scatter: an element's rank among equal digits in its tile follows
 // (iteration, warp, lane), i.e. index order.
 template <class K>
@@ -444,8 +505,29 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 }  // namespace
 
 // ---------------------------------------------------------------- sort driver
+// Histogram (RADIX x blocks, digit-major) followed, 256-byte aligned, by the
+// chunk sums of the multi-block scan.
+static int64_t hist_words(int64_t n) {
+    const int64_t m = (int64_t)RADIX * (sort_blocks(n) > 0 ? sort_blocks(n) : 1);
+    return (m + 63) & ~int64_t(63);
+}
+
 size_t radix_sort_scratch_bytes(int64_t n) {
-    return (size_t)RADIX * (size_t)(sort_blocks(n) > 0 ? sort_blocks(n) : 1) * sizeof(uint32_t);
+    const int64_t m = hist_words(n);
+    return (size_t)(m + (m + SCAN_CHUNK - 1) / SCAN_CHUNK + 64) * sizeof(uint32_t);
+}
+
+// Exclusive scan of the m = RADIX * nb histogram counters.
+static fipt_status scan_hist(uint32_t* hist, int64_t m, uint32_t* bsum, cudaStream_t st) {
+    if (m <= 4 * SCAN_CHUNK) {
+        FIPT_LAUNCH(k_scan_single, 1, SCAN_THREADS, 0, st, hist, m);
+        return FIPT_OK;
+    }
+    const int64_t nc = (m + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    FIPT_LAUNCH(k_scan_reduce, (unsigned)nc, SCAN_THREADS, 0, st, hist, m, bsum);
+    FIPT_LAUNCH(k_scan_single, 1, SCAN_THREADS, 0, st, bsum, nc);
+    FIPT_LAUNCH(k_scan_apply, (unsigned)nc, SCAN_THREADS, 0, st, hist, m, bsum);
+    return FIPT_OK;
 }
 
 template <class K>
@@ -458,7 +540,8 @@ fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
     if (n > 0) {
         for (int shift = 0; shift < bits; shift += 8) {
             FIPT_LAUNCH(k_sort_hist<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, n, shift, hist);
-            FIPT_LAUNCH(k_scan_single, 1, SCAN_THREADS, 0, st, hist, (int64_t)RADIX * nb);
+            fipt_status r = scan_hist(hist, (int64_t)RADIX * nb, hist + hist_words(n), st);
+            if (r != FIPT_OK) return r;
             FIPT_LAUNCH(k_sort_scatter<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, va, kb, vb, n, shift, hist);
             K* tk = ka; ka = kb; kb = tk;
             uint32_t* tv = va; va = vb; vb = tv;

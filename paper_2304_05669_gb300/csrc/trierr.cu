@@ -2,8 +2,9 @@
 // term leaves large error exactly where the emitters are.  Pixels are
 // grouped by their first-hit triangle with a stable radix sort, each
 // triangle's segment boundaries are marked in one pass over the sorted
-// keys, and one thread per triangle sums its pixels' squared errors in
-// pixel order (FP64), so the result is deterministic.
+// keys, and one warp per triangle sums its pixels' squared errors in FP64
+// (lane l takes pixels l, l + 32, ... of the segment in order, then a fixed
+// butterfly), so the result is deterministic.
 #include "fipt_internal.cuh"
 
 namespace {
@@ -31,11 +32,12 @@ __global__ void k_segment_sums(const uint32_t* __restrict__ pix, const int32_t* 
                                const int32_t* __restrict__ seg_end, const float* __restrict__ Lr,
                                const float* __restrict__ Lgt, int64_t T, double* __restrict__ err,
                                int32_t* __restrict__ count) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= T) return;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= T) return;                      // whole warp
     const int32_t b = seg_begin[t], e = seg_end[t];
     double s = 0.0;
-    for (int32_t j = b; j < e; ++j) {
+    for (int32_t j = b + lane; j < e; j += 32) {
         const int64_t p = pix[j];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -43,8 +45,12 @@ __global__ void k_segment_sums(const uint32_t* __restrict__ pix, const int32_t* 
             s = fma(d, d, s);
         }
     }
-    err[t] = s;
-    count[t] = e - b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        err[t] = s;
+        count[t] = e - b;
+    }
 }
 
 struct TriErrLayout {
@@ -109,7 +115,8 @@ extern "C" fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, co
         if (r != FIPT_OK) return r;
         FIPT_LAUNCH(k_mark_segments, blocks(P, 256), 256, 0, st, sk, P, T, L.seg_begin, L.seg_end);
     }
-    FIPT_LAUNCH(k_segment_sums, blocks(T, 256), 256, 0, st, sv, L.seg_begin, L.seg_end, Lr, Lgt, T, err_sum, count);
+    FIPT_LAUNCH(k_segment_sums, blocks(T * 32, 256), 256, 0, st, sv, L.seg_begin, L.seg_end, Lr, Lgt, T,
+                err_sum, count);
     FIPT_LAUNCHED("tri_error");
     return FIPT_OK;
 }
