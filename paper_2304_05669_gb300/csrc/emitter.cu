@@ -20,46 +20,65 @@ namespace {
 constexpr uint32_t EMIT_LANE = 0x400u;
 
 // IDX: uint32_t when T * n < 2^32 (a 32-bit division splits the sample
-// index), int64_t otherwise.
+// index), int64_t otherwise.  A block stages its PTS_THREADS points in
+// shared memory and writes them as float4 (the block's 12 * PTS_THREADS
+// bytes start 16-byte aligned when x is).
+constexpr int PTS_THREADS = 256;
+
 template <class IDX>
-__global__ void k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv,
-                              int64_t T, int n, uint2 key, uint32_t rid, float* __restrict__ x) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T * n) return;
-    const IDX t = (IDX)i / (IDX)n;
-    const uint32_t j = (uint32_t)((IDX)i - t * (IDX)n);
-    const int leaf = inv[t];
-    const float4 p0 = __ldg(tris + 3 * leaf), p1 = __ldg(tris + 3 * leaf + 1), p2 = __ldg(tris + 3 * leaf + 2);
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)t, j, EMIT_LANE, rid), key);
-    const float u1 = u24f(w.x), u2 = u24f(w.y);
-    const float r1 = sqrtf(u1);
-    const float b0 = 1.0f - r1, b1 = r1 * (1.0f - u2), b2 = r1 * u2;
-    x[3 * i + 0] = b0 * p0.x + b1 * p1.x + b2 * p2.x;
-    x[3 * i + 1] = b0 * p0.y + b1 * p1.y + b2 * p2.y;
-    x[3 * i + 2] = b0 * p0.z + b1 * p1.z + b2 * p2.z;
+__global__ void __launch_bounds__(PTS_THREADS)
+k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv, int64_t T, int n, uint2 key,
+              uint32_t rid, float* __restrict__ x) {
+    __shared__ float4 buf[3 * PTS_THREADS / 4];
+    float* sb = reinterpret_cast<float*>(buf);
+    const int64_t total = T * n;
+    const int64_t base = (int64_t)blockIdx.x * PTS_THREADS;
+    const int64_t i = base + threadIdx.x;
+    if (i < total) {
+        const IDX t = (IDX)i / (IDX)n;
+        const uint32_t j = (uint32_t)((IDX)i - t * (IDX)n);
+        const int leaf = inv[t];
+        const float4 p0 = __ldg(tris + 3 * leaf), p1 = __ldg(tris + 3 * leaf + 1), p2 = __ldg(tris + 3 * leaf + 2);
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)t, j, EMIT_LANE, rid), key);
+        const float u1 = u24f(w.x), u2 = u24f(w.y);
+        const float r1 = sqrtf(u1);
+        const float b0 = 1.0f - r1, b1 = r1 * (1.0f - u2), b2 = r1 * u2;
+        sb[3 * threadIdx.x + 0] = b0 * p0.x + b1 * p1.x + b2 * p2.x;
+        sb[3 * threadIdx.x + 1] = b0 * p0.y + b1 * p1.y + b2 * p2.y;
+        sb[3 * threadIdx.x + 2] = b0 * p0.z + b1 * p1.z + b2 * p2.z;
+    }
+    __syncthreads();
+    const int64_t here = total - base < PTS_THREADS ? total - base : PTS_THREADS;
+    if (here == PTS_THREADS && (reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        float4* dst = reinterpret_cast<float4*>(x + 3 * base);
+        if (threadIdx.x < 3 * PTS_THREADS / 4) dst[threadIdx.x] = buf[threadIdx.x];
+    } else {
+        for (int k = threadIdx.x; k < 3 * here; k += PTS_THREADS) x[3 * base + k] = sb[k];
+    }
 }
 
-// One thread per triangle.  When a block's CLS_THREADS rows of alpha fit in
-// shared memory, the block first copies them there with coalesced loads;
-// each thread then sums its row in order.
-constexpr int CLS_THREADS = 64;
+// One thread per triangle sums its row of alpha in order.  When the block's
+// CLS_ROWS rows fit in shared memory, all CLS_THREADS threads first copy
+// them there with coalesced loads.
+constexpr int CLS_THREADS = 256;
+constexpr int CLS_ROWS = 64;
 constexpr int CLS_MAX_N = 192;            // 64 rows x 192 floats = 48 KB
 
 __global__ void __launch_bounds__(CLS_THREADS)
 k_emit_classify(const float* __restrict__ alpha, int64_t T, int n, double thr,
                 double* __restrict__ mean, uint8_t* __restrict__ flag) {
-    __shared__ float rows[CLS_THREADS * CLS_MAX_N];
-    const int64_t t0 = (int64_t)blockIdx.x * CLS_THREADS;
-    const int64_t t = t0 + threadIdx.x;
+    extern __shared__ float rows[];
+    const int64_t t0 = (int64_t)blockIdx.x * CLS_ROWS;
     const bool staged = n <= CLS_MAX_N;
     if (staged) {
-        const int64_t rows_here = (T - t0) < CLS_THREADS ? (T - t0) : CLS_THREADS;
+        const int64_t rows_here = (T - t0) < CLS_ROWS ? (T - t0) : CLS_ROWS;
         const int64_t cnt = rows_here * n;
         const float* src = alpha + t0 * n;
         for (int64_t k = threadIdx.x; k < cnt; k += CLS_THREADS) rows[k] = __ldg(src + k);
         __syncthreads();
     }
-    if (t >= T) return;
+    const int64_t t = t0 + threadIdx.x;
+    if (threadIdx.x >= CLS_ROWS || t >= T) return;
     double s = 0.0;
     if (staged) {
         const float* a = rows + threadIdx.x * n;
@@ -165,11 +184,11 @@ extern "C" fipt_status fipt_emitter_sample_points(fipt_scene* s, uint64_t seed, 
     const int64_t n = s->T * n_per_tri;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     if (n < ((int64_t)1 << 32))
-        FIPT_LAUNCH(k_emit_points<uint32_t>, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
-                    s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
+        FIPT_LAUNCH(k_emit_points<uint32_t>, blocks(n, PTS_THREADS), PTS_THREADS, 0,
+                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
     else
-        FIPT_LAUNCH(k_emit_points<int64_t>, blocks(n, 256), 256, 0, static_cast<cudaStream_t>(stream),
-                    s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
+        FIPT_LAUNCH(k_emit_points<int64_t>, blocks(n, PTS_THREADS), PTS_THREADS, 0,
+                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
     FIPT_LAUNCHED("emitter sample points");
     return FIPT_OK;
 }
@@ -182,7 +201,8 @@ extern "C" fipt_status fipt_emitter_classify(const float* alpha, int64_t T, int3
     if (T == 0) return FIPT_OK;
     FIPT_REQUIRE(alpha && is_emitter && fipt_aligned(alpha, 4), "alpha / is_emitter NULL or misaligned");
     FIPT_REQUIRE(!mean_alpha || fipt_aligned(mean_alpha, 8), "mean_alpha misaligned");
-    FIPT_LAUNCH(k_emit_classify, blocks(T, CLS_THREADS), CLS_THREADS, 0, static_cast<cudaStream_t>(stream),
+    const size_t smem = n_per_tri <= CLS_MAX_N ? sizeof(float) * CLS_ROWS * (size_t)n_per_tri : 0;
+    FIPT_LAUNCH(k_emit_classify, blocks(T, CLS_ROWS), CLS_THREADS, smem, static_cast<cudaStream_t>(stream),
                 alpha, T, n_per_tri, (double)threshold, mean_alpha, is_emitter);
     FIPT_LAUNCHED("emitter classify");
     return FIPT_OK;

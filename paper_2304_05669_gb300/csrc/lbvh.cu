@@ -353,71 +353,73 @@ __global__ void k_inverse(const int32_t* __restrict__ order, int64_t T, int32_t*
 
 // Emitter table for area sampling: emitter triangles (L_e > 0 in some
 // channel) in original index order, their leaf, and cumulative areas in
-// FP64 (areas from the packed float vertices in double), built by one block
-// scanning T in chunks.
+// FP64 (areas from the packed float vertices in double).  k_emit_mark
+// writes a 0/1 mark per triangle, an exclusive scan of the marks gives each
+// emitter its position, k_emit_place writes leaf and area there, and one
+// block turns the areas into the cumulative table and sets n_emit, A_emit.
+__device__ __forceinline__ bool leaf_emits(const float4* shade, int leaf) {
+    const float4 le = shade[2 * leaf];
+    return le.x > 0.0f || le.y > 0.0f || le.z > 0.0f;
+}
+
+__global__ void k_emit_mark(const float4* __restrict__ shade, const int32_t* __restrict__ inv, int64_t T,
+                            uint32_t* __restrict__ mark) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < T) mark[t] = leaf_emits(shade, inv[t]) ? 1u : 0u;
+}
+
+__global__ void k_emit_place(const float4* __restrict__ tris, const float4* __restrict__ shade,
+                             const int32_t* __restrict__ inv, int64_t T, const uint32_t* __restrict__ pos,
+                             int32_t* __restrict__ emit_leaf, double* __restrict__ emit_area) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int leaf = inv[t];
+    if (!leaf_emits(shade, leaf)) return;
+    const float4 p0 = tris[3 * leaf], p1 = tris[3 * leaf + 1], p2 = tris[3 * leaf + 2];
+    const double e1[3] = {(double)p1.x - (double)p0.x, (double)p1.y - (double)p0.y, (double)p1.z - (double)p0.z};
+    const double e2[3] = {(double)p2.x - (double)p0.x, (double)p2.y - (double)p0.y, (double)p2.z - (double)p0.z};
+    const double cx = e1[1] * e2[2] - e1[2] * e2[1];
+    const double cy = e1[2] * e2[0] - e1[0] * e2[2];
+    const double cz = e1[0] * e2[1] - e1[1] * e2[0];
+    emit_leaf[pos[t]] = leaf;
+    emit_area[pos[t]] = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+}
+
+// In-place inclusive FP64 scan of the n_emit areas (n_emit = last position
+// + last mark), one block walking them in chunks of 1024.
 __global__ void __launch_bounds__(1024)
-k_emitters(const float4* __restrict__ tris, const float4* __restrict__ shade, int64_t T,
-           const int32_t* __restrict__ inv, int32_t* __restrict__ emit_leaf,
-           double* __restrict__ emit_cdf, SceneConst* c) {
-    __shared__ int wcnt[32];
-    __shared__ double warea[32];
-    int carry = 0;
-    double carry_area = 0.0;
+k_emit_cdf(const uint32_t* __restrict__ pos, const float4* __restrict__ shade, const int32_t* __restrict__ inv,
+           int64_t T, double* __restrict__ cdf, SceneConst* c) {
+    __shared__ double wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t base = 0; base < T; base += 1024) {
-        const int64_t t = base + threadIdx.x;
-        int flag = 0;
-        double area = 0.0;
-        const int leaf = t < T ? inv[t] : 0;
-        const float4 le = t < T ? shade[2 * leaf] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (le.x > 0.0f || le.y > 0.0f || le.z > 0.0f) {
-            flag = 1;
-            const float4 p0 = tris[3 * leaf], p1 = tris[3 * leaf + 1], p2 = tris[3 * leaf + 2];
-            const double e1[3] = {(double)p1.x - (double)p0.x, (double)p1.y - (double)p0.y,
-                                  (double)p1.z - (double)p0.z};
-            const double e2[3] = {(double)p2.x - (double)p0.x, (double)p2.y - (double)p0.y,
-                                  (double)p2.z - (double)p0.z};
-            const double cx = e1[1] * e2[2] - e1[2] * e2[1];
-            const double cy = e1[2] * e2[0] - e1[0] * e2[2];
-            const double cz = e1[0] * e2[1] - e1[1] * e2[0];
-            area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
-        }
-        // inclusive warp scans of the flags and areas
-        int ic = flag;
-        double ia = area;
+    const int64_t n = (int64_t)pos[T - 1] + (leaf_emits(shade, inv[T - 1]) ? 1 : 0);
+    double carry = 0.0;
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t k = base + threadIdx.x;
+        const double a = k < n ? cdf[k] : 0.0;
+        double v = a;
         for (int o = 1; o < 32; o <<= 1) {
-            const int yc = __shfl_up_sync(0xffffffffu, ic, o);
-            const double ya = __shfl_up_sync(0xffffffffu, ia, o);
-            if (lane >= o) { ic += yc; ia += ya; }
+            const double y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
-        if (lane == 31) { wcnt[warp] = ic; warea[warp] = ia; }
+        if (lane == 31) wsum[warp] = v;
         __syncthreads();
         if (warp == 0) {
-            int sc = wcnt[lane];
-            double sa = warea[lane];
+            double u = wsum[lane];
             for (int o = 1; o < 32; o <<= 1) {
-                const int yc = __shfl_up_sync(0xffffffffu, sc, o);
-                const double ya = __shfl_up_sync(0xffffffffu, sa, o);
-                if (lane >= o) { sc += yc; sa += ya; }
+                const double y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
             }
-            wcnt[lane] = sc;
-            warea[lane] = sa;
+            wsum[lane] = u;
         }
         __syncthreads();
-        const int before = warp > 0 ? wcnt[warp - 1] : 0;
-        const double before_a = warp > 0 ? warea[warp - 1] : 0.0;
-        if (flag) {
-            const int pos = carry + before + ic - 1;
-            emit_leaf[pos] = leaf;
-            emit_cdf[pos] = carry_area + before_a + ia;
-        }
-        carry += wcnt[31];
-        carry_area += warea[31];
+        if (k < n) cdf[k] = carry + (warp > 0 ? wsum[warp - 1] : 0.0) + v;
+        carry += wsum[31];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        c->n_emit = carry;
-        c->A_emit = carry_area;
+        c->n_emit = (int)n;
+        c->A_emit = carry;
     }
 }
 
@@ -562,8 +564,14 @@ template fipt_status radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*,
 
 fipt_status rebuild_emitter_table(fipt_scene* s, cudaStream_t st) {
     if (s->T == 0) return FIPT_OK;
-    FIPT_LAUNCH(k_emitters, 1, 1024, 0, st, s->tris, s->shade, s->T, s->inv, s->emit_leaf, s->emit_cdf,
-                s->cst);
+    const int64_t T = s->T;
+    // the sort scratch (values, histogram) is free once the tree is built
+    FIPT_LAUNCH(k_emit_mark, grid_for(T, 256), 256, 0, st, s->shade, s->inv, T, s->vals);
+    fipt_status r = scan_hist(s->vals, T, s->hist, st);
+    if (r != FIPT_OK) return r;
+    FIPT_LAUNCH(k_emit_place, grid_for(T, 256), 256, 0, st, s->tris, s->shade, s->inv, T, s->vals,
+                s->emit_leaf, s->emit_cdf);
+    FIPT_LAUNCH(k_emit_cdf, 1, 1024, 0, st, s->vals, s->shade, s->inv, T, s->emit_cdf, s->cst);
     FIPT_LAUNCHED("emitter table");
     return FIPT_OK;
 }
