@@ -46,10 +46,15 @@ WORKLOADS = {
     "room": dict(scene="room", views=24, W=320, H=208, N=1 << 20, spp_d=128, spp_s=128,
                  desc="procedural room 175,926 tris; 24 views 320x208; first 2^20 hits; "
                       "128 spp; 6-level roughness grid"),
-    "cornell": dict(scene="cornell", views=4, W=64, H=64, N=4096, spp_d=64, spp_s=64,
-                    desc="Cornell box 36 tris; 4096 first hits; 64 spp"),
+    "cornell": dict(scene="cornell", views=4, W=64, H=64, N=4096, spp_d=64, spp_s=64, surface=True,
+                    desc="Cornell box 36 tris; 4096 points uniform on surfaces (seed 0); 64 spp"),
     "floor": dict(scene="floor", views=16, W=512, H=512, N=1 << 22, spp_d=256, spp_s=256,
                   desc="building floor 2,045,464 tris; 16 views 512x512; 2^22 hits; 256 spp"),
+    # the differentiation config: factorized render forward (+ loss) and
+    # backward over 24 views at 640x416 with synthetic shading tables
+    "render": dict(scene=None, views=24, W=640, H=416, N=24 * 640 * 416, spp_d=0, spp_s=0,
+                   desc="factorized render fwd+bwd, 24 views 640x416 = 6,389,760 pixels, "
+                        "6-level roughness grid, synthetic tables"),
 }
 
 
@@ -84,7 +89,7 @@ def make_scene(name):
     if name == "room":
         return procedural_room(1)
     if name == "cornell":
-        return cornell_box(closed=True)
+        return cornell_box()            # open front, as the 36-triangle config states
     return building_floor(5)
 
 
@@ -203,17 +208,24 @@ def max_over_ranks(x, world, device):
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_sample(mesh, cams, W, H, npts, spp_d, spp_s, request_id=0):
+def oracle_sample(mesh, cams, W, H, npts, spp_d, spp_s, request_id=0, surface=False):
     """Oracle first hits of the first pixels (view-major order), then the
-    oracle bake of the first ``npts`` valid points.
+    oracle bake of the first ``npts`` valid points (surface workloads:
+    ``npts`` seeded surface points of the same distribution).
     Returns (rays, seconds, threads, points)."""
     import oracle as O
     S = O.OracleScene.from_mesh(mesh)
-    pix = np.arange(min(len(cams) * W * H, int(npts * 1.5) + 64))
-    cq = S.camera_queries(cams, W, H, pix)
-    ok = np.nonzero(cq["tri"] >= 0)[0][:npts]
-    q = {"x": cq["x"][ok].astype(np.float32), "n": cq["n"][ok].astype(np.float32),
-         "wo": cq["wo"][ok].astype(np.float32), "tri": cq["tri"][ok].astype(np.int32)}
+    if surface:
+        from workloads import surface_queries
+        sq = surface_queries(mesh, npts, seed=0)
+        q = {k: sq[k] for k in ("x", "n", "wo", "tri")}
+        ok = np.arange(npts)
+    else:
+        pix = np.arange(min(len(cams) * W * H, int(npts * 1.5) + 64))
+        cq = S.camera_queries(cams, W, H, pix)
+        ok = np.nonzero(cq["tri"] >= 0)[0][:npts]
+        q = {"x": cq["x"][ok].astype(np.float32), "n": cq["n"][ok].astype(np.float32),
+             "wo": cq["wo"][ok].astype(np.float32), "tri": cq["tri"][ok].astype(np.int32)}
     threads = O.default_threads()
     t0 = time.perf_counter()
     S.bake(q, SIGMA, spp_d, spp_s, seed=0, request_id=request_id, nthreads=threads)
@@ -222,23 +234,61 @@ def oracle_sample(mesh, cams, W, H, npts, spp_d, spp_s, request_id=0):
     return rays, dt, threads, len(ok)
 
 
+def run_reference_render(args, wl):
+    """The oracle's render forward + loss + analytic gradient on a bounded
+    sample of the render workload's pixels."""
+    import oracle as O
+    from workloads import material_params, shading_tables
+    n = 1 << 18
+    Ld, Ls0, Ls1 = shading_tables(n, K=len(SIGMA), seed=7)
+    mp, gt = material_params(n, seed=3), material_params(n, seed=4)
+    Lgt = O.render_forward(Ld, Ls0, Ls1, SIGMA, gt["albedo"], gt["rough"], gt["metal"])[0]
+
+    def one():
+        O.render_forward(Ld, Ls0, Ls1, SIGMA, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+        O.render_grad(Ld, Ls0, Ls1, SIGMA, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt / 1e6
+    sample = "first %d pixels per step, forward + loss + analytic gradient, numpy FP64" % n
+    print(json.dumps({
+        "impl": "reference", "metric": "factorized render fwd+bwd pixels/s", "value": round(v, 4),
+        "unit": "Mpixels/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"], "sample": sample},
+        "cpu_baseline": {"value": round(v, 4), "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def run_reference(args, wl, world, rank):
     if rank != 0:
+        return
+    if wl["scene"] is None:
+        run_reference_render(args, wl)
         return
     mesh = make_scene(wl["scene"])
     from workloads import pinhole_views
     cams = pinhole_views(mesh, wl["views"], seed=2)
     npts = max(64, min(args.cpu_points, 2048))
     for _ in range(args.warmup):
-        oracle_sample(mesh, cams, wl["W"], wl["H"], 64, wl["spp_d"], wl["spp_s"])
+        oracle_sample(mesh, cams, wl["W"], wl["H"], 64, wl["spp_d"], wl["spp_s"],
+                      surface=wl.get("surface", False))
     tot_rays, tot_t, threads, n = 0, 0.0, 1, 0
     for s in range(args.steps):
         r, dt, threads, n = oracle_sample(mesh, cams, wl["W"], wl["H"], npts, wl["spp_d"],
-                                          wl["spp_s"], request_id=s)
+                                          wl["spp_s"], request_id=s, surface=wl.get("surface", False))
         tot_rays += r
         tot_t += dt
     v = tot_rays / tot_t / 1e6
-    sample = "%d oracle first hits (first pixels of view 0) per step, %d+6x%d spp, FP64" % (n, wl["spp_d"], wl["spp_s"])
+    sample = "%d oracle query points (%s) per step, %d+6x%d spp, FP64" % (
+        n, "surface points" if wl.get("surface") else "first hits of view 0", wl["spp_d"], wl["spp_s"])
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mrays/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -249,6 +299,121 @@ def run_reference(args, wl, world, rank):
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- render workload
+RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12 + 12) + (12 + 72 + 72 + 12 + 4 + 4 + 12 + 20)
+
+
+def run_render(args, wl, world, rank, local):
+    """Factorized render fwd (Eq. 5, 8, with the Eq. 14 loss) and backward
+    over the pixels of 24 640x416 views.  value = pixels / step time."""
+    import torch
+    import paper_2304_05669_gb300 as F
+    from paper_2304_05669_gb300._native import lib
+    from workloads import material_params, shading_tables
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = wl["N"]
+    Ld, Ls0, Ls1 = shading_tables(N, K=len(SIGMA), seed=7 + rank)
+    mp, gt = material_params(N, seed=3), material_params(N, seed=4)
+    host = {"Ld": Ld, "Ls0": Ls0, "Ls1": Ls1, "albedo": mp["albedo"], "rough": mp["rough"],
+            "metal": mp["metal"]}
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    d = {k: v.to(dev) for k, v in pinned.items()}
+    gtd = {k: torch.from_numpy(v).to(dev) for k, v in gt.items()}
+    Lgt = F.render_fwd(d["Ld"], d["Ls0"], d["Ls1"], SIGMA, gtd["albedo"], gtd["rough"], gtd["metal"])[0]
+    Lgt_host = Lgt.cpu().pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def step(x, lg):
+        Lr, loss = F.render_fwd(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"], x["metal"], lg)
+        g = F.render_bwd(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"], x["metal"], lg)
+        return loss, g
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(d, Lgt)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    launches0 = lib().fipt_launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            step(d, Lgt)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = lib().fipt_launch_count() - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = max_over_ranks(sum(ms) / 1e3, world, dev)
+    F.context().sync_status()
+    # e2e: tables, parameters and targets copied in, loss and gradients copied out
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values()) + Lgt_host.numel() * 4
+        out_host = None
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d2h = 0
+        for s in range(args.steps):
+            x = {k: v.to(dev, non_blocking=True) for k, v in pinned.items()}
+            lg = Lgt_host.to(dev, non_blocking=True)
+            loss, g = step(x, lg)
+            res = [loss, g[0], g[1], g[2]]
+            if out_host is None:
+                out_host = [torch.empty(r.shape, dtype=r.dtype, pin_memory=True) for r in res]
+            for h, r in zip(out_host, res):
+                h.copy_(r, non_blocking=True)
+            d2h = sum(r.numel() * r.element_size() for r in res)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+        e2e = {"value": round(world * N * args.steps / t_e2e / 1e6, 3), "unit": "Mpixels/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        n = 1 << 20
+        sl = slice(0, n)
+        t0 = time.perf_counter()
+        O.render_forward(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, mp["albedo"][sl], mp["rough"][sl], mp["metal"][sl],
+                         Lgt_host.numpy()[sl])
+        O.render_grad(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, mp["albedo"][sl], mp["rough"][sl], mp["metal"][sl],
+                      Lgt_host.numpy()[sl])
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(n / dt / 1e6, 4), "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d pixels, forward + loss + analytic gradient, numpy FP64, %.1f s" % (n, dt)}
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peaks()
+    step_s = t_total / args.steps
+    achieved = RENDER_BYTES_PER_PX * N / step_s / 1e9
+    print(json.dumps({
+        "metric": "factorized render fwd+bwd pixels/s", "value": round(world * N * args.steps / t_total / 1e6, 3),
+        "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * step_s, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["desc"], "pixels": N, "roughness_levels": len(SIGMA),
+                   "l2": "flushed between steps (512 MB write outside the timed events)"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_render_fwd + k_render_bwd", "peak_kind": peak_kind,
+                     "alg_bytes_per_pixel": RENDER_BYTES_PER_PX},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }))
 
 
@@ -559,6 +724,14 @@ def run_ours(args, wl, world, rank, local):
     rays_per_step = N * (spp_d + K * spp_s)
 
     host = {"V": mesh.V, "F": mesh.F, "Le": mesh.Le, "cache": mesh.cache, "cams": cams}
+    surface = wl.get("surface", False)
+    if surface:          # query records of points drawn uniformly on the surfaces
+        from workloads import surface_queries
+        sq = surface_queries(mesh, N, seed=0)
+        rec = np.zeros((N, 10), np.float32)
+        rec[:, 0:3], rec[:, 3:6], rec[:, 6:9] = sq["x"], sq["n"], sq["wo"]
+        rec[:, 9] = sq["tri"].astype(np.int32).view(np.float32)
+        host["q"] = rec
     mp = material_params(N, seed=3)
     gt = material_params(N, seed=4)
     host.update({"albedo": mp["albedo"], "rough": mp["rough"], "metal": mp["metal"]})
@@ -571,8 +744,11 @@ def run_ours(args, wl, world, rank, local):
 
     def step(d, Lgt, ev=None):
         sc = F.Scene(d["V"], d["F"], d["Le"], d["cache"], ctx=ctx)
-        qa, valid = sc.camera_queries(d["cams"], W, H)
-        q, _pix, _n = F.compact_queries(qa, valid, N)
+        if surface:
+            q = d["q"]
+        else:
+            qa, valid = sc.camera_queries(d["cams"], W, H)
+            q, _pix, _n = F.compact_queries(qa, valid, N)
         if ev is not None:
             ev[0].record(stream)
         Ld, Ls0, Ls1 = F.bake(sc, q, SIGMA, spp_d, spp_s, seed=0, request_id=request_id)
@@ -589,7 +765,7 @@ def run_ours(args, wl, world, rank, local):
     # a second set of material parameters (computed once, an input)
     sc0, tabs0, q0 = step(dv, None)
     Lgt = F.render_fwd(*tabs0, SIGMA, gt_d["albedo"], gt_d["rough"], gt_d["metal"])[0].clone()
-    n_valid = int(F.compact_queries(*sc0.camera_queries(dv["cams"], W, H), N)[2].item())
+    n_valid = N if surface else int(F.compact_queries(*sc0.camera_queries(dv["cams"], W, H), N)[2].item())
     ctx.sync_status()
     if n_valid < N:
         raise RuntimeError("workload has only %d hits < %d" % (n_valid, N))
@@ -632,7 +808,7 @@ def run_ours(args, wl, world, rank, local):
     e2e = None
     if not args.no_e2e:
         out_host = None
-        in_keys = ["V", "F", "Le", "cache", "cams", "albedo", "rough", "metal"]
+        in_keys = ["V", "F", "Le", "cache", "cams", "albedo", "rough", "metal"] + (["q"] if surface else [])
         Lgt_host = Lgt.cpu().pin_memory()
         h2d = sum(pinned[k].numel() * pinned[k].element_size() for k in in_keys) \
             + Lgt_host.numel() * 4
@@ -673,11 +849,12 @@ def run_ours(args, wl, world, rank, local):
     # -------------------------------------------------- CPU baseline (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, dt, threads, n = oracle_sample(mesh, cams, W, H, args.cpu_points, spp_d, spp_s)
+        r, dt, threads, n = oracle_sample(mesh, cams, W, H, min(args.cpu_points, N), spp_d, spp_s,
+                                          surface=surface)
         cpu = {"value": round(r / dt / 1e6, 4), "unit": "Mrays/s", "cores": threads,
                "kind": "oracle",
-               "sample": "%d oracle first hits (first pixels of view 0), %d+6x%d spp, FP64, %.1f s" %
-                         (n, spp_d, spp_s, dt)}
+               "sample": "%d oracle query points (%s), %d+6x%d spp, FP64, %.1f s" %
+                         (n, "surface points" if surface else "first hits of view 0", spp_d, spp_s, dt)}
 
     refine = None
     if rank == 0 and world == 1 and args.refine_points > 0:
@@ -742,6 +919,8 @@ def main():
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
+    elif args.workload == "render":
+        run_render(args, wl, world, rank, local)
     else:
         run_ours(args, wl, world, rank, local)
     if world > 1:
