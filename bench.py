@@ -883,8 +883,9 @@ def run_ours(args, wl, world, rank, local):
                    "rays_per_step": rays_per_step, "views": wl["views"], "resolution": [W, H],
                    "l2": "flushed between steps (512 MB write outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "step": "scene build + first hits + compaction + bake + render fwd/bwd + "
-                           "per-triangle error"},
+                   "step": ("scene build + bake + render fwd/bwd + per-triangle error" if surface else
+                            "scene build + first hits + compaction + bake + render fwd/bwd + "
+                            "per-triangle error")},
         "points_per_s": round(world * N * args.steps / t_total, 1),
         "bake_ms": round(1e3 * bake_s, 3),
         "bake_mrays_per_s": round(rays_per_step / bake_s / 1e6, 3),
