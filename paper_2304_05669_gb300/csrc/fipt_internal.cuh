@@ -439,3 +439,90 @@ __device__ __forceinline__ void closest_hit(const SceneView& sc, const TraceRay&
     }
 }
 
+// Counters of an instrumented walk: node visits, triangle tests, deepest
+// stack.
+struct WalkStats {
+    unsigned long long nodes = 0, tris = 0;
+    int max_sp = 0;
+};
+
+// One round of a warp's speculative walk (Aila and Laine 2009).  Every lane
+// descends inner nodes; a lane that reaches a leaf parks it (pleaf) and,
+// with SPECULATE, keeps descending until every lane holds a leaf or is
+// done; the parked leaves, and leaves that follow them on the stack, are
+// then tested.  A lane whose walk is over has node == FIPT_DONE and
+// pleaf < 0; lanes without a ray call with that state and just vote.  All
+// 32 lanes of the warp must call it together.  `stack` is the lane's
+// column of the shared stack (entry k at stack[k * STRIDE]).
+template <int STRIDE, bool STATS, bool SPECULATE>
+__device__ __forceinline__ void warp_walk(const SceneView& sc, const TraceRay& r, int skip, BestHit& best,
+                                          int& node, int& pleaf, int& sp, int& steps, int* stack,
+                                          int32_t* status, WalkStats& ws) {
+    for (;;) {
+        if (node >= 0 && (SPECULATE || pleaf < 0)) {
+            if (node >= sc.n_inner || ++steps > sc.max_steps) {
+                atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+                node = FIPT_DONE;
+                pleaf = -1;
+                sp = 0;
+            } else {
+                const BvhNode n = load_node(sc.nodes, node);
+                if (STATS) ++ws.nodes;
+                bool h0, h1;
+                float t0, t1;
+                node_test(r, n, best.t, h0, h1, t0, t1);
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    if (sp < STACK_DEPTH) {
+                        stack[sp * STRIDE] = first0 ? n.d.y : n.d.x;
+                        ++sp;
+                        if (STATS) ws.max_sp = max(ws.max_sp, sp);
+                    } else {
+                        atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
+                    }
+                    node = first0 ? n.d.x : n.d.y;
+                } else if (h0) {
+                    node = n.d.x;
+                } else if (h1) {
+                    node = n.d.y;
+                } else {
+                    node = sp > 0 ? stack[--sp * STRIDE] : FIPT_DONE;
+                }
+            }
+        }
+        if (node < 0 && node != FIPT_DONE && pleaf < 0) {   // park the first leaf found
+            pleaf = ~node;
+            node = sp > 0 ? stack[--sp * STRIDE] : FIPT_DONE;
+        }
+        if (!__any_sync(0xffffffffu, pleaf < 0 && node >= 0)) break;   // every lane has a leaf or is done
+    }
+    while (pleaf >= 0) {
+        const int leaf = pleaf;
+        pleaf = -1;
+        if (leaf >= sc.T || ++steps > sc.max_steps) {
+            atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
+            node = FIPT_DONE;
+            sp = 0;
+            break;
+        }
+        const float4 p0 = __ldg(sc.tris + 3 * leaf);
+        const int orig = __float_as_int(p0.w);
+        if (orig != skip) {
+            if (STATS) ++ws.tris;
+            const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
+            float t;
+            bool fr;
+            if (tri_intersect(r, p0, p1, p2, t, fr) && (t < best.t || (t == best.t && orig < best.orig))) {
+                best.t = t;
+                best.leaf = leaf;
+                best.orig = orig;
+                best.front = fr;
+            }
+        }
+        if (node < 0 && node != FIPT_DONE) {      // the next entry is a leaf too
+            pleaf = ~node;
+            node = sp > 0 ? stack[--sp * STRIDE] : FIPT_DONE;
+        }
+    }
+}
+

@@ -252,6 +252,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
     best.front = false;
     r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
     int node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
+    WalkStats ws;
 
 #define FIPT_ADD6(cv, av, v)       \
     do {                           \
@@ -517,72 +518,8 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                 act = A_RAY;
             }
         }
-        // ---------------- inner nodes (speculative)
-        for (;;) {
-            if (node >= 0) {
-                if (node >= sc.n_inner || ++steps > sc.max_steps) {
-                    atomicOr(status, node >= sc.n_inner ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
-                    node = FIPT_DONE;
-                    pleaf = -1;
-                    sp = 0;
-                } else {
-                    const BvhNode nd = load_node(sc.nodes, node);
-                    bool h0, h1;
-                    float t0, t1;
-                    node_test(r, nd, best.t, h0, h1, t0, t1);
-                    if (h0 && h1) {
-                        const bool first0 = t0 <= t1;
-                        if (sp < STACK_DEPTH) {
-                            stack[sp * REFINE_THREADS] = first0 ? nd.d.y : nd.d.x;
-                            ++sp;
-                        } else {
-                            atomicOr(status, FIPT_DEV_STACK_OVERFLOW);
-                        }
-                        node = first0 ? nd.d.x : nd.d.y;
-                    } else if (h0) {
-                        node = nd.d.x;
-                    } else if (h1) {
-                        node = nd.d.y;
-                    } else {
-                        node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
-                    }
-                }
-            }
-            if (node < 0 && node != FIPT_DONE && pleaf < 0) {   // park the first leaf found
-                pleaf = ~node;
-                node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
-            }
-            if (!__any_sync(FULL, pleaf < 0 && node >= 0)) break;
-        }
-        // ---------------- leaves
-        while (pleaf >= 0) {
-            const int leaf = pleaf;
-            pleaf = -1;
-            if (leaf >= sc.T || ++steps > sc.max_steps) {
-                atomicOr(status, leaf >= sc.T ? FIPT_DEV_BAD_NODE : FIPT_DEV_STEP_LIMIT);
-                node = FIPT_DONE;
-                sp = 0;
-                break;
-            }
-            const float4 p0 = __ldg(sc.tris + 3 * leaf);
-            const int orig = __float_as_int(p0.w);
-            if (orig != skip) {
-                const float4 p1 = __ldg(sc.tris + 3 * leaf + 1), p2 = __ldg(sc.tris + 3 * leaf + 2);
-                float t;
-                bool fr;
-                if (tri_intersect(r, p0, p1, p2, t, fr) &&
-                    (t < best.t || (t == best.t && orig < best.orig))) {
-                    best.t = t;
-                    best.leaf = leaf;
-                    best.orig = orig;
-                    best.front = fr;
-                }
-            }
-            if (node < 0 && node != FIPT_DONE) {
-                pleaf = ~node;
-                node = sp > 0 ? stack[--sp * REFINE_THREADS] : FIPT_DONE;
-            }
-        }
+        // ---------------- inner nodes (speculative), then leaves
+        warp_walk<REFINE_THREADS, false, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
     }
 #undef FIPT_ADD6
 

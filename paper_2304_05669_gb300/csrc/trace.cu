@@ -333,6 +333,9 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
             }
         }
         // ---------------- inner nodes (speculative)
+        // (the same walk as warp_walk in fipt_internal.cuh, written out here:
+        // calling warp_walk from this kernel changes its register allocation
+        // and measured 3.8 % slower, with bit-identical results)
         for (;;) {
             if (node >= 0 && (FIPT_BAKE_SPECULATE || pleaf < 0)) {
                 if (node >= sc.n_inner || ++steps > sc.max_steps) {
