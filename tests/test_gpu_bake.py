@@ -6,7 +6,7 @@ import torch
 
 import oracle as O
 from parity import ETA_BAKE, bake_flat, check_bake
-from workloads import cornell_box, procedural_room, surface_queries
+from workloads import building_floor, cornell_box, procedural_room, surface_queries
 
 pytestmark = pytest.mark.gpu
 
@@ -69,6 +69,31 @@ def test_room_full_size_sampled(fipt):
     for j, i in enumerate(idx):
         one = {k: v[i:i + 1] for k, v in q.items()}
         r = S.bake(one, SIGMA, 128, 128, seed=5, point_base=int(i), eta=ETA_BAKE)
+        flat[j], lo[j], hi[j], namb[j] = r["flat"][0], r["lo"][0], r["hi"][0], r["n_amb"][0]
+    print(check_bake(g[idx], {"flat": flat, "lo": lo, "hi": hi, "n_amb": namb}))
+
+
+def test_floor_full_size_sampled(fipt):
+    """The 2,045,464-triangle building floor at 2^22 points and 256 spp in one
+    launch (the large-scene configuration); the oracle recomputes a sample
+    of points one by one with their global Philox indices."""
+    m = building_floor(5)
+    N = 1 << 22
+    q = surface_queries(m, N, seed=23)
+    sc = fipt.Scene.from_mesh(m)
+    g = gpu_bake(fipt, sc, q, 256, 256, seed=9)
+    assert np.all(np.isfinite(g))
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(N, 40, replace=False))
+    idx[0], idx[-1] = 0, N - 1
+    flat = np.zeros((len(idx), 3 + 6 * len(SIGMA)))
+    lo = np.zeros_like(flat)
+    hi = np.zeros_like(flat)
+    namb = np.zeros(len(idx), np.int64)
+    S = O.OracleScene.from_mesh(m)
+    for j, i in enumerate(idx):
+        one = {k: v[i:i + 1] for k, v in q.items()}
+        r = S.bake(one, SIGMA, 256, 256, seed=9, point_base=int(i), eta=ETA_BAKE)
         flat[j], lo[j], hi[j], namb[j] = r["flat"][0], r["lo"][0], r["hi"][0], r["n_amb"][0]
     print(check_bake(g[idx], {"flat": flat, "lo": lo, "hi": hi, "n_amb": namb}))
 

@@ -53,6 +53,23 @@ def test_render_forward_and_loss(fipt, N):
     assert abs(loss.item() - loss_o) <= REL * abs(loss_o)
 
 
+def test_render_full_size(fipt):
+    """Forward, loss and backward over all 6,389,760 pixels of the
+    differentiation configuration (24 views at 640x416), element by element."""
+    N = 24 * 640 * 416
+    Ld, Ls0, Ls1, mp, Lgt, mask = inputs(N, 30)
+    t = cu(Ld, Ls0, Ls1, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+    Lr, loss = fipt.render_fwd(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6])
+    ga, gs, gm = fipt.render_bwd(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6])
+    Lr_o, loss_o = O.render_forward(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+    close(Lr.cpu().numpy(), Lr_o)
+    assert abs(loss.item() - loss_o) <= REL * abs(loss_o)
+    del Lr_o
+    for got, ref in zip((ga, gs, gm), O.render_grad(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"],
+                                                     mp["metal"], Lgt)):
+        close(got.cpu().numpy(), ref)
+
+
 def test_render_backward_matches_analytic_gradient(fipt):
     N = 200003
     Ld, Ls0, Ls1, mp, Lgt, mask = inputs(N, 20)
