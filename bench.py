@@ -110,9 +110,10 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload):
-    """DRAM bytes per ray of the bake kernel from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+def recorded_profile(workload):
+    """The bake kernel's counters from the committed ncu summary (DRAM bytes
+    per ray, issue-slot activity, L2 hit rate, active lanes per warp
+    instruction), or None when the kernel source changed since the capture."""
     p = os.path.join(ROOT, "profiles", "bake_%s_traffic.json" % workload)
     if not os.path.exists(p):
         return None
@@ -120,7 +121,7 @@ def recorded_traffic(workload):
         d = json.load(f)
     if d.get("source_digest") != source_digest():
         return None
-    return float(d["dram_bytes_per_ray"])
+    return d
 
 
 class ClockSampler:
@@ -866,7 +867,8 @@ def run_ours(args, wl, world, rank, local):
     bake_s = float(np.mean(bake_ms)) / 1e3
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / bake_s / 1e9
-    traffic_per_ray = recorded_traffic(args.workload)
+    prof = recorded_profile(args.workload)
+    traffic_per_ray = float(prof["dram_bytes_per_ray"]) if prof else None
 
     # -------------------------------------------------- CPU baseline (rank 0, N=1)
     cpu = None
@@ -918,7 +920,9 @@ def run_ours(args, wl, world, rank, local):
                      "alg_bytes_per_ray": round(bytes_per_ray, 1),
                      "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2),
                      "tris_per_ray": round(n_tris / max(n_rays, 1), 2),
-                     "max_stack": max_depth},
+                     "max_stack": max_depth,
+                     "ncu": ({k: prof[k] for k in ("issue_active_pct", "l2_hit_pct", "lanes_per_warp_inst")
+                              if k in prof} if prof else None)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "refine": refine,
