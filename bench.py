@@ -684,12 +684,15 @@ def run_next_rows(args, F, dev, mesh, sc, q, Lgt, qa, with_cpu, peak):
     t_cls = _device_time(lambda: F.emitter_classify(alpha, n_per, 0.01))
     flag, _ = F.emitter_classify(alpha, n_per, 0.01)
     t_rad = _device_time(lambda: F.emitter_radiance(qa, rgb, flag))
-    seg_bits = 32 + int(np.ceil(np.log2(T + 1)))
-    rad_bytes = 3 * Pq * (4 + 4 + 12 + 24 * _sort_passes(seg_bits) + 8) + 3 * T * 16
+    M = int(F.emitter_radiance(qa, rgb, flag)[1].sum().item())     # pixels on emitter triangles
+    seg_bits = 32 + int(np.ceil(np.log2(T)))
+    # gather: triangle id + flag per pixel; per channel and gathered pixel:
+    # index + value + key/value out, the sort passes, the segment bounds
+    rad_bytes = Pq * (4 + 1 + 4) + 3 * M * (4 + 4 + 12 + 24 * _sort_passes(seg_bits) + 8) + 3 * T * 16
     b_pts = 12.0 * T * n_per + 52.0 * T
     b_cls = 4.0 * T * n_per + 9.0 * T
     em = {"triangles": T, "samples_per_triangle": n_per, "pixels": Pq,
-          "emitters_found": int(flag.sum().item()),
+          "emitters_found": int(flag.sum().item()), "emitter_pixels": M,
           "points_ms": round(1e3 * t_pts, 3), "classify_ms": round(1e3 * t_cls, 3),
           "radiance_ms": round(1e3 * t_rad, 3),
           "points_roofline_frac": round(b_pts / t_pts / 1e9 / peak, 4),

@@ -8,9 +8,11 @@
 //    FP64, so the decision is deterministic.
 // 3. With zero reflectance at emitters, the L1 problem of Eq. 12 is solved
 //    per channel by the median of the radiance of the input pixels whose
-//    first hit is the triangle.  Pixels are sorted per channel by the 64-bit
-//    key (triangle << 32 | order-preserving bits of the value); non-emitter
-//    pixels get triangle T and sort last.  Each triangle's segment in the
+//    first hit is the triangle.  The pixels that hit an emitter are first
+//    gathered (in any order: the sort key alone decides the result, and
+//    equal keys carry equal values), then sorted per channel by the 64-bit
+//    key (triangle << 32 | order-preserving bits of the value), with the
+//    gathered count read on the device.  Each triangle's segment in the
 //    sorted keys gives its count, and the lower median (index (c - 1) / 2)
 //    its value.
 #include "fipt_internal.cuh"
@@ -102,20 +104,40 @@ __device__ __forceinline__ float funkey(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-__global__ void k_emit_keys(const int32_t* __restrict__ tri, int64_t stride, const float* __restrict__ rgb,
-                            int64_t P, const uint8_t* __restrict__ flag, int64_t T, int c,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Gathers the pixels whose triangle is an emitter (one atomic per warp).
+__global__ void k_emit_gather(const int32_t* __restrict__ tri, int64_t stride, int64_t P,
+                              const uint8_t* __restrict__ flag, int64_t T, uint32_t* __restrict__ idx,
+                              uint32_t* __restrict__ cnt) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int32_t t = tri[p * stride];
-    const uint64_t seg = (t >= 0 && t < T && flag[t]) ? (uint64_t)t : (uint64_t)T;
-    keys[p] = (seg << 32) | fkey(rgb[3 * p + c]);
-    vals[p] = (uint32_t)p;
+    const int lane = threadIdx.x & 31;
+    bool e = false;
+    if (p < P) {
+        const int32_t t = tri[p * stride];
+        e = t >= 0 && t < T && flag[t];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, e);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (e) idx[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)p;
 }
 
-__global__ void k_emit_bounds(const uint64_t* __restrict__ keys, int64_t P, int64_t T,
+__global__ void k_emit_keys(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ cnt,
+                            const int32_t* __restrict__ tri, int64_t stride, const float* __restrict__ rgb,
+                            int c, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= (int64_t)*cnt) return;
+    const int64_t p = idx[j];
+    keys[j] = ((uint64_t)(uint32_t)tri[p * stride] << 32) | fkey(rgb[3 * p + c]);
+    vals[j] = (uint32_t)j;
+}
+
+__global__ void k_emit_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ cnt, int64_t T,
                               int32_t* __restrict__ start, int32_t* __restrict__ end) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t P = *cnt;
     if (j >= P) return;
     const uint64_t s = keys[j] >> 32;
     if (s >= (uint64_t)T) return;
@@ -149,7 +171,7 @@ __global__ void k_set_emission(const float* __restrict__ Le, const int32_t* __re
 
 struct EmitLayout {
     uint64_t *keys, *keys_alt;
-    uint32_t *vals, *vals_alt, *hist;
+    uint32_t *vals, *vals_alt, *hist, *idx, *cnt;
     int32_t *start, *end;
     size_t bytes;
 };
@@ -165,6 +187,8 @@ EmitLayout carve(void* ws, int64_t P, int64_t T) {
     L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(p1) / sizeof(uint32_t));
     L.start = c.take<int32_t>((size_t)t1);
     L.end = c.take<int32_t>((size_t)t1);
+    L.idx = c.take<uint32_t>((size_t)p1);
+    L.cnt = c.take<uint32_t>(1);
     L.bytes = c.off + 256;
     return L;
 }
@@ -234,18 +258,21 @@ extern "C" fipt_status fipt_emitter_radiance(const int32_t* tri, int64_t tri_str
     FIPT_CUDA(cudaMemsetAsync(Y.start, 0xFF, sizeof(int32_t) * (size_t)T, st));
     FIPT_CUDA(cudaMemsetAsync(Y.end, 0xFF, sizeof(int32_t) * (size_t)T, st));
     int bits = 32;
-    while (((int64_t)1 << (bits - 32)) <= T) ++bits;       // segment ids 0..T
+    while (((int64_t)1 << (bits - 32)) < T) ++bits;        // segment ids 0..T-1
     bits = (bits + 7) & ~7;
+    FIPT_CUDA(cudaMemsetAsync(Y.cnt, 0, sizeof(uint32_t), st));
+    if (P > 0)
+        FIPT_LAUNCH(k_emit_gather, blocks(P, 256), 256, 0, st, tri, tri_stride, P, is_emitter, T, Y.idx, Y.cnt);
     for (int c = 0; c < 3; ++c) {
         uint64_t* sk = Y.keys;
         if (P > 0) {
-            FIPT_LAUNCH(k_emit_keys, blocks(P, 256), 256, 0, st, tri, tri_stride, rgb, P, is_emitter, T, c,
+            FIPT_LAUNCH(k_emit_keys, blocks(P, 256), 256, 0, st, Y.idx, Y.cnt, tri, tri_stride, rgb, c,
                         Y.keys, Y.vals);
             uint32_t* sv;
             fipt_status r = radix_sort_pairs<uint64_t>(Y.keys, Y.keys_alt, Y.vals, Y.vals_alt, Y.hist, P,
-                                                       bits, st, &sk, &sv);
+                                                       bits, st, &sk, &sv, Y.cnt);
             if (r != FIPT_OK) return r;
-            if (c == 0) FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, P, T, Y.start, Y.end);
+            if (c == 0) FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, Y.cnt, T, Y.start, Y.end);
         }
         FIPT_LAUNCH(k_emit_median, blocks(T, 256), 256, 0, st, sk, Y.start, Y.end, T, c, Le, count);
     }

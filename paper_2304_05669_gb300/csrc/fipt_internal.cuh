@@ -158,7 +158,9 @@ struct Carver {
 // ---------------------------------------------------------------- radix sort
 // Stable LSD radix sort of (key, value) pairs, 8 bits per pass, in caller
 // scratch.  Sorts bits [0, bits) of the keys; returns in *out_keys/out_vals
-// which of the two buffers holds the result.
+// which of the two buffers holds the result.  With n_dev (a device count
+// <= n) only the first *n_dev keys take part, without a host round trip;
+// the buffers past them are left undefined.
 size_t radix_sort_scratch_bytes(int64_t n);
 // Rebuilds the emitter table (leaves, FP64 area CDF, n_emit, A_emit) from
 // the packed triangles and their current L_e.
@@ -166,7 +168,7 @@ fipt_status rebuild_emitter_table(fipt_scene* s, cudaStream_t st);
 template <class K>
 fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              uint32_t* hist, int64_t n, int bits, cudaStream_t st,
-                             K** out_keys, uint32_t** out_vals);
+                             K** out_keys, uint32_t** out_vals, const uint32_t* n_dev = nullptr);
 
 // ---------------------------------------------------------------- device math
 #define FIPT_DONE (-2147483647 - 1)   // traversal finished (not a node, not a leaf)

@@ -22,9 +22,11 @@ int64_t sort_blocks(int64_t n) { return (n + SORT_TILE - 1) / SORT_TILE; }
 // ---------------------------------------------------------------- radix sort
 template <class K>
 __global__ void __launch_bounds__(SORT_THREADS)
-k_sort_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist) {
+k_sort_hist(const K* __restrict__ keys, int64_t n, const uint32_t* __restrict__ n_dev, int shift,
+            uint32_t* __restrict__ hist) {
     __shared__ uint32_t cnt[RADIX];
     cnt[threadIdx.x] = 0;
+    if (n_dev && (int64_t)*n_dev < n) n = *n_dev;      // a device-side count bounds the keys
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
 #pragma unroll
@@ -126,7 +128,10 @@ k_scan_apply(uint32_t* __restrict__ a, int64_t m, const uint32_t* __restrict__ b
 template <class K>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
-               uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist) {
+               uint32_t* __restrict__ vout, int64_t n, const uint32_t* __restrict__ n_dev, int shift,
+               const uint32_t* __restrict__ hist) {
+    if (n_dev && (int64_t)*n_dev < n) n = *n_dev;
+    if ((int64_t)blockIdx.x * SORT_TILE >= n) return;   // the whole tile is past the keys
     constexpr int WARPS = SORT_THREADS / 32;
     __shared__ uint32_t base_off[RADIX];
     __shared__ uint32_t run[RADIX];
@@ -535,16 +540,17 @@ static fipt_status scan_hist(uint32_t* hist, int64_t m, uint32_t* bsum, cudaStre
 template <class K>
 fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              uint32_t* hist, int64_t n, int bits, cudaStream_t st, K** out_keys,
-                             uint32_t** out_vals) {
+                             uint32_t** out_vals, const uint32_t* n_dev) {
     K *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     const int64_t nb = sort_blocks(n);
     if (n > 0) {
         for (int shift = 0; shift < bits; shift += 8) {
-            FIPT_LAUNCH(k_sort_hist<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, n, shift, hist);
+            FIPT_LAUNCH(k_sort_hist<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, n, n_dev, shift, hist);
             fipt_status r = scan_hist(hist, (int64_t)RADIX * nb, hist + hist_words(n), st);
             if (r != FIPT_OK) return r;
-            FIPT_LAUNCH(k_sort_scatter<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, va, kb, vb, n, shift, hist);
+            FIPT_LAUNCH(k_sort_scatter<K>, (unsigned)nb, SORT_THREADS, 0, st, ka, va, kb, vb, n, n_dev, shift,
+                        hist);
             K* tk = ka; ka = kb; kb = tk;
             uint32_t* tv = va; va = vb; vb = tv;
         }
@@ -557,10 +563,10 @@ fipt_status radix_sort_pairs(K* keys, K* keys_alt, uint32_t* vals, uint32_t* val
 
 template fipt_status radix_sort_pairs<uint64_t>(uint64_t*, uint64_t*, uint32_t*, uint32_t*,
                                                 uint32_t*, int64_t, int, cudaStream_t,
-                                                uint64_t**, uint32_t**);
+                                                uint64_t**, uint32_t**, const uint32_t*);
 template fipt_status radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                                 uint32_t*, int64_t, int, cudaStream_t,
-                                                uint32_t**, uint32_t**);
+                                                uint32_t**, uint32_t**, const uint32_t*);
 
 fipt_status rebuild_emitter_table(fipt_scene* s, cudaStream_t st) {
     if (s->T == 0) return FIPT_OK;

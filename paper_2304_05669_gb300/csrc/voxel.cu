@@ -9,18 +9,25 @@
 
 namespace {
 
+// The per-axis scale R / (hi - lo) is the same correctly rounded double for
+// every pixel; the first three threads of a block compute it once.
 __global__ void k_vox_keys(const float* __restrict__ x, int64_t stride, int64_t P,
                            const SceneConst* __restrict__ c, int R, uint32_t* __restrict__ keys,
                            uint32_t* __restrict__ vals) {
+    __shared__ double scale[3];
+    if (threadIdx.x < 3) {
+        const double ext = __dsub_rn((double)c->hi[threadIdx.x], (double)c->lo[threadIdx.x]);
+        scale[threadIdx.x] = ext > 0.0 ? __ddiv_rn((double)R, ext) : 0.0;
+    }
+    __syncthreads();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= P) return;
     uint32_t ix[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const double lo = (double)c->lo[a];
-        const double ext = __dsub_rn((double)c->hi[a], lo);
         double f = 0.0;
-        if (ext > 0.0) f = __dmul_rn(__dsub_rn((double)x[p * stride + a], lo), __ddiv_rn((double)R, ext));
+        if (scale[a] > 0.0) f = __dmul_rn(__dsub_rn((double)x[p * stride + a], lo), scale[a]);
         double fl = floor(f);
         fl = fl < 0.0 ? 0.0 : (fl > (double)(R - 1) ? (double)(R - 1) : fl);
         ix[a] = (uint32_t)fl;
@@ -35,13 +42,34 @@ __global__ void k_vox_means(const uint32_t* __restrict__ keys, const uint32_t* _
     if (j >= P) return;
     const uint32_t k = keys[j];
     if (j > 0 && keys[j - 1] == k) return;          // not the first pixel of its voxel
+    // the segment's pixels are fetched 8 at a time (independent loads in
+    // flight together) and added strictly in order
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     int64_t e = j;
-    for (; e < P && keys[e] == k; ++e) {
-        const int64_t p = pix[e];
-        s0 += (double)L[3 * p];
-        s1 += (double)L[3 * p + 1];
-        s2 += (double)L[3 * p + 2];
+    bool more = true;
+    while (more) {
+        float v[8][3];
+        bool in[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) in[u] = e + u < P && keys[e + u] == k;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (u > 0) in[u] = in[u] && in[u - 1];
+            const int64_t q = in[u] ? (int64_t)pix[e + u] : 0;
+            v[u][0] = in[u] ? L[3 * q] : 0.0f;
+            v[u][1] = in[u] ? L[3 * q + 1] : 0.0f;
+            v[u][2] = in[u] ? L[3 * q + 2] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (in[u]) {
+                s0 += (double)v[u][0];
+                s1 += (double)v[u][1];
+                s2 += (double)v[u][2];
+                ++e;
+            }
+        }
+        more = in[7];
     }
     const double n = (double)(e - j);
     grid[k] = make_float4((float)(s0 / n), (float)(s1 / n), (float)(s2 / n), (float)n);
