@@ -20,10 +20,10 @@
 namespace {
 
 #ifndef FIPT_REFINE_THREADS
-#define FIPT_REFINE_THREADS 64
+#define FIPT_REFINE_THREADS 64   // small blocks: the shared stack bounds residency
 #endif
 #ifndef FIPT_REFINE_MINB
-#define FIPT_REFINE_MINB 20
+#define FIPT_REFINE_MINB 20      // resident blocks per SM the register budget must allow
 #endif
 constexpr int REFINE_THREADS = FIPT_REFINE_THREADS;
 constexpr int REFINE_MINB = FIPT_REFINE_MINB;
@@ -178,7 +178,7 @@ enum : int { K_NONE = 0, K_S0 = 1, K_PATH = 2, K_SV = 3 };
 enum : int { A_START, A_MAIN, A_VERTEX_BSDF, A_END_PATH, A_END_SAMPLE, A_RAY };
 
 #ifndef FIPT_REFINE_REFILL
-#define FIPT_REFINE_REFILL 24
+#define FIPT_REFINE_REFILL 24    // lanes that must be waiting before a warp sets up new rays
 #endif
 
 __device__ __forceinline__ void start_ray(TraceRay& r, BestHit& best, int& node, int& sp, int& steps,
