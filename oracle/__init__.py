@@ -85,6 +85,7 @@ def _L():
         L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
         L.oracle_voxel_pool.argtypes = [P, P, P, I64, I32, P]
         L.oracle_scene_set_voxel_cache.argtypes = [P, P, I32]
+        L.oracle_brdf_cos.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P]
         L.oracle_emitter_points.argtypes = [P, U64, U32, I32, P]
         L.oracle_emitter_classify.argtypes = [P, I64, I32, ctypes.c_float, P, P]
         L.oracle_emitter_radiance.argtypes = [P, I64, P, I64, P, I64, P, P]
@@ -448,3 +449,13 @@ def emitter_radiance(tri, rgb, flag, tri_stride=1):
     cnt = np.zeros(T, np.int32)
     _L().oracle_emitter_radiance(_p(tri), int(tri_stride), _p(rgb), P, _p(flag), T, _p(Le), _p(cnt))
     return Le, cnt
+
+
+def brdf_cos(n, wo, wi, albedo, sigma, metal):
+    """Eq. 1's BRDF times (n . wi), as the refinement evaluates it at a path
+    vertex: diffuse k_d / pi plus GGX with the Fresnel split of Eq. 7
+    (k_s F0 + F1), k_d = a (1 - m), k_s = 0.04 (1 - m) + a m.  -> [3]."""
+    f = np.zeros(3)
+    _L().oracle_brdf_cos(_p(_c(n, np.float64)), _p(_c(wo, np.float64)), _p(_c(wi, np.float64)),
+                         _p(_c(albedo, np.float32)), float(sigma), float(metal), _p(f))
+    return f

@@ -1527,3 +1527,23 @@ void oracle_emitter_radiance(const int32_t* tri, int64_t stride, const float* rg
     free(vals);
     free(fill);
 }
+
+/* ------------------------------------------------------------------ */
+/* The BRDF of Eq. 1 as the refinement evaluates it                      */
+/* ------------------------------------------------------------------ */
+
+/* f[c] = f_r(wo, wi)[c] * (n . wi) for one material (albedo, roughness,
+ * metallic), the product the refinement's path vertices use; exposed so
+ * that its symmetry (f_r(wo, wi) = f_r(wi, wo)) can be checked. */
+void oracle_brdf_cos(const double* n, const double* wo, const double* wi, const float* albedo,
+                     float sigma, float metal, double* f)
+{
+    refine_job R;
+    memset(&R, 0, sizeof(R));
+    R.ma = albedo;
+    R.ms = &sigma;
+    R.mm = &metal;
+    double pdf, Pd;
+    int amb = 0;
+    vertex_brdf_h(&R, 0, n, wo, wi, NULL, f, &pdf, &Pd, &amb);
+}
