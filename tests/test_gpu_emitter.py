@@ -146,3 +146,38 @@ def test_extract_emitters_end_to_end(fipt):
     oLe, ocnt = O.emitter_radiance(tri, rgb, m.emitter.astype(np.uint8))
     assert np.array_equal(Le.cpu().numpy(), oLe)
     assert np.allclose(oLe[m.emitter], m.Le[m.emitter], rtol=0.03)
+
+
+def test_emitter_detection_sanity_on_the_floor(fipt):
+    """The large-scene configuration end to end (Sec. 4.4): first hits of 64
+    256x256 views of the 2,045,464-triangle floor, shading tables baked at
+    16 spp, targets = the factorized render with true materials plus the
+    emission of emitter hits, renders with perturbed materials.  Ranked by
+    mean per-pixel error, the top-c triangles (c = emitter triangles that
+    some pixel sees) are those emitters (IoU >= 0.9)."""
+    from workloads import building_floor, material_params, pinhole_views
+    m = building_floor(5)
+    sc = fipt.Scene.from_mesh(m)
+    qa, valid = sc.camera_queries(cu(pinhole_views(m, 64, seed=2)), 256, 256)
+    q, _pix, n = fipt.compact_queries(qa, valid, qa.shape[0])
+    q = q[:int(n.item())]
+    N = q.shape[0]
+    sigma = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
+    Ld, Ls0, Ls1 = fipt.bake(sc, q, sigma, 16, 16, seed=4)
+    true, est = material_params(N, seed=3), material_params(N, seed=3)
+    rng = np.random.default_rng(5)
+    est["albedo"] = np.clip(est["albedo"] * rng.uniform(0.9, 1.1, est["albedo"].shape), 0, 1).astype(np.float32)
+    est["rough"] = np.clip(est["rough"] + rng.normal(0, 0.02, N), 0.02, 1).astype(np.float32)
+    tri = q[:, 9].contiguous().view(torch.int32)
+    Lgt = fipt.render_fwd(Ld, Ls0, Ls1, sigma, cu(true["albedo"]), cu(true["rough"]), cu(true["metal"]))[0]
+    Lgt = Lgt + cu(m.Le)[tri.long()]
+    Lr = fipt.render_fwd(Ld, Ls0, Ls1, sigma, cu(est["albedo"]), cu(est["rough"]), cu(est["metal"]))[0]
+    err, cnt = fipt.tri_error(q, Lr, Lgt, m.T)
+    fipt.context().sync_status()
+    err, cnt = err.cpu().numpy(), cnt.cpu().numpy()
+    seen = np.nonzero(m.emitter & (cnt > 0))[0]
+    assert len(seen) >= 4
+    mean = np.where(cnt > 0, err / np.maximum(cnt, 1), -1.0)
+    top = np.argsort(-mean, kind="stable")[:len(seen)]
+    iou = len(set(top) & set(seen)) / len(set(top) | set(seen))
+    assert iou >= 0.9, (iou, len(seen))
