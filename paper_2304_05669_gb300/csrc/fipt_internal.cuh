@@ -208,8 +208,6 @@ struct TraceRay {
     float ix, iy, iz;       // 1/d for the slab tests
     float Sx, Sy, Sz;
     int k;                  // kx | ky << 2 | kz << 4
-    float qx, qy, qz;       // o * (1/d), rounded: a slab distance is fma(plane, 1/d, -q)
-    float slack;            // bound on the error the rounding of q adds to a box test
 };
 
 __device__ __forceinline__ float pick3(float x, float y, float z, int k) {
@@ -234,12 +232,6 @@ __device__ __forceinline__ TraceRay make_ray(float ox, float oy, float oz, float
     r.Sy = pick3(dx, dy, dz, ky) / dkz;
     r.Sz = 1.0f / dkz;
     r.k = kx | (ky << 2) | (kz << 4);
-    r.qx = ox * r.ix; r.qy = oy * r.iy; r.qz = oz * r.iz;
-    // a slab distance fma(p, 1/d, -q) is off from (p - o) / d by the rounding
-    // of q (at most 2^-24 |q|, an absolute error) and by relative roundings
-    // (1/d, the fma) that the robust factor of the box test covers; entry and
-    // exit may both be off, hence twice the largest |q|, with a margin
-    r.slack = 1.25e-7f * fmaxf(fmaxf(fabsf(r.qx), fabsf(r.qy)), fabsf(r.qz));
     return r;
 }
 
@@ -278,26 +270,25 @@ __device__ __forceinline__ bool tri_intersect(const TraceRay& r, float4 p0, floa
     return t > 0.0f;
 }
 
-// Slab test of both child boxes of a node against [0, tmax]: each plane
-// distance is one fma, p * (1/d) - o * (1/d), and the test entry <= exit is
-// widened by the robust factor (relative roundings) and the ray's slack (the
-// rounding of o * (1/d)), so float rounding never culls a box the exact
-// test would keep.
+// Slab test of both child boxes of a node against [0, tmax]; conservative by
+// a few ulps so that float rounding never culls a box the triangle test
+// would hit.
 __device__ __forceinline__ void node_test(const TraceRay& r, const BvhNode& n, float tmax,
                                           bool& hit0, bool& hit1, float& t0, float& t1) {
-    const float a0 = fmaf(n.a.x, r.ix, -r.qx), a1 = fmaf(n.a.y, r.ix, -r.qx);
-    const float a2 = fmaf(n.a.z, r.iy, -r.qy), a3 = fmaf(n.a.w, r.iy, -r.qy);
-    const float a4 = fmaf(n.c.x, r.iz, -r.qz), a5 = fmaf(n.c.y, r.iz, -r.qz);
-    const float b0 = fmaf(n.b.x, r.ix, -r.qx), b1 = fmaf(n.b.y, r.ix, -r.qx);
-    const float b2 = fmaf(n.b.z, r.iy, -r.qy), b3 = fmaf(n.b.w, r.iy, -r.qy);
-    const float b4 = fmaf(n.c.z, r.iz, -r.qz), b5 = fmaf(n.c.w, r.iz, -r.qz);
+    const float ox = r.ox, oy = r.oy, oz = r.oz;
+    const float a0 = (n.a.x - ox) * r.ix, a1 = (n.a.y - ox) * r.ix;
+    const float a2 = (n.a.z - oy) * r.iy, a3 = (n.a.w - oy) * r.iy;
+    const float a4 = (n.c.x - oz) * r.iz, a5 = (n.c.y - oz) * r.iz;
+    const float b0 = (n.b.x - ox) * r.ix, b1 = (n.b.y - ox) * r.ix;
+    const float b2 = (n.b.z - oy) * r.iy, b3 = (n.b.w - oy) * r.iy;
+    const float b4 = (n.c.z - oz) * r.iz, b5 = (n.c.w - oz) * r.iz;
     const float robust = 1.0000005f;
     const float n0 = fmaxf(fmaxf(fminf(a0, a1), fminf(a2, a3)), fmaxf(fminf(a4, a5), 0.0f));
     const float f0 = fminf(fminf(fmaxf(a0, a1), fmaxf(a2, a3)), fminf(fmaxf(a4, a5), tmax));
     const float n1 = fmaxf(fmaxf(fminf(b0, b1), fminf(b2, b3)), fmaxf(fminf(b4, b5), 0.0f));
     const float f1 = fminf(fminf(fmaxf(b0, b1), fmaxf(b2, b3)), fminf(fmaxf(b4, b5), tmax));
-    hit0 = n0 <= fmaf(f0, robust, r.slack);
-    hit1 = n1 <= fmaf(f1, robust, r.slack);
+    hit0 = n0 <= f0 * robust;
+    hit1 = n1 <= f1 * robust;
     t0 = n0;
     t1 = n1;
 }
