@@ -63,3 +63,46 @@ def test_query_record_is_40_bytes():
         _fields_ = [("x", ctypes.c_float * 3), ("n", ctypes.c_float * 3),
                     ("wo", ctypes.c_float * 3), ("tri", ctypes.c_int32)]
     assert ctypes.sizeof(Q) == 40
+
+
+def _toolchain():
+    import shutil
+    from paper_2304_05669_gb300 import build, _native
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    lib = _native.library_path()
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(build._nvcc())), "lib64")
+    return gcc, lib, cuda_lib
+
+
+def test_header_is_standalone_c_and_cxx(tmp_path):
+    """include/fipt.h compiles alone as C11 and as C++17, warnings as errors."""
+    import subprocess
+    gcc, _lib, _cuda = _toolchain()
+    src = tmp_path / "h.c"
+    src.write_text('#include "fipt.h"\nint main(void) { return (int)sizeof(fipt_query) - 40; }\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-fsyntax-only",
+                    str(src)], check=True)
+    subprocess.run([gcc, "-x", "c++", "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                    "-fsyntax-only", str(src)], check=True)
+
+
+def test_c_client_links_and_host_calls_answer(tmp_path):
+    """tests/c/abi_host.c, a C11 client, links against the library and checks
+    the host-side calls (version, status strings, workspace queries,
+    argument errors, the admission arena) without a GPU."""
+    import subprocess
+    gcc, lib, cuda_lib = _toolchain()
+    exe = tmp_path / "abi_host"
+    libdir = os.path.dirname(lib)
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "c", "abi_host.c"),
+                    "-L", libdir, "-l", "fipt", "-Wl,-rpath," + libdir, "-L", cuda_lib,
+                    "-Wl,-rpath-link," + cuda_lib, "-o", str(exe)], check=True)
+    env = dict(os.environ)
+    env["LD_LIBRARY_PATH"] = cuda_lib + os.pathsep + env.get("LD_LIBRARY_PATH", "")
+    out = subprocess.run([str(exe)], env=env, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    assert "abi host checks ok" in out.stdout
