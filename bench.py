@@ -565,12 +565,22 @@ def run_refine(args, F, dev, mesh, sc, q_all, with_cpu):
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) / 1e3)
+    st = torch.zeros(4, dtype=torch.int64, device=dev)     # instrumented, untimed
+    F.bake_refine(sc, q, SIGMA, S, S, stats=st)
     F.context().sync_status()
+    n_rays, n_nodes, n_tris, max_sp = [int(x) for x in st.cpu().tolist()]
+    t = float(np.median(ts))
     samples = N * S * (1 + len(SIGMA))
+    alg = 64.0 * n_nodes + 48.0 * n_tris + 24.0 * n_rays + N * (40 + 12 * (1 + 2 * len(SIGMA)))
+    peak, peak_kind = measured_peaks()
     out = {"points": N, "spp": S, "sigma_c": 0.6, "max_depth": 8, "mis": True,
-           "ms": round(1e3 * float(np.median(ts)), 3),
-           "msamples_per_s": round(samples / float(np.median(ts)) / 1e6, 2),
-           "points_per_s": round(N / float(np.median(ts)), 1)}
+           "ms": round(1e3 * t, 3),
+           "msamples_per_s": round(samples / t / 1e6, 2),
+           "points_per_s": round(N / t, 1),
+           "rays_per_sample": round(n_rays / samples, 3), "mrays_per_s": round(n_rays / t / 1e6, 1),
+           "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2), "max_stack": max_sp,
+           "roofline": {"bound": "hbm", "achieved": round(alg / t / 1e9, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(alg / t / 1e9 / peak, 4), "kernel": "k_refine", "peak_kind": peak_kind}}
     if with_cpu:
         import oracle as O
         cams = pinhole_views_for(mesh)

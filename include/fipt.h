@@ -294,7 +294,10 @@ fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, con
  * emitter sample at vertex i (pid, s, lobe|i<<9|0x100, rid).
  * Outputs as fipt_bake; per_sample (nullable, device f32
  * [N, 1+K, max(spp), 6]) receives every sample's contribution (L_d uses the
- * first 3 values, L_s0 / L_s1 the two triples).  Requires
+ * first 3 values, L_s0 / L_s1 the two triples).  params->stats (NULL, or
+ * 4 device u64 counters) receives, added, the rays traced (path segments
+ * and shadow rays), nodes visited and triangles tested, and the deepest
+ * stack (max); it cannot be combined with per_sample.  Requires
  * fipt_scene_set_materials. */
 fipt_status fipt_bake_refine(fipt_scene* scene, const fipt_query* q, int64_t N,
                              const fipt_bake_params* params, float sigma_c, int32_t max_depth,

@@ -300,8 +300,10 @@ def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request
 
 
 def bake_refine(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, sigma_c=0.6, max_depth=8,
-                mis=True, seed=0, request_id=0, point_base=0, per_sample=False, stream=None):
-    """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10, MIS) -> (Ld, Ls0, Ls1[, per_sample])."""
+                mis=True, seed=0, request_id=0, point_base=0, per_sample=False, stats=None, stream=None):
+    """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10, MIS) -> (Ld, Ls0, Ls1[, per_sample]).
+    ``stats``: an int64 [4] CUDA tensor that receives (added) rays, node
+    visits, triangle tests and (max) the deepest stack."""
     q = _dev(q, torch.float32, "q")
     N = q.shape[0]
     K = len(sigma)
@@ -311,7 +313,7 @@ def bake_refine(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, sigma_c=
            torch.empty((N, K, 3), dtype=torch.float32, device=q.device))
     ps = (torch.empty((N, K + 1, max(spp_diffuse, spp_s), 6), dtype=torch.float32, device=q.device)
           if per_sample else None)
-    p = bake_params(sigma, spp_diffuse, spp_s, seed, request_id, point_base)
+    p = bake_params(sigma, spp_diffuse, spp_s, seed, request_id, point_base, stats)
     check(lib().fipt_bake_refine(scene.handle, _ptr(q), N, ctypes.byref(p), float(sigma_c),
                                  int(max_depth), int(bool(mis)), _ptr(out[0]), _ptr(out[1]),
                                  _ptr(out[2]), _ptr(ps), _stream(stream)))

@@ -194,11 +194,14 @@ __device__ __forceinline__ void start_ray(TraceRay& r, BestHit& best, int& node,
     node = sc.T > 0 ? 0 : FIPT_DONE;
 }
 
-template <bool PER_SAMPLE>
+// STATS: an instrumented build of the same code that adds its rays, node
+// visits and triangle tests to stats[0..2] and raises stats[3] to its
+// deepest stack.
+template <bool PER_SAMPLE, bool STATS>
 __global__ void __launch_bounds__(REFINE_THREADS, REFINE_MINB)
 k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R, float* __restrict__ Ld,
          float* __restrict__ Ls0, float* __restrict__ Ls1, float* __restrict__ per_sample,
-         int32_t* status) {
+         int32_t* status, unsigned long long* stats) {
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ int stk[STACK_DEPTH * REFINE_THREADS];
     int* stack = stk + threadIdx.x;
@@ -253,6 +256,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
     r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
     int node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
     WalkStats ws;
+    unsigned long long n_rays = 0;
 
 #define FIPT_ADD6(cv, av, v)       \
     do {                           \
@@ -347,6 +351,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                                     tgt = e;
                                     start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, ex, ey, ez,
                                               1.001f * dist + eps);
+                                    if (STATS) ++n_rays;
                                     kind = K_SV;
                                     act = A_RAY;
                                 }
@@ -389,6 +394,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                     } else {
                         b0 *= f[0] / pdf; b1 *= f[1] / pdf; b2 *= f[2] / pdf;
                         start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, wi.x, wi.y, wi.z, FINF);
+                        if (STATS) ++n_rays;
                         dx = wi.x; dy = wi.y; dz = wi.z;
                         pdf_prev = pdf;
                         ++depth;
@@ -468,6 +474,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                             tgt = e;
                             skip = __float_as_int(q4.y);
                             start_ray(r, best, node, sp, steps, sc, ox, oy, oz, ex, ey, ez, 1.001f * dist + eps);
+                            if (STATS) ++n_rays;
                             kind = K_S0;
                             act = A_RAY;
                             break;
@@ -514,15 +521,22 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                 skip = __float_as_int(q4.y);
                 dx = wi.x; dy = wi.y; dz = wi.z;
                 start_ray(r, best, node, sp, steps, sc, ox, oy, oz, wi.x, wi.y, wi.z, FINF);
+                if (STATS) ++n_rays;
                 kind = K_PATH;
                 act = A_RAY;
             }
         }
         // ---------------- inner nodes (speculative), then leaves
-        warp_walk<REFINE_THREADS, false, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
+        warp_walk<REFINE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
     }
 #undef FIPT_ADD6
 
+    if (STATS) {
+        atomicAdd(&stats[0], n_rays);
+        atomicAdd(&stats[1], ws.nodes);
+        atomicAdd(&stats[2], ws.tris);
+        atomicMax(&stats[3], (unsigned long long)ws.max_sp);
+    }
     if (!valid) return;
     if (PER_SAMPLE) {
         float* ps = per_sample + (size_t)(p * L + lobe) * R.smax * 6;
@@ -558,6 +572,7 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
     FIPT_REQUIRE(max_depth >= 0 && max_depth < 4096, "max_depth must be in [0, 4096)");
     for (int k = 0; k < prm->K; ++k)
         FIPT_REQUIRE(prm->sigma[k] > 0.0f && prm->sigma[k] <= 1.0f, "sigma[%d] not in (0, 1]", k);
+    FIPT_REQUIRE(!(prm->stats && per_sample), "stats and per_sample cannot be combined");
     if (N == 0) return FIPT_OK;
     FIPT_REQUIRE(q && Ld && Ls0 && Ls1, "NULL query / output array");
     FIPT_REQUIRE(fipt_aligned(q, 8) && fipt_aligned(Ld, 4) && fipt_aligned(Ls0, 4) &&
@@ -578,11 +593,14 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
     const int64_t threads = ((N + 31) / 32) * (1 + prm->K) * 32;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (per_sample)
-        FIPT_LAUNCH(k_refine<true>, blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(), q,
-                    N, R, Ld, Ls0, Ls1, per_sample, s->ctx->status);
+        FIPT_LAUNCH((k_refine<true, false>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(),
+                    q, N, R, Ld, Ls0, Ls1, per_sample, s->ctx->status, nullptr);
+    else if (prm->stats)
+        FIPT_LAUNCH((k_refine<false, true>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(),
+                    q, N, R, Ld, Ls0, Ls1, nullptr, s->ctx->status, prm->stats);
     else
-        FIPT_LAUNCH(k_refine<false>, blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(),
-                    q, N, R, Ld, Ls0, Ls1, nullptr, s->ctx->status);
+        FIPT_LAUNCH((k_refine<false, false>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st,
+                    s->view(), q, N, R, Ld, Ls0, Ls1, nullptr, s->ctx->status, nullptr);
     FIPT_LAUNCHED("bake_refine");
     return FIPT_OK;
 }

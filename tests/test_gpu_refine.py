@@ -117,3 +117,34 @@ def test_refine_ragged_and_empty(fipt):
     sc.set_materials(cu(a), cu(r), cu(mt))
     out = fipt.bake_refine(sc, torch.zeros((0, 10), device="cuda"), SIGMA, 4)
     assert out[0].shape == (0, 3)
+
+
+def test_refine_stats_counters(fipt):
+    """The instrumented refinement gives the same shadings and counts its
+    rays: at least one per sample, and on an all-rough scene without MIS
+    exactly the stage-1 bake's rays (no path continues, no shadow ray)."""
+    m = cornell_box()
+    T = m.T
+    q = surface_queries(m, 500, seed=12)
+    qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+    sc = fipt.Scene.from_mesh(m)
+    sc.set_materials(cu(np.full((T, 3), 0.5, np.float32)), cu(np.ones(T, np.float32)),
+                     cu(np.zeros(T, np.float32)))
+    for mis in (False, True):
+        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        a = fipt.bake_refine(sc, qt, SIGMA, 16, 8, mis=mis, seed=3, stats=st)
+        b = fipt.bake_refine(sc, qt, SIGMA, 16, 8, mis=mis, seed=3)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        n_rays, n_nodes, n_tris, max_sp = st.cpu().tolist()
+        st0 = torch.zeros(4, dtype=torch.int64, device="cuda")
+        fipt.bake(sc, qt, SIGMA, 16, 8, seed=3, stats=st0)
+        bake_rays = st0.cpu().tolist()[0]
+        if mis:
+            assert n_rays > bake_rays
+        else:
+            assert n_rays == bake_rays
+        assert n_nodes > n_rays and 0 < max_sp <= 32
+    with pytest.raises(fipt.FiptError):
+        fipt.bake_refine(sc, qt, SIGMA, 4, 4, per_sample=True, stats=torch.zeros(4, dtype=torch.int64,
+                                                                                  device="cuda"))
