@@ -217,6 +217,9 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
     const int n_emit = sc.cst->n_emit;
     const double A_emit = sc.cst->A_emit;
     const bool mis = R.mis && n_emit > 0;
+    // the emitter choice compares FP64 cumulative areas (exact selection);
+    // the area-measure pdfs dist^2 / (A cos) feed weights only, in FP32
+    const float A_emit_f = (float)A_emit;
     const uint32_t pid = A.point_base + (uint32_t)p;
     float a2 = 0.0f;
     if (lobe > 0) {
@@ -305,7 +308,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                             if (mis) {
                                 const float3 ne = leaf_normal(sc, leaf);
                                 const float ce = fabsf(dx * ne.x + dy * ne.y + dz * ne.z);
-                                const float pl = (float)((double)best.t * best.t / (A_emit * ce));
+                                const float pl = best.t * best.t / (A_emit_f * ce);
                                 wgt = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
                             }
                             l0 += b0 * wgt * le.x; l1 += b1 * wgt * le.y; l2 += b2 * wgt * le.z;
@@ -343,7 +346,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                                 float f[3], pb;
                                 vertex_brdf(M, nv, wv, make_float3(ex, ey, ez), mu_v, f, pb);
                                 if (f[0] > 0.0f || f[1] > 0.0f || f[2] > 0.0f) {
-                                    const float pl = (float)((double)dist * dist / (A_emit * ce));
+                                    const float pl = dist * dist / (A_emit_f * ce);
                                     const float wgt = pl * pl / (pl * pl + pb * pb);
                                     sw0 = b0 * wgt * f[0] / pl;
                                     sw1 = b1 * wgt * f[1] / pl;
@@ -467,7 +470,7 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                             }
                         }
                         if (g0 > 0.0f || g1 > 0.0f) {
-                            const float pl = (float)((double)dist * dist / (A_emit * ce));
+                            const float pl = dist * dist / (A_emit_f * ce);
                             const float wgt = pl * pl / (pl * pl + pb * pb);
                             sw0 = wgt * g0 / pl;
                             sw1 = wgt * g1 / pl;
