@@ -748,6 +748,7 @@ def run_ours(args, wl, world, rank, local):
     import torch
     import paper_2304_05669_gb300 as F
     from paper_2304_05669_gb300._native import lib
+    from paper_2304_05669_gb300.sharded import global_loss, global_tri_error
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -795,6 +796,9 @@ def run_ours(args, wl, world, rank, local):
         Lr, loss = F.render_fwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
         grads = F.render_bwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
         err, cnt = F.tri_error(q, Lr, Lgt, mesh.T)
+        if world > 1:        # the two sums over all ranks' pixels (one all-reduce each)
+            global_loss(loss)
+            global_tri_error(err, cnt)
         return sc, (Ld, Ls0, Ls1), q, loss, grads, (err, cnt)
 
     # ground-truth images for the render loss: the same tables rendered with
