@@ -309,7 +309,8 @@ fipt_status fipt_bake_refine(fipt_scene* scene, const fipt_query* q, int64_t N,
  * and the roughness lerp of Eq. 8: sigma is clamped to
  * [sigma_grid[0], sigma_grid[K-1]], segment i is the largest i <= K-2 with
  * sigma_grid[i] <= sigma.  Inputs: tables as produced by fipt_bake;
- * sigma_grid [K] HOST f32 increasing; albedo [N,3], rough [N], metal [N]
+ * sigma_grid [K] HOST f32 increasing, K in [2, 8] (a lerp needs two
+ * nodes; other K is FIPT_ERR_INVALID_ARG); albedo [N,3], rough [N], metal [N]
  * f32.  Outputs: Lr [N,3] f32.  When Lgt [N,3] is given, *loss (device
  * f64) = sum over points with mask != 0 (mask [N] u8, NULL = all) and
  * channels of (Gamma(Lr) - Gamma(Lgt))^2 (Eq. 14 with alpha = 0),

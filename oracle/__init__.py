@@ -353,6 +353,8 @@ def lerp_segment(rough, grid):
     """Eq. 8: segment i (largest i <= K-2 with grid[i] <= sigma after
     clamping sigma to the grid), weight t, and whether sigma was clamped."""
     grid = np.asarray(grid, np.float64)
+    if len(grid) < 2:
+        raise ValueError("the lerp of Eq. 8 needs at least two roughness nodes")
     r = np.asarray(rough, np.float64)
     s = np.clip(r, grid[0], grid[-1])
     i = np.clip(np.searchsorted(grid, s, side="right") - 1, 0, len(grid) - 2)

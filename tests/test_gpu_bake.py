@@ -154,3 +154,13 @@ def test_stats_counters(fipt):
     rays, nodes, tris, depth = stats.cpu().tolist()
     assert 0 < rays <= 2048 * 8 * 7
     assert nodes > rays and tris > 0 and 0 < depth <= 32
+
+
+@pytest.mark.parametrize("sigma", [[0.5], [0.02, 0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1.0]])
+def test_bake_grid_sizes(fipt, sigma):
+    """One roughness level and the largest grid the parameters hold (8)."""
+    m = cornell_box()
+    q = surface_queries(m, 512, seed=31)
+    g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 16, 16, seed=8, sigma=sigma)
+    ora = O.OracleScene.from_mesh(m).bake(q, sigma, 16, 16, seed=8, eta=ETA_BAKE)
+    print(check_bake(g, ora))

@@ -135,3 +135,25 @@ def test_tri_error_matches_oracle(fipt, P, T):
     assert np.allclose(err.cpu().numpy(), e_o, rtol=1e-12, atol=0)
     err2, _ = fipt.tri_error(*cu(tri, Lr, Lgt), T)
     assert torch.equal(err, err2)        # deterministic
+
+
+@pytest.mark.parametrize("grid", [[0.1, 0.9], [0.02, 0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1.0]])
+def test_render_grid_sizes(fipt, grid):
+    """The smallest (K = 2) and the largest (K = 8) roughness grids, forward,
+    loss and backward; K = 1 and K = 9 are rejected."""
+    N = 4099
+    Ld, Ls0, Ls1 = shading_tables(N, len(grid), seed=40)
+    mp = material_params(N, seed=41)
+    gt = material_params(N, seed=42)
+    Lgt, _ = O.render_forward(Ld, Ls0, Ls1, grid, gt["albedo"], gt["rough"], gt["metal"])
+    Lgt = Lgt.astype(np.float32)
+    t = cu(Ld, Ls0, Ls1, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+    Lr, loss = fipt.render_fwd(t[0], t[1], t[2], grid, t[3], t[4], t[5], t[6])
+    Lr_o, loss_o = O.render_forward(Ld, Ls0, Ls1, grid, mp["albedo"], mp["rough"], mp["metal"], Lgt)
+    close(Lr.cpu().numpy(), Lr_o)
+    assert abs(loss.item() - loss_o) <= REL * abs(loss_o)
+    for got, ref in zip(fipt.render_bwd(t[0], t[1], t[2], grid, t[3], t[4], t[5], t[6]),
+                        O.render_grad(Ld, Ls0, Ls1, grid, mp["albedo"], mp["rough"], mp["metal"], Lgt)):
+        close(got.cpu().numpy(), ref)
+    with pytest.raises(fipt.FiptError):
+        fipt.render_fwd(t[0], t[1][:, :1].contiguous(), t[2][:, :1].contiguous(), [0.5], t[3], t[4], t[5])
