@@ -40,6 +40,32 @@ def _dev(t, dtype, name):
     return t.contiguous()
 
 
+def _need(t, dtype, name, shape):
+    """A CUDA tensor of this dtype and exact shape (contiguous; copied if not)."""
+    t = _dev(t, dtype, name)
+    if tuple(t.shape) != tuple(int(d) for d in shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t
+
+
+def _host(t, dtype, name, shape):
+    """A CPU tensor of this dtype and exact shape (contiguous; copied if not)."""
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a CPU tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(int(d) for d in shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t.contiguous()
+
+
+def _queries(q, name="q"):
+    q = _dev(q, torch.float32, name)
+    if q.dim() != 2 or q.shape[1] != 10:
+        raise ValueError("%s must be [N, 10] query records, got %s" % (name, tuple(q.shape)))
+    return q
+
+
 def _workspace(nbytes, device):
     """A byte tensor whose data pointer is 256-byte aligned."""
     buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
@@ -253,7 +279,9 @@ class Scene:
 
 def compact_queries(q, valid, max_out, stream=None):
     """First ``max_out`` valid records in order -> (out, pixel_of, n_out[1] int64)."""
+    q = _queries(q)
     P = q.shape[0]
+    valid = _need(valid, torch.int32, "valid", (P,))
     nbytes = ctypes.c_size_t()
     check(lib().fipt_compact_workspace_size(P, ctypes.byref(nbytes)))
     _b, ws = _workspace(nbytes.value, q.device)
@@ -286,7 +314,7 @@ def bake_params(sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0, poi
 def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0,
          point_base=0, stats=None, out=None, stream=None):
     """Shading terms (Eq. 6-7) at the query points -> (Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3])."""
-    q = _dev(q, torch.float32, "q")
+    q = _queries(q)
     N = q.shape[0]
     K = len(sigma)
     if out is None:
@@ -304,7 +332,7 @@ def bake_refine(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, sigma_c=
     """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10, MIS) -> (Ld, Ls0, Ls1[, per_sample]).
     ``stats``: an int64 [4] CUDA tensor that receives (added) rays, node
     visits, triangle tests and (max) the deepest stack."""
-    q = _dev(q, torch.float32, "q")
+    q = _queries(q)
     N = q.shape[0]
     K = len(sigma)
     spp_s = spp_diffuse if spp_specular is None else spp_specular
@@ -325,13 +353,31 @@ def _grid(sigma_grid):
     return g, len(sigma_grid)
 
 
+def _render_inputs(N, K, Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask):
+    Ld = _need(Ld, torch.float32, "Ld", (N, 3))
+    Ls0 = _need(Ls0, torch.float32, "Ls0", (N, K, 3))
+    Ls1 = _need(Ls1, torch.float32, "Ls1", (N, K, 3))
+    albedo = _need(albedo, torch.float32, "albedo", (N, 3))
+    rough = _need(rough, torch.float32, "rough", (N,))
+    metal = _need(metal, torch.float32, "metal", (N,))
+    if Lgt is not None:
+        Lgt = _need(Lgt, torch.float32, "Lgt", (N, 3))
+    if mask is not None:
+        mask = _need(mask, torch.uint8, "mask", (N,))
+    return Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask
+
+
 def render_fwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt=None, mask=None, stream=None,
                Lr=None):
     """Eq. 5 + Eq. 8 -> Lr [N,3]; with Lgt also the Eq. 14 loss (float64 [1])."""
     N = Ld.shape[0]
     g, K = _grid(sigma_grid)
+    Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask = _render_inputs(N, K, Ld, Ls0, Ls1, albedo, rough,
+                                                                   metal, Lgt, mask)
     if Lr is None:
         Lr = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
+    elif not (Lr.is_cuda and Lr.dtype == torch.float32 and tuple(Lr.shape) == (N, 3) and Lr.is_contiguous()):
+        raise ValueError("Lr must be a contiguous CUDA float32 [N, 3] tensor")
     loss = torch.zeros(1, dtype=torch.float64, device=Ld.device) if Lgt is not None else None
     nbytes = ctypes.c_size_t()
     check(lib().fipt_render_workspace_size(N, ctypes.byref(nbytes)))
@@ -347,6 +393,12 @@ def render_bwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask=None, g
     """d loss / d (albedo, rough, metal), scaled by grad_loss (float64 device scalar)."""
     N = Ld.shape[0]
     g, K = _grid(sigma_grid)
+    if Lgt is None:
+        raise ValueError("render_bwd needs Lgt")
+    Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask = _render_inputs(N, K, Ld, Ls0, Ls1, albedo, rough,
+                                                                   metal, Lgt, mask)
+    if grad_loss is not None:
+        grad_loss = _need(grad_loss, torch.float64, "grad_loss", (1,))
     ga = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
     gr = torch.empty(N, dtype=torch.float32, device=Ld.device)
     gm = torch.empty(N, dtype=torch.float32, device=Ld.device)
@@ -390,10 +442,15 @@ def tri_error(tri, Lr, Lgt, T, stream=None, tri_stride=1):
     ``tri`` is an int32 tensor of pixel triangle ids, or a [P,10] query tensor
     (its triangle field is read in place, tri_stride = 10)."""
     if tri.dtype == torch.float32 and tri.dim() == 2 and tri.shape[1] == 10:
+        tri = _queries(tri, "tri")
         P, tri_stride = tri.shape[0], 10
         tri = tri[:, 9:10]
     else:
         P = tri.shape[0]
+        tri = _need(tri, torch.int32, "tri", (P,))
+        tri_stride = 1
+    Lr = _need(Lr, torch.float32, "Lr", (P, 3))
+    Lgt = _need(Lgt, torch.float32, "Lgt", (P, 3))
     nbytes = ctypes.c_size_t()
     check(lib().fipt_tri_error_workspace_size(P, int(T), ctypes.byref(nbytes)))
     _b, ws = _workspace(nbytes.value, tri.device)
@@ -462,6 +519,8 @@ def extract_emitters(scene: Scene, alpha_fn, pixel_tri, pixel_rgb, n_per_tri=100
 def philox(ctr, key, stream=None):
     """Device Philox4x32-10: ctr [n,4], key [n,2] (int32 tensors holding u32 bits)."""
     n = ctr.shape[0]
+    ctr = _need(ctr, torch.int32, "ctr", (n, 4))
+    key = _need(key, torch.int32, "key", (n, 2))
     out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
     check(lib().fipt_debug_philox(_ptr(ctr), _ptr(key), n, _ptr(out), _stream(stream)))
     return out
@@ -509,8 +568,8 @@ class Server:
     def submit_bake(self, scene_id, queries, sigma, spp_diffuse, spp_specular=None, seed=0,
                     request_id=0):
         """queries: CPU float32 [n,10] (pinned for overlap).  Returns a ticket."""
-        q = queries.contiguous()
-        n, K = q.shape[0], len(sigma)
+        n, K = queries.shape[0], len(sigma)
+        q = _host(queries, torch.float32, "queries", (n, 10))
         out = {"Ld": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
                "Ls0": torch.empty((n, K, 3), dtype=torch.float32, pin_memory=True),
                "Ls1": torch.empty((n, K, 3), dtype=torch.float32, pin_memory=True)}
@@ -523,8 +582,9 @@ class Server:
 
     def submit_render(self, table_id, first, albedo, rough, metal, Lgt):
         """Render fwd/bwd over table rows [first, first+n); host tensors in."""
-        ins = [x.contiguous() for x in (albedo, rough, metal, Lgt)]
-        n = ins[0].shape[0]
+        n = albedo.shape[0]
+        ins = [_host(albedo, torch.float32, "albedo", (n, 3)), _host(rough, torch.float32, "rough", (n,)),
+               _host(metal, torch.float32, "metal", (n,)), _host(Lgt, torch.float32, "Lgt", (n, 3))]
         out = {"Lr": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
                "loss": torch.zeros(1, dtype=torch.float64, pin_memory=True),
                "g_albedo": torch.empty((n, 3), dtype=torch.float32, pin_memory=True),
