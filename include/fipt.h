@@ -323,9 +323,9 @@ fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1,
                             size_t ws_bytes, fipt_stream stream);
 
 /* fipt_render_fwd without a workspace, for callers that cannot allocate
- * device memory when they render (inside CUDA-graph capture, with a fixed
- * start-up memory pool, or on threads that must not take an allocator
- * lock).  The paper has no counterpart; this is a library convenience.
+ * device memory when they render (their device memory is a fixed pool
+ * sized at start-up, or they run on threads that must not take an
+ * allocator's lock).  The paper has no counterpart; this is a library convenience.
  * Same arguments and results as fipt_render_fwd; the loss partial sums live
  * in a 512 KiB array compiled into the library, present on every GPU that
  * loads it until the process exits.  N may be at most

@@ -253,7 +253,6 @@ extern "C" fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const 
 
 // ---------------------------------------------------------------- no-allocation variant
 // Some callers cannot allocate device memory at the point where they render:
-// code running while a CUDA graph is being captured around a training step,
 // callers whose memory comes from a fixed pool sized at start-up (embedded or
 // real-time services), or threads that must not take the allocator's lock.
 // fipt_render_fwd needs a caller workspace for its loss partial sums; this

@@ -1,6 +1,7 @@
 """fipt_render_fwd_noalloc: the render forward for callers that cannot
-allocate device memory while they render (for example code running under
-CUDA-graph capture, or a service whose memory is a fixed start-up pool).
+allocate device memory while they render (for example a service whose
+device memory is a fixed pool sized at start-up, or a thread that must not
+take an allocator's lock).
 Its loss partial sums live in a fixed array inside the library instead of a
 caller workspace.  Checked through the C ABI against fipt_render_fwd, on two
 calls in a row (the second call reuses the array the first one left behind).
