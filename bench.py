@@ -580,7 +580,8 @@ def run_refine(args, F, dev, mesh, sc, q_all, with_cpu):
            "rays_per_sample": round(n_rays / samples, 3), "mrays_per_s": round(n_rays / t / 1e6, 1),
            "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2), "max_stack": max_sp,
            "roofline": {"bound": "hbm", "achieved": round(alg / t / 1e9, 1), "peak": peak, "unit": "GB/s",
-                        "frac": round(alg / t / 1e9 / peak, 4), "kernel": "k_refine", "peak_kind": peak_kind}}
+                        "frac": round(alg / t / 1e9 / peak, 4), "peak_kind": peak_kind,
+                        "kernel": "whole call: k_rf_gen, k_rf_trace, k_rf_shade, k_rf_reduce"}}
     if with_cpu:
         import oracle as O
         cams = pinhole_views_for(mesh)

@@ -292,17 +292,29 @@ fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, con
  * Philox counters: lobe direction at x (pid, s, lobe, rid); emitter sample
  * at x (pid, s, lobe|0x100, rid); BRDF at vertex i (pid, s, lobe|i<<9, rid);
  * emitter sample at vertex i (pid, s, lobe|i<<9|0x100, rid).
- * Outputs as fipt_bake; per_sample (nullable, device f32
- * [N, 1+K, max(spp), 6]) receives every sample's contribution (L_d uses the
- * first 3 values, L_s0 / L_s1 the two triples).  params->stats (NULL, or
- * 4 device u64 counters) receives, added, the rays traced (path segments
- * and shadow rays), nodes visited and triangles tested, and the deepest
- * stack (max); it cannot be combined with per_sample.  Requires
- * fipt_scene_set_materials. */
+ * Outputs as fipt_bake: each value is the mean of its samples' values,
+ * summed in sample order.  per_sample (nullable, device f32
+ * [N, 1+K, max(spp), 6]) receives every sample's value (L_d uses the first
+ * 3 values, L_s0 / L_s1 the two triples; zeros past a lobe's sample
+ * count).  params->stats (NULL, or 4 device u64 counters) receives, added,
+ * the rays traced (path segments and shadow rays), nodes visited and
+ * triangles tested, and the deepest stack (max).  Requires
+ * fipt_scene_set_materials.
+ * workspace: device, 256-byte aligned, at least the bytes
+ * fipt_bake_refine_workspace_size gives for the same N, params and
+ * max_depth (the path state of up to 4,194,304 samples at a time, 184
+ * bytes each; larger calls run in chunks of whole points); owned by the
+ * caller, in use until the stream reaches the end of the call.
+ * spp_diffuse + K * spp_specular above 4,194,304 is FIPT_ERR_INVALID_ARG;
+ * a workspace below the size is FIPT_ERR_WORKSPACE.  max_depth > 15 makes
+ * the call wait for the stream every 16 path depths to stop once every
+ * path has ended. */
+fipt_status fipt_bake_refine_workspace_size(int64_t N, const fipt_bake_params* params,
+                                            int32_t max_depth, size_t* bytes);
 fipt_status fipt_bake_refine(fipt_scene* scene, const fipt_query* q, int64_t N,
                              const fipt_bake_params* params, float sigma_c, int32_t max_depth,
                              int32_t mis, float* Ld, float* Ls0, float* Ls1, float* per_sample,
-                             fipt_stream stream);
+                             void* workspace, size_t ws_bytes, fipt_stream stream);
 
 /* ------------------------------------------------------------ render */
 /* Factorized render, Eq. 5 with k_d = a(1-m), k_s = 0.04(1-m) + a m (Eq. 1)

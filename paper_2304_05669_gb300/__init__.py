@@ -342,9 +342,12 @@ def bake_refine(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, sigma_c=
     ps = (torch.empty((N, K + 1, max(spp_diffuse, spp_s), 6), dtype=torch.float32, device=q.device)
           if per_sample else None)
     p = bake_params(sigma, spp_diffuse, spp_s, seed, request_id, point_base, stats)
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_bake_refine_workspace_size(N, ctypes.byref(p), int(max_depth), ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, q.device)
     check(lib().fipt_bake_refine(scene.handle, _ptr(q), N, ctypes.byref(p), float(sigma_c),
                                  int(max_depth), int(bool(mis)), _ptr(out[0]), _ptr(out[1]),
-                                 _ptr(out[2]), _ptr(ps), _stream(stream)))
+                                 _ptr(out[2]), _ptr(ps), _ptr(ws), nbytes.value, _stream(stream)))
     return out + ((ps,) if per_sample else ())
 
 

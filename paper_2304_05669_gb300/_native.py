@@ -77,7 +77,8 @@ SIGNATURES = {
     "fipt_emitter_radiance_workspace_size": [I64, I64, P],
     "fipt_emitter_radiance": [P, I64, P, I64, P, I64, P, P, P, SZ, P],
     "fipt_scene_set_emission": [P, P, P],
-    "fipt_bake_refine": [P, P, I64, ctypes.POINTER(BakeParams), F32, I32, I32, P, P, P, P, P],
+    "fipt_bake_refine_workspace_size": [I64, ctypes.POINTER(BakeParams), I32, P],
+    "fipt_bake_refine": [P, P, I64, ctypes.POINTER(BakeParams), F32, I32, I32, P, P, P, P, P, SZ, P],
     "fipt_server_create": [P, SZ, I64, I64, P],
     "fipt_server_add_scene": [P, P, P],
     "fipt_server_add_table": [P, P, P, P, I64, I32, P, P],

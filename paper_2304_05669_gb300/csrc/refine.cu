@@ -15,18 +15,49 @@
 // At a vertex the diffuse lobe is drawn with probability
 // P_d = clamp(mean(k_d) / (mean(k_d) + mean(k_s)), 0.1, 0.9); vertices seen
 // at n.wo <= 1e-2 drop the specular lobe (P_d = 1).
+//
+// Organisation (wavefront path tracing, Laine, Karras and Aila 2013).  One
+// slot per sample (point, lobe, s); a chunk of at most FIPT_RF_SLOT_CAP
+// slots keeps its path state in the caller's workspace, 16-byte records
+// per slot.  Per chunk:
+//   k_rf_gen     sets up every slot at its query point: the emitter sample
+//                at x (a shadow ray) and the lobe sample (the first path
+//                segment), and queues both rays;
+//   k_rf_trace   closest hit of every queued ray: a persistent kernel whose
+//                warps draw rays from the queue and walk the tree with the
+//                stage-1 bake's speculative, warp-refilled traversal;
+//   k_rf_shade   consumes a slot's hits (the shadow ray first, then the
+//                path segment), and at a smooth surface queues the vertex's
+//                shadow ray and its next segment together (the BRDF sample
+//                does not depend on the shadow ray's outcome);
+//   k_rf_reduce  sums each (point, lobe)'s samples in sample order.
+// trace + shade run once per path depth (max_depth + 1 times).  Every
+// slot's arithmetic is the same sequence whatever the queue order, so the
+// results do not depend on scheduling.  The traversal kernel carries only
+// a ray; the shading state stays in HBM, and each kernel runs its lanes
+// through one kind of work.
 #include "fipt_internal.cuh"
 
 namespace {
 
-#ifndef FIPT_REFINE_THREADS
-#define FIPT_REFINE_THREADS 64   // small blocks: the shared stack bounds residency
+#ifndef FIPT_RF_TRACE_THREADS
+#define FIPT_RF_TRACE_THREADS 64     // small blocks: the shared stack bounds residency
 #endif
-#ifndef FIPT_REFINE_MINB
-#define FIPT_REFINE_MINB 20      // resident blocks per SM the register budget must allow
+#ifndef FIPT_RF_TRACE_MINB
+#define FIPT_RF_TRACE_MINB 24        // resident traversal blocks per SM (40 registers)
 #endif
-constexpr int REFINE_THREADS = FIPT_REFINE_THREADS;
-constexpr int REFINE_MINB = FIPT_REFINE_MINB;
+#ifndef FIPT_RF_REFILL
+#define FIPT_RF_REFILL 24            // idle lanes that make a warp draw new rays
+#endif
+#ifndef FIPT_RF_SLOT_CAP
+#define FIPT_RF_SLOT_CAP (1 << 22)   // samples per chunk
+#endif
+#ifndef FIPT_RF_SHADE_MINB
+#define FIPT_RF_SHADE_MINB 1         // resident shading blocks per SM the register budget must allow
+#endif
+constexpr int RF_TRACE_THREADS = FIPT_RF_TRACE_THREADS;
+constexpr int RF_SHADE_THREADS = 256;
+constexpr int64_t RF_SLOT_CAP = FIPT_RF_SLOT_CAP;
 constexpr float PI_F = 3.14159265358979f;
 
 struct RefineArgs {
@@ -35,6 +66,7 @@ struct RefineArgs {
     int max_depth;
     int mis;
     int smax;               // stride of the per-sample output
+    int per_pt;             // samples per point: spp_d + K * spp_s
 };
 
 __device__ __forceinline__ float ggx_d(float sin2, float cos2, float a2) {
@@ -161,58 +193,73 @@ __device__ __forceinline__ float3 to_world(float3 t, float3 b, float3 n, float x
                        x * t.z + y * b.z + z * n.z);
 }
 
-// Lane state machine of the refinement.  A lane owns one (point, lobe) pair
-// and walks its samples in order; each sample traces, one ray at a time:
-//   K_S0   the shadow ray of the emitter sample at x (MIS only),
-//   K_PATH a path segment (the lobe sample at x, then BRDF samples),
-//   K_SV   the shadow ray of the emitter sample at a path vertex; the
-//          vertex's BRDF sample (the next K_PATH) is drawn after it.
-// All rays go through the single traversal loop of k_refine, so lanes in
-// different states still walk the BVH together; a lane whose ray finished
-// waits until FIPT_REFINE_REFILL lanes (or all busy lanes) are waiting, and
-// the waiting lanes then consume their hits and set up their next rays
-// together, as the stage-1 bake does.  Shadow rays stop looking beyond the
-// sampled emitter point (only whether that emitter is the closest hit
-// matters).
-enum : int { K_NONE = 0, K_S0 = 1, K_PATH = 2, K_SV = 3 };
-enum : int { A_START, A_MAIN, A_VERTEX_BSDF, A_END_PATH, A_END_SAMPLE, A_RAY };
+// ---------------------------------------------------------------- path state
+// Flags word of a slot: bits 0-15 the path depth (segments issued), then
+// whether a path segment or a shadow ray is queued, whether that shadow ray
+// starts at the query point (its weights then go to the sample's value, not
+// to the path radiance), and whether the path is live (its radiance not
+// yet added to the sample's value).
+constexpr uint32_t F_DEPTH = 0xffffu;
+constexpr uint32_t F_PATH = 1u << 16, F_SHADOW = 1u << 17, F_AT_X = 1u << 18, F_LIVE = 1u << 19;
 
-#ifndef FIPT_REFINE_REFILL
-#define FIPT_REFINE_REFILL 24    // lanes that must be waiting before a warp sets up new rays
-#endif
+struct RfState {
+    float4* org;        // [P] origin of the slot's rays (xyz), the triangle they skip (int bits)
+    float4* dir;        // [2P] ray 2j: path segment, 2j+1: shadow ray; direction (xyz), t_max
+    int4* hit;          // [2P] t (float bits), leaf (-1: none), original triangle id, front face
+    float4* bp;         // [P] path throughput (rgb), pdf of the last BRDF sample
+    float4* lw;         // [P] path radiance (rgb), W0
+    float4* c0;         // [P] sample value for L_d / L_s0 (rgb), W1
+    float4* c1;         // [P] sample value for L_s1 (rgb), flags (int bits)
+    float4* sw;         // [P] shadow-ray weights (rgb), target emitter leaf (int bits)
+    uint32_t* act[2];   // slots with queued rays, by wave parity
+    uint32_t* tq[2];    // queued ray ids, by wave parity
+    uint32_t* cnt;      // wave w: [4w] rays queued, [4w+1] rays taken, [4w+2] slots active
+};
 
-__device__ __forceinline__ void start_ray(TraceRay& r, BestHit& best, int& node, int& sp, int& steps,
-                                          const SceneView& sc, float ox, float oy, float oz, float dx,
-                                          float dy, float dz, float tmax) {
-    r = make_ray(ox, oy, oz, dx, dy, dz);
-    best.t = tmax;
-    best.leaf = -1;
-    best.orig = 0x7fffffff;
-    best.front = false;
-    sp = 0;
-    steps = 0;
-    node = sc.T > 0 ? 0 : FIPT_DONE;
+struct RfChunk {
+    const fipt_query* q;    // the chunk's first query
+    int64_t p0;             // index of that query in the call
+    int64_t n_pts;          // points in the chunk
+    int64_t P;              // slots: n_pts * per_pt
+};
+
+// (point within the chunk, lobe, sample) of slot j: a point's slots are its
+// spp_d diffuse samples, then spp_s samples of each roughness level.
+__device__ __forceinline__ void slot_decode(int64_t j, const RefineArgs& R, int64_t& pc, int& lobe,
+                                            int& s) {
+    pc = j / R.per_pt;
+    int r = (int)(j - pc * R.per_pt);
+    if (r < R.A.spp_d) {
+        lobe = 0;
+        s = r;
+    } else {
+        r -= R.A.spp_d;
+        lobe = 1 + r / R.A.spp_s;
+        s = r - (lobe - 1) * R.A.spp_s;
+    }
 }
 
-// STATS: an instrumented build of the same code that adds its rays, node
-// visits and triangle tests to stats[0..2] and raises stats[3] to its
-// deepest stack.
-template <bool PER_SAMPLE, bool STATS>
-__global__ void __launch_bounds__(REFINE_THREADS, REFINE_MINB)
-k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R, float* __restrict__ Ld,
-         float* __restrict__ Ls0, float* __restrict__ Ls1, float* __restrict__ per_sample,
-         int32_t* status, unsigned long long* stats) {
-    constexpr unsigned FULL = 0xffffffffu;
-    __shared__ int stk[STACK_DEPTH * REFINE_THREADS];
-    int* stack = stk + threadIdx.x;
+// Appends v to list for every lane with pred (one atomic per warp); all 32
+// lanes of the warp call it together.
+__device__ __forceinline__ void warp_append(uint32_t* list, uint32_t* count, bool pred, uint32_t v) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// ---------------------------------------------------------------- generation
+// Every slot at its query point: the emitter sample at x (MIS) and the
+// lobe sample of the stage-1 bake, queued as rays of wave 0.
+__global__ void __launch_bounds__(RF_SHADE_THREADS)
+k_rf_gen(SceneView sc, RfChunk C, RefineArgs R, RfState st) {
     const BakeArgs& A = R.A;
-    const int K = A.K, L = 1 + K;
-    const int64_t g = blockIdx.x * (int64_t)REFINE_THREADS + threadIdx.x;
-    const int64_t w = g >> 5;
-    const int lobe = (int)(w % L);
-    const int64_t p = (w / L) * 32 + (int)(g & 31);
-    if ((w / L) * 32 >= N) return;          // whole warp past the end
-    const bool valid = p < N;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * RF_SHADE_THREADS;
     const float eps = sc.cst->eps;
     const int n_emit = sc.cst->n_emit;
     const double A_emit = sc.cst->A_emit;
@@ -220,280 +267,91 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
     // the emitter choice compares FP64 cumulative areas (exact selection);
     // the area-measure pdfs dist^2 / (A cos) feed weights only, in FP32
     const float A_emit_f = (float)A_emit;
-    const uint32_t pid = A.point_base + (uint32_t)p;
-    float a2 = 0.0f;
-    if (lobe > 0) {
-        float sg = A.sigma[0];
-#pragma unroll
-        for (int k = 1; k < FIPT_MAX_K; ++k)
-            if (lobe - 1 == k) sg = A.sigma[k];
-        const float al = sg * sg;
-        a2 = al * al;
-    }
-    int S = 0;
-    if (valid) {
-        const float2* qp = reinterpret_cast<const float2*>(q + p);
-        const float2 q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
-        const float nl = 1.0f / sqrtf(q1.y * q1.y + q2.x * q2.x + q2.y * q2.y);
-        const float wl = 1.0f / sqrtf(q3.x * q3.x + q3.y * q3.y + q4.x * q4.x);
-        const float mu = (q1.y * nl) * (q3.x * wl) + (q2.x * nl) * (q3.y * wl) + (q2.y * nl) * (q4.x * wl);
-        // specular terms of points seen at grazing angles are defined as zero
-        S = (lobe > 0 && mu <= 1e-2f) ? 0 : (lobe == 0 ? A.spp_d : A.spp_s);
-    }
-
-    // per-lane path state
-    int kind = K_NONE, s = 0, depth = 0, skip = -1, tgt = -1, vleaf = -1;
-    float dx = 0.0f, dy = 0.0f, dz = 1.0f;            // current path direction
-    float b0 = 1.0f, b1 = 1.0f, b2 = 1.0f;            // path throughput
-    float l0 = 0.0f, l1 = 0.0f, l2 = 0.0f;            // path radiance
-    float W0 = 1.0f, W1 = 0.0f, pdf_prev = 0.0f;
-    float sw0 = 0.0f, sw1 = 0.0f, sw2 = 0.0f;         // shadow-ray weights
-    float a0 = 0.0f, a1 = 0.0f, a2s = 0.0f, a3 = 0.0f, a4 = 0.0f, a5 = 0.0f;   // sums over samples
-    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f, c4 = 0.0f, c5 = 0.0f;    // this sample (per-sample output)
-    TraceRay r;
-    BestHit best;
-    best.t = FINF;
-    best.leaf = -1;
-    best.orig = 0x7fffffff;
-    best.front = false;
-    r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
-    int node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
-    WalkStats ws;
-    unsigned long long n_rays = 0;
-
-#define FIPT_ADD6(cv, av, v)       \
-    do {                           \
-        if (PER_SAMPLE) cv += (v); \
-        else av += (v);            \
-    } while (0)
-
-    for (;;) {
-        const bool idle = node == FIPT_DONE && pleaf < 0;
-        const bool need = idle && (kind != K_NONE || s < S);
-        const unsigned m_need = __ballot_sync(FULL, need);
-        const unsigned m_busy = __ballot_sync(FULL, !idle);
-        if ((m_need | m_busy) == 0) break;
-        if (m_need != 0 && (m_busy == 0 || __popc(m_need) >= FIPT_REFINE_REFILL) && need) {
-            // ---------------- consume the finished ray
-            int act = A_START;
-            float xox = 0.0f, xoy = 0.0f, xoz = 0.0f;     // origin of a vertex's continuation
-            if (kind == K_S0) {
-                if (best.leaf == tgt) {
-                    const float4 le = __ldg(sc.shade + 2 * tgt);
-                    FIPT_ADD6(c0, a0, sw0 * le.x); FIPT_ADD6(c1, a1, sw0 * le.y); FIPT_ADD6(c2, a2s, sw0 * le.z);
-                    FIPT_ADD6(c3, a3, sw1 * le.x); FIPT_ADD6(c4, a4, sw1 * le.y); FIPT_ADD6(c5, a5, sw1 * le.z);
-                }
-                act = A_MAIN;
-            } else if (kind == K_SV) {
-                if (best.leaf == tgt) {
-                    const float4 le = __ldg(sc.shade + 2 * tgt);
-                    l0 += sw0 * le.x; l1 += sw1 * le.y; l2 += sw2 * le.z;
-                }
-                xox = r.ox; xoy = r.oy; xoz = r.oz;
-                act = A_VERTEX_BSDF;
-            } else if (kind == K_PATH) {
-                act = A_END_PATH;
-                if (best.leaf < 0) {
-                    if (sc.env) {
-                        const float3 e = env_lookup(sc, dx, dy, dz);
-                        l0 += b0 * e.x; l1 += b1 * e.y; l2 += b2 * e.z;
-                    }
-                } else {
-                    const int leaf = best.leaf;
-                    const float hx = r.ox + best.t * dx, hy = r.oy + best.t * dy, hz = r.oz + best.t * dz;
-                    const float4 le = __ldg(sc.shade + 2 * leaf);
-                    if (is_emitter(le)) {
-                        if (best.front) {
-                            float wgt = 1.0f;
-                            if (mis) {
-                                const float3 ne = leaf_normal(sc, leaf);
-                                const float ce = fabsf(dx * ne.x + dy * ne.y + dz * ne.z);
-                                const float pl = best.t * best.t / (A_emit_f * ce);
-                                wgt = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
-                            }
-                            l0 += b0 * wgt * le.x; l1 += b1 * wgt * le.y; l2 += b2 * wgt * le.z;
-                        }
-                    } else if (__ldg(&sc.mats[2 * leaf].w) > R.sigma_c) {
-                        float3 ca;
-                        if (sc.vox) {
-                            ca = voxel_lookup(sc, hx, hy, hz);
-                        } else {
-                            const float4 c4 = __ldg(sc.shade + 2 * leaf + 1);
-                            ca = make_float3(c4.x, c4.y, c4.z);
-                        }
-                        l0 += b0 * ca.x; l1 += b1 * ca.y; l2 += b2 * ca.z;
-                    } else if (depth <= R.max_depth) {
-                        // a smooth surface: a path vertex
-                        float3 nv = leaf_normal(sc, leaf);
-                        if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
-                        xox = hx + eps * nv.x; xoy = hy + eps * nv.y; xoz = hz + eps * nv.z;
-                        vleaf = leaf;
-                        skip = best.orig;
-                        act = A_VERTEX_BSDF;
-                        if (mis) {
-                            const float3 wv = make_float3(-dx, -dy, -dz);
-                            const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
-                            const Mat M = vertex_mat(sc, leaf, mu_v);
-                            float3 y;
-                            const uint32_t lc = (uint32_t)lobe | ((uint32_t)depth << 9) | 0x100u;
-                            const int e = emitter_sample(sc, n_emit, A_emit, u4(pid, (uint32_t)s, lc, A), y);
-                            float ex = y.x - xox, ey = y.y - xoy, ez = y.z - xoz;
-                            const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
-                            ex /= dist; ey /= dist; ez /= dist;
-                            const float3 ne = leaf_normal(sc, e);
-                            const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
-                            if (ce > 0.0f) {
-                                float f[3], pb;
-                                vertex_brdf(M, nv, wv, make_float3(ex, ey, ez), mu_v, f, pb);
-                                if (f[0] > 0.0f || f[1] > 0.0f || f[2] > 0.0f) {
-                                    const float pl = dist * dist / (A_emit_f * ce);
-                                    const float wgt = pl * pl / (pl * pl + pb * pb);
-                                    sw0 = b0 * wgt * f[0] / pl;
-                                    sw1 = b1 * wgt * f[1] / pl;
-                                    sw2 = b2 * wgt * f[2] / pl;
-                                    tgt = e;
-                                    start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, ex, ey, ez,
-                                              1.001f * dist + eps);
-                                    if (STATS) ++n_rays;
-                                    kind = K_SV;
-                                    act = A_RAY;
-                                }
-                            }
-                        }
-                    }
-                }
+    for (int64_t base = (int64_t)blockIdx.x * RF_SHADE_THREADS + (threadIdx.x & ~31); base < C.P;
+         base += stride) {
+        const int64_t j = base + lane;
+        bool qpath = false, qshadow = false;
+        if (j < C.P) {
+            int64_t pc;
+            int lobe, s;
+            slot_decode(j, R, pc, lobe, s);
+            const float2* qp = reinterpret_cast<const float2*>(C.q + pc);
+            const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
+            float3 n = make_float3(q1.y, q2.x, q2.y), wo = make_float3(q3.x, q3.y, q4.x);
+            {
+                const float il = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+                n = make_float3(n.x * il, n.y * il, n.z * il);
+                const float jl = 1.0f / sqrtf(wo.x * wo.x + wo.y * wo.y + wo.z * wo.z);
+                wo = make_float3(wo.x * jl, wo.y * jl, wo.z * jl);
             }
-            // ---------------- set up the next ray
-            while (act != A_RAY) {
-                if (act == A_VERTEX_BSDF) {            // BRDF sample at path vertex `depth`
-                    float3 nv = leaf_normal(sc, vleaf);
-                    if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
-                    const float3 wv = make_float3(-dx, -dy, -dz);
-                    const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
-                    const Mat M = vertex_mat(sc, vleaf, mu_v);
-                    const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe | ((uint32_t)depth << 9), A);
-                    float3 tb, bb;
-                    onb(nv.x, nv.y, nv.z, tb, bb);
-                    float3 wi, hh = make_float3(0.0f, 0.0f, 1.0f);
-                    float sin2h = 0.0f, sn, cs;
-                    sincospif(2.0f * u.y, &sn, &cs);
-                    const bool glossy = !(u.z < M.Pd);
-                    if (!glossy) {
-                        const float rr = sqrtf(u.x);
-                        wi = to_world(tb, bb, nv, rr * cs, rr * sn, sqrtf(1.0f - u.x));
-                    } else {
-                        const float om = 1.0f - u.x;
-                        const float den = om + M.a2 * u.x;
-                        sin2h = M.a2 * u.x / den;
-                        const float ch = sqrtf(om / den), sh = sqrtf(sin2h);
-                        hh = to_world(tb, bb, nv, sh * cs, sh * sn, ch);
-                        const float c = wv.x * hh.x + wv.y * hh.y + wv.z * hh.z;
-                        wi = make_float3(2.0f * c * hh.x - wv.x, 2.0f * c * hh.y - wv.y, 2.0f * c * hh.z - wv.z);
-                    }
-                    float f[3], pdf;
-                    vertex_brdf(M, nv, wv, wi, mu_v, f, pdf, glossy, hh, sin2h);
-                    if (pdf <= 0.0f) {
-                        act = A_END_PATH;
-                    } else {
-                        b0 *= f[0] / pdf; b1 *= f[1] / pdf; b2 *= f[2] / pdf;
-                        start_ray(r, best, node, sp, steps, sc, xox, xoy, xoz, wi.x, wi.y, wi.z, FINF);
-                        if (STATS) ++n_rays;
-                        dx = wi.x; dy = wi.y; dz = wi.z;
-                        pdf_prev = pdf;
-                        ++depth;
-                        kind = K_PATH;
-                        act = A_RAY;
-                        break;
-                    }
+            const float mu_o = n.x * wo.x + n.y * wo.y + n.z * wo.z;
+            // specular terms of points seen at grazing angles are defined as zero
+            const bool grazing = lobe > 0 && mu_o <= 1e-2f;
+            float4 C0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), C1 = C0;
+            uint32_t flags = 0;
+            if (!grazing) {
+                float a2 = 0.0f, g1o = 0.0f;
+                if (lobe > 0) {
+                    float sg = A.sigma[0];
+#pragma unroll
+                    for (int k = 1; k < FIPT_MAX_K; ++k)
+                        if (lobe - 1 == k) sg = A.sigma[k];
+                    const float al = sg * sg;
+                    a2 = al * al;
+                    g1o = smith_g1(mu_o, a2);
                 }
-                if (act == A_END_PATH) {
-                    FIPT_ADD6(c0, a0, W0 * l0); FIPT_ADD6(c1, a1, W0 * l1); FIPT_ADD6(c2, a2s, W0 * l2);
-                    FIPT_ADD6(c3, a3, W1 * l0); FIPT_ADD6(c4, a4, W1 * l1); FIPT_ADD6(c5, a5, W1 * l2);
-                    act = A_END_SAMPLE;
-                }
-                if (act == A_END_SAMPLE) {
-                    if (PER_SAMPLE) {
-                        float* ps = per_sample + ((size_t)(p * L + lobe) * R.smax + s) * 6;
-                        a0 += c0; a1 += c1; a2s += c2; a3 += c3; a4 += c4; a5 += c5;
-                        ps[0] = c0; ps[1] = c1; ps[2] = c2; ps[3] = c3; ps[4] = c4; ps[5] = c5;
-                    }
-                    ++s;
-                    act = A_START;
-                }
-                kind = K_NONE;
-                if (act == A_START && s >= S) break;  // this pair is done
-                // A_START or A_MAIN: the query point's frame
-                const float2* qp = reinterpret_cast<const float2*>(q + p);
-                const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
-                float3 n = make_float3(q1.y, q2.x, q2.y), wo = make_float3(q3.x, q3.y, q4.x);
-                {
-                    const float il = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
-                    n = make_float3(n.x * il, n.y * il, n.z * il);
-                    const float jl = 1.0f / sqrtf(wo.x * wo.x + wo.y * wo.y + wo.z * wo.z);
-                    wo = make_float3(wo.x * jl, wo.y * jl, wo.z * jl);
-                }
-                const float mu_o = n.x * wo.x + n.y * wo.y + n.z * wo.z;
+                const uint32_t pid = A.point_base + (uint32_t)(C.p0 + pc);
                 const float ox = q0.x + eps * n.x, oy = q0.y + eps * n.y, oz = q1.x + eps * n.z;
-                const float g1o = lobe > 0 ? smith_g1(mu_o, a2) : 0.0f;
-                if (act == A_START) {
-                    c0 = c1 = c2 = c3 = c4 = c5 = 0.0f;
-                    act = A_MAIN;
-                    if (mis) {                         // emitter sample at x
-                        float3 y;
-                        const int e = emitter_sample(sc, n_emit, A_emit,
-                                                     u4(pid, (uint32_t)s, (uint32_t)lobe | 0x100u, A), y);
-                        float ex = y.x - ox, ey = y.y - oy, ez = y.z - oz;
-                        const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
-                        ex /= dist; ey /= dist; ez /= dist;
-                        const float3 ne = leaf_normal(sc, e);
-                        const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
-                        const float mu_i = n.x * ex + n.y * ey + n.z * ez;
-                        float g0 = 0.0f, g1 = 0.0f, pb = 0.0f;
-                        if (ce > 0.0f && mu_i > 0.0f) {
-                            if (lobe == 0) {
-                                g0 = mu_i / PI_F;
-                                pb = g0;
-                            } else {
-                                float hx = ex + wo.x, hy = ey + wo.y, hz = ez + wo.z;
-                                const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
-                                hx *= hl; hy *= hl; hz *= hl;
-                                const float ch = n.x * hx + n.y * hy + n.z * hz;
-                                const float c = wo.x * hx + wo.y * hy + wo.z * hz;
-                                if (ch > 0.0f && c > 0.0f) {
-                                    const float D = ggx_d(sin2_between(n, hx, hy, hz), ch * ch, a2);
-                                    const float G = smith_g1(mu_i, a2) * g1o;
-                                    const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
-                                    g0 = (1.0f - F1) * D * G / (4.0f * mu_o);
-                                    g1 = F1 * D * G / (4.0f * mu_o);
-                                    pb = D * ch / (4.0f * c);
-                                }
+                st.org[j] = make_float4(ox, oy, oz, q4.y);         // q4.y: the query's triangle
+                if (mis) {                                          // emitter sample at x
+                    float3 y;
+                    const int e = emitter_sample(sc, n_emit, A_emit,
+                                                 u4(pid, (uint32_t)s, (uint32_t)lobe | 0x100u, A), y);
+                    float ex = y.x - ox, ey = y.y - oy, ez = y.z - oz;
+                    const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                    ex /= dist; ey /= dist; ez /= dist;
+                    const float3 ne = leaf_normal(sc, e);
+                    const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
+                    const float mu_i = n.x * ex + n.y * ey + n.z * ez;
+                    float g0 = 0.0f, g1 = 0.0f, pb = 0.0f;
+                    if (ce > 0.0f && mu_i > 0.0f) {
+                        if (lobe == 0) {
+                            g0 = mu_i / PI_F;
+                            pb = g0;
+                        } else {
+                            float hx = ex + wo.x, hy = ey + wo.y, hz = ez + wo.z;
+                            const float hl = 1.0f / sqrtf(hx * hx + hy * hy + hz * hz);
+                            hx *= hl; hy *= hl; hz *= hl;
+                            const float ch = n.x * hx + n.y * hy + n.z * hz;
+                            const float c = wo.x * hx + wo.y * hy + wo.z * hz;
+                            if (ch > 0.0f && c > 0.0f) {
+                                const float D = ggx_d(sin2_between(n, hx, hy, hz), ch * ch, a2);
+                                const float G = smith_g1(mu_i, a2) * g1o;
+                                const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
+                                g0 = (1.0f - F1) * D * G / (4.0f * mu_o);
+                                g1 = F1 * D * G / (4.0f * mu_o);
+                                pb = D * ch / (4.0f * c);
                             }
                         }
-                        if (g0 > 0.0f || g1 > 0.0f) {
-                            const float pl = dist * dist / (A_emit_f * ce);
-                            const float wgt = pl * pl / (pl * pl + pb * pb);
-                            sw0 = wgt * g0 / pl;
-                            sw1 = wgt * g1 / pl;
-                            tgt = e;
-                            skip = __float_as_int(q4.y);
-                            start_ray(r, best, node, sp, steps, sc, ox, oy, oz, ex, ey, ez, 1.001f * dist + eps);
-                            if (STATS) ++n_rays;
-                            kind = K_S0;
-                            act = A_RAY;
-                            break;
-                        }
+                    }
+                    if (g0 > 0.0f || g1 > 0.0f) {
+                        const float pl = dist * dist / (A_emit_f * ce);
+                        const float wgt = pl * pl / (pl * pl + pb * pb);
+                        st.sw[j] = make_float4(wgt * g0 / pl, wgt * g1 / pl, 0.0f, __int_as_float(e));
+                        st.dir[2 * j + 1] = make_float4(ex, ey, ez, 1.001f * dist + eps);
+                        flags |= F_SHADOW | F_AT_X;
+                        qshadow = true;
                     }
                 }
-                // A_MAIN: the lobe sample at x (the stage-1 sampler)
+                // the lobe sample at x (the stage-1 sampler)
                 const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe, A);
                 float3 tb, bb;
                 onb(n.x, n.y, n.z, tb, bb);
                 float sn, cs;
                 sincospif(2.0f * u.y, &sn, &cs);
                 float3 wi;
-                W0 = 1.0f;
-                W1 = 0.0f;
-                float pb = 0.0f;
+                float W0 = 1.0f, W1 = 0.0f, pb = 0.0f;
+                bool ok = true;
                 if (lobe == 0) {
                     const float rr = sqrtf(u.x), lz = sqrtf(1.0f - u.x);
                     wi = to_world(tb, bb, n, rr * cs, rr * sn, lz);
@@ -507,66 +365,380 @@ k_refine(SceneView sc, const fipt_query* __restrict__ q, int64_t N, RefineArgs R
                     const float c = wo.x * h.x + wo.y * h.y + wo.z * h.z;
                     wi = make_float3(2.0f * c * h.x - wo.x, 2.0f * c * h.y - wo.y, 2.0f * c * h.z - wo.z);
                     const float mu_i = n.x * wi.x + n.y * wi.y + n.z * wi.z;
-                    if (mu_i <= 0.0f || c <= 0.0f) {   // a zero sample
-                        act = A_END_SAMPLE;
-                        continue;
+                    if (mu_i <= 0.0f || c <= 0.0f) {    // a zero sample: no path
+                        ok = false;
+                    } else {
+                        const float wt = smith_g1(mu_i, a2) * g1o * c / (mu_o * ch);
+                        const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
+                        W0 = (1.0f - F1) * wt;
+                        W1 = F1 * wt;
+                        pb = ggx_d(sin2, cos2, a2) * ch / (4.0f * c);
                     }
-                    const float wt = smith_g1(mu_i, a2) * g1o * c / (mu_o * ch);
-                    const float x1 = 1.0f - c, x2 = x1 * x1, F1 = x2 * x2 * x1;
-                    W0 = (1.0f - F1) * wt;
-                    W1 = F1 * wt;
-                    pb = ggx_d(sin2, cos2, a2) * ch / (4.0f * c);
                 }
-                b0 = b1 = b2 = 1.0f;
-                l0 = l1 = l2 = 0.0f;
-                pdf_prev = pb;
-                depth = 1;
-                skip = __float_as_int(q4.y);
-                dx = wi.x; dy = wi.y; dz = wi.z;
-                start_ray(r, best, node, sp, steps, sc, ox, oy, oz, wi.x, wi.y, wi.z, FINF);
-                if (STATS) ++n_rays;
-                kind = K_PATH;
-                act = A_RAY;
+                if (ok) {
+                    st.dir[2 * j] = make_float4(wi.x, wi.y, wi.z, FINF);
+                    st.bp[j] = make_float4(1.0f, 1.0f, 1.0f, pb);
+                    st.lw[j] = make_float4(0.0f, 0.0f, 0.0f, W0);
+                    C0.w = W1;
+                    flags |= F_PATH | F_LIVE | 1u;
+                    qpath = true;
+                }
+            }
+            C1.w = __uint_as_float(flags);
+            st.c0[j] = C0;
+            st.c1[j] = C1;
+        }
+        warp_append(st.act[0], st.cnt + 2, qpath || qshadow, (uint32_t)j);
+        warp_append(st.tq[0], st.cnt + 0, qpath, (uint32_t)(2 * j));
+        warp_append(st.tq[0], st.cnt + 0, qshadow, (uint32_t)(2 * j + 1));
+    }
+}
+
+// ---------------------------------------------------------------- traversal
+// Closest hit of every ray queued for wave w.  Persistent: each warp draws
+// rays from the queue (one atomic per refill) whenever FIPT_RF_REFILL of
+// its lanes are idle, or all of them, and walks the tree with the stage-1
+// bake's speculative loop.  Shadow rays carry their t_max (just past the
+// sampled emitter point): only whether that emitter is the closest hit
+// matters.  STATS: an instrumented build that adds its rays, node visits
+// and triangle tests to stats[0..2] and raises stats[3] to its deepest
+// stack.
+template <bool STATS>
+__global__ void __launch_bounds__(RF_TRACE_THREADS, FIPT_RF_TRACE_MINB)
+k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long* stats) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ int stk[STACK_DEPTH * RF_TRACE_THREADS];
+    int* stack = stk + threadIdx.x;
+    const uint32_t* __restrict__ queue = st.tq[w & 1];
+    uint32_t* cnt = st.cnt + 4 * w;
+    const uint32_t n = cnt[0];
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    int rid = -1, skip = -1;
+    bool drained = false;
+    TraceRay r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
+    BestHit best;
+    best.t = FINF;
+    best.leaf = -1;
+    best.orig = 0x7fffffff;
+    best.front = false;
+    int node = FIPT_DONE, pleaf = -1, sp = 0, steps = 0;
+    WalkStats ws;
+    unsigned long long n_rays = 0;
+    for (;;) {
+        const bool idle = node == FIPT_DONE && pleaf < 0;
+        if (idle && rid >= 0) {
+            st.hit[rid] = make_int4(__float_as_int(best.t), best.leaf, best.orig, best.front ? 1 : 0);
+            rid = -1;
+        }
+        const bool need = idle && !drained;
+        const unsigned m_need = __ballot_sync(FULL, need);
+        const unsigned m_busy = __ballot_sync(FULL, !idle);
+        if ((m_need | m_busy) == 0) break;
+        if (m_need != 0 && (m_busy == 0 || __popc(m_need) >= FIPT_RF_REFILL)) {
+            const int leader = __ffs(m_need) - 1;
+            uint32_t b = 0;
+            if (lane == leader) b = atomicAdd(cnt + 1, (uint32_t)__popc(m_need));
+            b = __shfl_sync(FULL, b, leader);
+            if (need) {
+                const uint32_t i = b + __popc(m_need & ((1u << lane) - 1u));
+                if (i < n) {
+                    rid = (int)__ldg(queue + i);
+                    const float4 o = __ldg(st.org + (rid >> 1)), d = __ldg(st.dir + rid);
+                    r = make_ray(o.x, o.y, o.z, d.x, d.y, d.z);
+                    skip = __float_as_int(o.w);
+                    best.t = d.w;
+                    best.leaf = -1;
+                    best.orig = 0x7fffffff;
+                    best.front = false;
+                    sp = 0;
+                    steps = 0;
+                    node = sc.T > 0 ? 0 : FIPT_DONE;
+                    if (STATS) ++n_rays;
+                } else {
+                    drained = true;      // the queue is empty for good
+                }
             }
         }
-        // ---------------- inner nodes (speculative), then leaves
-        warp_walk<REFINE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
+        warp_walk<RF_TRACE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
     }
-#undef FIPT_ADD6
-
     if (STATS) {
         atomicAdd(&stats[0], n_rays);
         atomicAdd(&stats[1], ws.nodes);
         atomicAdd(&stats[2], ws.tris);
         atomicMax(&stats[3], (unsigned long long)ws.max_sp);
     }
-    if (!valid) return;
-    if (PER_SAMPLE) {
-        float* ps = per_sample + (size_t)(p * L + lobe) * R.smax * 6;
-        for (int i = S; i < R.smax; ++i)
-            for (int c = 0; c < 6; ++c) ps[i * 6 + c] = 0.0f;
+}
+
+// ---------------------------------------------------------------- shading
+// Every slot active in wave w: the shadow ray's emitter (if it was hit
+// first), then the path segment's hit: a miss (environment), an emitter
+// (L_e of the front face, MIS-weighted), a rough surface (L'), or a smooth
+// one, where the vertex's emitter sample and BRDF sample are queued for
+// wave w + 1.  A slot with nothing queued adds its path radiance
+// (W0, W1 times l) to its value and leaves the lists.
+__global__ void __launch_bounds__(RF_SHADE_THREADS, FIPT_RF_SHADE_MINB)
+k_rf_shade(SceneView sc, RfChunk C, RefineArgs R, RfState st, int w) {
+    const BakeArgs& A = R.A;
+    const int lane = threadIdx.x & 31;
+    const uint32_t* __restrict__ act = st.act[w & 1];
+    uint32_t* nact = st.act[(w + 1) & 1];
+    uint32_t* ntq = st.tq[(w + 1) & 1];
+    uint32_t* ncnt = st.cnt + 4 * (w + 1);
+    const int64_t n = st.cnt[4 * w + 2];
+    const int64_t stride = (int64_t)gridDim.x * RF_SHADE_THREADS;
+    const float eps = sc.cst->eps;
+    const int n_emit = sc.cst->n_emit;
+    const double A_emit = sc.cst->A_emit;
+    const bool mis = R.mis && n_emit > 0;
+    const float A_emit_f = (float)A_emit;
+    for (int64_t base = (int64_t)blockIdx.x * RF_SHADE_THREADS + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const int64_t i = base + lane;
+        bool qpath = false, qshadow = false;
+        uint32_t j = 0;
+        if (i < n) {
+            j = act[i];
+            int64_t pc;
+            int lobe, s;
+            slot_decode(j, R, pc, lobe, s);
+            const uint32_t pid = A.point_base + (uint32_t)(C.p0 + pc);
+            float4 C0 = st.c0[j], C1 = st.c1[j], LW = st.lw[j];
+            const uint32_t f_in = __float_as_uint(C1.w);
+            uint32_t depth = f_in & F_DEPTH;
+            uint32_t flags = f_in & F_LIVE;
+            if (f_in & F_SHADOW) {                      // the shadow ray queued last wave
+                const float4 SW = st.sw[j];
+                const int tgt = __float_as_int(SW.w);
+                if (st.hit[2 * j + 1].y == tgt) {
+                    const float4 le = __ldg(sc.shade + 2 * tgt);
+                    if (f_in & F_AT_X) {
+                        C0.x += SW.x * le.x; C0.y += SW.x * le.y; C0.z += SW.x * le.z;
+                        C1.x += SW.y * le.x; C1.y += SW.y * le.y; C1.z += SW.y * le.z;
+                    } else {
+                        LW.x += SW.x * le.x; LW.y += SW.y * le.y; LW.z += SW.z * le.z;
+                    }
+                }
+            }
+            if (f_in & F_PATH) {                        // the path segment queued last wave
+                const int4 h = st.hit[2 * j];
+                const float4 D = st.dir[2 * j];
+                float4 BP = st.bp[j];
+                const float dx = D.x, dy = D.y, dz = D.z;
+                if (h.y < 0) {
+                    if (sc.env) {
+                        const float3 e = env_lookup(sc, dx, dy, dz);
+                        LW.x += BP.x * e.x; LW.y += BP.y * e.y; LW.z += BP.z * e.z;
+                    }
+                } else {
+                    const int leaf = h.y;
+                    const float t = __int_as_float(h.x);
+                    const float4 O = st.org[j];
+                    const float hx = O.x + t * dx, hy = O.y + t * dy, hz = O.z + t * dz;
+                    const float4 le = __ldg(sc.shade + 2 * leaf);
+                    if (is_emitter(le)) {
+                        if (h.w) {
+                            float wgt = 1.0f;
+                            if (mis) {
+                                const float3 ne = leaf_normal(sc, leaf);
+                                const float ce = fabsf(dx * ne.x + dy * ne.y + dz * ne.z);
+                                const float pl = t * t / (A_emit_f * ce);
+                                wgt = BP.w * BP.w / (BP.w * BP.w + pl * pl);
+                            }
+                            LW.x += BP.x * wgt * le.x; LW.y += BP.y * wgt * le.y; LW.z += BP.z * wgt * le.z;
+                        }
+                    } else if (__ldg(&sc.mats[2 * leaf].w) > R.sigma_c) {
+                        float3 ca;
+                        if (sc.vox) {
+                            ca = voxel_lookup(sc, hx, hy, hz);
+                        } else {
+                            const float4 c4 = __ldg(sc.shade + 2 * leaf + 1);
+                            ca = make_float3(c4.x, c4.y, c4.z);
+                        }
+                        LW.x += BP.x * ca.x; LW.y += BP.y * ca.y; LW.z += BP.z * ca.z;
+                    } else if ((int)depth <= R.max_depth) {
+                        // a smooth surface: path vertex `depth`
+                        float3 nv = leaf_normal(sc, leaf);
+                        if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
+                        const float xox = hx + eps * nv.x, xoy = hy + eps * nv.y, xoz = hz + eps * nv.z;
+                        st.org[j] = make_float4(xox, xoy, xoz, __int_as_float(h.z));
+                        const float3 wv = make_float3(-dx, -dy, -dz);
+                        const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
+                        const Mat M = vertex_mat(sc, leaf, mu_v);
+                        const uint32_t lc = (uint32_t)lobe | (depth << 9);
+                        if (mis) {                      // emitter sample at the vertex
+                            float3 y;
+                            const int e = emitter_sample(sc, n_emit, A_emit, u4(pid, (uint32_t)s, lc | 0x100u, A), y);
+                            float ex = y.x - xox, ey = y.y - xoy, ez = y.z - xoz;
+                            const float dist = sqrtf(ex * ex + ey * ey + ez * ez);
+                            ex /= dist; ey /= dist; ez /= dist;
+                            const float3 ne = leaf_normal(sc, e);
+                            const float ce = -(ex * ne.x + ey * ne.y + ez * ne.z);
+                            if (ce > 0.0f) {
+                                float f[3], pb;
+                                vertex_brdf(M, nv, wv, make_float3(ex, ey, ez), mu_v, f, pb);
+                                if (f[0] > 0.0f || f[1] > 0.0f || f[2] > 0.0f) {
+                                    const float pl = dist * dist / (A_emit_f * ce);
+                                    const float wgt = pl * pl / (pl * pl + pb * pb);
+                                    st.sw[j] = make_float4(BP.x * wgt * f[0] / pl, BP.y * wgt * f[1] / pl,
+                                                           BP.z * wgt * f[2] / pl, __int_as_float(e));
+                                    st.dir[2 * j + 1] = make_float4(ex, ey, ez, 1.001f * dist + eps);
+                                    flags |= F_SHADOW;
+                                    qshadow = true;
+                                }
+                            }
+                        }
+                        // BRDF sample at the vertex
+                        const float4 u = u4(pid, (uint32_t)s, lc, A);
+                        float3 tb, bb;
+                        onb(nv.x, nv.y, nv.z, tb, bb);
+                        float3 wi, hh = make_float3(0.0f, 0.0f, 1.0f);
+                        float sin2h = 0.0f, sn, cs;
+                        sincospif(2.0f * u.y, &sn, &cs);
+                        const bool glossy = !(u.z < M.Pd);
+                        if (!glossy) {
+                            const float rr = sqrtf(u.x);
+                            wi = to_world(tb, bb, nv, rr * cs, rr * sn, sqrtf(1.0f - u.x));
+                        } else {
+                            const float om = 1.0f - u.x;
+                            const float den = om + M.a2 * u.x;
+                            sin2h = M.a2 * u.x / den;
+                            const float ch = sqrtf(om / den), sh = sqrtf(sin2h);
+                            hh = to_world(tb, bb, nv, sh * cs, sh * sn, ch);
+                            const float c = wv.x * hh.x + wv.y * hh.y + wv.z * hh.z;
+                            wi = make_float3(2.0f * c * hh.x - wv.x, 2.0f * c * hh.y - wv.y, 2.0f * c * hh.z - wv.z);
+                        }
+                        float f[3], pdf;
+                        vertex_brdf(M, nv, wv, wi, mu_v, f, pdf, glossy, hh, sin2h);
+                        if (pdf > 0.0f) {
+                            st.bp[j] = make_float4(BP.x * (f[0] / pdf), BP.y * (f[1] / pdf), BP.z * (f[2] / pdf), pdf);
+                            st.dir[2 * j] = make_float4(wi.x, wi.y, wi.z, FINF);
+                            ++depth;
+                            flags |= F_PATH;
+                            qpath = true;
+                        }
+                    }
+                }
+            }
+            if (!qpath && !qshadow && (flags & F_LIVE)) {   // the path is over
+                const float W0 = LW.w, W1 = C0.w;
+                C0.x += W0 * LW.x; C0.y += W0 * LW.y; C0.z += W0 * LW.z;
+                C1.x += W1 * LW.x; C1.y += W1 * LW.y; C1.z += W1 * LW.z;
+                flags &= ~F_LIVE;
+            }
+            C1.w = __uint_as_float(flags | depth);
+            st.c0[j] = C0;
+            st.c1[j] = C1;
+            st.lw[j] = LW;
+        }
+        warp_append(nact, ncnt + 2, qpath || qshadow, j);
+        warp_append(ntq, ncnt + 0, qpath, 2 * j);
+        warp_append(ntq, ncnt + 0, qshadow, 2 * j + 1);
     }
-    const float fs = (float)(S > 0 ? S : 1);
+}
+
+// ---------------------------------------------------------------- reduction
+// Each (point, lobe) of the chunk: the mean of its samples' values, summed
+// in sample order; PER_SAMPLE also writes every sample's value (zeros past
+// the lobe's sample count).
+template <bool PER_SAMPLE>
+__global__ void __launch_bounds__(RF_SHADE_THREADS)
+k_rf_reduce(RfChunk C, RefineArgs R, RfState st, float* __restrict__ Ld, float* __restrict__ Ls0,
+            float* __restrict__ Ls1, float* __restrict__ per_sample) {
+    const int K = R.A.K, L = 1 + K;
+    const int64_t t = blockIdx.x * (int64_t)RF_SHADE_THREADS + threadIdx.x;
+    if (t >= C.n_pts * L) return;
+    const int64_t pc = t / L;
+    const int lobe = (int)(t - pc * L);
+    const int64_t p = C.p0 + pc;
+    const int S = lobe == 0 ? R.A.spp_d : R.A.spp_s;
+    const int64_t j0 = pc * R.per_pt + (lobe == 0 ? 0 : R.A.spp_d + (int64_t)(lobe - 1) * R.A.spp_s);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f, a4 = 0.0f, a5 = 0.0f;
+    float* ps = PER_SAMPLE ? per_sample + (size_t)(p * L + lobe) * R.smax * 6 : nullptr;
+    for (int s = 0; s < S; ++s) {
+        const float4 x = st.c0[j0 + s], y = st.c1[j0 + s];
+        a0 += x.x; a1 += x.y; a2 += x.z;
+        a3 += y.x; a4 += y.y; a5 += y.z;
+        if (PER_SAMPLE) {
+            float* o = ps + (size_t)s * 6;
+            o[0] = x.x; o[1] = x.y; o[2] = x.z; o[3] = y.x; o[4] = y.y; o[5] = y.z;
+        }
+    }
+    if (PER_SAMPLE)
+        for (int s = S; s < R.smax; ++s)
+            for (int c = 0; c < 6; ++c) ps[(size_t)s * 6 + c] = 0.0f;
+    const float fs = (float)S;
     if (lobe == 0) {
         Ld[3 * p + 0] = a0 / fs;
         Ld[3 * p + 1] = a1 / fs;
-        Ld[3 * p + 2] = a2s / fs;
+        Ld[3 * p + 2] = a2 / fs;
     } else {
         float* o0 = Ls0 + (p * K + (lobe - 1)) * 3;
         float* o1 = Ls1 + (p * K + (lobe - 1)) * 3;
-        o0[0] = a0 / fs; o0[1] = a1 / fs; o0[2] = a2s / fs;
+        o0[0] = a0 / fs; o0[1] = a1 / fs; o0[2] = a2 / fs;
         o1[0] = a3 / fs; o1[1] = a4 / fs; o1[2] = a5 / fs;
     }
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+struct RfLayout {
+    RfState st;
+    size_t bytes;
+};
+
+RfLayout carve_refine(void* base, int64_t P, int waves) {
+    Carver c{static_cast<char*>(base), 0};
+    RfLayout L;
+    L.st.org = c.take<float4>(P);
+    L.st.dir = c.take<float4>(2 * P);
+    L.st.hit = c.take<int4>(2 * P);
+    L.st.bp = c.take<float4>(P);
+    L.st.lw = c.take<float4>(P);
+    L.st.c0 = c.take<float4>(P);
+    L.st.c1 = c.take<float4>(P);
+    L.st.sw = c.take<float4>(P);
+    L.st.act[0] = c.take<uint32_t>(P);
+    L.st.act[1] = c.take<uint32_t>(P);
+    L.st.tq[0] = c.take<uint32_t>(2 * P);
+    L.st.tq[1] = c.take<uint32_t>(2 * P);
+    L.st.cnt = c.take<uint32_t>(4 * (size_t)(waves + 1));
+    L.bytes = (c.off + 255) & ~size_t(255);
+    return L;
+}
+
+// Samples per point and points per chunk; false if one point's samples
+// exceed a chunk.
+bool refine_chunking(const fipt_bake_params* prm, int64_t N, int64_t& per_pt, int64_t& pts, int64_t& P) {
+    per_pt = (int64_t)prm->spp_diffuse + (int64_t)prm->K * prm->spp_specular;
+    if (per_pt > RF_SLOT_CAP) return false;
+    pts = RF_SLOT_CAP / per_pt;
+    P = (N < pts ? N : pts) * per_pt;
+    return true;
+}
+
 }  // namespace
+
+extern "C" fipt_status fipt_bake_refine_workspace_size(int64_t N, const fipt_bake_params* prm,
+                                                       int32_t max_depth, size_t* bytes) {
+    FIPT_REQUIRE(prm && bytes, "params / bytes is NULL");
+    FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 32), "bad point count %lld", (long long)N);
+    FIPT_REQUIRE(prm->K >= 1 && prm->K <= FIPT_MAX_K, "K must be in [1, %d]", FIPT_MAX_K);
+    FIPT_REQUIRE(prm->spp_diffuse >= 1 && prm->spp_specular >= 1, "spp must be >= 1");
+    FIPT_REQUIRE(max_depth >= 0 && max_depth < 4096, "max_depth must be in [0, 4096)");
+    int64_t per_pt, pts, P;
+    FIPT_REQUIRE(refine_chunking(prm, N, per_pt, pts, P),
+                 "spp_diffuse + K * spp_specular = %lld exceeds %lld samples per point", (long long)per_pt,
+                 (long long)RF_SLOT_CAP);
+    *bytes = N == 0 ? 0 : carve_refine(nullptr, P, max_depth + 1).bytes;
+    return FIPT_OK;
+}
 
 extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int64_t N,
                                         const fipt_bake_params* prm, float sigma_c, int32_t max_depth,
                                         int32_t mis, float* Ld, float* Ls0, float* Ls1,
-                                        float* per_sample, fipt_stream stream) {
+                                        float* per_sample, void* workspace, size_t ws_bytes,
+                                        fipt_stream stream) {
     FIPT_REQUIRE(s && prm, "scene / params is NULL");
     FIPT_REQUIRE(s->has_materials, "fipt_scene_set_materials must be called before a refinement");
     FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 32), "bad point count %lld", (long long)N);
@@ -575,11 +747,20 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
     FIPT_REQUIRE(max_depth >= 0 && max_depth < 4096, "max_depth must be in [0, 4096)");
     for (int k = 0; k < prm->K; ++k)
         FIPT_REQUIRE(prm->sigma[k] > 0.0f && prm->sigma[k] <= 1.0f, "sigma[%d] not in (0, 1]", k);
-    FIPT_REQUIRE(!(prm->stats && per_sample), "stats and per_sample cannot be combined");
+    int64_t per_pt, pts, P;
+    FIPT_REQUIRE(refine_chunking(prm, N, per_pt, pts, P),
+                 "spp_diffuse + K * spp_specular = %lld exceeds %lld samples per point", (long long)per_pt,
+                 (long long)RF_SLOT_CAP);
     if (N == 0) return FIPT_OK;
     FIPT_REQUIRE(q && Ld && Ls0 && Ls1, "NULL query / output array");
     FIPT_REQUIRE(fipt_aligned(q, 8) && fipt_aligned(Ld, 4) && fipt_aligned(Ls0, 4) &&
                  fipt_aligned(Ls1, 4) && fipt_aligned(per_sample, 4), "misaligned array");
+    const int waves = max_depth + 1;
+    RfLayout lay = carve_refine(nullptr, P, waves);
+    FIPT_REQUIRE(workspace && fipt_aligned(workspace, 256), "workspace must be 256-byte aligned");
+    if (ws_bytes < lay.bytes)
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "refine workspace %zu < %zu bytes", ws_bytes, lay.bytes);
+    lay = carve_refine(workspace, P, waves);
     FIPT_CUDA(cudaSetDevice(s->ctx->device));
     RefineArgs R;
     R.A.key = make_uint2((uint32_t)prm->seed, (uint32_t)(prm->seed >> 32));
@@ -593,17 +774,48 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
     R.max_depth = max_depth;
     R.mis = mis != 0;
     R.smax = prm->spp_diffuse > prm->spp_specular ? prm->spp_diffuse : prm->spp_specular;
-    const int64_t threads = ((N + 31) / 32) * (1 + prm->K) * 32;
+    R.per_pt = (int)per_pt;
+    const bool stats = prm->stats != nullptr;
+    int sms = 0, occ = 0;
+    FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->ctx->device));
+    FIPT_CUDA(stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rf_trace<true>, RF_TRACE_THREADS, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rf_trace<false>, RF_TRACE_THREADS, 0));
+    const unsigned trace_grid = (unsigned)(sms * (occ > 0 ? occ : 1));
+    const unsigned shade_grid = (unsigned)(sms * 8);
+    const SceneView sv = s->view();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (per_sample)
-        FIPT_LAUNCH((k_refine<true, false>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(),
-                    q, N, R, Ld, Ls0, Ls1, per_sample, s->ctx->status, nullptr);
-    else if (prm->stats)
-        FIPT_LAUNCH((k_refine<false, true>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st, s->view(),
-                    q, N, R, Ld, Ls0, Ls1, nullptr, s->ctx->status, prm->stats);
-    else
-        FIPT_LAUNCH((k_refine<false, false>), blocks(threads, REFINE_THREADS), REFINE_THREADS, 0, st,
-                    s->view(), q, N, R, Ld, Ls0, Ls1, nullptr, s->ctx->status, nullptr);
+    for (int64_t p0 = 0; p0 < N; p0 += pts) {
+        RfChunk C;
+        C.q = q + p0;
+        C.p0 = p0;
+        C.n_pts = N - p0 < pts ? N - p0 : pts;
+        C.P = C.n_pts * per_pt;
+        FIPT_CUDA(cudaMemsetAsync(lay.st.cnt, 0, sizeof(uint32_t) * 4 * (size_t)(waves + 1), st));
+        const unsigned gen_grid = blocks(C.P, RF_SHADE_THREADS) < shade_grid ? blocks(C.P, RF_SHADE_THREADS) : shade_grid;
+        FIPT_LAUNCH(k_rf_gen, gen_grid, RF_SHADE_THREADS, 0, st, sv, C, R, lay.st);
+        for (int w = 0; w < waves; ++w) {
+            if (w >= 16 && (w & 15) == 0) {    // deep limits: stop once no ray is queued
+                uint32_t queued = 0;
+                FIPT_CUDA(cudaMemcpyAsync(&queued, lay.st.cnt + 4 * w, sizeof(queued), cudaMemcpyDeviceToHost, st));
+                FIPT_CUDA(cudaStreamSynchronize(st));
+                if (queued == 0) break;
+            }
+            if (stats)
+                FIPT_LAUNCH(k_rf_trace<true>, trace_grid, RF_TRACE_THREADS, 0, st, sv, lay.st, w,
+                            s->ctx->status, prm->stats);
+            else
+                FIPT_LAUNCH(k_rf_trace<false>, trace_grid, RF_TRACE_THREADS, 0, st, sv, lay.st, w,
+                            s->ctx->status, nullptr);
+            FIPT_LAUNCH(k_rf_shade, shade_grid, RF_SHADE_THREADS, 0, st, sv, C, R, lay.st, w);
+        }
+        const unsigned red_grid = blocks(C.n_pts * (1 + prm->K), RF_SHADE_THREADS);
+        if (per_sample)
+            FIPT_LAUNCH(k_rf_reduce<true>, red_grid, RF_SHADE_THREADS, 0, st, C, R, lay.st, Ld, Ls0, Ls1,
+                        per_sample);
+        else
+            FIPT_LAUNCH(k_rf_reduce<false>, red_grid, RF_SHADE_THREADS, 0, st, C, R, lay.st, Ld, Ls0, Ls1,
+                        nullptr);
+    }
     FIPT_LAUNCHED("bake_refine");
     return FIPT_OK;
 }

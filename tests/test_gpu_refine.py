@@ -145,6 +145,55 @@ def test_refine_stats_counters(fipt):
         else:
             assert n_rays == bake_rays
         assert n_nodes > n_rays and 0 < max_sp <= 32
+    st = torch.zeros(4, dtype=torch.int64, device="cuda")
+    c = fipt.bake_refine(sc, qt, SIGMA, 16, 8, seed=3, per_sample=True, stats=st)
+    for x, y in zip(c, b):
+        assert torch.equal(x, y)
+    assert st[0].item() == n_rays
+
+
+def test_refine_chunks(fipt):
+    """A call larger than one chunk of samples equals its points refined in
+    separate calls (chunks are runs of whole points, the Philox counters
+    carry global point indices); one point whose samples exceed a chunk is
+    refused."""
+    m = cornell_box()
+    T = m.T
+    a, r, mt = np.full((T, 3), 0.5, np.float32), np.ones(T, np.float32), np.zeros(T, np.float32)
+    r[m.floor] = 0.05
+    sc = fipt.Scene.from_mesh(m)
+    sc.set_materials(cu(a), cu(r), cu(mt))
+    spp_d, spp_s = 4096, 2048                       # 4096 + 3 * 2048 = 10,240 samples per point
+    N = 600                                         # 6,144,000 samples: chunks of 409 points
+    q = surface_queries(m, N, seed=21)
+    qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+    whole = fipt.bake_refine(sc, qt, SIGMA, spp_d, spp_s, seed=5)
+    cut = 4194304 // (spp_d + 3 * spp_s)
+    parts = [fipt.bake_refine(sc, qt[lo:hi], SIGMA, spp_d, spp_s, seed=5, point_base=lo)
+             for lo, hi in ((0, cut), (cut, N))]
+    fipt.context().sync_status()
+    for k in range(3):
+        assert torch.equal(whole[k], torch.cat([parts[0][k], parts[1][k]]))
     with pytest.raises(fipt.FiptError):
-        fipt.bake_refine(sc, qt, SIGMA, 4, 4, per_sample=True, stats=torch.zeros(4, dtype=torch.int64,
-                                                                                  device="cuda"))
+        fipt.bake_refine(sc, qt[:4], SIGMA, 4194304, 1)  # 4,194,307 samples for one point
+
+
+def test_refine_deep_paths_match_oracle(fipt):
+    """Glossy walls (sigma = 0.3 < sigma_c) keep paths going until they
+    reach the light or leave through the open side; with max_depth = 40
+    some paths pass 16 vertices (the call then checks every 16 depths
+    whether any path is left, and must go on)."""
+    m = cornell_box()
+    T = m.T
+    a, r, mt = np.full((T, 3), 0.8, np.float32), np.full(T, 0.3, np.float32), np.zeros(T, np.float32)
+    q = surface_queries(m, 48, seed=22)
+    g, ora = run_both(fipt, m, q, a, r, mt, 4, max_depth=40)
+    print(check(g, ora, 0.5, 0.0))
+    sc = fipt.Scene.from_mesh(m)
+    sc.set_materials(cu(a), cu(r), cu(mt))
+    qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+    d16 = fipt.bake_refine(sc, qt, SIGMA, 4, 4, seed=3, request_id=1, max_depth=16)
+    d40 = fipt.bake_refine(sc, qt, SIGMA, 4, 4, seed=3, request_id=1, max_depth=40)
+    assert any(not torch.equal(x, y) for x, y in zip(d16, d40))
+    for x, y in zip(d40, (g["Ld"], g["Ls0"], g["Ls1"])):
+        assert np.array_equal(x.cpu().numpy(), y)
