@@ -302,10 +302,10 @@ fipt_status fipt_scene_set_materials(fipt_scene* scene, const float* albedo, con
  * fipt_scene_set_materials.
  * workspace: device, 256-byte aligned, at least the bytes
  * fipt_bake_refine_workspace_size gives for the same N, params and
- * max_depth (the path state of up to 4,194,304 samples at a time, 184
- * bytes each; larger calls run in chunks of whole points); owned by the
- * caller, in use until the stream reaches the end of the call.
- * spp_diffuse + K * spp_specular above 4,194,304 is FIPT_ERR_INVALID_ARG;
+ * max_depth (the path state of up to 16,777,216 samples at a time, 184
+ * bytes each, about 3.1 GB; larger calls run in chunks of whole points);
+ * owned by the caller, in use until the stream reaches the end of the call.
+ * spp_diffuse + K * spp_specular above 16,777,216 is FIPT_ERR_INVALID_ARG;
  * a workspace below the size is FIPT_ERR_WORKSPACE.  max_depth > 15 makes
  * the call wait for the stream every 16 path depths to stop once every
  * path has ended. */

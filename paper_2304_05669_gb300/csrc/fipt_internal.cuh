@@ -455,11 +455,12 @@ struct WalkStats {
 // then tested.  A lane whose walk is over has node == FIPT_DONE and
 // pleaf < 0; lanes without a ray call with that state and just vote.  All
 // 32 lanes of the warp must call it together.  `stack` is the lane's
-// column of the shared stack (entry k at stack[k * STRIDE]).
+// column of the shared stack (entry k at stack[k * STRIDE]).  A lane with
+// stop_on_hit ends its walk at the first triangle that improves `best`.
 template <int STRIDE, bool STATS, bool SPECULATE>
 __device__ __forceinline__ void warp_walk(const SceneView& sc, const TraceRay& r, int skip, BestHit& best,
                                           int& node, int& pleaf, int& sp, int& steps, int* stack,
-                                          int32_t* status, WalkStats& ws) {
+                                          int32_t* status, WalkStats& ws, bool stop_on_hit = false) {
     for (;;) {
         if (node >= 0 && (SPECULATE || pleaf < 0)) {
             if (node >= sc.n_inner || ++steps > sc.max_steps) {
@@ -519,6 +520,11 @@ __device__ __forceinline__ void warp_walk(const SceneView& sc, const TraceRay& r
                 best.leaf = leaf;
                 best.orig = orig;
                 best.front = fr;
+                if (stop_on_hit) {
+                    node = FIPT_DONE;
+                    sp = 0;
+                    break;
+                }
             }
         }
         if (node < 0 && node != FIPT_DONE) {      // the next entry is a leaf too

@@ -44,16 +44,16 @@ namespace {
 #define FIPT_RF_TRACE_THREADS 64     // small blocks: the shared stack bounds residency
 #endif
 #ifndef FIPT_RF_TRACE_MINB
-#define FIPT_RF_TRACE_MINB 24        // resident traversal blocks per SM (40 registers)
+#define FIPT_RF_TRACE_MINB 20        // resident traversal blocks per SM (48 registers)
 #endif
 #ifndef FIPT_RF_REFILL
 #define FIPT_RF_REFILL 24            // idle lanes that make a warp draw new rays
 #endif
 #ifndef FIPT_RF_SLOT_CAP
-#define FIPT_RF_SLOT_CAP (1 << 22)   // samples per chunk
+#define FIPT_RF_SLOT_CAP (1 << 24)   // samples per chunk (184 B of workspace each)
 #endif
 #ifndef FIPT_RF_SHADE_MINB
-#define FIPT_RF_SHADE_MINB 1         // resident shading blocks per SM the register budget must allow
+#define FIPT_RF_SHADE_MINB 3         // resident shading blocks per SM the register budget must allow
 #endif
 constexpr int RF_TRACE_THREADS = FIPT_RF_TRACE_THREADS;
 constexpr int RF_SHADE_THREADS = 256;
@@ -398,11 +398,21 @@ k_rf_gen(SceneView sc, RfChunk C, RefineArgs R, RfState st) {
 // Closest hit of every ray queued for wave w.  Persistent: each warp draws
 // rays from the queue (one atomic per refill) whenever FIPT_RF_REFILL of
 // its lanes are idle, or all of them, and walks the tree with the stage-1
-// bake's speculative loop.  Shadow rays carry their t_max (just past the
-// sampled emitter point): only whether that emitter is the closest hit
-// matters.  STATS: an instrumented build that adds its rays, node visits
-// and triangle tests to stats[0..2] and raises stats[3] to its deepest
-// stack.
+// bake's speculative loop.
+//
+// A shadow ray only asks whether its target emitter triangle is the
+// closest hit within t_max (just past the sampled point), ties going to the
+// lower triangle id.  The target is tested first, with the same watertight
+// test: if its (t, id) is not below (t_max, INT_MAX), or it is the skipped
+// triangle, no walk can make it the closest hit and the ray ends there.
+// Otherwise it seeds the closest hit and the walk stops at the first
+// triangle that improves on it (a blocker: the answer is no).  Culling
+// against the seeded t keeps every box that can hold a blocker, so the
+// answer is the one a full closest-hit walk gives; only the recorded leaf
+// of a blocked ray may differ (any blocker instead of the nearest).
+//
+// STATS: an instrumented build that adds its rays, node visits and
+// triangle tests to stats[0..2] and raises stats[3] to its deepest stack.
 template <bool STATS>
 __global__ void __launch_bounds__(RF_TRACE_THREADS, FIPT_RF_TRACE_MINB)
 k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long* stats) {
@@ -415,7 +425,7 @@ k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long*
     if (n == 0) return;
     const int lane = threadIdx.x & 31;
     int rid = -1, skip = -1;
-    bool drained = false;
+    bool drained = false, shadow = false;
     TraceRay r = make_ray(0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f);
     BestHit best;
     best.t = FINF;
@@ -455,12 +465,32 @@ k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long*
                     steps = 0;
                     node = sc.T > 0 ? 0 : FIPT_DONE;
                     if (STATS) ++n_rays;
+                    shadow = (rid & 1) != 0;
+                    if (shadow) {                  // settle the target first
+                        const int tgt = __float_as_int(__ldg(&st.sw[rid >> 1].w));
+                        const float4 p0 = __ldg(sc.tris + 3 * tgt);
+                        const int orig = __float_as_int(p0.w);
+                        float t;
+                        bool fr;
+                        if (STATS) ++ws.tris;
+                        if (orig != skip &&
+                            tri_intersect(r, p0, __ldg(sc.tris + 3 * tgt + 1), __ldg(sc.tris + 3 * tgt + 2), t, fr) &&
+                            (t < best.t || (t == best.t && orig < best.orig))) {
+                            best.t = t;
+                            best.leaf = tgt;
+                            best.orig = orig;
+                            best.front = fr;
+                        } else {
+                            node = FIPT_DONE;      // unlit whatever else the ray meets
+                        }
+                    }
                 } else {
                     drained = true;      // the queue is empty for good
                 }
             }
         }
-        warp_walk<RF_TRACE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws);
+        warp_walk<RF_TRACE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws,
+                                                 shadow);
     }
     if (STATS) {
         atomicAdd(&stats[0], n_rays);

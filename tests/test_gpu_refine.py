@@ -152,6 +152,9 @@ def test_refine_stats_counters(fipt):
     assert st[0].item() == n_rays
 
 
+CHUNK = 1 << 24        # samples per chunk of a refinement call (documented in fipt.h)
+
+
 def test_refine_chunks(fipt):
     """A call larger than one chunk of samples equals its points refined in
     separate calls (chunks are runs of whole points, the Philox counters
@@ -163,19 +166,20 @@ def test_refine_chunks(fipt):
     r[m.floor] = 0.05
     sc = fipt.Scene.from_mesh(m)
     sc.set_materials(cu(a), cu(r), cu(mt))
-    spp_d, spp_s = 4096, 2048                       # 4096 + 3 * 2048 = 10,240 samples per point
-    N = 600                                         # 6,144,000 samples: chunks of 409 points
+    spp_d, spp_s = 16384, 8192                      # 16384 + 3 * 8192 = 40,960 samples per point
+    N = 600                                         # 24,576,000 samples: two chunks
+    cut = CHUNK // (spp_d + 3 * spp_s)              # points in the first chunk
+    assert cut < N
     q = surface_queries(m, N, seed=21)
     qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
     whole = fipt.bake_refine(sc, qt, SIGMA, spp_d, spp_s, seed=5)
-    cut = 4194304 // (spp_d + 3 * spp_s)
     parts = [fipt.bake_refine(sc, qt[lo:hi], SIGMA, spp_d, spp_s, seed=5, point_base=lo)
              for lo, hi in ((0, cut), (cut, N))]
     fipt.context().sync_status()
     for k in range(3):
         assert torch.equal(whole[k], torch.cat([parts[0][k], parts[1][k]]))
     with pytest.raises(fipt.FiptError):
-        fipt.bake_refine(sc, qt[:4], SIGMA, 4194304, 1)  # 4,194,307 samples for one point
+        fipt.bake_refine(sc, qt[:4], SIGMA, CHUNK, 1)  # CHUNK + 3 samples for one point
 
 
 def test_refine_deep_paths_match_oracle(fipt):
