@@ -306,7 +306,9 @@ def run_reference(args, wl, world, rank):
 
 
 # ---------------------------------------------------------------- render workload
-RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12 + 12) + (12 + 72 + 72 + 12 + 4 + 4 + 12 + 20)
+# one pass: Ld, the two specular rows (K = 6), albedo, rough, metal, Lgt in;
+# Lr and the three gradients out
+RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12) + (12 + 12 + 4 + 4)
 
 
 def run_render(args, wl, world, rank, local):
@@ -340,9 +342,14 @@ def run_render(args, wl, world, rank, local):
     Lgt_host = Lgt.cpu().pin_memory()
     stream = torch.cuda.current_stream()
 
+    one = torch.ones(1, dtype=torch.float64, device=dev)     # d(step loss) / d(loss)
+
     def step(x, lg):
-        Lr, loss = F.render_fwd(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"], x["metal"], lg)
-        g = F.render_bwd(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"], x["metal"], lg)
+        # forward, loss and gradient in one pass over the inputs, then the
+        # upstream gradient applied (the library's backward of the loss)
+        Lr, loss, g = F.render_fwd_grad(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"],
+                                        x["metal"], lg)
+        F.render_grad_scale(g, one)
         return loss, g
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -424,7 +431,7 @@ def run_render(args, wl, world, rank, local):
                    "l2": "flushed between steps (512 MB write outside the timed events)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_render_fwd + k_render_bwd", "peak_kind": peak_kind,
+                     "kernel": "k_render_fwd_grad + k_render_grad_scale", "peak_kind": peak_kind,
                      "alg_bytes_per_pixel": RENDER_BYTES_PER_PX},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary(),
     }))
@@ -777,6 +784,7 @@ def run_ours(args, wl, world, rank, local):
     dv = {k: v.to(dev) for k, v in pinned.items()}
     gt_d = {k: torch.from_numpy(v).to(dev) for k, v in gt.items()}
     stream = torch.cuda.current_stream()
+    one = torch.ones(1, dtype=torch.float64, device=dev)     # d(step loss) / d(loss)
     ctx = F.context(local)
     request_id = rank
 
@@ -794,8 +802,9 @@ def run_ours(args, wl, world, rank, local):
             ev[1].record(stream)
         if Lgt is None:
             return sc, (Ld, Ls0, Ls1), q
-        Lr, loss = F.render_fwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
-        grads = F.render_bwd(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
+        # render forward, loss and gradient in one pass, then the upstream gradient
+        Lr, loss, grads = F.render_fwd_grad(Ld, Ls0, Ls1, SIGMA, d["albedo"], d["rough"], d["metal"], Lgt)
+        F.render_grad_scale(grads, one)
         err, cnt = F.tri_error(q, Lr, Lgt, mesh.T)
         if world > 1:        # the two sums over all ranks' pixels (one all-reduce each)
             global_loss(loss)

@@ -366,6 +366,27 @@ fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const float* Ls1,
                             const uint8_t* mask, const double* grad_loss, float* g_albedo,
                             float* g_rough, float* g_metal, fipt_stream stream);
 
+/* Forward, loss and gradient in one pass (one training step's render):
+ * writes Lr and *loss as fipt_render_fwd with the same Lgt and mask, and
+ * g_albedo [N,3], g_rough [N], g_metal [N] as fipt_render_bwd with
+ * grad_loss = NULL (an upstream gradient of 1), reading each input once
+ * instead of twice.  Lgt, loss, Lr and the gradient outputs are required;
+ * workspace as fipt_render_fwd (fipt_render_workspace_size bytes, 8-byte
+ * aligned, caller-owned).  Sec. 4.1, Eq. 5, 8, 14. */
+fipt_status fipt_render_fwd_grad(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                                 int32_t K, const float* sigma_grid, const float* albedo,
+                                 const float* rough, const float* metal, const float* Lgt,
+                                 const uint8_t* mask, float* Lr, double* loss, float* g_albedo,
+                                 float* g_rough, float* g_metal, void* workspace, size_t ws_bytes,
+                                 fipt_stream stream);
+
+/* Multiplies the gradients of fipt_render_fwd_grad in place by the
+ * upstream gradient *grad_loss (device f64 scalar, read on the device and
+ * rounded to f32 as fipt_render_bwd does); a factor of exactly 1 leaves
+ * them unchanged without touching them. */
+fipt_status fipt_render_grad_scale(int64_t N, const double* grad_loss, float* g_albedo,
+                                   float* g_rough, float* g_metal, fipt_stream stream);
+
 /* ------------------------------------------------------------ emitters */
 /* Per-triangle rendering error (Sec. 4.4: rendering without emission
  * leaves large error on emitters).  tri: first-hit triangle of each pixel

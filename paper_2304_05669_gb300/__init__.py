@@ -17,7 +17,8 @@ import torch
 from ._native import (BakeParams, FiptError, FIPT_MAX_K, Request, ServerStats, check, lib,
                       library_path)
 
-__all__ = ["Context", "Scene", "bake", "bake_refine", "render_fwd", "render_bwd", "FactorizedRender",
+__all__ = ["Context", "Scene", "bake", "bake_refine", "render_fwd", "render_bwd", "render_fwd_grad",
+           "render_grad_scale", "FactorizedRender",
            "factorized_render_loss", "tri_error", "compact_queries", "pack_queries",
            "unpack_queries", "philox", "emitter_classify", "emitter_radiance", "extract_emitters",
            "FiptError", "library_path", "context", "Server"]
@@ -411,14 +412,56 @@ def render_bwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask=None, g
     return ga, gr, gm
 
 
+def render_fwd_grad(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask=None, stream=None):
+    """Forward, loss and gradient in one pass -> (Lr, loss, (g_albedo, g_rough, g_metal)):
+    render_fwd's results and render_bwd's for grad_loss = 1, each input read once."""
+    N = Ld.shape[0]
+    g, K = _grid(sigma_grid)
+    if Lgt is None:
+        raise ValueError("render_fwd_grad needs Lgt")
+    Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask = _render_inputs(N, K, Ld, Ls0, Ls1, albedo, rough,
+                                                                   metal, Lgt, mask)
+    Lr = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
+    loss = torch.zeros(1, dtype=torch.float64, device=Ld.device)
+    ga = torch.empty((N, 3), dtype=torch.float32, device=Ld.device)
+    gr = torch.empty(N, dtype=torch.float32, device=Ld.device)
+    gm = torch.empty(N, dtype=torch.float32, device=Ld.device)
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_render_workspace_size(N, ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, Ld.device)
+    check(lib().fipt_render_fwd_grad(_ptr(Ld), _ptr(Ls0), _ptr(Ls1), N, K, g, _ptr(albedo), _ptr(rough),
+                                     _ptr(metal), _ptr(Lgt), _ptr(mask), _ptr(Lr), _ptr(loss), _ptr(ga),
+                                     _ptr(gr), _ptr(gm), _ptr(ws), nbytes.value, _stream(stream)))
+    return Lr, loss, (ga, gr, gm)
+
+
+def render_grad_scale(grads, grad_loss, stream=None):
+    """Multiplies render_fwd_grad's gradients in place by grad_loss (float64 CUDA [1])."""
+    ga, gr, gm = grads
+    N = gr.shape[0]
+    ga = _need(ga, torch.float32, "g_albedo", (N, 3))
+    gr = _need(gr, torch.float32, "g_rough", (N,))
+    gm = _need(gm, torch.float32, "g_metal", (N,))
+    grad_loss = _need(grad_loss, torch.float64, "grad_loss", (1,))
+    check(lib().fipt_render_grad_scale(N, _ptr(grad_loss), _ptr(ga), _ptr(gr), _ptr(gm), _stream(stream)))
+    return ga, gr, gm
+
+
 class FactorizedRender(torch.autograd.Function):
     """Tone-mapped factorized-render loss (Eq. 5, 8, 14) with the library's
-    hand-written backward for per-point albedo, roughness and metallic."""
+    hand-written backward for per-point albedo, roughness and metallic.
+    When a gradient is needed the forward computes it too (one pass over
+    the inputs) and the backward only scales it by the upstream gradient;
+    a second backward through the same graph recomputes it."""
 
     @staticmethod
     def forward(ctx, albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask, sigma_grid):
         albedo, rough, metal = albedo.contiguous(), rough.contiguous(), metal.contiguous()
-        _, loss = render_fwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask)
+        ctx.grads = None
+        if any(ctx.needs_input_grad[:3]):
+            _, loss, ctx.grads = render_fwd_grad(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask)
+        else:
+            _, loss = render_fwd(Ld, Ls0, Ls1, sigma_grid, albedo, rough, metal, Lgt, mask)
         ctx.save_for_backward(albedo, rough, metal, Ld, Ls0, Ls1, Lgt,
                               mask if mask is not None else torch.empty(0, device=Ld.device))
         ctx.has_mask = mask is not None
@@ -427,10 +470,14 @@ class FactorizedRender(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_out):
-        albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask = ctx.saved_tensors
         g = grad_out.detach().to(torch.float64).reshape(1).contiguous()
-        ga, gr, gm = render_bwd(Ld, Ls0, Ls1, ctx.sigma_grid, albedo, rough, metal, Lgt,
-                                mask if ctx.has_mask else None, g)
+        if ctx.grads is not None:        # computed by the forward pass; handed out once
+            grads, ctx.grads = ctx.grads, None
+            ga, gr, gm = render_grad_scale(grads, g)
+        else:
+            albedo, rough, metal, Ld, Ls0, Ls1, Lgt, mask = ctx.saved_tensors
+            ga, gr, gm = render_bwd(Ld, Ls0, Ls1, ctx.sigma_grid, albedo, rough, metal, Lgt,
+                                    mask if ctx.has_mask else None, g)
         return ga, gr, gm, None, None, None, None, None, None
 
 

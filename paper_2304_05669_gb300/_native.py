@@ -64,6 +64,8 @@ SIGNATURES = {
     "fipt_render_fwd": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P, SZ, P],
     "fipt_render_bwd": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P, P, P],
     "fipt_render_fwd_noalloc": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P],
+    "fipt_render_fwd_grad": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P, P, P, P, SZ, P],
+    "fipt_render_grad_scale": [I64, P, P, P, P, P],
     "fipt_tri_error_workspace_size": [I64, I64, P],
     "fipt_tri_error": [P, I64, P, P, I64, I64, P, P, P, SZ, P],
     "fipt_debug_philox": [P, P, I64, P, P],

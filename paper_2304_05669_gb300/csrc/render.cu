@@ -1,8 +1,11 @@
 // Factorized render (Eq. 5 with the lerp of Eq. 8), the tone-mapped loss of
 // Eq. 14 (alpha = 0) and its gradient with respect to per-point albedo,
-// roughness and metallic.  Both kernels stream one point per thread; the
+// roughness and metallic.  The kernels stream one point per thread; the
 // loss is reduced in a fixed order (per-block FP64 partials, then one block
-// over the partials) so it is bit-reproducible.
+// over the partials) so it is bit-reproducible.  k_render_fwd_grad computes
+// the forward, the loss and the gradient (for an upstream gradient of 1)
+// in one pass, so that a training step reads its inputs once;
+// k_render_grad_scale applies the upstream gradient afterwards.
 #include <mutex>
 
 #include "fipt_internal.cuh"
@@ -39,17 +42,27 @@ __device__ __forceinline__ Lerp lerp_of(float rough, const Grid& g) {
     return l;
 }
 
-// Gamma of Eq. 14: sRGB transfer curve of log(1 + max(x, 0)).
+// y^(1/2.4) for y > 0.0031308 as 2^(log2(y) / 2.4): with |log2 y| < 8.4
+// the exponent is off by at most a few 1e-7, so is the power (relative).
+__device__ __forceinline__ float srgb_pow(float y) { return exp2f(log2f(y) * (1.0f / 2.4f)); }
+
+// Gamma of Eq. 14: sRGB transfer curve of y = log(1 + max(x, 0)).
 __device__ __forceinline__ float tonemap(float x) {
     const float y = log1pf(fmaxf(x, 0.0f));
-    return y <= 0.0031308f ? 12.92f * y : 1.055f * powf(y, 1.0f / 2.4f) - 0.055f;
+    return y <= 0.0031308f ? 12.92f * y : 1.055f * srgb_pow(y) - 0.055f;
 }
 
-__device__ __forceinline__ float tonemap_grad(float x) {
-    if (x < 0.0f) return 0.0f;
-    const float y = log1pf(x);
-    const float ds = y <= 0.0031308f ? 12.92f : (1.055f / 2.4f) * powf(y, 1.0f / 2.4f - 1.0f);
-    return ds / (1.0f + x);
+// Gamma(x) and its derivative dt from one logarithm and one power:
+// d/dx of 1.055 y^(1/2.4) is (1.055 / 2.4) y^(1/2.4) / y / (1 + x); 0 for x < 0.
+__device__ __forceinline__ float tonemap_d(float x, float& dt) {
+    const float y = log1pf(fmaxf(x, 0.0f));
+    if (y <= 0.0031308f) {
+        dt = x < 0.0f ? 0.0f : 12.92f / (1.0f + x);
+        return 12.92f * y;
+    }
+    const float pw = srgb_pow(y);
+    dt = (1.055f / 2.4f) * (pw / y) / (1.0f + x);
+    return 1.055f * pw - 0.055f;
 }
 
 struct PointShade {
@@ -81,13 +94,28 @@ __device__ __forceinline__ void load_point(int64_t p, int K, const Grid& g, cons
     P.m = metal[p];
 }
 
+// The block's loss to partial[blockIdx.x]: a point's three channels and a
+// warp's 32 points are summed in float32 (fixed shuffle order), the
+// block's warps in FP64 in order.  Every thread of the block calls it.
+__device__ __forceinline__ void block_loss(float loss, double* partial) {
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    __shared__ double ws[RENDER_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < RENDER_THREADS / 32; ++w) s += ws[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
 __global__ void __launch_bounds__(RENDER_THREADS)
 k_render_fwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const float* __restrict__ Ls1,
              int64_t N, Grid g, const float* __restrict__ albedo, const float* __restrict__ rough,
              const float* __restrict__ metal, const float* __restrict__ Lgt,
              const uint8_t* __restrict__ mask, float* __restrict__ Lr, double* __restrict__ partial) {
     const int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x;
-    double loss = 0.0;
+    float loss = 0.0f;
     if (p < N) {
         PointShade P;
         load_point(p, g.K, g, Ld, Ls0, Ls1, albedo, rough, metal, P, false);
@@ -104,20 +132,11 @@ k_render_fwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const 
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float d = tonemap(lr[c]) - tonemap(Lgt[3 * p + c]);
-                loss += (double)d * (double)d;
+                loss += d * d;
             }
         }
     }
-    if (!partial) return;
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
-    __shared__ double ws[RENDER_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = loss;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < RENDER_THREADS / 32; ++w) s += ws[w];
-        partial[blockIdx.x] = s;
-    }
+    if (partial) block_loss(loss, partial);
 }
 
 __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partial, int64_t n,
@@ -155,14 +174,69 @@ k_render_bwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const 
         const float kd = a * (1.0f - m);
         const float ks = 0.04f * (1.0f - m) + a * m;
         const float lr = kd * P.Ld[c] + ks * P.S0[c] + P.S1[c];
-        const float gc = on ? 2.0f * (tonemap(lr) - tonemap(Lgt[3 * p + c])) * tonemap_grad(lr) * scale
-                            : 0.0f;
+        float dt;
+        const float d = tonemap_d(lr, dt) - tonemap(Lgt[3 * p + c]);
+        const float gc = on ? 2.0f * d * dt * scale : 0.0f;
         g_albedo[3 * p + c] = gc * ((1.0f - m) * P.Ld[c] + m * P.S0[c]);
         gm += gc * (-a * P.Ld[c] + (a - 0.04f) * P.S0[c]);
         gs += gc * (ks * P.dS0[c] + P.dS1[c]);
     }
     g_rough[p] = P.l.clamped ? 0.0f : gs;
     g_metal[p] = gm;
+}
+
+// Forward, loss and loss gradient in one pass: the values of k_render_fwd
+// and of k_render_bwd with grad_loss = 1, each input read once.
+__global__ void __launch_bounds__(RENDER_THREADS)
+k_render_fwd_grad(const float* __restrict__ Ld, const float* __restrict__ Ls0, const float* __restrict__ Ls1,
+                  int64_t N, Grid g, const float* __restrict__ albedo, const float* __restrict__ rough,
+                  const float* __restrict__ metal, const float* __restrict__ Lgt,
+                  const uint8_t* __restrict__ mask, float* __restrict__ Lr, double* __restrict__ partial,
+                  float* __restrict__ g_albedo, float* __restrict__ g_rough, float* __restrict__ g_metal) {
+    const int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x;
+    float loss = 0.0f;
+    if (p < N) {
+        PointShade P;
+        load_point(p, g.K, g, Ld, Ls0, Ls1, albedo, rough, metal, P, true);
+        const bool on = !mask || mask[p];
+        const float m = P.m;
+        float gs = 0.0f, gm = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float a = P.a[c];
+            const float kd = a * (1.0f - m);
+            const float ks = 0.04f * (1.0f - m) + a * m;
+            const float lr = kd * P.Ld[c] + ks * P.S0[c] + P.S1[c];
+            Lr[3 * p + c] = lr;
+            float dt;
+            const float d = tonemap_d(lr, dt) - tonemap(Lgt[3 * p + c]);
+            if (on) loss += d * d;
+            const float gc = on ? 2.0f * d * dt : 0.0f;
+            g_albedo[3 * p + c] = gc * ((1.0f - m) * P.Ld[c] + m * P.S0[c]);
+            gm += gc * (-a * P.Ld[c] + (a - 0.04f) * P.S0[c]);
+            gs += gc * (ks * P.dS0[c] + P.dS1[c]);
+        }
+        g_rough[p] = P.l.clamped ? 0.0f : gs;
+        g_metal[p] = gm;
+    }
+    block_loss(loss, partial);
+}
+
+// Multiplies the gradients of k_render_fwd_grad by the upstream gradient
+// of the loss; a factor of exactly 1 leaves them as they are.
+__global__ void __launch_bounds__(RENDER_THREADS)
+k_render_grad_scale(int64_t N, const double* __restrict__ grad_loss, float* __restrict__ g_albedo,
+                    float* __restrict__ g_rough, float* __restrict__ g_metal) {
+    const float s = (float)*grad_loss;
+    if (s == 1.0f) return;
+    for (int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * RENDER_THREADS) {
+        g_albedo[3 * p + 0] *= s;
+        g_albedo[3 * p + 1] *= s;
+        g_albedo[3 * p + 2] *= s;
+        g_rough[p] *= s;
+        g_metal[p] *= s;
+    }
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -248,6 +322,58 @@ extern "C" fipt_status fipt_render_bwd(const float* Ld, const float* Ls0, const 
                  fipt_aligned(g_metal, 4) && fipt_aligned(grad_loss, 8), "misaligned array");
     FIPT_LAUNCH(k_render_bwd, blocks(N, RENDER_THREADS), RENDER_THREADS, 0, static_cast<cudaStream_t>(stream), Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt, mask, grad_loss, g_albedo, g_rough, g_metal);
     FIPT_LAUNCHED("render_bwd");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_render_fwd_grad(const float* Ld, const float* Ls0, const float* Ls1, int64_t N,
+                                            int32_t K, const float* sigma_grid, const float* albedo,
+                                            const float* rough, const float* metal, const float* Lgt,
+                                            const uint8_t* mask, float* Lr, double* loss, float* g_albedo,
+                                            float* g_rough, float* g_metal, void* ws, size_t ws_bytes,
+                                            fipt_stream stream) {
+    Grid g;
+    fipt_status r = make_grid(K, sigma_grid, g);
+    if (r != FIPT_OK) return r;
+    r = check_render_arrays(N, Ld, Ls0, Ls1, albedo, rough, metal);
+    if (r != FIPT_OK) return r;
+    FIPT_REQUIRE(loss && fipt_aligned(loss, 8), "loss is NULL or misaligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (N == 0) {
+        FIPT_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), st));
+        return FIPT_OK;
+    }
+    FIPT_REQUIRE(Lgt && Lr && g_albedo && g_rough && g_metal, "Lgt / Lr / gradient output is NULL");
+    FIPT_REQUIRE(fipt_aligned(Lgt, 4) && fipt_aligned(Lr, 4) && fipt_aligned(g_albedo, 4) &&
+                 fipt_aligned(g_rough, 4) && fipt_aligned(g_metal, 4), "misaligned array");
+    size_t need;
+    fipt_render_workspace_size(N, &need);
+    if (!ws || ws_bytes < need)
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "render workspace %zu < %zu", ws_bytes, need);
+    FIPT_REQUIRE(fipt_aligned(ws, 8), "workspace must be 8-byte aligned");
+    double* partial = static_cast<double*>(ws);
+    const unsigned nb = blocks(N, RENDER_THREADS);
+    FIPT_LAUNCH(k_render_fwd_grad, nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt,
+                mask, Lr, partial, g_albedo, g_rough, g_metal);
+    FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    FIPT_LAUNCHED("render_fwd_grad");
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_render_grad_scale(int64_t N, const double* grad_loss, float* g_albedo,
+                                              float* g_rough, float* g_metal, fipt_stream stream) {
+    FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 40), "bad point count");
+    if (N == 0) return FIPT_OK;
+    FIPT_REQUIRE(grad_loss && g_albedo && g_rough && g_metal, "NULL argument");
+    FIPT_REQUIRE(fipt_aligned(grad_loss, 8) && fipt_aligned(g_albedo, 4) && fipt_aligned(g_rough, 4) &&
+                 fipt_aligned(g_metal, 4), "misaligned array");
+    int dev = 0, sms = 0;
+    FIPT_CUDA(cudaGetDevice(&dev));
+    FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned nb = blocks(N, RENDER_THREADS);
+    const unsigned grid = nb < (unsigned)(8 * sms) ? nb : (unsigned)(8 * sms);
+    FIPT_LAUNCH(k_render_grad_scale, grid, RENDER_THREADS, 0, static_cast<cudaStream_t>(stream), N, grad_loss,
+                g_albedo, g_rough, g_metal);
+    FIPT_LAUNCHED("render_grad_scale");
     return FIPT_OK;
 }
 

@@ -157,3 +157,56 @@ def test_render_grid_sizes(fipt, grid):
         close(got.cpu().numpy(), ref)
     with pytest.raises(fipt.FiptError):
         fipt.render_fwd(t[0], t[1][:, :1].contiguous(), t[2][:, :1].contiguous(), [0.5], t[3], t[4], t[5])
+
+
+@pytest.mark.parametrize("N,with_mask", [(1, False), (65537, True), (200003, False)])
+def test_fused_forward_gradient(fipt, N, with_mask):
+    """render_fwd_grad (one pass) gives render_fwd's Lr and loss and
+    render_bwd's gradients for an upstream gradient of 1, and the oracle's;
+    render_grad_scale by 1 leaves them untouched, by 0.5 gives the oracle's
+    gradients at grad_scale 0.5."""
+    Ld, Ls0, Ls1, mp, Lgt, mask = inputs(N, 50)
+    mk = mask if with_mask else None
+    t = cu(Ld, Ls0, Ls1, mp["albedo"], mp["rough"], mp["metal"], Lgt, mask)
+    m_t = t[7] if with_mask else None
+    Lr, loss, grads = fipt.render_fwd_grad(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6], m_t)
+    Lr1, loss1 = fipt.render_fwd(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6], m_t)
+    close(Lr.cpu().numpy(), Lr1.cpu().numpy(), rel=1e-6)
+    assert abs(loss.item() - loss1.item()) <= 1e-6 * abs(loss1.item())
+    for x, y in zip(grads, fipt.render_bwd(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6], m_t)):
+        close(x.cpu().numpy(), y.cpu().numpy(), rel=1e-6)
+    Lr_o, loss_o = O.render_forward(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"], Lgt, mk)
+    close(Lr.cpu().numpy(), Lr_o)
+    assert abs(loss.item() - loss_o) <= REL * abs(loss_o)
+    for got, ref in zip(grads, O.render_grad(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"],
+                                             Lgt, mk)):
+        close(got.cpu().numpy(), ref)
+    before = [x.clone() for x in grads]
+    fipt.render_grad_scale(grads, torch.ones(1, dtype=torch.float64, device="cuda"))
+    assert all(torch.equal(x, y) for x, y in zip(grads, before))
+    fipt.render_grad_scale(grads, torch.full((1,), 0.5, dtype=torch.float64, device="cuda"))
+    for got, ref in zip(grads, O.render_grad(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"],
+                                             Lgt, mk, grad_scale=0.5)):
+        close(got.cpu().numpy(), ref)
+
+
+def test_autograd_backward_twice_and_without_grad(fipt):
+    """The autograd function hands out the forward pass's gradient once; a
+    second backward through the same graph recomputes it, so two leave
+    twice the gradient.  Under no_grad the loss is the same."""
+    N = 4099
+    Ld, Ls0, Ls1, mp, Lgt, mask = inputs(N, 60)
+    t = cu(Ld, Ls0, Ls1, Lgt)
+    a = torch.from_numpy(mp["albedo"]).cuda().requires_grad_()
+    r = torch.from_numpy(mp["rough"]).cuda().requires_grad_()
+    m = torch.from_numpy(mp["metal"]).cuda().requires_grad_()
+    loss = fipt.factorized_render_loss(a, r, m, (t[0], t[1], t[2]), t[3], GRID)
+    loss.backward(retain_graph=True)
+    loss.backward()
+    for got, ref in zip((a.grad, r.grad, m.grad),
+                        O.render_grad(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"], Lgt,
+                                      grad_scale=2.0)):
+        close(got.cpu().numpy(), ref)
+    with torch.no_grad():
+        l2 = fipt.factorized_render_loss(a, r, m, (t[0], t[1], t[2]), t[3], GRID)
+    assert abs(l2.item() - loss.item()) <= 1e-6 * abs(loss.item())
