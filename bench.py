@@ -136,7 +136,17 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
+    def _once(self):
+        """One synchronous query (brackets timed regions shorter than the loop's period)."""
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            self.lines.extend(l.strip() for l in out.splitlines() if l.strip())
+        except Exception:
+            pass
+
     def __enter__(self):
+        self._once()
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -159,6 +169,7 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.t.join(timeout=2)
+        self._once()
 
     def summary(self):
         rows = []
