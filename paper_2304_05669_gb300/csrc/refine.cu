@@ -25,7 +25,8 @@
 //                segment), and queues both rays;
 //   k_rf_trace   closest hit of every queued ray: a persistent kernel whose
 //                warps draw rays from the queue and walk the tree with the
-//                stage-1 bake's speculative, warp-refilled traversal;
+//                stage-1 bake's speculative, warp-refilled traversal (stack
+//                in local memory, as the bake's);
 //   k_rf_shade   consumes a slot's hits (the shadow ray first, then the
 //                path segment), and at a smooth surface queues the vertex's
 //                shadow ray and its next segment together (the BRDF sample
@@ -41,10 +42,10 @@
 namespace {
 
 #ifndef FIPT_RF_TRACE_THREADS
-#define FIPT_RF_TRACE_THREADS 64     // small blocks: the shared stack bounds residency
+#define FIPT_RF_TRACE_THREADS 64
 #endif
 #ifndef FIPT_RF_TRACE_MINB
-#define FIPT_RF_TRACE_MINB 20        // resident traversal blocks per SM (48 registers)
+#define FIPT_RF_TRACE_MINB 24        // resident traversal blocks per SM (40 registers)
 #endif
 #ifndef FIPT_RF_REFILL
 #define FIPT_RF_REFILL 24            // idle lanes that make a warp draw new rays
@@ -417,8 +418,7 @@ template <bool STATS>
 __global__ void __launch_bounds__(RF_TRACE_THREADS, FIPT_RF_TRACE_MINB)
 k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long* stats) {
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ int stk[STACK_DEPTH * RF_TRACE_THREADS];
-    int* stack = stk + threadIdx.x;
+    int stack[STACK_DEPTH];             // local memory, as the stage-1 bake's
     const uint32_t* __restrict__ queue = st.tq[w & 1];
     uint32_t* cnt = st.cnt + 4 * w;
     const uint32_t n = cnt[0];
@@ -489,7 +489,7 @@ k_rf_trace(SceneView sc, RfState st, int w, int32_t* status, unsigned long long*
                 }
             }
         }
-        warp_walk<RF_TRACE_THREADS, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws,
+        warp_walk<1, STATS, true>(sc, r, skip, best, node, pleaf, sp, steps, stack, status, ws,
                                                  shadow);
     }
     if (STATS) {

@@ -2,10 +2,12 @@
 // and the bake of the factorized shading terms (Eq. 6-7, Eq. 9, Sec. 6).
 //
 // Traversal is a per-thread stack walk of the binary LBVH in "while-while"
-// form (inner nodes until a leaf, then leaves until an inner node), with
-// the stack in shared memory, laid out [depth][thread] so that the threads
-// of a warp touch consecutive banks.  Node (64 B) and triangle (48 B) reads
-// are 16-byte vector loads through the read-only path.
+// form (inner nodes until a leaf, then leaves until an inner node).  The
+// first-hit kernels keep the stack in shared memory, laid out
+// [depth][thread] so that the threads of a warp touch consecutive banks;
+// the bake keeps it in local memory (see bake_item).  Node (64 B) and
+// triangle (48 B) reads are 16-byte vector loads through the read-only
+// path.
 #include "fipt_internal.cuh"
 
 namespace {
@@ -162,16 +164,16 @@ k_compact(const fipt_query* __restrict__ in, const int32_t* __restrict__ valid, 
 
 // ---------------------------------------------------------------- bake
 #ifndef FIPT_BAKE_THREADS
-#define FIPT_BAKE_THREADS 64      // small blocks: the shared stack, not threads, bounds residency
+#define FIPT_BAKE_THREADS 64
 #endif
 #ifndef FIPT_BAKE_MINB
-#define FIPT_BAKE_MINB 24        // blocks per SM the register budget must allow (75% occupancy)
+#define FIPT_BAKE_MINB 32        // blocks per SM the register budget must allow (full occupancy, 32 registers)
 #endif
 constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 
 
 #ifndef FIPT_BAKE_REFILL
-#define FIPT_BAKE_REFILL 24      // lanes that must be waiting before a warp draws new rays
+#define FIPT_BAKE_REFILL 28      // lanes that must be waiting before a warp draws new rays
 #endif
 #ifndef FIPT_BAKE_SPECULATE
 #define FIPT_BAKE_SPECULATE 1    // keep walking inner nodes while other lanes look for a leaf
@@ -190,14 +192,19 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 //  * speculation (Aila and Laine 2009): a lane that reaches a leaf parks
 //    it and keeps descending inner nodes until every lane has a leaf;
 //  * leaves are then tested together.
+// The traversal stack is a per-thread array in local memory, not a shared
+// memory column: the bake then reserves no shared memory and the SM's
+// unified L1 / shared storage serves as cache for the nodes and for the
+// stack entries actually in use.
 // FLAGS: 1 = environment light for misses, 2 = voxel radiance cache.
 template <bool STATS, int FLAGS>
 __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
                                           const int64_t p, const int lobe, const bool valid,
                                           const BakeArgs& A, float* __restrict__ Ld,
                                           float* __restrict__ Ls0, float* __restrict__ Ls1,
-                                          int32_t* status, unsigned long long* stats, int* stack) {
+                                          int32_t* status, unsigned long long* stats) {
     constexpr unsigned FULL = 0xffffffffu;
+    int stack[STACK_DEPTH];
     float nx = 0.0f, ny = 0.0f, nz = 1.0f, wox = 0.0f, woy = 0.0f, woz = 1.0f;
     float px = 0.0f, py = 0.0f, pz = 0.0f;
     int skip = -1;
@@ -352,7 +359,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     if (h0 && h1) {
                         const bool first0 = t0 <= t1;
                         if (sp < STACK_DEPTH) {
-                            stack[sp * BAKE_THREADS] = first0 ? n.d.y : n.d.x;
+                            stack[sp] = first0 ? n.d.y : n.d.x;
                             ++sp;
                             if (STATS) max_sp = max(max_sp, sp);
                         } else {
@@ -364,13 +371,13 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     } else if (h1) {
                         node = n.d.y;
                     } else {
-                        node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+                        node = sp > 0 ? stack[--sp] : FIPT_DONE;
                     }
                 }
             }
             if (node < 0 && node != FIPT_DONE && pleaf < 0) {   // park the first leaf found
                 pleaf = ~node;
-                node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+                node = sp > 0 ? stack[--sp] : FIPT_DONE;
             }
             if (!__any_sync(FULL, pleaf < 0 && node >= 0)) break;   // every lane has a leaf or is done
         }
@@ -401,7 +408,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
             }
             if (node < 0 && node != FIPT_DONE) {      // the next entry is a leaf too
                 pleaf = ~node;
-                node = sp > 0 ? stack[--sp * BAKE_THREADS] : FIPT_DONE;
+                node = sp > 0 ? stack[--sp] : FIPT_DONE;
             }
         }
     }
@@ -434,7 +441,6 @@ __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
        float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
        unsigned long long* stats) {
-    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
     const int L = 1 + A.K;
     const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
     const int64_t w = g >> 5;
@@ -442,7 +448,7 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int lobe = (int)(w % L);
     const int64_t p = (w / L) * 32 + lane;
     if ((w / L) * 32 >= N) return;          // whole warp past the end
-    bake_item<STATS, FLAGS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats, stk + threadIdx.x);
+    bake_item<STATS, FLAGS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats);
 }
 
 // One launch over chunks of several requests, possibly on several scenes
@@ -455,7 +461,6 @@ template <int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
              int32_t* status) {
-    __shared__ int stk[STACK_DEPTH * BAKE_THREADS];
     const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
     const int64_t w = g >> 5;
     const int lane = (int)(g & 31);
@@ -471,8 +476,7 @@ k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_w
     const int L = 1 + A.K;
     const int lobe = (int)(wl % L);
     const int64_t p = (wl / L) * 32 + lane;
-    bake_item<false, FLAGS>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr,
-                            stk + threadIdx.x);
+    bake_item<false, FLAGS>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr);
 }
 
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
