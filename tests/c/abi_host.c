@@ -34,6 +34,15 @@ int main(void)
     CHECK(fipt_tri_error_workspace_size(1000, 10, &bytes) == FIPT_OK && bytes > 0);
     CHECK(fipt_voxel_cache_workspace_size(1000, &bytes) == FIPT_OK && bytes > 0);
     CHECK(fipt_emitter_radiance_workspace_size(1000, 10, &bytes) == FIPT_OK && bytes > 0);
+    fipt_bake_params bp;
+    memset(&bp, 0, sizeof(bp));
+    bp.K = 6;
+    bp.spp_diffuse = 32;
+    bp.spp_specular = 32;
+    CHECK(fipt_bake_refine_workspace_size(1000, &bp, 8, &bytes) == FIPT_OK && bytes >= 1000u * 224u * 184u);
+    bp.spp_diffuse = 1 << 24;
+    CHECK(fipt_bake_refine_workspace_size(1, &bp, 8, &bytes) == FIPT_ERR_INVALID_ARG);
+    CHECK(fipt_render_grad_scale(0, NULL, NULL, NULL, NULL, NULL) == FIPT_OK);
 
     /* NULL arguments are rejected before any device work */
     CHECK(fipt_bake(NULL, NULL, 0, NULL, NULL, NULL, NULL, NULL) == FIPT_ERR_INVALID_ARG);

@@ -57,6 +57,32 @@ def test_host_side_argument_checks(L):
     assert L.fipt_version().startswith(b"fipt-gb300")
 
 
+def test_refine_workspace_and_render_pass_checks(L):
+    """Host arithmetic of the refinement's workspace (184 B of path state per
+    sample, at most 2^24 samples per chunk, whole points) and the argument
+    checks of the one-pass render, none of which touches a device."""
+    from paper_2304_05669_gb300 import _native
+    n = ctypes.c_size_t()
+    p = _native.BakeParams()
+    p.K, p.spp_diffuse, p.spp_specular = 6, 32, 32           # 224 samples per point
+    assert L.fipt_bake_refine_workspace_size(1000, ctypes.byref(p), 8, ctypes.byref(n)) == 0
+    assert 1000 * 224 * 184 <= n.value <= 1000 * 224 * 184 + 64 * 1024
+    small = n.value
+    assert L.fipt_bake_refine_workspace_size(1 << 20, ctypes.byref(p), 8, ctypes.byref(n)) == 0
+    per_chunk = (1 << 24) // 224
+    assert per_chunk * 224 * 184 <= n.value <= per_chunk * 224 * 184 + 64 * 1024 and n.value > small
+    assert L.fipt_bake_refine_workspace_size(0, ctypes.byref(p), 8, ctypes.byref(n)) == 0 and n.value == 0
+    p.spp_diffuse = 1 << 24                                    # one point over a chunk
+    assert L.fipt_bake_refine_workspace_size(1, ctypes.byref(p), 8, ctypes.byref(n)) == 1
+    p.spp_diffuse = 32
+    assert L.fipt_bake_refine_workspace_size(1, ctypes.byref(p), 4096, ctypes.byref(n)) == 1
+    grid = (ctypes.c_float * 1)(0.5)                           # K = 1: a lerp needs two nodes
+    assert L.fipt_render_fwd_grad(None, None, None, 10, 1, grid, None, None, None, None, None, None, None,
+                                  None, None, None, None, 0, None) == 1
+    assert L.fipt_render_grad_scale(0, None, None, None, None, None) == 0
+    assert L.fipt_render_grad_scale(5, None, None, None, None, None) == 1
+
+
 def test_query_record_is_40_bytes():
     # x, n, wo (9 floats) + tri (int32), the layout the bindings pack
     class Q(ctypes.Structure):
