@@ -115,15 +115,18 @@ __device__ __forceinline__ int emitter_sample(const SceneView& sc, int n_emit, d
     return leaf;
 }
 
-// Unit face normal of a leaf (not oriented) and twice its area.
-__device__ __forceinline__ float3 leaf_normal(const SceneView& sc, int leaf) {
-    const float4 p0 = __ldg(sc.tris + 3 * leaf), p1 = __ldg(sc.tris + 3 * leaf + 1),
-                 p2 = __ldg(sc.tris + 3 * leaf + 2);
+// Unit face normal (not oriented) of the triangle with vertices p0, p1, p2.
+__device__ __forceinline__ float3 tri_normal(float4 p0, float4 p1, float4 p2) {
     const float e1x = p1.x - p0.x, e1y = p1.y - p0.y, e1z = p1.z - p0.z;
     const float e2x = p2.x - p0.x, e2y = p2.y - p0.y, e2z = p2.z - p0.z;
     float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
     const float il = 1.0f / sqrtf(nx * nx + ny * ny + nz * nz);
     return make_float3(nx * il, ny * il, nz * il);
+}
+
+// Unit face normal of a leaf (not oriented).
+__device__ __forceinline__ float3 leaf_normal(const SceneView& sc, int leaf) {
+    return tri_normal(__ldg(sc.tris + 3 * leaf), __ldg(sc.tris + 3 * leaf + 1), __ldg(sc.tris + 3 * leaf + 2));
 }
 
 struct Mat {
@@ -133,8 +136,9 @@ struct Mat {
     bool spec;
 };
 
-__device__ __forceinline__ Mat vertex_mat(const SceneView& sc, int leaf, float mu_o) {
-    const float4 m0 = __ldg(sc.mats + 2 * leaf), m1 = __ldg(sc.mats + 2 * leaf + 1);
+// Eq. 1's k_d, k_s, alpha^2 and the diffuse-lobe probability from a leaf's
+// material records m0 = (albedo, roughness), m1 = (metallic, ...).
+__device__ __forceinline__ Mat vertex_mat(float4 m0, float4 m1, float mu_o) {
     Mat M;
     const float m = m1.x;
     const float a[3] = {m0.x, m0.y, m0.z};
@@ -534,13 +538,17 @@ k_rf_shade(SceneView sc, RfChunk C, RefineArgs R, RfState st, int w) {
             slot_decode(j, R, pc, lobe, s);
             const uint32_t pid = A.point_base + (uint32_t)(C.p0 + pc);
             float4 C0 = st.c0[j], C1 = st.c1[j], LW = st.lw[j];
+            // the slot's other records, loaded together whether or not a ray
+            // of their kind was queued (they are unused then)
+            const float4 SW = st.sw[j], D = st.dir[2 * j], O = st.org[j];
+            const int4 hs = st.hit[2 * j + 1], h = st.hit[2 * j];
+            const float4 BP = st.bp[j];
             const uint32_t f_in = __float_as_uint(C1.w);
             uint32_t depth = f_in & F_DEPTH;
             uint32_t flags = f_in & F_LIVE;
             if (f_in & F_SHADOW) {                      // the shadow ray queued last wave
-                const float4 SW = st.sw[j];
                 const int tgt = __float_as_int(SW.w);
-                if (st.hit[2 * j + 1].y == tgt) {
+                if (hs.y == tgt) {
                     const float4 le = __ldg(sc.shade + 2 * tgt);
                     if (f_in & F_AT_X) {
                         C0.x += SW.x * le.x; C0.y += SW.x * le.y; C0.z += SW.x * le.z;
@@ -551,9 +559,6 @@ k_rf_shade(SceneView sc, RfChunk C, RefineArgs R, RfState st, int w) {
                 }
             }
             if (f_in & F_PATH) {                        // the path segment queued last wave
-                const int4 h = st.hit[2 * j];
-                const float4 D = st.dir[2 * j];
-                float4 BP = st.bp[j];
                 const float dx = D.x, dy = D.y, dz = D.z;
                 if (h.y < 0) {
                     if (sc.env) {
@@ -563,38 +568,35 @@ k_rf_shade(SceneView sc, RfChunk C, RefineArgs R, RfState st, int w) {
                 } else {
                     const int leaf = h.y;
                     const float t = __int_as_float(h.x);
-                    const float4 O = st.org[j];
                     const float hx = O.x + t * dx, hy = O.y + t * dy, hz = O.z + t * dz;
-                    const float4 le = __ldg(sc.shade + 2 * leaf);
+                    // everything the hit's shading can need, loaded together
+                    const float4 le = __ldg(sc.shade + 2 * leaf), c4 = __ldg(sc.shade + 2 * leaf + 1);
+                    const float4 m0 = __ldg(sc.mats + 2 * leaf), m1 = __ldg(sc.mats + 2 * leaf + 1);
+                    const float4 p0 = __ldg(sc.tris + 3 * leaf), p1 = __ldg(sc.tris + 3 * leaf + 1),
+                                 p2 = __ldg(sc.tris + 3 * leaf + 2);
                     if (is_emitter(le)) {
                         if (h.w) {
                             float wgt = 1.0f;
                             if (mis) {
-                                const float3 ne = leaf_normal(sc, leaf);
+                                const float3 ne = tri_normal(p0, p1, p2);
                                 const float ce = fabsf(dx * ne.x + dy * ne.y + dz * ne.z);
                                 const float pl = t * t / (A_emit_f * ce);
                                 wgt = BP.w * BP.w / (BP.w * BP.w + pl * pl);
                             }
                             LW.x += BP.x * wgt * le.x; LW.y += BP.y * wgt * le.y; LW.z += BP.z * wgt * le.z;
                         }
-                    } else if (__ldg(&sc.mats[2 * leaf].w) > R.sigma_c) {
-                        float3 ca;
-                        if (sc.vox) {
-                            ca = voxel_lookup(sc, hx, hy, hz);
-                        } else {
-                            const float4 c4 = __ldg(sc.shade + 2 * leaf + 1);
-                            ca = make_float3(c4.x, c4.y, c4.z);
-                        }
+                    } else if (m0.w > R.sigma_c) {
+                        const float3 ca = sc.vox ? voxel_lookup(sc, hx, hy, hz) : make_float3(c4.x, c4.y, c4.z);
                         LW.x += BP.x * ca.x; LW.y += BP.y * ca.y; LW.z += BP.z * ca.z;
                     } else if ((int)depth <= R.max_depth) {
                         // a smooth surface: path vertex `depth`
-                        float3 nv = leaf_normal(sc, leaf);
+                        float3 nv = tri_normal(p0, p1, p2);
                         if (nv.x * dx + nv.y * dy + nv.z * dz > 0.0f) nv = make_float3(-nv.x, -nv.y, -nv.z);
                         const float xox = hx + eps * nv.x, xoy = hy + eps * nv.y, xoz = hz + eps * nv.z;
                         st.org[j] = make_float4(xox, xoy, xoz, __int_as_float(h.z));
                         const float3 wv = make_float3(-dx, -dy, -dz);
                         const float mu_v = nv.x * wv.x + nv.y * wv.y + nv.z * wv.z;
-                        const Mat M = vertex_mat(sc, leaf, mu_v);
+                        const Mat M = vertex_mat(m0, m1, mu_v);
                         const uint32_t lc = (uint32_t)lobe | (depth << 9);
                         if (mis) {                      // emitter sample at the vertex
                             float3 y;
