@@ -104,7 +104,7 @@ def measured_peaks():
 
 def source_digest():
     h = hashlib.sha256()
-    for f in ("trace.cu", "fipt_internal.cuh"):
+    for f in ("trace.cu", "fipt_internal.cuh", "lbvh.cu"):      # the kernel and the tree it walks
         with open(os.path.join(ROOT, "paper_2304_05669_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -134,6 +134,21 @@ fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t nV, const i
                               int64_t T, const float* Le, const float* cache, void* workspace,
                               size_t ws_bytes, fipt_stream stream, fipt_scene** out);
 
+/* Treelet restructuring of the scene's tree (Karras and Aila 2013), in
+ * place, `passes` bottom-up passes (0 to 16; 0 does nothing): at every
+ * internal node the treelet of up to 7 subtrees reached by expanding the
+ * largest-area children is given the topology with the least total
+ * surface area of its internal nodes (the SAH cost with one triangle per
+ * leaf), if that is strictly cheaper.  Leaves and their boxes stay and
+ * walks visit fewer nodes.  The closest hit, the (t, triangle) minimum, does
+ * not depend on the tree, except where float32 leaves several triangles
+ * within a few ulps of it (a ray along a shared edge): the culling bound
+ * then depends on the visit order and another of those equally correct
+ * hits may be returned.  The radix-tree ranges of fipt_scene_debug_export
+ * no longer describe the tree afterwards.  Not an operation of the paper:
+ * a property of the acceleration structure only. */
+fipt_status fipt_scene_optimize(fipt_scene* scene, int32_t passes, fipt_stream stream);
+
 /* Replaces the radiance cache (cache [T,3] f32, original triangle order)
  * without rebuilding the BVH -- the refined-cache update between stages. */
 fipt_status fipt_scene_set_cache(fipt_scene* scene, const float* cache, fipt_stream stream);
@@ -148,10 +163,13 @@ fipt_status fipt_scene_info(fipt_scene* scene, fipt_stream stream, int64_t* T, f
 /* Parity export of the LBVH (device outputs, any may be NULL):
  *  morton [T] u64 codes in sorted order; order [T] i32 triangle index at
  *  each sorted position; node_range [(T-1),3] i32 (first, last, split) of
- *  every internal node over sorted positions; node_box [(T-1),6] f32 the
- *  node's box (lo xyz, hi xyz) = union of its two child boxes. */
+ *  every internal node over sorted positions (FIPT_ERR_INVALID_ARG after
+ *  fipt_scene_optimize); node_box [(T-1),6] f32 the node's box (lo xyz,
+ *  hi xyz) = union of its two child boxes; node_child [(T-1),2] i32 the
+ *  node's child references (>= 0 an internal node, < 0 the leaf ~ref). */
 fipt_status fipt_scene_debug_export(fipt_scene* scene, uint64_t* morton, int32_t* order,
-                                    int32_t* node_range, float* node_box, fipt_stream stream);
+                                    int32_t* node_range, float* node_box, int32_t* node_child,
+                                    fipt_stream stream);
 
 /* ------------------------------------------------------------ rays */
 /* Closest hit of nR rays o + t d, t > 0 (orig, dir [nR,3] f32; dir need

@@ -130,10 +130,15 @@ def unpack_queries(q):
             "tri": q[:, 9:10].contiguous().view(torch.int32)[:, 0]}
 
 
-class Scene:
-    """A triangle mesh with its device-built LBVH (``fipt_scene_create``)."""
+OPTIMIZE_PASSES = 2      # treelet-restructuring passes a Scene gets by default
 
-    def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None):
+
+class Scene:
+    """A triangle mesh with its device-built LBVH (``fipt_scene_create``),
+    then ``optimize`` treelet-restructuring passes (``fipt_scene_optimize``;
+    0 keeps the radix tree as built)."""
+
+    def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None, optimize=None):
         V = _dev(V, torch.float32, "V")
         F = _dev(F, torch.int32, "F")
         Le = _dev(Le, torch.float32, "Le")
@@ -151,6 +156,10 @@ class Scene:
                                       _stream(stream), ctypes.byref(h)))
         self.handle = h
         self._keep = (V, F, Le, cache)    # alive until the stream has consumed them
+        optimize = OPTIMIZE_PASSES if optimize is None else int(optimize)
+        self.optimized = optimize
+        if optimize:
+            check(lib().fipt_scene_optimize(h, int(optimize), _stream(stream)))
 
     @classmethod
     def from_mesh(cls, mesh, device="cuda", **kw):
@@ -236,10 +245,13 @@ class Scene:
         d = self.device
         out = {"morton": torch.empty(T, dtype=torch.int64, device=d),
                "order": torch.empty(T, dtype=torch.int32, device=d),
-               "range": torch.empty((ni, 3), dtype=torch.int32, device=d),
-               "box": torch.empty((ni, 6), dtype=torch.float32, device=d)}
+               "box": torch.empty((ni, 6), dtype=torch.float32, device=d),
+               "child": torch.empty((ni, 2), dtype=torch.int32, device=d)}
+        if not self.optimized:
+            out["range"] = torch.empty((ni, 3), dtype=torch.int32, device=d)
         check(lib().fipt_scene_debug_export(self.handle, _ptr(out["morton"]), _ptr(out["order"]),
-                                            _ptr(out["range"]), _ptr(out["box"]), _stream(stream)))
+                                            _ptr(out.get("range")), _ptr(out["box"]), _ptr(out["child"]),
+                                            _stream(stream)))
         return out
 
     def trace(self, orig, dirs, skip=None, stream=None):

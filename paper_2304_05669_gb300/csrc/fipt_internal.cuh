@@ -77,6 +77,7 @@ struct fipt_scene {
     int32_t* emit_leaf;    // [T] (first n_emit used)
     double* emit_cdf;      // [T]
     bool has_materials = false;
+    bool restructured = false;    // fipt_scene_optimize ran (range[] is the radix tree's only)
     const float* env = nullptr;   // caller-owned environment map
     int env_w = 0, env_h = 0;
     const float4* vox = nullptr;  // caller-owned voxel radiance cache

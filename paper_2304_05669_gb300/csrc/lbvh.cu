@@ -483,6 +483,176 @@ __global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
     }
 }
 
+// ---------------------------------------------------------------- treelets
+// Treelet restructuring (Karras and Aila, HPG 2013) of the built tree.  A
+// walk from every leaf climbs as in k_refit; the second thread to reach an
+// internal node p (its subtree is final) forms a treelet: p's two children,
+// then, until there are TREELET leaves or only triangles, the treelet leaf
+// with the largest surface area is replaced by its two children.  With one
+// triangle per leaf the SAH cost of a topology differs from another's only
+// in the areas of its internal nodes, so the optimal topology over the
+// treelet's leaves minimises that sum; a dynamic programme over the 2^m - 1
+// subsets finds it, and the treelet's internal nodes (p first, so p keeps
+// its place under its parent) are rewritten when it is strictly cheaper.
+// Leaves and their boxes are unchanged: the tree covers the same triangles
+// with boxes as tight as before, and a closest-hit walk returns the same
+// (t, triangle) minimum on any valid tree, up to near-ties that float32
+// cannot separate (the culling bound depends on the visit order).
+constexpr int TREELET = 7;
+
+__device__ __forceinline__ float half_area(const Box& b) {
+    const float dx = fmaxf(b.hx - b.lx, 0.0f), dy = fmaxf(b.hy - b.ly, 0.0f), dz = fmaxf(b.hz - b.lz, 0.0f);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ Box box_union(const Box& a, const Box& b) {
+    return Box{fminf(a.lx, b.lx), fminf(a.ly, b.ly), fminf(a.lz, b.lz),
+               fmaxf(a.hx, b.hx), fmaxf(a.hy, b.hy), fmaxf(a.hz, b.hz)};
+}
+
+// The two child boxes stored in node n's record (read through L2).
+__device__ __forceinline__ void child_boxes(const BvhNode* nodes, int n, Box& b0, Box& b1, int4& ch) {
+    const float4* q = reinterpret_cast<const float4*>(nodes + n);
+    const float4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    ch = __ldcg(reinterpret_cast<const int4*>(q + 3));
+    b0 = Box{a.x, a.z, c.x, a.y, a.w, c.y};
+    b1 = Box{b.x, b.z, c.z, b.y, b.w, c.w};
+}
+
+__device__ void restructure(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int p) {
+    int ref[TREELET];
+    Box box[TREELET];
+    int inner[TREELET - 1];
+    float area_l[TREELET];
+    int m = 2, ni = 1;
+    inner[0] = p;
+    int4 ch;
+    child_boxes(nodes, p, box[0], box[1], ch);
+    ref[0] = ch.x;
+    ref[1] = ch.y;
+    area_l[0] = half_area(box[0]);
+    area_l[1] = half_area(box[1]);
+    float cur = half_area(box_union(box[0], box[1]));     // the current internal areas
+    while (m < TREELET) {
+        int best = -1;
+        float ba = -1.0f;
+        for (int i = 0; i < m; ++i)
+            if (ref[i] >= 0 && area_l[i] > ba) {
+                ba = area_l[i];
+                best = i;
+            }
+        if (best < 0) break;
+        const int n = ref[best];
+        cur += ba;
+        inner[ni++] = n;
+        child_boxes(nodes, n, box[best], box[m], ch);
+        ref[best] = ch.x;
+        ref[m] = ch.y;
+        area_l[best] = half_area(box[best]);
+        area_l[m] = half_area(box[m]);
+        ++m;
+    }
+    if (m < 3) return;                                     // two leaves have one topology
+    const int full = (1 << m) - 1;
+    float area[1 << TREELET], cost[1 << TREELET];
+    uint8_t part[1 << TREELET];
+    for (int S = 1; S <= full; ++S) {
+        const int i0 = __ffs(S) - 1;
+        Box b = box[i0];
+        for (int i = i0 + 1; i < m; ++i)
+            if (S & (1 << i)) b = box_union(b, box[i]);
+        area[S] = half_area(b);
+    }
+    for (int S = 1; S <= full; ++S) {
+        if ((S & (S - 1)) == 0) {
+            cost[S] = 0.0f;
+            part[S] = 0;
+            continue;
+        }
+        const int low = S & -S;
+        float best = __int_as_float(0x7f800000);
+        int bp = low;
+        for (int P = (S - 1) & S; P > 0; P = (P - 1) & S) {
+            if (!(P & low)) continue;
+            const float v = cost[P] + cost[S ^ P];
+            if (v < best) {
+                best = v;
+                bp = P;
+            }
+        }
+        cost[S] = best + area[S];
+        part[S] = (uint8_t)bp;
+    }
+    if (!(cost[full] < cur * 0.99999f)) return;            // keep the current topology
+    // rebuild: depth-first from the full set; internal node k = inner[k]
+    BvhNode rec[TREELET - 1];
+    int stk_s[2 * TREELET], stk_par[2 * TREELET], stk_side[2 * TREELET];
+    int sp = 0, next = 0;
+    stk_s[sp] = full; stk_par[sp] = -1; stk_side[sp] = 0; ++sp;
+    while (sp > 0) {
+        --sp;
+        const int S = stk_s[sp], par = stk_par[sp], side = stk_side[sp];
+        int r;
+        const int i0 = __ffs(S) - 1;
+        Box b = box[i0];
+        for (int i = i0 + 1; i < m; ++i)
+            if (S & (1 << i)) b = box_union(b, box[i]);
+        if ((S & (S - 1)) == 0) {
+            r = ref[i0];
+        } else {
+            const int k = next++;
+            r = inner[k];
+            const int P = part[S];
+            stk_s[sp] = S ^ P; stk_par[sp] = k; stk_side[sp] = 1; ++sp;
+            stk_s[sp] = P; stk_par[sp] = k; stk_side[sp] = 0; ++sp;
+        }
+        if (par >= 0) {
+            BvhNode& R = rec[par];
+            if (side == 0) {
+                R.a = make_float4(b.lx, b.hx, b.ly, b.hy);
+                R.c.x = b.lz; R.c.y = b.hz;
+                R.d.x = r;
+            } else {
+                R.b = make_float4(b.lx, b.hx, b.ly, b.hy);
+                R.c.z = b.lz; R.c.w = b.hz;
+                R.d.y = r;
+            }
+            if (r >= 0) __stcg(parent + r, inner[par]);
+            else __stcg(leaf_parent + ~r, inner[par]);
+        }
+    }
+    for (int k = 0; k < ni; ++k) {
+        rec[k].d.z = 0;
+        rec[k].d.w = 0;
+        float4* q = reinterpret_cast<float4*>(nodes + inner[k]);
+        __stcg(q + 0, rec[k].a);
+        __stcg(q + 1, rec[k].b);
+        __stcg(q + 2, rec[k].c);
+        __stcg(reinterpret_cast<int4*>(q + 3), rec[k].d);
+    }
+}
+
+// One restructuring pass.  flags[] must be zero; a climb longer than any
+// valid tree allows (a corrupt parent chain) stops and raises the step flag.
+__global__ void k_treelets(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int32_t* flags, int64_t T,
+                           int32_t* status) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    int p = __ldcg(leaf_parent + leaf);
+    for (int level = 0; p >= 0 && p < T - 1; ++level) {
+        if (level >= 4096) {
+            atomicOr(status, FIPT_DEV_STEP_LIMIT);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;          // the other child's walk continues
+        __threadfence();
+        restructure(nodes, parent, leaf_parent, p);
+        __threadfence();
+        p = __ldcg(parent + p);
+    }
+}
+
 // One-triangle scene: a root whose first child is leaf 0 and whose second
 // child has an empty box.
 __global__ void k_single(BvhNode* nodes, const float4* __restrict__ tris, int32_t* range) {
@@ -495,10 +665,16 @@ __global__ void k_single(BvhNode* nodes, const float4* __restrict__ tris, int32_
     range[0] = 0; range[1] = 0; range[2] = 0;
 }
 
-__global__ void k_export_boxes(const BvhNode* __restrict__ nodes, int64_t n, float* __restrict__ out) {
+__global__ void k_export_boxes(const BvhNode* __restrict__ nodes, int64_t n, float* __restrict__ out,
+                               int32_t* __restrict__ child) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const BvhNode nd = nodes[i];
+    if (child) {
+        child[2 * i] = nd.d.x;
+        child[2 * i + 1] = nd.d.y;
+    }
+    if (!out) return;
     out[6 * i + 0] = fminf(nd.a.x, nd.b.x);
     out[6 * i + 1] = fminf(nd.a.z, nd.b.z);
     out[6 * i + 2] = fminf(nd.c.x, nd.c.z);
@@ -698,6 +874,23 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
     return FIPT_OK;
 }
 
+extern "C" fipt_status fipt_scene_optimize(fipt_scene* s, int32_t passes, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(passes >= 0 && passes <= 16, "passes must be in [0, 16]");
+    const int64_t T = s->T;
+    if (T < 3 || passes == 0) return FIPT_OK;
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < passes; ++k) {
+        FIPT_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (size_t)(T - 1), st));
+        FIPT_LAUNCH(k_treelets, grid_for(T, 128), 128, 0, st, s->nodes, s->parent, s->leaf_parent, s->flags, T,
+                    s->ctx->status);
+    }
+    FIPT_LAUNCHED("treelet restructuring");
+    s->restructured = true;
+    return FIPT_OK;
+}
+
 extern "C" fipt_status fipt_scene_set_cache(fipt_scene* s, const float* cache, fipt_stream stream) {
     FIPT_REQUIRE(s, "scene is NULL");
     FIPT_REQUIRE(s->T == 0 || (cache && fipt_aligned(cache, 4)), "cache is NULL or misaligned");
@@ -731,7 +924,7 @@ extern "C" fipt_status fipt_scene_info(fipt_scene* s, fipt_stream stream, int64_
 }
 
 extern "C" fipt_status fipt_scene_debug_export(fipt_scene* s, uint64_t* morton, int32_t* order,
-                                               int32_t* node_range, float* node_box,
+                                               int32_t* node_range, float* node_box, int32_t* node_child,
                                                fipt_stream stream) {
     FIPT_REQUIRE(s, "scene is NULL");
     FIPT_CUDA(cudaSetDevice(s->ctx->device));
@@ -740,10 +933,12 @@ extern "C" fipt_status fipt_scene_debug_export(fipt_scene* s, uint64_t* morton, 
     if (T == 0) return FIPT_OK;
     if (morton) FIPT_CUDA(cudaMemcpyAsync(morton, s->keys, 8 * (size_t)T, cudaMemcpyDeviceToDevice, st));
     if (order) FIPT_CUDA(cudaMemcpyAsync(order, s->order, 4 * (size_t)T, cudaMemcpyDeviceToDevice, st));
+    FIPT_REQUIRE(!(node_range && s->restructured),
+                 "the tree was restructured: its nodes no longer match the radix-tree ranges");
     if (node_range)
         FIPT_CUDA(cudaMemcpyAsync(node_range, s->range, 12 * (size_t)ni, cudaMemcpyDeviceToDevice, st));
-    if (node_box) {
-        FIPT_LAUNCH(k_export_boxes, grid_for(ni, 256), 256, 0, st, s->nodes, ni, node_box);
+    if (node_box || node_child) {
+        FIPT_LAUNCH(k_export_boxes, grid_for(ni, 256), 256, 0, st, s->nodes, ni, node_box, node_child);
         FIPT_LAUNCHED("export boxes");
     }
     return FIPT_OK;

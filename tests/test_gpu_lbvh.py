@@ -21,7 +21,7 @@ def _compare(F, V, F_idx):
     T = len(F_idx)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     Le = np.zeros((T, 3), np.float32)
-    sc = F.Scene(t(V), t(F_idx), t(Le), t(Le))
+    sc = F.Scene(t(V), t(F_idx), t(Le), t(Le), optimize=0)      # the radix tree as built
     ex = {k: v.cpu().numpy() for k, v in sc.export().items()}
     ref = O.lbvh_reference(V, F_idx)
     assert np.array_equal(ex["morton"].view(np.uint64), ref["sorted_codes"])
