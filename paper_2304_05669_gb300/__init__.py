@@ -130,13 +130,15 @@ def unpack_queries(q):
             "tri": q[:, 9:10].contiguous().view(torch.int32)[:, 0]}
 
 
-OPTIMIZE_PASSES = 2      # treelet-restructuring passes a Scene gets by default
+OPTIMIZE_PASSES = 2      # treelet-restructuring passes a Scene gets by default ...
+OPTIMIZE_MIN_TRIS = 4096  # ... from this many triangles (smaller trees stay cache-resident)
 
 
 class Scene:
     """A triangle mesh with its device-built LBVH (``fipt_scene_create``),
     then ``optimize`` treelet-restructuring passes (``fipt_scene_optimize``;
-    0 keeps the radix tree as built)."""
+    0 keeps the radix tree as built; by default OPTIMIZE_PASSES for scenes
+    of at least OPTIMIZE_MIN_TRIS triangles)."""
 
     def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None, optimize=None):
         V = _dev(V, torch.float32, "V")
@@ -156,7 +158,9 @@ class Scene:
                                       _stream(stream), ctypes.byref(h)))
         self.handle = h
         self._keep = (V, F, Le, cache)    # alive until the stream has consumed them
-        optimize = OPTIMIZE_PASSES if optimize is None else int(optimize)
+        if optimize is None:
+            optimize = OPTIMIZE_PASSES if self.T >= OPTIMIZE_MIN_TRIS else 0
+        optimize = int(optimize)
         self.optimized = optimize
         if optimize:
             check(lib().fipt_scene_optimize(h, int(optimize), _stream(stream)))

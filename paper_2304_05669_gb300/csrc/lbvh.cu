@@ -519,7 +519,19 @@ __device__ __forceinline__ void child_boxes(const BvhNode* nodes, int n, Box& b0
     b1 = Box{b.x, b.z, c.z, b.y, b.w, c.w};
 }
 
-__device__ void restructure(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int p) {
+// Per-warp tables of the dynamic programme (shared memory).
+struct TreeletTables {
+    float area[1 << TREELET];
+    float cost[1 << TREELET];
+    uint8_t part[1 << TREELET];
+};
+
+// Restructures the treelet rooted at p; all 32 lanes of the warp call it
+// with the same p.  Every lane forms the treelet (the same loads, served
+// once), the lanes share the subsets of each size in the programme, and
+// lane 0 writes the new internal nodes.
+__device__ void restructure_warp(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int p,
+                                 TreeletTables& tb, int lane) {
     int ref[TREELET];
     Box box[TREELET];
     int inner[TREELET - 1];
@@ -533,6 +545,7 @@ __device__ void restructure(BvhNode* nodes, int32_t* parent, int32_t* leaf_paren
     area_l[0] = half_area(box[0]);
     area_l[1] = half_area(box[1]);
     float cur = half_area(box_union(box[0], box[1]));     // the current internal areas
+#pragma unroll 1
     while (m < TREELET) {
         int best = -1;
         float ba = -1.0f;
@@ -552,104 +565,130 @@ __device__ void restructure(BvhNode* nodes, int32_t* parent, int32_t* leaf_paren
         area_l[m] = half_area(box[m]);
         ++m;
     }
-    if (m < 3) return;                                     // two leaves have one topology
+    if (m < 3) return;                                     // two leaves have one topology (uniform)
     const int full = (1 << m) - 1;
-    float area[1 << TREELET], cost[1 << TREELET];
-    uint8_t part[1 << TREELET];
-    for (int S = 1; S <= full; ++S) {
+    for (int S = lane + 1; S <= full; S += 32) {
         const int i0 = __ffs(S) - 1;
         Box b = box[i0];
         for (int i = i0 + 1; i < m; ++i)
             if (S & (1 << i)) b = box_union(b, box[i]);
-        area[S] = half_area(b);
-    }
-    for (int S = 1; S <= full; ++S) {
+        tb.area[S] = half_area(b);
         if ((S & (S - 1)) == 0) {
-            cost[S] = 0.0f;
-            part[S] = 0;
-            continue;
+            tb.cost[S] = 0.0f;
+            tb.part[S] = 0;
         }
-        const int low = S & -S;
-        float best = __int_as_float(0x7f800000);
-        int bp = low;
-        for (int P = (S - 1) & S; P > 0; P = (P - 1) & S) {
-            if (!(P & low)) continue;
-            const float v = cost[P] + cost[S ^ P];
-            if (v < best) {
-                best = v;
-                bp = P;
+    }
+    __syncwarp();
+    for (int k = 2; k <= m; ++k) {                         // subsets by size: smaller ones are done
+        for (int S = lane + 1; S <= full; S += 32) {
+            if (__popc(S) != k) continue;
+            const int low = S & -S;
+            float best = __int_as_float(0x7f800000);
+            int bp = low;
+            for (int P = (S - 1) & S; P > 0; P = (P - 1) & S) {
+                if (!(P & low)) continue;
+                const float v = tb.cost[P] + tb.cost[S ^ P];
+                if (v < best) {
+                    best = v;
+                    bp = P;
+                }
             }
+            tb.cost[S] = best + tb.area[S];
+            tb.part[S] = (uint8_t)bp;
         }
-        cost[S] = best + area[S];
-        part[S] = (uint8_t)bp;
+        __syncwarp();
     }
-    if (!(cost[full] < cur * 0.99999f)) return;            // keep the current topology
-    // rebuild: depth-first from the full set; internal node k = inner[k]
-    BvhNode rec[TREELET - 1];
-    int stk_s[2 * TREELET], stk_par[2 * TREELET], stk_side[2 * TREELET];
-    int sp = 0, next = 0;
-    stk_s[sp] = full; stk_par[sp] = -1; stk_side[sp] = 0; ++sp;
-    while (sp > 0) {
-        --sp;
-        const int S = stk_s[sp], par = stk_par[sp], side = stk_side[sp];
-        int r;
-        const int i0 = __ffs(S) - 1;
-        Box b = box[i0];
-        for (int i = i0 + 1; i < m; ++i)
-            if (S & (1 << i)) b = box_union(b, box[i]);
-        if ((S & (S - 1)) == 0) {
-            r = ref[i0];
-        } else {
-            const int k = next++;
-            r = inner[k];
-            const int P = part[S];
-            stk_s[sp] = S ^ P; stk_par[sp] = k; stk_side[sp] = 1; ++sp;
-            stk_s[sp] = P; stk_par[sp] = k; stk_side[sp] = 0; ++sp;
-        }
-        if (par >= 0) {
-            BvhNode& R = rec[par];
-            if (side == 0) {
-                R.a = make_float4(b.lx, b.hx, b.ly, b.hy);
-                R.c.x = b.lz; R.c.y = b.hz;
-                R.d.x = r;
+    if (lane == 0 && tb.cost[full] < cur * 0.99999f) {    // else keep the current topology
+        // rebuild: depth-first from the full set; internal node k = inner[k]
+        BvhNode rec[TREELET - 1];
+        int stk_s[2 * TREELET], stk_par[2 * TREELET], stk_side[2 * TREELET];
+        int sp = 0, next = 0;
+        stk_s[sp] = full; stk_par[sp] = -1; stk_side[sp] = 0; ++sp;
+        while (sp > 0) {
+            --sp;
+            const int S = stk_s[sp], par = stk_par[sp], side = stk_side[sp];
+            int r;
+            const int i0 = __ffs(S) - 1;
+            Box b = box[i0];
+            for (int i = i0 + 1; i < m; ++i)
+                if (S & (1 << i)) b = box_union(b, box[i]);
+            if ((S & (S - 1)) == 0) {
+                r = ref[i0];
             } else {
-                R.b = make_float4(b.lx, b.hx, b.ly, b.hy);
-                R.c.z = b.lz; R.c.w = b.hz;
-                R.d.y = r;
+                const int k = next++;
+                r = inner[k];
+                const int P = tb.part[S];
+                stk_s[sp] = S ^ P; stk_par[sp] = k; stk_side[sp] = 1; ++sp;
+                stk_s[sp] = P; stk_par[sp] = k; stk_side[sp] = 0; ++sp;
             }
-            if (r >= 0) __stcg(parent + r, inner[par]);
-            else __stcg(leaf_parent + ~r, inner[par]);
+            if (par >= 0) {
+                BvhNode& R = rec[par];
+                if (side == 0) {
+                    R.a = make_float4(b.lx, b.hx, b.ly, b.hy);
+                    R.c.x = b.lz; R.c.y = b.hz;
+                    R.d.x = r;
+                } else {
+                    R.b = make_float4(b.lx, b.hx, b.ly, b.hy);
+                    R.c.z = b.lz; R.c.w = b.hz;
+                    R.d.y = r;
+                }
+                if (r >= 0) __stcg(parent + r, inner[par]);
+                else __stcg(leaf_parent + ~r, inner[par]);
+            }
         }
+        for (int k = 0; k < ni; ++k) {
+            rec[k].d.z = 0;
+            rec[k].d.w = 0;
+            float4* q = reinterpret_cast<float4*>(nodes + inner[k]);
+            __stcg(q + 0, rec[k].a);
+            __stcg(q + 1, rec[k].b);
+            __stcg(q + 2, rec[k].c);
+            __stcg(reinterpret_cast<int4*>(q + 3), rec[k].d);
+        }
+        __threadfence();
     }
-    for (int k = 0; k < ni; ++k) {
-        rec[k].d.z = 0;
-        rec[k].d.w = 0;
-        float4* q = reinterpret_cast<float4*>(nodes + inner[k]);
-        __stcg(q + 0, rec[k].a);
-        __stcg(q + 1, rec[k].b);
-        __stcg(q + 2, rec[k].c);
-        __stcg(reinterpret_cast<int4*>(q + 3), rec[k].d);
-    }
+    __syncwarp();
 }
 
-// One restructuring pass.  flags[] must be zero; a climb longer than any
-// valid tree allows (a corrupt parent chain) stops and raises the step flag.
-__global__ void k_treelets(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int32_t* flags, int64_t T,
-                           int32_t* status) {
-    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (leaf >= T) return;
-    int p = __ldcg(leaf_parent + leaf);
-    for (int level = 0; p >= 0 && p < T - 1; ++level) {
-        if (level >= 4096) {
-            atomicOr(status, FIPT_DEV_STEP_LIMIT);
-            return;
+constexpr int TL_THREADS = 128;
+
+// One restructuring pass.  flags[] must be zero.  Each thread climbs from
+// its leaf; at every round the warp restructures, one after the other, the
+// nodes its lanes were second to reach.  A climb longer than any valid
+// tree allows (a corrupt parent chain) stops and raises the step flag.
+__global__ void __launch_bounds__(TL_THREADS)
+k_treelets(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int32_t* flags, int64_t T, int32_t* status) {
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ TreeletTables tabs[TL_THREADS / 32];
+    TreeletTables& tb = tabs[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t leaf = blockIdx.x * (int64_t)TL_THREADS + threadIdx.x;
+    int p = leaf < T ? __ldcg(leaf_parent + leaf) : -1;
+    bool act = p >= 0 && p < T - 1;
+    int level = 0;
+    for (;;) {
+        if (act) {
+            if (++level > 4096) {
+                atomicOr(status, FIPT_DEV_STEP_LIMIT);
+                act = false;
+            } else {
+                __threadfence();
+                if (atomicAdd(&flags[p], 1) == 0) act = false;   // the other child's climb goes on
+                __threadfence();
+            }
         }
-        __threadfence();
-        if (atomicAdd(&flags[p], 1) == 0) return;          // the other child's walk continues
-        __threadfence();
-        restructure(nodes, parent, leaf_parent, p);
-        __threadfence();
-        p = __ldcg(parent + p);
+        unsigned todo = __ballot_sync(FULL, act);
+        if (todo == 0) break;
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            restructure_warp(nodes, parent, leaf_parent, __shfl_sync(FULL, p, l), tb, lane);
+        }
+        if (act) {
+            __threadfence();
+            p = __ldcg(parent + p);
+            act = p >= 0 && p < T - 1;
+        }
     }
 }
 
@@ -883,7 +922,7 @@ extern "C" fipt_status fipt_scene_optimize(fipt_scene* s, int32_t passes, fipt_s
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     for (int k = 0; k < passes; ++k) {
         FIPT_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (size_t)(T - 1), st));
-        FIPT_LAUNCH(k_treelets, grid_for(T, 128), 128, 0, st, s->nodes, s->parent, s->leaf_parent, s->flags, T,
+        FIPT_LAUNCH(k_treelets, grid_for(T, TL_THREADS), TL_THREADS, 0, st, s->nodes, s->parent, s->leaf_parent, s->flags, T,
                     s->ctx->status);
     }
     FIPT_LAUNCHED("treelet restructuring");
