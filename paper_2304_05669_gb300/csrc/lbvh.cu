@@ -498,7 +498,10 @@ __global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
 // with boxes as tight as before, and a closest-hit walk returns the same
 // (t, triangle) minimum on any valid tree, up to near-ties that float32
 // cannot separate (the culling bound depends on the visit order).
-constexpr int TREELET = 7;
+#ifndef FIPT_TREELET
+#define FIPT_TREELET 7           // leaves per treelet: 2^7 - 1 subsets in the programme
+#endif
+constexpr int TREELET = FIPT_TREELET;
 
 __device__ __forceinline__ float half_area(const Box& b) {
     const float dx = fmaxf(b.hx - b.lx, 0.0f), dy = fmaxf(b.hy - b.ly, 0.0f), dz = fmaxf(b.hz - b.lz, 0.0f);
@@ -523,7 +526,7 @@ __device__ __forceinline__ void child_boxes(const BvhNode* nodes, int n, Box& b0
 struct TreeletTables {
     float area[1 << TREELET];
     float cost[1 << TREELET];
-    uint8_t part[1 << TREELET];
+    uint16_t part[1 << TREELET];
 };
 
 // Restructures the treelet rooted at p; all 32 lanes of the warp call it
@@ -594,7 +597,7 @@ __device__ void restructure_warp(BvhNode* nodes, int32_t* parent, int32_t* leaf_
                 }
             }
             tb.cost[S] = best + tb.area[S];
-            tb.part[S] = (uint8_t)bp;
+            tb.part[S] = (uint16_t)bp;
         }
         __syncwarp();
     }
