@@ -142,3 +142,47 @@ def test_trace_and_refine_on_restructured_tree(fipt):
     (h0, r0), (h1, r1) = res
     assert (h0[0] != h1[0]).mean() < 1e-4                    # rays from inside the room
     assert (r0 != r1).any(1).mean() < 0.02
+
+
+@pytest.mark.parametrize("case", ["T3", "T4", "T9", "identical", "planar"])
+def test_restructuring_edge_cases(fipt, case):
+    """The smallest trees a treelet can reshape, 500 copies of one triangle
+    (every box the same: no topology is cheaper, nothing is rewritten) and a
+    planar grid (boxes flat in one axis): the tree stays valid and closest
+    hits stay those of the radix tree."""
+    rng = np.random.default_rng(17)
+    if case.startswith("T"):
+        T = int(case[1:])
+        V = rng.uniform(0, 1, (3 * T, 3)).astype(np.float32)
+        Fi = np.arange(3 * T, dtype=np.int32).reshape(T, 3)
+    elif case == "identical":
+        T = 500
+        V = np.tile(np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32), (T, 1))
+        Fi = np.arange(3 * T, dtype=np.int32).reshape(T, 3)
+    else:
+        n = 40
+        g = np.stack(np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij"), -1).reshape(-1, 2)
+        V = np.concatenate([g, np.zeros((len(g), 1))], 1).astype(np.float32)
+        idx = lambda i, j: i * (n + 1) + j
+        Fi = np.array([[idx(i, j), idx(i + 1, j), idx(i + 1, j + 1)] for i in range(n) for j in range(n)]
+                      + [[idx(i, j), idx(i + 1, j + 1), idx(i, j + 1)] for i in range(n) for j in range(n)],
+                      np.int32)
+        T = len(Fi)
+    z = cu(np.zeros((T, 3), np.float32))
+    opt = fipt.Scene(cu(V), cu(Fi), z, z, optimize=3)
+    plain = fipt.Scene(cu(V), cu(Fi), z, z, optimize=0)
+    ex = {k: v.cpu().numpy() for k, v in opt.export().items()}
+    ex0 = {k: v.cpu().numpy() for k, v in plain.export().items()}
+    tv = V[Fi[ex["order"]]]
+    check_tree(ex, T, np.concatenate([tv.min(1), tv.max(1)], 1).astype(np.float32))
+    if case == "identical":
+        assert np.array_equal(ex["child"], ex0["child"])
+    P = 20000
+    lo, hi = V.min(0) - 0.5, V.max(0) + 0.5
+    o = (lo + rng.uniform(0, 1, (P, 3)) * (hi - lo)).astype(np.float32)
+    d = rng.normal(size=(P, 3)).astype(np.float32)
+    a = [x.cpu().numpy() for x in opt.trace(cu(o), cu(d))]
+    b = [x.cpu().numpy() for x in plain.trace(cu(o), cu(d))]
+    fipt.context().sync_status()
+    assert np.array_equal(a[0] >= 0, b[0] >= 0)        # a hit exists or not, whatever the tree
+    assert (a[0] != b[0]).mean() < 1e-3
