@@ -485,8 +485,9 @@ __global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
 
 // ---------------------------------------------------------------- treelets
 // Treelet restructuring (Karras and Aila, HPG 2013) of the built tree.  A
-// walk from every leaf climbs as in k_refit; the second thread to reach an
-// internal node p (its subtree is final) forms a treelet: p's two children,
+// walk from every leaf climbs as in k_refit; when the second climb reaches
+// an internal node p (its subtree is final), that thread's warp forms a
+// treelet: p's two children,
 // then, until there are TREELET leaves or only triangles, the treelet leaf
 // with the largest surface area is replaced by its two children.  With one
 // triangle per leaf the SAH cost of a topology differs from another's only
@@ -502,6 +503,7 @@ __global__ void k_refit(BvhNode* nodes, const float4* __restrict__ tris,
 #define FIPT_TREELET 7           // leaves per treelet: 2^7 - 1 subsets in the programme
 #endif
 constexpr int TREELET = FIPT_TREELET;
+static_assert(TREELET >= 3 && TREELET <= 12, "treelets of 3 to 12 leaves");
 
 __device__ __forceinline__ float half_area(const Box& b) {
     const float dx = fmaxf(b.hx - b.lx, 0.0f), dy = fmaxf(b.hy - b.ly, 0.0f), dz = fmaxf(b.hz - b.lz, 0.0f);
