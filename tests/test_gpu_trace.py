@@ -27,6 +27,33 @@ def test_philox_stream_matches_oracle(fipt):
     assert np.array_equal(g, O.philox4x32_10(ctr, key))
 
 
+def test_philox_matches_curand(fipt, tmp_path):
+    """The library's Philox4x32-10 and the oracle's against CUDA's own
+    (curand_Philox4x32_10, compiled here into a small test helper) on the
+    same counters and keys."""
+    import ctypes
+    import os
+    import subprocess
+    from paper_2304_05669_gb300 import build as nb
+    so = tmp_path / "libcurand_philox.so"
+    subprocess.run([nb._nvcc(), *nb.ARCH, "-O2", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                    os.path.join(os.path.dirname(__file__), "c", "curand_philox.cu"), "-o", str(so)], check=True)
+    L = ctypes.CDLL(str(so))
+    rng = np.random.default_rng(1)
+    n = 1 << 18
+    ctr = rng.integers(0, 2 ** 32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xffffffff] * 4, [1, 2, 3, 4], [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]]
+    key[:4] = [[0, 0], [0xffffffff] * 2, [5, 6], [0xa4093822, 0x299f31d0]]
+    ref = np.zeros((n, 4), np.uint32)
+    P = ctypes.c_void_p
+    assert L.curand_philox_batch(P(ctr.ctypes.data), P(key.ctypes.data), ctypes.c_int64(n), P(ref.ctypes.data)) == 0
+    g = fipt.philox(torch.from_numpy(ctr.view(np.int32)).cuda(),
+                    torch.from_numpy(key.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+    assert np.array_equal(g, ref)
+    assert np.array_equal(O.philox4x32_10(ctr, key), ref)
+
+
 def _rays(rng, lo, hi, n):
     o = rng.uniform(lo + 0.02, hi - 0.02, (n, 3)).astype(np.float32)
     d = rng.normal(size=(n, 3)).astype(np.float32)
