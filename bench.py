@@ -317,9 +317,9 @@ def run_reference(args, wl, world, rank):
 
 
 # ---------------------------------------------------------------- render workload
-# one pass: Ld, the two specular rows (K = 6), albedo, rough, metal, Lgt in;
-# Lr and the three gradients out
-RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12) + (12 + 12 + 4 + 4)
+# one pass: Ld, the two specular rows (K = 6), albedo, rough, metal, Lgt and
+# the emitter mask in; Lr and the three gradients out
+RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12 + 1) + (12 + 12 + 4 + 4)
 
 
 def run_render(args, wl, world, rank, local):
@@ -342,10 +342,13 @@ def run_render(args, wl, world, rank, local):
     tabs = F.bake(sc, q[:N], SIGMA, wl["spp_d"], wl["spp_s"], seed=0, request_id=rank)
     F.context().sync_status()
     Ld, Ls0, Ls1 = (t.cpu().numpy() for t in tabs)
+    # pixels whose first hit is an emitter are left out of the loss (an input, built once)
+    tri = q[:N, 9].contiguous().view(torch.int32).cpu().numpy()
+    mask = (~mesh.emitter[tri]).astype(np.uint8)
     del q, qa, valid, tabs
     mp, gt = material_params(N, seed=3), material_params(N, seed=4)
     host = {"Ld": Ld, "Ls0": Ls0, "Ls1": Ls1, "albedo": mp["albedo"], "rough": mp["rough"],
-            "metal": mp["metal"]}
+            "metal": mp["metal"], "mask": mask}
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
     d = {k: v.to(dev) for k, v in pinned.items()}
     gtd = {k: torch.from_numpy(v).to(dev) for k, v in gt.items()}
@@ -359,7 +362,7 @@ def run_render(args, wl, world, rank, local):
         # forward, loss and gradient in one pass over the inputs, then the
         # upstream gradient applied (the library's backward of the loss)
         Lr, loss, g = F.render_fwd_grad(x["Ld"], x["Ls0"], x["Ls1"], SIGMA, x["albedo"], x["rough"],
-                                        x["metal"], lg)
+                                        x["metal"], lg, x["mask"])
         F.render_grad_scale(g, one)
         return loss, g
 
@@ -422,9 +425,9 @@ def run_render(args, wl, world, rank, local):
         sl = slice(0, n)
         t0 = time.perf_counter()
         O.render_forward(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, mp["albedo"][sl], mp["rough"][sl], mp["metal"][sl],
-                         Lgt_host.numpy()[sl])
+                         Lgt_host.numpy()[sl], mask[sl])
         O.render_grad(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, mp["albedo"][sl], mp["rough"][sl], mp["metal"][sl],
-                      Lgt_host.numpy()[sl])
+                      Lgt_host.numpy()[sl], mask[sl])
         dt = time.perf_counter() - t0
         cpu = {"value": round(n / dt / 1e6, 4), "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
                "sample": "first %d pixels, forward + loss + analytic gradient, numpy FP64, %.1f s" % (n, dt)}
