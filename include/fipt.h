@@ -149,6 +149,16 @@ fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t nV, const i
  * a property of the acceleration structure only. */
 fipt_status fipt_scene_optimize(fipt_scene* scene, int32_t passes, fipt_stream stream);
 
+/* Renumbers the scene's internal nodes depth-first (root 0, a node's first
+ * child right after it, its second child after the first child's subtree)
+ * so that a walk's node records share cache lines more often; topology,
+ * child order and boxes are unchanged, so every walk visits the same nodes
+ * in the same order and every result is bit-identical.  Run it after
+ * fipt_scene_optimize and before the scene is given to a server.  The
+ * radix-tree ranges of fipt_scene_debug_export no longer describe the tree
+ * afterwards.  Not an operation of the paper. */
+fipt_status fipt_scene_relayout(fipt_scene* scene, fipt_stream stream);
+
 /* Replaces the radiance cache (cache [T,3] f32, original triangle order)
  * without rebuilding the BVH -- the refined-cache update between stages. */
 fipt_status fipt_scene_set_cache(fipt_scene* scene, const float* cache, fipt_stream stream);

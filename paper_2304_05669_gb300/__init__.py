@@ -132,15 +132,19 @@ def unpack_queries(q):
 
 OPTIMIZE_PASSES = 2      # treelet-restructuring passes a Scene gets by default ...
 OPTIMIZE_MIN_TRIS = 4096  # ... from this many triangles (smaller trees stay cache-resident)
+RELAYOUT = True           # depth-first node renumbering after the passes
 
 
 class Scene:
     """A triangle mesh with its device-built LBVH (``fipt_scene_create``),
     then ``optimize`` treelet-restructuring passes (``fipt_scene_optimize``;
     0 keeps the radix tree as built; by default OPTIMIZE_PASSES for scenes
-    of at least OPTIMIZE_MIN_TRIS triangles)."""
+    of at least OPTIMIZE_MIN_TRIS triangles) and, after them, a depth-first
+    renumbering of the nodes (``fipt_scene_relayout``; ``relayout=False``
+    skips it)."""
 
-    def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None, optimize=None):
+    def __init__(self, V, F, Le, cache, ctx: Context | None = None, stream=None, optimize=None,
+                 relayout=None):
         V = _dev(V, torch.float32, "V")
         F = _dev(F, torch.int32, "F")
         Le = _dev(Le, torch.float32, "Le")
@@ -164,6 +168,8 @@ class Scene:
         self.optimized = optimize
         if optimize:
             check(lib().fipt_scene_optimize(h, int(optimize), _stream(stream)))
+            if RELAYOUT if relayout is None else relayout:
+                check(lib().fipt_scene_relayout(h, _stream(stream)))
 
     @classmethod
     def from_mesh(cls, mesh, device="cuda", **kw):

@@ -56,6 +56,7 @@ SIGNATURES = {
     "fipt_scene_info": [P, P, P, P, P, P],
     "fipt_scene_debug_export": [P, P, P, P, P, P, P],
     "fipt_scene_optimize": [P, I32, P],
+    "fipt_scene_relayout": [P, P],
     "fipt_trace_closest": [P, P, P, I64, P, P, P, P, P],
     "fipt_camera_queries": [P, P, I32, I32, I32, P, P, P],
     "fipt_compact_workspace_size": [I64, P],

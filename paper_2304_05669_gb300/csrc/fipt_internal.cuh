@@ -77,7 +77,9 @@ struct fipt_scene {
     int32_t* emit_leaf;    // [T] (first n_emit used)
     double* emit_cdf;      // [T]
     bool has_materials = false;
-    bool restructured = false;    // fipt_scene_optimize ran (range[] is the radix tree's only)
+    bool restructured = false;    // fipt_scene_optimize / relayout ran (range[] is the radix tree's only)
+    BvhNode* nodes_alt = nullptr; // second node array (relayout target)
+    int32_t* scratch = nullptr;   // [3 (T-1)] relayout scratch
     const float* env = nullptr;   // caller-owned environment map
     int env_w = 0, env_h = 0;
     const float4* vox = nullptr;  // caller-owned voxel radiance cache

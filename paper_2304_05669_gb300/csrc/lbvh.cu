@@ -697,6 +697,86 @@ k_treelets(BvhNode* nodes, int32_t* parent, int32_t* leaf_parent, int32_t* flags
     }
 }
 
+// ---------------------------------------------------------------- relayout
+// Depth-first renumbering of the internal nodes: the root stays 0, a node's
+// first child follows it, its second child follows the first child's
+// subtree.  Walks descend into the first child most of the time and
+// subtrees occupy contiguous records, so a walk's records share cache lines
+// more often.  The topology, child order and boxes are unchanged: every walk
+// visits the same nodes in the same order as before, on new addresses.
+
+// Internal nodes in every subtree (a climb as in k_refit; flags zeroed).
+__global__ void k_subtree_sizes(const BvhNode* nodes, const int32_t* parent, const int32_t* leaf_parent,
+                                int32_t* flags, int32_t* size, int64_t T, int32_t* status) {
+    const int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (leaf >= T) return;
+    int p = __ldcg(leaf_parent + leaf);
+    for (int level = 0; p >= 0 && p < T - 1; ++level) {
+        if (level >= 4096) {
+            atomicOr(status, FIPT_DEV_STEP_LIMIT);
+            return;
+        }
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;          // the other child's climb goes on
+        __threadfence();
+        const int4 ch = __ldcg(reinterpret_cast<const int4*>(nodes + p) + 3);
+        const int s0 = (ch.x >= 0 && ch.x < T - 1) ? __ldcg(size + ch.x) : 0;
+        const int s1 = (ch.y >= 0 && ch.y < T - 1) ? __ldcg(size + ch.y) : 0;
+        __stcg(size + p, s0 + s1 + 1);
+        __threadfence();
+        p = __ldcg(parent + p);
+    }
+}
+
+// Depth-first index of every internal node: the sum, over the path from
+// the root, of 1 per step plus the first child's subtree size where the
+// path takes the second child.
+__global__ void k_dfs_index(const BvhNode* __restrict__ nodes, const int32_t* __restrict__ parent,
+                            const int32_t* __restrict__ size, int32_t* __restrict__ idx, int64_t n,
+                            int32_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cur = (int)i, pos = 0;
+    for (int level = 0; cur != 0; ++level) {
+        const int p = cur > 0 && cur < n ? parent[cur] : -1;
+        if (level >= 4096 || p < 0 || p >= n) {
+            atomicOr(status, FIPT_DEV_STEP_LIMIT);
+            idx[i] = -1;
+            return;
+        }
+        const int4 ch = __ldg(reinterpret_cast<const int4*>(nodes + p) + 3);
+        pos += (cur == ch.y && ch.x >= 0 && ch.x < n) ? 1 + size[ch.x] : 1;
+        cur = p;
+    }
+    idx[i] = pos;
+}
+
+// Writes node i's record at idx[i] with renumbered child and parent links.
+__global__ void k_relabel(const BvhNode* __restrict__ nodes, const int32_t* __restrict__ parent,
+                          const int32_t* __restrict__ idx, BvhNode* __restrict__ out,
+                          int32_t* __restrict__ out_parent, int64_t n, int32_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = idx[i];
+    if (j < 0 || j >= n) {
+        atomicOr(status, FIPT_DEV_BAD_NODE);
+        return;
+    }
+    BvhNode r = nodes[i];
+    if (r.d.x >= 0) r.d.x = r.d.x < n ? idx[r.d.x] : r.d.x;
+    if (r.d.y >= 0) r.d.y = r.d.y < n ? idx[r.d.y] : r.d.y;
+    out[j] = r;
+    const int p = parent[i];
+    out_parent[j] = (p >= 0 && p < n) ? idx[p] : -1;
+}
+
+__global__ void k_relabel_leaves(int32_t* leaf_parent, const int32_t* __restrict__ idx, int64_t T, int64_t n) {
+    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= T) return;
+    const int p = leaf_parent[l];
+    if (p >= 0 && p < n) leaf_parent[l] = idx[p];
+}
+
 // One-triangle scene: a root whose first child is leaf 0 and whose second
 // child has an empty box.
 __global__ void k_single(BvhNode* nodes, const float4* __restrict__ tris, int32_t* range) {
@@ -807,6 +887,8 @@ namespace {
 struct SceneLayout {
     SceneConst* cst;
     BvhNode* nodes;
+    BvhNode* nodes_alt;     // the relayout's target
+    int32_t* scratch;       // [3 (T-1)] subtree sizes, new indices, new parents
     float4* tris;
     float4* shade;
     int32_t* order;
@@ -826,6 +908,8 @@ SceneLayout carve_scene(void* ws, int64_t T) {
     const int64_t t1 = T > 0 ? T : 1;
     L.cst = c.take<SceneConst>(1);
     L.nodes = c.take<BvhNode>((size_t)ni);
+    L.nodes_alt = c.take<BvhNode>((size_t)ni);
+    L.scratch = c.take<int32_t>((size_t)(3 * ni));
     L.tris = c.take<float4>((size_t)(3 * t1));
     L.shade = c.take<float4>((size_t)(2 * t1));
     L.order = c.take<int32_t>((size_t)t1);
@@ -880,6 +964,7 @@ extern "C" fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t 
     s->hist = L.hist; s->range = L.range; s->parent = L.parent; s->leaf_parent = L.leaf_parent;
     s->flags = L.flags; s->ws_bytes = L.bytes;
     s->mats = L.mats; s->inv = L.inv; s->emit_leaf = L.emit_leaf; s->emit_cdf = L.emit_cdf;
+    s->nodes_alt = L.nodes_alt; s->scratch = L.scratch;
 
     FIPT_LAUNCH(k_bounds_init, 1, 32, 0, st, L.cst);
     if (nV > 0) {
@@ -931,6 +1016,31 @@ extern "C" fipt_status fipt_scene_optimize(fipt_scene* s, int32_t passes, fipt_s
                     s->ctx->status);
     }
     FIPT_LAUNCHED("treelet restructuring");
+    s->restructured = true;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_scene_relayout(fipt_scene* s, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    const int64_t T = s->T, n = T - 1;
+    if (T < 3) return FIPT_OK;
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t* size = s->scratch;
+    int32_t* idx = s->scratch + n;
+    int32_t* new_parent = s->scratch + 2 * n;
+    FIPT_CUDA(cudaMemsetAsync(s->flags, 0, sizeof(int32_t) * (size_t)n, st));
+    FIPT_LAUNCH(k_subtree_sizes, grid_for(T, 256), 256, 0, st, s->nodes, s->parent, s->leaf_parent, s->flags, size,
+                T, s->ctx->status);
+    FIPT_LAUNCH(k_dfs_index, grid_for(n, 256), 256, 0, st, s->nodes, s->parent, size, idx, n, s->ctx->status);
+    FIPT_LAUNCH(k_relabel, grid_for(n, 256), 256, 0, st, s->nodes, s->parent, idx, s->nodes_alt, new_parent, n,
+                s->ctx->status);
+    FIPT_LAUNCH(k_relabel_leaves, grid_for(T, 256), 256, 0, st, s->leaf_parent, idx, T, n);
+    FIPT_LAUNCHED("relayout");
+    BvhNode* t = s->nodes;
+    s->nodes = s->nodes_alt;
+    s->nodes_alt = t;
+    FIPT_CUDA(cudaMemcpyAsync(s->parent, new_parent, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     s->restructured = true;
     return FIPT_OK;
 }

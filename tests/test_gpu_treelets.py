@@ -169,7 +169,8 @@ def test_restructuring_edge_cases(fipt, case):
                       np.int32)
         T = len(Fi)
     z = cu(np.zeros((T, 3), np.float32))
-    opt = fipt.Scene(cu(V), cu(Fi), z, z, optimize=3)
+    # no relayout where the test asks that restructuring rewrote nothing
+    opt = fipt.Scene(cu(V), cu(Fi), z, z, optimize=3, relayout=(case != "identical"))
     plain = fipt.Scene(cu(V), cu(Fi), z, z, optimize=0)
     ex = {k: v.cpu().numpy() for k, v in opt.export().items()}
     ex0 = {k: v.cpu().numpy() for k, v in plain.export().items()}
@@ -186,3 +187,33 @@ def test_restructuring_edge_cases(fipt, case):
     fipt.context().sync_status()
     assert np.array_equal(a[0] >= 0, b[0] >= 0)        # a hit exists or not, whatever the tree
     assert (a[0] != b[0]).mean() < 1e-3
+
+
+def test_relayout_is_depth_first_and_changes_no_result(fipt):
+    """fipt_scene_relayout renumbers the internal nodes depth-first (a node's
+    first internal child is the next record) without touching the topology:
+    the same boxes, the same walks (identical node, triangle and stack
+    counts) and bit-identical bakes."""
+    m = procedural_room(1)
+    T = m.T
+    q = surface_queries(m, 20000, seed=13)
+    res = []
+    for rl in (False, True):
+        sc = fipt.Scene.from_mesh(m, optimize=2, relayout=rl)
+        ex = {k: v.cpu().numpy() for k, v in sc.export().items()}
+        qt = fipt.pack_queries(cu(q["x"]), cu(q["n"]), cu(q["wo"]), cu(q["tri"]))
+        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        out = [x.cpu() for x in fipt.bake(sc, qt, SIGMA, 16, 16, seed=4, stats=st)]
+        fipt.context().sync_status()
+        res.append((ex, out, st.cpu().tolist()))
+    (ex0, out0, st0), (ex1, out1, st1) = res
+    ch = ex1["child"]
+    first = np.nonzero(ch[:, 0] >= 0)[0]
+    assert np.array_equal(ch[first, 0], first + 1)
+    tv = m.V[m.F[ex1["order"]]]
+    check_tree(ex1, T, np.concatenate([tv.min(1), tv.max(1)], 1).astype(np.float32))
+    key = lambda b: b[np.lexsort(b.T[::-1])]
+    assert np.array_equal(key(ex0["box"]), key(ex1["box"]))
+    assert st0 == st1
+    for x, y in zip(out0, out1):
+        assert torch.equal(x, y)
