@@ -124,41 +124,125 @@ __global__ void k_emit_gather(const int32_t* __restrict__ tri, int64_t stride, i
     if (e) idx[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)p;
 }
 
-__global__ void k_emit_keys(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ cnt,
-                            const int32_t* __restrict__ tri, int64_t stride, const float* __restrict__ rgb,
-                            int c, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Sort keys of the gathered pixels: their triangle (stable sort keeps
+// gather order within a triangle, which the median does not depend on).
+__global__ void k_emit_tri_keys(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ cnt,
+                                const int32_t* __restrict__ tri, int64_t stride, uint32_t* __restrict__ keys,
+                                uint32_t* __restrict__ vals) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= (int64_t)*cnt) return;
     const int64_t p = idx[j];
-    keys[j] = ((uint64_t)(uint32_t)tri[p * stride] << 32) | fkey(rgb[3 * p + c]);
-    vals[j] = (uint32_t)j;
+    keys[j] = (uint32_t)tri[p * stride];
+    vals[j] = (uint32_t)p;
 }
 
-__global__ void k_emit_bounds(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ cnt, int64_t T,
-                              int32_t* __restrict__ start, int32_t* __restrict__ end) {
+// Segment bounds of every triangle with pixels, and the list of those
+// triangles (one atomic per warp; the list's order does not matter).
+__global__ void k_emit_bounds(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cnt, int64_t T,
+                              int32_t* __restrict__ start, int32_t* __restrict__ end, uint32_t* __restrict__ segs,
+                              uint32_t* __restrict__ nseg) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t P = *cnt;
-    if (j >= P) return;
-    const uint64_t s = keys[j] >> 32;
-    if (s >= (uint64_t)T) return;
-    if (j == 0 || (keys[j - 1] >> 32) != s) start[s] = (int32_t)j;
-    if (j == P - 1 || (keys[j + 1] >> 32) != s) end[s] = (int32_t)j;
+    const int lane = threadIdx.x & 31;
+    bool first = false;
+    uint32_t s = 0;
+    if (j < P) {
+        s = keys[j];
+        if (s < (uint64_t)T) {
+            first = j == 0 || keys[j - 1] != s;
+            if (first) start[s] = (int32_t)j;
+            if (j == P - 1 || keys[j + 1] != s) end[s] = (int32_t)j;
+        }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    if (m == 0) return;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(nseg, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (first) segs[base + __popc(m & ((1u << lane) - 1u))] = s;
 }
 
-__global__ void k_emit_median(const uint64_t* __restrict__ keys, const int32_t* __restrict__ start,
-                              const int32_t* __restrict__ end, int64_t T, int c,
-                              float* __restrict__ Le, int32_t* __restrict__ count) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    const int32_t a = start[t];
-    float v = 0.0f;
-    int32_t cnt = 0;
-    if (a >= 0) {
-        cnt = end[t] - a + 1;
-        v = funkey((uint32_t)(keys[a + (cnt - 1) / 2] & 0xFFFFFFFFu));
+// The three channels' order-preserving keys of the sorted pixels, laid out
+// [channel][sorted position] so that a triangle's keys are contiguous.
+__global__ void k_emit_chan_keys(const uint32_t* __restrict__ pix, const uint32_t* __restrict__ cnt,
+                                 const float* __restrict__ rgb, int64_t P, uint32_t* __restrict__ keys3) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= (int64_t)*cnt) return;
+    const int64_t p = pix[j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) keys3[c * P + j] = fkey(rgb[3 * p + c]);
+}
+
+constexpr int SEL_THREADS = 256;            // a block per triangle
+
+// Lower median of each channel of triangle t's pixels (positions a..e of
+// keys3) by radix selection on the order-preserving keys: four 8-bit
+// digits from the top, each pass counting the candidates' digit in a
+// shared histogram and keeping the bucket that holds rank (n - 1) / 2.  The
+// selected key is the one a sort would put at that rank, so the result
+// equals the sorted lower median.  Triangles without pixels get 0 and
+// count 0 (set beforehand).  Persistent: the blocks take the listed
+// triangles in turn.
+__global__ void __launch_bounds__(SEL_THREADS)
+k_emit_select(const uint32_t* __restrict__ keys3, int64_t P, const int32_t* __restrict__ start,
+              const int32_t* __restrict__ end, const uint32_t* __restrict__ segs, const uint32_t* __restrict__ nseg,
+              float* __restrict__ Le, int32_t* __restrict__ count) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t pick[2];
+    const int tid = threadIdx.x;
+    const uint32_t ns = *nseg;
+    for (uint32_t si = blockIdx.x; si < ns; si += gridDim.x) {
+        const int64_t t = segs[si];
+        const int32_t a = start[t];                         // the same for the whole block
+        const int32_t n = end[t] - a + 1;
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t* key = keys3 + c * P + a;
+            uint32_t prefix = 0, mask = 0, k = (uint32_t)(n - 1) / 2;
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                hist[tid] = 0;
+                __syncthreads();
+                for (int32_t j = tid; j < n; j += SEL_THREADS) {
+                    const uint32_t v = key[j];
+                    if ((v & mask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                if (tid < 32) {                             // warp 0 finds the bucket holding rank k
+                    uint32_t h[8], sum = 0;
+    #pragma unroll
+                    for (int b = 0; b < 8; ++b) {
+                        h[b] = hist[tid * 8 + b];
+                        sum += h[b];
+                    }
+                    uint32_t incl = sum;
+    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (tid >= o) incl += y;
+                    }
+                    const uint32_t excl = incl - sum;
+                    if (excl <= k && k < incl) {
+                        uint32_t run = excl;
+                        for (int b = 0; b < 8; ++b) {
+                            if (k < run + h[b]) {
+                                pick[0] = (uint32_t)(tid * 8 + b);
+                                pick[1] = run;
+                                break;
+                            }
+                            run += h[b];
+                        }
+                    }
+                }
+                __syncthreads();
+                k -= pick[1];
+                prefix |= pick[0] << shift;
+                mask |= 255u << shift;
+                __syncthreads();                            // pick[] and hist[] are reused
+            }
+            if (tid == 0) Le[3 * t + c] = funkey(prefix);
+        }
+        if (count && tid == 0) count[t] = n;
     }
-    Le[3 * t + c] = v;
-    if (count && c == 0) count[t] = cnt;
 }
 
 __global__ void k_set_emission(const float* __restrict__ Le, const int32_t* __restrict__ order,
@@ -170,8 +254,7 @@ __global__ void k_set_emission(const float* __restrict__ Le, const int32_t* __re
 }
 
 struct EmitLayout {
-    uint64_t *keys, *keys_alt;
-    uint32_t *vals, *vals_alt, *hist, *idx, *cnt;
+    uint32_t *keys, *keys_alt, *vals, *vals_alt, *hist, *idx, *keys3, *segs, *cnt;
     int32_t *start, *end;
     size_t bytes;
 };
@@ -180,15 +263,17 @@ EmitLayout carve(void* ws, int64_t P, int64_t T) {
     Carver c{static_cast<char*>(ws), 0};
     EmitLayout L;
     const int64_t p1 = P > 0 ? P : 1, t1 = T > 0 ? T : 1;
-    L.keys = c.take<uint64_t>((size_t)p1);
-    L.keys_alt = c.take<uint64_t>((size_t)p1);
+    L.keys = c.take<uint32_t>((size_t)p1);
+    L.keys_alt = c.take<uint32_t>((size_t)p1);
     L.vals = c.take<uint32_t>((size_t)p1);
     L.vals_alt = c.take<uint32_t>((size_t)p1);
     L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(p1) / sizeof(uint32_t));
     L.start = c.take<int32_t>((size_t)t1);
     L.end = c.take<int32_t>((size_t)t1);
     L.idx = c.take<uint32_t>((size_t)p1);
-    L.cnt = c.take<uint32_t>(1);
+    L.keys3 = c.take<uint32_t>((size_t)(3 * p1));
+    L.segs = c.take<uint32_t>((size_t)t1);
+    L.cnt = c.take<uint32_t>(2);                       // gathered pixels, listed triangles
     L.bytes = c.off + 256;
     return L;
 }
@@ -257,24 +342,27 @@ extern "C" fipt_status fipt_emitter_radiance(const int32_t* tri, int64_t tri_str
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     FIPT_CUDA(cudaMemsetAsync(Y.start, 0xFF, sizeof(int32_t) * (size_t)T, st));
     FIPT_CUDA(cudaMemsetAsync(Y.end, 0xFF, sizeof(int32_t) * (size_t)T, st));
-    int bits = 32;
-    while (((int64_t)1 << (bits - 32)) < T) ++bits;        // segment ids 0..T-1
-    bits = (bits + 7) & ~7;
-    FIPT_CUDA(cudaMemsetAsync(Y.cnt, 0, sizeof(uint32_t), st));
-    if (P > 0)
+    int bits = 0;
+    while (((int64_t)1 << bits) < T) ++bits;               // triangle ids 0..T-1
+    bits = bits > 0 ? (bits + 7) & ~7 : 8;
+    FIPT_CUDA(cudaMemsetAsync(Y.cnt, 0, 2 * sizeof(uint32_t), st));
+    FIPT_CUDA(cudaMemsetAsync(Le, 0, 3 * sizeof(float) * (size_t)T, st));
+    if (count) FIPT_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)T, st));
+    uint32_t* sv = Y.vals;
+    if (P > 0) {
         FIPT_LAUNCH(k_emit_gather, blocks(P, 256), 256, 0, st, tri, tri_stride, P, is_emitter, T, Y.idx, Y.cnt);
-    for (int c = 0; c < 3; ++c) {
-        uint64_t* sk = Y.keys;
-        if (P > 0) {
-            FIPT_LAUNCH(k_emit_keys, blocks(P, 256), 256, 0, st, Y.idx, Y.cnt, tri, tri_stride, rgb, c,
-                        Y.keys, Y.vals);
-            uint32_t* sv;
-            fipt_status r = radix_sort_pairs<uint64_t>(Y.keys, Y.keys_alt, Y.vals, Y.vals_alt, Y.hist, P,
-                                                       bits, st, &sk, &sv, Y.cnt);
-            if (r != FIPT_OK) return r;
-            if (c == 0) FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, Y.cnt, T, Y.start, Y.end);
-        }
-        FIPT_LAUNCH(k_emit_median, blocks(T, 256), 256, 0, st, sk, Y.start, Y.end, T, c, Le, count);
+        FIPT_LAUNCH(k_emit_tri_keys, blocks(P, 256), 256, 0, st, Y.idx, Y.cnt, tri, tri_stride, Y.keys, Y.vals);
+        uint32_t* sk;
+        fipt_status r = radix_sort_pairs<uint32_t>(Y.keys, Y.keys_alt, Y.vals, Y.vals_alt, Y.hist, P, bits, st,
+                                                   &sk, &sv, Y.cnt);
+        if (r != FIPT_OK) return r;
+        FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, Y.cnt, T, Y.start, Y.end, Y.segs, Y.cnt + 1);
+        FIPT_LAUNCH(k_emit_chan_keys, blocks(P, 256), 256, 0, st, sv, Y.cnt, rgb, P, Y.keys3);
+        int dev = 0, sms = 0;
+        FIPT_CUDA(cudaGetDevice(&dev));
+        FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FIPT_LAUNCH(k_emit_select, (unsigned)(8 * sms), SEL_THREADS, 0, st, Y.keys3, P, Y.start, Y.end, Y.segs,
+                    Y.cnt + 1, Le, count);
     }
     FIPT_LAUNCHED("emitter radiance");
     return FIPT_OK;
