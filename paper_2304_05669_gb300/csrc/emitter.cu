@@ -9,12 +9,11 @@
 // 3. With zero reflectance at emitters, the L1 problem of Eq. 12 is solved
 //    per channel by the median of the radiance of the input pixels whose
 //    first hit is the triangle.  The pixels that hit an emitter are first
-//    gathered (in any order: the sort key alone decides the result, and
-//    equal keys carry equal values), then sorted per channel by the 64-bit
-//    key (triangle << 32 | order-preserving bits of the value), with the
-//    gathered count read on the device.  Each triangle's segment in the
-//    sorted keys gives its count, and the lower median (index (c - 1) / 2)
-//    its value.
+//    gathered (in any order), sorted by triangle with the gathered count
+//    read on the device, and each triangle's segment gives its count c;
+//    the lower median (rank (c - 1) / 2 in each channel's order) is found
+//    by radix selection on order-preserving bits of the values, which picks
+//    the element a sort would put at that rank whatever the pixel order.
 #include "fipt_internal.cuh"
 
 namespace {
