@@ -50,6 +50,75 @@ def test_pool_matches_oracle_exactly(fipt, R):
     assert o[..., 3].sum() == len(x)
 
 
+@pytest.mark.parametrize("R", [64, 128])
+def test_pool_cell_faces_match_oracle(fipt, R):
+    """Pixels exactly on a cell face and 1-2 float32 ulps either side of it,
+    on every axis: the cell is decided in correctly rounded FP64 on both
+    sides, and those pixels are the ones a float32 estimate cannot place."""
+    m = cornell_box()
+    V = np.asarray(m.V, np.float32)
+    lo, hi = V.min(0).astype(np.float64), V.max(0).astype(np.float64)
+    rng = np.random.default_rng(R)
+    n = 6000
+    k = rng.integers(0, R + 1, (n, 3))
+    x = (lo + k * (hi - lo) / R).astype(np.float32)
+    for step in (-2, -1, 1, 2):
+        sel = rng.random((n, 3)) < 0.2
+        for _ in range(abs(step)):
+            x = np.where(sel, np.nextafter(x, np.float32(np.inf if step > 0 else -np.inf)), x)
+    x = np.concatenate([x, rng.uniform(lo, hi, (4000, 3)).astype(np.float32)])
+    L = rng.uniform(0.0, 2.0, (len(x), 3)).astype(np.float32)
+    g = fipt.Scene.from_mesh(m).voxel_cache(cu(x), cu(L), R).cpu().numpy()
+    o = O.OracleScene.from_mesh(m).voxel_pool(x, L, R)
+    assert np.array_equal(g[..., 3], o[..., 3])
+    assert np.array_equal(g, o.astype(np.float32))
+
+
+def test_pool_mixed_magnitudes_match_oracle(fipt):
+    """Voxels whose pixels mix zeros, both signs, subnormals, infinities,
+    NaNs and magnitudes far apart (sums that leave the range in which the
+    in-order FP64 sum is exact), interleaved with ordinary pixels: the mean
+    is the oracle's in-order FP64 sum over the count, rounded to float32."""
+    m = cornell_box()
+    V = np.asarray(m.V, np.float32)
+    lo, hi = V.min(0), V.max(0)
+    R = 16
+    f = np.float32
+    special = [
+        [1.0, 1.5, 2.0 ** -29],                    # magnitudes reach 2^53 units
+        [1e-12, 1e3, 7.0],                         # exponents 50 apart
+        [0.0, -0.0, 0.0],                          # zeros only: +0
+        [3.0, -3.0, 1e-3, -1e-3],                  # cancellations
+        [1e-40, 1.0, 2e-45],                       # subnormals
+        [np.inf, 1.0], [np.inf, -np.inf], [np.nan, 2.0],
+        [2.0 ** -100, 2.0 ** -110, 3 * 2.0 ** -120],  # tiny normals, exact
+        [-(2.0 ** 20), 2.0 ** -9, 2.0 ** 20],      # exact: 2^20 - 2^20 + 2^-9
+        list(np.random.default_rng(1).uniform(0.5, 2.0, 5000)),   # one long run
+    ]
+    rng = np.random.default_rng(2)
+    xs, Ls = [], []
+    for i, vals in enumerate(special):
+        cell = np.array([i % R, (i // R) % R, 3], np.float64) + 0.5
+        p = (lo + cell * (hi - lo) / R).astype(np.float32)
+        vv = np.array(vals, np.float32)
+        Lv = np.stack([vv, vv[::-1], rng.permutation(vv)], 1)   # each channel its own order
+        xs.append(np.repeat(p[None], len(vv), 0))
+        Ls.append(Lv)
+    xs.append(rng.uniform(lo, hi, (3000, 3)).astype(f))
+    Ls.append(rng.uniform(0.0, 2.0, (3000, 3)).astype(f))
+    x = np.concatenate(xs)
+    L = np.concatenate(Ls).astype(f)
+    perm = rng.permutation(len(x))                   # interleave the voxels' pixels
+    x, L = x[perm], L[perm]
+    g = fipt.Scene.from_mesh(m).voxel_cache(cu(x), cu(L), R).cpu().numpy()
+    o = O.OracleScene.from_mesh(m).voxel_pool(x, L, R)
+    assert np.array_equal(g[..., 3], o[..., 3])
+    with np.errstate(invalid="ignore", over="ignore"):
+        o32 = o.astype(np.float32)
+    assert np.array_equal(g.view(np.uint32)[~np.isnan(g)], o32.view(np.uint32)[~np.isnan(o32)])
+    assert np.array_equal(np.isnan(g), np.isnan(o32))
+
+
 def test_pool_from_query_records_and_empty(fipt):
     m = cornell_box()
     q, L = pixels(m, 5000, 2)
