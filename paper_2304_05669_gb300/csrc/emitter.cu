@@ -15,6 +15,7 @@
 //    by radix selection on order-preserving bits of the values, which picks
 //    the element a sort would put at that rank whatever the pixel order.
 #include "fipt_internal.cuh"
+#include "exact_sum.cuh"
 
 namespace {
 
@@ -58,35 +59,68 @@ k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv, 
     }
 }
 
-// One thread per triangle sums its row of alpha in order.  When the block's
-// CLS_ROWS rows fit in shared memory, all CLS_THREADS threads first copy
-// them there with coalesced loads.
-constexpr int CLS_THREADS = 256;
-constexpr int CLS_ROWS = 64;
-constexpr int CLS_MAX_N = 192;            // 64 rows x 192 floats = 48 KB
+// A thread per triangle; its mean is the FP64 sum of its row of alpha in
+// sample order over n.  Rows of up to CLS_STAGE_N samples are first copied
+// to shared memory (a block's rows are contiguous: one coalesced float4
+// stream).  A row within the exact range (exact_sum.cuh) is summed in
+// integers in two passes (exponent range, then the sum), each thread
+// starting at a column skewed by its index so that a warp's lanes read
+// distinct banks (integer addition is associative, so the order does not
+// change the sum); other rows (a wider exponent range, subnormals,
+// infinities, NaNs) are summed in sample order in FP64.  The FP64 work
+// left is one division per triangle, shared by the lanes of a warp.
+constexpr int CLS_THREADS = 96;
+constexpr int CLS_STAGE_N = 127;          // 96 rows x 127 floats = 48,768 B
 
+template <bool STAGED>
 __global__ void __launch_bounds__(CLS_THREADS)
 k_emit_classify(const float* __restrict__ alpha, int64_t T, int n, double thr,
                 double* __restrict__ mean, uint8_t* __restrict__ flag) {
-    extern __shared__ float rows[];
-    const int64_t t0 = (int64_t)blockIdx.x * CLS_ROWS;
-    const bool staged = n <= CLS_MAX_N;
-    if (staged) {
-        const int64_t rows_here = (T - t0) < CLS_ROWS ? (T - t0) : CLS_ROWS;
-        const int64_t cnt = rows_here * n;
-        const float* src = alpha + t0 * n;
-        for (int64_t k = threadIdx.x; k < cnt; k += CLS_THREADS) rows[k] = __ldg(src + k);
-        __syncthreads();
-    }
+    __shared__ float4 tile4[STAGED ? (CLS_THREADS * CLS_STAGE_N + 3) / 4 : 1];
+    float* tile = reinterpret_cast<float*>(tile4);
+    const int64_t t0 = (int64_t)blockIdx.x * CLS_THREADS;
     const int64_t t = t0 + threadIdx.x;
-    if (threadIdx.x >= CLS_ROWS || t >= T) return;
-    double s = 0.0;
-    if (staged) {
-        const float* a = rows + threadIdx.x * n;
-        for (int j = 0; j < n; ++j) s += (double)a[j];
+    const float* row;
+    int c0 = 0;
+    if (STAGED) {
+        const int rows = (int)(T - t0 < CLS_THREADS ? T - t0 : CLS_THREADS);
+        const float* src = alpha + t0 * (int64_t)n;
+        const int cnt = rows * n;
+        int done = 0;
+        if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const int c4 = cnt >> 2;
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll 8
+            for (int k = threadIdx.x; k < c4; k += CLS_THREADS) tile4[k] = __ldg(s4 + k);
+            done = 4 * c4;
+        }
+#pragma unroll 4
+        for (int k = done + threadIdx.x; k < cnt; k += CLS_THREADS) tile[k] = __ldg(src + k);
+        __syncthreads();
+        row = tile + threadIdx.x * n;
+        c0 = threadIdx.x % n;
     } else {
-        const float* a = alpha + t * n;
-        for (int j = 0; j < n; ++j) s += (double)__ldg(a + j);
+        row = alpha + t * (int64_t)n;
+    }
+    if (t >= T) return;
+    fipt_exact::Range rg;
+    int c = c0;
+    for (int j = 0; j < n; ++j) {
+        rg.note(row[c]);
+        c = c + 1 == n ? 0 : c + 1;
+    }
+    double s = 0.0;
+    if (!rg.special() && rg.exact_for(n)) {
+        const int emin = rg.emin();
+        long long acc = 0;
+        c = c0;
+        for (int j = 0; j < n; ++j) {
+            acc += fipt_exact::term(row[c], emin);
+            c = c + 1 == n ? 0 : c + 1;
+        }
+        s = fipt_exact::scaled_double(acc, emin);
+    } else {
+        for (int j = 0; j < n; ++j) s += (double)row[j];
     }
     const double m = s / (double)n;
     if (mean) mean[t] = m;
@@ -309,9 +343,14 @@ extern "C" fipt_status fipt_emitter_classify(const float* alpha, int64_t T, int3
     if (T == 0) return FIPT_OK;
     FIPT_REQUIRE(alpha && is_emitter && fipt_aligned(alpha, 4), "alpha / is_emitter NULL or misaligned");
     FIPT_REQUIRE(!mean_alpha || fipt_aligned(mean_alpha, 8), "mean_alpha misaligned");
-    const size_t smem = n_per_tri <= CLS_MAX_N ? sizeof(float) * CLS_ROWS * (size_t)n_per_tri : 0;
-    FIPT_LAUNCH(k_emit_classify, blocks(T, CLS_ROWS), CLS_THREADS, smem, static_cast<cudaStream_t>(stream),
-                alpha, T, n_per_tri, (double)threshold, mean_alpha, is_emitter);
+    const unsigned nb = blocks(T, CLS_THREADS);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_per_tri <= CLS_STAGE_N)
+        FIPT_LAUNCH(k_emit_classify<true>, nb, CLS_THREADS, 0, st, alpha, T, n_per_tri, (double)threshold,
+                    mean_alpha, is_emitter);
+    else
+        FIPT_LAUNCH(k_emit_classify<false>, nb, CLS_THREADS, 0, st, alpha, T, n_per_tri, (double)threshold,
+                    mean_alpha, is_emitter);
     FIPT_LAUNCHED("emitter classify");
     return FIPT_OK;
 }

@@ -9,6 +9,7 @@
 // means: cells in float32 away from cell faces, sums in integers while
 // they are provably exact (k_vox_keys, k_vox_means), FP64 otherwise.
 #include "fipt_internal.cuh"
+#include "exact_sum.cuh"
 
 namespace {
 
@@ -155,33 +156,13 @@ k_vox_compact(const uint32_t* __restrict__ keys, int64_t P, const uint32_t* __re
 constexpr int MEAN_THREADS = FIPT_VOX_THREADS;
 constexpr int VU = FIPT_VOX_UNROLL;
 
-// acc * 2^(emin - 150) as a double (|acc| < 2^53: exact), built from its
-// bits; an exact cancellation gives +0 as FP64 addition does.
-__device__ __forceinline__ double scaled_double(long long acc, int emin) {
-    if (acc == 0) return 0.0;
-    const unsigned long long a = acc < 0 ? (unsigned long long)(-acc) : (unsigned long long)acc;
-    const int t = 63 - __clzll((long long)a);
-    const unsigned long long bits = (acc < 0 ? (1ull << 63) : 0ull) |
-                                    ((unsigned long long)(t + 1023 + emin - 150) << 52) |
-                                    ((a << (52 - t)) & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
-}
-
 // A thread per voxel run: the run's pixels are taken VU at a time, the next
 // group's pixel indices loading while this group's radiance is fetched, and
-// each channel's FP64 sum in pixel order is carried exactly in integers.
-//
-// A nonzero normal float is M * 2^(e - 150) with M < 2^24 (IEEE 754
-// binary32), so every value and every partial sum of a run is an integer
-// multiple of u = 2^(emin - 150), emin the smallest exponent in the run,
-// and each |value| < 2^(emax - emin + 24) u.  With n pixels and
-// emax - emin <= 29 - bitlen(n), every partial sum is a multiple of u below
-// 2^53 u, exactly a double: each FP64 addition of the in-order sum is then
-// exact, and the sum equals acc * u with acc an int64 (zeros add nothing
-// to an FP64 sum that starts at +0).  emin and emax are tracked over the
-// three channels together and acc is rescaled when a group brings a
-// smaller exponent.  A run with a wider exponent range, a subnormal, an
-// infinity or a NaN is summed again with FP64 additions in pixel order.
+// each channel's FP64 sum in pixel order is carried exactly in integers
+// (exact_sum.cuh) while the run's exponent range allows it.  emin and emax
+// are tracked over the three channels together, and the sums are rescaled
+// when a group brings a smaller exponent.  A run that leaves the exact range
+// is summed again with FP64 additions in pixel order.
 __global__ void __launch_bounds__(MEAN_THREADS)
 k_vox_means(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pix, const uint32_t* __restrict__ heads,
             const uint32_t* __restrict__ nhead, const float* __restrict__ L, float4* __restrict__ grid) {
@@ -191,9 +172,9 @@ k_vox_means(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pix,
         const int64_t j0 = heads[h], j1 = heads[h + 1];
         const uint32_t k = keys[j0];
         long long acc[3] = {0, 0, 0};
-        int emin = 255, emax = 0;
-        const int spread = 29 - (64 - __clzll((long long)(j1 - j0)));
-        bool ok = spread >= 0;
+        int emin = fipt_exact::EMPTY_EMIN;
+        fipt_exact::Range run;
+        bool ok = fipt_exact::spread_limit(j1 - j0) >= 0;
         uint32_t qn[VU];
 #pragma unroll
         for (int u = 0; u < VU; ++u) qn[u] = j0 + u < j1 ? pix[j0 + u] : 0u;
@@ -209,48 +190,30 @@ k_vox_means(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pix,
             }
 #pragma unroll
             for (int u = 0; u < VU; ++u) qn[u] = e + VU + u < j1 ? pix[e + VU + u] : 0u;
-            int bmin = 255, bmax = 0;
-            bool special = false;
 #pragma unroll
-            for (int u = 0; u < VU; ++u) {
+            for (int u = 0; u < VU; ++u)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const uint32_t b = __float_as_uint(v[u][c]);
-                    const int ex = (int)((b >> 23) & 0xFFu);
-                    const bool nz = (b << 1) != 0u;
-                    special |= nz && (ex == 0 || ex == 0xFF);
-                    bmin = min(bmin, nz ? ex : 255);
-                    bmax = max(bmax, nz ? ex : 0);
-                }
-            }
-            if (bmin < emin) {          // from the sentinel 255 the sums are still 0
-                const int sh = min(emin - bmin, 63);
+                for (int c = 0; c < 3; ++c) run.note(v[u][c]);
+            const int em = run.emin();
+            if (em < emin) {            // from EMPTY_EMIN the sums are still 0
+                const int sh = min(emin - em, 63);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[c] = (long long)((unsigned long long)acc[c] << sh);
-                emin = bmin;
+                emin = em;
             }
-            emax = max(emax, bmax);
-            ok = !special && emax - emin <= spread;
+            ok = !run.special() && run.exact_for(j1 - j0);
             if (ok) {
 #pragma unroll
-                for (int u = 0; u < VU; ++u) {
+                for (int u = 0; u < VU; ++u)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const uint32_t b = __float_as_uint(v[u][c]);
-                        const bool nz = (b << 1) != 0u;
-                        const unsigned long long m = nz ? (unsigned long long)((b & 0x7FFFFFu) | 0x800000u) : 0ull;
-                        const int d = nz ? (int)((b >> 23) & 0xFFu) - emin : 0;
-                        const long long t = (long long)(m << d);
-                        acc[c] += (b >> 31) ? -t : t;
-                    }
-                }
+                    for (int c = 0; c < 3; ++c) acc[c] += fipt_exact::term(v[u][c], emin);
             }
         }
         double s0, s1, s2;
         if (ok) {
-            s0 = scaled_double(acc[0], emin);
-            s1 = scaled_double(acc[1], emin);
-            s2 = scaled_double(acc[2], emin);
+            s0 = fipt_exact::scaled_double(acc[0], emin);
+            s1 = fipt_exact::scaled_double(acc[1], emin);
+            s2 = fipt_exact::scaled_double(acc[2], emin);
         } else {
             s0 = s1 = s2 = 0.0;
             for (int64_t e = j0; e < j1; ++e) {

@@ -49,6 +49,50 @@ def test_classify_bit_exact(fipt):
     assert 0.05 < o_flag.mean() < 0.95
 
 
+@pytest.mark.parametrize("n", [1, 3, 31, 32, 33, 100, 1000])
+def test_classify_row_kinds_bit_exact(fipt, n):
+    """Rows of every kind the mean can meet, at row lengths around the warp
+    width: ordinary values, zeros only, two-valued masks, both signs with
+    cancellations, values 2^-60 apart, subnormals, infinities and NaNs; the
+    mean is the in-order FP64 sum over n on both sides, bit for bit."""
+    rng = np.random.default_rng(n)
+    kinds = 9
+    T = kinds * 40
+    a = np.empty((T, n), np.float32)
+    for t in range(T):
+        k = t % kinds
+        if k == 0:
+            r = rng.uniform(0, 1, n)
+        elif k == 1:
+            r = np.zeros(n)
+        elif k == 2:
+            r = (rng.uniform(size=n) < 0.3) * 0.05
+        elif k == 3:
+            r = rng.uniform(-1, 1, n) * 2.0 ** rng.integers(-8, 8, n)
+            r[::2] = -np.roll(r, 1)[::2]
+        elif k == 4:
+            r = rng.uniform(0.5, 1, n) * 2.0 ** rng.integers(-60, 1, n)
+        elif k == 5:
+            r = rng.uniform(0, 1, n)
+            r[rng.integers(0, n)] = 1e-41
+        elif k == 6:
+            r = rng.uniform(0, 1, n)
+            r[rng.integers(0, n)] = np.inf
+        elif k == 7:
+            r = rng.uniform(0, 1, n)
+            r[rng.integers(0, n)] = np.nan
+        else:
+            r = rng.uniform(0, 0.02, n) * 2.0 ** rng.integers(-20, 0, n)
+        a[t] = r
+    g_flag, g_mean = fipt.emitter_classify(cu(a.reshape(-1)), n, 0.01)
+    o_flag, o_mean = O.emitter_classify(a.reshape(-1), n, 0.01)
+    g_mean = g_mean.cpu().numpy()
+    assert np.array_equal(np.isnan(g_mean), np.isnan(o_mean))
+    ok = ~np.isnan(o_mean)
+    assert np.array_equal(g_mean[ok].view(np.uint64), o_mean[ok].view(np.uint64))
+    assert np.array_equal(g_flag.cpu().numpy(), o_flag)
+
+
 def test_worked_example(fipt):
     rows = read_golden("emitter_extraction_worked_example.txt")
     alpha = np.array([[float(v) for v in r[2:]] for r in rows if r[0] == "alpha"], np.float32)
