@@ -49,12 +49,15 @@ def test_classify_bit_exact(fipt):
     assert 0.05 < o_flag.mean() < 0.95
 
 
-@pytest.mark.parametrize("n", [1, 3, 31, 32, 33, 100, 1000])
-def test_classify_row_kinds_bit_exact(fipt, n):
+@pytest.mark.parametrize("n,offset", [(1, 0), (3, 0), (31, 0), (32, 0), (33, 0), (100, 0), (100, 1), (127, 0),
+                                      (127, 3), (128, 0), (1000, 0)])
+def test_classify_row_kinds_bit_exact(fipt, n, offset):
     """Rows of every kind the mean can meet, at row lengths around the warp
     width: ordinary values, zeros only, two-valued masks, both signs with
     cancellations, values 2^-60 apart, subnormals, infinities and NaNs; the
-    mean is the in-order FP64 sum over n on both sides, bit for bit."""
+    mean is the in-order FP64 sum over n on both sides, bit for bit.  Rows
+    of up to 127 samples are staged through shared memory and longer ones
+    are not; a nonzero offset starts alpha off a 16-byte boundary."""
     rng = np.random.default_rng(n)
     kinds = 9
     T = kinds * 40
@@ -84,7 +87,8 @@ def test_classify_row_kinds_bit_exact(fipt, n):
         else:
             r = rng.uniform(0, 0.02, n) * 2.0 ** rng.integers(-20, 0, n)
         a[t] = r
-    g_flag, g_mean = fipt.emitter_classify(cu(a.reshape(-1)), n, 0.01)
+    buf = cu(np.concatenate([np.zeros(offset, np.float32), a.reshape(-1)]))
+    g_flag, g_mean = fipt.emitter_classify(buf[offset:], n, 0.01)
     o_flag, o_mean = O.emitter_classify(a.reshape(-1), n, 0.01)
     g_mean = g_mean.cpu().numpy()
     assert np.array_equal(np.isnan(g_mean), np.isnan(o_mean))

@@ -129,6 +129,10 @@ def test_pool_from_query_records_and_empty(fipt):
     assert np.array_equal(a, b)
     e = sc.voxel_cache(torch.zeros((0, 3), device="cuda"), torch.zeros((0, 3), device="cuda"), 4)
     assert e.shape == (4, 4, 4, 4) and not e.any()
+    S = O.OracleScene.from_mesh(m)
+    for P in (1, 33, 1025):                       # one pixel; ragged tiles of the run-head scan
+        g = sc.voxel_cache(cu(q["x"][:P]), cu(L[:P]), 16).cpu().numpy()
+        assert np.array_equal(g, S.voxel_pool(q["x"][:P], L[:P], 16).astype(np.float32))
 
 
 def bake_both(fipt, m, grid_R, spp_d, spp_s, nq, seed):
