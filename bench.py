@@ -717,13 +717,10 @@ def run_next_rows(args, F, dev, mesh, sc, q, Lgt, qa, with_cpu, peak):
     flag, _ = F.emitter_classify(alpha, n_per, 0.01)
     t_rad = _device_time(lambda: F.emitter_radiance(qa, rgb, flag))
     M = int(F.emitter_radiance(qa, rgb, flag)[1].sum().item())     # pixels on emitter triangles
-    tri_bits = max(int(np.ceil(np.log2(T))), 1)
-    # gather: triangle id + flag per pixel; per gathered pixel: index + triangle
-    # in, key/value out, 16 B per sort pass, bounds, rgb gathered into three
-    # contiguous key rows, four 8-bit selection passes over each row; per
-    # triangle its bounds, L_e and count
-    rad_bytes = (Pq * (4 + 1) + M * (4 + 4 + 8) + M * 16 * _sort_passes(tri_bits) + M * 4
-                 + M * (4 + 12 + 12) + 3 * 4 * M * 4 + T * (8 + 12 + 4))
+    # triangle id + flag per pixel in the count and scatter passes; per
+    # emitter pixel its rgb, the three key rows and four 8-bit selection
+    # passes over them; per triangle its count, segment, L_e and pixel count
+    rad_bytes = Pq * 2 * (4 + 1) + M * (12 + 12 + 3 * 4 * 4) + T * (4 + 8 + 12 + 4)
     b_pts = 12.0 * T * n_per + 52.0 * T
     b_cls = 4.0 * T * n_per + 9.0 * T
     em = {"triangles": T, "samples_per_triangle": n_per, "pixels": Pq,

@@ -8,12 +8,14 @@
 //    FP64, so the decision is deterministic.
 // 3. With zero reflectance at emitters, the L1 problem of Eq. 12 is solved
 //    per channel by the median of the radiance of the input pixels whose
-//    first hit is the triangle.  The pixels that hit an emitter are first
-//    gathered (in any order), sorted by triangle with the gathered count
-//    read on the device, and each triangle's segment gives its count c;
-//    the lower median (rank (c - 1) / 2 in each channel's order) is found
-//    by radix selection on order-preserving bits of the values, which picks
-//    the element a sort would put at that rank whatever the pixel order.
+//    first hit is the triangle.  The pixels on emitter triangles are
+//    grouped by triangle with a counting sort: per-triangle counts, a scan
+//    over the triangles for each one's segment, and a scatter of each
+//    pixel's three channel keys into its segment (in any order within it);
+//    the lower median (rank (c - 1) / 2 of a segment's c keys in each
+//    channel's order) is found by radix selection on order-preserving bits
+//    of the values, which picks the element a sort would put at that rank
+//    whatever the order within the segment.
 #include "fipt_internal.cuh"
 #include "exact_sum.cuh"
 
@@ -137,74 +139,170 @@ __device__ __forceinline__ float funkey(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-// Gathers the pixels whose triangle is an emitter (one atomic per warp).
-__global__ void k_emit_gather(const int32_t* __restrict__ tri, int64_t stride, int64_t P,
-                              const uint8_t* __restrict__ flag, int64_t T, uint32_t* __restrict__ idx,
-                              uint32_t* __restrict__ cnt) {
+// Pixel p's triangle when it is an emitter, else -1.
+__device__ __forceinline__ int32_t emitter_of(const int32_t* __restrict__ tri, int64_t stride, int64_t p,
+                                              const uint8_t* __restrict__ flag, int64_t T) {
+    const int32_t t = tri[p * stride];
+    return (t >= 0 && t < T && flag[t]) ? t : -1;
+}
+
+// Pixels per emitter triangle: the lanes of a warp on the same triangle
+// (grouped by __match_any_sync) add with one atomic.
+__global__ void k_emit_count(const int32_t* __restrict__ tri, int64_t stride, int64_t P,
+                             const uint8_t* __restrict__ flag, int64_t T, uint32_t* __restrict__ tcount) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    bool e = false;
-    if (p < P) {
-        const int32_t t = tri[p * stride];
-        e = t >= 0 && t < T && flag[t];
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, e);
-    if (m == 0) return;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(cnt, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (e) idx[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)p;
+    const int32_t t = p < P ? emitter_of(tri, stride, p, flag, T) : -1;
+    const unsigned act = __ballot_sync(0xffffffffu, t >= 0);
+    if (t < 0) return;
+    const unsigned same = __match_any_sync(act, (unsigned)t);
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&tcount[t], (uint32_t)__popc(same));
 }
 
-// Sort keys of the gathered pixels: their triangle (stable sort keeps
-// gather order within a triangle, which the median does not depend on).
-__global__ void k_emit_tri_keys(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ cnt,
-                                const int32_t* __restrict__ tri, int64_t stride, uint32_t* __restrict__ keys,
-                                uint32_t* __restrict__ vals) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= (int64_t)*cnt) return;
-    const int64_t p = idx[j];
-    keys[j] = (uint32_t)tri[p * stride];
-    vals[j] = (uint32_t)p;
-}
+// Segments of the triangles (tiles of SEG_TILE triangles): k_emit_seg_tiles
+// sums each tile's pixel counts and counts its triangles with pixels,
+// k_emit_seg_scan turns both into offsets (one block; cnt[0] = pixels on
+// emitters, cnt[1] = triangles with pixels), k_emit_seg_apply gives each
+// triangle with pixels its segment [start, end], a cursor at start, and its
+// place in the list of such triangles (in triangle order).
+constexpr int SEG_TILE = 1024;
 
-// Segment bounds of every triangle with pixels, and the list of those
-// triangles (one atomic per warp; the list's order does not matter).
-__global__ void k_emit_bounds(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ cnt, int64_t T,
-                              int32_t* __restrict__ start, int32_t* __restrict__ end, uint32_t* __restrict__ segs,
-                              uint32_t* __restrict__ nseg) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t P = *cnt;
-    const int lane = threadIdx.x & 31;
-    bool first = false;
-    uint32_t s = 0;
-    if (j < P) {
-        s = keys[j];
-        if (s < (uint64_t)T) {
-            first = j == 0 || keys[j - 1] != s;
-            if (first) start[s] = (int32_t)j;
-            if (j == P - 1 || keys[j + 1] != s) end[s] = (int32_t)j;
-        }
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, first);
-    if (m == 0) return;
-    const int leader = __ffs(m) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(nseg, (uint32_t)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (first) segs[base + __popc(m & ((1u << lane) - 1u))] = s;
-}
-
-// The three channels' order-preserving keys of the sorted pixels, laid out
-// [channel][sorted position] so that a triangle's keys are contiguous.
-__global__ void k_emit_chan_keys(const uint32_t* __restrict__ pix, const uint32_t* __restrict__ cnt,
-                                 const float* __restrict__ rgb, int64_t P, uint32_t* __restrict__ keys3) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= (int64_t)*cnt) return;
-    const int64_t p = pix[j];
+// Exclusive prefix of v over a block of SEG_TILE threads; total receives
+// the block's sum.  ws: 33 words of shared memory.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t* ws, uint32_t& total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) keys3[c * P + j] = fkey(rgb[3 * p + c]);
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t s0 = ws[lane];
+        uint32_t s = s0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s - s0;
+        if (lane == 31) ws[32] = s;
+    }
+    __syncthreads();
+    const uint32_t r = ws[w] + x - v;
+    total = ws[32];
+    __syncthreads();                                       // ws is reused by the next call
+    return r;
+}
+
+__global__ void __launch_bounds__(SEG_TILE)
+k_emit_seg_tiles(const uint32_t* __restrict__ tcount, int64_t T, uint32_t* __restrict__ tsum,
+                 uint32_t* __restrict__ tnz) {
+    __shared__ uint32_t ws[33];
+    const int64_t t = blockIdx.x * (int64_t)SEG_TILE + threadIdx.x;
+    const uint32_t c = t < T ? tcount[t] : 0u;
+    uint32_t s, z;
+    block_exclusive(c, ws, s);
+    block_exclusive(c > 0u ? 1u : 0u, ws, z);
+    if (threadIdx.x == 0) {
+        tsum[blockIdx.x] = s;
+        tnz[blockIdx.x] = z;
+    }
+}
+
+__global__ void __launch_bounds__(SEG_TILE)
+k_emit_seg_scan(uint32_t* __restrict__ tsum, uint32_t* __restrict__ tnz, int64_t nt, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t ws[33];
+    uint32_t carry_s = 0, carry_z = 0;
+    for (int64_t base = 0; base < nt; base += SEG_TILE) {
+        const int64_t i = base + threadIdx.x;
+        uint32_t ts, tz;
+        const uint32_t es = block_exclusive(i < nt ? tsum[i] : 0u, ws, ts);
+        const uint32_t ez = block_exclusive(i < nt ? tnz[i] : 0u, ws, tz);
+        if (i < nt) {
+            tsum[i] = carry_s + es;
+            tnz[i] = carry_z + ez;
+        }
+        carry_s += ts;
+        carry_z += tz;
+    }
+    if (threadIdx.x == 0) {
+        cnt[0] = carry_s;
+        cnt[1] = carry_z;
+    }
+}
+
+__global__ void __launch_bounds__(SEG_TILE)
+k_emit_seg_apply(const uint32_t* __restrict__ tcount, int64_t T, const uint32_t* __restrict__ tsum,
+                 const uint32_t* __restrict__ tnz, int32_t* __restrict__ start, int32_t* __restrict__ end,
+                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ segs) {
+    __shared__ uint32_t ws[33];
+    const int64_t t = blockIdx.x * (int64_t)SEG_TILE + threadIdx.x;
+    const uint32_t c = t < T ? tcount[t] : 0u;
+    uint32_t total;
+    const uint32_t ps = tsum[blockIdx.x] + block_exclusive(c, ws, total);
+    const uint32_t pz = tnz[blockIdx.x] + block_exclusive(c > 0u ? 1u : 0u, ws, total);
+    if (c > 0u) {
+        start[t] = (int32_t)ps;
+        end[t] = (int32_t)(ps + c - 1u);
+        cursor[t] = ps;
+        segs[pz] = (uint32_t)t;
+    }
+}
+
+// Each emitter pixel's three channel keys go to its triangle's segment,
+// laid out [channel][position] (P positions per channel); the lanes of a
+// warp on the same triangle take consecutive positions with one atomic.
+__global__ void k_emit_scatter(const int32_t* __restrict__ tri, int64_t stride, int64_t P,
+                               const uint8_t* __restrict__ flag, int64_t T, const float* __restrict__ rgb,
+                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ keys3) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t t = p < P ? emitter_of(tri, stride, p, flag, T) : -1;
+    const unsigned act = __ballot_sync(0xffffffffu, t >= 0);
+    if (t < 0) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned same = __match_any_sync(act, (unsigned)t);
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[t], (uint32_t)__popc(same));
+    base = __shfl_sync(act, base, leader);
+    const int64_t pos = base + __popc(same & ((1u << lane) - 1u));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) keys3[c * P + pos] = fkey(rgb[3 * p + c]);
+}
+
+// Lower median of each channel of the triangles with at most 32 pixels, a
+// warp per triangle: lane j holds the triangle's j-th key, counts the keys
+// ordered before it by (key, position) with 32 shuffles, and the lane whose
+// count is (n - 1) / 2 holds the key a sort would put at that rank.
+// Triangles with more pixels are left to k_emit_select.
+constexpr int SEL_SMALL = 32;
+
+__global__ void k_emit_select_small(const uint32_t* __restrict__ keys3, int64_t P, const int32_t* __restrict__ start,
+                                    const int32_t* __restrict__ end, const uint32_t* __restrict__ segs,
+                                    const uint32_t* __restrict__ nseg, float* __restrict__ Le,
+                                    int32_t* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t ns = *nseg;
+    const uint32_t nwarps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t si = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); si < ns; si += nwarps) {
+        const int64_t t = segs[si];
+        const int32_t a = start[t];
+        const int32_t n = end[t] - a + 1;
+        if (n > SEL_SMALL) continue;                      // whole warp
+        const int k = (n - 1) / 2;
+        for (int c = 0; c < 3; ++c) {
+            const uint32_t mine = lane < n ? keys3[c * P + a + lane] : 0xFFFFFFFFu;
+            int before = 0;
+            for (int j = 0; j < n; ++j) {
+                const uint32_t v = __shfl_sync(0xffffffffu, mine, j);
+                before += (v < mine || (v == mine && j < lane)) ? 1 : 0;
+            }
+            if (lane < n && before == k) Le[3 * t + c] = funkey(mine);
+        }
+        if (count && lane == 0) count[t] = n;
+    }
 }
 
 constexpr int SEL_THREADS = 256;            // a block per triangle
@@ -212,68 +310,78 @@ constexpr int SEL_THREADS = 256;            // a block per triangle
 // Lower median of each channel of triangle t's pixels (positions a..e of
 // keys3) by radix selection on the order-preserving keys: four 8-bit
 // digits from the top, each pass counting the candidates' digit in a
-// shared histogram and keeping the bucket that holds rank (n - 1) / 2.  The
-// selected key is the one a sort would put at that rank, so the result
-// equals the sorted lower median.  Triangles without pixels get 0 and
-// count 0 (set beforehand).  Persistent: the blocks take the listed
-// triangles in turn.
+// shared histogram and keeping the bucket that holds rank (n - 1) / 2; the
+// three channels are selected in the same passes (three histograms, a warp
+// each to find the bucket).  The selected key is the one a sort would put
+// at that rank, so the result equals the sorted lower median.  Triangles
+// without pixels get 0 and count 0 (set beforehand).  Persistent: the
+// blocks take the listed triangles with more than SEL_SMALL pixels in turn.
 __global__ void __launch_bounds__(SEL_THREADS)
 k_emit_select(const uint32_t* __restrict__ keys3, int64_t P, const int32_t* __restrict__ start,
               const int32_t* __restrict__ end, const uint32_t* __restrict__ segs, const uint32_t* __restrict__ nseg,
               float* __restrict__ Le, int32_t* __restrict__ count) {
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t pick[2];
+    __shared__ uint32_t hist[3][256];
+    __shared__ uint32_t pick[3][2];
     const int tid = threadIdx.x;
     const uint32_t ns = *nseg;
     for (uint32_t si = blockIdx.x; si < ns; si += gridDim.x) {
         const int64_t t = segs[si];
         const int32_t a = start[t];                         // the same for the whole block
         const int32_t n = end[t] - a + 1;
-        for (int c = 0; c < 3; ++c) {
-            const uint32_t* key = keys3 + c * P + a;
-            uint32_t prefix = 0, mask = 0, k = (uint32_t)(n - 1) / 2;
-            for (int shift = 24; shift >= 0; shift -= 8) {
-                hist[tid] = 0;
-                __syncthreads();
-                for (int32_t j = tid; j < n; j += SEL_THREADS) {
-                    const uint32_t v = key[j];
-                    if ((v & mask) == prefix) atomicAdd(&hist[(v >> shift) & 255u], 1u);
+        if (n <= SEL_SMALL) continue;                       // taken by k_emit_select_small
+        const uint32_t* key0 = keys3 + a;
+        uint32_t prefix[3] = {0u, 0u, 0u}, kk[3];
+        kk[0] = kk[1] = kk[2] = (uint32_t)(n - 1) / 2;
+        uint32_t mask = 0;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 3 * 256; i += SEL_THREADS) (&hist[0][0])[i] = 0;
+            __syncthreads();
+            for (int32_t j = tid; j < n; j += SEL_THREADS) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const uint32_t v = key0[c * P + j];
+                    if ((v & mask) == prefix[c]) atomicAdd(&hist[c][(v >> shift) & 255u], 1u);
                 }
-                __syncthreads();
-                if (tid < 32) {                             // warp 0 finds the bucket holding rank k
-                    uint32_t h[8], sum = 0;
-    #pragma unroll
-                    for (int b = 0; b < 8; ++b) {
-                        h[b] = hist[tid * 8 + b];
-                        sum += h[b];
-                    }
-                    uint32_t incl = sum;
-    #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (tid >= o) incl += y;
-                    }
-                    const uint32_t excl = incl - sum;
-                    if (excl <= k && k < incl) {
-                        uint32_t run = excl;
-                        for (int b = 0; b < 8; ++b) {
-                            if (k < run + h[b]) {
-                                pick[0] = (uint32_t)(tid * 8 + b);
-                                pick[1] = run;
-                                break;
-                            }
-                            run += h[b];
-                        }
-                    }
-                }
-                __syncthreads();
-                k -= pick[1];
-                prefix |= pick[0] << shift;
-                mask |= 255u << shift;
-                __syncthreads();                            // pick[] and hist[] are reused
             }
-            if (tid == 0) Le[3 * t + c] = funkey(prefix);
+            __syncthreads();
+            if (tid < 96) {                                 // warp c finds channel c's bucket holding rank kk[c]
+                const int c = tid >> 5, lane = tid & 31;
+                const uint32_t k = c == 0 ? kk[0] : (c == 1 ? kk[1] : kk[2]);
+                uint32_t h[8], sum = 0;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    h[b] = hist[c][lane * 8 + b];
+                    sum += h[b];
+                }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t excl = incl - sum;
+                if (excl <= k && k < incl) {
+                    uint32_t run = excl;
+                    for (int b = 0; b < 8; ++b) {
+                        if (k < run + h[b]) {
+                            pick[c][0] = (uint32_t)(lane * 8 + b);
+                            pick[c][1] = run;
+                            break;
+                        }
+                        run += h[b];
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                kk[c] -= pick[c][1];
+                prefix[c] |= pick[c][0] << shift;
+            }
+            mask |= 255u << shift;
+            __syncthreads();                                // pick[] and hist[] are reused
         }
+        if (tid < 3) Le[3 * t + tid] = funkey(tid == 0 ? prefix[0] : (tid == 1 ? prefix[1] : prefix[2]));
         if (count && tid == 0) count[t] = n;
     }
 }
@@ -287,7 +395,7 @@ __global__ void k_set_emission(const float* __restrict__ Le, const int32_t* __re
 }
 
 struct EmitLayout {
-    uint32_t *keys, *keys_alt, *vals, *vals_alt, *hist, *idx, *keys3, *segs, *cnt;
+    uint32_t *tcount, *cursor, *segs, *tsum, *tnz, *keys3, *cnt;
     int32_t *start, *end;
     size_t bytes;
 };
@@ -296,17 +404,15 @@ EmitLayout carve(void* ws, int64_t P, int64_t T) {
     Carver c{static_cast<char*>(ws), 0};
     EmitLayout L;
     const int64_t p1 = P > 0 ? P : 1, t1 = T > 0 ? T : 1;
-    L.keys = c.take<uint32_t>((size_t)p1);
-    L.keys_alt = c.take<uint32_t>((size_t)p1);
-    L.vals = c.take<uint32_t>((size_t)p1);
-    L.vals_alt = c.take<uint32_t>((size_t)p1);
-    L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(p1) / sizeof(uint32_t));
+    L.tcount = c.take<uint32_t>((size_t)t1);
+    L.cursor = c.take<uint32_t>((size_t)t1);
     L.start = c.take<int32_t>((size_t)t1);
     L.end = c.take<int32_t>((size_t)t1);
-    L.idx = c.take<uint32_t>((size_t)p1);
-    L.keys3 = c.take<uint32_t>((size_t)(3 * p1));
     L.segs = c.take<uint32_t>((size_t)t1);
-    L.cnt = c.take<uint32_t>(2);                       // gathered pixels, listed triangles
+    L.tsum = c.take<uint32_t>((size_t)((t1 + SEG_TILE - 1) / SEG_TILE));
+    L.tnz = c.take<uint32_t>((size_t)((t1 + SEG_TILE - 1) / SEG_TILE));
+    L.keys3 = c.take<uint32_t>((size_t)(3 * p1));
+    L.cnt = c.take<uint32_t>(2);                       // pixels on emitters, triangles with pixels
     L.bytes = c.off + 256;
     return L;
 }
@@ -378,27 +484,23 @@ extern "C" fipt_status fipt_emitter_radiance(const int32_t* tri, int64_t tri_str
         return fipt_set_error(FIPT_ERR_WORKSPACE, "emitter workspace %zu < %zu bytes (256-aligned)",
                               ws_bytes, Y.bytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    FIPT_CUDA(cudaMemsetAsync(Y.start, 0xFF, sizeof(int32_t) * (size_t)T, st));
-    FIPT_CUDA(cudaMemsetAsync(Y.end, 0xFF, sizeof(int32_t) * (size_t)T, st));
-    int bits = 0;
-    while (((int64_t)1 << bits) < T) ++bits;               // triangle ids 0..T-1
-    bits = bits > 0 ? (bits + 7) & ~7 : 8;
-    FIPT_CUDA(cudaMemsetAsync(Y.cnt, 0, 2 * sizeof(uint32_t), st));
     FIPT_CUDA(cudaMemsetAsync(Le, 0, 3 * sizeof(float) * (size_t)T, st));
     if (count) FIPT_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)T, st));
-    uint32_t* sv = Y.vals;
     if (P > 0) {
-        FIPT_LAUNCH(k_emit_gather, blocks(P, 256), 256, 0, st, tri, tri_stride, P, is_emitter, T, Y.idx, Y.cnt);
-        FIPT_LAUNCH(k_emit_tri_keys, blocks(P, 256), 256, 0, st, Y.idx, Y.cnt, tri, tri_stride, Y.keys, Y.vals);
-        uint32_t* sk;
-        fipt_status r = radix_sort_pairs<uint32_t>(Y.keys, Y.keys_alt, Y.vals, Y.vals_alt, Y.hist, P, bits, st,
-                                                   &sk, &sv, Y.cnt);
-        if (r != FIPT_OK) return r;
-        FIPT_LAUNCH(k_emit_bounds, blocks(P, 256), 256, 0, st, sk, Y.cnt, T, Y.start, Y.end, Y.segs, Y.cnt + 1);
-        FIPT_LAUNCH(k_emit_chan_keys, blocks(P, 256), 256, 0, st, sv, Y.cnt, rgb, P, Y.keys3);
+        FIPT_CUDA(cudaMemsetAsync(Y.tcount, 0, sizeof(uint32_t) * (size_t)T, st));
+        FIPT_LAUNCH(k_emit_count, blocks(P, 256), 256, 0, st, tri, tri_stride, P, is_emitter, T, Y.tcount);
+        const int64_t nt = (T + SEG_TILE - 1) / SEG_TILE;
+        FIPT_LAUNCH(k_emit_seg_tiles, (unsigned)nt, SEG_TILE, 0, st, Y.tcount, T, Y.tsum, Y.tnz);
+        FIPT_LAUNCH(k_emit_seg_scan, 1, SEG_TILE, 0, st, Y.tsum, Y.tnz, nt, Y.cnt);
+        FIPT_LAUNCH(k_emit_seg_apply, (unsigned)nt, SEG_TILE, 0, st, Y.tcount, T, Y.tsum, Y.tnz, Y.start, Y.end,
+                    Y.cursor, Y.segs);
+        FIPT_LAUNCH(k_emit_scatter, blocks(P, 256), 256, 0, st, tri, tri_stride, P, is_emitter, T, rgb, Y.cursor,
+                    Y.keys3);
         int dev = 0, sms = 0;
         FIPT_CUDA(cudaGetDevice(&dev));
         FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        FIPT_LAUNCH(k_emit_select_small, (unsigned)(8 * sms), 256, 0, st, Y.keys3, P, Y.start, Y.end, Y.segs,
+                    Y.cnt + 1, Le, count);
         FIPT_LAUNCH(k_emit_select, (unsigned)(8 * sms), SEL_THREADS, 0, st, Y.keys3, P, Y.start, Y.end, Y.segs,
                     Y.cnt + 1, Le, count);
     }
