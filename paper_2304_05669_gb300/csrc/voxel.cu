@@ -25,16 +25,21 @@ namespace {
 // the FP64 value and floor(f) clamps to the same cell; a cell face at 0 or
 // R clamps either side to the same cell, and an f that underflows keeps
 // the sign of x - lo.  Pixels near an inner cell face (and NaNs) take the
-// FP64 arithmetic.
+// FP64 arithmetic, and so does every pixel on an axis whose float32 scale
+// is infinite or subnormal (extents below ~1e-35 or near 1e38), where the
+// bound does not hold.
 __global__ void k_vox_keys(const float* __restrict__ x, int64_t stride, int64_t P,
                            const SceneConst* __restrict__ c, int R, uint32_t* __restrict__ keys,
                            uint32_t* __restrict__ vals) {
     __shared__ double scale[3];
     __shared__ float scale32[3];
+    __shared__ bool fast[3];
     if (threadIdx.x < 3) {
         const double ext = __dsub_rn((double)c->hi[threadIdx.x], (double)c->lo[threadIdx.x]);
         scale[threadIdx.x] = ext > 0.0 ? __ddiv_rn((double)R, ext) : 0.0;
-        scale32[threadIdx.x] = __double2float_rn(scale[threadIdx.x]);
+        const float s32 = __double2float_rn(scale[threadIdx.x]);
+        scale32[threadIdx.x] = s32;
+        fast[threadIdx.x] = s32 == 0.0f || (s32 >= 1.17549435e-38f && s32 <= 3.40282347e38f);
     }
     __syncthreads();
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -47,7 +52,7 @@ __global__ void k_vox_keys(const float* __restrict__ x, int64_t stride, int64_t 
         const float f = __fmul_rn(__fsub_rn(xa, lo32), scale32[a]);
         const float r = rintf(f);
         const bool near_face = r >= 1.0f && r <= (float)(R - 1) && fabsf(f - r) <= fabsf(f) * 0x1p-21f;
-        if (!near_face && f == f) {
+        if (fast[a] && !near_face && f == f) {
             const float fl = floorf(f);
             ix[a] = fl < 0.0f ? 0u : (fl > (float)(R - 1) ? (uint32_t)(R - 1) : (uint32_t)fl);
         } else {

@@ -74,6 +74,25 @@ def test_pool_cell_faces_match_oracle(fipt, R):
     assert np.array_equal(g, o.astype(np.float32))
 
 
+def test_pool_degenerate_extent_matches_oracle(fipt):
+    """A scene box whose z extent is the subnormal 1e-39: R / extent is
+    larger than any float32, so every pixel's z cell comes from the FP64
+    arithmetic; the x and y axes keep the float32 route."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 1e-39], [1, 1, 1e-39]], np.float32)
+    F = np.array([[0, 1, 2], [1, 3, 2]], np.int32)
+    z = np.array([0.0, 1e-45, 1e-40, 2.5e-40, 3e-40, 5e-40, 7.5e-40, 1e-39, 2e-39, -1e-45], np.float32)
+    rng = np.random.default_rng(4)
+    n = 4000
+    x = np.stack([rng.uniform(0, 1, n), rng.uniform(0, 1, n), rng.choice(z, n)], 1).astype(np.float32)
+    L = rng.uniform(0, 2, (n, 3)).astype(np.float32)
+    sc = fipt.Scene(cu(V), cu(F), cu(np.zeros((2, 3), np.float32)), cu(np.zeros((2, 3), np.float32)))
+    for R in (4, 16):
+        g = sc.voxel_cache(cu(x), cu(L), R).cpu().numpy()
+        o = O.OracleScene(V, F).voxel_pool(x, L, R)
+        assert np.array_equal(g, o.astype(np.float32))
+        assert (o[..., 3].sum(axis=(1, 2)) > 0).sum() >= 3          # several z layers are occupied
+
+
 def test_pool_mixed_magnitudes_match_oracle(fipt):
     """Voxels whose pixels mix zeros, both signs, subnormals, infinities,
     NaNs and magnitudes far apart (sums that leave the range in which the
