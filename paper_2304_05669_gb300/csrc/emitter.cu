@@ -4,8 +4,9 @@
 //    Philox uniforms, counter (t, j, 0x400, request)); the caller evaluates
 //    its emission-mask field alpha there.
 // 2. A triangle is an emitter when the mean of its n alphas exceeds the
-//    threshold (0.01 in the paper); the mean is summed in sample order in
-//    FP64, so the decision is deterministic.
+//    threshold (0.01 in the paper); the mean is the FP64 sum in sample
+//    order over n (reached by exact integer sums where those apply), so
+//    the decision is deterministic.
 // 3. With zero reflectance at emitters, the L1 problem of Eq. 12 is solved
 //    per channel by the median of the radiance of the input pixels whose
 //    first hit is the triangle.  The pixels on emitter triangles are
@@ -13,8 +14,9 @@
 //    over the triangles for each one's segment, and a scatter of each
 //    pixel's three channel keys into its segment (in any order within it);
 //    the lower median (rank (c - 1) / 2 of a segment's c keys in each
-//    channel's order) is found by radix selection on order-preserving bits
-//    of the values, which picks the element a sort would put at that rank
+//    channel's order) is found on order-preserving bits of the values, by
+//    ranking for segments of at most 32 keys and by radix selection for
+//    longer ones; both pick the element a sort would put at that rank
 //    whatever the order within the segment.
 #include "fipt_internal.cuh"
 #include "exact_sum.cuh"
@@ -274,7 +276,7 @@ __global__ void k_emit_scatter(const int32_t* __restrict__ tri, int64_t stride, 
 
 // Lower median of each channel of the triangles with at most 32 pixels, a
 // warp per triangle: lane j holds the triangle's j-th key, counts the keys
-// ordered before it by (key, position) with 32 shuffles, and the lane whose
+// ordered before it by (key, position) with n shuffles, and the lane whose
 // count is (n - 1) / 2 holds the key a sort would put at that rank.
 // Triangles with more pixels are left to k_emit_select.
 constexpr int SEL_SMALL = 32;
