@@ -25,23 +25,45 @@ namespace {
 
 constexpr uint32_t EMIT_LANE = 0x400u;
 
-// IDX: uint32_t when T * n < 2^32 (a 32-bit division splits the sample
-// index), int64_t otherwise.  A block stages its PTS_THREADS points in
-// shared memory and writes them as float4 (the block's 12 * PTS_THREADS
-// bytes start 16-byte aligned when x is).
+// Division of 32-bit indices by the invariant n (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with
+// l = ceil(log2 n) and m = floor(2^32 (2^l - n) / n) + 1, every 32-bit i
+// has i / n = (t + ((i - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, i).
+struct DivN {
+    uint32_t m;
+    int s1, s2;
+};
+
+DivN div_by(uint32_t n) {
+    int l = 0;
+    while (((uint64_t)1 << l) < n) ++l;
+    const uint64_t m = (((uint64_t)1 << 32) * (((uint64_t)1 << l) - n)) / n + 1;
+    return DivN{(uint32_t)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
+}
+
+// IDX: uint32_t when T * n < 2^32 (the sample index splits by the
+// multiply-high division above), int64_t otherwise.  A block stages its
+// PTS_THREADS points in shared memory and writes them as float4 (the
+// block's 12 * PTS_THREADS bytes start 16-byte aligned when x is).
 constexpr int PTS_THREADS = 256;
 
 template <class IDX>
 __global__ void __launch_bounds__(PTS_THREADS)
-k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv, int64_t T, int n, uint2 key,
-              uint32_t rid, float* __restrict__ x) {
+k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv, int64_t T, int n, DivN dn,
+              uint2 key, uint32_t rid, float* __restrict__ x) {
     __shared__ float4 buf[3 * PTS_THREADS / 4];
     float* sb = reinterpret_cast<float*>(buf);
     const int64_t total = T * n;
     const int64_t base = (int64_t)blockIdx.x * PTS_THREADS;
     const int64_t i = base + threadIdx.x;
     if (i < total) {
-        const IDX t = (IDX)i / (IDX)n;
+        IDX t;
+        if constexpr (sizeof(IDX) == 4) {
+            const uint32_t i32 = (uint32_t)i, hi = __umulhi(dn.m, i32);
+            t = (hi + ((i32 - hi) >> dn.s1)) >> dn.s2;
+        } else {
+            t = (IDX)i / (IDX)n;
+        }
         const uint32_t j = (uint32_t)((IDX)i - t * (IDX)n);
         const int leaf = inv[t];
         const float4 p0 = __ldg(tris + 3 * leaf), p1 = __ldg(tris + 3 * leaf + 1), p2 = __ldg(tris + 3 * leaf + 2);
@@ -433,12 +455,13 @@ extern "C" fipt_status fipt_emitter_sample_points(fipt_scene* s, uint64_t seed, 
     FIPT_CUDA(cudaSetDevice(s->ctx->device));
     const int64_t n = s->T * n_per_tri;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const DivN dn = div_by((uint32_t)n_per_tri);
     if (n < ((int64_t)1 << 32))
         FIPT_LAUNCH(k_emit_points<uint32_t>, blocks(n, PTS_THREADS), PTS_THREADS, 0,
-                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
+                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, dn, key, request_id, x);
     else
         FIPT_LAUNCH(k_emit_points<int64_t>, blocks(n, PTS_THREADS), PTS_THREADS, 0,
-                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, key, request_id, x);
+                    static_cast<cudaStream_t>(stream), s->tris, s->inv, s->T, n_per_tri, dn, key, request_id, x);
     FIPT_LAUNCHED("emitter sample points");
     return FIPT_OK;
 }
