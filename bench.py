@@ -1,14 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the factorized shading-term bake hot path on one GB300.
 
-Workload (default): the ~176k-triangle procedural room, 24 pinhole views
-at 320x208 whose first 2^20 hits are the query points, 128 samples per
-point for L_d and for each of the 6 roughness levels of L_s0/L_s1.  One
-step runs the whole path on device-resident inputs:
+Workload (default): the 2,045,464-triangle building floor (four rooms), 16
+pinhole views at 512x512 whose first 2^22 hits are the query points, 256
+samples per point for L_d and for each of the 6 roughness levels of
+L_s0/L_s1.  ``--workload room`` selects the ~176k-triangle procedural room
+(24 views at 320x208, first 2^20 hits, 128 spp).  One step runs the whole
+path on device-resident inputs:
 
-  scene build (bounds, Morton, radix sort, Karras tree, pack, refit)
-  -> pinhole first hits -> compaction to 2^20 queries
-  -> bake of L_d, L_s0, L_s1 (N * S * (1 + K) = 939,524,096 rays)
+  scene build (bounds, Morton, radix sort, Karras tree, pack, refit,
+  treelet restructuring, depth-first relayout)
+  -> pinhole first hits -> compaction to N queries
+  -> bake of L_d, L_s0, L_s1 (N * S * (1 + K) rays: 7,516,192,768 on the floor)
   -> factorized render forward (+ tone-mapped loss) and backward
   -> per-triangle rendering error.
 
@@ -43,12 +46,13 @@ METRIC = ("Mrays/s and shading-term points/s at 1e-4 rel. vs oracle; "
 SIGMA = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
 WORKLOADS = {
     # name: scene, views, W, H, N, spp_d, spp_s, scene seed, view seed
-    "room": dict(scene="room", views=24, W=320, H=208, N=1 << 20, spp_d=128, spp_s=128,
+    "room": dict(scene="room", views=24, W=320, H=208, N=1 << 20, spp_d=128, spp_s=128, cpu_points=16384,
                  desc="procedural room 175,926 tris; 24 views 320x208; first 2^20 hits; "
                       "128 spp; 6-level roughness grid"),
     "cornell": dict(scene="cornell", views=4, W=64, H=64, N=4096, spp_d=64, spp_s=64, surface=True,
+                    cpu_points=4096,
                     desc="Cornell box 36 tris; 4096 points uniform on surfaces (seed 0); 64 spp"),
-    "floor": dict(scene="floor", views=16, W=512, H=512, N=1 << 22, spp_d=256, spp_s=256,
+    "floor": dict(scene="floor", views=16, W=512, H=512, N=1 << 22, spp_d=256, spp_s=256, cpu_points=4096,
                   desc="building floor 2,045,464 tris; 16 views 512x512; 2^22 hits; 256 spp"),
     # the differentiation config: factorized render forward (+ loss) and
     # backward over 24 views at 640x416 with synthetic shading tables
@@ -64,9 +68,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-points", type=int, default=16384,
-                    help="points in the CPU-oracle sample (cpu_baseline)")
+    ap.add_argument("--workload", default="floor", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-points", type=int, default=None,
+                    help="points in the CPU-oracle sample (cpu_baseline; default: 4096 on the "
+                         "floor, 16384 on the room)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--points", type=int, default=None,
@@ -100,6 +105,14 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def measured_sm_max():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def source_digest():
@@ -246,7 +259,7 @@ def oracle_sample(mesh, cams, W, H, npts, spp_d, spp_s, request_id=0, surface=Fa
     return rays, dt, threads, len(ok)
 
 
-def run_reference_render(args, wl):
+def run_reference_render(args, wl, world):
     """The oracle's render forward + loss + analytic gradient on a bounded
     sample of the render workload's size (the tables are drawn by the
     shading-table generator: the arithmetic does not depend on their values
@@ -274,7 +287,7 @@ def run_reference_render(args, wl):
         "unit": "Mpixels/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample": sample},
+        "config": render_config(wl, world),
         "cpu_baseline": {"value": round(v, 4), "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -285,7 +298,7 @@ def run_reference(args, wl, world, rank):
     if rank != 0:
         return
     if wl["scene"] is None:
-        run_reference_render(args, wl)
+        run_reference_render(args, wl, world)
         return
     mesh = make_scene(wl["scene"])
     from workloads import pinhole_views
@@ -308,7 +321,7 @@ def run_reference(args, wl, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * tot_t / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample": sample},
+        "config": bake_config(wl, mesh.T, world),
         "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0,
@@ -317,6 +330,12 @@ def run_reference(args, wl, world, rank):
 
 
 # ---------------------------------------------------------------- render workload
+def render_config(wl, world):
+    return {"workload": wl["desc"], "pixels": wl["N"], "roughness_levels": len(SIGMA),
+            "scene_tris": 175926, "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "flushed between steps (512 MB write outside the timed events)"}
+
+
 # one pass: Ld, the two specular rows (K = 6), albedo, rough, metal, Lgt and
 # the emitter mask in; Lr and the three gradients out
 RENDER_BYTES_PER_PX = (12 + 72 + 72 + 12 + 4 + 4 + 12 + 1) + (12 + 12 + 4 + 4)
@@ -441,8 +460,7 @@ def run_render(args, wl, world, rank, local):
         "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * step_s, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "pixels": N, "roughness_levels": len(SIGMA), "scene_tris": mesh.T,
-                   "l2": "flushed between steps (512 MB write outside the timed events)"},
+        "config": render_config(wl, world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "k_render_fwd_grad + k_render_grad_scale", "peak_kind": peak_kind,
@@ -760,6 +778,63 @@ def run_next_rows(args, F, dev, mesh, sc, q, Lgt, qa, with_cpu, peak):
     return out
 
 
+def bake_config(wl, scene_tris, world):
+    """The workload description both arms print (identical dicts, so the
+    two lines describe the same configuration)."""
+    K = len(SIGMA)
+    surface = wl.get("surface", False)
+    return {"workload": wl["desc"], "scene_tris": int(scene_tris), "points": wl["N"],
+            "spp_diffuse": wl["spp_d"], "spp_specular": wl["spp_s"], "roughness_levels": K,
+            "rays_per_step": wl["N"] * (wl["spp_d"] + K * wl["spp_s"]), "views": wl["views"],
+            "resolution": [wl["W"], wl["H"]],
+            "l2": "flushed between steps (512 MB write outside the timed events)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "step": ("scene build + bake + render fwd/bwd + per-triangle error" if surface else
+                     "scene build + first hits + compaction + bake + render fwd/bwd + "
+                     "per-triangle error")}
+
+
+def bake_roofline(prof, rays_per_step, n_rays_traced, alg_bytes, bake_s, sm_mhz, n_sm):
+    """Ceilings of the bake kernel.  The one that binds is instruction
+    issue: one warp instruction per scheduler per SM clock (4 schedulers
+    per SM), so peak = SMs x 4 x the SM clock sampled during the timed
+    region.  Issued warp instructions, DRAM bytes and active lanes per warp
+    instruction come from the committed ncu capture of the same kernel
+    source (per nominal ray, scaled to this launch).  Beside it: DRAM
+    traffic against the measured HBM copy rate, and the algorithmic node /
+    triangle bytes of the walk, which L1 and L2 serve (so that figure is a
+    cache-served rate, not HBM traffic)."""
+    hbm, hbm_kind = measured_peaks()
+    cache = {"bound": "l1l2_algorithmic", "achieved": round(alg_bytes / bake_s / 1e9, 1),
+             "peak": hbm, "unit": "GB/s", "frac": round(alg_bytes / bake_s / 1e9 / hbm, 4),
+             "peak_kind": hbm_kind,
+             "note": "algorithmic node + triangle + gather bytes per ray / bake time; served by L1/L2"}
+    if prof is None or "warp_inst_per_ray" not in prof:
+        out = dict(cache)
+        out.update({"traffic": None, "kernel": "k_bake",
+                    "note": cache["note"] + "; no ncu capture of the current kernel source"})
+        return out
+    traffic = float(prof["dram_bytes_per_ray"]) * rays_per_step
+    inst = float(prof["warp_inst_per_ray"]) * rays_per_step
+    peak_issue = n_sm * 4 * sm_mhz / 1e3                # G warp instructions / s
+    ach_issue = inst / bake_s / 1e9
+    lanes = float(prof["lanes_per_warp_inst"])
+    return {"bound": "alu", "achieved": round(ach_issue, 1), "peak": round(peak_issue, 1),
+            "unit": "Gwarp-inst/s", "frac": round(ach_issue / peak_issue, 4),
+            "traffic": int(round(traffic)), "kernel": "k_bake",
+            "peak_kind": "derived: %d SMs x 4 schedulers x %.0f MHz sampled SM clock" % (n_sm, sm_mhz),
+            "what": "warp-instruction issue (the walk is bound by issue and divergence, not by HBM)",
+            "warp_inst_per_ray": round(float(prof["warp_inst_per_ray"]), 2),
+            "lanes_per_warp_inst": lanes,
+            "lane_frac": round(ach_issue / peak_issue * lanes / 32.0, 4),
+            "dram": {"achieved": round(traffic / bake_s / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(traffic / bake_s / 1e9 / hbm, 4), "peak_kind": hbm_kind,
+                     "bytes_per_ray": round(float(prof["dram_bytes_per_ray"]), 2)},
+            "cache_served": cache,
+            "ncu": {k: prof[k] for k in ("issue_active_pct", "l1_hit_pct", "l2_hit_pct", "capture")
+                    if k in prof}}
+
+
 def pinhole_views_for(mesh):
     from workloads import pinhole_views
     return pinhole_views(mesh, 24, seed=2)
@@ -880,8 +955,9 @@ def run_ours(args, wl, world, rank, local):
         barrier(world)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = min(args.steps, 5)
         e0.record(stream)
-        for s in range(args.steps):
+        for s in range(e2e_steps):
             d = {k: pinned[k].to(dev, non_blocking=True) for k in in_keys}
             Lg = Lgt_host.to(dev, non_blocking=True)
             _sc, (Ld, Ls0, Ls1), _q, loss, grads, (err, cnt) = step(d, Lg)
@@ -894,9 +970,9 @@ def run_ours(args, wl, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
-        e2e = {"value": round(world * rays_per_step * args.steps / t_e2e / 1e6, 3),
+        e2e = {"value": round(world * rays_per_step * e2e_steps / t_e2e / 1e6, 3),
                "unit": "Mrays/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": round(1e3 * t_e2e / args.steps, 3)}
+               "ms_per_step": round(1e3 * t_e2e / e2e_steps, 3), "steps": e2e_steps}
 
     # -------------------------------------------------- roofline of the bake
     stats = torch.zeros(4, dtype=torch.int64, device=dev)
@@ -906,10 +982,14 @@ def run_ours(args, wl, world, rank, local):
     bytes_per_ray = (64.0 * n_nodes + 48.0 * n_tris + 24.0 * n_rays) / max(n_rays, 1)
     alg_bytes = bytes_per_ray * n_rays + N * (40 + 4 * 3 * (1 + 2 * K))
     bake_s = float(np.mean(bake_ms)) / 1e3
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / bake_s / 1e9
-    prof = recorded_profile(args.workload)
-    traffic_per_ray = float(prof["dram_bytes_per_ray"]) if prof else None
+    prof = recorded_profile(args.workload) if args.points is None and args.spp is None else None
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or measured_sm_max()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = bake_roofline(prof, rays_per_step, n_rays, alg_bytes, bake_s, sm_mhz, n_sm)
+    roof.update({"alg_bytes_per_ray": round(bytes_per_ray, 1),
+                 "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2),
+                 "tris_per_ray": round(n_tris / max(n_rays, 1), 2), "max_stack": max_depth})
 
     # -------------------------------------------------- CPU baseline (rank 0, N=1)
     cpu = None
@@ -943,34 +1023,22 @@ def run_ours(args, wl, world, rank, local):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * t_total / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["desc"], "scene_tris": mesh.T, "points": N,
-                   "spp_diffuse": spp_d, "spp_specular": spp_s, "roughness_levels": K,
-                   "rays_per_step": rays_per_step, "views": wl["views"], "resolution": [W, H],
-                   "l2": "flushed between steps (512 MB write outside the timed events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "step": ("scene build + bake + render fwd/bwd + per-triangle error" if surface else
-                            "scene build + first hits + compaction + bake + render fwd/bwd + "
-                            "per-triangle error")},
+        "config": bake_config(wl, mesh.T, world),
         "points_per_s": round(world * N * args.steps / t_total, 1),
         "bake_ms": round(1e3 * bake_s, 3),
         "bake_mrays_per_s": round(rays_per_step / bake_s / 1e6, 3),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": (round(traffic_per_ray * n_rays) if traffic_per_ray else None),
-                     "kernel": "k_bake", "peak_kind": peak_kind,
-                     "alg_bytes_per_ray": round(bytes_per_ray, 1),
-                     "nodes_per_ray": round(n_nodes / max(n_rays, 1), 2),
-                     "tris_per_ray": round(n_tris / max(n_rays, 1), 2),
-                     "max_stack": max_depth,
-                     "ncu": ({k: prof[k] for k in ("issue_active_pct", "l2_hit_pct", "lanes_per_warp_inst")
-                              if k in prof} if prof else None)},
+        # rays = N * S * (1 + K) samples; specular samples with n.wi <= 0 or
+        # wo.h <= 0 contribute zero and trace nothing
+        "traced_rays_per_step": int(n_rays),
+        "bake_traced_mrays_per_s": round(n_rays / bake_s / 1e6, 3),
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "refine": refine,
         "next_rows": next_rows,
         "serving": serving,
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     print(json.dumps(out))
 
@@ -978,6 +1046,8 @@ def run_ours(args, wl, world, rank, local):
 def main():
     args = parse()
     wl = dict(WORKLOADS[args.workload])
+    if args.cpu_points is None:
+        args.cpu_points = wl.get("cpu_points", 4096)
     if args.points:
         wl["N"] = args.points
         wl["desc"] += "; overridden to %d points" % args.points

@@ -83,6 +83,7 @@ def _L():
         L.oracle_refine.argtypes = [P, P, P, P, P, P, P, P, I64, U64, U32, U32, I32, I32, I32, P,
                                     D, I32, I32, D, I32, P, P, P]
         L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
+        L.oracle_env_lookup.argtypes = [P, P, I64, P]
         L.oracle_voxel_pool.argtypes = [P, P, P, I64, I32, P]
         L.oracle_scene_set_voxel_cache.argtypes = [P, P, I32]
         L.oracle_brdf_cos.argtypes = [P, P, P, P, ctypes.c_float, ctypes.c_float, P]
@@ -161,6 +162,14 @@ class OracleScene:
         self._env = _c(env, np.float32)
         H, W = self._env.shape[:2]
         _L().oracle_scene_set_environment(self._h, _p(self._env), int(W), int(H))
+
+    def env_lookup(self, dirs):
+        """Environment radiance [n, 3] seen along unit directions dirs [n, 3]
+        (zero without a map)."""
+        d = _c(dirs, np.float64).reshape(-1, 3)
+        out = np.zeros((len(d), 3))
+        _L().oracle_env_lookup(self._h, _p(d), len(d), _p(out))
+        return out
 
     def voxel_pool(self, x, L, R):
         """Sec. 4.2: average pooling of pixel radiance L [P,3] at first-hit

@@ -351,6 +351,12 @@ static void env_lookup(const oscene* S, const double d[3], double L[3])
         }
 }
 
+/* Environment radiance for n unit directions (rows of dirs) -> out [n][3]. */
+void oracle_env_lookup(const oscene* S, const double* dirs, int64_t n, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) env_lookup(S, dirs + 3 * i, out + 3 * i);
+}
+
 void oracle_scene_info(const oscene* S, double* lo, double* hi, double* eps, double* L)
 {
     for (int a = 0; a < 3; ++a) { lo[a] = S->slo[a]; hi[a] = S->shi[a]; }

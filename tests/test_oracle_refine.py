@@ -93,3 +93,104 @@ def test_mirror_floor_reflects_the_emitter():
     # without the floor's reflection (all rough, cache 0) the point stays dark
     dark = S.refine(q, [0.5], 1024, 1, a, np.ones(T, np.float32), mt, mis=True)["flat"][0, :3]
     assert np.all(dark == 0)
+
+
+def _mirror_pair_scene(a_mirror):
+    """Cornell box without boxes, cache 0: floor and ceiling are metallic
+    GGX mirrors (sigma = 0.02 <= sigma_c, metallic 1, albedo a, so
+    k_d = 0 and the reflectance is Schlick's a + (1 - a)(1 - cos)^5); the
+    side walls are rough (sigma = 1 > sigma_c) and dark, so paths that meet
+    them end with 0."""
+    m = cornell_box(with_boxes=False, cache_value=0.0)
+    T = m.T
+    ys = m.V[m.F][:, :, 1]
+    ceiling = (ys == 1.0).all(1) & ~m.emitter
+    mirror = m.floor | ceiling
+    assert mirror.sum() == 4
+    a = np.ones((T, 3), np.float32)
+    r = np.ones(T, np.float32)
+    mt = np.zeros(T, np.float32)
+    a[mirror] = a_mirror
+    r[mirror] = 0.02
+    mt[mirror] = 1.0
+    # wind the mirrors to face out of the box: a path vertex must turn the
+    # geometric normal toward the ray it arrives on
+    m.F[mirror] = m.F[mirror][:, ::-1]
+    return m, a, r, mt
+
+
+def test_two_mirror_image_and_depth_cut():
+    """Floor and ceiling mirrors facing each other under the Cornell light.
+    A floor point at (0.1, 0, 0.1) sees the light directly and, through the
+    ceiling then the floor mirror, the light's second image: unfolded, the
+    quad at y = 2 + 0.999, same x/z footprint (for this point the cone to
+    that image clears the real light and its first, back-facing image).  The
+    image reaches L_d through a path whose vertices 1 and 2 are mirrors, so
+    with max_depth = 1 it is cut and L_d = L_e F_direct (Lambert's closed
+    form); with max_depth = 2 (4-mirror images still cut)
+    L_d = L_e (F_direct + J), J = (1/pi) int_quad R(cos)^2 h^2 / r^4 dA with
+    R the Schlick reflectance of each bounce at the ray's incidence angle
+    (h / r), by 2-D quadrature.  The throughput product at depth 2 (R^2 with
+    a = 0.5, not R), the depth cut, the skipped triangle and the origin
+    offset at later vertices all enter this difference."""
+    from scipy import integrate
+    from test_oracle_bake import lambert_form_factor
+    am = 0.5
+    m, a, r, mt = _mirror_pair_scene(am)
+    S = O.OracleScene.from_mesh(m)
+    npts = 32
+    x = np.array([0.1, 0.0, 0.1])
+    q = {"x": np.tile(x.astype(np.float32), (npts, 1)), "n": np.tile(np.float32([0, 1, 0]), (npts, 1)),
+         "wo": np.tile(np.float32([0, 1, 0]), (npts, 1)), "tri": np.full(npts, -1, np.int32)}
+    Le = m.Le[m.emitter][0].astype(np.float64)
+    p = x + np.array([0, S.eps, 0])
+    y = 0.999
+    poly = np.array([[0.35, y, 0.35], [0.65, y, 0.35], [0.65, y, 0.65], [0.35, y, 0.65]])
+    f_direct = lambert_form_factor(p, np.array([0, 1.0, 0]), poly)
+
+    def kern(Z, X):
+        h = 2.0 + y - p[1]
+        r2 = (X - p[0]) ** 2 + h ** 2 + (Z - p[2]) ** 2
+        c = h / np.sqrt(r2)
+        R = am + (1 - am) * (1 - c) ** 5
+        return R * R * h * h / (np.pi * r2 * r2)
+    J = integrate.dblquad(kern, 0.35, 0.65, 0.35, 0.65, epsabs=1e-13, epsrel=1e-11)[0]
+    for depth, ref in ((1, Le * f_direct), (2, Le * (f_direct + J))):
+        out = S.refine(q, [0.5], 65536, 1, a, r, mt, max_depth=depth, mis=True, seed=7,
+                       request_id=depth)["flat"][:, :3]
+        mean, se = out.mean(0), out.std(0, ddof=1) / np.sqrt(npts)
+        # the GGX lobe at sigma = 0.02 is a mirror to ~1e-5 in energy
+        assert np.all(np.abs(mean - ref) <= 4 * se + 2e-3 * Le * J), (depth, mean, ref, se, Le * J)
+
+
+def test_vertex_brdf_directional_albedo():
+    """The full BRDF of Eq. 1 that a path vertex samples and evaluates
+    (k_d / pi + (k_s F0 + F1) D G / (4 mu_o mu_i), times mu_i), integrated
+    over incoming directions, is the directional albedo
+    k_d + k_s A(mu_o, sigma) + B(mu_o, sigma), with A and B the split-sum
+    integrals of the Fresnel factors (computed independently by quadrature in
+    the bake's pins).  Metallic 1 leaves only the specular part
+    (a A + B): a Fresnel split F0 = 1 would add a B; metallic 0 on a rough
+    surface gives a + 0.04 A + B."""
+    from test_oracle_bake import half_vector_nodes, hemisphere_nodes, white_furnace_AB
+    n = np.array([0.0, 0.0, 1.0])
+    alb = np.float32([0.7, 0.4, 0.2])
+    for mu_o, sg, mt in ((0.3, 0.5, 1.0), (0.8, 0.3, 1.0), (0.5, 1.0, 0.0)):
+        al = sg * sg
+        wo = np.array([np.sqrt(1 - mu_o ** 2), 0.0, mu_o])
+        A, B = white_furnace_AB(mu_o, al, 256, 256)
+        if mt == 1.0:      # half-vector nodes follow the specular peak
+            h, W = half_vector_nodes(al, 160, 160)
+            c = h @ wo
+            wi = 2.0 * c[:, None] * h - wo
+            W = W * 4.0 * np.maximum(c, 0.0)
+        else:              # a broad lobe: plain hemisphere nodes
+            wi, W = hemisphere_nodes(160, 160)
+        keep = (wi @ n > 0) & (W > 0)
+        tot = np.zeros(3)
+        for d, w in zip(wi[keep], W[keep]):
+            tot += w * O.brdf_cos(n, wo, d, alb, sg, mt)
+        kd = alb * (1 - mt)
+        ks = 0.04 * (1 - mt) + alb * mt
+        ref = kd + ks * A + B
+        assert np.allclose(tot, ref, rtol=2e-5, atol=0), (mu_o, sg, mt, tot, ref)
