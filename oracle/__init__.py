@@ -81,7 +81,7 @@ def _L():
                                             P, P, P]
         L.oracle_camera_queries.restype = I32
         L.oracle_refine.argtypes = [P, P, P, P, P, P, P, P, I64, U64, U32, U32, I32, I32, I32, P,
-                                    D, I32, I32, D, I32, P, P, P]
+                                    D, I32, I32, D, I32, P, P, P, P, P, P]
         L.oracle_scene_set_environment.argtypes = [P, P, I32, I32]
         L.oracle_env_lookup.argtypes = [P, P, I64, P]
         L.oracle_voxel_pool.argtypes = [P, P, P, I64, I32, P]
@@ -251,13 +251,17 @@ class OracleScene:
 
     def refine(self, q, sigma, spp_d, spp_s, albedo, rough, metal, sigma_c=0.6, max_depth=8,
                mis=True, seed=0, request_id=0, point_base=0, eta=0.0, per_sample=False,
-               nthreads=None):
+               bounds=False, nthreads=None):
         """Stage-3 path-traced shadings (Sec. 4.3, Eq. 10; MIS per Sec. 6) with
         per-triangle materials albedo [T,3], rough [T], metal [T].  Returns the
         bake layout; with per_sample also every sample's 6 values
-        ([N, 1+K, Smax, 6]) and its ambiguity flag ([N, 1+K, Smax]).  The
-        roughness threshold is rounded to float32 first: materials are
-        float32, so "rougher than sigma_c" is decided on float32 values."""
+        ([N, 1+K, Smax, 6]) and its ambiguity flag ([N, 1+K, Smax]).  With
+        bounds (needs per_sample and eta > 0) also ``lo`` / ``hi``, each
+        sample's range over every decision a float32 path may take the other
+        way, and ``unbounded`` ([N, 1+K, Smax] bool) where that range is
+        [0, inf].  The roughness threshold is rounded to float32 first:
+        materials are float32, so "rougher than sigma_c" is decided on
+        float32 values."""
         sig = _c(sigma, np.float64)
         K = len(sig)
         x, nn, wo, tri = (_c(q["x"], np.float32), _c(q["n"], np.float32),
@@ -269,16 +273,23 @@ class OracleScene:
         smax = max(spp_d, spp_s)
         ps = np.zeros((N, K + 1, smax, 6)) if per_sample else None
         amb = np.zeros((N, K + 1, smax), np.uint8) if per_sample else None
+        bounds = bool(bounds and per_sample and eta > 0)
+        lo = np.zeros((N, K + 1, smax, 6)) if bounds else None
+        hi = np.zeros((N, K + 1, smax, 6)) if bounds else None
+        unb = np.zeros((N, K + 1, smax), np.uint8) if bounds else None
         _L().oracle_refine(self._h, _p(a), _p(r), _p(m), _p(x), _p(nn), _p(wo), _p(tri), N,
                            int(seed) & (2**64 - 1), int(request_id), int(point_base), int(spp_d),
                            int(spp_s), K, _p(sig), float(np.float32(sigma_c)), int(max_depth),
                            int(bool(mis)),
-                           float(eta), int(nthreads or default_threads()), _p(out), _p(ps), _p(amb))
+                           float(eta), int(nthreads or default_threads()), _p(out), _p(ps), _p(amb),
+                           _p(lo), _p(hi), _p(unb))
         res = {"Ld": out[:, :3], "Ls0": out[:, 3:3 + 3 * K].reshape(N, K, 3),
                "Ls1": out[:, 3 + 3 * K:].reshape(N, K, 3), "flat": out}
         if per_sample:
             res["per_sample"] = ps
             res["amb"] = amb.astype(bool)
+        if bounds:
+            res["lo"], res["hi"], res["unbounded"] = lo, hi, unb.astype(bool)
         return res
 
     def camera_queries(self, cams, W, H, pixels, eta=0.0):

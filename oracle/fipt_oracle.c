@@ -606,8 +606,15 @@ static void radiance(const oscene* S, int32_t id, int front, const double o[3], 
     for (int a = 0; a < 3; ++a) L[a] = (front ? S->Le[3*id+a] : 0.0) + C[a];
 }
 
-/* Cache values of every voxel a float32 hit point near p may fall in. */
+/* Cache values of every voxel a float32 hit point near p may fall in:
+ * the cell of p and its neighbours across faces within w (a fraction of
+ * the cell) of p. */
+static void voxel_range_w(const oscene* S, const double p[3], double w, double lo[3], double hi[3]);
 static void voxel_range(const oscene* S, const double p[3], double lo[3], double hi[3])
+{
+    voxel_range_w(S, p, 1e-3, lo, hi);
+}
+static void voxel_range_w(const oscene* S, const double p[3], double w, double lo[3], double hi[3])
 {
     const int R = S->vox_r;
     double fr[3];
@@ -621,8 +628,8 @@ static void voxel_range(const oscene* S, const double p[3], double lo[3], double
                 int ok = 1;
                 int64_t ix[3];
                 for (int a = 0; a < 3; ++a) {
-                    if (dd[a] == -1 && !(fr[a] < 1e-3)) ok = 0;
-                    if (dd[a] == 1 && !(fr[a] > 1.0 - 1e-3)) ok = 0;
+                    if (dd[a] == -1 && !(fr[a] < w)) ok = 0;
+                    if (dd[a] == 1 && !(fr[a] > 1.0 - w)) ok = 0;
                     ix[a] = base[a] + dd[a];
                     if (ix[a] < 0 || ix[a] > R - 1) ok = 0;
                 }
@@ -1017,6 +1024,8 @@ typedef struct {
     double* out;                 /* N x (3 + 6K) */
     double* per_sample;          /* nullable: N x (1+K) x Smax x 6 */
     uint8_t* amb;                /* nullable: N x (1+K) x Smax */
+    double *ps_lo, *ps_hi;       /* nullable: N x (1+K) x Smax x 6, ranges (see sample_range) */
+    uint8_t* unb;                /* nullable: N x (1+K) x Smax, 1 = range not bounded */
     int smax;
     int64_t next;
 } refine_job;
@@ -1269,6 +1278,571 @@ static void path_radiance(const refine_job* R, const double o0[3], const double 
     }
 }
 
+/* ------------------------------------------------------------------ */
+/* Ranges of refinement samples over the decisions float32 can flip     */
+/* ------------------------------------------------------------------ */
+/* A float32 path may take the other side of any decision that lies
+ * within its rounding of a threshold, and along a path that rounding
+ * grows: the hit point of a ray whose origin is uncertain by e_o and whose
+ * direction by e_d is uncertain by (e_o + t e_d) / |cos| on the surface it
+ * meets, a glossy reflection keeps its incoming direction's uncertainty,
+ * and every float32 step adds a few units of 2^-24.  For each sample the
+ * functions below carry (e_o, e_d) along every branch and follow every
+ * alternative within them:
+ *   - every hit a perturbed ray may report (closest() with its window
+ *     widened to the ray's uncertainty), both facings where grazing, a miss
+ *     where one is possible;
+ *   - both emitter triangles where the area-sampling uniform lies within
+ *     1e-6 A of a cumulative boundary;
+ *   - zero for an emitter sample whose cosine at the emitter or at the
+ *     receiver is within its uncertainty (at least 1e-5) of 0; lit and
+ *     unlit where the shadow ray's candidates disagree about reaching the
+ *     sampled triangle;
+ *   - the specular lobe on and off where n.wo is within max(1e-6, 2 e_d)
+ *     of 1e-2; with and without the specular part where wo.h is within
+ *     max(1e-5, ...) of 0; with and without the n.wi > 0 branch where n.wi
+ *     is within max(1e-5, ...) of 0;
+ *   - both lobes where the lobe uniform lies within 1e-5 of P_d;
+ *   - both tangent frames where the normal's z is within 2e-7 of the
+ *     frame branch;
+ *   - GGX D at a recomputed half vector tilted by -tau, 0, +tau, tau =
+ *     max(2e-6 rad, the directions' uncertainty), where D changes by more
+ *     than 1e-4 under that tilt;
+ *   - every voxel the hit point may fall in.
+ * Each combination of alternatives accumulates its terms in the nominal
+ * order, so without any alternative the range is the nominal value
+ * exactly.  Every term is non-negative; a sample whose hit points become
+ * uncertain by more than 1e-4 of the scene size, whose alternatives need
+ * more than OR_RANGE_BUDGET path segments, or whose ray meets more
+ * candidates than closest() holds, gets the range [0, inf]. */
+#define OR_RANGE_BUDGET 4096
+#define OR_TILT 2e-6
+#define OR_U32 (1.0 / 16777216.0)     /* 2^-24 */
+
+typedef struct { int32_t id; double t; int front; } oalt;
+#define OMAXALT (2 * OMAXC + 4)
+
+typedef struct {
+    const refine_job* R;
+    uint32_t pid, s, lobe;
+    int segments;
+    int unbounded;
+    double mag;                  /* largest |coordinate| of the scene box */
+    double Lmin[3], Lmax[3];
+} rwalk;
+
+static void rw_leaf(rwalk* W, const double L[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        if (L[c] < W->Lmin[c]) W->Lmin[c] = L[c];
+        if (L[c] > W->Lmax[c]) W->Lmax[c] = L[c];
+    }
+}
+
+static void alt_add(oalt* a, int* n, int32_t id, double t, int front)
+{
+    for (int i = 0; i < *n; ++i) if (a[i].id == id && (id < 0 || a[i].front == front)) return;
+    if (*n < OMAXALT) { a[*n].id = id; a[*n].t = t; a[*n].front = front; ++*n; }
+}
+
+/* Every hit a float32 ray o + t d may report (skip excluded), for an
+ * origin uncertain by eo and a direction uncertain by ed. */
+static int hit_alts(const refine_job* R, const double o[3], const double d[3], int skip,
+                    double eo, double ed, oalt* a, int* unbounded)
+{
+    double eta = R->eta;
+    if (2.0 * eo / R->S->L > eta) eta = 2.0 * eo / R->S->L;
+    if (2.0 * ed > eta) eta = 2.0 * ed;
+    ocands c;
+    closest(R->S, o, d, skip, eta, &c);
+    int n = 0;
+    if (c.overflow) *unbounded = 1;
+    alt_add(a, &n, c.nominal.id, c.nominal.t, c.nominal.front);
+    if (c.nominal.id >= 0 && c.nominal.front_amb) alt_add(a, &n, c.nominal.id, c.nominal.t, !c.nominal.front);
+    for (int i = 0; i < c.n; ++i) {
+        alt_add(a, &n, c.c[i].id, c.c[i].t, c.c[i].front);
+        if (c.c[i].front_amb) alt_add(a, &n, c.c[i].id, c.c[i].t, !c.c[i].front);
+    }
+    if (c.miss_possible) alt_add(a, &n, -1, INFINITY, 0);
+    return n;
+}
+
+/* Emitter triangles (indices into R->emit) that a float32 search of the
+ * cumulative areas may pick for uniform u0; returns how many (1 to 3). */
+static int emitter_alts(const refine_job* R, double u0, int* k)
+{
+    double target = u0 * R->A;
+    int lo = 0, hi = R->n_emit - 1;
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (R->cdf[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    int n = 0;
+    k[n++] = lo;
+    if (R->n_emit > 1) {
+        if (fabs(R->cdf[lo] - target) < 1e-6 * R->A && lo + 1 < R->n_emit) k[n++] = lo + 1;
+        if (lo > 0 && fabs(R->cdf[lo - 1] - target) < 1e-6 * R->A) k[n++] = lo - 1;
+    }
+    return n;
+}
+
+/* The point the area sample draws on emitter list entry k. */
+static int emitter_point(const refine_job* R, int k, const double u[4], double y[3])
+{
+    const otri* tr = &R->S->tri[R->emit[k]];
+    double r1 = sqrt(u[1]);
+    double b0 = 1.0 - r1, b1 = r1 * (1.0 - u[2]), b2 = r1 * u[2];
+    for (int a = 0; a < 3; ++a) y[a] = b0 * tr->v0[a] + b1 * tr->v1[a] + b2 * tr->v2[a];
+    return R->emit[k];
+}
+
+/* Frame of onb() with its branch forced (s = +1 or -1). */
+static void onb_forced(const double n[3], double s, double t[3], double b[3])
+{
+    double a = -1.0 / (s + n[2]);
+    double c = n[0] * n[1] * a;
+    t[0] = 1.0 + s * n[0] * n[0] * a; t[1] = s * c; t[2] = -s * n[0];
+    b[0] = c; b[1] = s + n[1] * n[1] * a; b[2] = -n[1];
+}
+
+/* GGX D at polar angle theta of the half vector. */
+static double ggx_D_theta(double th, double a2)
+{
+    double sn = sin(th), cs = cos(th);
+    double den = sn * sn + a2 * cs * cs;
+    return a2 / (OPI * den * den);
+}
+
+typedef struct { double f[3]; double pdf; } bvar;
+#define OMAXBV 16
+
+/* The values (f, pdf) that vertex_brdf_h may take for a float32 evaluation,
+ * with the specular lobe forced on or off (spec), wo uncertain by ed_o and
+ * wi by ed_i.  The first entry is the nominal one, computed as
+ * vertex_brdf_h computes it. */
+static int brdf_alts(const refine_job* R, int t, const double n[3], const double wo[3],
+                     const double wi[3], const double* hs, int spec, double ed_o, double ed_i,
+                     bvar* out)
+{
+    const double a[3] = {R->ma[3*t], R->ma[3*t+1], R->ma[3*t+2]};
+    const double sg = R->ms[t], m = R->mm[t];
+    const double al = sg * sg, a2 = al * al;
+    double kd[3], ks[3], kdm = 0, ksm = 0;
+    for (int c = 0; c < 3; ++c) {
+        kd[c] = a[c] * (1.0 - m); ks[c] = 0.04 * (1.0 - m) + a[c] * m;
+        kdm += R->ma[3*t+c] * (1.0 - m); ksm += 0.04 * (1.0 - m) + R->ma[3*t+c] * m;
+    }
+    double Pd = kdm / (kdm + ksm);
+    if (Pd < 0.1) Pd = 0.1;
+    if (Pd > 0.9) Pd = 0.9;
+    if (!spec) Pd = 1.0;
+    const double mu_o = dot3(n, wo), mu_i0 = dot3(n, wi);
+    const double w_mu = fmax(1e-5, 2.0 * ed_i), w_co = fmax(1e-5, 2.0 * (ed_o + ed_i));
+    const double tilt = fmax(OR_TILT, ed_o + ed_i);
+    int nv = 0;
+    /* n.wi branch: nominal first, the other side where within its window of 0 */
+    const int mu_cases[2] = {mu_i0 > 0.0, !(mu_i0 > 0.0)};
+    const int n_mu = fabs(mu_i0) < w_mu ? 2 : 1;
+    for (int im = 0; im < n_mu; ++im) {
+        if (!mu_cases[im]) {
+            bvar z = {{0, 0, 0}, 0.0};
+            if (nv < OMAXBV) out[nv++] = z;
+            continue;
+        }
+        const double mu_i = mu_i0 > 0.0 ? mu_i0 : (mu_i0 < 0.0 ? -mu_i0 : 1e-300);
+        bvar base;
+        for (int c = 0; c < 3; ++c) base.f[c] = kd[c] * mu_i / OPI;
+        base.pdf = Pd * mu_i / OPI;
+        if (!spec) { if (nv < OMAXBV) out[nv++] = base; continue; }
+        double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+        if (hs) { h[0] = hs[0]; h[1] = hs[1]; h[2] = hs[2]; }
+        normalize3(h);
+        const double ch = dot3(n, h), co0 = dot3(wo, h);
+        /* wo.h branch */
+        const int co_cases[2] = {ch > 0.0 && co0 > 0.0, !(ch > 0.0 && co0 > 0.0)};
+        const int n_co = (fabs(co0) < w_co && ch > 0.0) ? 2 : 1;
+        for (int ic = 0; ic < n_co; ++ic) {
+            if (!co_cases[ic]) { if (nv < OMAXBV) out[nv++] = base; continue; }
+            const double co = co0 > 0.0 ? co0 : (co0 < 0.0 ? -co0 : 1e-300);
+            double Ds[3];
+            int nD = 1;
+            Ds[0] = ggx_D(ch, a2);
+            if (!hs) {
+                double cr[3];
+                cross3(n, h, cr);
+                if (ggx_log_slope(ch, norm3(cr), a2) * tilt > 1e-4) {
+                    double th = atan2(norm3(cr), ch);
+                    Ds[nD++] = ggx_D_theta(th > tilt ? th - tilt : 0.0, a2);
+                    Ds[nD++] = ggx_D_theta(th + tilt, a2);
+                }
+            }
+            const double G = smith_g1(mu_i, a2) * smith_g1(mu_o, a2);
+            const double F1 = pow(1.0 - co, 5.0), F0 = 1.0 - F1;
+            for (int iD = 0; iD < nD && nv < OMAXBV; ++iD) {
+                bvar v = base;
+                const double D = Ds[iD];
+                for (int c = 0; c < 3; ++c) v.f[c] += (ks[c] * F0 + F1) * D * G / (4.0 * mu_o);
+                v.pdf += (1.0 - Pd) * D * ch / (4.0 * co);
+                out[nv++] = v;
+            }
+        }
+    }
+    return nv;
+}
+
+static void path_range(rwalk* W, const double o[3], const double d[3], int skip, double pdf_prev,
+                       const double beta[3], int depth, const double L[3], double eo, double ed);
+
+/* A path vertex on alternative hit h of the ray (o, d) at path depth
+ * `depth`, with L accumulated so far and the hit point uncertain by ex, the
+ * incoming direction by ed: next-event estimation, then every
+ * continuation. */
+static void vertex_range(rwalk* W, const double o[3], const double d[3], const oalt* h,
+                         const double beta[3], int depth, const double L[3], int nominal_facing,
+                         double ex, double ed)
+{
+    const refine_job* R = W->R;
+    const oscene* S = R->S;
+    const otri* tr = &S->tri[h->id];
+    double x[3], n[3] = {tr->ng[0], tr->ng[1], tr->ng[2]}, wo[3] = {-d[0], -d[1], -d[2]};
+    normalize3(n);
+    for (int a = 0; a < 3; ++a) x[a] = o[a] + h->t * d[a];
+    int flip = dot3(n, wo) < 0;
+    if (!nominal_facing) flip = !flip;
+    if (flip) for (int a = 0; a < 3; ++a) n[a] = -n[a];
+    const int famb = fabs(n[2] - OR_ONB_BRANCH) < 2e-7;
+    double xo[3];
+    for (int a = 0; a < 3; ++a) xo[a] = x[a] + S->eps * n[a];
+    const double exo = ex + 4.0 * OR_U32 * W->mag;     /* the offset origin in float32 */
+    const uint32_t lane = W->lobe | ((uint32_t)depth << 9);
+    const double mu_o = dot3(n, wo);
+    const int spec_nom = mu_o > 1e-2;
+    const int n_spec = fabs(mu_o - 1e-2) < fmax(1e-6, 2.0 * ed) ? 2 : 1;
+    for (int isp = 0; isp < n_spec; ++isp) {
+        const int spec = isp == 0 ? spec_nom : !spec_nom;
+        /* next-event estimation: every accumulated value it may leave */
+        double Ln[64][3];
+        int nn = 0;
+        if (R->mis && R->n_emit > 0) {
+            double u[4];
+            philox_words(W->pid, W->s, lane | 0x100u, R->request_id, R->seed, u);
+            int ks[3];
+            const int nk = emitter_alts(R, u[0], ks);
+            for (int ik = 0; ik < nk; ++ik) {
+                double y[3], wl[3];
+                const int e = emitter_point(R, ks[ik], u, y);
+                sub3(y, xo, wl);
+                double dist = norm3(wl);
+                for (int a = 0; a < 3; ++a) wl[a] /= dist;
+                const double ed_sh = exo / dist + 4.0 * OR_U32;
+                const otri* te = &S->tri[e];
+                double ce = -dot3(wl, te->ng) / te->area2;
+                int zero = !(ce > 0) || fabs(ce) < fmax(1e-5, 2.0 * ed_sh);
+                if (zero && nn < 64) { for (int c = 0; c < 3; ++c) Ln[nn][c] = L[c]; ++nn; }
+                if (!(ce > 0)) continue;
+                bvar bv[OMAXBV];
+                const int nb = brdf_alts(R, h->id, n, wo, wl, NULL, spec, ed, ed_sh, bv);
+                oalt sa[OMAXALT];
+                int sna = -1;
+                for (int ib = 0; ib < nb; ++ib) {
+                    const double* f = bv[ib].f;
+                    const double pb = bv[ib].pdf;
+                    if (!(f[0] > 0 || f[1] > 0 || f[2] > 0)) {
+                        if (nn < 64) { for (int c = 0; c < 3; ++c) Ln[nn][c] = L[c]; ++nn; }
+                        continue;
+                    }
+                    if (sna < 0) sna = hit_alts(R, xo, wl, h->id, exo, ed_sh, sa, &W->unbounded);
+                    int lit = 0, unlit = 0;
+                    for (int i = 0; i < sna; ++i) { if (sa[i].id == e) lit = 1; else unlit = 1; }
+                    if (unlit && nn < 64) { for (int c = 0; c < 3; ++c) Ln[nn][c] = L[c]; ++nn; }
+                    if (lit && nn < 64) {
+                        double pl = dist * dist / (R->A * ce);
+                        double w = pl * pl / (pl * pl + pb * pb);
+                        for (int c = 0; c < 3; ++c) Ln[nn][c] = L[c] + beta[c] * w * S->Le[3*e+c] * f[c] / pl;
+                        ++nn;
+                    }
+                }
+            }
+            if (nn >= 64) W->unbounded = 1;
+        } else {
+            for (int c = 0; c < 3; ++c) Ln[0][c] = L[c];
+            nn = 1;
+        }
+        /* BRDF sample: every lobe, frame and evaluation alternative */
+        double u[4];
+        philox_words(W->pid, W->s, lane, R->request_id, R->seed, u);
+        double kdm = 0, ksm = 0;
+        const double mm = R->mm[h->id];
+        for (int c = 0; c < 3; ++c) {
+            kdm += R->ma[3*h->id+c] * (1.0 - mm);
+            ksm += 0.04 * (1.0 - mm) + R->ma[3*h->id+c] * mm;
+        }
+        double Pd = kdm / (kdm + ksm);
+        if (Pd < 0.1) Pd = 0.1;
+        if (Pd > 0.9) Pd = 0.9;
+        if (!spec) Pd = 1.0;
+        const int glossy_nom = !(u[2] < Pd);
+        const int n_lobe = fabs(u[2] - Pd) < 1e-5 ? 2 : 1;
+        const double s_nom = n[2] >= OR_ONB_BRANCH ? 1.0 : -1.0;
+        const int n_frame = famb ? 2 : 1;
+        for (int in_ = 0; in_ < nn; ++in_) {
+            for (int il = 0; il < n_lobe; ++il) {
+                const int glossy = il == 0 ? glossy_nom : !glossy_nom;
+                /* a reflection keeps the incoming direction's uncertainty */
+                const double ed_i = (glossy ? ed : 0.0) + 8.0 * OR_U32;
+                for (int iff = 0; iff < n_frame; ++iff) {
+                    double tb[3], bb[3], wi[3], hh[3];
+                    if (iff == 0) onb(n, tb, bb); else onb_forced(n, -s_nom, tb, bb);
+                    if (!glossy) {
+                        double rad = sqrt(u[0]), phi = 2.0 * OPI * u[1];
+                        to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u[0]), wi);
+                    } else {
+                        const double al = (double)R->ms[h->id] * (double)R->ms[h->id], a2 = al * al;
+                        double cos2 = (1.0 - u[0]) / (1.0 + (a2 - 1.0) * u[0]);
+                        double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2)), phi = 2.0 * OPI * u[1];
+                        to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, hh);
+                        double c = dot3(wo, hh);
+                        for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * hh[a] - wo[a];
+                    }
+                    bvar bv[OMAXBV];
+                    const int nb = brdf_alts(R, h->id, n, wo, wi, glossy ? hh : NULL, spec, ed, ed_i, bv);
+                    for (int ib = 0; ib < nb; ++ib) {
+                        if (bv[ib].pdf <= 0.0) { rw_leaf(W, Ln[in_]); continue; }
+                        double b2[3];
+                        for (int c = 0; c < 3; ++c) b2[c] = beta[c] * (bv[ib].f[c] / bv[ib].pdf);
+                        path_range(W, xo, wi, h->id, bv[ib].pdf, b2, depth + 1, Ln[in_], exo, ed_i);
+                        if (W->unbounded) return;
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* Every value the path radiance may take from the ray (o, d) on (see the
+ * header of this section), each branch adding to L in the nominal order;
+ * beta and pdf_prev as in path_radiance; eo, ed the uncertainty of the
+ * ray's origin and direction. */
+static void path_range(rwalk* W, const double o[3], const double d[3], int skip, double pdf_prev,
+                       const double beta[3], int depth, const double L[3], double eo, double ed)
+{
+    const refine_job* R = W->R;
+    const oscene* S = R->S;
+    if (W->unbounded) return;
+    if (++W->segments > OR_RANGE_BUDGET) { W->unbounded = 1; return; }
+    oalt al[OMAXALT];
+    const int na = hit_alts(R, o, d, skip, eo, ed, al, &W->unbounded);
+    if (W->unbounded) return;
+    const double dl = norm3(d);
+    for (int i = 0; i < na; ++i) {
+        const oalt* h = &al[i];
+        double Lt[3] = {L[0], L[1], L[2]};
+        if (h->id < 0) {
+            double Le[3];
+            env_lookup(S, d, Le);
+            for (int c = 0; c < 3; ++c) Lt[c] += beta[c] * Le[c];
+            rw_leaf(W, Lt);
+            continue;
+        }
+        /* the hit point's uncertainty on the surface */
+        const otri* tr = &S->tri[h->id];
+        const double cs = fabs(dot3(d, tr->ng)) / (dl * tr->area2);
+        const double ex = (eo + h->t * ed) / fmax(cs, 1e-3) + 4.0 * OR_U32 * (W->mag + h->t);
+        if (is_emitter(S, h->id)) {
+            if (h->front) {
+                double w = 1.0;
+                if (R->mis && R->n_emit > 0) {
+                    double ce = fabs(dot3(d, tr->ng)) / tr->area2;
+                    double pl = h->t * h->t / (R->A * ce);
+                    w = pdf_prev * pdf_prev / (pdf_prev * pdf_prev + pl * pl);
+                }
+                for (int c = 0; c < 3; ++c) Lt[c] += beta[c] * w * S->Le[3*h->id+c];
+            }
+            rw_leaf(W, Lt);
+            continue;
+        }
+        if ((double)R->ms[h->id] > R->sigma_c) {
+            double p[3] = {o[0] + h->t * d[0], o[1] + h->t * d[1], o[2] + h->t * d[2]};
+            if (S->vox) {
+                double ext = 0.0;
+                for (int a = 0; a < 3; ++a) ext = fmax(ext, S->shi[a] - S->slo[a]);
+                double vl[3], vh[3], A[3], B[3];
+                voxel_range_w(S, p, fmax(1e-3, 2.0 * ex * S->vox_r / ext), vl, vh);
+                for (int c = 0; c < 3; ++c) { A[c] = Lt[c] + beta[c] * vl[c]; B[c] = Lt[c] + beta[c] * vh[c]; }
+                rw_leaf(W, A);
+                rw_leaf(W, B);
+            } else {
+                double C[3];
+                cache_at(S, h->id, p, C);
+                for (int c = 0; c < 3; ++c) Lt[c] += beta[c] * C[c];
+                rw_leaf(W, Lt);
+            }
+            continue;
+        }
+        if (depth > R->max_depth) { rw_leaf(W, Lt); continue; }
+        if (ex > 1e-4 * S->L) { W->unbounded = 1; return; }
+        /* the facing FP64 gives this triangle, or the other one (grazing) */
+        const int nominal_facing = h->front == (dot3(d, tr->ng) < 0.0);
+        vertex_range(W, o, d, h, beta, depth, Lt, nominal_facing, ex, ed);
+        if (W->unbounded) return;
+    }
+}
+
+/* Range of one sample's six values (see the section header): the
+ * emitter sample at the query point, then the lobe sample's path; lo / hi
+ * receive the extremes, or [0, inf] when unbounded (returns 1 then). */
+static int sample_range(const refine_job* R, const double o[3], const double n[3], const double wo[3],
+                        const double tb[3], const double bb[3], int32_t skip, uint32_t pid,
+                        uint32_t s, uint32_t lobe, double a2, double g1o, double mu_o,
+                        double lo[6], double hi[6])
+{
+    const oscene* S = R->S;
+    rwalk W;
+    memset(&W, 0, sizeof(W));
+    W.R = R; W.pid = pid; W.s = s; W.lobe = lobe;
+    for (int a = 0; a < 3; ++a) W.mag = fmax(W.mag, fmax(fabs(S->slo[a]), fabs(S->shi[a])));
+    const double eo = 4.0 * OR_U32 * W.mag, ed = 8.0 * OR_U32;
+    /* every six-value partial sum the emitter sample at x may leave */
+    double N6[64][6];
+    int nn = 0;
+    if (R->mis && R->n_emit > 0) {
+        double u[4];
+        philox_words(pid, s, lobe | 0x100u, R->request_id, R->seed, u);
+        int ks[3];
+        const int nk = emitter_alts(R, u[0], ks);
+        for (int ik = 0; ik < nk; ++ik) {
+            double y[3], wl[3];
+            const int e = emitter_point(R, ks[ik], u, y);
+            sub3(y, o, wl);
+            double dist = norm3(wl);
+            for (int a = 0; a < 3; ++a) wl[a] /= dist;
+            const double ed_sh = eo / dist + 4.0 * OR_U32;
+            const double wz = fmax(1e-5, 2.0 * ed_sh);
+            const otri* te = &S->tri[e];
+            double ce = -dot3(wl, te->ng) / te->area2;
+            double mu_i = dot3(n, wl);
+            /* the zero contribution, wherever a decision may zero it */
+            const int maybe_zero = !(ce > 0 && mu_i > 0) || fabs(ce) < wz || fabs(mu_i) < wz;
+            if (maybe_zero && nn < 64) { memset(N6[nn], 0, sizeof(N6[nn])); ++nn; }
+            const double mu_e = mu_i > 0 ? mu_i : (mu_i < 0 ? -mu_i : 1e-300);
+            if (!(ce > 0) || !(mu_i > 0 || fabs(mu_i) < wz)) continue;
+            double g0s[3], g1s[3], pbs[3];
+            int ng = 0;
+            if (lobe == 0) { g0s[0] = mu_e / OPI; g1s[0] = 0; pbs[0] = mu_e / OPI; ng = 1; }
+            else {
+                double h[3] = {wl[0] + wo[0], wl[1] + wo[1], wl[2] + wo[2]};
+                normalize3(h);
+                double ch = dot3(n, h), c = dot3(wo, h);
+                const int c_ok = ch > 0 && c > 0, c_near = fabs(c) < wz && ch > 0;
+                if ((!c_ok || c_near) && nn < 64) { memset(N6[nn], 0, sizeof(N6[nn])); ++nn; }
+                if (!c_ok && !c_near) continue;
+                const double cc = c > 0 ? c : (c < 0 ? -c : 1e-300);
+                const double tilt = fmax(OR_TILT, ed + ed_sh);
+                double cr[3];
+                cross3(n, h, cr);
+                double Ds[3];
+                int nD = 1;
+                Ds[0] = ggx_D(ch, a2);
+                if (ggx_log_slope(ch, norm3(cr), a2) * tilt > 1e-4) {
+                    double th = atan2(norm3(cr), ch);
+                    Ds[nD++] = ggx_D_theta(th > tilt ? th - tilt : 0.0, a2);
+                    Ds[nD++] = ggx_D_theta(th + tilt, a2);
+                }
+                for (int iD = 0; iD < nD; ++iD) {
+                    double D = Ds[iD], G = smith_g1(mu_e, a2) * g1o;
+                    double F1 = pow(1.0 - cc, 5.0);
+                    g0s[ng] = (1.0 - F1) * D * G / (4.0 * mu_o);
+                    g1s[ng] = F1 * D * G / (4.0 * mu_o);
+                    pbs[ng] = D * ch / (4.0 * cc);
+                    ++ng;
+                }
+            }
+            oalt sa[OMAXALT];
+            int sna = -1;
+            for (int ig = 0; ig < ng; ++ig) {
+                if (!(g0s[ig] > 0 || g1s[ig] > 0)) {
+                    if (nn < 64) { memset(N6[nn], 0, sizeof(N6[nn])); ++nn; }
+                    continue;
+                }
+                if (sna < 0) sna = hit_alts(R, o, wl, skip, eo, ed_sh, sa, &W.unbounded);
+                int lit = 0, unlit = 0;
+                for (int i = 0; i < sna; ++i) { if (sa[i].id == e) lit = 1; else unlit = 1; }
+                if (unlit && nn < 64) { memset(N6[nn], 0, sizeof(N6[nn])); ++nn; }
+                if (lit && nn < 64) {
+                    double pl = dist * dist / (R->A * ce);
+                    double w = pl * pl / (pl * pl + pbs[ig] * pbs[ig]);
+                    for (int c = 0; c < 3; ++c) {
+                        N6[nn][c] = 0.0 + w * S->Le[3*e+c] * g0s[ig] / pl;
+                        N6[nn][3+c] = 0.0 + w * S->Le[3*e+c] * g1s[ig] / pl;
+                    }
+                    ++nn;
+                }
+            }
+        }
+        if (nn >= 64) W.unbounded = 1;
+    } else {
+        memset(N6[0], 0, sizeof(N6[0]));
+        nn = 1;
+    }
+    /* the lobe sample at x, as in the bake */
+    double u[4];
+    philox_words(pid, s, lobe, R->request_id, R->seed, u);
+    double wi[3], W0 = 1.0, W1 = 0.0, pb = 0.0;
+    int can_zero = 0, can_go = 1;
+    if (lobe == 0) {
+        double rad = sqrt(u[0]), phi = 2.0 * OPI * u[1];
+        to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u[0]), wi);
+        pb = sqrt(1.0 - u[0]) / OPI;
+    } else {
+        double cos2 = (1.0 - u[0]) / (1.0 + (a2 - 1.0) * u[0]);
+        double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2)), phi = 2.0 * OPI * u[1];
+        double h[3];
+        to_world(tb, bb, n, sh * cos(phi), sh * sin(phi), ch, h);
+        double c = dot3(wo, h);
+        for (int a = 0; a < 3; ++a) wi[a] = 2.0 * c * h[a] - wo[a];
+        double mu_i = dot3(n, wi);
+        const int valid = mu_i > 0.0 && c > 0.0;
+        const int near = fabs(mu_i) < 1e-5 || fabs(c) < 1e-5;
+        can_zero = !valid || near;
+        can_go = valid || near;
+        const double mu_e = mu_i > 0 ? mu_i : (mu_i < 0 ? -mu_i : 1e-300);
+        const double cc = c > 0 ? c : (c < 0 ? -c : 1e-300);
+        double G = smith_g1(mu_e, a2) * g1o, w = G * cc / (mu_o * ch);
+        double F1 = pow(1.0 - cc, 5.0);
+        W0 = (1.0 - F1) * w;
+        W1 = F1 * w;
+        pb = ggx_D(ch, a2) * ch / (4.0 * cc);
+    }
+    double Lmin[3] = {0, 0, 0}, Lmax[3] = {0, 0, 0};
+    if (can_go) {
+        for (int c = 0; c < 3; ++c) { W.Lmin[c] = INFINITY; W.Lmax[c] = -INFINITY; }
+        const double one[3] = {1, 1, 1}, zero3[3] = {0, 0, 0};
+        path_range(&W, o, wi, skip, pb, one, 1, zero3, eo, ed);
+        for (int c = 0; c < 3; ++c) { Lmin[c] = W.Lmin[c]; Lmax[c] = W.Lmax[c]; }
+    }
+    if (W.unbounded) {
+        for (int i = 0; i < 6; ++i) { lo[i] = 0.0; hi[i] = INFINITY; }
+        return 1;
+    }
+    for (int i = 0; i < 6; ++i) { lo[i] = INFINITY; hi[i] = -INFINITY; }
+    for (int k = 0; k < nn; ++k) {
+        for (int c = 0; c < 3; ++c) {
+            double v0[3], v1[3];
+            int m = 0;
+            if (can_go) {
+                v0[m] = N6[k][c] + W0 * Lmin[c]; v1[m] = N6[k][3+c] + W1 * Lmin[c]; ++m;
+                v0[m] = N6[k][c] + W0 * Lmax[c]; v1[m] = N6[k][3+c] + W1 * Lmax[c]; ++m;
+            }
+            if (can_zero) { v0[m] = N6[k][c]; v1[m] = N6[k][3+c]; ++m; }
+            for (int j = 0; j < m; ++j) {
+                lo[c] = fmin(lo[c], v0[j]);   hi[c] = fmax(hi[c], v0[j]);
+                lo[3+c] = fmin(lo[3+c], v1[j]); hi[3+c] = fmax(hi[3+c], v1[j]);
+            }
+        }
+    }
+    return 0;
+}
+
 static void refine_point(refine_job* R, int64_t p)
 {
     const oscene* S = R->S;
@@ -1382,6 +1956,13 @@ static void refine_point(refine_job* R, int64_t p)
                 for (int i = 0; i < 6; ++i) ps[i] = c6[i];
             }
             if (R->amb) R->amb[(size_t)(p * (K + 1) + lobe) * R->smax + s] = (uint8_t)amb;
+            if (R->ps_lo) {
+                const size_t at = (size_t)(p * (K + 1) + lobe) * R->smax + s;
+                int unb = sample_range(R, o, n, wo, tb, bb, skip, pid, (uint32_t)s, (uint32_t)lobe,
+                                       a2, g1o, mu_o, R->ps_lo + 6 * at, R->ps_hi + 6 * at);
+                if (lobe == 0) for (int c = 3; c < 6; ++c) { R->ps_lo[6*at+c] = 0.0; R->ps_hi[6*at+c] = 0.0; }
+                if (R->unb) R->unb[at] = (uint8_t)unb;
+            }
         }
         if (lobe == 0) for (int c = 0; c < 3; ++c) out[c] = acc[c] / Sn;
         else for (int c = 0; c < 3; ++c) {
@@ -1405,12 +1986,16 @@ static void* refine_worker(void* arg)
 /* Stage-3 bake.  mat_a [T,3], mat_sigma [T], mat_m [T] per triangle.
  * Outputs as oracle_bake (nominal only); per_sample (nullable) gets every
  * sample's 6 values (L_d uses the first 3), amb (nullable) 1 for samples
- * whose path takes a decision within rounding of a threshold. */
+ * whose path takes a decision within rounding of a threshold.  With
+ * per_sample and eta > 0, ps_lo / ps_hi (nullable) receive each sample's
+ * range over those decisions (sample_range) and unb (nullable) 1 where the
+ * range is [0, inf]. */
 int oracle_refine(const oscene* S, const float* mat_a, const float* mat_sigma, const float* mat_m,
                   const float* qx, const float* qn, const float* qwo, const int32_t* qtri, int64_t N,
                   uint64_t seed, uint32_t request_id, uint32_t point_base, int spp_d, int spp_s,
                   int K, const double* sigma, double sigma_c, int max_depth, int mis, double eta,
-                  int nthreads, double* out, double* per_sample, uint8_t* amb)
+                  int nthreads, double* out, double* per_sample, uint8_t* amb,
+                  double* ps_lo, double* ps_hi, uint8_t* unb)
 {
     refine_job R;
     memset(&R, 0, sizeof(R));
@@ -1431,6 +2016,9 @@ int oracle_refine(const oscene* S, const float* mat_a, const float* mat_sigma, c
     R.spp_d = spp_d; R.spp_s = spp_s; R.K = K; R.sigma = sigma;
     R.sigma_c = sigma_c; R.max_depth = max_depth; R.mis = mis; R.eta = eta;
     R.out = out; R.per_sample = per_sample; R.amb = amb;
+    R.ps_lo = (eta > 0 && per_sample) ? ps_lo : NULL;
+    R.ps_hi = R.ps_lo ? ps_hi : NULL;
+    R.unb = R.ps_lo ? unb : NULL;
     R.smax = spp_d > spp_s ? spp_d : spp_s;
     R.next = 0;
     if (nthreads < 1) nthreads = 1;

@@ -194,3 +194,58 @@ def test_vertex_brdf_directional_albedo():
         ks = 0.04 * (1 - mt) + alb * mt
         ref = kd + ks * A + B
         assert np.allclose(tot, ref, rtol=2e-5, atol=0), (mu_o, sg, mt, tot, ref)
+
+
+def _perturb(q, seed):
+    """The query records moved by 1-3 float32 ulps per component."""
+    rng = np.random.default_rng(seed)
+    out = dict(q)
+    for k in ("x", "n", "wo"):
+        v = np.array(q[k], np.float32)
+        for _ in range(3):
+            step = rng.integers(-1, 2, v.shape)
+            v = np.where(step > 0, np.nextafter(v, np.float32(np.inf)),
+                         np.where(step < 0, np.nextafter(v, np.float32(-np.inf)), v)).astype(np.float32)
+        out[k] = v
+    return out
+
+
+def test_sample_ranges_bound_the_nominal_and_perturbed_paths():
+    """The per-sample ranges (every decision a float32 path's accumulated
+    rounding may flip) contain the nominal value and the values of the same
+    samples computed from query records moved by a few float32 ulps, whose
+    FP64 paths take some of those decisions the other way and drift
+    continuously.  Room with random per-triangle materials (many glossy
+    vertices, max_depth 8): few samples become unbounded.  Glossy Cornell
+    walls with paths up to 40 vertices: the rounding of a hit point grows by
+    about 1/cos per bounce, so a sizeable share of the deep samples lose
+    track of their FP64 twin and are unbounded."""
+    from workloads import procedural_room
+    rng = np.random.default_rng(8)
+    cases = []
+    m = procedural_room(1)
+    T = m.T
+    cases.append((m, rng.uniform(0, 1, (T, 3)).astype(np.float32),
+                  rng.uniform(0.02, 1.0, T).astype(np.float32),
+                  rng.uniform(0, 1, T).astype(np.float32), surface_queries(m, 96, seed=6), 8, 8, 0.03))
+    m2 = cornell_box()
+    T2 = m2.T
+    cases.append((m2, np.full((T2, 3), 0.8, np.float32), np.full(T2, 0.3, np.float32),
+                  np.zeros(T2, np.float32), surface_queries(m2, 48, seed=22), 4, 40, 0.4))
+    moved = 0
+    for m, a, r, mt, q, spp, depth, max_unb in cases:
+        S = O.OracleScene.from_mesh(m)
+        o = S.refine(q, SIGMA, spp, spp, a, r, mt, max_depth=depth, eta=1e-5, per_sample=True,
+                     bounds=True, seed=3, request_id=1)
+        ps, lo, hi, unb = o["per_sample"], o["lo"], o["hi"], o["unbounded"]
+        assert np.all(lo <= ps) and np.all(ps <= hi)
+        assert unb.mean() <= max_unb, unb.mean()
+        col = np.mean(np.abs(ps), axis=(0, 2), keepdims=True)
+        tol = 1e-4 * np.maximum(np.abs(ps), col)
+        for k in range(4):
+            p = S.refine(_perturb(q, 100 + k), SIGMA, spp, spp, a, r, mt, max_depth=depth,
+                         per_sample=True, seed=3, request_id=1)["per_sample"]
+            out = ((p < lo - tol) | (p > hi + tol)) & ~unb[..., None]
+            assert not out.any(), np.argwhere(out)[:5]
+            moved += int(np.sum((np.abs(p - ps) > tol) & ~unb[..., None]))
+    assert moved > 0            # some bounded samples did take another branch
