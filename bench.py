@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--points", type=int, default=None,
                     help="override the query count (small profiling cases)")
     ap.add_argument("--spp", type=int, default=None, help="override both sample counts")
-    ap.add_argument("--serve-requests", type=int, default=48,
+    ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests in the serving trace (0 = skip the serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, req/s")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0, help="HBM admission budget")
@@ -472,13 +472,16 @@ def run_render(args, wl, world, rank, local):
 # ---------------------------------------------------------------- serving
 def run_serving(args, F, dev):
     """Poisson trace of bake and render requests over four resident scenes
-    (Cornell box, room, two-room and four-room floors), served with
-    continuous batching, then the same trace one request at a time."""
+    (the 36-triangle Cornell box, the 175,926-triangle room, two rooms of the
+    floor at 1,022,732 triangles and the 2,045,464-triangle floor), served
+    with continuous batching, then the same trace one request at a time,
+    then the trace slowed to a sustainable rate (utilisation 0.7 of the
+    serial service time)."""
     import torch
     from workloads import (building_floor, cornell_box, material_params, pinhole_views,
                            procedural_room, shading_tables)
     rng = np.random.default_rng(6)
-    meshes = [cornell_box(closed=True), procedural_room(1), building_floor(5, rooms=2),
+    meshes = [cornell_box(), procedural_room(1), building_floor(5, rooms=2),
               building_floor(5, rooms=4)]
     scenes = [F.Scene.from_mesh(m) for m in meshes]
     # query pools: pinhole first hits of each scene, kept in pinned host memory

@@ -372,8 +372,11 @@ fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1,
  * FIPT_NOALLOC_RENDER_MAX_BLOCKS * 256 = 16,777,216 points; larger N returns
  * FIPT_ERR_INVALID_ARG without launching.  Allocates nothing: the first call
  * on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current), so make that first call before any stream
- * capture.  Every call on a device shares the one array: calls that overlap
+ * with that device current) and keeps it; later calls check with
+ * cudaPointerGetAttributes that the driver still knows that address as
+ * memory of the device, and look it up again if not (after a
+ * cudaDeviceReset, say).  Make the first call on each device before any
+ * stream capture.  Every call on a device shares the one array: calls that overlap
  * on the GPU (different streams, no ordering between them) race and may
  * return a wrong loss; serialise them on one stream.  Each call overwrites
  * every partial it reads, so no clearing is needed between calls. */
@@ -512,6 +515,16 @@ fipt_status fipt_server_times(fipt_server* srv, uint64_t ticket, double* t_submi
 /* Forgets a finished request. */
 fipt_status fipt_server_release(fipt_server* srv, uint64_t ticket);
 fipt_status fipt_server_get_stats(fipt_server* srv, fipt_server_stats* out);
+/* Failure handling.  When a batch fails to launch, or its device work
+ * fails, the server starts no new work and every unfinished request ends
+ * with that error (its *result) -- each one only after none of its input
+ * copy, kernels or output copies is still queued, so a caller whose wait
+ * returns may free or reuse the request's host buffers at once.  Requests
+ * whose last batch ran before the failing one keep their own results.
+ * Test hook (the paper has no counterpart): makes the launch of the batch
+ * after the next after_batches ones fail with FIPT_ERR_CUDA instead of
+ * running, without touching the device. */
+fipt_status fipt_server_inject_launch_failure(fipt_server* srv, int64_t after_batches);
 /* Cancels requests not yet admitted (result FIPT_ERR_NOT_FOUND), drains
  * admitted work, joins the scheduler and frees the arena. */
 fipt_status fipt_server_destroy(fipt_server* srv);
@@ -530,6 +543,14 @@ fipt_status fipt_arena_destroy(fipt_arena* a);
  * ctr [n,4] u32, key [n,2] u32 -> out [n,4] u32. */
 fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n,
                               uint32_t* out, fipt_stream stream);
+/* The emitter sampler's split of a sample index i into (triangle i / n,
+ * sample i mod n) divides by the invariant n with one multiply-high
+ * (Granlund and Montgomery 1994); the paper has no counterpart.  out[k] =
+ * i[k] / n by that same routine, on the host (on_device = 0: i and out
+ * HOST arrays, stream ignored) or in a kernel (on_device != 0: DEVICE
+ * arrays on the stream).  n >= 1. */
+fipt_status fipt_debug_divide(uint32_t n, const uint32_t* i, int64_t count, uint32_t* out,
+                              int32_t on_device, fipt_stream stream);
 
 #ifdef __cplusplus
 }

@@ -695,6 +695,11 @@ class Server:
         check(lib().fipt_server_release(self.handle, int(ticket)))
         self._keep.pop(ticket, None)
 
+    def inject_launch_failure(self, after_batches: int = 0):
+        """Test hook: the launch after the next ``after_batches`` batches fails
+        (FIPT_ERR_CUDA) on the host, as a failed kernel launch would."""
+        check(lib().fipt_server_inject_launch_failure(self.handle, int(after_batches)))
+
     def stats(self):
         s = ServerStats()
         check(lib().fipt_server_get_stats(self.handle, ctypes.byref(s)))

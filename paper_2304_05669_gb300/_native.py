@@ -71,6 +71,7 @@ SIGNATURES = {
     "fipt_tri_error_workspace_size": [I64, I64, P],
     "fipt_tri_error": [P, I64, P, P, I64, I64, P, P, P, SZ, P],
     "fipt_debug_philox": [P, P, I64, P, P],
+    "fipt_debug_divide": [ctypes.c_uint32, P, I64, P, I32, P],
     "fipt_scene_set_materials": [P, P, P, P, P],
     "fipt_scene_set_environment": [P, P, I32, I32],
     "fipt_voxel_cache_workspace_size": [I64, P],
@@ -92,6 +93,7 @@ SIGNATURES = {
     "fipt_server_times": [P, U64, P, P, P],
     "fipt_server_release": [P, U64],
     "fipt_server_get_stats": [P, P],
+    "fipt_server_inject_launch_failure": [P, I64],
     "fipt_server_destroy": [P],
     "fipt_arena_create": [SZ, P],
     "fipt_arena_alloc": [P, SZ, P],

@@ -41,6 +41,22 @@ DivN div_by(uint32_t n) {
     return DivN{(uint32_t)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
 }
 
+// i / n for the divisor d was made for (device: one multiply-high).
+__host__ __device__ __forceinline__ uint32_t div_apply(const DivN& d, uint32_t i) {
+#ifdef __CUDA_ARCH__
+    const uint32_t hi = __umulhi(d.m, i);
+#else
+    const uint32_t hi = (uint32_t)(((uint64_t)d.m * i) >> 32);
+#endif
+    return (hi + ((i - hi) >> d.s1)) >> d.s2;
+}
+
+__global__ void k_debug_divide(DivN d, const uint32_t* __restrict__ i, int64_t count,
+                               uint32_t* __restrict__ out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < count) out[k] = div_apply(d, i[k]);
+}
+
 // IDX: uint32_t when T * n < 2^32 (the sample index splits by the
 // multiply-high division above), int64_t otherwise.  A block stages its
 // PTS_THREADS points in shared memory and writes them as float4 (the
@@ -59,8 +75,7 @@ k_emit_points(const float4* __restrict__ tris, const int32_t* __restrict__ inv, 
     if (i < total) {
         IDX t;
         if constexpr (sizeof(IDX) == 4) {
-            const uint32_t i32 = (uint32_t)i, hi = __umulhi(dn.m, i32);
-            t = (hi + ((i32 - hi) >> dn.s1)) >> dn.s2;
+            t = div_apply(dn, (uint32_t)i);
         } else {
             t = (IDX)i / (IDX)n;
         }
@@ -541,4 +556,19 @@ extern "C" fipt_status fipt_scene_set_emission(fipt_scene* s, const float* Le, f
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     FIPT_LAUNCH(k_set_emission, blocks(s->T, 256), 256, 0, st, Le, s->order, s->T, s->shade);
     return rebuild_emitter_table(s, st);
+}
+
+extern "C" fipt_status fipt_debug_divide(uint32_t n, const uint32_t* i, int64_t count, uint32_t* out,
+                                         int32_t on_device, fipt_stream stream) {
+    FIPT_REQUIRE(n >= 1 && count >= 0 && (count == 0 || (i && out)), "bad arguments");
+    const DivN d = div_by(n);
+    if (!on_device) {
+        for (int64_t k = 0; k < count; ++k) out[k] = div_apply(d, i[k]);
+        return FIPT_OK;
+    }
+    if (count == 0) return FIPT_OK;
+    FIPT_LAUNCH(k_debug_divide, (unsigned)((count + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream),
+                d, i, count, out);
+    FIPT_LAUNCHED("debug_divide");
+    return FIPT_OK;
 }

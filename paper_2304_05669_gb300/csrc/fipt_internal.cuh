@@ -367,8 +367,14 @@ __device__ __forceinline__ float3 voxel_lookup(const SceneView& sc, float px, fl
 }
 
 // ---------------------------------------------------------------- traversal
+// Traversal stack entries per thread.  k_trace and k_camera keep the stack
+// in shared memory (a [depth][thread] column per block); the bake (k_bake,
+// k_bake_batch) and the refinement's traversal keep it in a per-thread
+// local-memory array.  A ray whose stack would overflow drops the far
+// child it could not push (that subtree is not searched) and sets
+// FIPT_DEV_STACK_OVERFLOW in the device status word.
 #ifndef FIPT_STACK_DEPTH
-#define FIPT_STACK_DEPTH 32      // traversal stack entries per thread (shared memory)
+#define FIPT_STACK_DEPTH 32
 #endif
 constexpr int STACK_DEPTH = FIPT_STACK_DEPTH;
 constexpr float FINF = __builtin_huge_valf();

@@ -392,13 +392,24 @@ constexpr int kMaxDevices = 64;
 double* g_noalloc_ptr[kMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
-// Device address of g_noalloc_partials on the current device, looked up once
-// per device (host code only ever sees a host-side stand-in for the symbol).
+// Device address of g_noalloc_partials on the current device (host code
+// only ever sees a host-side stand-in for the symbol).  Looked up on a
+// device's first call and kept; a kept address that the driver no longer
+// knows as memory of this device (the device was reset and its module
+// reloaded elsewhere) is looked up again.
 fipt_status noalloc_partials(double** out) {
     int dev = -1;
     FIPT_CUDA(cudaGetDevice(&dev));
     FIPT_REQUIRE(dev >= 0 && dev < kMaxDevices, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev]) {
+        cudaPointerAttributes at;
+        const cudaError_t e = cudaPointerGetAttributes(&at, g_noalloc_ptr[dev]);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != dev) {
+            (void)cudaGetLastError();      // the query's error is not the caller's
+            g_noalloc_ptr[dev] = nullptr;
+        }
+    }
     if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;
         FIPT_CUDA(cudaGetSymbolAddress(&p, g_noalloc_partials));

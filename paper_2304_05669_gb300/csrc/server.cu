@@ -17,6 +17,9 @@
 //    copied back on the copy stream and its arena space is freed.
 //  * All waits are on the host (event queries with short sleeps, bounded by
 //    the caller's timeouts); no kernel waits on anything.
+//  * Failure.  A launch that fails, or a batch whose device work fails, stops
+//    the server: no new work starts and every unfinished request ends with
+//    that error once none of its copies or kernels is still queued.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -197,6 +200,8 @@ struct fipt_server {
     bool stop = false;
     std::thread worker;
     fipt_status fatal = FIPT_OK;
+    uint64_t fatal_batch = 0;                  // first batch whose work is lost
+    int64_t fail_after = -1;                   // test hook: batches left before a launch failure
     char fatal_msg[256] = "";
 
     void run();
@@ -204,7 +209,8 @@ struct fipt_server {
     void launch_batch();
     void retire(Batch& b);
     void finish_copies();
-    void fail_all(fipt_status s);
+    void drain_after_fatal();
+    void set_fatal(fipt_status st, uint64_t batch, const char* msg);
 };
 
 namespace {
@@ -316,8 +322,14 @@ void fipt_server::launch_batch() {
         int flags = 0;
         for (int c = 0; c < nch; ++c) flags |= (H[c].sc.env ? 1 : 0) | (H[c].sc.vox ? 2 : 0);
         cudaMemcpyAsync(chunk_dev[slot], H, sizeof(BakeChunk) * (size_t)nch, cudaMemcpyHostToDevice, compute);
-        fipt_status st = launch_bake_batch(chunk_dev[slot], nch, warps, status, compute, flags);
-        if (st != FIPT_OK) { fatal = st; snprintf(fatal_msg, sizeof(fatal_msg), "%s", fipt_last_error()); }
+        fipt_status st;
+        if (fail_after == 0) {          // injected by fipt_server_inject_launch_failure
+            st = fipt_set_error(FIPT_ERR_CUDA, "injected launch failure");
+        } else {
+            st = launch_bake_batch(chunk_dev[slot], nch, warps, status, compute, flags);
+        }
+        if (fail_after >= 0) --fail_after;
+        if (st != FIPT_OK) set_fatal(st, next_batch, fipt_last_error());
     }
     for (uint64_t t : involved) {
         Req* q = reqs[t];
@@ -405,17 +417,61 @@ void fipt_server::finish_copies() {
     }
 }
 
-void fipt_server::fail_all(fipt_status s) {
-    for (auto& kv : reqs) {
-        Req* q = kv.second;
-        if (q->state != DONE) {
-            q->result = s;
-            q->state = DONE;
-            q->t_done = now_s();
-        }
+void fipt_server::set_fatal(fipt_status st, uint64_t batch, const char* msg) {
+    if (fatal != FIPT_OK) return;
+    fatal = st;
+    fatal_batch = batch;
+    snprintf(fatal_msg, sizeof(fatal_msg), "%s", msg ? msg : "");
+}
+
+// After a fatal error no new work starts, and every request ends with that
+// error -- but only once nothing of it is still in flight: a request whose
+// input copy, batch or output copy is still queued on the device keeps the
+// caller's host buffers in use until that work has completed (or failed),
+// so it is marked done only then.  Batches before the failing one complete
+// normally and their requests keep their own results.
+void fipt_server::drain_after_fatal() {
+    for (uint64_t t : pending) {
+        Req* q = reqs[t];
+        q->result = fatal;
+        q->state = DONE;
+        q->t_done = now_s();
     }
     pending.clear();
-    active.clear();
+    for (size_t i = 0; i < active.size();) {
+        Req* q = reqs[active[i]];
+        if (cudaEventQuery(q->h2d) == cudaErrorNotReady) { ++i; continue; }
+        q->result = fatal;
+        q->state = DONE;
+        q->t_done = now_s();
+        active.erase(active.begin() + (long)i);
+    }
+    while (!inflight.empty()) {
+        Batch& b = inflight.front();
+        const cudaError_t e = cudaEventQuery(b.done);
+        if (e == cudaErrorNotReady) break;
+        if (e == cudaSuccess && b.seq < fatal_batch) {
+            retire(b);                   // its requests' copies go out as usual
+        } else {
+            for (uint64_t t : b.finishing) {
+                Req* q = reqs[t];
+                q->result = fatal;
+                q->state = DONE;
+                q->t_done = now_s();
+            }
+            cudaEventDestroy(b.done);
+        }
+        inflight.pop_front();
+    }
+    for (size_t i = 0; i < copying.size();) {
+        Req* q = reqs[copying[i]];
+        const cudaError_t e = cudaEventQuery(q->d2h);
+        if (e == cudaErrorNotReady) { ++i; continue; }
+        if (e != cudaSuccess && q->result == FIPT_OK) q->result = fatal;
+        q->state = DONE;
+        q->t_done = now_s();
+        copying.erase(copying.begin() + (long)i);
+    }
     cv_done.notify_all();
 }
 
@@ -424,9 +480,15 @@ void fipt_server::run() {
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
         if (fatal != FIPT_OK) {
-            fail_all(fatal);
-            if (stop) break;
-            cv_work.wait_for(lk, std::chrono::milliseconds(10));
+            drain_after_fatal();
+            if (stop && pending.empty() && active.empty() && inflight.empty() && copying.empty()) break;
+            if (pending.empty() && active.empty() && inflight.empty() && copying.empty())
+                cv_work.wait_for(lk, std::chrono::milliseconds(10));
+            else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(50));
+                lk.lock();
+            }
             continue;
         }
         bool progress = false;
@@ -435,8 +497,9 @@ void fipt_server::run() {
             const cudaError_t e = cudaEventQuery(inflight.front().done);
             if (e == cudaErrorNotReady) break;
             if (e != cudaSuccess) {
-                fatal = FIPT_ERR_CUDA;
-                snprintf(fatal_msg, sizeof(fatal_msg), "batch failed: %s", cudaGetErrorString(e));
+                char m[200];
+                snprintf(m, sizeof(m), "batch failed: %s", cudaGetErrorString(e));
+                set_fatal(FIPT_ERR_CUDA, inflight.front().seq, m);
                 break;
             }
             retire(inflight.front());
@@ -621,6 +684,13 @@ extern "C" fipt_status fipt_server_release(fipt_server* s, uint64_t ticket) {
     cudaEventDestroy(it->second->d2h);
     delete it->second;
     s->reqs.erase(it);
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_server_inject_launch_failure(fipt_server* s, int64_t after_batches) {
+    FIPT_REQUIRE(s && after_batches >= 0, "bad arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fail_after = after_batches;
     return FIPT_OK;
 }
 

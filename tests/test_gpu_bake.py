@@ -164,3 +164,51 @@ def test_bake_grid_sizes(fipt, sigma):
     g = gpu_bake(fipt, fipt.Scene.from_mesh(m), q, 16, 16, seed=8, sigma=sigma)
     ora = O.OracleScene.from_mesh(m).bake(q, sigma, 16, 16, seed=8, eta=ETA_BAKE)
     print(check_bake(g, ora))
+
+
+@pytest.mark.parametrize("wl", ["room", "floor"])
+def test_bench_inputs_sampled(fipt, wl):
+    """The benchmark's own inputs at full size: the scene, the pinhole first
+    hits of its views compacted to the first N hits, and one bake launch at
+    its sample count (room: 24 views 320x208, 2^20 points, 128 spp; floor:
+    16 views 512x512, 2^22 points, 256 spp).  For sampled points the oracle
+    recomputes the camera query of the same pixel (the GPU's hit must be one
+    the oracle accepts, at the same place) and the bake of the GPU's query
+    record with its global Philox index."""
+    from workloads import pinhole_views
+    if wl == "room":
+        m, views, W, H, N, spp = procedural_room(1), 24, 320, 208, 1 << 20, 128
+    else:
+        m, views, W, H, N, spp = building_floor(5), 16, 512, 512, 1 << 22, 256
+    cams = pinhole_views(m, views, seed=2)
+    sc = fipt.Scene.from_mesh(m)
+    qa, valid = sc.camera_queries(torch.from_numpy(cams).cuda(), W, H)
+    q, pix, n = fipt.compact_queries(qa, valid, N)
+    assert int(n.item()) == N
+    Ld, Ls0, Ls1 = fipt.bake(sc, q, SIGMA, spp, spp, seed=0, request_id=0)
+    fipt.context().sync_status()
+    g = bake_flat(Ld.cpu().numpy(), Ls0.cpu().numpy(), Ls1.cpu().numpy())
+    assert np.all(np.isfinite(g))
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(N, 32, replace=False))
+    idx[0], idx[-1] = 0, N - 1
+    qh = q[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ph = pix[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.int64)
+    S = O.OracleScene.from_mesh(m)
+    cq = S.camera_queries(cams, W, H, ph, eta=1e-6)
+    tri_g = qh[:, 9].copy().view(np.int32)
+    scale = float(np.abs(m.V).max())
+    for j in range(len(idx)):
+        ok = tri_g[j] == cq["tri"][j] or tri_g[j] in cq["cand_id"][j][:max(cq["n_cand"][j], 0)]
+        assert ok, (j, tri_g[j], cq["tri"][j], cq["cand_id"][j][:4])
+        if tri_g[j] == cq["tri"][j]:
+            assert np.max(np.abs(qh[j, 0:3] - cq["x"][j])) <= 1e-5 * scale
+            assert np.max(np.abs(qh[j, 3:6] - cq["n"][j])) <= 1e-5
+    flat = np.zeros((len(idx), 3 + 6 * len(SIGMA)))
+    lo, hi = np.zeros_like(flat), np.zeros_like(flat)
+    namb = np.zeros(len(idx), np.int64)
+    for j, i in enumerate(idx):
+        one = {"x": qh[j:j + 1, 0:3], "n": qh[j:j + 1, 3:6], "wo": qh[j:j + 1, 6:9], "tri": tri_g[j:j + 1]}
+        r = S.bake(one, SIGMA, spp, spp, seed=0, request_id=0, point_base=int(i), eta=ETA_BAKE)
+        flat[j], lo[j], hi[j], namb[j] = r["flat"][0], r["lo"][0], r["hi"][0], r["n_amb"][0]
+    print(check_bake(g[idx], {"flat": flat, "lo": lo, "hi": hi, "n_amb": namb}))

@@ -26,10 +26,10 @@ def cu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("mesh", ["cornell", "room"])
-def test_points_match_oracle(fipt, mesh):
+@pytest.mark.parametrize("mesh,n", [("cornell", 100), ("room", 3), ("cornell", 1), ("cornell", 2),
+                                    ("cornell", 7), ("cornell", 64), ("cornell", 1000)])
+def test_points_match_oracle(fipt, mesh, n):
     m = cornell_box() if mesh == "cornell" else procedural_room(1)
-    n = 100 if mesh == "cornell" else 3
     sc = fipt.Scene.from_mesh(m)
     g = sc.emitter_points(n, seed=11, request_id=2).cpu().numpy().astype(np.float64)
     o = O.OracleScene.from_mesh(m).emitter_points(n, seed=11, request_id=2)

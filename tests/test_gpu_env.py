@@ -79,7 +79,7 @@ def test_refinement_sees_the_sky(fipt):
     fipt.context().sync_status()
     S = O.OracleScene.from_mesh(m)
     S.set_environment(env)
-    ora = S.refine(q, SIGMA, 8, 8, a, r, mt, seed=2, eta=1e-5, per_sample=True)
+    ora = S.refine(q, SIGMA, 8, 8, a, r, mt, seed=2, eta=1e-5, per_sample=True, bounds=True)
     g = {"Ld": Ld.cpu().numpy(), "Ls0": Ls0.cpu().numpy(), "Ls1": Ls1.cpu().numpy(),
          "ps": ps.cpu().numpy().astype(np.float64)}
-    print(check(g, ora, 0.95, 0.5))
+    print(check(g, ora, 8, 0.05))

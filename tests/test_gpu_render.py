@@ -210,3 +210,25 @@ def test_autograd_backward_twice_and_without_grad(fipt):
     with torch.no_grad():
         l2 = fipt.factorized_render_loss(a, r, m, (t[0], t[1], t[2]), t[3], GRID)
     assert abs(l2.item() - loss.item()) <= 1e-6 * abs(loss.item())
+
+
+def test_render_fwd_grad_full_size(fipt):
+    """The training step's fused pass (forward, loss and gradient in one
+    kernel) and its upstream-gradient scale over all 6,389,760 pixels of the
+    differentiation configuration, element by element against the oracle,
+    with the emitter mask, and then scaled by an upstream gradient of 0.75."""
+    N = 24 * 640 * 416
+    Ld, Ls0, Ls1, mp, Lgt, mask = inputs(N, 31)
+    t = cu(Ld, Ls0, Ls1, mp["albedo"], mp["rough"], mp["metal"], Lgt, mask)
+    Lr, loss, grads = fipt.render_fwd_grad(t[0], t[1], t[2], GRID, t[3], t[4], t[5], t[6], t[7])
+    fipt.context().sync_status()
+    Lr_o, loss_o = O.render_forward(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"], Lgt, mask)
+    close(Lr.cpu().numpy(), Lr_o)
+    assert abs(loss.item() - loss_o) <= REL * abs(loss_o)
+    del Lr_o, Lr
+    refs = O.render_grad(Ld, Ls0, Ls1, GRID, mp["albedo"], mp["rough"], mp["metal"], Lgt, mask)
+    for got, ref in zip(grads, refs):
+        close(got.cpu().numpy(), ref)
+    fipt.render_grad_scale(grads, torch.full((1,), 0.75, dtype=torch.float64, device="cuda"))
+    for got, ref in zip(grads, refs):
+        close(got.cpu().numpy(), 0.75 * ref)

@@ -199,7 +199,7 @@ def test_refine_reads_voxel_cache(fipt):
     fipt.context().sync_status()
     S = O.OracleScene.from_mesh(m)
     S.set_voxel_cache(S.voxel_pool(qp["x"], L, 32))
-    ora = S.refine(q, SIGMA, 8, 8, a, r, mt, seed=4, eta=1e-5, per_sample=True)
+    ora = S.refine(q, SIGMA, 8, 8, a, r, mt, seed=4, eta=1e-5, per_sample=True, bounds=True)
     g = {"Ld": Ld.cpu().numpy(), "Ls0": Ls0.cpu().numpy(), "Ls1": Ls1.cpu().numpy(),
          "ps": ps.cpu().numpy().astype(np.float64)}
-    print(check(g, ora, 0.9, 0.3))
+    print(check(g, ora, 8, 0.05))
