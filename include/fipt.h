@@ -439,10 +439,12 @@ fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* 
  * fipt_server_create allocates one device arena of hbm_budget bytes (the
  * admission budget), two streams, and starts a host scheduler thread.
  * Requests are admitted in arrival order as arena space frees up; each
- * batch takes chunks of up to chunk_points points round-robin from every
- * admitted bake request (any scene) until max_batch_rays rays and runs them
- * in ONE kernel launch, together with the render requests admitted so far;
- * up to two batches are in flight, so later arrivals overlap earlier work.
+ * batch takes chunks of up to chunk_points points from the admitted bake
+ * requests (any scene) until max_batch_rays rays -- the oldest request
+ * first, up to a quarter of the batch, then the requests with the least
+ * remaining work -- and runs them in ONE kernel launch, together with the
+ * render requests admitted so far; up to three batches are in flight, so
+ * later arrivals overlap earlier work.
  * A chunk keeps the request-local Philox counters (point_base = its offset
  * in the request), so every result is bit-identical to a standalone
  * fipt_bake / fipt_render_fwd / fipt_render_bwd of the same request.

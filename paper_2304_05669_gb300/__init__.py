@@ -606,7 +606,7 @@ class Server:
 
     BAKE, RENDER = 0, 1
 
-    def __init__(self, hbm_budget: int, max_batch_rays: int = 1 << 28, chunk_points: int = 65536,
+    def __init__(self, hbm_budget: int, max_batch_rays: int = 1 << 26, chunk_points: int = 16384,
                  ctx: Context | None = None):
         self.ctx = ctx or context()
         h = ctypes.c_void_p()

@@ -6,12 +6,13 @@
 //    the arena; one larger than the whole budget completes at once with
 //    FIPT_ERR_BUDGET.  Inputs are copied in on a copy stream.
 //  * Continuous batching.  Each batch takes chunks of up to `chunk_points`
-//    points round-robin from every admitted bake request (any scene) until
-//    `max_batch_rays` rays, and runs them in one launch of the batched bake
-//    kernel; render requests run their forward/backward kernels in the same
-//    batch.  Up to two batches are in flight, so a request that arrives
-//    while others run joins the next batch, and its work overlaps theirs on
-//    the device.  Chunks keep request-local Philox counters, so a result is
+//    points from the admitted bake requests (any scene) until
+//    `max_batch_rays` rays -- the oldest request first, up to a quarter of
+//    the batch, then the requests with the least remaining work -- and runs
+//    them in one launch of the batched bake kernel; render requests run
+//    their forward/backward kernels in the same batch.  Up to three batches
+//    are in flight, so a request that arrives while others run joins the
+//    next batch, and its work overlaps theirs on the device.  Chunks keep request-local Philox counters, so a result is
 //    identical alone and in any mix.
 //  * Completion.  When a request's last chunk has run, its outputs are
 //    copied back on the copy stream and its arena space is freed.
@@ -42,7 +43,7 @@ double now_s() {
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kMaxChunks = 8192;   // descriptors per batch
-constexpr int kSlots = 2;          // batches in flight
+constexpr int kSlots = 3;          // batches in flight
 
 }  // namespace
 
@@ -281,17 +282,33 @@ void fipt_server::launch_batch() {
         if (q->r.kind != FIPT_REQ_RENDER) continue;
         involved.push_back(t);
     }
-    // bake requests: round-robin chunks up to the ray budget
-    bool any = true;
-    while (any && nch < kMaxChunks) {
-        any = false;
-        for (uint64_t t : active) {
-            Req* q = reqs[t];
-            if (q->r.kind != FIPT_REQ_BAKE || q->next >= q->r.n) continue;
-            const fipt_bake_params& P = q->r.params;
-            const int64_t rays_per_pt = P.spp_diffuse + (int64_t)P.K * P.spp_specular;
+    // bake requests: the oldest admitted request first takes up to a quarter
+    // of the batch's rays (so no request starves), then the requests with the
+    // least remaining work take chunks in that order (shortest remaining work
+    // first keeps small requests' latency low), then the oldest again
+    std::vector<uint64_t> order;
+    for (uint64_t t : active) {
+        Req* q = reqs[t];
+        if (q->r.kind == FIPT_REQ_BAKE && q->next < q->r.n) order.push_back(t);
+    }
+    auto remaining = [&](uint64_t t) {
+        const Req* q = reqs[t];
+        const fipt_bake_params& P = q->r.params;
+        return (q->r.n - q->next) * (P.spp_diffuse + (int64_t)P.K * P.spp_specular);
+    };
+    if (order.size() > 1)
+        std::stable_sort(order.begin() + 1, order.end(),
+                         [&](uint64_t a, uint64_t b) { return remaining(a) < remaining(b); });
+    // takes chunks of request t while its share (rays) and the batch allow
+    auto take = [&](uint64_t t, int64_t share) {
+        Req* q = reqs[t];
+        const fipt_bake_params& P = q->r.params;
+        const int64_t rays_per_pt = P.spp_diffuse + (int64_t)P.K * P.spp_specular;
+        int64_t got = 0;
+        while (q->next < q->r.n && nch < kMaxChunks) {
             const int64_t c = std::min<int64_t>(chunk_points, q->r.n - q->next);
-            if (nch > 0 && batch_rays + c * rays_per_pt > max_batch_rays) { any = false; break; }
+            if (nch > 0 && (batch_rays + c * rays_per_pt > max_batch_rays || got + c * rays_per_pt > share))
+                break;
             BakeChunk& C = H[nch++];
             fipt_scene* sc = scenes[q->r.target];
             C.sc = sc->view();
@@ -310,11 +327,16 @@ void fipt_server::launch_batch() {
             for (int k = 0; k < FIPT_MAX_K; ++k) C.A.sigma[k] = k < P.K ? P.sigma[k] : 1.0f;
             warps += ((c + 31) / 32) * (1 + P.K);
             batch_rays += c * rays_per_pt;
+            got += c * rays_per_pt;
             q->next += c;
             if (std::find(involved.begin(), involved.end(), t) == involved.end()) involved.push_back(t);
-            any = true;
-            if (nch >= kMaxChunks) break;
         }
+    };
+    if (!order.empty()) {
+        take(order[0], max_batch_rays / 4);
+        for (size_t i = 1; i < order.size() && batch_rays < max_batch_rays && nch < kMaxChunks; ++i)
+            take(order[i], max_batch_rays);
+        take(order[0], max_batch_rays);
     }
     if (involved.empty()) return;
     for (uint64_t t : involved) cudaStreamWaitEvent(compute, reqs[t]->h2d, 0);
