@@ -367,9 +367,9 @@ fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1,
  * sized at start-up, or they run on threads that must not take an
  * allocator's lock).  The paper has no counterpart; this is a library convenience.
  * Same arguments and results as fipt_render_fwd; the loss partial sums live
- * in a 512 KiB array compiled into the library, present on every GPU that
+ * in a 1 MiB array compiled into the library, present on every GPU that
  * loads it until the process exits.  N may be at most
- * FIPT_NOALLOC_RENDER_MAX_BLOCKS * 256 = 16,777,216 points; larger N returns
+ * FIPT_NOALLOC_RENDER_MAX_BLOCKS * 128 = 16,777,216 points; larger N returns
  * FIPT_ERR_INVALID_ARG without launching.  Allocates nothing: the first call
  * on a device looks up the array's device address (cudaGetSymbolAddress,
  * with that device current) and keeps it; later calls check with
@@ -380,7 +380,7 @@ fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const float* Ls1,
  * on the GPU (different streams, no ordering between them) race and may
  * return a wrong loss; serialise them on one stream.  Each call overwrites
  * every partial it reads, so no clearing is needed between calls. */
-#define FIPT_NOALLOC_RENDER_MAX_BLOCKS 65536
+#define FIPT_NOALLOC_RENDER_MAX_BLOCKS 131072
 fipt_status fipt_render_fwd_noalloc(const float* Ld, const float* Ls0, const float* Ls1,
                                     int64_t N, int32_t K, const float* sigma_grid,
                                     const float* albedo, const float* rough, const float* metal,
@@ -437,20 +437,32 @@ fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* 
  * pattern around the bake; the paper runs one bake per scene offline).
  *
  * fipt_server_create allocates one device arena of hbm_budget bytes (the
- * admission budget), two streams, and starts a host scheduler thread.
- * Requests are admitted in arrival order as arena space frees up; each
- * batch takes chunks of up to chunk_points points from the admitted bake
- * requests (any scene) until max_batch_rays rays -- the oldest request
- * first, up to a quarter of the batch, then the requests with the least
- * remaining work -- and runs them in ONE kernel launch, together with the
- * render requests admitted so far; up to three batches are in flight, so
- * later arrivals overlap earlier work.
+ * admission budget), a work queue (device descriptors plus a host-mapped
+ * control block and per-chunk done flags), three streams, and starts a host
+ * scheduler thread.  Requests are admitted in arrival order as arena space
+ * frees up.  Bakes run in a device-resident loop: one kernel keeps warps
+ * resident on every SM (as many blocks of 64 threads as leave room for a
+ * block of each render kernel: 28 of 32 on GB300), and they take warp items (32 points of one
+ * chunk, one lobe) in the order the scheduler publishes chunks, one
+ * atomic add per item.  The
+ * scheduler keeps warp items published ahead of the loop and not yet
+ * taken -- two per resident warp, and at least max_batch_rays rays -- in
+ * chunks of up to chunk_points points: the oldest request first, up to a
+ * quarter of that, then the requests with the least remaining work -- so
+ * a request that arrives while others run joins their warps on the device
+ * without a new launch.  The scheduler stops the loop after a millisecond
+ * without work and starts it again when new work is published.  Scene environment maps and voxel caches must be set before a
+ * scene is added.  Render requests run their forward and backward kernels
+ * on their own stream as soon as they are admitted.
  * A chunk keeps the request-local Philox counters (point_base = its offset
  * in the request), so every result is bit-identical to a standalone
  * fipt_bake / fipt_render_fwd / fipt_render_bwd of the same request.
  * All host buffers of a request must stay valid until it completes; pinned
- * (page-locked) buffers let copies overlap compute.  No device code waits;
- * the scheduler polls CUDA events on the host. */
+ * (page-locked) buffers let copies overlap compute.  Every wait is bounded:
+ * the scheduler polls events and the mapped flags; a loop warp that has
+ * polled the published count about half a second in vain ends the launch
+ * (its item, like every item a stopped launch holds, runs first in the
+ * next launch). */
 #define FIPT_REQ_BAKE 0
 #define FIPT_REQ_RENDER 1
 
@@ -483,10 +495,10 @@ typedef struct fipt_request {
 } fipt_request;
 
 typedef struct fipt_server_stats {
-    uint64_t batches;                /* batches launched */
-    uint64_t chunks;                 /* bake chunks launched */
-    uint64_t rays;                   /* bake rays launched */
-    uint64_t max_requests_per_batch; /* most requests sharing one batch */
+    uint64_t batches;                /* launches of the resident bake loop */
+    uint64_t chunks;                 /* bake chunks published */
+    uint64_t rays;                   /* bake rays completed */
+    uint64_t max_requests_per_batch; /* most bake requests with chunks on the device at once */
     uint64_t bytes_in_use;           /* arena bytes held by admitted requests */
     uint64_t peak_bytes;
     uint64_t pending;                /* requests waiting for admission */
@@ -517,16 +529,18 @@ fipt_status fipt_server_times(fipt_server* srv, uint64_t ticket, double* t_submi
 /* Forgets a finished request. */
 fipt_status fipt_server_release(fipt_server* srv, uint64_t ticket);
 fipt_status fipt_server_get_stats(fipt_server* srv, fipt_server_stats* out);
-/* Failure handling.  When a batch fails to launch, or its device work
- * fails, the server starts no new work and every unfinished request ends
- * with that error (its *result) -- each one only after none of its input
- * copy, kernels or output copies is still queued, so a caller whose wait
- * returns may free or reuse the request's host buffers at once.  Requests
- * whose last batch ran before the failing one keep their own results.
- * Test hook (the paper has no counterpart): makes the launch of the batch
- * after the next after_batches ones fail with FIPT_ERR_CUDA instead of
- * running, without touching the device. */
-fipt_status fipt_server_inject_launch_failure(fipt_server* srv, int64_t after_batches);
+/* Failure handling.  When a submission to the device fails (a descriptor
+ * copy, a start of the loop, a render launch) or device work fails, the
+ * server tells the loop to stop, starts no new work, and every unfinished
+ * request ends with that error (its *result) -- each one only after none
+ * of its input copy, kernels or output copies is still queued, so a caller
+ * whose wait returns may free or reuse the request's host buffers at once.
+ * Requests already copying their outputs keep their own results.
+ * Test hook (the paper has no counterpart): after the next after_launches
+ * device submissions (a publication of chunk descriptors, a start of the
+ * loop, a render request's kernels) the following one fails with
+ * FIPT_ERR_CUDA on the host instead of reaching the device. */
+fipt_status fipt_server_inject_launch_failure(fipt_server* srv, int64_t after_launches);
 /* Cancels requests not yet admitted (result FIPT_ERR_NOT_FOUND), drains
  * admitted work, joins the scheduler and frees the arena. */
 fipt_status fipt_server_destroy(fipt_server* srv);

@@ -695,10 +695,10 @@ class Server:
         check(lib().fipt_server_release(self.handle, int(ticket)))
         self._keep.pop(ticket, None)
 
-    def inject_launch_failure(self, after_batches: int = 0):
-        """Test hook: the launch after the next ``after_batches`` batches fails
-        (FIPT_ERR_CUDA) on the host, as a failed kernel launch would."""
-        check(lib().fipt_server_inject_launch_failure(self.handle, int(after_batches)))
+    def inject_launch_failure(self, after_launches: int = 0):
+        """Test hook: the device submission after the next ``after_launches``
+        ones fails (FIPT_ERR_CUDA) on the host, as a failed launch would."""
+        check(lib().fipt_server_inject_launch_failure(self.handle, int(after_launches)))
 
     def stats(self):
         s = ServerStats()

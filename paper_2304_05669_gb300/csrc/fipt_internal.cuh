@@ -102,8 +102,11 @@ struct BakeArgs {
     float sigma[FIPT_MAX_K];
 };
 
-// A slice of one request's points for the batched bake.
-struct BakeChunk {
+// A slice of one request's points for the server's resident bake loop.
+// 256-byte aligned and sized: a descriptor never shares a cache line with
+// another, so the resident loop can read a published descriptor through L1
+// without meeting a line cached before that descriptor was written.
+struct alignas(256) BakeChunk {
     SceneView sc;
     const fipt_query* q;     // the chunk's first query
     float *Ld, *Ls0, *Ls1;   // the chunk's first output rows
@@ -112,9 +115,36 @@ struct BakeChunk {
     BakeArgs A;              // A.point_base = request-local index of the first point
 };
 
-// Bake of a list of chunks (several requests / scenes) in one launch.
-fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st, int flags);
+// Host-mapped control block of the server's resident bake loop.
+struct ServeShared {
+    long long taken;       // one past a recently taken warp item (device: relaxed store; the host's estimate)
+    int stop;              // nonzero: every warp leaves after the item it holds
+    int pad;
+};
+
+// Device counters of the resident bake loop.  `pub` is written only by the
+// host's copy stream, after the descriptors it covers (stream order):
+// (published warp items << FIPT_PUB_CHUNK_BITS) | published descriptors.
+constexpr int FIPT_PUB_CHUNK_BITS = 17;
+struct ServeCounters {
+    unsigned long long head;   // warp items handed out
+    long long pub;             // what is published (see above)
+    int take_in;               // orphans of the previous launch taken
+    int n_in;                  // orphans of the previous launch
+    int n_out;                 // orphans this launch leaves
+    int quit;                  // nonzero: a warp gave up waiting; the whole launch leaves
+};
+
+// The server's resident bake loop (see k_serve_bake).
+fipt_status launch_serve_bake(const BakeChunk* d_chunks, ServeShared* sh, ServeCounters* ctr,
+                              const long long* orphan_in, long long* orphan_out, int32_t* done_count,
+                              int32_t* done_flag, int32_t* status, int wait_polls, int blocks_per_sm,
+                              cudaStream_t st, int flags);
+int serve_loop_warps(int blocks_per_sm);
+// Registers per warp (allocated) and warps per block of the loop's kernels
+// and of the render kernels (the largest of each); loads those kernels too.
+fipt_status serve_kernels_footprint(int* warp_regs, int* warps);
+fipt_status render_kernels_footprint(int* warp_regs, int* warps);
 
 fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
 void fipt_count_launch();
@@ -369,7 +399,7 @@ __device__ __forceinline__ float3 voxel_lookup(const SceneView& sc, float px, fl
 // ---------------------------------------------------------------- traversal
 // Traversal stack entries per thread.  k_trace and k_camera keep the stack
 // in shared memory (a [depth][thread] column per block); the bake (k_bake,
-// k_bake_batch) and the refinement's traversal keep it in a per-thread
+// k_serve_bake) and the refinement's traversal keep it in a per-thread
 // local-memory array.  A ray whose stack would overflow drops the far
 // child it could not push (that subtree is not searched) and sets
 // FIPT_DEV_STACK_OVERFLOW in the device status word.

@@ -6,13 +6,14 @@
 // the forward, the loss and the gradient (for an upstream gradient of 1)
 // in one pass, so that a training step reads its inputs once;
 // k_render_grad_scale applies the upstream gradient afterwards.
+#include <algorithm>
 #include <mutex>
 
 #include "fipt_internal.cuh"
 
 namespace {
 
-constexpr int RENDER_THREADS = 256;
+constexpr int RENDER_THREADS = 128;   // small blocks fit beside the serving loop's resident blocks
 
 struct Grid {
     int K;
@@ -139,17 +140,19 @@ k_render_fwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const 
     if (partial) block_loss(loss, partial);
 }
 
-__global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partial, int64_t n,
-                                                      double* __restrict__ out) {
+// One block of SUM_THREADS sums the per-block partials in a fixed order.
+constexpr int SUM_THREADS = 128;
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_partials(const double* __restrict__ partial, int64_t n,
+                                                             double* __restrict__ out) {
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += 1024) s += partial[i];
+    for (int64_t i = threadIdx.x; i < n; i += SUM_THREADS) s += partial[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __shared__ double ws[32];
+    __shared__ double ws[SUM_THREADS / 32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < 32; ++w) t += ws[w];
+        for (int w = 0; w < SUM_THREADS / 32; ++w) t += ws[w];
         *out = t;
     }
 }
@@ -301,7 +304,7 @@ extern "C" fipt_status fipt_render_fwd(const float* Ld, const float* Ls0, const 
     const unsigned nb = blocks(N, RENDER_THREADS);
     FIPT_LAUNCH(k_render_fwd, nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt, mask,
                                                 Lr, partial);
-    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, SUM_THREADS, 0, st, partial, nb, loss);
     FIPT_LAUNCHED("render_fwd");
     return FIPT_OK;
 }
@@ -354,7 +357,7 @@ extern "C" fipt_status fipt_render_fwd_grad(const float* Ld, const float* Ls0, c
     const unsigned nb = blocks(N, RENDER_THREADS);
     FIPT_LAUNCH(k_render_fwd_grad, nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough, metal, Lgt,
                 mask, Lr, partial, g_albedo, g_rough, g_metal);
-    FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    FIPT_LAUNCH(k_sum_partials, 1, SUM_THREADS, 0, st, partial, nb, loss);
     FIPT_LAUNCHED("render_fwd_grad");
     return FIPT_OK;
 }
@@ -377,6 +380,24 @@ extern "C" fipt_status fipt_render_grad_scale(int64_t N, const double* grad_loss
     return FIPT_OK;
 }
 
+// The most registers a warp of any render kernel holds (as the SM allocates
+// them: in units of 256) and the most warps in one of their blocks.
+// Querying the attributes also loads the kernels, so a server never loads
+// one while its resident loop holds the GPU.
+fipt_status render_kernels_footprint(int* warp_regs, int* warps) {
+    const void* fns[] = {(const void*)k_render_fwd, (const void*)k_render_bwd, (const void*)k_sum_partials};
+    const int nthreads[] = {RENDER_THREADS, RENDER_THREADS, SUM_THREADS};
+    *warp_regs = 0;
+    *warps = 0;
+    for (int i = 0; i < 3; ++i) {
+        cudaFuncAttributes at;
+        FIPT_CUDA(cudaFuncGetAttributes(&at, fns[i]));
+        *warp_regs = std::max(*warp_regs, (at.numRegs * 32 + 255) / 256 * 256);
+        *warps = std::max(*warps, (nthreads[i] + 31) / 32);
+    }
+    return FIPT_OK;
+}
+
 // ---------------------------------------------------------------- no-allocation variant
 // Some callers cannot allocate device memory at the point where they render:
 // callers whose memory comes from a fixed pool sized at start-up (embedded or
@@ -384,7 +405,7 @@ extern "C" fipt_status fipt_render_grad_scale(int64_t N, const double* grad_loss
 // fipt_render_fwd needs a caller workspace for its loss partial sums; this
 // variant keeps them in a fixed array compiled into the library instead.
 // The array lives on every GPU that loads the library until the process
-// exits (FIPT_NOALLOC_RENDER_MAX_BLOCKS doubles = 512 KiB).
+// exits (FIPT_NOALLOC_RENDER_MAX_BLOCKS doubles = 1 MiB).
 static __device__ __align__(256) double g_noalloc_partials[FIPT_NOALLOC_RENDER_MAX_BLOCKS];
 
 namespace {
@@ -453,7 +474,7 @@ extern "C" fipt_status fipt_render_fwd_noalloc(const float* Ld, const float* Ls0
     // nb of them, so nothing left over from an earlier call is ever read.
     FIPT_LAUNCH(k_render_fwd, (unsigned)nb, RENDER_THREADS, 0, st, Ld, Ls0, Ls1, N, g, albedo, rough,
                 metal, Lgt, mask, Lr, Lgt ? partial : nullptr);
-    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, 1024, 0, st, partial, nb, loss);
+    if (Lgt) FIPT_LAUNCH(k_sum_partials, 1, SUM_THREADS, 0, st, partial, nb, loss);
     FIPT_LAUNCHED("render_fwd_noalloc");
     return FIPT_OK;
 }

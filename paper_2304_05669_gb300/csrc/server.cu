@@ -1,27 +1,39 @@
-// Serving runtime: continuous batching of bake and render requests over
-// several resident scenes on one GPU.
+// Serving runtime: a device-resident request loop for bakes, with
+// continuous batching over several resident scenes on one GPU.
 //
 //  * Admission.  The server owns one device arena of `hbm_budget` bytes.  A
 //    request is admitted (in arrival order) when its device buffers fit in
 //    the arena; one larger than the whole budget completes at once with
 //    FIPT_ERR_BUDGET.  Inputs are copied in on a copy stream.
-//  * Continuous batching.  Each batch takes chunks of up to `chunk_points`
-//    points from the admitted bake requests (any scene) until
-//    `max_batch_rays` rays -- the oldest request first, up to a quarter of
-//    the batch, then the requests with the least remaining work -- and runs
-//    them in one launch of the batched bake kernel; render requests run
-//    their forward/backward kernels in the same batch.  Up to three batches
-//    are in flight, so a request that arrives while others run joins the
-//    next batch, and its work overlaps theirs on the device.  Chunks keep request-local Philox counters, so a result is
-//    identical alone and in any mix.
-//  * Completion.  When a request's last chunk has run, its outputs are
+//  * The resident loop.  One kernel (k_serve_bake) keeps warps resident on
+//    every SM; they take warp items (32 points of one chunk, one lobe) from
+//    a device counter in the order the host publishes them and bake each
+//    exactly as a standalone fipt_bake would (chunks keep request-local
+//    Philox counters), so a result is bit-identical alone and in any mix.
+//    The warp that finishes a chunk raises its flag in host-mapped memory.
+//    Warps without work poll with short naps.  The loop ends as a whole:
+//    the scheduler stops it after a millisecond without work (or on
+//    failure), and starts it again when new work is published.
+//  * Continuous batching.  The scheduler thread keeps warp items (32
+//    points of one chunk, one lobe) published ahead of the loop and not yet
+//    taken -- two per resident warp, and at least `max_batch_rays` rays --
+//    in chunks of up to `chunk_points` points: the oldest admitted request
+//    first, up to a quarter of that, then the requests with the least
+//    remaining work, then the oldest again.  A request that arrives while others run has its
+//    chunks published as soon as its inputs are on the device, and its warp
+//    items interleave with theirs without a new launch.  Render requests run
+//    their forward/backward kernels on a stream of their own as soon as they
+//    are admitted; the loop leaves room for them on every SM.
+//  * Completion.  When a request's last chunk is done, its outputs are
 //    copied back on the copy stream and its arena space is freed.
-//  * All waits are on the host (event queries with short sleeps, bounded by
-//    the caller's timeouts); no kernel waits on anything.
-//  * Failure.  A launch that fails, or a batch whose device work fails, stops
-//    the server: no new work starts and every unfinished request ends with
-//    that error once none of its copies or kernels is still queued.
+//  * All waits are bounded: the scheduler polls events and flags on the
+//    host, and the loop's warps give up after a bounded number of polls.
+//  * Failure.  A launch that fails, a descriptor copy that fails, or device
+//    work that fails stops the server: the loop is told to stop, no new work
+//    starts, and every unfinished request ends with that error once none of
+//    its copies or kernels is still queued.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,8 +54,10 @@ double now_s() {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-constexpr int kMaxChunks = 8192;   // descriptors per batch
-constexpr int kSlots = 3;          // batches in flight
+constexpr int kQueue = 1 << 16;          // chunk descriptors per queue epoch
+static_assert(kQueue < (1 << FIPT_PUB_CHUNK_BITS), "descriptor count must fit beside the item count");
+constexpr int kWaitPolls = 1 << 14;     // naps (about half a second) before a waiting warp ends the launch
+constexpr double kIdleStop = 1e-3;       // seconds the loop may idle before the scheduler stops it
 
 }  // namespace
 
@@ -160,17 +174,16 @@ struct Req {
     double* dloss = nullptr;
     void* dws = nullptr;
     size_t ws_bytes = 0;
-    int64_t next = 0;             // bake: next unscheduled point
-    uint64_t last_batch = 0;      // batch that runs this request's last work
-    cudaEvent_t h2d = nullptr, d2h = nullptr;
+    int64_t next = 0;             // bake: next point not yet in a chunk
+    int chunks_open = 0;          // bake: chunks staged and not yet done
+    cudaEvent_t h2d = nullptr, d2h = nullptr, run = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
-struct Batch {
-    uint64_t seq;
-    int slot;
-    cudaEvent_t done;
-    std::vector<uint64_t> finishing;
+struct Publish {
+    cudaEvent_t ev;
+    int n_chunks;
+    long long warps;
 };
 
 }  // namespace
@@ -178,40 +191,73 @@ struct Batch {
 struct fipt_server {
     fipt_ctx* ctx = nullptr;
     size_t budget = 0;
-    int64_t max_batch_rays = 0, chunk_points = 0;
+    int64_t lookahead_rays = 0, chunk_points = 0;
+    int64_t lookahead_items = 0;               // warp items kept published and not yet taken
+    int loop_blocks_per_sm = 0;                // resident loop blocks per SM (room left for a render block)
     char* arena_dev = nullptr;
     fipt_arena* arena = nullptr;
-    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaStream_t loop = nullptr, copy = nullptr, d2h = nullptr, render = nullptr;
     int32_t* status = nullptr;                 // device status word of this server
-    int32_t* status_host = nullptr;            // pinned, one per slot
-    BakeChunk* chunk_dev[kSlots] = {};
-    BakeChunk* chunk_host[kSlots] = {};        // pinned staging
+    int32_t* status_host = nullptr;            // pinned snapshot, copied with each request's outputs
+    // the resident loop's queue
+    ServeShared* sh = nullptr;                 // host-mapped control block
+    ServeShared* sh_dev = nullptr;
+    int32_t* flag_host = nullptr;              // host-mapped per-chunk done flags
+    int32_t* flag_dev = nullptr;
+    BakeChunk* q_dev = nullptr;                // descriptors on the device
+    BakeChunk* q_host = nullptr;               // pinned staging (each slot written once per epoch)
+    long long* pub_host = nullptr;             // pinned values of ctr->pub, one per publication this epoch
+    int n_pub = 0;
+    long long published = 0;                   // warp items whose publication has landed
+    ServeCounters* ctr = nullptr;              // device counters of the loop
+    long long* orphans[2] = {};                // items a launch leaves to the next one (ping-pong)
+    int orphan_parity = 0;
+    int32_t* done_dev = nullptr;               // warp items done per chunk
+    int n_staged = 0;                          // descriptors staged this epoch
+    long long warps_staged = 0;
+    std::vector<uint64_t> chunk_req;           // owner of each staged chunk
+    std::vector<int64_t> chunk_rays;
+    std::vector<int64_t> chunk_items;
+    std::vector<long long> chunk_begin;        // first warp item of each staged chunk
+    size_t first_untaken = 0;                  // first chunk with items the loop has not taken
+    long long taken_seen = 0;                  // most warp items the loop was seen to have taken
+    std::vector<int> open_chunks;              // staged, not yet done
+    std::deque<Publish> publishes;             // descriptor copies not yet published
+    cudaEvent_t loop_done = nullptr, copy_mark = nullptr;
+    bool loop_running = false;
+    double idle_since = -1.0;                  // when the running loop last ran out of work
     std::vector<fipt_scene*> scenes;
     std::vector<Table> tables;
     std::map<uint64_t, Req*> reqs;
     std::deque<uint64_t> pending;              // arrival order
-    std::vector<uint64_t> active;              // admitted, work left to schedule (admission order)
-    std::deque<Batch> inflight;
+    std::vector<uint64_t> active;              // admitted bakes with points not yet staged (admission order)
+    std::vector<uint64_t> renders;             // render requests whose kernels are queued
     std::vector<uint64_t> copying;
-    uint64_t next_ticket = 1, next_batch = 1;
+    uint64_t next_ticket = 1;
     // statistics
-    uint64_t n_batches = 0, n_chunks = 0, max_reqs_in_batch = 0, rays = 0;
+    uint64_t n_launches = 0, n_chunks = 0, max_reqs_open = 0, rays = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
     std::thread worker;
     fipt_status fatal = FIPT_OK;
-    uint64_t fatal_batch = 0;                  // first batch whose work is lost
-    int64_t fail_after = -1;                   // test hook: batches left before a launch failure
+    int64_t fail_after = -1;                   // test hook: stagings left before an injected failure
     char fatal_msg[256] = "";
 
     void run();
     bool admit(Req* q);
-    void launch_batch();
-    void retire(Batch& b);
+    void launch_render(Req* q);
+    void stage_chunks();
+    void untaken(int64_t* items, int64_t* rays);
+    void publish_landed();
+    void collect_chunks();
+    void retire(Req* q);
     void finish_copies();
+    void maybe_reset_epoch();
+    void launch_loop();
+    void stop_idle_loop();
     void drain_after_fatal();
-    void set_fatal(fipt_status st, uint64_t batch, const char* msg);
+    void set_fatal(fipt_status st, const char* msg);
 };
 
 namespace {
@@ -226,6 +272,10 @@ size_t request_bytes(const fipt_request& r, const fipt_server* s) {
     const size_t n = (size_t)r.n;
     (void)s;
     return 4 * up256(n * 12) + 4 * up256(n * 4) + up256(n * 12) + up256(8) + up256(ws) + 256;
+}
+
+int64_t rays_per_point(const fipt_bake_params& P) {
+    return P.spp_diffuse + (int64_t)P.K * P.spp_specular;
 }
 
 }  // namespace
@@ -270,46 +320,83 @@ bool fipt_server::admit(Req* q) {
     return true;
 }
 
-void fipt_server::launch_batch() {
-    const int slot = (int)(next_batch % kSlots);
-    BakeChunk* H = chunk_host[slot];
-    int nch = 0;
-    int64_t warps = 0, batch_rays = 0;
-    std::vector<uint64_t> involved, finishing;
-    // render requests: all of their work runs in this batch
-    for (uint64_t t : active) {
-        Req* q = reqs[t];
-        if (q->r.kind != FIPT_REQ_RENDER) continue;
-        involved.push_back(t);
+// A render request's forward and backward kernels, on the render stream
+// once its inputs are on the device.
+void fipt_server::launch_render(Req* q) {
+    if (fail_after >= 0 && fail_after-- == 0) {
+        set_fatal(FIPT_ERR_CUDA, "injected launch failure");
+        return;
     }
-    // bake requests: the oldest admitted request first takes up to a quarter
-    // of the batch's rays (so no request starves), then the requests with the
-    // least remaining work take chunks in that order (shortest remaining work
-    // first keeps small requests' latency low), then the oldest again
+    cudaStreamWaitEvent(render, q->h2d, 0);
+    const Table& tb = tables[q->r.target];
+    const size_t row = (size_t)q->r.first;
+    const float* Ld = tb.Ld + row * 3;
+    const float* Ls0 = tb.Ls0 + row * tb.K * 3;
+    const float* Ls1 = tb.Ls1 + row * tb.K * 3;
+    fipt_status st = fipt_render_fwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm, q->dLgt,
+                                     nullptr, q->dLr, q->dloss, q->dws, q->ws_bytes, render);
+    if (st == FIPT_OK)
+        st = fipt_render_bwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm, q->dLgt, nullptr,
+                             nullptr, q->dga, q->dgr, q->dgm, render);
+    if (st != FIPT_OK) q->result = st;
+    cudaEventRecord(q->run, render);
+    q->state = LAUNCHED;
+    renders.push_back(q->ticket);
+}
+
+// Warp items (and their rays) staged but not yet taken by the loop.  The
+// loop's warps take items in staging order, so everything below the taken
+// mark is taken; the mark the warps write is a recent one, not always the
+// highest, so the scheduler keeps the highest it has seen.
+void fipt_server::untaken(int64_t* items, int64_t* rays) {
+    taken_seen = std::max(taken_seen, __atomic_load_n(&sh->taken, __ATOMIC_RELAXED));
+    const long long t = std::min<long long>(taken_seen, warps_staged);
+    while (first_untaken < chunk_begin.size() &&
+           chunk_begin[first_untaken] + chunk_items[first_untaken] <= t)
+        ++first_untaken;
+    int64_t r = 0;
+    for (size_t c = first_untaken; c < chunk_begin.size(); ++c) {
+        const long long from = std::max<long long>(chunk_begin[c], t);
+        r += (int64_t)((double)chunk_rays[c] * (double)(chunk_begin[c] + chunk_items[c] - from) / (double)chunk_items[c]);
+    }
+    *items = warps_staged - t;
+    *rays = r;
+}
+
+// Stages chunk descriptors while fewer than lookahead_items warp items (two
+// per resident warp of the loop) and fewer than lookahead_rays rays are
+// published and not yet taken: the oldest admitted bake first, up to a
+// quarter of lookahead_items, then the bakes with the least remaining work,
+// then the oldest again.  Counting items not yet taken (rather than items
+// not yet done) keeps the loop fed while a chunk's last items run long.
+// The new descriptors go to the device on the copy stream (after the
+// requests' input copies) and are published once that copy has landed.
+void fipt_server::stage_chunks() {
+    int64_t items_ahead = 0, rays_ahead = 0;
+    untaken(&items_ahead, &rays_ahead);
+    if (n_staged >= kQueue || (items_ahead >= lookahead_items && rays_ahead >= lookahead_rays)) return;
     std::vector<uint64_t> order;
-    for (uint64_t t : active) {
-        Req* q = reqs[t];
-        if (q->r.kind == FIPT_REQ_BAKE && q->next < q->r.n) order.push_back(t);
-    }
+    for (uint64_t t : active) order.push_back(t);
+    if (order.empty()) return;
     auto remaining = [&](uint64_t t) {
         const Req* q = reqs[t];
-        const fipt_bake_params& P = q->r.params;
-        return (q->r.n - q->next) * (P.spp_diffuse + (int64_t)P.K * P.spp_specular);
+        return (q->r.n - q->next) * rays_per_point(q->r.params);
     };
     if (order.size() > 1)
         std::stable_sort(order.begin() + 1, order.end(),
                          [&](uint64_t a, uint64_t b) { return remaining(a) < remaining(b); });
-    // takes chunks of request t while its share (rays) and the batch allow
+    const int first = n_staged;
     auto take = [&](uint64_t t, int64_t share) {
         Req* q = reqs[t];
         const fipt_bake_params& P = q->r.params;
-        const int64_t rays_per_pt = P.spp_diffuse + (int64_t)P.K * P.spp_specular;
+        const int64_t rpp = rays_per_point(P);
         int64_t got = 0;
-        while (q->next < q->r.n && nch < kMaxChunks) {
+        while (q->next < q->r.n && n_staged < kQueue) {
             const int64_t c = std::min<int64_t>(chunk_points, q->r.n - q->next);
-            if (nch > 0 && (batch_rays + c * rays_per_pt > max_batch_rays || got + c * rays_per_pt > share))
-                break;
-            BakeChunk& C = H[nch++];
+            const int64_t items = ((c + 31) / 32) * (1 + P.K);
+            const bool full = items_ahead + items > lookahead_items && rays_ahead + c * rpp > lookahead_rays;
+            if (items_ahead > 0 && (full || got + items > share)) break;
+            BakeChunk& C = q_host[n_staged];
             fipt_scene* sc = scenes[q->r.target];
             C.sc = sc->view();
             C.q = q->dq + q->next;
@@ -317,7 +404,7 @@ void fipt_server::launch_batch() {
             C.Ls0 = q->dLs0 + q->next * P.K * 3;
             C.Ls1 = q->dLs1 + q->next * P.K * 3;
             C.n = c;
-            C.warp_begin = warps;
+            C.warp_begin = warps_staged;
             C.A.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
             C.A.request_id = P.request_id;
             C.A.point_base = (uint32_t)q->next;
@@ -325,109 +412,134 @@ void fipt_server::launch_batch() {
             C.A.spp_s = P.spp_specular;
             C.A.K = P.K;
             for (int k = 0; k < FIPT_MAX_K; ++k) C.A.sigma[k] = k < P.K ? P.sigma[k] : 1.0f;
-            warps += ((c + 31) / 32) * (1 + P.K);
-            batch_rays += c * rays_per_pt;
-            got += c * rays_per_pt;
+            chunk_begin.push_back(warps_staged);
+            warps_staged += items;
+            chunk_req.push_back(t);
+            chunk_rays.push_back(c * rpp);
+            chunk_items.push_back(items);
+            open_chunks.push_back(n_staged);
+            items_ahead += items;
+            rays_ahead += c * rpp;
+            got += items;
             q->next += c;
-            if (std::find(involved.begin(), involved.end(), t) == involved.end()) involved.push_back(t);
+            ++q->chunks_open;
+            ++n_staged;
         }
     };
-    if (!order.empty()) {
-        take(order[0], max_batch_rays / 4);
-        for (size_t i = 1; i < order.size() && batch_rays < max_batch_rays && nch < kMaxChunks; ++i)
-            take(order[i], max_batch_rays);
-        take(order[0], max_batch_rays);
-    }
-    if (involved.empty()) return;
-    for (uint64_t t : involved) cudaStreamWaitEvent(compute, reqs[t]->h2d, 0);
-    if (nch > 0) {
-        int flags = 0;
-        for (int c = 0; c < nch; ++c) flags |= (H[c].sc.env ? 1 : 0) | (H[c].sc.vox ? 2 : 0);
-        cudaMemcpyAsync(chunk_dev[slot], H, sizeof(BakeChunk) * (size_t)nch, cudaMemcpyHostToDevice, compute);
-        fipt_status st;
-        if (fail_after == 0) {          // injected by fipt_server_inject_launch_failure
-            st = fipt_set_error(FIPT_ERR_CUDA, "injected launch failure");
-        } else {
-            st = launch_bake_batch(chunk_dev[slot], nch, warps, status, compute, flags);
-        }
-        if (fail_after >= 0) --fail_after;
-        if (st != FIPT_OK) set_fatal(st, next_batch, fipt_last_error());
-    }
-    for (uint64_t t : involved) {
-        Req* q = reqs[t];
-        if (q->r.kind == FIPT_REQ_RENDER) {
-            const Table& tb = tables[q->r.target];
-            const int64_t f = q->r.first;
-            const size_t row = (size_t)f;
-            const float* Ld = tb.Ld + row * 3;
-            const float* Ls0 = tb.Ls0 + row * tb.K * 3;
-            const float* Ls1 = tb.Ls1 + row * tb.K * 3;
-            fipt_status st = fipt_render_fwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm,
-                                             q->dLgt, nullptr, q->dLr, q->dloss, q->dws, q->ws_bytes,
-                                             compute);
-            if (st == FIPT_OK)
-                st = fipt_render_bwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm, q->dLgt,
-                                     nullptr, nullptr, q->dga, q->dgr, q->dgm, compute);
-            if (st != FIPT_OK) q->result = st;
-            q->state = LAUNCHED;
-            finishing.push_back(t);
-        } else if (q->next >= q->r.n) {
-            q->state = LAUNCHED;
-            finishing.push_back(t);
-        }
-    }
-    // the batch's device status word lands in this slot's pinned copy
-    cudaMemcpyAsync(status_host + slot, status, sizeof(int32_t), cudaMemcpyDeviceToHost, compute);
-    cudaMemsetAsync(status, 0, sizeof(int32_t), compute);
-    Batch b;
-    b.seq = next_batch++;
-    b.slot = slot;
-    cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
-    cudaEventRecord(b.done, compute);
-    b.finishing = finishing;
-    for (uint64_t t : finishing) reqs[t]->last_batch = b.seq;
-    inflight.push_back(b);
+    const int64_t total = std::max<int64_t>(lookahead_items, 1);
+    take(order[0], total / 4);
+    for (size_t i = 1; i < order.size() && n_staged < kQueue &&
+                       (items_ahead < lookahead_items || rays_ahead < lookahead_rays); ++i)
+        take(order[i], INT64_MAX);
+    take(order[0], INT64_MAX);
     active.erase(std::remove_if(active.begin(), active.end(),
-                                [&](uint64_t t) { return reqs[t]->state == LAUNCHED; }),
+                                [&](uint64_t t) {
+                                    Req* q = reqs[t];
+                                    if (q->next < q->r.n) return false;
+                                    q->state = LAUNCHED;
+                                    return true;
+                                }),
                  active.end());
-    ++n_batches;
-    n_chunks += (uint64_t)nch;
-    rays += (uint64_t)batch_rays;
-    max_reqs_in_batch = std::max<uint64_t>(max_reqs_in_batch, involved.size());
+    const int count = n_staged - first;
+    if (count == 0) return;
+    if (fail_after >= 0 && fail_after-- == 0) {    // injected by fipt_server_inject_launch_failure
+        set_fatal(FIPT_ERR_CUDA, "injected launch failure");
+        return;
+    }
+    cudaMemcpyAsync(q_dev + first, q_host + first, sizeof(BakeChunk) * (size_t)count, cudaMemcpyHostToDevice,
+                    copy);
+    // then the count the loop polls, behind the descriptors on the same stream
+    pub_host[n_pub] = ((long long)warps_staged << FIPT_PUB_CHUNK_BITS) | n_staged;
+    cudaMemcpyAsync(&ctr->pub, pub_host + n_pub, sizeof(long long), cudaMemcpyHostToDevice, copy);
+    ++n_pub;
+    Publish p;
+    cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming);
+    cudaEventRecord(p.ev, copy);
+    p.n_chunks = n_staged;
+    p.warps = warps_staged;
+    publishes.push_back(p);
+    n_chunks += (uint64_t)count;
+    uint64_t open_reqs = 0;
+    for (auto& kv : reqs)
+        if (kv.second->r.kind == FIPT_REQ_BAKE && kv.second->chunks_open > 0) ++open_reqs;
+    max_reqs_open = std::max(max_reqs_open, open_reqs);
 }
 
-void fipt_server::retire(Batch& b) {
-    const int32_t dev_bits = status_host[b.slot];
-    for (uint64_t t : b.finishing) {
-        Req* q = reqs[t];
-        if (dev_bits != 0 && q->result == FIPT_OK) q->result = FIPT_ERR_DEVICE_CHECK;
-        cudaStreamWaitEvent(copy, b.done, 0);
-        const size_t n = (size_t)q->r.n;
-        if (q->r.kind == FIPT_REQ_BAKE) {
-            const size_t K = (size_t)q->r.params.K;
-            if (n) {
-                cudaMemcpyAsync(q->r.Ld, q->dLd, n * 12, cudaMemcpyDeviceToHost, copy);
-                cudaMemcpyAsync(q->r.Ls0, q->dLs0, n * K * 12, cudaMemcpyDeviceToHost, copy);
-                cudaMemcpyAsync(q->r.Ls1, q->dLs1, n * K * 12, cudaMemcpyDeviceToHost, copy);
-            }
-        } else if (n) {
-            if (q->r.Lr) cudaMemcpyAsync(q->r.Lr, q->dLr, n * 12, cudaMemcpyDeviceToHost, copy);
-            if (q->r.loss) cudaMemcpyAsync(q->r.loss, q->dloss, 8, cudaMemcpyDeviceToHost, copy);
-            if (q->r.g_albedo) cudaMemcpyAsync(q->r.g_albedo, q->dga, n * 12, cudaMemcpyDeviceToHost, copy);
-            if (q->r.g_rough) cudaMemcpyAsync(q->r.g_rough, q->dgr, n * 4, cudaMemcpyDeviceToHost, copy);
-            if (q->r.g_metal) cudaMemcpyAsync(q->r.g_metal, q->dgm, n * 4, cudaMemcpyDeviceToHost, copy);
+// Notes the publications that have landed (the loop sees each as soon as
+// its copy lands; the scheduler's record is for starting the loop).
+void fipt_server::publish_landed() {
+    while (!publishes.empty()) {
+        Publish& p = publishes.front();
+        const cudaError_t e = cudaEventQuery(p.ev);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) {
+            set_fatal(FIPT_ERR_CUDA, "descriptor copy failed");
+            return;
         }
-        cudaEventRecord(q->d2h, copy);
-        q->state = COPYING;
-        copying.push_back(t);
+        published = p.warps;
+        cudaEventDestroy(p.ev);
+        publishes.pop_front();
     }
-    cudaEventDestroy(b.done);
+}
+
+// Chunks whose flags the loop has raised: a request whose last chunk is
+// done gets its outputs copied back.
+void fipt_server::collect_chunks() {
+    for (size_t i = 0; i < open_chunks.size();) {
+        const int c = open_chunks[i];
+        if (__atomic_load_n(flag_host + c, __ATOMIC_ACQUIRE) == 0) { ++i; continue; }
+        open_chunks[i] = open_chunks.back();
+        open_chunks.pop_back();
+        rays += (uint64_t)chunk_rays[c];
+        Req* q = reqs[chunk_req[c]];
+        if (--q->chunks_open == 0 && q->next >= q->r.n) retire(q);
+    }
+}
+
+// Copies a finished request's outputs back (with a snapshot of the device
+// status word) on the output stream, so they never hold up a publication.
+void fipt_server::retire(Req* q) {
+    const size_t n = (size_t)q->r.n;
+    if (q->r.kind == FIPT_REQ_BAKE) {
+        const size_t K = (size_t)q->r.params.K;
+        if (n) {
+            cudaMemcpyAsync(q->r.Ld, q->dLd, n * 12, cudaMemcpyDeviceToHost, d2h);
+            cudaMemcpyAsync(q->r.Ls0, q->dLs0, n * K * 12, cudaMemcpyDeviceToHost, d2h);
+            cudaMemcpyAsync(q->r.Ls1, q->dLs1, n * K * 12, cudaMemcpyDeviceToHost, d2h);
+        }
+    } else {
+        cudaStreamWaitEvent(d2h, q->run, 0);
+        if (n) {
+            if (q->r.Lr) cudaMemcpyAsync(q->r.Lr, q->dLr, n * 12, cudaMemcpyDeviceToHost, d2h);
+            if (q->r.loss) cudaMemcpyAsync(q->r.loss, q->dloss, 8, cudaMemcpyDeviceToHost, d2h);
+            if (q->r.g_albedo) cudaMemcpyAsync(q->r.g_albedo, q->dga, n * 12, cudaMemcpyDeviceToHost, d2h);
+            if (q->r.g_rough) cudaMemcpyAsync(q->r.g_rough, q->dgr, n * 4, cudaMemcpyDeviceToHost, d2h);
+            if (q->r.g_metal) cudaMemcpyAsync(q->r.g_metal, q->dgm, n * 4, cudaMemcpyDeviceToHost, d2h);
+        }
+    }
+    cudaMemcpyAsync(status_host, status, sizeof(int32_t), cudaMemcpyDeviceToHost, d2h);
+    cudaEventRecord(q->d2h, d2h);
+    q->state = COPYING;
+    copying.push_back(q->ticket);
 }
 
 void fipt_server::finish_copies() {
+    for (size_t i = 0; i < renders.size();) {
+        Req* q = reqs[renders[i]];
+        const cudaError_t e = cudaEventQuery(q->run);
+        if (e == cudaErrorNotReady) { ++i; continue; }
+        renders.erase(renders.begin() + (long)i);
+        if (e != cudaSuccess) {
+            set_fatal(FIPT_ERR_CUDA, "render kernels failed");
+            return;
+        }
+        retire(q);
+    }
     for (size_t i = 0; i < copying.size();) {
         Req* q = reqs[copying[i]];
         if (cudaEventQuery(q->d2h) == cudaSuccess) {
+            if (*reinterpret_cast<volatile int32_t*>(status_host) != 0 && q->result == FIPT_OK)
+                q->result = FIPT_ERR_DEVICE_CHECK;
             arena->release(q->off, q->bytes);
             q->state = DONE;
             q->t_done = now_s();
@@ -439,19 +551,85 @@ void fipt_server::finish_copies() {
     }
 }
 
-void fipt_server::set_fatal(fipt_status st, uint64_t batch, const char* msg) {
-    if (fatal != FIPT_OK) return;
-    fatal = st;
-    fatal_batch = batch;
-    snprintf(fatal_msg, sizeof(fatal_msg), "%s", msg ? msg : "");
+// Starts a new queue epoch once every staged chunk is done and the loop
+// has left: counters back to zero on the device and in the mapped block.
+void fipt_server::maybe_reset_epoch() {
+    if (n_staged == 0 || loop_running || !open_chunks.empty() || !publishes.empty()) return;
+    std::memset(flag_host, 0, sizeof(int32_t) * (size_t)n_staged);
+    // on the copy stream, ahead of the next epoch's publications
+    cudaMemsetAsync(ctr, 0, sizeof(ServeCounters), copy);
+    cudaMemsetAsync(done_dev, 0, sizeof(int32_t) * (size_t)n_staged, copy);
+    published = 0;
+    n_pub = 0;
+    __atomic_store_n(&sh->taken, 0LL, __ATOMIC_RELAXED);
+    n_staged = 0;
+    warps_staged = 0;
+    taken_seen = 0;
+    first_untaken = 0;
+    chunk_req.clear();
+    chunk_rays.clear();
+    chunk_items.clear();
+    chunk_begin.clear();
 }
 
-// After a fatal error no new work starts, and every request ends with that
-// error -- but only once nothing of it is still in flight: a request whose
-// input copy, batch or output copy is still queued on the device keeps the
-// caller's host buffers in use until that work has completed (or failed),
-// so it is marked done only then.  Batches before the failing one complete
-// normally and their requests keep their own results.
+// Starts the resident loop when it is not running and staged work waits:
+// items not yet taken, or items an earlier launch left behind.  It waits
+// for the epoch's first publication, so its warps do not spend their idle
+// polls on a descriptor copy.
+void fipt_server::launch_loop() {
+    if (loop_running || open_chunks.empty() || published == 0) return;
+    if (fail_after >= 0 && fail_after-- == 0) {
+        set_fatal(FIPT_ERR_CUDA, "injected launch failure");
+        return;
+    }
+    int flags = 0;
+    for (fipt_scene* sc : scenes) flags |= (sc->env ? 1 : 0) | (sc->vox ? 2 : 0);
+    // after the copy stream's counter resets; the previous launch's orphans
+    // become this one's inputs
+    cudaEventRecord(copy_mark, copy);
+    cudaStreamWaitEvent(loop, copy_mark, 0);
+    cudaMemcpyAsync(&ctr->n_in, &ctr->n_out, sizeof(int), cudaMemcpyDeviceToDevice, loop);
+    cudaMemsetAsync(&ctr->take_in, 0, sizeof(int), loop);
+    cudaMemsetAsync(&ctr->n_out, 0, sizeof(int), loop);
+    cudaMemsetAsync(&ctr->quit, 0, sizeof(int), loop);
+    __atomic_store_n(&sh->stop, 0, __ATOMIC_RELAXED);   // ordered before the launch by the launch itself
+    idle_since = -1.0;
+    fipt_status st = launch_serve_bake(q_dev, sh_dev, ctr, orphans[orphan_parity], orphans[1 - orphan_parity],
+                                       done_dev, flag_dev, status, kWaitPolls, loop_blocks_per_sm, loop, flags);
+    orphan_parity ^= 1;
+    if (st != FIPT_OK) {
+        set_fatal(st, fipt_last_error());
+        return;
+    }
+    cudaEventRecord(loop_done, loop);
+    loop_running = true;
+    ++n_launches;
+}
+
+// Stops the running loop once it has had no work for kIdleStop seconds, so
+// its resident blocks do not hold the SMs while the server is idle.
+void fipt_server::stop_idle_loop() {
+    if (!loop_running || !open_chunks.empty() || !publishes.empty()) {
+        idle_since = -1.0;
+        return;
+    }
+    const double t = now_s();
+    if (idle_since < 0.0) idle_since = t;
+    else if (t - idle_since > kIdleStop) __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);
+}
+
+void fipt_server::set_fatal(fipt_status st, const char* msg) {
+    if (fatal != FIPT_OK) return;
+    fatal = st;
+    snprintf(fatal_msg, sizeof(fatal_msg), "%s", msg ? msg : "");
+    __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);    // the loop leaves after the items it holds
+}
+
+// After a fatal error no new work starts, and every unfinished request ends
+// with that error -- but only once nothing of it is still in flight: its
+// input copy, the loop (which may hold its chunks) and its output copies
+// must have completed or failed before the caller may reuse its buffers.
+// Requests already copying their outputs keep their own results.
 void fipt_server::drain_after_fatal() {
     for (uint64_t t : pending) {
         Req* q = reqs[t];
@@ -460,30 +638,29 @@ void fipt_server::drain_after_fatal() {
         q->t_done = now_s();
     }
     pending.clear();
-    for (size_t i = 0; i < active.size();) {
-        Req* q = reqs[active[i]];
-        if (cudaEventQuery(q->h2d) == cudaErrorNotReady) { ++i; continue; }
+    if (loop_running && cudaEventQuery(loop_done) != cudaErrorNotReady) loop_running = false;
+    while (!publishes.empty() && cudaEventQuery(publishes.front().ev) != cudaErrorNotReady) {
+        cudaEventDestroy(publishes.front().ev);
+        publishes.pop_front();
+    }
+    const bool device_quiet = !loop_running && publishes.empty();
+    for (auto& kv : reqs) {
+        Req* q = kv.second;
+        if (q->state == DONE || q->state == COPYING) continue;
+        if (!device_quiet) continue;
+        if (q->state == LAUNCHED && q->r.kind == FIPT_REQ_RENDER &&
+            cudaEventQuery(q->run) == cudaErrorNotReady) continue;
+        if (cudaEventQuery(q->h2d) == cudaErrorNotReady) continue;
         q->result = fatal;
         q->state = DONE;
         q->t_done = now_s();
-        active.erase(active.begin() + (long)i);
     }
-    while (!inflight.empty()) {
-        Batch& b = inflight.front();
-        const cudaError_t e = cudaEventQuery(b.done);
-        if (e == cudaErrorNotReady) break;
-        if (e == cudaSuccess && b.seq < fatal_batch) {
-            retire(b);                   // its requests' copies go out as usual
-        } else {
-            for (uint64_t t : b.finishing) {
-                Req* q = reqs[t];
-                q->result = fatal;
-                q->state = DONE;
-                q->t_done = now_s();
-            }
-            cudaEventDestroy(b.done);
-        }
-        inflight.pop_front();
+    if (device_quiet) {
+        active.clear();
+        renders.erase(std::remove_if(renders.begin(), renders.end(),
+                                     [&](uint64_t t) { return reqs[t]->state == DONE; }),
+                      renders.end());
+        open_chunks.clear();
     }
     for (size_t i = 0; i < copying.size();) {
         Req* q = reqs[copying[i]];
@@ -503,8 +680,10 @@ void fipt_server::run() {
     for (;;) {
         if (fatal != FIPT_OK) {
             drain_after_fatal();
-            if (stop && pending.empty() && active.empty() && inflight.empty() && copying.empty()) break;
-            if (pending.empty() && active.empty() && inflight.empty() && copying.empty())
+            bool busy = false;
+            for (auto& kv : reqs) busy = busy || kv.second->state != DONE;
+            if (stop && !busy && !loop_running && publishes.empty()) break;
+            if (!busy && !loop_running)
                 cv_work.wait_for(lk, std::chrono::milliseconds(10));
             else {
                 lk.unlock();
@@ -513,49 +692,56 @@ void fipt_server::run() {
             }
             continue;
         }
-        bool progress = false;
-        // retire finished batches in order
-        while (!inflight.empty()) {
-            const cudaError_t e = cudaEventQuery(inflight.front().done);
-            if (e == cudaErrorNotReady) break;
-            if (e != cudaSuccess) {
-                char m[200];
-                snprintf(m, sizeof(m), "batch failed: %s", cudaGetErrorString(e));
-                set_fatal(FIPT_ERR_CUDA, inflight.front().seq, m);
-                break;
+        if (loop_running) {
+            const cudaError_t e = cudaEventQuery(loop_done);
+            if (e != cudaErrorNotReady) {
+                loop_running = false;
+                if (e != cudaSuccess) {
+                    char m[200];
+                    snprintf(m, sizeof(m), "serving loop failed: %s", cudaGetErrorString(e));
+                    set_fatal(FIPT_ERR_CUDA, m);
+                    continue;
+                }
             }
-            retire(inflight.front());
-            inflight.pop_front();
-            progress = true;
         }
+        publish_landed();
+        collect_chunks();
         finish_copies();
+        if (fatal != FIPT_OK) continue;
         // admit in arrival order while the arena has room
+        bool admitted = false;
         while (!pending.empty()) {
             Req* q = reqs[pending.front()];
             if (!admit(q)) break;
-            active.push_back(q->ticket);
             pending.pop_front();
-            progress = true;
-        }
-        if ((int)inflight.size() < kSlots && !active.empty()) {
-            const uint64_t before = n_batches;
-            launch_batch();
-            progress = progress || n_batches != before;
-        }
-        if (stop && pending.empty() && active.empty() && inflight.empty() && copying.empty()) break;
-        if (!progress) {
-            if (inflight.empty() && copying.empty() && active.empty())
-                cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            else {
-                lk.unlock();
-                std::this_thread::sleep_for(std::chrono::microseconds(50));
-                lk.lock();
+            admitted = true;
+            if (q->r.kind == FIPT_REQ_BAKE) {
+                if (q->r.n > 0) active.push_back(q->ticket);
+                else retire(q);
+            } else {
+                launch_render(q);
             }
+        }
+        if (fatal != FIPT_OK) continue;
+        maybe_reset_epoch();
+        stage_chunks();
+        if (fatal != FIPT_OK) continue;
+        publish_landed();
+        launch_loop();
+        stop_idle_loop();
+        const bool idle = pending.empty() && active.empty() && open_chunks.empty() && renders.empty() &&
+                          copying.empty() && publishes.empty();
+        if (stop && idle && !loop_running) break;
+        if (idle && !admitted && !loop_running) {
+            cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        } else {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
         }
     }
 }
 
-// ---------------------------------------------------------------- C ABI
 extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int64_t max_batch_rays,
                                           int64_t chunk_points, fipt_server** out) {
     FIPT_REQUIRE(ctx && out, "ctx / out is NULL");
@@ -563,25 +749,69 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
     FIPT_REQUIRE(max_batch_rays > 0 && chunk_points > 0 && chunk_points < ((int64_t)1 << 31),
                  "max_batch_rays and chunk_points must be positive");
     FIPT_CUDA(cudaSetDevice(ctx->device));
+    int loop_bps = 0;
+    {
+        // The loop takes as many block slots as leave room for one block of
+        // the largest render kernel, so render requests always run beside
+        // it: a block slot, warp slots, and registers in each of the SM's
+        // kSubPartitions quarters (warps are spread evenly over them, each
+        // with a quarter of the register file).
+        constexpr int kSubPartitions = 4;
+        int lw_regs = 0, lwarps = 0, rw_regs = 0, rwarps = 0, sm_regs = 0, sm_threads = 0, sm_blocks = 0;
+        fipt_status fs = serve_kernels_footprint(&lw_regs, &lwarps);
+        if (fs == FIPT_OK) fs = render_kernels_footprint(&rw_regs, &rwarps);
+        if (fs != FIPT_OK) return fs;
+        FIPT_CUDA(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device));
+        FIPT_CUDA(cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, ctx->device));
+        FIPT_CUDA(cudaDeviceGetAttribute(&sm_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, ctx->device));
+        const int q_regs = sm_regs / kSubPartitions;
+        const int render_q = (rwarps + kSubPartitions - 1) / kSubPartitions * rw_regs;
+        int b = 0;
+        for (int c = 1; c < sm_blocks; ++c) {
+            const int lw = c * lwarps;
+            const bool fits = lw + rwarps <= sm_threads / 32 &&
+                              (lw + kSubPartitions - 1) / kSubPartitions * lw_regs + render_q <= q_regs;
+            if (fits) b = c;
+        }
+        FIPT_REQUIRE(b >= 1, "no room for the serving loop beside the render kernels");
+        loop_bps = b;
+    }
     fipt_server* s = new fipt_server();
     s->ctx = ctx;
     s->budget = hbm_budget & ~size_t(255);
-    s->max_batch_rays = max_batch_rays;
+    s->lookahead_rays = max_batch_rays;
+    s->loop_blocks_per_sm = loop_bps;
+    s->lookahead_items = 2 * (int64_t)serve_loop_warps(s->loop_blocks_per_sm);
     s->chunk_points = chunk_points;
     cudaError_t e = cudaMalloc(&s->arena_dev, s->budget);
     if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMallocHost(&s->status_host, sizeof(int32_t) * kSlots);
-    for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
-        e = cudaMalloc(&s->chunk_dev[i], sizeof(BakeChunk) * kMaxChunks);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->chunk_host[i], sizeof(BakeChunk) * kMaxChunks);
-    }
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->status_host, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->sh, sizeof(ServeShared), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->sh_dev, s->sh, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->flag_host, sizeof(int32_t) * kQueue, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->flag_dev, s->flag_host, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&s->q_dev, sizeof(BakeChunk) * kQueue);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->q_host, sizeof(BakeChunk) * kQueue);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->pub_host, sizeof(long long) * kQueue);
+    if (e == cudaSuccess) e = cudaMalloc(&s->ctr, sizeof(ServeCounters));
+    if (e == cudaSuccess) e = cudaMemset(s->ctr, 0, sizeof(ServeCounters));
+    const size_t max_orphans = (size_t)serve_loop_warps(s->loop_blocks_per_sm);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&s->orphans[i], sizeof(long long) * max_orphans);
+    if (e == cudaSuccess) e = cudaMalloc(&s->done_dev, sizeof(int32_t) * kQueue);
+    if (e == cudaSuccess) e = cudaMemset(s->done_dev, 0, sizeof(int32_t) * kQueue);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->loop, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->render, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_mark, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fipt_server_destroy(s);
         return fipt_check_cuda(e, "server create");
     }
+    std::memset(s->sh, 0, sizeof(ServeShared));
+    std::memset(s->flag_host, 0, sizeof(int32_t) * kQueue);
     s->arena = new fipt_arena(s->budget);
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -640,6 +870,7 @@ extern "C" fipt_status fipt_server_submit(fipt_server* s, const fipt_request* r,
     cudaSetDevice(s->ctx->device);
     cudaEventCreateWithFlags(&q->h2d, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&q->d2h, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&q->run, cudaEventDisableTiming);
     s->reqs[q->ticket] = q;
     *ticket = q->ticket;
     if (q->bytes > s->budget) {
@@ -704,25 +935,26 @@ extern "C" fipt_status fipt_server_release(fipt_server* s, uint64_t ticket) {
     FIPT_REQUIRE(it->second->state == DONE, "request still running");
     cudaEventDestroy(it->second->h2d);
     cudaEventDestroy(it->second->d2h);
+    cudaEventDestroy(it->second->run);
     delete it->second;
     s->reqs.erase(it);
     return FIPT_OK;
 }
 
-extern "C" fipt_status fipt_server_inject_launch_failure(fipt_server* s, int64_t after_batches) {
-    FIPT_REQUIRE(s && after_batches >= 0, "bad arguments");
+extern "C" fipt_status fipt_server_inject_launch_failure(fipt_server* s, int64_t after_launches) {
+    FIPT_REQUIRE(s && after_launches >= 0, "bad arguments");
     std::lock_guard<std::mutex> lk(s->mu);
-    s->fail_after = after_batches;
+    s->fail_after = after_launches;
     return FIPT_OK;
 }
 
 extern "C" fipt_status fipt_server_get_stats(fipt_server* s, fipt_server_stats* out) {
     FIPT_REQUIRE(s && out, "NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
-    out->batches = s->n_batches;
+    out->batches = s->n_launches;
     out->chunks = s->n_chunks;
     out->rays = s->rays;
-    out->max_requests_per_batch = s->max_reqs_in_batch;
+    out->max_requests_per_batch = s->max_reqs_open;
     out->bytes_in_use = s->arena ? s->arena->used : 0;
     out->peak_bytes = s->arena ? s->arena->peak : 0;
     out->pending = s->pending.size();
@@ -747,22 +979,36 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
         s->worker.join();
     }
     cudaSetDevice(s->ctx ? s->ctx->device : 0);
-    if (s->compute) cudaStreamSynchronize(s->compute);
+    if (s->sh) __atomic_store_n(&s->sh->stop, 1, __ATOMIC_RELEASE);
+    if (s->loop) cudaStreamSynchronize(s->loop);
     if (s->copy) cudaStreamSynchronize(s->copy);
+    if (s->d2h) cudaStreamSynchronize(s->d2h);
+    if (s->render) cudaStreamSynchronize(s->render);
+    for (auto& p : s->publishes) cudaEventDestroy(p.ev);
     for (auto& kv : s->reqs) {
         cudaEventDestroy(kv.second->h2d);
         cudaEventDestroy(kv.second->d2h);
+        cudaEventDestroy(kv.second->run);
         delete kv.second;
     }
-    for (int i = 0; i < kSlots; ++i) {
-        cudaFree(s->chunk_dev[i]);
-        cudaFreeHost(s->chunk_host[i]);
-    }
+    if (s->loop_done) cudaEventDestroy(s->loop_done);
+    if (s->copy_mark) cudaEventDestroy(s->copy_mark);
+    cudaFree(s->q_dev);
+    cudaFreeHost(s->q_host);
+    cudaFreeHost(s->pub_host);
+    cudaFree(s->ctr);
+    cudaFree(s->orphans[0]);
+    cudaFree(s->orphans[1]);
+    cudaFree(s->done_dev);
+    cudaFreeHost(s->flag_host);
+    cudaFreeHost(s->sh);
     cudaFreeHost(s->status_host);
     cudaFree(s->status);
     cudaFree(s->arena_dev);
-    if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->loop) cudaStreamDestroy(s->loop);
     if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->d2h) cudaStreamDestroy(s->d2h);
+    if (s->render) cudaStreamDestroy(s->render);
     delete s->arena;
     delete s;
     return FIPT_OK;

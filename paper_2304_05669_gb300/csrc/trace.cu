@@ -196,7 +196,9 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 // memory column: the bake then reserves no shared memory and the SM's
 // unified L1 / shared storage serves as cache for the nodes and for the
 // stack entries actually in use.
-// FLAGS: 1 = environment light for misses, 2 = voxel radiance cache.
+// FLAGS: 1 = environment light for misses, 2 = voxel radiance cache (each
+// used only where the pair's scene has one, so a launch over chunks of
+// several scenes takes the union of their flags).
 template <bool STATS, int FLAGS>
 __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query* __restrict__ q,
                                           const int64_t p, const int lobe, const bool valid,
@@ -267,7 +269,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                 if (lit) {
                     const float4 le = __ldg(sc.shade + 2 * best.leaf);
                     float3 ca;
-                    if (FLAGS & 2) {
+                    if ((FLAGS & 2) && sc.vox) {
                         ca = voxel_lookup(sc, ox + best.t * rdx, oy + best.t * rdy, oz + best.t * rdz);
                     } else {
                         const float4 c4 = __ldg(sc.shade + 2 * best.leaf + 1);
@@ -276,7 +278,7 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     lx = (best.front ? le.x : 0.0f) + ca.x;
                     ly = (best.front ? le.y : 0.0f) + ca.y;
                     lz = (best.front ? le.z : 0.0f) + ca.z;
-                } else if (FLAGS & 1) {
+                } else if ((FLAGS & 1) && sc.env) {
                     const float3 e = env_lookup(sc, rdx, rdy, rdz);
                     lx = e.x; ly = e.y; lz = e.z;
                     lit = true;
@@ -451,32 +453,107 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     bake_item<STATS, FLAGS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats);
 }
 
-// One launch over chunks of several requests, possibly on several scenes
-// (continuous batching in the server).  Chunk c owns global warps
-// [warp_begin, warp_begin + ceil(n/32) * (1 + K)); inside a chunk the
-// mapping is the single-request one, and the Philox counter uses the
-// chunk's request-local point_base, so every value equals the one a
-// separate fipt_bake of that request would produce.
+// ---------------------------------------------------------------- device-resident serving loop
+__device__ __forceinline__ long long ld_relaxed_gpu(const long long* p) {
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_acquire_gpu(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+__device__ __forceinline__ void st_release_sys(int* p, int v) {
+    asm volatile("st.release.sys.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_sys(long long* p, long long v) {
+    asm volatile("st.relaxed.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// The server's bake loop: resident warps take warp items (32 points of one
+// chunk, one lobe) in publication order from a device counter with one
+// atomicAdd each (no compare-and-swap retries, so thousands of warps do not
+// serialise on the counter), bake each exactly as k_bake would, and count it
+// done; the warp that completes a chunk raises the chunk's flag in
+// host-mapped memory, where the server's scheduler sees it without a copy.
+// The host publishes work by copying chunk descriptors to `chunks` and then
+// the published item and descriptor counts to ctr->pub, in that order on
+// one copy stream, so the loop polls device memory (never host memory,
+// whose system-scope loads would slow the warps still baking); each warp
+// that takes a new item writes how far it got to sh->taken, from which the
+// host decides how much more to publish.  A warp whose item is not
+// published yet polls with naps growing to 32 microseconds and reads the
+// count once more with acquire semantics before it uses the descriptor.  The launch ends as a
+// whole: when the host sets sh->stop (it has no work left, or it failed),
+// or when a warp has waited wait_polls naps (the host did not answer) and
+// sets ctr->quit, every warp leaves -- a waiting warp at once, recording
+// its item in `orphan_out`, a busy one after its item, without taking
+// another.  The next launch takes the orphans first (from `orphan_in`), so
+// no item is lost or taken twice, and no orphan waits behind warps that
+// keep running.  A descriptor is read
+// only after its publication, and no cache line holds parts of two
+// descriptors, so L1 never serves one from before it was written.
 template <int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
-k_bake_batch(const BakeChunk* __restrict__ chunks, int n_chunks, int64_t total_warps,
-             int32_t* status) {
-    const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
-    const int64_t w = g >> 5;
-    const int lane = (int)(g & 31);
-    if (w >= total_warps) return;
-    int lo = 0, hi = n_chunks - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (chunks[mid].warp_begin <= w) lo = mid; else hi = mid - 1;
+k_serve_bake(const BakeChunk* __restrict__ chunks, ServeShared* sh, ServeCounters* ctr,
+             const long long* __restrict__ orphan_in, long long* __restrict__ orphan_out,
+             int32_t* __restrict__ done_count, int32_t* done_flag, int32_t* status, int wait_polls) {
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(sizeof(BakeChunk) == 256, "one descriptor per pair of cache lines");
+    const int lane = threadIdx.x & 31;
+    int ci = 0;
+    for (;;) {
+        long long w = -1;
+        int nch = 0;
+        if (lane == 0 && !ld_volatile_int(&ctr->quit) && !ld_volatile_int(&sh->stop)) {
+            const int k = atomicAdd(&ctr->take_in, 1);
+            if (k < ctr->n_in) {
+                w = __ldcg(orphan_in + k);
+            } else {
+                w = (long long)atomicAdd(&ctr->head, 1ULL);
+                st_relaxed_sys(&sh->taken, w + 1);          // tells the scheduler how far the loop has got
+            }
+            int idle = 0;
+            unsigned nap = 256;
+            for (;;) {
+                if ((ld_relaxed_gpu(&ctr->pub) >> FIPT_PUB_CHUNK_BITS) > w) {
+                    nch = (int)(ld_acquire_gpu(&ctr->pub) & ((1 << FIPT_PUB_CHUNK_BITS) - 1));
+                    break;
+                }
+                const bool give_up = ++idle > wait_polls;
+                if (give_up) atomicExch(&ctr->quit, 1);
+                if (give_up || ld_volatile_int(&ctr->quit) || ((idle & 7) == 0 && ld_volatile_int(&sh->stop))) {
+                    orphan_out[atomicAdd(&ctr->n_out, 1)] = w;
+                    w = -1;
+                    break;
+                }
+                __nanosleep(nap);
+                if (nap < 32768) nap *= 2;
+            }
+        }
+        w = __shfl_sync(FULL, w, 0);
+        nch = __shfl_sync(FULL, nch, 0);
+        if (w < 0) return;
+        if (w < chunks[ci].warp_begin) ci = 0;              // an orphan from earlier
+        while (ci + 1 < nch && chunks[ci + 1].warp_begin <= w) ++ci;
+        const BakeChunk& C = chunks[ci];
+        const int L = 1 + C.A.K;
+        const int64_t wl = w - C.warp_begin;
+        const int lobe = (int)(wl % L);
+        const int64_t p = (wl / L) * 32 + lane;
+        bake_item<false, FLAGS>(C.sc, C.q, p, lobe, p < C.n, C.A, C.Ld, C.Ls0, C.Ls1, status, nullptr);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            const int items = (int)(((C.n + 31) / 32) * L);
+            if (atomicAdd(done_count + ci, 1) == items - 1) {
+                __threadfence_system();
+                st_release_sys(done_flag + ci, 1);
+            }
+        }
     }
-    const BakeChunk* C = chunks + lo;
-    const BakeArgs A = C->A;
-    const int64_t wl = w - C->warp_begin;
-    const int L = 1 + A.K;
-    const int lobe = (int)(wl % L);
-    const int64_t p = (wl / L) * 32 + lane;
-    bake_item<false, FLAGS>(C->sc, C->q, p, lobe, p < C->n, A, C->Ld, C->Ls0, C->Ls1, status, nullptr);
 }
 
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
@@ -623,17 +700,48 @@ extern "C" fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* ke
     return FIPT_OK;
 }
 
-// Internal launcher used by the serving runtime.
-fipt_status launch_bake_batch(const BakeChunk* d_chunks, int n_chunks, int64_t total_warps,
-                              int32_t* status, cudaStream_t st, int flags) {
-    if (n_chunks <= 0 || total_warps <= 0) return FIPT_OK;
-    const unsigned nb = blocks(total_warps * 32, BAKE_THREADS);
+// Launcher of the server's resident bake loop: blocks_per_sm resident blocks
+// on every SM of the current device.
+fipt_status launch_serve_bake(const BakeChunk* d_chunks, ServeShared* sh, ServeCounters* ctr,
+                              const long long* orphan_in, long long* orphan_out, int32_t* done_count,
+                              int32_t* done_flag, int32_t* status, int wait_polls, int blocks_per_sm,
+                              cudaStream_t st, int flags) {
+    int dev = 0, sms = 0;
+    FIPT_CUDA(cudaGetDevice(&dev));
+    FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned nb = (unsigned)(sms * blocks_per_sm);
+#define FIPT_SERVE_CASE(FL) \
+    FIPT_LAUNCH(k_serve_bake<FL>, nb, BAKE_THREADS, 0, st, d_chunks, sh, ctr, orphan_in, orphan_out, done_count, \
+                done_flag, status, wait_polls)
     switch (flags) {
-        case 0: FIPT_LAUNCH(k_bake_batch<0>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
-        case 1: FIPT_LAUNCH(k_bake_batch<1>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
-        case 2: FIPT_LAUNCH(k_bake_batch<2>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
-        default: FIPT_LAUNCH(k_bake_batch<3>, nb, BAKE_THREADS, 0, st, d_chunks, n_chunks, total_warps, status); break;
+        case 0: FIPT_SERVE_CASE(0); break;
+        case 1: FIPT_SERVE_CASE(1); break;
+        case 2: FIPT_SERVE_CASE(2); break;
+        default: FIPT_SERVE_CASE(3); break;
     }
-    FIPT_LAUNCHED("bake_batch");
+#undef FIPT_SERVE_CASE
+    FIPT_LAUNCHED("serve_bake");
     return FIPT_OK;
+}
+
+fipt_status serve_kernels_footprint(int* warp_regs, int* warps) {
+    const void* fns[] = {(const void*)k_serve_bake<0>, (const void*)k_serve_bake<1>,
+                         (const void*)k_serve_bake<2>, (const void*)k_serve_bake<3>};
+    *warp_regs = 0;
+    for (const void* f : fns) {
+        cudaFuncAttributes at;
+        FIPT_CUDA(cudaFuncGetAttributes(&at, f));
+        *warp_regs = std::max(*warp_regs, (at.numRegs * 32 + 255) / 256 * 256);
+    }
+    *warps = BAKE_THREADS / 32;
+    return FIPT_OK;
+}
+
+// Most warps a launch of the resident loop can have (each leaves at most
+// one orphan).
+int serve_loop_warps(int blocks_per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * blocks_per_sm * (BAKE_THREADS / 32);
 }

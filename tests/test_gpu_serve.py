@@ -99,7 +99,9 @@ def test_mixed_requests_equal_standalone_results(setup):
         for g, r in ((got["g_albedo"], ga), (got["g_rough"], gr), (got["g_metal"], gm)):
             assert np.array_equal(g.numpy(), r.cpu().numpy())
     st = srv.stats()
-    assert st["batches"] > 1 and st["max_requests_per_batch"] > 2   # requests share batches
+    # the resident loop ran (its launches are counted as batches) and many
+    # requests had work in flight on the device at once
+    assert st["batches"] >= 1 and st["max_requests_per_batch"] > 2
     assert st["peak_bytes"] <= 256 << 20 and st["bytes_in_use"] == 0
     srv.close()
     F.context().sync_status()
@@ -156,7 +158,7 @@ def test_failed_launch_drains_in_flight_work(setup):
     srv = F.Server(1 << 30, max_batch_rays=1 << 24, chunk_points=8192)
     sid = srv.add_scene(scenes[1])
     qs = [host_queries(F, surface_queries(meshes[1], 60000, seed=70 + i)) for i in range(3)]
-    srv.inject_launch_failure(2)          # the third batch fails to launch
+    srv.inject_launch_failure(2)          # the third device submission fails
     tickets = [srv.submit_bake(sid, q, SIGMA, 32, 32, seed=3, request_id=i) for i, q in enumerate(qs)]
     results = [srv.wait(t, 60.0) for t in tickets]
     assert any(r == 2 for r in results), results      # FIPT_ERR_CUDA reached the requests

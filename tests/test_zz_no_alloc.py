@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 GRID = [0.02, 0.1, 0.25, 0.5, 0.75, 1.0]
 REL = 1e-4   # the render tests' tolerance
-N_MAX = 65536 * 256          # FIPT_NOALLOC_RENDER_MAX_BLOCKS x 256 threads
+N_MAX = 131072 * 128         # FIPT_NOALLOC_RENDER_MAX_BLOCKS x 128 threads
 
 
 def _p(t):
