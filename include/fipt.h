@@ -567,6 +567,16 @@ fipt_status fipt_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t 
  * arrays on the stream).  n >= 1. */
 fipt_status fipt_debug_divide(uint32_t n, const uint32_t* i, int64_t count, uint32_t* out,
                               int32_t on_device, fipt_stream stream);
+/* The server's resident loop on a queue that nothing ever publishes to
+ * (check of its bounded wait; no counterpart in the paper): one block per
+ * SM, every warp takes one item and waits for it; after wait_polls naps
+ * (each at most about 32 microseconds) a warp gives up and the whole
+ * launch leaves.  Blocks the calling thread until the kernel has ended by
+ * itself.  -> *quit = the launch's quit flag (1), *orphans = items the
+ * warps left behind (one per warp), *warps = warps launched, *seconds =
+ * the kernel's duration.  1 <= wait_polls <= 65536. */
+fipt_status fipt_debug_serve_wait_bound(int32_t wait_polls, int32_t* quit, int32_t* orphans,
+                                        int32_t* warps, double* seconds);
 
 #ifdef __cplusplus
 }

@@ -1013,3 +1013,57 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
     delete s;
     return FIPT_OK;
 }
+
+// ---------------------------------------------------------------- check of the loop's bounded wait
+extern "C" fipt_status fipt_debug_serve_wait_bound(int32_t wait_polls, int32_t* quit, int32_t* orphans,
+                                                   int32_t* warps, double* seconds) {
+    FIPT_REQUIRE(quit && orphans && warps && seconds, "NULL output");
+    FIPT_REQUIRE(wait_polls >= 1 && wait_polls <= 65536, "wait_polls must be in [1, 65536]");
+    const int n_warps = serve_loop_warps(1);
+    ServeShared* sh = nullptr;
+    ServeShared* sh_dev = nullptr;
+    BakeChunk* chunks = nullptr;
+    ServeCounters* ctr = nullptr;
+    long long* orph = nullptr;
+    int32_t* ints = nullptr;           // done count, done flag, status
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaHostAlloc(&sh, sizeof(ServeShared), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&sh_dev, sh, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&chunks, sizeof(BakeChunk));
+    if (e == cudaSuccess) e = cudaMalloc(&ctr, sizeof(ServeCounters));
+    if (e == cudaSuccess) e = cudaMalloc(&orph, sizeof(long long) * (size_t)n_warps);
+    if (e == cudaSuccess) e = cudaMalloc(&ints, 3 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    fipt_status r = FIPT_OK;
+    if (e == cudaSuccess) {
+        std::memset(sh, 0, sizeof(ServeShared));
+        e = cudaMemsetAsync(ctr, 0, sizeof(ServeCounters), st);      // nothing published, ever
+        if (e == cudaSuccess) e = cudaMemsetAsync(ints, 0, 3 * sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess)
+            r = launch_serve_bake(chunks, sh_dev, ctr, orph, orph, ints, ints + 1, ints + 2, wait_polls, 1, st, 0);
+        if (e == cudaSuccess && r == FIPT_OK) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess && r == FIPT_OK) e = cudaStreamSynchronize(st);   // the launch ends by itself
+        ServeCounters c{};
+        if (e == cudaSuccess && r == FIPT_OK) e = cudaMemcpy(&c, ctr, sizeof(c), cudaMemcpyDeviceToHost);
+        float ms = 0.0f;
+        if (e == cudaSuccess && r == FIPT_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+        *quit = c.quit;
+        *orphans = c.n_out;
+        *warps = n_warps;
+        *seconds = 1e-3 * ms;
+    }
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(ints);
+    cudaFree(orph);
+    cudaFree(ctr);
+    cudaFree(chunks);
+    if (sh) cudaFreeHost(sh);
+    if (r != FIPT_OK) return r;
+    return e == cudaSuccess ? FIPT_OK : fipt_check_cuda(e, "serve wait-bound check");
+}

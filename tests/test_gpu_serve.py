@@ -177,3 +177,42 @@ def test_failed_launch_drains_in_flight_work(setup):
     # the device is still usable
     F.bake(scenes[1], qs[0][:1000].cuda(), SIGMA, 4, 4)
     F.context().sync_status()
+
+
+def test_loop_wait_is_bounded():
+    """The resident loop on a queue nothing publishes to ends by itself: a
+    warp gives up after its bounded polls and the whole launch leaves, each
+    warp's item recorded for the next launch."""
+    import ctypes
+    from paper_2304_05669_gb300._native import check, lib
+    import paper_2304_05669_gb300 as F
+    F.context()
+    quit_, orphans, warps = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    secs = ctypes.c_double()
+    check(lib().fipt_debug_serve_wait_bound(64, ctypes.byref(quit_), ctypes.byref(orphans),
+                                            ctypes.byref(warps), ctypes.byref(secs)))
+    assert quit_.value == 1
+    assert 1 <= orphans.value <= warps.value
+    assert secs.value < 0.5, secs.value        # 64 naps of at most ~32 us each, with margin
+
+
+def test_relaunched_loop_keeps_results_identical(setup):
+    """Requests that arrive after the loop has stopped for want of work start
+    it again (each launch first runs the items the stopped one held); results
+    stay bit-identical to standalone bakes across the relaunches."""
+    import time
+    F, scenes, meshes = setup
+    srv = F.Server(256 << 20, max_batch_rays=1 << 22, chunk_points=4096)
+    ids = [srv.add_scene(s) for s in scenes]
+    runs = [(0, 3000, 8), (1, 9000, 16), (1, 70, 4), (0, 20000, 8)]
+    for j, (sc, n, spp) in enumerate(runs):
+        qh = host_queries(F, surface_queries(meshes[sc], n, seed=200 + j))
+        t = srv.submit_bake(ids[sc], qh, SIGMA, spp, spp, seed=11, request_id=j)
+        assert srv.wait(t) == 0
+        ref = F.bake(scenes[sc], qh.cuda(), SIGMA, spp, spp, seed=11, request_id=j)
+        for g, r in zip((srv.result(t)["Ld"], srv.result(t)["Ls0"], srv.result(t)["Ls1"]), ref):
+            assert np.array_equal(g.numpy(), r.cpu().numpy())
+        time.sleep(0.05)                   # the loop stops after a millisecond without work
+    assert srv.stats()["batches"] >= len(runs)
+    srv.close()
+    F.context().sync_status()
