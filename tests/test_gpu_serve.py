@@ -216,3 +216,38 @@ def test_relaunched_loop_keeps_results_identical(setup):
     assert srv.stats()["batches"] >= len(runs)
     srv.close()
     F.context().sync_status()
+
+
+def test_scenes_with_sky_and_voxel_cache_serve_identically(setup):
+    """The loop's instances that read an environment map and a voxel radiance
+    cache (scenes that carry them, served side by side with a plain scene)
+    give the same bits as standalone bakes."""
+    F, scenes, meshes = setup
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(12)
+    sky = F.Scene.from_mesh(cornell_box())           # open front: rays leave through it
+    sky.set_environment(torch.from_numpy(rng.uniform(0, 3, (16, 32, 3)).astype(np.float32)).to(dev))
+    vox = F.Scene.from_mesh(meshes[1])
+    qv = surface_queries(meshes[1], 30000, seed=13)
+    L = torch.from_numpy(rng.uniform(0, 2, (30000, 3)).astype(np.float32)).to(dev)
+    vox.set_voxel_cache(vox.voxel_cache(torch.from_numpy(qv["x"]).to(dev), L, 32))
+    both = F.Scene.from_mesh(cornell_box())
+    both.set_environment(torch.from_numpy(rng.uniform(0, 1, (8, 16, 3)).astype(np.float32)).to(dev))
+    qb = surface_queries(cornell_box(), 4000, seed=14)
+    both.set_voxel_cache(both.voxel_cache(torch.from_numpy(qb["x"]).to(dev),
+                                          torch.from_numpy(rng.uniform(0, 2, (4000, 3)).astype(np.float32)).to(dev), 16))
+    trio = [(sky, cornell_box()), (vox, meshes[1]), (both, cornell_box()), (scenes[1], meshes[1])]
+    srv = F.Server(256 << 20, max_batch_rays=1 << 22, chunk_points=2048)
+    ids = [srv.add_scene(s) for s, _ in trio]
+    jobs = []
+    for j, (s, m) in enumerate(trio):
+        qh = host_queries(F, surface_queries(m, 5000 + 1000 * j, seed=300 + j))
+        jobs.append((srv.submit_bake(ids[j], qh, SIGMA, 8, 8, seed=5, request_id=j), s, qh, j))
+    for t, s, qh, j in jobs:
+        assert srv.wait(t) == 0
+        ref = F.bake(s, qh.cuda(), SIGMA, 8, 8, seed=5, request_id=j)
+        got = srv.result(t)
+        for g, r in zip((got["Ld"], got["Ls0"], got["Ls1"]), ref):
+            assert np.array_equal(g.numpy(), r.cpu().numpy())
+    srv.close()
+    F.context().sync_status()
