@@ -19,13 +19,15 @@
 //    taken -- two per resident warp, and at least `max_batch_rays` rays --
 //    in chunks of up to `chunk_points` points: the oldest admitted request
 //    first, up to a quarter of that, then the requests with the least
-//    remaining work, then the oldest again.  A request that arrives while others run has its
-//    chunks published as soon as its inputs are on the device, and its warp
-//    items interleave with theirs without a new launch.  Render requests run
-//    their forward/backward kernels on a stream of their own as soon as they
-//    are admitted; the loop leaves room for them on every SM.
+//    remaining work, then the oldest again.  A request that arrives while
+//    others run has its chunks published as soon as its inputs are on the
+//    device, and its warp items interleave with theirs without a new
+//    launch.  Render requests run their forward/backward kernels on a
+//    stream of their own as soon as they are admitted; the loop leaves room
+//    for one block of each on every SM, and every kernel the server
+//    launches is loaded when the server is created.
 //  * Completion.  When a request's last chunk is done, its outputs are
-//    copied back on the copy stream and its arena space is freed.
+//    copied back on an output stream and its arena space is freed.
 //  * All waits are bounded: the scheduler polls events and flags on the
 //    host, and the loop's warps give up after a bounded number of polls.
 //  * Failure.  A launch that fails, a descriptor copy that fails, or device
@@ -181,9 +183,8 @@ struct Req {
 };
 
 struct Publish {
-    cudaEvent_t ev;
-    int n_chunks;
-    long long warps;
+    cudaEvent_t ev;      // recorded after the publication's copies
+    long long warps;     // warp items published once it has landed
 };
 
 }  // namespace
@@ -455,7 +456,6 @@ void fipt_server::stage_chunks() {
     Publish p;
     cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming);
     cudaEventRecord(p.ev, copy);
-    p.n_chunks = n_staged;
     p.warps = warps_staged;
     publishes.push_back(p);
     n_chunks += (uint64_t)count;
