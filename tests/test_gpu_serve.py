@@ -251,3 +251,28 @@ def test_scenes_with_sky_and_voxel_cache_serve_identically(setup):
             assert np.array_equal(g.numpy(), r.cpu().numpy())
     srv.close()
     F.context().sync_status()
+
+
+def test_ragged_chunks_and_mixed_levels_serve_identically(setup):
+    """Chunks that do not fill their last warp (1000-point chunks), requests
+    of 1, 999, 1001 and 5000 points, and roughness grids of 2, 4 and 6
+    levels in one burst: every warp item finds its own chunk's level count,
+    and every result equals a standalone bake bit for bit."""
+    F, scenes, meshes = setup
+    srv = F.Server(256 << 20, max_batch_rays=1 << 21, chunk_points=1000)
+    sid = srv.add_scene(scenes[1])
+    grids = [[0.1, 0.8], [0.02, 0.3, 0.6, 1.0], SIGMA]
+    jobs = []
+    for j, n in enumerate([1, 999, 1001, 5000, 2500, 31]):
+        g = grids[j % 3]
+        qh = host_queries(F, surface_queries(meshes[1], n, seed=400 + j))
+        jobs.append((srv.submit_bake(sid, qh, g, 8, 4, seed=9, request_id=j), qh, g, j))
+    for t, qh, g, j in jobs:
+        assert srv.wait(t) == 0
+        ref = F.bake(scenes[1], qh.cuda(), g, 8, 4, seed=9, request_id=j)
+        got = srv.result(t)
+        assert got["Ls0"].shape[1] == len(g)
+        for a, b in zip((got["Ld"], got["Ls0"], got["Ls1"]), ref):
+            assert np.array_equal(a.numpy(), b.cpu().numpy())
+    srv.close()
+    F.context().sync_status()
