@@ -437,32 +437,38 @@ fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* 
  * pattern around the bake; the paper runs one bake per scene offline).
  *
  * fipt_server_create allocates one device arena of hbm_budget bytes (the
- * admission budget), a work queue (device descriptors plus a host-mapped
- * control block and per-chunk done flags), three streams, and starts a host
+ * admission budget), two work queues (device descriptors plus a
+ * host-mapped control block and per-chunk done flags), and starts a host
  * scheduler thread.  Requests are admitted in arrival order as arena space
- * frees up.  Bakes run in a device-resident loop: one kernel keeps warps
- * resident on every SM (as many blocks of 64 threads as leave room for a
- * block of each render kernel: 28 of 32 on GB300), and they take warp items (32 points of one
- * chunk, one lobe) in the order the scheduler publishes chunks, one
- * atomic add per item.  The
- * scheduler keeps warp items published ahead of the loop and not yet
- * taken -- two per resident warp, and at least max_batch_rays rays -- in
- * chunks of up to chunk_points points: the oldest request first, up to a
- * quarter of that, then the requests with the least remaining work -- so
- * a request that arrives while others run joins their warps on the device
- * without a new launch.  The scheduler stops the loop after a millisecond
- * without work and starts it again when new work is published.  Scene environment maps and voxel caches must be set before a
- * scene is added.  Render requests run their forward and backward kernels
- * on their own stream as soon as they are admitted.
- * A chunk keeps the request-local Philox counters (point_base = its offset
- * in the request), so every result is bit-identical to a standalone
- * fipt_bake / fipt_render_fwd / fipt_render_bwd of the same request.
+ * frees up.  Requests run in two device-resident loops, kernels whose
+ * warps stay resident on every SM and take warp items as the scheduler
+ * publishes them, without a launch per request:
+ *  - the bake loop (all block slots of 64 threads but two per SM): warp
+ *    items of 32 points of one chunk and one lobe, one atomic add each.
+ *    The scheduler keeps bake items published ahead of the loop and not
+ *    yet taken -- two per resident warp, and at least max_batch_rays rays
+ *    -- in chunks of up to chunk_points points: the oldest request first,
+ *    up to a quarter of that, then the requests with the least remaining
+ *    work -- so a request that arrives while others run joins their warps
+ *    on the device;
+ *  - the render loop (two block slots per SM): a render request
+ *    (Eq. 5, 8, 14 and the loss gradient for an upstream gradient of 1)
+ *    is published whole, in items of 512 rows, and starts as soon as its
+ *    inputs are on the device, whatever the bake loop holds.
+ * The scheduler stops the loops after a millisecond without work and
+ * starts them again when new work is published.  Scene environment maps
+ * and voxel caches must be set before a scene is added.
+ * A bake chunk keeps the request-local Philox counters (point_base = its
+ * offset in the request) and a render item sums the loss in the render
+ * kernels' order, so every result is bit-identical to a standalone
+ * fipt_bake / fipt_render_fwd_grad of the same request.
  * All host buffers of a request must stay valid until it completes; pinned
  * (page-locked) buffers let copies overlap compute.  Every wait is bounded:
- * the scheduler polls events and the mapped flags; a loop warp that has
+ * the scheduler polls events and the mapped flags; a bake warp that has
  * polled the published count about half a second in vain ends the launch
  * (its item, like every item a stopped launch holds, runs first in the
- * next launch). */
+ * next launch), and a render warp that has found no render work for as
+ * long ends the render launch. */
 #define FIPT_REQ_BAKE 0
 #define FIPT_REQ_RENDER 1
 
@@ -530,16 +536,16 @@ fipt_status fipt_server_times(fipt_server* srv, uint64_t ticket, double* t_submi
 fipt_status fipt_server_release(fipt_server* srv, uint64_t ticket);
 fipt_status fipt_server_get_stats(fipt_server* srv, fipt_server_stats* out);
 /* Failure handling.  When a submission to the device fails (a descriptor
- * copy, a start of the loop, a render launch) or device work fails, the
- * server tells the loop to stop, starts no new work, and every unfinished
+ * copy, a start of a loop) or device work fails, the
+ * server tells the loops to stop, starts no new work, and every unfinished
  * request ends with that error (its *result) -- each one only after none
  * of its input copy, kernels or output copies is still queued, so a caller
  * whose wait returns may free or reuse the request's host buffers at once.
  * Requests already copying their outputs keep their own results.
  * Test hook (the paper has no counterpart): after the next after_launches
- * device submissions (a publication of chunk descriptors, a start of the
- * loop, a render request's kernels) the following one fails with
- * FIPT_ERR_CUDA on the host instead of reaching the device. */
+ * device submissions (a publication of bake or render descriptors, a start
+ * of either loop) the following one fails with FIPT_ERR_CUDA on the host
+ * instead of reaching the device. */
 fipt_status fipt_server_inject_launch_failure(fipt_server* srv, int64_t after_launches);
 /* Cancels requests not yet admitted (result FIPT_ERR_NOT_FOUND), drains
  * admitted work, joins the scheduler and frees the arena. */

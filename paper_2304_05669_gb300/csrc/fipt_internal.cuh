@@ -118,33 +118,57 @@ struct alignas(256) BakeChunk {
 // Host-mapped control block of the server's resident bake loop.
 struct ServeShared {
     long long taken;       // one past a recently taken warp item (device: relaxed store; the host's estimate)
-    int stop;              // nonzero: every warp leaves after the item it holds
-    int pad;
+    int stop;              // nonzero: every bake-loop warp leaves after the item it holds
+    int stop_r;            // nonzero: every render-loop warp leaves after its item
 };
 
-// Device counters of the resident bake loop.  `pub` is written only by the
-// host's copy stream, after the descriptors it covers (stream order):
-// (published warp items << FIPT_PUB_CHUNK_BITS) | published descriptors.
+// A render request for the server's resident loop (Eq. 5, 8, 14 and the
+// loss gradient over rows [0, n) of its slice), in RENDER_ITEM_ROWS-row
+// warp items.  256-byte slots, like BakeChunk.
+constexpr int FIPT_RENDER_ITEM_ROWS = 512;
+struct alignas(256) RenderChunk {
+    const float *Ld, *Ls0, *Ls1;                 // the request's table rows
+    const float *albedo, *rough, *metal, *Lgt;   // its inputs (device copies)
+    float *Lr, *g_albedo, *g_rough, *g_metal;    // its outputs
+    double* partial;                             // [ceil(n / 128)] loss partials
+    double* loss;
+    int64_t n;                                   // rows
+    int64_t item_begin;                          // first render item of the chunk
+    int K;
+    float grid[FIPT_MAX_K];
+};
+
+// Device counters of the resident loops.  `pub` and `pub_r` are written only
+// by the host's copy stream, each after the descriptors it covers (stream
+// order): (published items << FIPT_PUB_CHUNK_BITS) | published descriptors,
+// for bake and render items.
 constexpr int FIPT_PUB_CHUNK_BITS = 17;
 struct ServeCounters {
-    unsigned long long head;   // warp items handed out
-    long long pub;             // what is published (see above)
+    unsigned long long head;   // bake items handed out
+    long long pub;             // what is published of the bake queue (see above)
+    unsigned long long head_r; // render items handed out
+    long long pub_r;           // what is published of the render queue
     int take_in;               // orphans of the previous launch taken
     int n_in;                  // orphans of the previous launch
     int n_out;                 // orphans this launch leaves
-    int quit;                  // nonzero: a warp gave up waiting; the whole launch leaves
+    int quit;                  // nonzero: a bake warp gave up waiting; the whole bake launch leaves
+    int quit_r;                // nonzero: a render warp found no work for long; the render launch leaves
+    int pad;
 };
 
-// The server's resident bake loop (see k_serve_bake).
+// The server's resident bake loop (see k_serve_bake) and render loop (see
+// k_serve_render).
 fipt_status launch_serve_bake(const BakeChunk* d_chunks, ServeShared* sh, ServeCounters* ctr,
                               const long long* orphan_in, long long* orphan_out, int32_t* done_count,
                               int32_t* done_flag, int32_t* status, int wait_polls, int blocks_per_sm,
                               cudaStream_t st, int flags);
+fipt_status launch_serve_render(const RenderChunk* d_rchunks, ServeShared* sh, ServeCounters* ctr, int32_t* rdone,
+                                int32_t* rflag, int wait_polls, int blocks_per_sm, cudaStream_t st);
+// Blocks of the loops that fit on one SM (the least over their kernels,
+// all of 64 threads; loads them too).
+fipt_status serve_loop_blocks_per_sm(int* blocks);
 int serve_loop_warps(int blocks_per_sm);
-// Registers per warp (allocated) and warps per block of the loop's kernels
-// and of the render kernels (the largest of each); loads those kernels too.
-fipt_status serve_kernels_footprint(int* warp_regs, int* warps);
-fipt_status render_kernels_footprint(int* warp_regs, int* warps);
+
 
 fipt_status fipt_set_error(fipt_status s, const char* fmt, ...);
 void fipt_count_launch();

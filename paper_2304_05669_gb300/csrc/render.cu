@@ -10,96 +10,18 @@
 #include <mutex>
 
 #include "fipt_internal.cuh"
+#include "render_math.cuh"
 
 namespace {
 
-constexpr int RENDER_THREADS = 128;   // small blocks fit beside the serving loop's resident blocks
-
-struct Grid {
-    int K;
-    float s[FIPT_MAX_K];
-};
-
-struct Lerp {
-    int i;
-    float t;
-    float inv_w;
-    bool clamped;
-};
-
-__device__ __forceinline__ Lerp lerp_of(float rough, const Grid& g) {
-    Lerp l;
-    const float lo = g.s[0], hi = g.s[g.K - 1];
-    l.clamped = rough < lo || rough > hi;
-    const float s = fminf(fmaxf(rough, lo), hi);
-    int i = 0;
-#pragma unroll
-    for (int k = 1; k < FIPT_MAX_K - 1; ++k)
-        if (k <= g.K - 2 && g.s[k] <= s) i = k;
-    l.i = i;
-    const float w = g.s[i + 1] - g.s[i];
-    l.inv_w = 1.0f / w;
-    l.t = (s - g.s[i]) / w;
-    return l;
-}
-
-// y^(1/2.4) for y > 0.0031308 as 2^(log2(y) / 2.4): with |log2 y| < 8.4
-// the exponent is off by at most a few 1e-7, so is the power (relative).
-__device__ __forceinline__ float srgb_pow(float y) { return exp2f(log2f(y) * (1.0f / 2.4f)); }
-
-// Gamma of Eq. 14: sRGB transfer curve of y = log(1 + max(x, 0)).
-__device__ __forceinline__ float tonemap(float x) {
-    const float y = log1pf(fmaxf(x, 0.0f));
-    return y <= 0.0031308f ? 12.92f * y : 1.055f * srgb_pow(y) - 0.055f;
-}
-
-// Gamma(x) and its derivative dt from one logarithm and one power:
-// d/dx of 1.055 y^(1/2.4) is (1.055 / 2.4) y^(1/2.4) / y / (1 + x); 0 for x < 0.
-__device__ __forceinline__ float tonemap_d(float x, float& dt) {
-    const float y = log1pf(fmaxf(x, 0.0f));
-    if (y <= 0.0031308f) {
-        dt = x < 0.0f ? 0.0f : 12.92f / (1.0f + x);
-        return 12.92f * y;
-    }
-    const float pw = srgb_pow(y);
-    dt = (1.055f / 2.4f) * (pw / y) / (1.0f + x);
-    return 1.055f * pw - 0.055f;
-}
-
-struct PointShade {
-    float Ld[3], S0[3], S1[3], dS0[3], dS1[3];
-    float a[3], m;
-    Lerp l;
-};
-
-__device__ __forceinline__ void load_point(int64_t p, int K, const Grid& g, const float* Ld,
-                                           const float* Ls0, const float* Ls1, const float* albedo,
-                                           const float* rough, const float* metal, PointShade& P,
-                                           bool with_slopes) {
-    P.l = lerp_of(rough[p], g);
-    const float t = P.l.t;
-    const float* s0 = Ls0 + (p * K + P.l.i) * 3;
-    const float* s1 = Ls1 + (p * K + P.l.i) * 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        P.Ld[c] = Ld[3 * p + c];
-        const float a0 = s0[c], b0 = s0[3 + c], a1 = s1[c], b1 = s1[3 + c];
-        P.S0[c] = (1.0f - t) * a0 + t * b0;
-        P.S1[c] = (1.0f - t) * a1 + t * b1;
-        if (with_slopes) {
-            P.dS0[c] = (b0 - a0) * P.l.inv_w;
-            P.dS1[c] = (b1 - a1) * P.l.inv_w;
-        }
-        P.a[c] = albedo[3 * p + c];
-    }
-    P.m = metal[p];
-}
+using namespace fipt_render;
+constexpr int RENDER_THREADS = RENDER_BLOCK;   // one loss partial per block
 
 // The block's loss to partial[blockIdx.x]: a point's three channels and a
 // warp's 32 points are summed in float32 (fixed shuffle order), the
 // block's warps in FP64 in order.  Every thread of the block calls it.
 __device__ __forceinline__ void block_loss(float loss, double* partial) {
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_down_sync(0xffffffffu, loss, o);
+    loss = warp_sum_down(loss);
     __shared__ double ws[RENDER_THREADS / 32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = (double)loss;
     __syncthreads();
@@ -141,12 +63,12 @@ k_render_fwd(const float* __restrict__ Ld, const float* __restrict__ Ls0, const 
 }
 
 // One block of SUM_THREADS sums the per-block partials in a fixed order.
-constexpr int SUM_THREADS = 128;
+constexpr int SUM_THREADS = RENDER_SUM_THREADS;
 __global__ void __launch_bounds__(SUM_THREADS) k_sum_partials(const double* __restrict__ partial, int64_t n,
                                                              double* __restrict__ out) {
     double s = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += SUM_THREADS) s += partial[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    s = warp_sum_down(s);
     __shared__ double ws[SUM_THREADS / 32];
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -198,30 +120,9 @@ k_render_fwd_grad(const float* __restrict__ Ld, const float* __restrict__ Ls0, c
                   float* __restrict__ g_albedo, float* __restrict__ g_rough, float* __restrict__ g_metal) {
     const int64_t p = blockIdx.x * (int64_t)RENDER_THREADS + threadIdx.x;
     float loss = 0.0f;
-    if (p < N) {
-        PointShade P;
-        load_point(p, g.K, g, Ld, Ls0, Ls1, albedo, rough, metal, P, true);
-        const bool on = !mask || mask[p];
-        const float m = P.m;
-        float gs = 0.0f, gm = 0.0f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float a = P.a[c];
-            const float kd = a * (1.0f - m);
-            const float ks = 0.04f * (1.0f - m) + a * m;
-            const float lr = kd * P.Ld[c] + ks * P.S0[c] + P.S1[c];
-            Lr[3 * p + c] = lr;
-            float dt;
-            const float d = tonemap_d(lr, dt) - tonemap(Lgt[3 * p + c]);
-            if (on) loss += d * d;
-            const float gc = on ? 2.0f * d * dt : 0.0f;
-            g_albedo[3 * p + c] = gc * ((1.0f - m) * P.Ld[c] + m * P.S0[c]);
-            gm += gc * (-a * P.Ld[c] + (a - 0.04f) * P.S0[c]);
-            gs += gc * (ks * P.dS0[c] + P.dS1[c]);
-        }
-        g_rough[p] = P.l.clamped ? 0.0f : gs;
-        g_metal[p] = gm;
-    }
+    if (p < N)
+        loss = render_point_fwd_grad(p, g, Ld, Ls0, Ls1, albedo, rough, metal, Lgt, mask, Lr, g_albedo, g_rough,
+                                     g_metal);
     block_loss(loss, partial);
 }
 
@@ -377,24 +278,6 @@ extern "C" fipt_status fipt_render_grad_scale(int64_t N, const double* grad_loss
     FIPT_LAUNCH(k_render_grad_scale, grid, RENDER_THREADS, 0, static_cast<cudaStream_t>(stream), N, grad_loss,
                 g_albedo, g_rough, g_metal);
     FIPT_LAUNCHED("render_grad_scale");
-    return FIPT_OK;
-}
-
-// The most registers a warp of any render kernel holds (as the SM allocates
-// them: in units of 256) and the most warps in one of their blocks.
-// Querying the attributes also loads the kernels, so a server never loads
-// one while its resident loop holds the GPU.
-fipt_status render_kernels_footprint(int* warp_regs, int* warps) {
-    const void* fns[] = {(const void*)k_render_fwd, (const void*)k_render_bwd, (const void*)k_sum_partials};
-    const int nthreads[] = {RENDER_THREADS, RENDER_THREADS, SUM_THREADS};
-    *warp_regs = 0;
-    *warps = 0;
-    for (int i = 0; i < 3; ++i) {
-        cudaFuncAttributes at;
-        FIPT_CUDA(cudaFuncGetAttributes(&at, fns[i]));
-        *warp_regs = std::max(*warp_regs, (at.numRegs * 32 + 255) / 256 * 256);
-        *warps = std::max(*warps, (nthreads[i] + 31) / 32);
-    }
     return FIPT_OK;
 }
 

@@ -1,39 +1,45 @@
-// Serving runtime: a device-resident request loop for bakes, with
-// continuous batching over several resident scenes on one GPU.
+// Serving runtime: device-resident request loops for bakes and renders,
+// with continuous batching over several resident scenes on one GPU.
 //
 //  * Admission.  The server owns one device arena of `hbm_budget` bytes.  A
 //    request is admitted (in arrival order) when its device buffers fit in
 //    the arena; one larger than the whole budget completes at once with
 //    FIPT_ERR_BUDGET.  Inputs are copied in on a copy stream.
-//  * The resident loop.  One kernel (k_serve_bake) keeps warps resident on
-//    every SM; they take warp items (32 points of one chunk, one lobe) from
-//    a device counter in the order the host publishes them and bake each
-//    exactly as a standalone fipt_bake would (chunks keep request-local
-//    Philox counters), so a result is bit-identical alone and in any mix.
-//    The warp that finishes a chunk raises its flag in host-mapped memory.
-//    Warps without work poll with short naps.  The loop ends as a whole:
-//    the scheduler stops it after a millisecond without work (or on
-//    failure), and starts it again when new work is published.
-//  * Continuous batching.  The scheduler thread keeps warp items (32
-//    points of one chunk, one lobe) published ahead of the loop and not yet
-//    taken -- two per resident warp, and at least `max_batch_rays` rays --
-//    in chunks of up to `chunk_points` points: the oldest admitted request
-//    first, up to a quarter of that, then the requests with the least
-//    remaining work, then the oldest again.  A request that arrives while
-//    others run has its chunks published as soon as its inputs are on the
-//    device, and its warp items interleave with theirs without a new
-//    launch.  Render requests run their forward/backward kernels on a
-//    stream of their own as soon as they are admitted; the loop leaves room
-//    for one block of each on every SM, and every kernel the server
-//    launches is loaded when the server is created.
+//  * The bake loop.  One kernel (k_serve_bake) keeps warps resident on all
+//    block slots of every SM but kRenderBlocksPerSM; they take warp items
+//    (32 points of one chunk, one lobe) from a device counter in the order
+//    the host publishes them and bake each exactly as a standalone
+//    fipt_bake would (chunks keep request-local Philox counters), so a
+//    result is bit-identical alone and in any mix.  The warp that finishes
+//    a chunk raises its flag in host-mapped memory.
+//  * The render loop.  A second kernel (k_serve_render) on the remaining
+//    block slots takes render items (512 rows of one request) as soon as
+//    they are published and computes k_render_fwd_grad's values and loss
+//    partials; the warp that finishes a request sums its loss in the render
+//    kernels' order.  It is a kernel of its own because render code inside
+//    the bake loop cost the bake walk 7 % through register allocation.
+//  * Both loops end as a whole: the scheduler stops each (its own flag)
+//    after a millisecond without work or on failure, and starts it again
+//    when new work is published; a bake warp that waits about half a second
+//    in vain ends the bake launch, a render warp that finds no render work
+//    for as long ends the render launch.
+//  * Continuous batching.  The scheduler thread keeps bake items published
+//    ahead of the loop and not yet taken -- two per resident warp, and at
+//    least `max_batch_rays` rays -- in chunks of up to `chunk_points`
+//    points: the oldest admitted request first, up to a quarter of that,
+//    then the requests with the least remaining work, then the oldest
+//    again.  A request that arrives while others run has its chunks
+//    published as soon as its inputs are on the device, and its warp items
+//    interleave with theirs without a new launch.  Render requests are
+//    published whole as soon as they are admitted.
 //  * Completion.  When a request's last chunk is done, its outputs are
 //    copied back on an output stream and its arena space is freed.
 //  * All waits are bounded: the scheduler polls events and flags on the
-//    host, and the loop's warps give up after a bounded number of polls.
+//    host, and the loops' warps give up after a bounded number of polls.
 //  * Failure.  A launch that fails, a descriptor copy that fails, or device
-//    work that fails stops the server: the loop is told to stop, no new work
-//    starts, and every unfinished request ends with that error once none of
-//    its copies or kernels is still queued.
+//    work that fails stops the server: the loops are told to stop, no new
+//    work starts, and every unfinished request ends with that error once
+//    none of its copies or kernels is still queued.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -59,7 +65,8 @@ size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr int kQueue = 1 << 16;          // chunk descriptors per queue epoch
 static_assert(kQueue < (1 << FIPT_PUB_CHUNK_BITS), "descriptor count must fit beside the item count");
 constexpr int kWaitPolls = 1 << 14;     // naps (about half a second) before a waiting warp ends the launch
-constexpr double kIdleStop = 1e-3;       // seconds the loop may idle before the scheduler stops it
+constexpr double kIdleStop = 1e-3;       // seconds the loops may idle before the scheduler stops them
+constexpr int kRenderBlocksPerSM = 2;    // block slots per SM of the render loop (the bake loop has the rest)
 
 }  // namespace
 
@@ -178,13 +185,13 @@ struct Req {
     size_t ws_bytes = 0;
     int64_t next = 0;             // bake: next point not yet in a chunk
     int chunks_open = 0;          // bake: chunks staged and not yet done
-    cudaEvent_t h2d = nullptr, d2h = nullptr, run = nullptr;
+    cudaEvent_t h2d = nullptr, d2h = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
 struct Publish {
     cudaEvent_t ev;      // recorded after the publication's copies
-    long long warps;     // warp items published once it has landed
+    long long warps;     // bake items published once it has landed (-1: a render publication)
 };
 
 }  // namespace
@@ -194,10 +201,11 @@ struct fipt_server {
     size_t budget = 0;
     int64_t lookahead_rays = 0, chunk_points = 0;
     int64_t lookahead_items = 0;               // warp items kept published and not yet taken
-    int loop_blocks_per_sm = 0;                // resident loop blocks per SM (room left for a render block)
+    int loop_blocks_per_sm = 0;                // resident bake-loop blocks per SM
+    int32_t* zero_host = nullptr;              // pinned 0, copied to device flags by the copy engines
     char* arena_dev = nullptr;
     fipt_arena* arena = nullptr;
-    cudaStream_t loop = nullptr, copy = nullptr, d2h = nullptr, render = nullptr;
+    cudaStream_t loop = nullptr, loop_r = nullptr, copy = nullptr, d2h = nullptr;
     int32_t* status = nullptr;                 // device status word of this server
     int32_t* status_host = nullptr;            // pinned snapshot, copied with each request's outputs
     // the resident loop's queue
@@ -223,16 +231,28 @@ struct fipt_server {
     size_t first_untaken = 0;                  // first chunk with items the loop has not taken
     long long taken_seen = 0;                  // most warp items the loop was seen to have taken
     std::vector<int> open_chunks;              // staged, not yet done
+    // the render queue (one chunk per render request)
+    RenderChunk* r_dev = nullptr;
+    RenderChunk* r_host = nullptr;             // pinned staging
+    long long* pubr_host = nullptr;            // pinned values of ctr->pub_r
+    int32_t* rflag_host = nullptr;             // host-mapped per-chunk done flags
+    int32_t* rflag_dev = nullptr;
+    int32_t* rdone_dev = nullptr;              // render items done per chunk
+    int n_rstaged = 0, n_rpub = 0;
+    long long ritems_staged = 0;
+    bool published_r = false;                  // a render publication of this epoch has landed
+    std::vector<uint64_t> rchunk_req;          // owner of each staged render chunk
+    std::vector<int> open_rchunks;
     std::deque<Publish> publishes;             // descriptor copies not yet published
-    cudaEvent_t loop_done = nullptr, copy_mark = nullptr;
-    bool loop_running = false;
+    cudaEvent_t loop_done = nullptr, loop_r_done = nullptr, copy_mark = nullptr;
+    bool loop_running = false, loop_r_running = false;
     double idle_since = -1.0;                  // when the running loop last ran out of work
     std::vector<fipt_scene*> scenes;
     std::vector<Table> tables;
     std::map<uint64_t, Req*> reqs;
     std::deque<uint64_t> pending;              // arrival order
     std::vector<uint64_t> active;              // admitted bakes with points not yet staged (admission order)
-    std::vector<uint64_t> renders;             // render requests whose kernels are queued
+    std::deque<uint64_t> renders;              // admitted render requests not yet staged
     std::vector<uint64_t> copying;
     uint64_t next_ticket = 1;
     // statistics
@@ -247,7 +267,8 @@ struct fipt_server {
 
     void run();
     bool admit(Req* q);
-    void launch_render(Req* q);
+    void stage_renders();
+    void complete_empty_render(Req* q);
     void stage_chunks();
     void untaken(int64_t* items, int64_t* rays);
     void publish_landed();
@@ -256,6 +277,7 @@ struct fipt_server {
     void finish_copies();
     void maybe_reset_epoch();
     void launch_loop();
+    void launch_render_loop();
     void stop_idle_loop();
     void drain_after_fatal();
     void set_fatal(fipt_status st, const char* msg);
@@ -321,28 +343,66 @@ bool fipt_server::admit(Req* q) {
     return true;
 }
 
-// A render request's forward and backward kernels, on the render stream
-// once its inputs are on the device.
-void fipt_server::launch_render(Req* q) {
-    if (fail_after >= 0 && fail_after-- == 0) {
+// Publishes the admitted render requests, one chunk each.  The loop takes
+// a render item before any bake item, so a render request starts as soon
+// as warps finish the items they hold.  Its descriptor goes to the device
+// on the copy stream after its input copies.
+void fipt_server::stage_renders() {
+    const int first = n_rstaged;
+    while (!renders.empty() && n_rstaged < kQueue) {
+        Req* q = reqs[renders.front()];
+        renders.pop_front();
+        const Table& tb = tables[q->r.target];
+        const size_t row = (size_t)q->r.first;
+        RenderChunk& C = r_host[n_rstaged];
+        C.Ld = tb.Ld + row * 3;
+        C.Ls0 = tb.Ls0 + row * tb.K * 3;
+        C.Ls1 = tb.Ls1 + row * tb.K * 3;
+        C.albedo = q->da;
+        C.rough = q->dr;
+        C.metal = q->dm;
+        C.Lgt = q->dLgt;
+        C.Lr = q->dLr;
+        C.g_albedo = q->dga;
+        C.g_rough = q->dgr;
+        C.g_metal = q->dgm;
+        C.partial = static_cast<double*>(q->dws);
+        C.loss = q->dloss;
+        C.n = q->r.n;
+        C.item_begin = ritems_staged;
+        C.K = tb.K;
+        for (int k = 0; k < FIPT_MAX_K; ++k) C.grid[k] = tb.grid[k];
+        ritems_staged += (q->r.n + FIPT_RENDER_ITEM_ROWS - 1) / FIPT_RENDER_ITEM_ROWS;
+        rchunk_req.push_back(q->ticket);
+        open_rchunks.push_back(n_rstaged);
+        q->state = LAUNCHED;
+        ++n_rstaged;
+    }
+    const int count = n_rstaged - first;
+    if (count == 0) return;
+    if (fail_after >= 0 && fail_after-- == 0) {    // injected by fipt_server_inject_launch_failure
         set_fatal(FIPT_ERR_CUDA, "injected launch failure");
         return;
     }
-    cudaStreamWaitEvent(render, q->h2d, 0);
-    const Table& tb = tables[q->r.target];
-    const size_t row = (size_t)q->r.first;
-    const float* Ld = tb.Ld + row * 3;
-    const float* Ls0 = tb.Ls0 + row * tb.K * 3;
-    const float* Ls1 = tb.Ls1 + row * tb.K * 3;
-    fipt_status st = fipt_render_fwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm, q->dLgt,
-                                     nullptr, q->dLr, q->dloss, q->dws, q->ws_bytes, render);
-    if (st == FIPT_OK)
-        st = fipt_render_bwd(Ld, Ls0, Ls1, q->r.n, tb.K, tb.grid, q->da, q->dr, q->dm, q->dLgt, nullptr,
-                             nullptr, q->dga, q->dgr, q->dgm, render);
-    if (st != FIPT_OK) q->result = st;
-    cudaEventRecord(q->run, render);
-    q->state = LAUNCHED;
-    renders.push_back(q->ticket);
+    cudaMemcpyAsync(r_dev + first, r_host + first, sizeof(RenderChunk) * (size_t)count, cudaMemcpyHostToDevice,
+                    copy);
+    pubr_host[n_rpub] = (ritems_staged << FIPT_PUB_CHUNK_BITS) | n_rstaged;
+    cudaMemcpyAsync(&ctr->pub_r, pubr_host + n_rpub, sizeof(long long), cudaMemcpyHostToDevice, copy);
+    ++n_rpub;
+    Publish p;
+    cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming);
+    cudaEventRecord(p.ev, copy);
+    p.warps = -1;
+    publishes.push_back(p);
+}
+
+// A render request of no rows: its loss is 0 and nothing runs.
+void fipt_server::complete_empty_render(Req* q) {
+    if (q->r.loss) *q->r.loss = 0.0;
+    arena->release(q->off, q->bytes);
+    q->state = DONE;
+    q->t_done = now_s();
+    cv_done.notify_all();
 }
 
 // Warp items (and their rays) staged but not yet taken by the loop.  The
@@ -476,14 +536,16 @@ void fipt_server::publish_landed() {
             set_fatal(FIPT_ERR_CUDA, "descriptor copy failed");
             return;
         }
-        published = p.warps;
+        if (p.warps < 0) published_r = true;
+        else published = p.warps;
         cudaEventDestroy(p.ev);
         publishes.pop_front();
     }
 }
 
-// Chunks whose flags the loop has raised: a request whose last chunk is
-// done gets its outputs copied back.
+// Chunks whose flags the loop has raised: a bake request whose last chunk
+// is done, and a render request whose chunk is, get their outputs copied
+// back.
 void fipt_server::collect_chunks() {
     for (size_t i = 0; i < open_chunks.size();) {
         const int c = open_chunks[i];
@@ -493,6 +555,13 @@ void fipt_server::collect_chunks() {
         rays += (uint64_t)chunk_rays[c];
         Req* q = reqs[chunk_req[c]];
         if (--q->chunks_open == 0 && q->next >= q->r.n) retire(q);
+    }
+    for (size_t i = 0; i < open_rchunks.size();) {
+        const int c = open_rchunks[i];
+        if (__atomic_load_n(rflag_host + c, __ATOMIC_ACQUIRE) == 0) { ++i; continue; }
+        open_rchunks[i] = open_rchunks.back();
+        open_rchunks.pop_back();
+        retire(reqs[rchunk_req[c]]);
     }
 }
 
@@ -508,7 +577,6 @@ void fipt_server::retire(Req* q) {
             cudaMemcpyAsync(q->r.Ls1, q->dLs1, n * K * 12, cudaMemcpyDeviceToHost, d2h);
         }
     } else {
-        cudaStreamWaitEvent(d2h, q->run, 0);
         if (n) {
             if (q->r.Lr) cudaMemcpyAsync(q->r.Lr, q->dLr, n * 12, cudaMemcpyDeviceToHost, d2h);
             if (q->r.loss) cudaMemcpyAsync(q->r.loss, q->dloss, 8, cudaMemcpyDeviceToHost, d2h);
@@ -524,17 +592,6 @@ void fipt_server::retire(Req* q) {
 }
 
 void fipt_server::finish_copies() {
-    for (size_t i = 0; i < renders.size();) {
-        Req* q = reqs[renders[i]];
-        const cudaError_t e = cudaEventQuery(q->run);
-        if (e == cudaErrorNotReady) { ++i; continue; }
-        renders.erase(renders.begin() + (long)i);
-        if (e != cudaSuccess) {
-            set_fatal(FIPT_ERR_CUDA, "render kernels failed");
-            return;
-        }
-        retire(q);
-    }
     for (size_t i = 0; i < copying.size();) {
         Req* q = reqs[copying[i]];
         if (cudaEventQuery(q->d2h) == cudaSuccess) {
@@ -554,13 +611,22 @@ void fipt_server::finish_copies() {
 // Starts a new queue epoch once every staged chunk is done and the loop
 // has left: counters back to zero on the device and in the mapped block.
 void fipt_server::maybe_reset_epoch() {
-    if (n_staged == 0 || loop_running || !open_chunks.empty() || !publishes.empty()) return;
+    if ((n_staged == 0 && n_rstaged == 0) || loop_running || loop_r_running || !open_chunks.empty() ||
+        !open_rchunks.empty() || !publishes.empty())
+        return;
     std::memset(flag_host, 0, sizeof(int32_t) * (size_t)n_staged);
+    std::memset(rflag_host, 0, sizeof(int32_t) * (size_t)n_rstaged);
     // on the copy stream, ahead of the next epoch's publications
     cudaMemsetAsync(ctr, 0, sizeof(ServeCounters), copy);
-    cudaMemsetAsync(done_dev, 0, sizeof(int32_t) * (size_t)n_staged, copy);
+    if (n_staged) cudaMemsetAsync(done_dev, 0, sizeof(int32_t) * (size_t)n_staged, copy);
+    if (n_rstaged) cudaMemsetAsync(rdone_dev, 0, sizeof(int32_t) * (size_t)n_rstaged, copy);
     published = 0;
     n_pub = 0;
+    published_r = false;
+    n_rstaged = 0;
+    n_rpub = 0;
+    ritems_staged = 0;
+    rchunk_req.clear();
     __atomic_store_n(&sh->taken, 0LL, __ATOMIC_RELAXED);
     n_staged = 0;
     warps_staged = 0;
@@ -606,23 +672,56 @@ void fipt_server::launch_loop() {
     ++n_launches;
 }
 
-// Stops the running loop once it has had no work for kIdleStop seconds, so
-// its resident blocks do not hold the SMs while the server is idle.
+// Starts the render loop when it is not running and published render work
+// waits (its warps leave when they find none for a while).  Its quit flag
+// is cleared by a copy, not a memset kernel: the bake loop may hold every
+// other block slot.
+void fipt_server::launch_render_loop() {
+    if (loop_r_running || open_rchunks.empty() || !published_r) return;
+    if (fail_after >= 0 && fail_after-- == 0) {
+        set_fatal(FIPT_ERR_CUDA, "injected launch failure");
+        return;
+    }
+    cudaEventRecord(copy_mark, copy);
+    cudaStreamWaitEvent(loop_r, copy_mark, 0);
+    cudaMemcpyAsync(&ctr->quit_r, zero_host, sizeof(int32_t), cudaMemcpyHostToDevice, loop_r);
+    // each loop has its own stop flag, cleared only when that loop has left
+    // entirely (a bake warp that saw its flag cleared while the others left
+    // would stay resident alone)
+    __atomic_store_n(&sh->stop_r, 0, __ATOMIC_RELAXED);   // ordered before the launch by the launch itself
+    idle_since = -1.0;
+    const fipt_status st = launch_serve_render(r_dev, sh_dev, ctr, rdone_dev, rflag_dev, kWaitPolls,
+                                               kRenderBlocksPerSM, loop_r);
+    if (st != FIPT_OK) {
+        set_fatal(st, fipt_last_error());
+        return;
+    }
+    cudaEventRecord(loop_r_done, loop_r);
+    loop_r_running = true;
+}
+
+// Stops the running loops once they have had no work for kIdleStop seconds,
+// so their resident blocks do not hold the SMs while the server is idle.
 void fipt_server::stop_idle_loop() {
-    if (!loop_running || !open_chunks.empty() || !publishes.empty()) {
+    if ((!loop_running && !loop_r_running) || !open_chunks.empty() || !open_rchunks.empty() ||
+        !publishes.empty()) {
         idle_since = -1.0;
         return;
     }
     const double t = now_s();
     if (idle_since < 0.0) idle_since = t;
-    else if (t - idle_since > kIdleStop) __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);
+    else if (t - idle_since > kIdleStop) {
+        __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);
+        __atomic_store_n(&sh->stop_r, 1, __ATOMIC_RELEASE);
+    }
 }
 
 void fipt_server::set_fatal(fipt_status st, const char* msg) {
     if (fatal != FIPT_OK) return;
     fatal = st;
     snprintf(fatal_msg, sizeof(fatal_msg), "%s", msg ? msg : "");
-    __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);    // the loop leaves after the items it holds
+    __atomic_store_n(&sh->stop, 1, __ATOMIC_RELEASE);    // the loops leave after the items they hold
+    __atomic_store_n(&sh->stop_r, 1, __ATOMIC_RELEASE);
 }
 
 // After a fatal error no new work starts, and every unfinished request ends
@@ -639,17 +738,16 @@ void fipt_server::drain_after_fatal() {
     }
     pending.clear();
     if (loop_running && cudaEventQuery(loop_done) != cudaErrorNotReady) loop_running = false;
+    if (loop_r_running && cudaEventQuery(loop_r_done) != cudaErrorNotReady) loop_r_running = false;
     while (!publishes.empty() && cudaEventQuery(publishes.front().ev) != cudaErrorNotReady) {
         cudaEventDestroy(publishes.front().ev);
         publishes.pop_front();
     }
-    const bool device_quiet = !loop_running && publishes.empty();
+    const bool device_quiet = !loop_running && !loop_r_running && publishes.empty();
     for (auto& kv : reqs) {
         Req* q = kv.second;
         if (q->state == DONE || q->state == COPYING) continue;
         if (!device_quiet) continue;
-        if (q->state == LAUNCHED && q->r.kind == FIPT_REQ_RENDER &&
-            cudaEventQuery(q->run) == cudaErrorNotReady) continue;
         if (cudaEventQuery(q->h2d) == cudaErrorNotReady) continue;
         q->result = fatal;
         q->state = DONE;
@@ -661,6 +759,7 @@ void fipt_server::drain_after_fatal() {
                                      [&](uint64_t t) { return reqs[t]->state == DONE; }),
                       renders.end());
         open_chunks.clear();
+        open_rchunks.clear();
     }
     for (size_t i = 0; i < copying.size();) {
         Req* q = reqs[copying[i]];
@@ -682,8 +781,8 @@ void fipt_server::run() {
             drain_after_fatal();
             bool busy = false;
             for (auto& kv : reqs) busy = busy || kv.second->state != DONE;
-            if (stop && !busy && !loop_running && publishes.empty()) break;
-            if (!busy && !loop_running)
+            if (stop && !busy && !loop_running && !loop_r_running && publishes.empty()) break;
+            if (!busy && !loop_running && !loop_r_running)
                 cv_work.wait_for(lk, std::chrono::milliseconds(10));
             else {
                 lk.unlock();
@@ -692,18 +791,21 @@ void fipt_server::run() {
             }
             continue;
         }
-        if (loop_running) {
-            const cudaError_t e = cudaEventQuery(loop_done);
-            if (e != cudaErrorNotReady) {
-                loop_running = false;
-                if (e != cudaSuccess) {
-                    char m[200];
-                    snprintf(m, sizeof(m), "serving loop failed: %s", cudaGetErrorString(e));
-                    set_fatal(FIPT_ERR_CUDA, m);
-                    continue;
-                }
+        bool failed = false;
+        for (int k = 0; k < 2; ++k) {
+            bool& running = k == 0 ? loop_running : loop_r_running;
+            if (!running) continue;
+            const cudaError_t e = cudaEventQuery(k == 0 ? loop_done : loop_r_done);
+            if (e == cudaErrorNotReady) continue;
+            running = false;
+            if (e != cudaSuccess) {
+                char m[200];
+                snprintf(m, sizeof(m), "serving loop failed: %s", cudaGetErrorString(e));
+                set_fatal(FIPT_ERR_CUDA, m);
+                failed = true;
             }
         }
+        if (failed) continue;
         publish_landed();
         collect_chunks();
         finish_copies();
@@ -718,21 +820,27 @@ void fipt_server::run() {
             if (q->r.kind == FIPT_REQ_BAKE) {
                 if (q->r.n > 0) active.push_back(q->ticket);
                 else retire(q);
+            } else if (q->r.n > 0) {
+                renders.push_back(q->ticket);
             } else {
-                launch_render(q);
+                complete_empty_render(q);
             }
         }
         if (fatal != FIPT_OK) continue;
         maybe_reset_epoch();
+        stage_renders();
+        if (fatal != FIPT_OK) continue;
         stage_chunks();
         if (fatal != FIPT_OK) continue;
         publish_landed();
+        launch_render_loop();
+        if (fatal != FIPT_OK) continue;
         launch_loop();
         stop_idle_loop();
         const bool idle = pending.empty() && active.empty() && open_chunks.empty() && renders.empty() &&
-                          copying.empty() && publishes.empty();
-        if (stop && idle && !loop_running) break;
-        if (idle && !admitted && !loop_running) {
+                          open_rchunks.empty() && copying.empty() && publishes.empty();
+        if (stop && idle && !loop_running && !loop_r_running) break;
+        if (idle && !admitted && !loop_running && !loop_r_running) {
             cv_work.wait_for(lk, std::chrono::milliseconds(50));
         } else {
             lk.unlock();
@@ -749,32 +857,15 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
     FIPT_REQUIRE(max_batch_rays > 0 && chunk_points > 0 && chunk_points < ((int64_t)1 << 31),
                  "max_batch_rays and chunk_points must be positive");
     FIPT_CUDA(cudaSetDevice(ctx->device));
+    // the render loop takes kRenderBlocksPerSM block slots of every SM and
+    // the bake loop all the others its registers allow; asking also loads
+    // the loops' kernels
     int loop_bps = 0;
     {
-        // The loop takes as many block slots as leave room for one block of
-        // the largest render kernel, so render requests always run beside
-        // it: a block slot, warp slots, and registers in each of the SM's
-        // kSubPartitions quarters (warps are spread evenly over them, each
-        // with a quarter of the register file).
-        constexpr int kSubPartitions = 4;
-        int lw_regs = 0, lwarps = 0, rw_regs = 0, rwarps = 0, sm_regs = 0, sm_threads = 0, sm_blocks = 0;
-        fipt_status fs = serve_kernels_footprint(&lw_regs, &lwarps);
-        if (fs == FIPT_OK) fs = render_kernels_footprint(&rw_regs, &rwarps);
+        const fipt_status fs = serve_loop_blocks_per_sm(&loop_bps);
         if (fs != FIPT_OK) return fs;
-        FIPT_CUDA(cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device));
-        FIPT_CUDA(cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, ctx->device));
-        FIPT_CUDA(cudaDeviceGetAttribute(&sm_blocks, cudaDevAttrMaxBlocksPerMultiprocessor, ctx->device));
-        const int q_regs = sm_regs / kSubPartitions;
-        const int render_q = (rwarps + kSubPartitions - 1) / kSubPartitions * rw_regs;
-        int b = 0;
-        for (int c = 1; c < sm_blocks; ++c) {
-            const int lw = c * lwarps;
-            const bool fits = lw + rwarps <= sm_threads / 32 &&
-                              (lw + kSubPartitions - 1) / kSubPartitions * lw_regs + render_q <= q_regs;
-            if (fits) b = c;
-        }
-        FIPT_REQUIRE(b >= 1, "no room for the serving loop beside the render kernels");
-        loop_bps = b;
+        loop_bps -= kRenderBlocksPerSM;
+        FIPT_REQUIRE(loop_bps >= 1, "the serving loops do not fit on an SM");
     }
     fipt_server* s = new fipt_server();
     s->ctx = ctx;
@@ -800,18 +891,29 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&s->orphans[i], sizeof(long long) * max_orphans);
     if (e == cudaSuccess) e = cudaMalloc(&s->done_dev, sizeof(int32_t) * kQueue);
     if (e == cudaSuccess) e = cudaMemset(s->done_dev, 0, sizeof(int32_t) * kQueue);
+    if (e == cudaSuccess) e = cudaMalloc(&s->r_dev, sizeof(RenderChunk) * kQueue);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->r_host, sizeof(RenderChunk) * kQueue);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->pubr_host, sizeof(long long) * kQueue);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->rflag_host, sizeof(int32_t) * kQueue, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->rflag_dev, s->rflag_host, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&s->rdone_dev, sizeof(int32_t) * kQueue);
+    if (e == cudaSuccess) e = cudaMemset(s->rdone_dev, 0, sizeof(int32_t) * kQueue);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->loop, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->loop_r, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->zero_host, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->render, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->loop_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->copy_mark, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->loop_r_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         fipt_server_destroy(s);
         return fipt_check_cuda(e, "server create");
     }
     std::memset(s->sh, 0, sizeof(ServeShared));
+    *s->zero_host = 0;
     std::memset(s->flag_host, 0, sizeof(int32_t) * kQueue);
+    std::memset(s->rflag_host, 0, sizeof(int32_t) * kQueue);
     s->arena = new fipt_arena(s->budget);
     s->worker = std::thread([s] { s->run(); });
     *out = s;
@@ -870,7 +972,6 @@ extern "C" fipt_status fipt_server_submit(fipt_server* s, const fipt_request* r,
     cudaSetDevice(s->ctx->device);
     cudaEventCreateWithFlags(&q->h2d, cudaEventDisableTiming);
     cudaEventCreateWithFlags(&q->d2h, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&q->run, cudaEventDisableTiming);
     s->reqs[q->ticket] = q;
     *ticket = q->ticket;
     if (q->bytes > s->budget) {
@@ -935,7 +1036,6 @@ extern "C" fipt_status fipt_server_release(fipt_server* s, uint64_t ticket) {
     FIPT_REQUIRE(it->second->state == DONE, "request still running");
     cudaEventDestroy(it->second->h2d);
     cudaEventDestroy(it->second->d2h);
-    cudaEventDestroy(it->second->run);
     delete it->second;
     s->reqs.erase(it);
     return FIPT_OK;
@@ -979,20 +1079,24 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
         s->worker.join();
     }
     cudaSetDevice(s->ctx ? s->ctx->device : 0);
-    if (s->sh) __atomic_store_n(&s->sh->stop, 1, __ATOMIC_RELEASE);
+    if (s->sh) {
+        __atomic_store_n(&s->sh->stop, 1, __ATOMIC_RELEASE);
+        __atomic_store_n(&s->sh->stop_r, 1, __ATOMIC_RELEASE);
+    }
     if (s->loop) cudaStreamSynchronize(s->loop);
+    if (s->loop_r) cudaStreamSynchronize(s->loop_r);
     if (s->copy) cudaStreamSynchronize(s->copy);
     if (s->d2h) cudaStreamSynchronize(s->d2h);
-    if (s->render) cudaStreamSynchronize(s->render);
     for (auto& p : s->publishes) cudaEventDestroy(p.ev);
     for (auto& kv : s->reqs) {
         cudaEventDestroy(kv.second->h2d);
         cudaEventDestroy(kv.second->d2h);
-        cudaEventDestroy(kv.second->run);
         delete kv.second;
     }
     if (s->loop_done) cudaEventDestroy(s->loop_done);
     if (s->copy_mark) cudaEventDestroy(s->copy_mark);
+    if (s->loop_r_done) cudaEventDestroy(s->loop_r_done);
+    if (s->zero_host) cudaFreeHost(s->zero_host);
     cudaFree(s->q_dev);
     cudaFreeHost(s->q_host);
     cudaFreeHost(s->pub_host);
@@ -1001,14 +1105,19 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
     cudaFree(s->orphans[1]);
     cudaFree(s->done_dev);
     cudaFreeHost(s->flag_host);
+    cudaFree(s->r_dev);
+    cudaFreeHost(s->r_host);
+    cudaFreeHost(s->pubr_host);
+    cudaFreeHost(s->rflag_host);
+    cudaFree(s->rdone_dev);
     cudaFreeHost(s->sh);
     cudaFreeHost(s->status_host);
     cudaFree(s->status);
     cudaFree(s->arena_dev);
     if (s->loop) cudaStreamDestroy(s->loop);
+    if (s->loop_r) cudaStreamDestroy(s->loop_r);
     if (s->copy) cudaStreamDestroy(s->copy);
     if (s->d2h) cudaStreamDestroy(s->d2h);
-    if (s->render) cudaStreamDestroy(s->render);
     delete s->arena;
     delete s;
     return FIPT_OK;

@@ -9,6 +9,7 @@
 // triangle (48 B) reads are 16-byte vector loads through the read-only
 // path.
 #include "fipt_internal.cuh"
+#include "render_math.cuh"
 
 namespace {
 
@@ -472,29 +473,132 @@ __device__ __forceinline__ void st_relaxed_sys(long long* p, long long v) {
     asm volatile("st.relaxed.sys.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// The server's bake loop: resident warps take warp items (32 points of one
+// Takes the next published render item, if there is one, with a
+// compare-and-swap (render items are taken only when published, so no warp
+// ever waits on one); *nch = render descriptors published.
+__device__ __forceinline__ bool take_render_item(ServeCounters* ctr, long long* w, int* nch) {
+    unsigned long long h = (unsigned long long)ld_relaxed_gpu(reinterpret_cast<const long long*>(&ctr->head_r));
+    const unsigned long long avail = (unsigned long long)(ld_relaxed_gpu(&ctr->pub_r) >> FIPT_PUB_CHUNK_BITS);
+    while (h < avail) {
+        const unsigned long long old = atomicCAS(&ctr->head_r, h, h + 1);
+        if (old == h) {
+            *w = (long long)h;
+            *nch = (int)(ld_acquire_gpu(&ctr->pub_r) & ((1 << FIPT_PUB_CHUNK_BITS) - 1));
+            return true;
+        }
+        h = old;
+    }
+    return false;
+}
+
+// One render item: rows [512 i, 512 i + 512) of the request, as four
+// blocks of fipt_render::RENDER_BLOCK rows, each block's loss partial in
+// the order the render kernels sum it (the warp stands in for the block's
+// four warps one after the other).
+__device__ __forceinline__ void render_item(const RenderChunk& RC, int64_t il, int lane) {
+    using namespace fipt_render;
+    Grid g;
+    g.K = RC.K;
+#pragma unroll
+    for (int k = 0; k < FIPT_MAX_K; ++k) g.s[k] = RC.grid[k];
+    const int64_t nb = (RC.n + RENDER_BLOCK - 1) / RENDER_BLOCK;
+    constexpr int BLOCKS = FIPT_RENDER_ITEM_ROWS / RENDER_BLOCK;
+    for (int vb = 0; vb < BLOCKS; ++vb) {
+        const int64_t b = il * BLOCKS + vb;
+        if (b >= nb) break;
+        double part = 0.0;
+        for (int j = 0; j < RENDER_BLOCK / 32; ++j) {
+            const int64_t p = b * RENDER_BLOCK + j * 32 + lane;
+            float loss = 0.0f;
+            if (p < RC.n)
+                loss = render_point_fwd_grad(p, g, RC.Ld, RC.Ls0, RC.Ls1, RC.albedo, RC.rough, RC.metal, RC.Lgt,
+                                             nullptr, RC.Lr, RC.g_albedo, RC.g_rough, RC.g_metal);
+            part += (double)warp_sum_down(loss);
+        }
+        if (lane == 0) RC.partial[b] = part;
+    }
+}
+
+// The request's loss from its partials, in the order of the render
+// kernels' final sum (RENDER_SUM_THREADS strided sums, a shuffle per warp,
+// the warps in order); lane 0 returns it.
+__device__ __forceinline__ double render_loss(const RenderChunk& RC, int lane) {
+    using namespace fipt_render;
+    const int64_t nb = (RC.n + RENDER_BLOCK - 1) / RENDER_BLOCK;
+    double t = 0.0;
+    for (int j = 0; j < RENDER_SUM_THREADS / 32; ++j) {
+        double acc = 0.0;
+        for (int64_t i = j * 32 + lane; i < nb; i += RENDER_SUM_THREADS) acc += __ldcg(RC.partial + i);
+        t += warp_sum_down(acc);
+    }
+    return t;
+}
+
+// Lane 0 of a bake-loop warp: the warp's next bake item (an orphan of the
+// previous launch first, else the next from the counter), waited for until
+// it is published -> 1 with *w and *nch (descriptors published), or 0 when
+// the warp leaves: the host stopped the launch, or a warp waited
+// wait_polls naps without work (it then makes the whole launch leave); a
+// leaving warp records its item as an orphan.  Not inlined, so the bake
+// walk's register allocation carries none of this.
+__device__ __noinline__ int serve_take_bake(ServeShared* sh, ServeCounters* ctr,
+                                            const long long* __restrict__ orphan_in,
+                                            long long* __restrict__ orphan_out, int wait_polls, long long* w,
+                                            int* nch) {
+    if (ld_volatile_int(&ctr->quit) || ld_volatile_int(&sh->stop)) return 0;
+    long long held;
+    const int k = atomicAdd(&ctr->take_in, 1);
+    if (k < ctr->n_in) {
+        held = __ldcg(orphan_in + k);
+    } else {
+        held = (long long)atomicAdd(&ctr->head, 1ULL);
+        st_relaxed_sys(&sh->taken, held + 1);   // tells the scheduler how far the loop has got
+    }
+    int idle = 0;
+    unsigned nap = 256;
+    for (;;) {
+        if ((ld_relaxed_gpu(&ctr->pub) >> FIPT_PUB_CHUNK_BITS) > held) {
+            *nch = (int)(ld_acquire_gpu(&ctr->pub) & ((1 << FIPT_PUB_CHUNK_BITS) - 1));
+            *w = held;
+            return 1;
+        }
+        const bool give_up = ++idle > wait_polls;
+        if (give_up) atomicExch(&ctr->quit, 1);
+        if (give_up || ld_volatile_int(&ctr->quit) || ((idle & 7) == 0 && ld_volatile_int(&sh->stop))) {
+            orphan_out[atomicAdd(&ctr->n_out, 1)] = held;
+            return 0;
+        }
+        __nanosleep(nap);
+        if (nap < 32768) nap *= 2;
+    }
+}
+
+// The server's bake loop: resident warps take bake items (32 points of one
 // chunk, one lobe) in publication order from a device counter with one
 // atomicAdd each (no compare-and-swap retries, so thousands of warps do not
-// serialise on the counter), bake each exactly as k_bake would, and count it
-// done; the warp that completes a chunk raises the chunk's flag in
+// serialise on the counter), bake each exactly as k_bake would, and count
+// it done; the warp that completes a chunk raises the chunk's flag in
 // host-mapped memory, where the server's scheduler sees it without a copy.
-// The host publishes work by copying chunk descriptors to `chunks` and then
-// the published item and descriptor counts to ctr->pub, in that order on
-// one copy stream, so the loop polls device memory (never host memory,
+// The host publishes work by copying chunk descriptors to `chunks` and
+// then the published item and descriptor counts to ctr->pub, in that order
+// on one copy stream, so the loop polls device memory (never host memory,
 // whose system-scope loads would slow the warps still baking); each warp
 // that takes a new item writes how far it got to sh->taken, from which the
 // host decides how much more to publish.  A warp whose item is not
 // published yet polls with naps growing to 32 microseconds and reads the
-// count once more with acquire semantics before it uses the descriptor.  The launch ends as a
-// whole: when the host sets sh->stop (it has no work left, or it failed),
-// or when a warp has waited wait_polls naps (the host did not answer) and
-// sets ctr->quit, every warp leaves -- a waiting warp at once, recording
-// its item in `orphan_out`, a busy one after its item, without taking
-// another.  The next launch takes the orphans first (from `orphan_in`), so
-// no item is lost or taken twice, and no orphan waits behind warps that
-// keep running.  A descriptor is read
+// count once more with acquire semantics before it uses the descriptor.
+// The launch ends as a whole: when the host sets sh->stop (it has no work
+// left, or it failed), or when a warp has waited wait_polls naps in vain
+// (the host did not answer) and sets ctr->quit, every warp leaves -- a
+// waiting warp at once, recording its item in `orphan_out`, a busy one
+// after its item, without taking another.  The next launch takes the
+// orphans first (from `orphan_in`), so no item is lost or taken twice, and
+// no orphan waits behind warps that keep running.  A descriptor is read
 // only after its publication, and no cache line holds parts of two
-// descriptors, so L1 never serves one from before it was written.
+// descriptors, so L1 never serves one from before it was written.  Render
+// requests have a loop of their own (k_serve_render) beside this one: code
+// for them in this kernel cost the bake walk 7 % through its register
+// allocation.
 template <int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_serve_bake(const BakeChunk* __restrict__ chunks, ServeShared* sh, ServeCounters* ctr,
@@ -505,37 +609,14 @@ k_serve_bake(const BakeChunk* __restrict__ chunks, ServeShared* sh, ServeCounter
     const int lane = threadIdx.x & 31;
     int ci = 0;
     for (;;) {
+        int act = 0;
         long long w = -1;
         int nch = 0;
-        if (lane == 0 && !ld_volatile_int(&ctr->quit) && !ld_volatile_int(&sh->stop)) {
-            const int k = atomicAdd(&ctr->take_in, 1);
-            if (k < ctr->n_in) {
-                w = __ldcg(orphan_in + k);
-            } else {
-                w = (long long)atomicAdd(&ctr->head, 1ULL);
-                st_relaxed_sys(&sh->taken, w + 1);          // tells the scheduler how far the loop has got
-            }
-            int idle = 0;
-            unsigned nap = 256;
-            for (;;) {
-                if ((ld_relaxed_gpu(&ctr->pub) >> FIPT_PUB_CHUNK_BITS) > w) {
-                    nch = (int)(ld_acquire_gpu(&ctr->pub) & ((1 << FIPT_PUB_CHUNK_BITS) - 1));
-                    break;
-                }
-                const bool give_up = ++idle > wait_polls;
-                if (give_up) atomicExch(&ctr->quit, 1);
-                if (give_up || ld_volatile_int(&ctr->quit) || ((idle & 7) == 0 && ld_volatile_int(&sh->stop))) {
-                    orphan_out[atomicAdd(&ctr->n_out, 1)] = w;
-                    w = -1;
-                    break;
-                }
-                __nanosleep(nap);
-                if (nap < 32768) nap *= 2;
-            }
-        }
+        if (lane == 0) act = serve_take_bake(sh, ctr, orphan_in, orphan_out, wait_polls, &w, &nch);
+        act = __shfl_sync(FULL, act, 0);
         w = __shfl_sync(FULL, w, 0);
         nch = __shfl_sync(FULL, nch, 0);
-        if (w < 0) return;
+        if (act == 0) return;
         if (w < chunks[ci].warp_begin) ci = 0;              // an orphan from earlier
         while (ci + 1 < nch && chunks[ci + 1].warp_begin <= w) ++ci;
         const BakeChunk& C = chunks[ci];
@@ -551,6 +632,74 @@ k_serve_bake(const BakeChunk* __restrict__ chunks, ServeShared* sh, ServeCounter
             if (atomicAdd(done_count + ci, 1) == items - 1) {
                 __threadfence_system();
                 st_release_sys(done_flag + ci, 1);
+            }
+        }
+    }
+}
+
+// The server's render loop, resident beside the bake loop on a few block
+// slots per SM: its warps take render items (512 rows of one render
+// request) by compare-and-swap as the host publishes them (to `rchunks`,
+// then ctr->pub_r, on the copy stream), so a render request starts at once
+// whatever the bake loop holds; each item runs k_render_fwd_grad's
+// arithmetic and writes its blocks' loss partials, and the warp that
+// completes a request sums its loss in the render kernels' order, then
+// raises the request's flag in host-mapped memory.  Warps never hold an
+// item they cannot run, so they may leave one by one: when the host sets
+// sh->stop_r, or after wait_polls naps without a render item (ctr->quit_r
+// then tells the others); the host starts the loop again when new render
+// work is published.
+__global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
+k_serve_render(const RenderChunk* __restrict__ rchunks, ServeShared* sh, ServeCounters* ctr,
+               int32_t* __restrict__ rdone, int32_t* rflag, int wait_polls) {
+    constexpr unsigned FULL = 0xffffffffu;
+    static_assert(sizeof(RenderChunk) == 256, "one descriptor per pair of cache lines");
+    const int lane = threadIdx.x & 31;
+    int cr = 0;
+    for (;;) {
+        int act = 0;
+        long long w = -1;
+        int nch = 0;
+        if (lane == 0) {
+            int idle = 0;
+            unsigned nap = 256;
+            for (;;) {
+                if (ld_volatile_int(&ctr->quit_r) || ((idle & 7) == 0 && ld_volatile_int(&sh->stop_r))) break;
+                if (take_render_item(ctr, &w, &nch)) {
+                    act = 1;
+                    break;
+                }
+                if (++idle > wait_polls) {
+                    atomicExch(&ctr->quit_r, 1);
+                    break;
+                }
+                __nanosleep(nap);
+                if (nap < 32768) nap *= 2;
+            }
+        }
+        act = __shfl_sync(FULL, act, 0);
+        w = __shfl_sync(FULL, w, 0);
+        nch = __shfl_sync(FULL, nch, 0);
+        if (act == 0) return;
+        if (w < rchunks[cr].item_begin) cr = 0;
+        while (cr + 1 < nch && rchunks[cr + 1].item_begin <= w) ++cr;
+        const RenderChunk& RC = rchunks[cr];
+        render_item(RC, w - RC.item_begin, lane);
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence();
+            const int items = (int)((RC.n + FIPT_RENDER_ITEM_ROWS - 1) / FIPT_RENDER_ITEM_ROWS);
+            last = atomicAdd(rdone + cr, 1) == items - 1;
+        }
+        last = __shfl_sync(FULL, last, 0);
+        if (last) {                                      // every partial is written: the loss
+            __threadfence();
+            const double loss = render_loss(RC, lane);
+            if (lane == 0) {
+                *RC.loss = loss;
+                __threadfence_system();
+                st_release_sys(rflag + cr, 1);
             }
         }
     }
@@ -724,16 +873,28 @@ fipt_status launch_serve_bake(const BakeChunk* d_chunks, ServeShared* sh, ServeC
     return FIPT_OK;
 }
 
-fipt_status serve_kernels_footprint(int* warp_regs, int* warps) {
+fipt_status launch_serve_render(const RenderChunk* d_rchunks, ServeShared* sh, ServeCounters* ctr, int32_t* rdone,
+                                int32_t* rflag, int wait_polls, int blocks_per_sm, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    FIPT_CUDA(cudaGetDevice(&dev));
+    FIPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FIPT_LAUNCH(k_serve_render, (unsigned)(sms * blocks_per_sm), BAKE_THREADS, 0, st, d_rchunks, sh, ctr, rdone,
+                rflag, wait_polls);
+    FIPT_LAUNCHED("serve_render");
+    return FIPT_OK;
+}
+
+fipt_status serve_loop_blocks_per_sm(int* blocks) {
     const void* fns[] = {(const void*)k_serve_bake<0>, (const void*)k_serve_bake<1>,
-                         (const void*)k_serve_bake<2>, (const void*)k_serve_bake<3>};
-    *warp_regs = 0;
+                         (const void*)k_serve_bake<2>, (const void*)k_serve_bake<3>,
+                         (const void*)k_serve_render};
+    int b = 1 << 30;
     for (const void* f : fns) {
-        cudaFuncAttributes at;
-        FIPT_CUDA(cudaFuncGetAttributes(&at, f));
-        *warp_regs = std::max(*warp_regs, (at.numRegs * 32 + 255) / 256 * 256);
+        int occ = 0;
+        FIPT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, BAKE_THREADS, 0));
+        b = std::min(b, occ);
     }
-    *warps = BAKE_THREADS / 32;
+    *blocks = b;
     return FIPT_OK;
 }
 

@@ -1,6 +1,8 @@
-"""Serving loop (continuous batching over resident scenes): every request's
-result is bit-identical to a standalone bake / render of the same request
-(chunks keep request-local Philox counters), sampled served bake points
+"""Serving loop (continuous batching over resident scenes in one
+device-resident kernel): every request's result is bit-identical to a
+standalone bake / one-pass render of the same request (chunks keep
+request-local Philox counters; render items sum the loss in the render
+kernels' order), sampled served bake points
 agree with the FP64 oracle, requests from several scenes share batches,
 admission respects the HBM budget, waits time out instead of hanging, and a
 failed launch ends every request only once none of its work is in flight."""
@@ -92,8 +94,7 @@ def test_mixed_requests_equal_standalone_results(setup):
         got = srv.result(t)
         d = [x.cuda() for x in ins]
         sl = slice(first, first + n)
-        Lr, loss = F.render_fwd(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
-        ga, gr, gm = F.render_bwd(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
+        Lr, loss, (ga, gr, gm) = F.render_fwd_grad(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
         assert np.array_equal(got["Lr"].numpy(), Lr.cpu().numpy())
         assert got["loss"].item() == loss.item()
         for g, r in ((got["g_albedo"], ga), (got["g_rough"], gr), (got["g_metal"], gm)):
@@ -274,5 +275,49 @@ def test_ragged_chunks_and_mixed_levels_serve_identically(setup):
         assert got["Ls0"].shape[1] == len(g)
         for a, b in zip((got["Ld"], got["Ls0"], got["Ls1"]), ref):
             assert np.array_equal(a.numpy(), b.cpu().numpy())
+    srv.close()
+    F.context().sync_status()
+
+
+def test_renders_run_in_the_loop_ahead_of_bakes(setup):
+    """Render requests of 0 to 100,000 rows (item edges at multiples of 512
+    rows, loss blocks of 128) go through the resident loop while a large
+    bake runs: each equals the one-pass render bit for bit, loss included,
+    and, as render items are taken before bake items, they finish before
+    the bake does."""
+    F, scenes, meshes = setup
+    srv = F.Server(1 << 30, max_batch_rays=1 << 24, chunk_points=16384)
+    sid = srv.add_scene(scenes[1])
+    N = 120000
+    Ld, Ls0, Ls1 = [torch.from_numpy(a).cuda() for a in shading_tables(N, 6, seed=21)]
+    tab = srv.add_table(Ld, Ls0, Ls1, SIGMA)
+    qh = host_queries(F, surface_queries(meshes[1], 200000, seed=22))
+    tb = srv.submit_bake(sid, qh, SIGMA, 256, 256, seed=2, request_id=77)
+    jobs = []
+    for j, (first, n) in enumerate([(0, 0), (5, 1), (100, 127), (0, 128), (7, 511), (9, 512), (11, 513),
+                                    (200, 1537), (1000, 4096), (20000, 100000)]):
+        mp = material_params(n, seed=80 + j)
+        Lgt = (np.asarray(mp["albedo"]) * 0.5 + 0.1).astype(np.float32)
+        ins = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (mp["albedo"], mp["rough"], mp["metal"], Lgt)]
+        jobs.append((srv.submit_render(tab, first, *ins), first, n, ins))
+    for t, first, n, ins in jobs:
+        assert srv.wait(t) == 0
+        got = srv.result(t)
+        if n == 0:
+            assert got["loss"].item() == 0.0
+            continue
+        d = [x.cuda() for x in ins]
+        sl = slice(first, first + n)
+        Lr, loss, (ga, gr, gm) = F.render_fwd_grad(Ld[sl], Ls0[sl], Ls1[sl], SIGMA, d[0], d[1], d[2], d[3])
+        assert np.array_equal(got["Lr"].numpy(), Lr.cpu().numpy())
+        assert got["loss"].item() == loss.item()
+        for g, r in ((got["g_albedo"], ga), (got["g_rough"], gr), (got["g_metal"], gm)):
+            assert np.array_equal(g.numpy(), r.cpu().numpy())
+    assert srv.wait(tb) == 0
+    t_bake = srv.times(tb)[2]
+    assert max(srv.times(t)[2] for t, _, n, _ in jobs) < t_bake
+    ref = F.bake(scenes[1], qh.cuda(), SIGMA, 256, 256, seed=2, request_id=77)
+    assert np.array_equal(srv.result(tb)["Ld"].numpy(), ref[0].cpu().numpy())
     srv.close()
     F.context().sync_status()
