@@ -69,6 +69,7 @@ def _L():
         P, I64, I32, D, U64, U32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32)
         L.oracle_philox4x32_10.argtypes = [P, P, I64, P]
+        L.oracle_strat_uv.argtypes = [ctypes.c_int, P, P, P, I64, P, P]
         L.oracle_scene_create.argtypes = [P, I64, P, I64, P, P]
         L.oracle_scene_create.restype = P
         L.oracle_scene_destroy.argtypes = [P]
@@ -117,6 +118,19 @@ def philox4x32_10(ctr, key):
     out = np.empty_like(ctr)
     _L().oracle_philox4x32_10(_p(ctr), _p(key), len(ctr), _p(out))
     return out
+
+
+def strat_uv(S, s, r1, r2):
+    """The jittered stratification of a (point, lobe) pair's S lobe samples:
+    sample s in cell (s mod nx, s div nx) of an nx x ny grid over (u1, u2),
+    placed by its uniforms (r1, r2) -> (u1, u2)."""
+    s = _c(s, np.uint32).ravel()
+    r1 = _c(r1, np.float64).ravel()
+    r2 = _c(r2, np.float64).ravel()
+    u1 = np.empty_like(r1)
+    u2 = np.empty_like(r2)
+    _L().oracle_strat_uv(int(S), _p(s), _p(r1), _p(r2), len(s), _p(u1), _p(u2))
+    return u1, u2
 
 
 def uniforms24(words):

@@ -65,6 +65,42 @@ void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 /* A 32-bit output word -> uniform in [0,1): its top 24 bits times 2^-24. */
 static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
+/* Jittered stratification of the lobe samples at a query point (the
+ * paper fixes no sampler; this is the reading of its importance-sampled
+ * estimates used here).  The S samples of a (point, lobe) pair cover an
+ * nx x ny grid over (u1, u2), nx the largest divisor of S with nx^2 <= S
+ * and ny = S / nx: sample s lies in cell (s mod nx, s div nx), placed in
+ * it by the pair's own Philox uniforms.  Every cell holds one sample, each
+ * sample is uniform over [0,1)^2 and the pairs stay independent, so each
+ * estimate keeps its expectation and its variance does not grow. */
+static int strat_cols(int S)
+{
+    int nx = 1;
+    for (int d = 1; (int64_t)d * d <= S; ++d)
+        if (S % d == 0) nx = d;
+    return nx;
+}
+
+static void strat_uv(uint32_t s, int S, double* u1, double* u2)
+{
+    if (S <= 0) return;
+    const int nx = strat_cols(S), ny = S / nx;
+    const uint32_t i = s % (uint32_t)nx, j = s / (uint32_t)nx;
+    *u1 = ((double)i + *u1) / nx;
+    *u2 = ((double)j + *u2) / ny;
+}
+
+/* strat_uv over arrays (pins of the stratification). */
+void oracle_strat_uv(int S, const uint32_t* s, const double* r1, const double* r2, int64_t n, double* u1,
+                     double* u2)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        u1[k] = r1[k];
+        u2[k] = r2[k];
+        strat_uv(s[k], S, &u1[k], &u2[k]);
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Small vector helpers                                                 */
 /* ------------------------------------------------------------------ */
@@ -707,6 +743,7 @@ static void bake_point(bake_job* J, int64_t p)
         uint32_t ctr[4] = {pid, (uint32_t)s, 0u, J->request_id}, r[4];
         philox10(ctr, key, r);
         double u1 = u24(r[0]), u2 = u24(r[1]);
+        strat_uv((uint32_t)s, J->spp_d, &u1, &u2);
         double rad = sqrt(u1), phi = 2.0 * OPI * u2;
         double wi[3];
         to_world(tb, bb, n, rad * cos(phi), rad * sin(phi), sqrt(1.0 - u1), wi);
@@ -741,6 +778,7 @@ static void bake_point(bake_job* J, int64_t p)
             uint32_t ctr[4] = {pid, (uint32_t)s, (uint32_t)(k + 1), J->request_id}, r[4];
             philox10(ctr, key, r);
             double u1 = u24(r[0]), u2 = u24(r[1]);
+            strat_uv((uint32_t)s, J->spp_s, &u1, &u2);
             double cos2 = (1.0 - u1) / (1.0 + (a2 - 1.0) * u1);
             double ch = sqrt(cos2), sh = sqrt(fmax(0.0, 1.0 - cos2));
             double phi = 2.0 * OPI * u2;
@@ -1787,6 +1825,7 @@ static int sample_range(const refine_job* R, const double o[3], const double n[3
     /* the lobe sample at x, as in the bake */
     double u[4];
     philox_words(pid, s, lobe, R->request_id, R->seed, u);
+    strat_uv(s, lobe == 0 ? R->spp_d : R->spp_s, &u[0], &u[1]);
     double wi[3], W0 = 1.0, W1 = 0.0, pb = 0.0;
     int can_zero = 0, can_go = 1;
     if (lobe == 0) {
@@ -1921,6 +1960,7 @@ static void refine_point(refine_job* R, int64_t p)
             /* lobe sample at x, as in the bake */
             double u[4];
             philox_words(pid, (uint32_t)s, (uint32_t)lobe, R->request_id, R->seed, u);
+            strat_uv((uint32_t)s, Sn, &u[0], &u[1]);
             double wi[3], W0 = 1.0, W1 = 0.0, pb = 0.0;
             int valid = 1;
             if (lobe == 0) {

@@ -170,9 +170,15 @@ def test_white_furnace_specular_matches_quadrature(mu_o):
         se_b = se[0, 3 + 3 * K + 3 * k]
         # 1e-6 absolute: GGX's long tail carries ~alpha^2 of the mass at
         # probabilities a 65536-sample run rarely visits, which the batch
-        # standard error cannot see.
-        assert abs(est_a - L * A2) <= 4 * se_a + qerr_a + 1e-6, (s, est_a, A2, se_a)
-        assert abs(est_b - L * B2) <= 4 * se_b + qerr_b + 1e-6, (s, est_b, B2, se_b)
+        # standard error cannot see.  Likewise the samples whose reflected
+        # direction falls below the horizon and count zero: a share q of at
+        # most 1 - A - B, a handful of events in the run, so the bound adds
+        # their binomial standard error sqrt(q / N) (stratified samples
+        # leave little else for the batch error to show).
+        N = 16 * 4096
+        rare = np.sqrt(max(0.0, 1.0 - A2 - B2) / N)
+        assert abs(est_a - L * A2) <= 4 * (se_a + rare) + qerr_a + 1e-6, (s, est_a, A2, se_a)
+        assert abs(est_b - L * B2) <= 4 * (se_b + rare) + qerr_b + 1e-6, (s, est_b, B2, se_b)
         assert est_a + est_b <= 1.0 + 4 * (se_a + se_b) + 1e-7   # energy
 
 
@@ -266,3 +272,44 @@ def test_cornell_point_matches_brute_force_hemisphere_quadrature(idx):
         est = mean[0, 3 * j:3 * j + 3]
         err = se[0, 3 * j:3 * j + 3]
         assert np.all(np.abs(est - a) <= 4 * err + 2 * np.abs(a - b) + 1e-6), (j, est, a, b, err)
+
+
+@pytest.mark.parametrize("S", [1, 2, 7, 12, 16, 100, 128, 256, 4096])
+def test_lobe_samples_are_jittered_strata(S):
+    """A pair's S lobe samples cover an nx x ny grid over (u1, u2) with
+    nx * ny = S, one sample per cell (nx the largest divisor of S with
+    nx^2 <= S), each placed in its cell by its own uniforms, all in [0, 1)."""
+    s = np.arange(S, dtype=np.uint32)
+    c1, c2 = O.strat_uv(S, s, np.zeros(S), np.zeros(S))       # cell corners
+    x1, x2 = np.unique(c1), np.unique(c2)
+    nx, ny = len(x1), len(x2)
+    assert nx * ny == S and nx <= ny and S % nx == 0
+    assert all(S % d or d <= nx for d in range(1, int(np.sqrt(S)) + 1))  # nx the largest such divisor
+    assert np.allclose(x1, np.arange(nx) / nx) and np.allclose(x2, np.arange(ny) / ny)
+    cells = set(zip(np.rint(c1 * nx).astype(int), np.rint(c2 * ny).astype(int)))
+    assert len(cells) == S                                       # every cell exactly once
+    rng = np.random.default_rng(S)
+    r1, r2 = rng.random(S), rng.random(S)
+    r1[:2] = [0.0, 1.0 - 2.0 ** -24][:S]               # the extreme uniforms a Philox word gives
+    r2[:2] = [1.0 - 2.0 ** -24, 0.0][:S]
+    u1, u2 = O.strat_uv(S, s, r1, r2)
+    assert np.all((u1 >= 0) & (u1 < 1) & (u2 >= 0) & (u2 < 1))
+    assert np.array_equal(np.floor(u1 * nx), np.rint(c1 * nx)) and np.array_equal(np.floor(u2 * ny), np.rint(c2 * ny))
+    assert np.allclose(u1 - c1, r1 / nx) and np.allclose(u2 - c2, r2 / ny)
+
+
+def test_stratified_estimate_keeps_its_mean_and_lowers_its_variance():
+    """Over many independent pairs the stratified estimate of a smooth
+    integral over [0,1)^2 has the integral's mean and a far smaller spread
+    than independent samples."""
+    S, pairs = 64, 2000
+    rng = np.random.default_rng(3)
+    f = lambda a, b: np.sin(3 * a) * (1 + b * b)
+    exact = (1 - np.cos(3.0)) / 3 * (4.0 / 3)
+    s = np.tile(np.arange(S, dtype=np.uint32), pairs)
+    r1, r2 = rng.random(S * pairs), rng.random(S * pairs)
+    u1, u2 = O.strat_uv(S, s, r1, r2)
+    strat = f(u1, u2).reshape(pairs, S).mean(1)
+    iid = f(r1, r2).reshape(pairs, S).mean(1)
+    assert abs(strat.mean() - exact) < 4 * strat.std() / np.sqrt(pairs)
+    assert strat.std() < 0.35 * iid.std()          # 0.24 measured; independent samples give 1
