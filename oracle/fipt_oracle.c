@@ -81,13 +81,25 @@ static int strat_cols(int S)
     return nx;
 }
 
+/* The stratified uniform is formed in float32, fl(fl(cell + r) / n) capped
+ * at the largest float below 1, exactly as the kernels form it, so the
+ * uniforms stay bit-identical on both sides (r, a 24-bit uniform, is exact
+ * in float32; a sample at the far edge of its cell can round onto the next
+ * cell's boundary, about 2^-22 of them, a float32 quantisation like the
+ * 24-bit uniform's own). */
+static double strat_one(uint32_t cell, int n, double r)
+{
+    const float u = ((float)cell + (float)r) / (float)n;
+    return (double)fminf(u, 0x1.fffffep-1f);
+}
+
 static void strat_uv(uint32_t s, int S, double* u1, double* u2)
 {
     if (S <= 0) return;
     const int nx = strat_cols(S), ny = S / nx;
     const uint32_t i = s % (uint32_t)nx, j = s / (uint32_t)nx;
-    *u1 = ((double)i + *u1) / nx;
-    *u2 = ((double)j + *u2) / ny;
+    *u1 = strat_one(i, nx, *u1);
+    *u2 = strat_one(j, ny, *u2);
 }
 
 /* strat_uv over arrays (pins of the stratification). */

@@ -99,8 +99,34 @@ struct BakeArgs {
     uint32_t request_id;
     uint32_t point_base;
     int spp_d, spp_s, K;
+    int nx_d, nx_s;          // strata along u1 of the diffuse / specular samples (see strat_cols)
     float sigma[FIPT_MAX_K];
 };
+
+// Jittered strata of a (point, lobe) pair's S lobe samples: an nx x ny grid
+// over the sampling uniforms (u1, u2), nx the largest divisor of S with
+// nx^2 <= S, ny = S / nx; sample s lies in cell (s mod nx, s div nx).
+inline int strat_cols(int S) {
+    int nx = 1;
+    for (int d = 1; (int64_t)d * d <= S; ++d)
+        if (S % d == 0) nx = d;
+    return nx;
+}
+inline void set_strata(BakeArgs& A) {
+    A.nx_d = strat_cols(A.spp_d);
+    A.nx_s = strat_cols(A.spp_s);
+}
+
+// Sample s of S in its stratum: u1 = (s mod nx + r1)/nx, u2 = (s div nx +
+// r2)/ny, each one IEEE float32 addition and division (round to nearest)
+// capped below 1, so the FP64 oracle, forming them the same way, gets the
+// same bits.
+__device__ __forceinline__ void strat_uv(uint32_t s, int S, int nx, float& u1, float& u2) {
+    const uint32_t j = s / (uint32_t)nx, i = s - j * (uint32_t)nx;
+    const int ny = S / nx;
+    u1 = fminf(__fdiv_rn(__fadd_rn((float)i, u1), (float)nx), 0x1.fffffep-1f);
+    u2 = fminf(__fdiv_rn(__fadd_rn((float)j, u2), (float)ny), 0x1.fffffep-1f);
+}
 
 // A slice of one request's points for the server's resident bake loop.
 // 256-byte aligned and sized: a descriptor never shares a cache line with

@@ -348,8 +348,9 @@ k_rf_gen(SceneView sc, RfChunk C, RefineArgs R, RfState st) {
                         qshadow = true;
                     }
                 }
-                // the lobe sample at x (the stage-1 sampler)
-                const float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe, A);
+                // the lobe sample at x (the stage-1 sampler, stratified as there)
+                float4 u = u4(pid, (uint32_t)s, (uint32_t)lobe, A);
+                strat_uv((uint32_t)s, lobe == 0 ? A.spp_d : A.spp_s, lobe == 0 ? A.nx_d : A.nx_s, u.x, u.y);
                 float3 tb, bb;
                 onb(n.x, n.y, n.z, tb, bb);
                 float sn, cs;
@@ -801,6 +802,7 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
     R.A.spp_d = prm->spp_diffuse;
     R.A.spp_s = prm->spp_specular;
     R.A.K = prm->K;
+    set_strata(R.A);
     for (int k = 0; k < FIPT_MAX_K; ++k) R.A.sigma[k] = k < prm->K ? prm->sigma[k] : 1.0f;
     R.sigma_c = sigma_c;
     R.max_depth = max_depth;

@@ -472,6 +472,7 @@ void fipt_server::stage_chunks() {
             C.A.spp_d = P.spp_diffuse;
             C.A.spp_s = P.spp_specular;
             C.A.K = P.K;
+            set_strata(C.A);
             for (int k = 0; k < FIPT_MAX_K; ++k) C.A.sigma[k] = k < P.K ? P.sigma[k] : 1.0f;
             chunk_begin.push_back(warps_staged);
             warps_staged += items;

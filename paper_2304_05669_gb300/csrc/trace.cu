@@ -296,8 +296,9 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
             }
             while (s < S) {
                 const uint4 rnd = philox4x32_10(make_uint4(pid, (uint32_t)s, (uint32_t)lobe, A.request_id), A.key);
+                float u1 = u24f(rnd.x), u2 = u24f(rnd.y);
+                strat_uv((uint32_t)s, S, lobe == 0 ? A.nx_d : A.nx_s, u1, u2);
                 ++s;
-                const float u1 = u24f(rnd.x), u2 = u24f(rnd.y);
                 float sn, cs;
                 sincospif(2.0f * u2, &sn, &cs);
                 float dx, dy, dz;
@@ -808,6 +809,7 @@ extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
     A.spp_d = prm->spp_diffuse;
     A.spp_s = prm->spp_specular;
     A.K = prm->K;
+    set_strata(A);
     for (int k = 0; k < FIPT_MAX_K; ++k) A.sigma[k] = k < prm->K ? prm->sigma[k] : 1.0f;
     const int64_t warps = ((N + 31) / 32) * (1 + prm->K);
     const int64_t threads = warps * 32;
