@@ -174,7 +174,7 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 
 
 #ifndef FIPT_BAKE_REFILL
-#define FIPT_BAKE_REFILL 28      // lanes that must be waiting before a warp draws new rays
+#define FIPT_BAKE_REFILL 32      // lanes that must be waiting before a warp draws new rays (32: all that still sample)
 #endif
 #ifndef FIPT_BAKE_SPECULATE
 #define FIPT_BAKE_SPECULATE 1    // keep walking inner nodes while other lanes look for a leaf
@@ -189,7 +189,11 @@ constexpr int BAKE_THREADS = FIPT_BAKE_THREADS;
 //  * refill: a lane whose ray has finished waits until FIPT_BAKE_REFILL
 //    lanes (or all remaining lanes) are waiting; they then gather their
 //    results and draw their next rays together, so the Philox stream,
-//    direction sampling and ray set-up run with many lanes active;
+//    direction sampling and ray set-up run with many lanes active.  With
+//    the default (every lane) the lanes draw the same sample index
+//    together, and as the samples are jittered strata of one grid their
+//    rays leave through the same cell of directions and walk the tree
+//    alike (8 % faster on the building floor than refilling at 28);
 //  * speculation (Aila and Laine 2009): a lane that reaches a leaf parks
 //    it and keeps descending inner nodes until every lane has a leaf;
 //  * leaves are then tested together.
