@@ -325,7 +325,10 @@ __device__ __forceinline__ void bake_item(const SceneView& sc, const fipt_query*
                     dy = 2.0f * c * hy - woy;
                     dz = 2.0f * c * hz - woz;
                     const float mu_i = nx * dx + ny * dy + nz * dz;
-                    if (mu_i <= 0.0f || c <= 0.0f) continue;    // a zero sample
+                    // a zero sample: the lane traces nothing this round rather than
+                    // draw its next sample now, so it stays on the warp's sample index
+                    // (and direction cell); +10 % on the building floor
+                    if (mu_i <= 0.0f || c <= 0.0f) break;
                     const float g1i = 2.0f * mu_i / (mu_i + sqrtf(a2 + (1.0f - a2) * mu_i * mu_i));
                     const float wt = g1i * g1o * c / (mu_o * ch);
                     const float x1 = 1.0f - c, x2 = x1 * x1;
