@@ -334,9 +334,30 @@ def bake_params(sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0, poi
     return p
 
 
+def query_order(scene: Scene, q, stream=None):
+    """Indices of the query points sorted by the Morton code of their
+    positions (``fipt_query_order``) -> int32 [N] on the queries' device."""
+    q = _queries(q)
+    N = q.shape[0]
+    order = torch.empty(N, dtype=torch.int32, device=q.device)
+    if N == 0:
+        return order
+    nbytes = ctypes.c_size_t()
+    check(lib().fipt_query_order_workspace_size(N, ctypes.byref(nbytes)))
+    _b, ws = _workspace(nbytes.value, q.device)
+    check(lib().fipt_query_order(scene.handle, _ptr(q), N, _ptr(order), _ptr(ws), nbytes.value, _stream(stream)))
+    if stream is not None:             # the buffers outlive this call on that stream's work
+        _b.record_stream(stream)
+        order.record_stream(stream)
+    return order
+
+
 def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request_id=0,
-         point_base=0, stats=None, out=None, stream=None):
-    """Shading terms (Eq. 6-7) at the query points -> (Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3])."""
+         point_base=0, stats=None, out=None, stream=None, order=True):
+    """Shading terms (Eq. 6-7) at the query points -> (Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3]).
+    ``order``: True bakes the points in Morton order of their positions
+    (``query_order``; faster, same results), False in the given order, or
+    an int32 [N] CUDA permutation to use."""
     q = _queries(q)
     N = q.shape[0]
     K = len(sigma)
@@ -345,6 +366,14 @@ def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request
                torch.empty((N, K, 3), dtype=torch.float32, device=q.device),
                torch.empty((N, K, 3), dtype=torch.float32, device=q.device))
     p = bake_params(sigma, spp_diffuse, spp_specular, seed, request_id, point_base, stats)
+    perm = None
+    if order is True:
+        perm = query_order(scene, q, stream) if N > 0 else None
+    elif order is not None and order is not False:
+        perm = _need(order, torch.int32, "order", (N,))
+    p.order = perm.data_ptr() if perm is not None else None
+    if perm is not None and stream is not None:
+        perm.record_stream(stream)
     check(lib().fipt_bake(scene.handle, _ptr(q), N, ctypes.byref(p), _ptr(out[0]), _ptr(out[1]),
                           _ptr(out[2]), _stream(stream)))
     return out

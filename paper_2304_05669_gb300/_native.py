@@ -22,7 +22,8 @@ class BakeParams(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("request_id", ctypes.c_uint32),
                 ("point_base", ctypes.c_uint32), ("spp_diffuse", ctypes.c_int32),
                 ("spp_specular", ctypes.c_int32), ("K", ctypes.c_int32),
-                ("sigma", ctypes.c_float * FIPT_MAX_K), ("stats", ctypes.c_void_p)]
+                ("sigma", ctypes.c_float * FIPT_MAX_K), ("stats", ctypes.c_void_p),
+                ("order", ctypes.c_void_p)]
 
 
 class Request(ctypes.Structure):
@@ -62,6 +63,8 @@ SIGNATURES = {
     "fipt_compact_workspace_size": [I64, P],
     "fipt_compact_queries": [P, P, I64, I64, P, P, P, P, SZ, P],
     "fipt_bake": [P, P, I64, ctypes.POINTER(BakeParams), P, P, P, P],
+    "fipt_query_order_workspace_size": [I64, P],
+    "fipt_query_order": [P, P, I64, P, P, SZ, P],
     "fipt_render_workspace_size": [I64, P],
     "fipt_render_fwd": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P, SZ, P],
     "fipt_render_bwd": [P, P, P, I64, I32, P, P, P, P, P, P, P, P, P, P, P],

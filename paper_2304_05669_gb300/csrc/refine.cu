@@ -774,6 +774,7 @@ extern "C" fipt_status fipt_bake_refine(fipt_scene* s, const fipt_query* q, int6
                                         fipt_stream stream) {
     FIPT_REQUIRE(s && prm, "scene / params is NULL");
     FIPT_REQUIRE(s->has_materials, "fipt_scene_set_materials must be called before a refinement");
+    FIPT_REQUIRE(prm->order == nullptr, "params->order is for fipt_bake only");
     FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 32), "bad point count %lld", (long long)N);
     FIPT_REQUIRE(prm->K >= 1 && prm->K <= FIPT_MAX_K, "K must be in [1, %d]", FIPT_MAX_K);
     FIPT_REQUIRE(prm->spp_diffuse >= 1 && prm->spp_specular >= 1, "spp must be >= 1");

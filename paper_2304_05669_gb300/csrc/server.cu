@@ -951,8 +951,8 @@ extern "C" fipt_status fipt_server_submit(fipt_server* s, const fipt_request* r,
         FIPT_REQUIRE(r->target >= 0 && r->target < (int32_t)s->scenes.size(), "unknown scene %d",
                      r->target);
         FIPT_REQUIRE(r->params.K >= 1 && r->params.K <= FIPT_MAX_K && r->params.spp_diffuse >= 1 &&
-                     r->params.spp_specular >= 1 && r->params.stats == nullptr,
-                     "bad bake parameters (K, spp, stats must be NULL)");
+                     r->params.spp_specular >= 1 && r->params.stats == nullptr && r->params.order == nullptr,
+                     "bad bake parameters (K, spp; stats and order must be NULL)");
         for (int k = 0; k < r->params.K; ++k)
             FIPT_REQUIRE(r->params.sigma[k] > 0.0f && r->params.sigma[k] <= 1.0f, "sigma out of (0, 1]");
         FIPT_REQUIRE(r->n == 0 || (r->queries && r->Ld && r->Ls0 && r->Ls1), "NULL host buffer");

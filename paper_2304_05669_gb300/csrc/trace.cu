@@ -451,7 +451,7 @@ template <bool STATS, int FLAGS>
 __global__ void __launch_bounds__(BAKE_THREADS, FIPT_BAKE_MINB)
 k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
        float* __restrict__ Ld, float* __restrict__ Ls0, float* __restrict__ Ls1, int32_t* status,
-       unsigned long long* stats) {
+       unsigned long long* stats, const int32_t* __restrict__ order) {
     const int L = 1 + A.K;
     const int64_t g = blockIdx.x * (int64_t)BAKE_THREADS + threadIdx.x;
     const int64_t w = g >> 5;
@@ -459,7 +459,17 @@ k_bake(SceneView sc, const fipt_query* __restrict__ q, int64_t N, BakeArgs A,
     const int lobe = (int)(w % L);
     const int64_t p = (w / L) * 32 + lane;
     if ((w / L) * 32 >= N) return;          // whole warp past the end
-    bake_item<STATS, FLAGS>(sc, q, p, lobe, p < N, A, Ld, Ls0, Ls1, status, stats);
+    bool valid = p < N;
+    int64_t pq = p;                         // the query this slot bakes
+    if (order && valid) {
+        pq = order[p];
+        if (pq < 0 || pq >= N) {
+            atomicOr(status, FIPT_DEV_BAD_INDEX);
+            valid = false;
+            pq = 0;
+        }
+    }
+    bake_item<STATS, FLAGS>(sc, q, pq, lobe, valid, A, Ld, Ls0, Ls1, status, stats);
 }
 
 // ---------------------------------------------------------------- device-resident serving loop
@@ -713,6 +723,37 @@ k_serve_render(const RenderChunk* __restrict__ rchunks, ServeShared* sh, ServeCo
     }
 }
 
+// Bit k of a 10-bit value to bit 3k (room for the other two axes).
+__device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// Sort keys of the query points: the 30-bit Morton code of each position
+// in the scene's bounding box (1024 cells per axis); values = indices.
+__global__ void k_query_keys(const fipt_query* __restrict__ q, int64_t N, const SceneConst* __restrict__ cst,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float2* qp = reinterpret_cast<const float2*>(q + i);
+    const float2 a = qp[0], b = qp[1];
+    const float x[3] = {a.x, a.y, b.x};
+    uint32_t key = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const float ext = cst->hi[ax] - cst->lo[ax];
+        const float u = ext > 0.0f ? (x[ax] - cst->lo[ax]) / ext : 0.0f;
+        const float c = fminf(fmaxf(u * 1024.0f, 0.0f), 1023.0f);   // NaN -> 0
+        key |= spread3_10((uint32_t)c) << ax;
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
 __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key, int64_t n,
                          uint32_t* __restrict__ out) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -793,6 +834,54 @@ extern "C" fipt_status fipt_compact_queries(const fipt_query* in, const int32_t*
     return FIPT_OK;
 }
 
+namespace {
+struct OrderLayout {
+    uint32_t *keys, *keys_alt, *vals_alt, *hist;
+    size_t bytes;
+};
+OrderLayout carve_order(void* ws, int64_t N) {
+    Carver c{static_cast<char*>(ws), 0};
+    OrderLayout L;
+    L.keys = c.take<uint32_t>((size_t)N);
+    L.keys_alt = c.take<uint32_t>((size_t)N);
+    L.vals_alt = c.take<uint32_t>((size_t)N);
+    L.hist = c.take<uint32_t>(radix_sort_scratch_bytes(N) / sizeof(uint32_t) + 1);
+    L.bytes = c.off + 256;
+    return L;
+}
+}  // namespace
+
+extern "C" fipt_status fipt_query_order_workspace_size(int64_t N, size_t* bytes) {
+    FIPT_REQUIRE(bytes && N >= 0 && N < ((int64_t)1 << 31), "bad point count");
+    *bytes = carve_order(nullptr, N).bytes;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_query_order(fipt_scene* s, const fipt_query* q, int64_t N, int32_t* order,
+                                        void* workspace, size_t ws_bytes, fipt_stream stream) {
+    FIPT_REQUIRE(s, "scene is NULL");
+    FIPT_REQUIRE(N >= 0 && N < ((int64_t)1 << 31), "bad point count %lld", (long long)N);
+    if (N == 0) return FIPT_OK;
+    FIPT_REQUIRE(q && order, "NULL query / order array");
+    FIPT_REQUIRE(fipt_aligned(q, 8) && fipt_aligned(order, 4), "q must be 8-byte aligned, order 4-byte");
+    FIPT_REQUIRE(workspace && fipt_aligned(workspace, 256), "workspace must be 256-byte aligned");
+    const OrderLayout need = carve_order(nullptr, N);
+    if (ws_bytes < need.bytes)
+        return fipt_set_error(FIPT_ERR_WORKSPACE, "query order workspace %zu < %zu bytes", ws_bytes, need.bytes);
+    const OrderLayout L = carve_order(workspace, N);
+    FIPT_CUDA(cudaSetDevice(s->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t* vals = reinterpret_cast<uint32_t*>(order);
+    FIPT_LAUNCH(k_query_keys, blocks(N, 256), 256, 0, st, q, N, s->cst, L.keys, vals);
+    FIPT_LAUNCHED("query order keys");
+    uint32_t *sk = nullptr, *sv = nullptr;
+    const fipt_status r = radix_sort_pairs<uint32_t>(L.keys, L.keys_alt, vals, L.vals_alt, L.hist, N, 32, st,
+                                                     &sk, &sv);
+    if (r != FIPT_OK) return r;
+    if (sv != vals) FIPT_CUDA(cudaMemcpyAsync(order, sv, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+    return FIPT_OK;
+}
+
 extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
                                  const fipt_bake_params* prm, float* Ld, float* Ls0, float* Ls1,
                                  fipt_stream stream) {
@@ -806,8 +895,8 @@ extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
     if (N == 0) return FIPT_OK;
     FIPT_REQUIRE(q && Ld && Ls0 && Ls1, "NULL query / output array");
     FIPT_REQUIRE(fipt_aligned(q, 8) && fipt_aligned(Ld, 4) && fipt_aligned(Ls0, 4) &&
-                 fipt_aligned(Ls1, 4) && fipt_aligned(prm->stats, 8),
-                 "q must be 8-byte aligned, outputs 4-byte");
+                 fipt_aligned(Ls1, 4) && fipt_aligned(prm->stats, 8) && fipt_aligned(prm->order, 4),
+                 "q must be 8-byte aligned, outputs and order 4-byte");
     FIPT_CUDA(cudaSetDevice(s->ctx->device));
     BakeArgs A;
     A.key = make_uint2((uint32_t)prm->seed, (uint32_t)(prm->seed >> 32));
@@ -827,7 +916,7 @@ extern "C" fipt_status fipt_bake(fipt_scene* s, const fipt_query* q, int64_t N,
     unsigned long long* stats = prm->stats;
 #define FIPT_BAKE_CASE(ST, FL)                                                                   \
     FIPT_LAUNCH((k_bake<ST, FL>), nb, BAKE_THREADS, 0, st, sv, q, N, A, Ld, Ls0, Ls1, s->ctx->status, \
-                stats)
+                stats, prm->order)
     if (stats) {
         switch (flags) {
             case 0: FIPT_BAKE_CASE(true, 0); break;

@@ -212,3 +212,45 @@ def test_bench_inputs_sampled(fipt, wl):
         r = S.bake(one, SIGMA, spp, spp, seed=0, request_id=0, point_base=int(i), eta=ETA_BAKE)
         flat[j], lo[j], hi[j], namb[j] = r["flat"][0], r["lo"][0], r["hi"][0], r["n_amb"][0]
     print(check_bake(g[idx], {"flat": flat, "lo": lo, "hi": hi, "n_amb": namb}))
+
+
+def test_query_order_is_a_permutation_and_changes_no_result():
+    """fipt_query_order returns a permutation of [0, N) sorted by the Morton
+    code of the positions (checked on the host, from the scene box), and a
+    bake in that order, in the given order or in a random order gives the
+    same bits: a point's result depends on its own index only.  An order
+    with an entry outside [0, N) is reported (FIPT_DEV_BAD_INDEX) and that
+    slot bakes nothing."""
+    import paper_2304_05669_gb300 as F
+    from workloads import procedural_room, surface_queries
+    m = procedural_room(1)
+    sc = F.Scene.from_mesh(m)
+    q = surface_queries(m, 20001, seed=41)
+    qd = F.pack_queries(*[torch.from_numpy(np.ascontiguousarray(q[k])).cuda() for k in ("x", "n", "wo", "tri")])
+    order = F.query_order(sc, qd).cpu().numpy()
+    assert np.array_equal(np.sort(order), np.arange(len(order)))
+    x = q["x"].astype(np.float32)
+    lo, hi = m.V.min(0).astype(np.float32), m.V.max(0).astype(np.float32)
+    cell = np.clip(((x - lo) / (hi - lo) * np.float32(1024)).astype(np.int64), 0, 1023)
+    key = np.zeros(len(x), np.int64)
+    for b in range(10):
+        for a in range(3):
+            key |= ((cell[:, a] >> b) & 1) << (3 * b + a)
+    ks = key[order]
+    assert np.all(np.diff(ks) >= 0)                                  # sorted by code
+    tie = np.diff(ks) == 0
+    assert np.all(np.diff(order)[tie] > 0)                           # stable
+    ref = F.bake(sc, qd, SIGMA, 8, 8, seed=3, order=False)
+    for o in (True, torch.from_numpy(np.random.default_rng(2).permutation(len(x)).astype(np.int32)).cuda()):
+        got = F.bake(sc, qd, SIGMA, 8, 8, seed=3, order=o)
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+    F.context().sync_status()
+    bad = torch.arange(len(x), dtype=torch.int32, device="cuda")
+    bad[7] = len(x) + 5
+    out = [t.fill_(-1.0) for t in (torch.empty_like(ref[0]), torch.empty_like(ref[1]), torch.empty_like(ref[2]))]
+    F.bake(sc, qd, SIGMA, 8, 8, seed=3, order=bad, out=out)
+    with pytest.raises(F.FiptError):
+        F.context().sync_status()
+    assert torch.all(out[0][7] == -1.0)                              # slot 7 baked nothing
+    assert torch.equal(out[0][8:], ref[0][8:])
