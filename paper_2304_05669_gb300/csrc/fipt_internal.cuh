@@ -134,8 +134,9 @@ __device__ __forceinline__ void strat_uv(uint32_t s, int S, int nx, float& u1, f
 // without meeting a line cached before that descriptor was written.
 struct alignas(256) BakeChunk {
     SceneView sc;
-    const fipt_query* q;     // the chunk's first query
-    float *Ld, *Ls0, *Ls1;   // the chunk's first output rows
+    const fipt_query* q;     // the chunk's first query (the request's first, with an order)
+    float *Ld, *Ls0, *Ls1;   // the chunk's first output rows (the request's first, with an order)
+    const int32_t* order;    // NULL, or the chunk's slots of the request's order: slot p bakes query order[p]
     int64_t n;               // points in the chunk
     int64_t warp_begin;      // first global warp of the chunk
     BakeArgs A;              // A.point_base = request-local index of the first point

@@ -49,6 +49,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <cmath>
 #include <vector>
 
 #include "fipt_internal.cuh"
@@ -67,6 +68,58 @@ static_assert(kQueue < (1 << FIPT_PUB_CHUNK_BITS), "descriptor count must fit be
 constexpr int kWaitPolls = 1 << 14;     // naps (about half a second) before a waiting warp ends the launch
 constexpr double kIdleStop = 1e-3;       // seconds the loops may idle before the scheduler stops them
 constexpr int kRenderBlocksPerSM = 2;    // block slots per SM of the render loop (the bake loop has the rest)
+constexpr size_t kOrderPool = (size_t)64 << 20;   // pinned bytes for bake orders on their way to the device
+constexpr int64_t kOrderMin = 64;        // smaller bakes keep their own order
+
+// Bit k of a 10-bit value to bit 3k.
+uint32_t spread3_10_host(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// The order fipt_query_order gives, on the host: the indices of the points
+// sorted (stably) by the 30-bit Morton code of their positions in the box
+// [lo, hi]; three 10-bit LSD radix passes.  Served bakes take their points
+// in this order so that a warp's points lie together (the results do not
+// depend on it).
+void host_query_order(const fipt_query* q, int64_t n, const float lo[3], const float hi[3], int32_t* out) {
+    std::vector<uint32_t> key((size_t)n), key2((size_t)n);
+    std::vector<int32_t> idx2((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t k = 0;
+        for (int a = 0; a < 3; ++a) {
+            const float ext = hi[a] - lo[a];
+            const float u = ext > 0.0f ? (q[i].x[a] - lo[a]) / ext : 0.0f;
+            const float c = std::fmin(std::fmax(u * 1024.0f, 0.0f), 1023.0f);
+            k |= spread3_10_host((uint32_t)c) << a;
+        }
+        key[(size_t)i] = k;
+        out[i] = (int32_t)i;
+    }
+    std::vector<int64_t> count(1025);
+    uint32_t* ks = key.data();
+    uint32_t* kd = key2.data();
+    int32_t* is = out;
+    int32_t* id = idx2.data();
+    for (int pass = 0; pass < 3; ++pass) {
+        const int sh = 10 * pass;
+        std::fill(count.begin(), count.end(), 0);
+        for (int64_t i = 0; i < n; ++i) ++count[((ks[i] >> sh) & 1023u) + 1];
+        for (int b = 0; b < 1024; ++b) count[b + 1] += count[b];
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t d = count[(ks[i] >> sh) & 1023u]++;
+            kd[d] = ks[i];
+            id[d] = is[i];
+        }
+        std::swap(ks, kd);
+        std::swap(is, id);
+    }
+    if (is != out) std::memcpy(out, is, sizeof(int32_t) * (size_t)n);
+}
 
 }  // namespace
 
@@ -183,7 +236,9 @@ struct Req {
     double* dloss = nullptr;
     void* dws = nullptr;
     size_t ws_bytes = 0;
-    int64_t next = 0;             // bake: next point not yet in a chunk
+    int64_t next = 0;             // bake: next slot of its order not yet in a chunk
+    int64_t order_off = -1;       // bake: its order in the pinned order pool, or -1 (points in given order)
+    int32_t* dorder = nullptr;    // bake: that order on the device
     int chunks_open = 0;          // bake: chunks staged and not yet done
     cudaEvent_t h2d = nullptr, d2h = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -248,6 +303,10 @@ struct fipt_server {
     bool loop_running = false, loop_r_running = false;
     double idle_since = -1.0;                  // when the running loop last ran out of work
     std::vector<fipt_scene*> scenes;
+    std::vector<SceneConst> scene_box;         // host copies of the scenes' constants (bounding box)
+    char* order_pool = nullptr;                // pinned: bake orders until their copy to the device lands
+    fipt_arena* order_arena = nullptr;         // its bookkeeping
+    std::vector<uint64_t> order_staged;        // requests holding a part of the pool
     std::vector<Table> tables;
     std::map<uint64_t, Req*> reqs;
     std::deque<uint64_t> pending;              // arrival order
@@ -279,6 +338,7 @@ struct fipt_server {
     void launch_loop();
     void launch_render_loop();
     void stop_idle_loop();
+    void release_orders();
     void drain_after_fatal();
     void set_fatal(fipt_status st, const char* msg);
 };
@@ -288,7 +348,7 @@ namespace {
 size_t request_bytes(const fipt_request& r, const fipt_server* s) {
     if (r.kind == FIPT_REQ_BAKE) {
         const size_t n = (size_t)r.n, K = (size_t)r.params.K;
-        return up256(n * sizeof(fipt_query)) + up256(n * 3 * 4) + 2 * up256(n * K * 3 * 4) + 256;
+        return up256(n * sizeof(fipt_query)) + up256(n * 3 * 4) + 2 * up256(n * K * 3 * 4) + up256(n * 4) + 256;
     }
     size_t ws = 0;
     fipt_render_workspace_size(r.n, &ws);
@@ -317,7 +377,10 @@ bool fipt_server::admit(Req* q) {
         q->dLd = c.take<float>(n * 3);
         q->dLs0 = c.take<float>(n * K * 3);
         q->dLs1 = c.take<float>(n * K * 3);
+        q->dorder = c.take<int32_t>(n);
         if (n) cudaMemcpyAsync(q->dq, r.queries, n * sizeof(fipt_query), cudaMemcpyHostToDevice, copy);
+        if (q->order_off >= 0)
+            cudaMemcpyAsync(q->dorder, order_pool + q->order_off, n * sizeof(int32_t), cudaMemcpyHostToDevice, copy);
     } else {
         q->da = c.take<float>(n * 3);
         q->dr = c.take<float>(n);
@@ -460,15 +523,24 @@ void fipt_server::stage_chunks() {
             BakeChunk& C = q_host[n_staged];
             fipt_scene* sc = scenes[q->r.target];
             C.sc = sc->view();
-            C.q = q->dq + q->next;
-            C.Ld = q->dLd + 3 * q->next;
-            C.Ls0 = q->dLs0 + q->next * P.K * 3;
-            C.Ls1 = q->dLs1 + q->next * P.K * 3;
+            if (q->order_off >= 0) {            // slots of the order: the request's own indices
+                C.q = q->dq;
+                C.Ld = q->dLd;
+                C.Ls0 = q->dLs0;
+                C.Ls1 = q->dLs1;
+                C.order = q->dorder + q->next;
+            } else {
+                C.q = q->dq + q->next;
+                C.Ld = q->dLd + 3 * q->next;
+                C.Ls0 = q->dLs0 + q->next * P.K * 3;
+                C.Ls1 = q->dLs1 + q->next * P.K * 3;
+                C.order = nullptr;
+            }
             C.n = c;
             C.warp_begin = warps_staged;
             C.A.key = make_uint2((uint32_t)P.seed, (uint32_t)(P.seed >> 32));
             C.A.request_id = P.request_id;
-            C.A.point_base = (uint32_t)q->next;
+            C.A.point_base = q->order_off >= 0 ? 0u : (uint32_t)q->next;
             C.A.spp_d = P.spp_diffuse;
             C.A.spp_s = P.spp_specular;
             C.A.K = P.K;
@@ -701,6 +773,19 @@ void fipt_server::launch_render_loop() {
     loop_r_running = true;
 }
 
+// Returns a request's part of the order pool once its copy to the device
+// has landed (or the request ended without being admitted).
+void fipt_server::release_orders() {
+    for (size_t i = 0; i < order_staged.size();) {
+        Req* q = reqs[order_staged[i]];
+        const bool done = q->state == DONE || (q->state != PENDING && cudaEventQuery(q->h2d) == cudaSuccess);
+        if (!done) { ++i; continue; }
+        order_arena->release((size_t)q->order_off, (size_t)q->r.n * sizeof(int32_t));
+        order_staged[i] = order_staged.back();
+        order_staged.pop_back();
+    }
+}
+
 // Stops the running loops once they have had no work for kIdleStop seconds,
 // so their resident blocks do not hold the SMs while the server is idle.
 void fipt_server::stop_idle_loop() {
@@ -810,6 +895,7 @@ void fipt_server::run() {
         publish_landed();
         collect_chunks();
         finish_copies();
+        release_orders();
         if (fatal != FIPT_OK) continue;
         // admit in arrival order while the arena has room
         bool admitted = false;
@@ -895,6 +981,7 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
     if (e == cudaSuccess) e = cudaMalloc(&s->r_dev, sizeof(RenderChunk) * kQueue);
     if (e == cudaSuccess) e = cudaMallocHost(&s->r_host, sizeof(RenderChunk) * kQueue);
     if (e == cudaSuccess) e = cudaMallocHost(&s->pubr_host, sizeof(long long) * kQueue);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->order_pool, kOrderPool);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->rflag_host, sizeof(int32_t) * kQueue, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->rflag_dev, s->rflag_host, 0);
     if (e == cudaSuccess) e = cudaMalloc(&s->rdone_dev, sizeof(int32_t) * kQueue);
@@ -916,6 +1003,7 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
     std::memset(s->flag_host, 0, sizeof(int32_t) * kQueue);
     std::memset(s->rflag_host, 0, sizeof(int32_t) * kQueue);
     s->arena = new fipt_arena(s->budget);
+    s->order_arena = new fipt_arena(kOrderPool);
     s->worker = std::thread([s] { s->run(); });
     *out = s;
     return FIPT_OK;
@@ -923,8 +1011,11 @@ extern "C" fipt_status fipt_server_create(fipt_ctx* ctx, size_t hbm_budget, int6
 
 extern "C" fipt_status fipt_server_add_scene(fipt_server* s, fipt_scene* scene, int32_t* id) {
     FIPT_REQUIRE(s && scene && id, "NULL argument");
+    SceneConst box;
+    FIPT_CUDA(cudaMemcpy(&box, scene->cst, sizeof(box), cudaMemcpyDeviceToHost));
     std::lock_guard<std::mutex> lk(s->mu);
     s->scenes.push_back(scene);
+    s->scene_box.push_back(box);
     *id = (int32_t)s->scenes.size() - 1;
     return FIPT_OK;
 }
@@ -965,10 +1056,27 @@ extern "C" fipt_status fipt_server_submit(fipt_server* s, const fipt_request* r,
     } else {
         return fipt_set_error(FIPT_ERR_INVALID_ARG, "unknown request kind %d", r->kind);
     }
+    // a bake's points in Morton order of their positions: a part of the
+    // pinned order pool (or none when it is full: the points keep their
+    // order), filled by this thread outside the lock
+    const double t_submit = now_s();
+    int64_t order_off = -1;
+    if (r->kind == FIPT_REQ_BAKE && r->n >= kOrderMin && request_bytes(*r, s) <= s->budget) {
+        size_t off = 0;
+        if (s->order_arena->alloc((size_t)r->n * sizeof(int32_t), &off)) {
+            order_off = (int64_t)off;
+            const SceneConst box = s->scene_box[r->target];
+            lk.unlock();
+            host_query_order(r->queries, r->n, box.lo, box.hi, reinterpret_cast<int32_t*>(s->order_pool + off));
+            lk.lock();
+        }
+    }
     Req* q = new Req();
     q->ticket = s->next_ticket++;
     q->r = *r;
-    q->t_submit = now_s();
+    q->t_submit = t_submit;
+    q->order_off = order_off;
+    if (order_off >= 0) s->order_staged.push_back(q->ticket);
     q->bytes = request_bytes(*r, s);
     cudaSetDevice(s->ctx->device);
     cudaEventCreateWithFlags(&q->h2d, cudaEventDisableTiming);
@@ -1109,6 +1217,8 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
     cudaFree(s->r_dev);
     cudaFreeHost(s->r_host);
     cudaFreeHost(s->pubr_host);
+    if (s->order_pool) cudaFreeHost(s->order_pool);
+    delete s->order_arena;
     cudaFreeHost(s->rflag_host);
     cudaFree(s->rdone_dev);
     cudaFreeHost(s->sh);

@@ -642,7 +642,9 @@ k_serve_bake(const BakeChunk* __restrict__ chunks, ServeShared* sh, ServeCounter
         const int64_t wl = w - C.warp_begin;
         const int lobe = (int)(wl % L);
         const int64_t p = (wl / L) * 32 + lane;
-        bake_item<false, FLAGS>(C.sc, C.q, p, lobe, p < C.n, C.A, C.Ld, C.Ls0, C.Ls1, status, nullptr);
+        const bool valid = p < C.n;
+        const int64_t pq = (C.order && valid) ? (int64_t)C.order[p] : p;
+        bake_item<false, FLAGS>(C.sc, C.q, pq, lobe, valid, C.A, C.Ld, C.Ls0, C.Ls1, status, nullptr);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
