@@ -602,6 +602,12 @@ fipt_status fipt_debug_divide(uint32_t n, const uint32_t* i, int64_t count, uint
  * the kernel's duration.  1 <= wait_polls <= 65536. */
 fipt_status fipt_debug_serve_wait_bound(int32_t wait_polls, int32_t* quit, int32_t* orphans,
                                         int32_t* warps, double* seconds);
+/* The order the server gives a bake's points (the order of
+ * fipt_query_order, computed on the host by a threaded radix sort): q [n]
+ * HOST, lo [3] / hi [3] HOST box -> order [n] HOST.  Check entry point; no
+ * counterpart in the paper. */
+fipt_status fipt_debug_host_query_order(const fipt_query* q, int64_t n, const float* lo, const float* hi,
+                                        int32_t* order);
 
 #ifdef __cplusplus
 }

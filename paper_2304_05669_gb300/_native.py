@@ -76,6 +76,7 @@ SIGNATURES = {
     "fipt_debug_philox": [P, P, I64, P, P],
     "fipt_debug_divide": [ctypes.c_uint32, P, I64, P, I32, P],
     "fipt_debug_serve_wait_bound": [I32, P, P, P, P],
+    "fipt_debug_host_query_order": [P, I64, P, P, P],
     "fipt_scene_set_materials": [P, P, P, P, P],
     "fipt_scene_set_environment": [P, P, I32, I32],
     "fipt_voxel_cache_workspace_size": [I64, P],

@@ -83,38 +83,72 @@ uint32_t spread3_10_host(uint32_t v) {
 
 // The order fipt_query_order gives, on the host: the indices of the points
 // sorted (stably) by the 30-bit Morton code of their positions in the box
-// [lo, hi]; three 10-bit LSD radix passes.  Served bakes take their points
-// in this order so that a warp's points lie together (the results do not
-// depend on it).
+// [lo, hi]; three 10-bit LSD radix passes, each split over up to eight
+// threads (per-thread histograms, then each thread scatters its own range
+// after all earlier ranges, which keeps the sort stable).  Served bakes take
+// their points in this order so that a warp's points lie together (the
+// results do not depend on it).
 void host_query_order(const fipt_query* q, int64_t n, const float lo[3], const float hi[3], int32_t* out) {
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(),
+                                                              n / 65536}));
     std::vector<uint32_t> key((size_t)n), key2((size_t)n);
     std::vector<int32_t> idx2((size_t)n);
-    for (int64_t i = 0; i < n; ++i) {
-        uint32_t k = 0;
-        for (int a = 0; a < 3; ++a) {
-            const float ext = hi[a] - lo[a];
-            const float u = ext > 0.0f ? (q[i].x[a] - lo[a]) / ext : 0.0f;
-            const float c = std::fmin(std::fmax(u * 1024.0f, 0.0f), 1023.0f);
-            k |= spread3_10_host((uint32_t)c) << a;
+    auto range = [&](int t, int64_t* b, int64_t* e) {
+        *b = n * t / T;
+        *e = n * (t + 1) / T;
+    };
+    auto parallel = [&](auto&& fn) {
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; ++t) th.emplace_back(fn, t);
+        fn(0);
+        for (auto& x : th) x.join();
+    };
+    parallel([&](int t) {
+        int64_t b, e;
+        range(t, &b, &e);
+        for (int64_t i = b; i < e; ++i) {
+            uint32_t k = 0;
+            for (int a = 0; a < 3; ++a) {
+                const float ext = hi[a] - lo[a];
+                const float u = ext > 0.0f ? (q[i].x[a] - lo[a]) / ext : 0.0f;
+                const float c = std::fmin(std::fmax(u * 1024.0f, 0.0f), 1023.0f);
+                k |= spread3_10_host((uint32_t)c) << a;
+            }
+            key[(size_t)i] = k;
+            out[i] = (int32_t)i;
         }
-        key[(size_t)i] = k;
-        out[i] = (int32_t)i;
-    }
-    std::vector<int64_t> count(1025);
+    });
+    std::vector<int64_t> count((size_t)T * 1024);
     uint32_t* ks = key.data();
     uint32_t* kd = key2.data();
     int32_t* is = out;
     int32_t* id = idx2.data();
     for (int pass = 0; pass < 3; ++pass) {
         const int sh = 10 * pass;
-        std::fill(count.begin(), count.end(), 0);
-        for (int64_t i = 0; i < n; ++i) ++count[((ks[i] >> sh) & 1023u) + 1];
-        for (int b = 0; b < 1024; ++b) count[b + 1] += count[b];
-        for (int64_t i = 0; i < n; ++i) {
-            const int64_t d = count[(ks[i] >> sh) & 1023u]++;
-            kd[d] = ks[i];
-            id[d] = is[i];
-        }
+        parallel([&](int t) {
+            int64_t b, e;
+            range(t, &b, &e);
+            int64_t* c = count.data() + (size_t)t * 1024;
+            std::fill(c, c + 1024, 0);
+            for (int64_t i = b; i < e; ++i) ++c[(ks[i] >> sh) & 1023u];
+        });
+        int64_t run = 0;                           // offsets: digit-major, thread-minor
+        for (int d = 0; d < 1024; ++d)
+            for (int t = 0; t < T; ++t) {
+                const int64_t c = count[(size_t)t * 1024 + d];
+                count[(size_t)t * 1024 + d] = run;
+                run += c;
+            }
+        parallel([&](int t) {
+            int64_t b, e;
+            range(t, &b, &e);
+            int64_t* c = count.data() + (size_t)t * 1024;
+            for (int64_t i = b; i < e; ++i) {
+                const int64_t d = c[(ks[i] >> sh) & 1023u]++;
+                kd[d] = ks[i];
+                id[d] = is[i];
+            }
+        });
         std::swap(ks, kd);
         std::swap(is, id);
     }
@@ -1231,6 +1265,16 @@ extern "C" fipt_status fipt_server_destroy(fipt_server* s) {
     if (s->d2h) cudaStreamDestroy(s->d2h);
     delete s->arena;
     delete s;
+    return FIPT_OK;
+}
+
+// ---------------------------------------------------------------- check of the host order
+extern "C" fipt_status fipt_debug_host_query_order(const fipt_query* q, int64_t n, const float* lo,
+                                                   const float* hi, int32_t* order) {
+    FIPT_REQUIRE(n >= 0 && n < ((int64_t)1 << 31), "bad point count");
+    if (n == 0) return FIPT_OK;
+    FIPT_REQUIRE(q && lo && hi && order, "NULL argument");
+    host_query_order(q, n, lo, hi, order);
     return FIPT_OK;
 }
 
