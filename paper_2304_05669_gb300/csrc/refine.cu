@@ -228,12 +228,17 @@ struct RfChunk {
     int64_t P;              // slots: n_pts * per_pt
 };
 
-// (point within the chunk, lobe, sample) of slot j: a point's slots are its
-// spp_d diffuse samples, then spp_s samples of each roughness level.
-__device__ __forceinline__ void slot_decode(int64_t j, const RefineArgs& R, int64_t& pc, int& lobe,
-                                            int& s) {
-    pc = j / R.per_pt;
-    int r = (int)(j - pc * R.per_pt);
+// (point within the chunk, lobe, sample) of slot j.  A point's samples in
+// order are its spp_d diffuse samples, then spp_s of each roughness level;
+// slot j holds sample r = j / n_pts of point j mod n_pts, so the 32 slots
+// of a warp are 32 points at one lobe and sample index: their first rays
+// leave through the same stratum of directions (reading 26) and walk the
+// tree alike.
+__device__ __forceinline__ void slot_decode(int64_t j, const RefineArgs& R, int64_t n_pts, int64_t& pc,
+                                            int& lobe, int& s) {
+    const int64_t rr = j / n_pts;
+    pc = j - rr * n_pts;
+    int r = (int)rr;
     if (r < R.A.spp_d) {
         lobe = 0;
         s = r;
@@ -279,7 +284,7 @@ k_rf_gen(SceneView sc, RfChunk C, RefineArgs R, RfState st) {
         if (j < C.P) {
             int64_t pc;
             int lobe, s;
-            slot_decode(j, R, pc, lobe, s);
+            slot_decode(j, R, C.n_pts, pc, lobe, s);
             const float2* qp = reinterpret_cast<const float2*>(C.q + pc);
             const float2 q0 = qp[0], q1 = qp[1], q2 = qp[2], q3 = qp[3], q4 = qp[4];
             float3 n = make_float3(q1.y, q2.x, q2.y), wo = make_float3(q3.x, q3.y, q4.x);
@@ -536,7 +541,7 @@ k_rf_shade(SceneView sc, RfChunk C, RefineArgs R, RfState st, int w) {
             j = act[i];
             int64_t pc;
             int lobe, s;
-            slot_decode(j, R, pc, lobe, s);
+            slot_decode(j, R, C.n_pts, pc, lobe, s);
             const uint32_t pid = A.point_base + (uint32_t)(C.p0 + pc);
             float4 C0 = st.c0[j], C1 = st.c1[j], LW = st.lw[j];
             // the slot's other records, loaded together whether or not a ray
@@ -681,15 +686,16 @@ k_rf_reduce(RfChunk C, RefineArgs R, RfState st, float* __restrict__ Ld, float* 
     const int K = R.A.K, L = 1 + K;
     const int64_t t = blockIdx.x * (int64_t)RF_SHADE_THREADS + threadIdx.x;
     if (t >= C.n_pts * L) return;
-    const int64_t pc = t / L;
-    const int lobe = (int)(t - pc * L);
+    const int lobe = (int)(t / C.n_pts);          // neighbouring threads: neighbouring points
+    const int64_t pc = t - lobe * C.n_pts;
     const int64_t p = C.p0 + pc;
     const int S = lobe == 0 ? R.A.spp_d : R.A.spp_s;
-    const int64_t j0 = pc * R.per_pt + (lobe == 0 ? 0 : R.A.spp_d + (int64_t)(lobe - 1) * R.A.spp_s);
+    const int64_t r0 = lobe == 0 ? 0 : R.A.spp_d + (int64_t)(lobe - 1) * R.A.spp_s;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f, a4 = 0.0f, a5 = 0.0f;
     float* ps = PER_SAMPLE ? per_sample + (size_t)(p * L + lobe) * R.smax * 6 : nullptr;
     for (int s = 0; s < S; ++s) {
-        const float4 x = st.c0[j0 + s], y = st.c1[j0 + s];
+        const int64_t j = (r0 + s) * C.n_pts + pc;
+        const float4 x = st.c0[j], y = st.c1[j];
         a0 += x.x; a1 += x.y; a2 += x.z;
         a3 += y.x; a4 += y.y; a5 += y.z;
         if (PER_SAMPLE) {
