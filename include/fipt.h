@@ -566,6 +566,14 @@ fipt_status fipt_server_get_stats(fipt_server* srv, fipt_server_stats* out);
  * of either loop) the following one fails with FIPT_ERR_CUDA on the host
  * instead of reaching the device. */
 fipt_status fipt_server_inject_launch_failure(fipt_server* srv, int64_t after_launches);
+/* Test hook (host only): a request's input copies (at admission) and its
+ * output copies (at completion) each count as one copy step; after
+ * `after_steps` more steps, the next one is treated as refused, as if one
+ * of its cudaMemcpyAsync calls had returned an error.  A request whose copy
+ * step is refused -- injected or real -- ends with FIPT_ERR_CUDA once what
+ * it did enqueue has completed, without running if its inputs were
+ * refused; other requests and the server go on. */
+fipt_status fipt_server_inject_copy_failure(fipt_server* srv, int64_t after_steps);
 /* Cancels requests not yet admitted (result FIPT_ERR_NOT_FOUND), drains
  * admitted work, joins the scheduler and frees the arena. */
 fipt_status fipt_server_destroy(fipt_server* srv);

@@ -733,6 +733,13 @@ class Server:
         ones fails (FIPT_ERR_CUDA) on the host, as a failed launch would."""
         check(lib().fipt_server_inject_launch_failure(self.handle, int(after_launches)))
 
+    def inject_copy_failure(self, after_steps: int = 0):
+        """Test hook: after ``after_steps`` more request copy steps (a
+        request's inputs at admission, its outputs at completion), the next
+        one is refused on the host as a failed copy call would be; that
+        request ends with FIPT_ERR_CUDA and the server goes on."""
+        check(lib().fipt_server_inject_copy_failure(self.handle, int(after_steps)))
+
     def stats(self):
         s = ServerStats()
         check(lib().fipt_server_get_stats(self.handle, ctypes.byref(s)))

@@ -99,6 +99,7 @@ SIGNATURES = {
     "fipt_server_release": [P, U64],
     "fipt_server_get_stats": [P, P],
     "fipt_server_inject_launch_failure": [P, I64],
+    "fipt_server_inject_copy_failure": [P, I64],
     "fipt_server_destroy": [P],
     "fipt_arena_create": [SZ, P],
     "fipt_arena_alloc": [P, SZ, P],

@@ -356,6 +356,7 @@ struct fipt_server {
     std::thread worker;
     fipt_status fatal = FIPT_OK;
     int64_t fail_after = -1;                   // test hook: stagings left before an injected failure
+    int64_t fail_copy_after = -1;              // test hook: request copy steps left before a refused one
     char fatal_msg[256] = "";
 
     void run();
@@ -397,6 +398,22 @@ int64_t rays_per_point(const fipt_bake_params& P) {
 
 }  // namespace
 
+// The first error of a request's copy calls (a refused copy enqueues
+// nothing and leaves no sticky error; the thread's last error is cleared so
+// that the next launch check does not take it for its own).
+static void note_copy(cudaError_t e, cudaError_t* first) {
+    if (e == cudaSuccess) return;
+    if (*first == cudaSuccess) *first = e;
+    cudaGetLastError();
+}
+
+// One request's input or output copies were refused: the request ends with
+// FIPT_ERR_CUDA (the server goes on) once what it did enqueue is done.
+static bool copy_step_fails(int64_t* fail_copy_after, cudaError_t ce) {
+    if (*fail_copy_after >= 0 && (*fail_copy_after)-- == 0) return true;   // injected
+    return ce != cudaSuccess;
+}
+
 bool fipt_server::admit(Req* q) {
     size_t off;
     if (!arena->alloc(q->bytes, &off)) return false;
@@ -405,6 +422,7 @@ bool fipt_server::admit(Req* q) {
     Carver c{q->base, 0};
     const fipt_request& r = q->r;
     const size_t n = (size_t)r.n;
+    cudaError_t ce = cudaSuccess;
     if (r.kind == FIPT_REQ_BAKE) {
         const size_t K = (size_t)r.params.K;
         q->dq = c.take<fipt_query>(n);
@@ -412,9 +430,10 @@ bool fipt_server::admit(Req* q) {
         q->dLs0 = c.take<float>(n * K * 3);
         q->dLs1 = c.take<float>(n * K * 3);
         q->dorder = c.take<int32_t>(n);
-        if (n) cudaMemcpyAsync(q->dq, r.queries, n * sizeof(fipt_query), cudaMemcpyHostToDevice, copy);
+        if (n) note_copy(cudaMemcpyAsync(q->dq, r.queries, n * sizeof(fipt_query), cudaMemcpyHostToDevice, copy), &ce);
         if (q->order_off >= 0)
-            cudaMemcpyAsync(q->dorder, order_pool + q->order_off, n * sizeof(int32_t), cudaMemcpyHostToDevice, copy);
+            note_copy(cudaMemcpyAsync(q->dorder, order_pool + q->order_off, n * sizeof(int32_t),
+                                      cudaMemcpyHostToDevice, copy), &ce);
     } else {
         q->da = c.take<float>(n * 3);
         q->dr = c.take<float>(n);
@@ -428,13 +447,14 @@ bool fipt_server::admit(Req* q) {
         fipt_render_workspace_size(r.n, &q->ws_bytes);
         q->dws = c.take<char>(q->ws_bytes);
         if (n) {
-            cudaMemcpyAsync(q->da, r.albedo, n * 12, cudaMemcpyHostToDevice, copy);
-            cudaMemcpyAsync(q->dr, r.rough, n * 4, cudaMemcpyHostToDevice, copy);
-            cudaMemcpyAsync(q->dm, r.metal, n * 4, cudaMemcpyHostToDevice, copy);
-            cudaMemcpyAsync(q->dLgt, r.Lgt, n * 12, cudaMemcpyHostToDevice, copy);
+            note_copy(cudaMemcpyAsync(q->da, r.albedo, n * 12, cudaMemcpyHostToDevice, copy), &ce);
+            note_copy(cudaMemcpyAsync(q->dr, r.rough, n * 4, cudaMemcpyHostToDevice, copy), &ce);
+            note_copy(cudaMemcpyAsync(q->dm, r.metal, n * 4, cudaMemcpyHostToDevice, copy), &ce);
+            note_copy(cudaMemcpyAsync(q->dLgt, r.Lgt, n * 12, cudaMemcpyHostToDevice, copy), &ce);
         }
     }
-    cudaEventRecord(q->h2d, copy);
+    note_copy(cudaEventRecord(q->h2d, copy), &ce);
+    if (copy_step_fails(&fail_copy_after, ce)) q->result = FIPT_ERR_CUDA;
     q->state = ADMITTED;
     q->t_admit = now_s();
     return true;
@@ -676,24 +696,29 @@ void fipt_server::collect_chunks() {
 // status word) on the output stream, so they never hold up a publication.
 void fipt_server::retire(Req* q) {
     const size_t n = (size_t)q->r.n;
+    cudaError_t ce = cudaSuccess;
     if (q->r.kind == FIPT_REQ_BAKE) {
         const size_t K = (size_t)q->r.params.K;
         if (n) {
-            cudaMemcpyAsync(q->r.Ld, q->dLd, n * 12, cudaMemcpyDeviceToHost, d2h);
-            cudaMemcpyAsync(q->r.Ls0, q->dLs0, n * K * 12, cudaMemcpyDeviceToHost, d2h);
-            cudaMemcpyAsync(q->r.Ls1, q->dLs1, n * K * 12, cudaMemcpyDeviceToHost, d2h);
+            note_copy(cudaMemcpyAsync(q->r.Ld, q->dLd, n * 12, cudaMemcpyDeviceToHost, d2h), &ce);
+            note_copy(cudaMemcpyAsync(q->r.Ls0, q->dLs0, n * K * 12, cudaMemcpyDeviceToHost, d2h), &ce);
+            note_copy(cudaMemcpyAsync(q->r.Ls1, q->dLs1, n * K * 12, cudaMemcpyDeviceToHost, d2h), &ce);
         }
     } else {
         if (n) {
-            if (q->r.Lr) cudaMemcpyAsync(q->r.Lr, q->dLr, n * 12, cudaMemcpyDeviceToHost, d2h);
-            if (q->r.loss) cudaMemcpyAsync(q->r.loss, q->dloss, 8, cudaMemcpyDeviceToHost, d2h);
-            if (q->r.g_albedo) cudaMemcpyAsync(q->r.g_albedo, q->dga, n * 12, cudaMemcpyDeviceToHost, d2h);
-            if (q->r.g_rough) cudaMemcpyAsync(q->r.g_rough, q->dgr, n * 4, cudaMemcpyDeviceToHost, d2h);
-            if (q->r.g_metal) cudaMemcpyAsync(q->r.g_metal, q->dgm, n * 4, cudaMemcpyDeviceToHost, d2h);
+            if (q->r.Lr) note_copy(cudaMemcpyAsync(q->r.Lr, q->dLr, n * 12, cudaMemcpyDeviceToHost, d2h), &ce);
+            if (q->r.loss) note_copy(cudaMemcpyAsync(q->r.loss, q->dloss, 8, cudaMemcpyDeviceToHost, d2h), &ce);
+            if (q->r.g_albedo)
+                note_copy(cudaMemcpyAsync(q->r.g_albedo, q->dga, n * 12, cudaMemcpyDeviceToHost, d2h), &ce);
+            if (q->r.g_rough)
+                note_copy(cudaMemcpyAsync(q->r.g_rough, q->dgr, n * 4, cudaMemcpyDeviceToHost, d2h), &ce);
+            if (q->r.g_metal)
+                note_copy(cudaMemcpyAsync(q->r.g_metal, q->dgm, n * 4, cudaMemcpyDeviceToHost, d2h), &ce);
         }
     }
-    cudaMemcpyAsync(status_host, status, sizeof(int32_t), cudaMemcpyDeviceToHost, d2h);
-    cudaEventRecord(q->d2h, d2h);
+    note_copy(cudaMemcpyAsync(status_host, status, sizeof(int32_t), cudaMemcpyDeviceToHost, d2h), &ce);
+    note_copy(cudaEventRecord(q->d2h, d2h), &ce);
+    if (copy_step_fails(&fail_copy_after, ce) && q->result == FIPT_OK) q->result = FIPT_ERR_CUDA;
     q->state = COPYING;
     copying.push_back(q->ticket);
 }
@@ -938,6 +963,12 @@ void fipt_server::run() {
             if (!admit(q)) break;
             pending.pop_front();
             admitted = true;
+            if (q->result != FIPT_OK) {     // its input copies were refused: nothing of it runs
+                cudaEventRecord(q->d2h, copy);          // after what it did enqueue
+                q->state = COPYING;
+                copying.push_back(q->ticket);
+                continue;
+            }
             if (q->r.kind == FIPT_REQ_BAKE) {
                 if (q->r.n > 0) active.push_back(q->ticket);
                 else retire(q);
@@ -1188,6 +1219,13 @@ extern "C" fipt_status fipt_server_inject_launch_failure(fipt_server* s, int64_t
     FIPT_REQUIRE(s && after_launches >= 0, "bad arguments");
     std::lock_guard<std::mutex> lk(s->mu);
     s->fail_after = after_launches;
+    return FIPT_OK;
+}
+
+extern "C" fipt_status fipt_server_inject_copy_failure(fipt_server* s, int64_t after_steps) {
+    FIPT_REQUIRE(s && after_steps >= 0, "bad arguments");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->fail_copy_after = after_steps;
     return FIPT_OK;
 }
 

@@ -180,6 +180,29 @@ def test_failed_launch_drains_in_flight_work(setup):
     F.context().sync_status()
 
 
+
+def test_refused_copy_ends_only_its_request(setup):
+    """A request whose copies are refused (injected on the host, as a failed
+    cudaMemcpyAsync call would be) ends with FIPT_ERR_CUDA -- not with
+    FIPT_OK over outputs that never arrived -- while the server and the
+    requests after it go on."""
+    F, scenes, meshes = setup
+    srv = F.Server(1 << 30, max_batch_rays=1 << 22, chunk_points=4096)
+    sid = srv.add_scene(scenes[1])
+    qs = [host_queries(F, surface_queries(meshes[1], 5000, seed=90 + i)) for i in range(3)]
+    srv.inject_copy_failure(0)            # the next request's input copies
+    t0 = srv.submit_bake(sid, qs[0], SIGMA, 8, 8, seed=2, request_id=0)
+    assert srv.wait(t0, 30.0) == 2
+    srv.inject_copy_failure(1)            # the next request's output copies (its inputs are step 0)
+    t1 = srv.submit_bake(sid, qs[1], SIGMA, 8, 8, seed=2, request_id=1)
+    assert srv.wait(t1, 30.0) == 2
+    t2 = srv.submit_bake(sid, qs[2], SIGMA, 8, 8, seed=2, request_id=2)
+    assert srv.wait(t2, 30.0) == 0
+    ref = F.bake(scenes[1], qs[2].cuda(), SIGMA, 8, 8, seed=2, request_id=2)
+    assert np.array_equal(srv.result(t2)["Ld"].numpy(), ref[0].cpu().numpy())
+    assert srv.stats()["bytes_in_use"] == 0            # the refused requests gave their space back
+    srv.close()
+
 def test_loop_wait_is_bounded():
     """The resident loop on a queue nothing publishes to ends by itself: a
     warp gives up after its bounded polls and the whole launch leaves, each
