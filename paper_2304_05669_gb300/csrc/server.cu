@@ -501,14 +501,21 @@ void fipt_server::stage_renders() {
         set_fatal(FIPT_ERR_CUDA, "injected launch failure");
         return;
     }
-    cudaMemcpyAsync(r_dev + first, r_host + first, sizeof(RenderChunk) * (size_t)count, cudaMemcpyHostToDevice,
-                    copy);
+    cudaError_t ce = cudaSuccess;
+    note_copy(cudaMemcpyAsync(r_dev + first, r_host + first, sizeof(RenderChunk) * (size_t)count,
+                              cudaMemcpyHostToDevice, copy), &ce);
     pubr_host[n_rpub] = (ritems_staged << FIPT_PUB_CHUNK_BITS) | n_rstaged;
-    cudaMemcpyAsync(&ctr->pub_r, pubr_host + n_rpub, sizeof(long long), cudaMemcpyHostToDevice, copy);
+    note_copy(cudaMemcpyAsync(&ctr->pub_r, pubr_host + n_rpub, sizeof(long long), cudaMemcpyHostToDevice, copy),
+              &ce);
     ++n_rpub;
-    Publish p;
-    cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming);
-    cudaEventRecord(p.ev, copy);
+    Publish p{};
+    note_copy(cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming), &ce);
+    if (ce == cudaSuccess) note_copy(cudaEventRecord(p.ev, copy), &ce);
+    if (ce != cudaSuccess) {
+        if (p.ev) cudaEventDestroy(p.ev);
+        set_fatal(FIPT_ERR_CUDA, "render descriptor copy failed");
+        return;
+    }
     p.warps = -1;
     publishes.push_back(p);
 }
@@ -634,15 +641,21 @@ void fipt_server::stage_chunks() {
         set_fatal(FIPT_ERR_CUDA, "injected launch failure");
         return;
     }
-    cudaMemcpyAsync(q_dev + first, q_host + first, sizeof(BakeChunk) * (size_t)count, cudaMemcpyHostToDevice,
-                    copy);
+    cudaError_t ce = cudaSuccess;
+    note_copy(cudaMemcpyAsync(q_dev + first, q_host + first, sizeof(BakeChunk) * (size_t)count,
+                              cudaMemcpyHostToDevice, copy), &ce);
     // then the count the loop polls, behind the descriptors on the same stream
     pub_host[n_pub] = ((long long)warps_staged << FIPT_PUB_CHUNK_BITS) | n_staged;
-    cudaMemcpyAsync(&ctr->pub, pub_host + n_pub, sizeof(long long), cudaMemcpyHostToDevice, copy);
+    note_copy(cudaMemcpyAsync(&ctr->pub, pub_host + n_pub, sizeof(long long), cudaMemcpyHostToDevice, copy), &ce);
     ++n_pub;
-    Publish p;
-    cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming);
-    cudaEventRecord(p.ev, copy);
+    Publish p{};
+    note_copy(cudaEventCreateWithFlags(&p.ev, cudaEventDisableTiming), &ce);
+    if (ce == cudaSuccess) note_copy(cudaEventRecord(p.ev, copy), &ce);
+    if (ce != cudaSuccess) {
+        if (p.ev) cudaEventDestroy(p.ev);
+        set_fatal(FIPT_ERR_CUDA, "bake descriptor copy failed");
+        return;
+    }
     p.warps = warps_staged;
     publishes.push_back(p);
     n_chunks += (uint64_t)count;
@@ -749,9 +762,11 @@ void fipt_server::maybe_reset_epoch() {
     std::memset(flag_host, 0, sizeof(int32_t) * (size_t)n_staged);
     std::memset(rflag_host, 0, sizeof(int32_t) * (size_t)n_rstaged);
     // on the copy stream, ahead of the next epoch's publications
-    cudaMemsetAsync(ctr, 0, sizeof(ServeCounters), copy);
-    if (n_staged) cudaMemsetAsync(done_dev, 0, sizeof(int32_t) * (size_t)n_staged, copy);
-    if (n_rstaged) cudaMemsetAsync(rdone_dev, 0, sizeof(int32_t) * (size_t)n_rstaged, copy);
+    cudaError_t ce = cudaSuccess;
+    note_copy(cudaMemsetAsync(ctr, 0, sizeof(ServeCounters), copy), &ce);
+    if (n_staged) note_copy(cudaMemsetAsync(done_dev, 0, sizeof(int32_t) * (size_t)n_staged, copy), &ce);
+    if (n_rstaged) note_copy(cudaMemsetAsync(rdone_dev, 0, sizeof(int32_t) * (size_t)n_rstaged, copy), &ce);
+    if (ce != cudaSuccess) set_fatal(FIPT_ERR_CUDA, "queue reset failed");
     published = 0;
     n_pub = 0;
     published_r = false;
