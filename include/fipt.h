@@ -94,9 +94,13 @@ typedef struct fipt_bake_params {
     unsigned long long* stats;
     /* fipt_bake only (NULL elsewhere): NULL, or a DEVICE int32 [N]
      * permutation of [0, N) (see fipt_query_order); launch slot p then
-     * bakes query order[p].  A point's result does not depend on it (its
-     * Philox counters and outputs use its own index); only the grouping of
-     * points into warps changes. */
+     * bakes query order[p].  A point's random numbers and outputs use its
+     * own index, so only the grouping of points into warps changes; that
+     * grouping sets when a lane's parked triangles lower its culling bound,
+     * which could change a hit only where float32 puts two triangles' hit
+     * distances within rounding of each other (grazing rays), as for
+     * fipt_scene_optimize; none has been observed on the room and floor
+     * workloads. */
     const int32_t* order;
 } fipt_bake_params;
 
@@ -480,7 +484,9 @@ fipt_status fipt_tri_error(const int32_t* tri, int64_t tri_stride, const float* 
  * A bake chunk keeps the request-local Philox counters (point_base = its
  * offset in the request) and a render item sums the loss in the render
  * kernels' order, so every result is bit-identical to a standalone
- * fipt_bake / fipt_render_fwd_grad of the same request.
+ * fipt_bake / fipt_render_fwd_grad of the same request (where a chunk's
+ * warps group points differently from the standalone bake, with the
+ * float32 caveat stated at fipt_bake_params.order).
  * All host buffers of a request must stay valid until it completes; pinned
  * (page-locked) buffers let copies overlap compute.  Every wait is bounded:
  * the scheduler polls events and the mapped flags; a bake warp that has
