@@ -86,8 +86,8 @@ uint32_t spread3_10_host(uint32_t v) {
 // [lo, hi]; three 10-bit LSD radix passes, each split over up to eight
 // threads (per-thread histograms, then each thread scatters its own range
 // after all earlier ranges, which keeps the sort stable).  Served bakes take
-// their points in this order so that a warp's points lie together (the
-// results do not depend on it).
+// their points in this order so that a warp's points lie together (a
+// point's random numbers and outputs use its own index).
 void host_query_order(const fipt_query* q, int64_t n, const float lo[3], const float hi[3], int32_t* out) {
     const int T = (int)std::max<int64_t>(1, std::min<int64_t>({8, (int64_t)std::thread::hardware_concurrency(),
                                                               n / 65536}));
