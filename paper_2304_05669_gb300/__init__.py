@@ -360,7 +360,8 @@ def bake(scene: Scene, q, sigma, spp_diffuse, spp_specular=None, seed=0, request
          point_base=0, stats=None, out=None, stream=None, order=True):
     """Shading terms (Eq. 6-7) at the query points -> (Ld [N,3], Ls0 [N,K,3], Ls1 [N,K,3]).
     ``order``: True bakes the points in Morton order of their positions
-    (``query_order``; faster, same results), False in the given order, or
+    (``query_order``; faster, the same results up to the float32 caveat of
+    ``fipt_bake_params.order``), False in the given order, or
     an int32 [N] CUDA permutation to use."""
     q = _queries(q)
     N = q.shape[0]
