@@ -115,11 +115,40 @@ def measured_sm_max():
     return 2070.0
 
 
+def _code_only(text):
+    """C/CUDA source without its comments and whitespace (string literals are
+    kept), so that the digest changes with the code and not with its notes."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif c.isspace():
+            i += 1
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def source_digest():
+    """Digest of the bake kernel's code and of the tree it walks (trace.cu,
+    fipt_internal.cuh, lbvh.cu, comments and whitespace left out): recorded
+    ncu counters are used only while it matches."""
     h = hashlib.sha256()
-    for f in ("trace.cu", "fipt_internal.cuh", "lbvh.cu"):      # the kernel and the tree it walks
-        with open(os.path.join(ROOT, "paper_2304_05669_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in ("trace.cu", "fipt_internal.cuh", "lbvh.cu"):
+        with open(os.path.join(ROOT, "paper_2304_05669_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode("utf-8"))
     return h.hexdigest()[:16]
 
 

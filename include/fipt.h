@@ -152,10 +152,11 @@ fipt_status fipt_scene_create(fipt_ctx* ctx, const float* V, int64_t nV, const i
  * surface area of its internal nodes (the SAH cost with one triangle per
  * leaf), if that is strictly cheaper.  Leaves and their boxes stay and
  * walks visit fewer nodes.  The closest hit, the (t, triangle) minimum, does
- * not depend on the tree, except where float32 leaves several triangles
- * within a few ulps of it (a ray along a shared edge): the culling bound
- * then depends on the visit order and another of those equally correct
- * hits may be returned.  The radix-tree ranges of fipt_scene_debug_export
+ * not depend on the tree, except where float32 puts several triangles'
+ * hit distances within rounding of one another (a ray along a shared edge;
+ * a ray grazing a large triangle, whose distance can round about 1e-4 of
+ * itself low): the culling bound then depends on the visit order and
+ * another of those equally correct hits may be returned.  The radix-tree ranges of fipt_scene_debug_export
  * no longer describe the tree afterwards.  Not an operation of the paper:
  * a property of the acceleration structure only. */
 fipt_status fipt_scene_optimize(fipt_scene* scene, int32_t passes, fipt_stream stream);

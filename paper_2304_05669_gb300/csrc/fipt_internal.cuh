@@ -354,9 +354,12 @@ __device__ __forceinline__ bool tri_intersect(const TraceRay& r, float4 p0, floa
     return t > 0.0f;
 }
 
-// Slab test of both child boxes of a node against [0, tmax]; conservative by
-// a few ulps so that float rounding never culls a box the triangle test
-// would hit.
+// Slab test of both child boxes of a node against [0, tmax], widened by a
+// few ulps for the rounding of the slab test itself.  The triangle test can
+// round a grazing ray's hit distance further below the box's entry (its
+// distance sums vertex offsets that cancel; up to about 1e-4 of it), so a
+// box may be culled while it holds a triangle whose float32 distance is
+// just below tmax: then another triangle's hit within that gap is kept.
 __device__ __forceinline__ void node_test(const TraceRay& r, const BvhNode& n, float tmax,
                                           bool& hit0, bool& hit1, float& t0, float& t1) {
     const float ox = r.ox, oy = r.oy, oz = r.oz;
